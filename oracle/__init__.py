@@ -1,0 +1,282 @@
+"""Plain CPU oracle for the BP decoders of Zhao & Lau (arXiv 1204.0334).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
+with the CUDA path in ``paper_1204_0334_gb300``; neither imports the other.
+
+The arithmetic lives in ``oracle.c`` (double precision, one frame at a time,
+the steps of Algorithm 1 / Algorithm 2 in the paper's order).  This module
+holds the definitional pieces that are plain matrix constructions:
+
+* ``qc_parity_check``  -- H of a QC-LDPC code, eq. (qcH): block (j, l) is the
+  p x p identity with its columns shifted cyclically right a_jl times
+  (row r has its one in column (r + a_jl) mod p); a_jl = -1 is the zero block
+  (Sec. IV-B-1 footnote on shift numbers).
+* ``csr_rows``         -- the edge order of the message store H: row by row,
+  left to right (Sec. IV-A).
+* ``ldpccc_unwrap``    -- H of the LDPC convolutional code derived from a QC
+  base by the three steps of Sec. II-D (partition into Lambda x Lambda
+  sub-blocks, split into lower / strictly-upper parts, unwrap and repeat).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into a shared library next to it (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.c_void_p
+        i32, u32, u64, f64 = ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
+        lib.or_philox4x32_10.argtypes = [P, P, P]
+        lib.or_philox4x32_10.restype = None
+        lib.or_channel_awgn.argtypes = [u64, u64, i32, i32, f64, u32, P, P]
+        lib.or_channel_awgn.restype = None
+        lib.or_variable_edges.argtypes = [i32, i32, P, P, P, P]
+        lib.or_sp_decode.argtypes = [i32, i32, P, P, i32, P, i32, i32, f64, i32, P, P, P, P, i32]
+        lib.or_ms_decode.argtypes = [i32, i32, P, P, i32, P, i32, i32, i32, P, P, P, P, i32]
+        lib.or_quantize.argtypes = [P, i32, i32, P]
+        lib.or_ldpccc_decode.argtypes = [i32, i32, P, P, i32, i32, i32, i32, i32, i32, P, f64, P, P, P,
+                                         P, i32, P, i32]
+        _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# --------------------------------------------------------------------------
+# Code construction (Sec. II-A, eq. qcH) and the edge order (Sec. IV-A)
+# --------------------------------------------------------------------------
+def circulant(a: int, p: int) -> np.ndarray:
+    """P^a: the p x p identity with its columns shifted cyclically right a times.
+
+    Row r holds its one in column (r + a) mod p.  a = -1 gives the zero matrix.
+    """
+    P = np.zeros((p, p), dtype=np.uint8)
+    if a >= 0:
+        for r in range(p):
+            P[r, (r + a) % p] = 1
+    return P
+
+
+def qc_parity_check(shifts, p: int) -> np.ndarray:
+    """Dense H = [P^{a_jl}] of a (J, L) QC-LDPC code, eq. (qcH)."""
+    shifts = np.asarray(shifts, dtype=np.int64)
+    J, L = shifts.shape
+    return np.block([[circulant(int(shifts[j, l]), p) for l in range(L)] for j in range(J)])
+
+
+def csr_rows(H) -> tuple[np.ndarray, np.ndarray]:
+    """Edges of H row by row, left to right: (row_ptr[M+1], col[E]) as int32."""
+    import scipy.sparse as sp
+
+    Hc = sp.csr_matrix(H)
+    Hc.sort_indices()
+    return Hc.indptr.astype(np.int32), Hc.indices.astype(np.int32)
+
+
+def variable_edges(row_ptr, col, N: int):
+    """LUT_v of Sec. IV-A: for each variable, its edge indices (ascending)."""
+    lib = _load()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    M = len(row_ptr) - 1
+    vptr = np.zeros(N + 1, dtype=np.int32)
+    vedge = np.zeros(max(int(row_ptr[-1]), 1), dtype=np.int32)
+    if lib.or_variable_edges(M, N, _p(row_ptr), _p(col), _p(vptr), _p(vedge)) != 0:
+        raise RuntimeError("or_variable_edges failed")
+    return vptr, vedge[: int(row_ptr[-1])]
+
+
+def design_rate(shifts) -> float:
+    """R = 1 - M/N counted over the non-zero block structure (the bound of Sec. II-A)."""
+    shifts = np.asarray(shifts)
+    J, L = shifts.shape
+    return 1.0 - J / L
+
+
+def sigma_from_ebn0(ebn0_db: float, rate: float) -> float:
+    """Noise std for unit-energy BPSK: Es = 1, Eb = Es / R, sigma^2 = N0/2."""
+    return math.sqrt(1.0 / (2.0 * rate * 10.0 ** (ebn0_db / 10.0)))
+
+
+# --------------------------------------------------------------------------
+# LDPC convolutional code derived from a QC base (Sec. II-D)
+# --------------------------------------------------------------------------
+def ldpccc_geometry(J: int, L: int, p: int) -> dict:
+    lam = math.gcd(J, L)
+    return {"Lambda": lam, "ms": lam - 1, "c": (L // lam) * p, "cb": (J // lam) * p, "b": ((L - J) // lam) * p}
+
+
+def ldpccc_unwrap(shifts, p: int, T: int):
+    """H_[0,T) of the derived LDPCCC as a sparse CSR matrix (T*cb x T*c).
+
+    Step 1: partition H_QC into Lambda x Lambda sub-blocks H_{i,j}.
+    Step 2: H^L keeps the sub-blocks on and below the diagonal, H^U the ones
+            strictly above it.
+    Step 3: paste H^U below H^L (H_base = [H^L; H^U]) and repeat H_base down
+            the diagonal, one copy every Lambda sub-block rows / columns.
+    The result is cut to the first T check layers and T frames.
+    """
+    import scipy.sparse as sp
+
+    shifts = np.asarray(shifts, dtype=np.int64)
+    J, L = shifts.shape
+    geo = ldpccc_geometry(J, L, p)
+    lam, c, cb = geo["Lambda"], geo["c"], geo["cb"]
+    H = sp.csr_matrix(qc_parity_check(shifts, p))
+    # step 1
+    sub = [[H[i * cb:(i + 1) * cb, j * c:(j + 1) * c] for j in range(lam)] for i in range(lam)]
+    zero = sp.csr_matrix((cb, c), dtype=np.uint8)
+    # step 2
+    HL = sp.bmat([[sub[i][j] if j <= i else zero for j in range(lam)] for i in range(lam)], format="csr")
+    HU = sp.bmat([[sub[i][j] if j > i else zero for j in range(lam)] for i in range(lam)], format="csr")
+    # step 3
+    Hbase = sp.vstack([HL, HU], format="coo")
+    rows, cols = [], []
+    copies = (T + lam - 1) // lam + 1
+    for k in range(copies):
+        r = Hbase.row + k * lam * cb
+        cc = Hbase.col + k * lam * c
+        keep = (r < T * cb) & (cc < T * c)
+        rows.append(r[keep])
+        cols.append(cc[keep])
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    Hc = sp.csr_matrix((np.ones(len(rows), dtype=np.uint8), (rows, cols)), shape=(T * cb, T * c))
+    Hc.sort_indices()
+    return Hc, geo
+
+
+# --------------------------------------------------------------------------
+# Generator and channel (Sec. II-B)
+# --------------------------------------------------------------------------
+def philox4x32_10(ctr, key) -> np.ndarray:
+    lib = _load()
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib.or_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def channel_awgn(seed: int, first_frame: int, nfr: int, N: int, sigma: float, tag: int = 0,
+                 return_g: bool = False):
+    """mu[nfr][N] (float32) of the all-zero codeword over BPSK/AWGN."""
+    lib = _load()
+    mu = np.zeros((nfr, N), dtype=np.float32)
+    g = np.zeros((nfr, N), dtype=np.float64) if return_g else None
+    lib.or_channel_awgn(seed, first_frame, nfr, N, sigma, tag, _p(mu), _p(g) if return_g else None)
+    return (mu, g) if return_g else mu
+
+
+# --------------------------------------------------------------------------
+# Decoders
+# --------------------------------------------------------------------------
+def sp_decode(row_ptr, col, N: int, mu, max_iter: int, early_stop: bool = False, clip: float = 30.0,
+              form: str = "phi", nthreads: int = 1):
+    """Sum-product BP, Algorithm 1, double precision.
+
+    Returns (post[nfr][N] float64, hard[nfr][N] uint8, iters[nfr], ok[nfr]).
+    """
+    lib = _load()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    mu = np.ascontiguousarray(mu, dtype=np.float32)
+    if mu.ndim == 1:
+        mu = mu[None, :]
+    nfr = mu.shape[0]
+    M = len(row_ptr) - 1
+    post = np.zeros((nfr, N), dtype=np.float64)
+    hard = np.zeros((nfr, N), dtype=np.uint8)
+    iters = np.zeros(nfr, dtype=np.int32)
+    ok = np.zeros(nfr, dtype=np.int32)
+    f = {"phi": 0, "tanh": 1}[form]
+    rc = lib.or_sp_decode(M, N, _p(row_ptr), _p(col), nfr, _p(mu), max_iter, int(early_stop), clip, f,
+                          _p(post), _p(hard), _p(iters), _p(ok), nthreads)
+    if rc != 0:
+        raise ValueError("or_sp_decode rejected its arguments")
+    return post, hard, iters, ok
+
+
+def quantize(mu, frac_bits: int = 2) -> np.ndarray:
+    lib = _load()
+    mu = np.ascontiguousarray(mu, dtype=np.float32)
+    q = np.zeros(mu.shape, dtype=np.int8)
+    lib.or_quantize(_p(mu), mu.size, frac_bits, _p(q))
+    return q
+
+
+def ms_decode(row_ptr, col, N: int, mu, max_iter: int, early_stop: bool = False, frac_bits: int = 2,
+              nthreads: int = 1):
+    """Integer min-sum.  Returns (post int32, hard uint8, iters, ok)."""
+    lib = _load()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    mu = np.ascontiguousarray(mu, dtype=np.float32)
+    if mu.ndim == 1:
+        mu = mu[None, :]
+    nfr = mu.shape[0]
+    M = len(row_ptr) - 1
+    post = np.zeros((nfr, N), dtype=np.int32)
+    hard = np.zeros((nfr, N), dtype=np.uint8)
+    iters = np.zeros(nfr, dtype=np.int32)
+    ok = np.zeros(nfr, dtype=np.int32)
+    rc = lib.or_ms_decode(M, N, _p(row_ptr), _p(col), nfr, _p(mu), frac_bits, max_iter, int(early_stop),
+                          _p(post), _p(hard), _p(iters), _p(ok), nthreads)
+    if rc != 0:
+        raise ValueError("or_ms_decode rejected its arguments")
+    return post, hard, iters, ok
+
+
+def ldpccc_decode(Hconv, geo: dict, T: int, I: int, mu, clip: float = 30.0, nthreads: int = 1,
+                  log_cap: int = 0):
+    """Pipelined BP of Algorithm 2 over T slots.
+
+    mu is [nstreams][T*c] (or [T*c]).  Returns (post, hard, decided[nstreams][T], log) where
+    post/hard are [nstreams][T*c]; frames F <= T - I*(ms+1) are decided.
+    """
+    lib = _load()
+    row_ptr = np.ascontiguousarray(Hconv.indptr, dtype=np.int32)
+    col = np.ascontiguousarray(Hconv.indices, dtype=np.int32)
+    c, cb, ms = geo["c"], geo["cb"], geo["ms"]
+    mu = np.ascontiguousarray(mu, dtype=np.float32)
+    if mu.ndim == 1:
+        mu = mu[None, :]
+    ns = mu.shape[0]
+    N = T * c
+    M = T * cb
+    post = np.zeros((ns, N), dtype=np.float64)
+    hard = np.zeros((ns, N), dtype=np.uint8)
+    decided = np.zeros((ns, T), dtype=np.uint8)
+    log = np.zeros((max(log_cap, 1), 4), dtype=np.int32)
+    log_n = np.zeros(1, dtype=np.int32)
+    rc = lib.or_ldpccc_decode(M, N, _p(row_ptr), _p(col), T, c, cb, ms, I, ns, _p(mu), clip, _p(post),
+                              _p(hard), _p(decided), _p(log) if log_cap else None, log_cap, _p(log_n), nthreads)
+    if rc < 0:
+        raise ValueError("or_ldpccc_decode rejected its arguments")
+    return post, hard, decided, log[: min(int(log_n[0]), log_cap)]

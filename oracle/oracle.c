@@ -1,0 +1,491 @@
+/*
+ * Plain CPU oracle for the batched BP decoders of Zhao & Lau,
+ * "Implementation of Decoders for LDPC Block Codes and LDPC Convolutional
+ * Codes Based on GPUs" (arXiv 1204.0334).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or
+ * call this file: only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark do.  It shares no code, header, table or constant generator
+ * with the CUDA path.
+ *
+ * Everything here is slow on purpose: one frame at a time, plain loops over
+ * the edge lists of a general sparse H, double precision, in the order the
+ * paper states the steps.  OpenMP only distributes independent frames
+ * (the paper's own multi-thread CPU decoder is an OpenMP loop, Sec. IV-C).
+ *
+ * Contents
+ *   or_philox4x32_10   counter-based generator (Salmon et al., SC'11)
+ *   or_channel_awgn    BPSK over AWGN, all-zero codeword, channel LLR
+ *                      (Sec. II-B: x = 1 - 2c, y = x + g, mu = 2y/sigma^2)
+ *   or_sp_decode       sum-product BP, Algorithm 1 (eqs. bphs, bpvs, bpd,
+ *                      hrddcs), phi-form or literal tanh-form check update
+ *   or_ms_decode       integer min-sum (fixed-point variant of the CN rule)
+ *   or_noms_forward /  normalized/offset min-sum with per-iteration,
+ *   or_noms_backward   per-circulant parameters, and its reverse-mode
+ *                      gradient (hand-derived)
+ *   or_ldpccc_decode   pipelined BP of the LDPC convolutional code derived
+ *                      from a QC base matrix, Algorithm 2 and Sec. IV-B-2
+ *
+ * Build: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC oracle.c -lm
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as   */
+/* easy as 1, 2, 3", SC'11).  Ten rounds of the two-multiplier S-box with a   */
+/* Weyl-sequence key schedule.                                               */
+/* ------------------------------------------------------------------------ */
+void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t prod_a = (uint64_t)0xD2511F53u * (uint64_t)c[0];
+        uint64_t prod_b = (uint64_t)0xCD9E8D57u * (uint64_t)c[2];
+        uint32_t hi_a = (uint32_t)(prod_a >> 32), lo_a = (uint32_t)prod_a;
+        uint32_t hi_b = (uint32_t)(prod_b >> 32), lo_b = (uint32_t)prod_b;
+        uint32_t n0 = hi_b ^ c[1] ^ k0;
+        uint32_t n1 = lo_b;
+        uint32_t n2 = hi_a ^ c[3] ^ k1;
+        uint32_t n3 = lo_a;
+        c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+    }
+    out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
+}
+
+/* A 32-bit Philox word -> uniform in (0,1), as an odd multiple of 2^-24     */
+/* so that the value is exact in binary32 as well as binary64.               */
+static double or_uniform(uint32_t x)
+{
+    return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0); /* 2^-23 */
+}
+
+/*
+ * Channel of Sec. II-B for the all-zero codeword: x_n = 1 - 2*0 = +1,
+ * y_n = x_n + sigma*g_n with g_n standard normal, mu_n = 2 y_n / sigma^2.
+ * g_n comes from Box-Muller on two Philox uniforms.  Bit n of frame F uses
+ * counter (n/4, F_lo, F_hi, tag) under key (seed_lo, seed_hi); the four words
+ * give the normals of bits 4q..4q+3 as two Box-Muller pairs.
+ * mu is rounded to binary32 at the end; g_out (if non-NULL) receives g.
+ */
+void or_channel_awgn(uint64_t seed, uint64_t first_frame, int nfr, int N, double sigma,
+                     uint32_t tag, float *mu_out, double *g_out)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int f = 0; f < nfr; ++f) {
+        uint64_t F = first_frame + (uint64_t)f;
+        for (int q = 0; 4 * q < N; ++q) {
+            uint32_t ctr[4] = {(uint32_t)q, (uint32_t)F, (uint32_t)(F >> 32), tag};
+            uint32_t w[4];
+            or_philox4x32_10(ctr, key, w);
+            double g[4];
+            for (int pair = 0; pair < 2; ++pair) {
+                double u0 = or_uniform(w[2 * pair]);
+                double u1 = or_uniform(w[2 * pair + 1]);
+                double r = sqrt(-2.0 * log(u0));
+                g[2 * pair] = r * cos(two_pi * u1);
+                g[2 * pair + 1] = r * sin(two_pi * u1);
+            }
+            for (int e = 0; e < 4; ++e) {
+                int n = 4 * q + e;
+                if (n >= N) break;
+                double y = 1.0 + sigma * g[e];
+                double mu = 2.0 * y / (sigma * sigma);
+                mu_out[(size_t)f * N + n] = (float)mu;
+                if (g_out) g_out[(size_t)f * N + n] = g[e];
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Graph helpers.  H is given as CSR rows in the paper's edge order: row by   */
+/* row, left to right (Sec. IV-A, data structure H).  Edge e of row m is      */
+/* col[e] for e in [row_ptr[m], row_ptr[m+1]).  The column view (LUT_v)       */
+/* lists, for every variable, its edges in increasing edge index.             */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int M, N, E;
+    const int *row_ptr, *col;
+    int *vptr, *vedge; /* column view */
+} or_graph;
+
+static int or_graph_init(or_graph *g, int M, int N, const int *row_ptr, const int *col)
+{
+    g->M = M; g->N = N; g->row_ptr = row_ptr; g->col = col;
+    g->E = row_ptr[M];
+    g->vptr = (int *)calloc((size_t)N + 1, sizeof(int));
+    g->vedge = (int *)malloc(sizeof(int) * (size_t)(g->E > 0 ? g->E : 1));
+    if (!g->vptr || !g->vedge) return -1;
+    for (int e = 0; e < g->E; ++e) g->vptr[col[e] + 1]++;
+    for (int n = 0; n < N; ++n) g->vptr[n + 1] += g->vptr[n];
+    int *fill = (int *)calloc((size_t)N, sizeof(int));
+    if (!fill) return -1;
+    for (int e = 0; e < g->E; ++e) {
+        int n = col[e];
+        g->vedge[g->vptr[n] + fill[n]++] = e;
+    }
+    free(fill);
+    return 0;
+}
+
+static void or_graph_free(or_graph *g)
+{
+    free(g->vptr);
+    free(g->vedge);
+}
+
+/* LUT_v of the paper: for each variable, the indices of its edges.  Exposed  */
+/* so the worked example of Sec. IV-A can be checked.                         */
+int or_variable_edges(int M, int N, const int *row_ptr, const int *col, int *vptr_out, int *vedge_out)
+{
+    or_graph g;
+    if (or_graph_init(&g, M, N, row_ptr, col)) return -1;
+    memcpy(vptr_out, g.vptr, sizeof(int) * (size_t)(N + 1));
+    memcpy(vedge_out, g.vedge, sizeof(int) * (size_t)g.E);
+    or_graph_free(&g);
+    return 0;
+}
+
+static double or_clip(double x, double c)
+{
+    if (x > c) return c;
+    if (x < -c) return -c;
+    return x;
+}
+
+/* phi(x) = -ln tanh(x/2) = ln((e^x + 1)/(e^x - 1)) for x >= 0; phi(0) = +inf. */
+/* phi is its own inverse on [0, inf], and tanh(x/2) = exp(-phi(|x|)), so the   */
+/* product of tanh in eq. (bphs) becomes a sum of phi values.                   */
+static double or_phi(double x)
+{
+    if (x <= 0.0) return INFINITY;
+    return log1p(2.0 / expm1(x));
+}
+
+/*
+ * Horizontal step of Algorithm 1 for one check node, eq. (bphs).
+ * form 0: phi-form  alpha = prod(sign) * phi( sum_{n' != n} phi(|beta_n'|) )
+ * form 1: literal   alpha = 2 atanh( prod_{n' != n} tanh(beta_n'/2) )
+ * The extrinsic set excludes the edge itself; an empty product is 1.
+ * Every output is clipped to +-clip.
+ */
+static void or_check_update(const double *beta, double *alpha, int d, double clip, int form)
+{
+    for (int a = 0; a < d; ++a) {
+        if (form == 1) {
+            double prod = 1.0;
+            for (int b = 0; b < d; ++b)
+                if (b != a) prod *= tanh(beta[b] / 2.0);
+            double v;
+            if (prod >= 1.0) v = INFINITY;
+            else if (prod <= -1.0) v = -INFINITY;
+            else v = 2.0 * atanh(prod);
+            alpha[a] = or_clip(v, clip);
+        } else {
+            double s = 0.0;
+            int neg = 0;
+            for (int b = 0; b < d; ++b) {
+                if (b == a) continue;
+                s += or_phi(fabs(beta[b]));
+                if (beta[b] < 0.0) neg ^= 1;
+            }
+            double mag = or_phi(s); /* phi(0) = inf for an empty set */
+            if (mag > clip) mag = clip;
+            alpha[a] = neg ? -mag : mag;
+        }
+    }
+}
+
+/* One frame of Algorithm 1 with the syndrome stopping rule.                 */
+static void or_sp_frame(const or_graph *g, const float *mu_f, int max_iter, int early_stop, double clip,
+                        int form, double *post, uint8_t *hard, int *iters, int *ok)
+{
+    int E = g->E, M = g->M, N = g->N;
+    double *beta = (double *)malloc(sizeof(double) * (size_t)(E ? E : 1));
+    double *alpha = (double *)malloc(sizeof(double) * (size_t)(E ? E : 1));
+    double *mu = (double *)malloc(sizeof(double) * (size_t)(N ? N : 1));
+    double *in = (double *)malloc(sizeof(double) * (size_t)(N + 1));
+    double *outv = (double *)malloc(sizeof(double) * (size_t)(N + 1));
+    for (int n = 0; n < N; ++n) mu[n] = or_clip((double)mu_f[n], clip);
+
+    /* [Initialization] beta_mn = mu_n on every edge. */
+    for (int e = 0; e < E; ++e) beta[e] = mu[g->col[e]];
+
+    int it_done = max_iter, satisfied = 0;
+    for (int it = 1; it <= max_iter; ++it) {
+        /* [Horizontal step] every check node, eq. (bphs). */
+        for (int m = 0; m < M; ++m) {
+            int e0 = g->row_ptr[m], d = g->row_ptr[m + 1] - e0;
+            for (int k = 0; k < d; ++k) in[k] = beta[e0 + k];
+            or_check_update(in, outv, d, clip, form);
+            for (int k = 0; k < d; ++k) alpha[e0 + k] = outv[k];
+        }
+        /* [Vertical step] eqs. (bpvs) and (bpd). */
+        for (int n = 0; n < N; ++n) {
+            int v0 = g->vptr[n], dv = g->vptr[n + 1] - v0;
+            double total = mu[n];
+            for (int k = 0; k < dv; ++k) total += alpha[g->vedge[v0 + k]];
+            for (int k = 0; k < dv; ++k) {
+                double s = mu[n];
+                for (int k2 = 0; k2 < dv; ++k2)
+                    if (k2 != k) s += alpha[g->vedge[v0 + k2]];
+                beta[g->vedge[v0 + k]] = or_clip(s, clip);
+            }
+            post[n] = or_clip(total, clip);
+            /* eq. (hrddcs): 0 if beta_n >= 0, else 1 */
+            hard[n] = post[n] < 0.0 ? 1 : 0;
+        }
+        /* Syndrome of the current hard decisions. */
+        satisfied = 1;
+        for (int m = 0; m < M && satisfied; ++m) {
+            int par = 0;
+            for (int e = g->row_ptr[m]; e < g->row_ptr[m + 1]; ++e) par ^= hard[g->col[e]];
+            if (par) satisfied = 0;
+        }
+        if (early_stop && satisfied) {
+            it_done = it;
+            break;
+        }
+    }
+    *iters = it_done;
+    *ok = satisfied;
+    free(beta); free(alpha); free(mu); free(in); free(outv);
+}
+
+int or_sp_decode(int M, int N, const int *row_ptr, const int *col, int nfr, const float *mu, int max_iter,
+                 int early_stop, double clip, int form, double *post, uint8_t *hard, int *iters, int *ok,
+                 int nthreads)
+{
+    or_graph g;
+    if (max_iter < 1) return -1;
+    if (or_graph_init(&g, M, N, row_ptr, col)) return -1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+    for (int f = 0; f < nfr; ++f)
+        or_sp_frame(&g, mu + (size_t)f * N, max_iter, early_stop, clip, form, post + (size_t)f * N,
+                    hard + (size_t)f * N, iters + f, ok + f);
+    or_graph_free(&g);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Integer min-sum.  The paper cites 8-bit min-sum GPU decoders as prior art  */
+/* (Sec. I) but gives no definition; this follows the usual definition:       */
+/* quantize mu to q = clamp(rint(mu * 2^F), -127, 127) (round half to even),  */
+/* check update alpha = prod(sign) * min_{n' != n} |beta_n'|  (sign(0) = +),  */
+/* variable update beta = clamp(q + sum_{m' != m} alpha, -127, 127),          */
+/* posterior = q + sum alpha (int32, unclamped), hard = posterior < 0.        */
+/* ------------------------------------------------------------------------ */
+static int or_sat(int x, int lim)
+{
+    return x > lim ? lim : (x < -lim ? -lim : x);
+}
+
+int or_quantize(const float *mu, int count, int frac_bits, int8_t *q)
+{
+    double scale = ldexp(1.0, frac_bits);
+    for (int i = 0; i < count; ++i) {
+        double v = nearbyint((double)mu[i] * scale); /* default mode: half to even */
+        if (v > 127.0) v = 127.0;
+        if (v < -127.0) v = -127.0;
+        q[i] = (int8_t)v;
+    }
+    return 0;
+}
+
+static void or_ms_frame(const or_graph *g, const float *mu_f, int frac_bits, int max_iter, int early_stop,
+                        int32_t *post, uint8_t *hard, int *iters, int *ok)
+{
+    int E = g->E, M = g->M, N = g->N;
+    int *beta = (int *)malloc(sizeof(int) * (size_t)(E ? E : 1));
+    int *alpha = (int *)malloc(sizeof(int) * (size_t)(E ? E : 1));
+    int8_t *q8 = (int8_t *)malloc((size_t)(N ? N : 1));
+    or_quantize(mu_f, N, frac_bits, q8);
+    for (int e = 0; e < E; ++e) beta[e] = q8[g->col[e]];
+    int it_done = max_iter, satisfied = 0;
+    for (int it = 1; it <= max_iter; ++it) {
+        for (int m = 0; m < M; ++m) {
+            int e0 = g->row_ptr[m], e1 = g->row_ptr[m + 1];
+            for (int e = e0; e < e1; ++e) {
+                int mag = 127, neg = 0; /* empty set: saturated + */
+                for (int e2 = e0; e2 < e1; ++e2) {
+                    if (e2 == e) continue;
+                    int a = beta[e2] < 0 ? -beta[e2] : beta[e2];
+                    if (a < mag) mag = a;
+                    if (beta[e2] < 0) neg ^= 1;
+                }
+                alpha[e] = neg ? -mag : mag;
+            }
+        }
+        for (int n = 0; n < N; ++n) {
+            int v0 = g->vptr[n], dv = g->vptr[n + 1] - v0;
+            int total = q8[n];
+            for (int k = 0; k < dv; ++k) total += alpha[g->vedge[v0 + k]];
+            for (int k = 0; k < dv; ++k) {
+                int s = q8[n];
+                for (int k2 = 0; k2 < dv; ++k2)
+                    if (k2 != k) s += alpha[g->vedge[v0 + k2]];
+                beta[g->vedge[v0 + k]] = or_sat(s, 127);
+            }
+            post[n] = total;
+            hard[n] = total < 0 ? 1 : 0;
+        }
+        satisfied = 1;
+        for (int m = 0; m < M && satisfied; ++m) {
+            int par = 0;
+            for (int e = g->row_ptr[m]; e < g->row_ptr[m + 1]; ++e) par ^= hard[g->col[e]];
+            if (par) satisfied = 0;
+        }
+        if (early_stop && satisfied) {
+            it_done = it;
+            break;
+        }
+    }
+    *iters = it_done;
+    *ok = satisfied;
+    free(beta); free(alpha); free(q8);
+}
+
+int or_ms_decode(int M, int N, const int *row_ptr, const int *col, int nfr, const float *mu, int frac_bits,
+                 int max_iter, int early_stop, int32_t *post, uint8_t *hard, int *iters, int *ok, int nthreads)
+{
+    or_graph g;
+    if (max_iter < 1) return -1;
+    if (or_graph_init(&g, M, N, row_ptr, col)) return -1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+    for (int f = 0; f < nfr; ++f)
+        or_ms_frame(&g, mu + (size_t)f * N, frac_bits, max_iter, early_stop, post + (size_t)f * N,
+                    hard + (size_t)f * N, iters + f, ok + f);
+    or_graph_free(&g);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pipelined BP of an LDPC convolutional code, Algorithm 2.                   */
+/*                                                                            */
+/* H is the unwrapped parity-check matrix H_[0,T) truncated to T check layers */
+/* and T variable frames, given as CSR rows in the paper's edge order.  Check */
+/* layer R holds rows [R*cb, (R+1)*cb), frame F holds columns [F*c, (F+1)*c); */
+/* cb = c - b.  A layer only touches frames R - ms .. R.                      */
+/*                                                                            */
+/* Slot t (0-based) of Algorithm 2:                                           */
+/*   [Initialization] frame t enters processor 1: beta = mu on its edges;     */
+/*   shifting frames between processors moves no data (Sec. IV-B-2).          */
+/*   Processor i = 1..I: horizontal step on layer t-(i-1)(ms+1), eq. (bph);   */
+/*   then, for all i, vertical step on frame t-(i-1)(ms+1)-ms, eq. (bpvs).    */
+/*   The frame leaving processor I, t-(I-1)(ms+1)-ms, gets its a-posteriori   */
+/*   LLR and hard decision.  Indices outside [0,T) are skipped: the first     */
+/*   ms frames see only the layers that exist (start-up, Sec. IV-B-2 step 3). */
+/*                                                                            */
+/* Outputs post/hard are [T][c]; decided[F] = 1 for the frames decided within */
+/* the T slots (F <= T - I(ms+1)).  If log is non-NULL it receives one        */
+/* (slot, kind, index, processor) record per event, kind 0 = frame enters,    */
+/* 1 = check layer update, 2 = frame update, 3 = decision; at most log_cap.   */
+/* Returns the number of decided frames, or -1.                               */
+/* ------------------------------------------------------------------------ */
+static int or_ldpccc_stream(const or_graph *g, int T, int c, int cb, int ms, int I, const float *mu_f,
+                            double clip, double *post, uint8_t *hard, uint8_t *decided, int *log,
+                            int log_cap, int *log_n)
+{
+    int E = g->E;
+    double *beta = (double *)calloc((size_t)(E ? E : 1), sizeof(double));
+    double *alpha = (double *)calloc((size_t)(E ? E : 1), sizeof(double));
+    double *in = (double *)malloc(sizeof(double) * (size_t)(g->N + 1));
+    double *outv = (double *)malloc(sizeof(double) * (size_t)(g->N + 1));
+    int ndec = 0, nl = 0;
+#define OR_LOG(t_, k_, x_, i_)                                                                     \
+    do {                                                                                           \
+        if (log && nl < log_cap) {                                                                 \
+            log[4 * nl] = (t_); log[4 * nl + 1] = (k_); log[4 * nl + 2] = (x_); log[4 * nl + 3] = (i_); \
+        }                                                                                          \
+        ++nl;                                                                                      \
+    } while (0)
+    for (int F = 0; F < T; ++F) decided[F] = 0;
+    for (int t = 0; t < T; ++t) {
+        /* [Initialization] frame t and its channel messages enter processor 1. */
+        for (int v = t * c; v < (t + 1) * c; ++v) {
+            double m = or_clip((double)mu_f[v], clip);
+            for (int k = g->vptr[v]; k < g->vptr[v + 1]; ++k) beta[g->vedge[k]] = m;
+        }
+        OR_LOG(t, 0, t, 1);
+        /* [Horizontal step] processor i updates check layer t-(i-1)(ms+1). */
+        for (int i = 1; i <= I; ++i) {
+            int R = t - (i - 1) * (ms + 1);
+            if (R < 0 || R >= T) continue;
+            OR_LOG(t, 1, R, i);
+            for (int m = R * cb; m < (R + 1) * cb; ++m) {
+                int e0 = g->row_ptr[m], d = g->row_ptr[m + 1] - e0;
+                for (int k = 0; k < d; ++k) in[k] = beta[e0 + k];
+                or_check_update(in, outv, d, clip, 0);
+                for (int k = 0; k < d; ++k) alpha[e0 + k] = outv[k];
+            }
+        }
+        /* [Vertical step] processor i updates frame t-(i-1)(ms+1)-ms. */
+        for (int i = 1; i <= I; ++i) {
+            int F = t - (i - 1) * (ms + 1) - ms;
+            if (F < 0 || F >= T) continue;
+            OR_LOG(t, 2, F, i);
+            for (int n = F * c; n < (F + 1) * c; ++n) {
+                int v0 = g->vptr[n], dv = g->vptr[n + 1] - v0;
+                double m0 = or_clip((double)mu_f[n], clip);
+                for (int k = 0; k < dv; ++k) {
+                    double s = m0;
+                    for (int k2 = 0; k2 < dv; ++k2)
+                        if (k2 != k) s += alpha[g->vedge[v0 + k2]];
+                    beta[g->vedge[v0 + k]] = or_clip(s, clip);
+                }
+            }
+        }
+        /* [Making hard decision] for the frame leaving processor I. */
+        {
+            int F = t - (I - 1) * (ms + 1) - ms;
+            if (F >= 0 && F < T) {
+                OR_LOG(t, 3, F, I);
+                for (int n = F * c; n < (F + 1) * c; ++n) {
+                    int v0 = g->vptr[n], dv = g->vptr[n + 1] - v0;
+                    double total = or_clip((double)mu_f[n], clip);
+                    for (int k = 0; k < dv; ++k) total += alpha[g->vedge[v0 + k]];
+                    total = or_clip(total, clip);
+                    post[n] = total;
+                    hard[n] = total < 0.0 ? 1 : 0;
+                }
+                decided[F] = 1;
+                ++ndec;
+            }
+        }
+    }
+#undef OR_LOG
+    if (log_n) *log_n = nl;
+    free(beta); free(alpha); free(in); free(outv);
+    return ndec;
+}
+
+int or_ldpccc_decode(int M, int N, const int *row_ptr, const int *col, int T, int c, int cb, int ms, int I,
+                     int nstreams, const float *mu, double clip, double *post, uint8_t *hard, uint8_t *decided,
+                     int *log, int log_cap, int *log_n, int nthreads)
+{
+    if (I < 1 || ms < 0 || c <= 0 || cb <= 0 || M != T * cb || N != T * c) return -1;
+    or_graph g;
+    if (or_graph_init(&g, M, N, row_ptr, col)) return -1;
+    int ndec = 0;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1) reduction(max : ndec)
+    for (int s = 0; s < nstreams; ++s) {
+        int r = or_ldpccc_stream(&g, T, c, cb, ms, I, mu + (size_t)s * N, clip, post + (size_t)s * N,
+                                 hard + (size_t)s * N, decided + (size_t)s * T, s == 0 ? log : NULL,
+                                 log_cap, s == 0 ? log_n : NULL);
+        if (r > ndec) ndec = r;
+    }
+    or_graph_free(&g);
+    return ndec;
+}

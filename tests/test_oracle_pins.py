@@ -1,0 +1,392 @@
+"""Pins for the CPU oracle against what the paper and the mathematics fix.
+
+Every test here runs on the CPU.  None of them compares the oracle with
+itself: each checks it against a printed table of the paper, a closed form,
+brute force over all codewords, an invariant of BP, or a textbook special case.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import (TREE_BASES, brute_force_llr, brute_force_maxlog, random_codeword, read_sections,
+                     syndrome)
+
+
+# ---------------------------------------------------------------- graph, Sec. IV-A
+def test_edge_order_matches_paper_example():
+    """Eq. (simpleH): edges numbered row by row, left to right; eq. (LUT_c), eq. (LUT_v)."""
+    g = read_sections("simple_H_edges.txt")
+    H = np.array(g["H"], dtype=np.uint8)
+    row_ptr, col = oracle.csr_rows(H)
+    lut_c = [list(range(row_ptr[m], row_ptr[m + 1])) for m in range(H.shape[0])]
+    assert lut_c == g["LUT_c"]
+    vptr, vedge = oracle.variable_edges(row_ptr, col, H.shape[1])
+    lut_v = [list(vedge[vptr[n]:vptr[n + 1]]) for n in range(H.shape[1])]
+    assert lut_v == g["LUT_v"]
+    # package p_01 first, then p_03, p_04, p_07, p_10 ... (Example in Sec. IV-A)
+    assert list(zip(np.repeat(np.arange(4), np.diff(row_ptr))[:5], col[:5])) == [(0, 1), (0, 3), (0, 4), (0, 7),
+                                                                                 (1, 0)]
+
+
+def test_circulant_shift_direction():
+    """P^a is the identity with its columns shifted cyclically right a times (Sec. II-A)."""
+    P1 = oracle.circulant(1, 3)
+    I3 = np.eye(3, dtype=np.uint8)
+    assert np.array_equal(P1, np.roll(I3, 1, axis=1))
+    assert np.array_equal(P1, [[0, 1, 0], [0, 0, 1], [1, 0, 0]])
+    assert not oracle.circulant(-1, 4).any()
+
+
+def test_qc_code_dimensions_match_codes_table():
+    """Table of codes A-D: c x (c-b) and the number of edges E = J L p (Sec. IV-B-1)."""
+    rows = read_sections("codes_table.txt")[None]
+    for name, J, L, p, c, cb, edges in rows:
+        geo = oracle.ldpccc_geometry(J, L, p)
+        assert (geo["c"], geo["cb"]) == (c, cb)
+        shifts = synth.qc_shifts(J, L, p, seed=7, avoid_4cycles=False)
+        H = oracle.qc_parity_check(shifts, p)
+        assert H.shape == (J * p, L * p)
+        assert int(H.sum()) == edges == J * L * p
+        assert (H.sum(axis=0) == J).all() and (H.sum(axis=1) == L).all()  # regular (w_c, w_r) = (J, L)
+        assert abs(oracle.design_rate(shifts) - 5 / 6) < 1e-12
+
+
+# ---------------------------------------------------------------- generator and channel
+def test_philox_known_answers():
+    """Philox4x32-10 known-answer vectors published with the generator (Salmon et al., SC'11)."""
+    kat = [
+        ((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+        ((0xFFFFFFFF,) * 4, (0xFFFFFFFF,) * 2, (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+        ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
+         (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1)),
+    ]
+    for ctr, key, want in kat:
+        assert tuple(int(x) for x in oracle.philox4x32_10(ctr, key)) == want
+
+
+def test_channel_llr_statistics():
+    """mu = 2y/sigma^2 with y ~ N(1, sigma^2): mean 2/sigma^2, variance 4/sigma^2 (Sec. II-B)."""
+    sigma = oracle.sigma_from_ebn0(2.0, 0.5)
+    mu, g = oracle.channel_awgn(seed=11, first_frame=0, nfr=64, N=4096, sigma=sigma, return_g=True)
+    n = mu.size
+    m, v = mu.mean(), mu.var()
+    assert abs(m - 2 / sigma**2) < 5 * math.sqrt(4 / sigma**2 / n)
+    assert abs(v / (4 / sigma**2) - 1) < 5 * math.sqrt(2 / n)
+    assert abs(g.mean()) < 5 / math.sqrt(n) and abs(g.std() - 1) < 5 / math.sqrt(2 * n)
+    # uncoded BER of hard decisions on mu equals Q(1/sigma)
+    ber = (mu < 0).mean()
+    q = 0.5 * math.erfc(1 / sigma / math.sqrt(2))
+    assert abs(ber - q) < 5 * math.sqrt(q * (1 - q) / n)
+
+
+def test_channel_counter_partition_invariance():
+    """Frame F's noise depends only on (seed, F, bit): any split of the frame range gives the same values."""
+    sigma = 0.8
+    a = oracle.channel_awgn(5, 100, 6, 130, sigma)
+    b = np.concatenate([oracle.channel_awgn(5, 100, 2, 130, sigma), oracle.channel_awgn(5, 102, 4, 130, sigma)])
+    assert np.array_equal(a, b)
+    c = oracle.channel_awgn(6, 100, 6, 130, sigma)
+    assert not np.array_equal(a, c)
+
+
+# ---------------------------------------------------------------- sum-product, Algorithm 1
+def _tree_code(name, p=1):
+    H = oracle.qc_parity_check(np.array(TREE_BASES[name]), p)
+    rp, col = oracle.csr_rows(H)
+    return H, rp, col
+
+
+@pytest.mark.parametrize("name", sorted(TREE_BASES))
+def test_sp_exact_on_cycle_free_graphs(name):
+    """BP on a cycle-free Tanner graph returns the exact a-posteriori LLRs (brute force over all codewords)."""
+    H, rp, col = _tree_code(name)
+    rng = np.random.default_rng(3)
+    for trial in range(4):
+        mu = rng.normal(1.0, 1.5, size=H.shape[1]).astype(np.float32)
+        post, hard, iters, ok = oracle.sp_decode(rp, col, H.shape[1], mu, max_iter=12)
+        want = brute_force_llr(H, mu)
+        assert np.allclose(post[0], want, rtol=0, atol=1e-10), (name, trial)
+        assert np.array_equal(hard[0], (want < 0).astype(np.uint8))
+
+
+def test_sp_exact_on_lifted_tree():
+    """A tree lifted by p x p circulants is a forest of p trees: BP stays exact (N = 21 brute force)."""
+    H, rp, col = _tree_code("path3", p=3)
+    mu = np.random.default_rng(4).normal(0.8, 1.2, size=H.shape[1]).astype(np.float32)
+    post = oracle.sp_decode(rp, col, H.shape[1], mu, max_iter=10)[0][0]
+    assert np.allclose(post, brute_force_llr(H, mu), atol=1e-10)
+
+
+def test_single_parity_check_closed_form():
+    """Eq. (bphs) on one check: alpha_n = 2 atanh(prod_{n' != n} tanh(mu_n'/2)); post = mu + alpha."""
+    d = 6
+    H = np.ones((1, d), dtype=np.uint8)
+    rp, col = oracle.csr_rows(H)
+    mu = np.array([1.3, -0.4, 2.2, 0.7, -3.1, 5.0], dtype=np.float32)
+    post = oracle.sp_decode(rp, col, d, mu, max_iter=1)[0][0]
+    m = mu.astype(np.float64)
+    for n in range(d):
+        prod = np.prod([math.tanh(m[k] / 2) for k in range(d) if k != n])
+        assert abs(post[n] - (m[n] + 2 * math.atanh(prod))) < 1e-12
+
+
+def test_repetition_code_posterior_is_sum():
+    """A length-5 repetition code (path of degree-2 checks): every posterior equals sum(mu)."""
+    H, rp, col = _tree_code("rep5")
+    mu = np.array([0.5, -1.25, 2.0, 0.75, -0.5], dtype=np.float32)
+    post = oracle.sp_decode(rp, col, 5, mu, max_iter=6)[0][0]
+    assert np.allclose(post, mu.astype(np.float64).sum(), atol=1e-12)
+
+
+def test_phi_form_equals_tanh_form():
+    """The phi-form used by the oracle equals the literal tanh/atanh form of eq. (bphs) away from clipping."""
+    shifts = synth.qc_shifts(3, 6, 16, seed=1)
+    H = oracle.qc_parity_check(shifts, 16)
+    rp, col = oracle.csr_rows(H)
+    mu = synth.gaussian_llrs(8, H.shape[1], seed=2, ebn0_db=0.0, rate=0.5)
+    mu = np.clip(mu, -6, 6)
+    a = oracle.sp_decode(rp, col, H.shape[1], mu, max_iter=3, form="phi", clip=1e9)[0]
+    b = oracle.sp_decode(rp, col, H.shape[1], mu, max_iter=3, form="tanh", clip=1e9)[0]
+    assert np.max(np.abs(a - b)) < 1e-9
+
+
+def test_noiseless_fixed_point():
+    """A noiseless all-zero frame satisfies every check after the first iteration."""
+    shifts = synth.qc_shifts(4, 24, 31, seed=3)
+    H = oracle.qc_parity_check(shifts, 31)
+    rp, col = oracle.csr_rows(H)
+    mu = np.full((2, H.shape[1]), 8.0, dtype=np.float32)
+    post, hard, iters, ok = oracle.sp_decode(rp, col, H.shape[1], mu, max_iter=30, early_stop=True)
+    assert (iters == 1).all() and (ok == 1).all() and not hard.any()
+    # every check sees 23 equal inputs: alpha = 2 atanh(tanh(4)^23), posterior = mu + 4 alpha
+    alpha = 2 * math.atanh(math.tanh(4.0) ** 23)
+    assert np.allclose(post, 8.0 + 4 * alpha, atol=1e-12)
+
+
+def test_channel_symmetry_with_nonzero_codeword():
+    """BP commutes with the sign flip of a codeword: decode(mu * x(c)) = decode(mu) * x(c)."""
+    shifts = synth.qc_shifts(3, 6, 8, seed=9)
+    H = oracle.qc_parity_check(shifts, 8)
+    rp, col = oracle.csr_rows(H)
+    N = H.shape[1]
+    mu = synth.gaussian_llrs(4, N, seed=5, ebn0_db=1.0, rate=0.5)
+    cw = random_codeword(H, seed=6)
+    assert not syndrome(H, cw).any() and cw.any()
+    x = (1 - 2 * cw.astype(np.float32))
+    pa, ha, ia, oa = oracle.sp_decode(rp, col, N, mu, max_iter=7)
+    pb, hb, ib, ob = oracle.sp_decode(rp, col, N, mu * x, max_iter=7)
+    assert np.allclose(pb, pa * x, atol=1e-12)
+    assert np.array_equal(oa, ob)
+
+
+def test_converged_frames_satisfy_all_checks():
+    """ok = 1 exactly when H c_hat = 0; early stop freezes at the first such iteration."""
+    shifts = synth.qc_shifts(3, 6, 64, seed=1)
+    H = oracle.qc_parity_check(shifts, 64)
+    rp, col = oracle.csr_rows(H)
+    mu = synth.gaussian_llrs(32, H.shape[1], seed=1, ebn0_db=1.5, rate=0.5)
+    post, hard, iters, ok = oracle.sp_decode(rp, col, H.shape[1], mu, max_iter=30, early_stop=True)
+    for f in range(32):
+        s = syndrome(H, hard[f]).any()
+        assert ok[f] == (0 if s else 1)
+        if ok[f]:
+            # no earlier iteration satisfied the checks
+            if iters[f] > 1:
+                h2 = oracle.sp_decode(rp, col, H.shape[1], mu[f], max_iter=iters[f] - 1)[1][0]
+                assert syndrome(H, h2).any()
+            full = oracle.sp_decode(rp, col, H.shape[1], mu[f], max_iter=iters[f])
+            assert np.array_equal(full[0][0], post[f])
+        else:
+            assert iters[f] == 30
+    assert ok.sum() > 16
+
+
+def test_empty_extrinsic_set_and_degree_one_check():
+    """A degree-1 check sends +clip (empty product = 1); the posterior then carries it."""
+    H = np.array([[1, 0], [1, 1]], dtype=np.uint8)
+    rp, col = oracle.csr_rows(H)
+    mu = np.array([-2.0, 1.0], dtype=np.float32)
+    post = oracle.sp_decode(rp, col, 2, mu, max_iter=1, clip=30.0)[0][0]
+    # variable 0: mu + alpha(deg-1 check: +30) + alpha(check 2: mu_1 = 1.0 after one step)
+    assert abs(post[0] - max(-30, min(30, -2.0 + 30.0 + 1.0))) < 1e-12
+
+
+def test_frames_are_independent():
+    shifts = synth.qc_shifts(3, 6, 16, seed=2)
+    H = oracle.qc_parity_check(shifts, 16)
+    rp, col = oracle.csr_rows(H)
+    mu = synth.gaussian_llrs(6, H.shape[1], seed=8, ebn0_db=1.0, rate=0.5)
+    a = oracle.sp_decode(rp, col, H.shape[1], mu, 9)[0]
+    perm = np.array([3, 1, 5, 0, 2, 4])
+    b = oracle.sp_decode(rp, col, H.shape[1], mu[perm], 9, nthreads=3)[0]
+    assert np.array_equal(a[perm], b)
+
+
+# ---------------------------------------------------------------- integer min-sum
+@pytest.mark.parametrize("name", sorted(TREE_BASES))
+def test_min_sum_is_max_log_on_trees(name):
+    """On a cycle-free graph min-sum returns the max-log a-posteriori values (integer brute force)."""
+    H, rp, col = _tree_code(name)
+    rng = np.random.default_rng(12)
+    for trial in range(4):
+        mu = (rng.integers(-12, 13, size=H.shape[1]) * 0.25).astype(np.float32)  # exact on the F=2 grid
+        q = oracle.quantize(mu, 2).astype(np.int64)
+        assert np.array_equal(q, np.round(mu * 4).astype(np.int64))
+        post, hard, _, _ = oracle.ms_decode(rp, col, H.shape[1], mu, max_iter=12)
+        assert np.array_equal(post[0].astype(np.int64), brute_force_maxlog(H, q)), (name, trial)
+
+
+def test_quantizer_rounding_and_saturation():
+    """q = clamp(round-half-even(mu * 4), -127, 127)."""
+    mu = np.array([0.125, 0.375, -0.125, -0.375, 31.75, 40.0, -40.0, 0.0, 1.1], dtype=np.float32)
+    assert oracle.quantize(mu, 2).tolist() == [0, 2, 0, -2, 127, 127, -127, 0, 4]
+
+
+def test_min_sum_saturates_messages():
+    """Variable-to-check messages saturate at +-127; the posterior is the unsaturated sum."""
+    H = np.ones((3, 2), dtype=np.uint8)  # three degree-2 checks on the same two bits
+    rp, col = oracle.csr_rows(H)
+    mu = np.array([30.0, 30.0], dtype=np.float32)  # q = 120
+    post = oracle.ms_decode(rp, col, 2, mu, max_iter=2)[0][0]
+    # iteration 1: alpha = 120 on each edge; beta = clamp(120 + 240) = 127
+    # iteration 2: alpha = 127; post = 120 + 3 * 127
+    assert post.tolist() == [120 + 3 * 127] * 2
+
+
+# ---------------------------------------------------------------- LDPCCC, Sec. II-D, II-E, IV-B
+def _label_of(block, subs):
+    for lab, s in enumerate(subs):
+        if block.shape == s.shape and (block != s).nnz == 0:
+            return lab
+    return None
+
+
+def test_ldpccc_label_tables_match_paper():
+    """Eqs. (lut_c_ldpccc), (lut_v_ldpccc): sub-block labels seen by each check-layer / frame type (Lambda=4)."""
+    g = read_sections("ldpccc_luts_lambda4.txt")
+    J, L, p = 4, 24, 5
+    shifts = synth.qc_shifts(J, L, p, seed=21)
+    T = 12
+    Hc, geo = oracle.ldpccc_unwrap(shifts, p, T)
+    lam, c, cb, ms = geo["Lambda"], geo["c"], geo["cb"], geo["ms"]
+    assert (lam, ms) == (4, 3)
+    import scipy.sparse as sp
+    HQ = sp.csr_matrix(oracle.qc_parity_check(shifts, p))
+    subs = [HQ[i * cb:(i + 1) * cb, j * c:(j + 1) * c] for i in range(lam) for j in range(lam)]
+    lut_c, lut_v = [], []
+    for R in range(ms, ms + lam):  # one layer of each type, past start-up
+        lut_c.append([_label_of(Hc[R * cb:(R + 1) * cb, F * c:(F + 1) * c], subs) for F in range(R - ms, R + 1)])
+    lut_c = [lut_c[(k - ms) % lam] for k in range(lam)]  # row k = layer type k
+    for F in range(lam, 2 * lam):
+        lut_v.append([_label_of(Hc[R * cb:(R + 1) * cb, F * c:(F + 1) * c], subs) for R in range(F, F + ms + 1)])
+    lut_v = [lut_v[(k - lam) % lam] for k in range(lam)]
+    assert lut_c == g["LUT_c"]
+    assert lut_v == g["LUT_v"]
+
+
+def test_ldpccc_structure():
+    """Regular (ms, J, K) past start-up, period T = Lambda, and H^L + H^U reassembles H_QC (Sec. II-C, II-D)."""
+    import scipy.sparse as sp
+    J, L, p = 3, 6, 7
+    shifts = synth.qc_shifts(J, L, p, seed=4)
+    T = 10
+    Hc, geo = oracle.ldpccc_unwrap(shifts, p, T)
+    lam, c, cb, ms = geo["Lambda"], geo["c"], geo["cb"], geo["ms"]
+    assert (lam, ms, c, cb) == (3, 2, 2 * p, p)
+    rw = np.asarray(Hc.sum(axis=1)).ravel()
+    cw = np.asarray(Hc.sum(axis=0)).ravel()
+    assert (rw[ms * cb:] == L).all() and (rw[:ms * cb] < L).all()
+    assert (cw[: (T - ms) * c] == J).all()
+    # period Lambda
+    blk = lambda R, F: Hc[R * cb:(R + 1) * cb, F * c:(F + 1) * c].toarray()
+    for R in range(ms, T - lam):
+        for d in range(ms + 1):
+            assert np.array_equal(blk(R, R - d), blk(R + lam, R + lam - d))
+    # sum of the Lambda x Lambda window starting at layer lam reassembles H_QC
+    HQ = oracle.qc_parity_check(shifts, p)
+    rebuilt = np.zeros_like(HQ)
+    for a in range(lam):
+        for d in range(ms + 1):
+            R = lam + a
+            F = R - d
+            b = F % lam
+            rebuilt[a * cb:(a + 1) * cb, b * c:(b + 1) * c] |= blk(R, F).astype(np.uint8)
+    assert np.array_equal(rebuilt, HQ)
+
+
+def test_ldpccc_schedule_matches_narrative():
+    """Slots 0, 3, 4 and the first decision, Sec. IV-B-2 (Lambda = 4, ms = 3)."""
+    J, L, p, I = 4, 8, 3, 3
+    shifts = synth.qc_shifts(J, L, p, seed=5)
+    T = 20
+    Hc, geo = oracle.ldpccc_unwrap(shifts, p, T)
+    mu = np.full(T * geo["c"], 3.0, dtype=np.float32)
+    _, _, decided, log = oracle.ldpccc_decode(Hc, geo, T, I, mu, log_cap=10000)
+    ev = {}
+    for t, kind, idx, proc in log.tolist():
+        ev.setdefault(t, []).append((kind, idx, proc))
+    assert ev[0] == [(0, 0, 1), (1, 0, 1)]  # v0 enters, c0 updated, nothing else
+    assert ev[1] == [(0, 1, 1), (1, 1, 1)]
+    assert ev[3] == [(0, 3, 1), (1, 3, 1), (2, 0, 1)]  # after c3, v0 is updated
+    assert ev[4] == [(0, 4, 1), (1, 4, 1), (1, 0, 2), (2, 1, 1)]  # c4 and c0; v1 leaves processor 1
+    first_decision = min(t for t, k, i, _ in log.tolist() if k == 3)
+    assert first_decision == I * 4 - 1
+    assert decided[0].sum() == T - I * 4 + 1
+    # the first check layer holds edges to frame 0 only
+    assert Hc[0:geo["cb"], geo["c"]:].nnz == 0
+
+
+def test_ldpccc_lambda1_is_block_decoding():
+    """gcd(J, L) = 1: frames decouple (ms = 0) and I processors equal I iterations of Algorithm 1."""
+    J, L, p, I = 3, 7, 11, 5
+    shifts = synth.qc_shifts(J, L, p, seed=8)
+    T = 12
+    Hc, geo = oracle.ldpccc_unwrap(shifts, p, T)
+    assert geo["Lambda"] == 1 and geo["ms"] == 0
+    c = geo["c"]
+    mu = synth.gaussian_llrs(1, T * c, seed=9, ebn0_db=1.5, rate=1 - J / L)[0]
+    post, hard, decided, _ = oracle.ldpccc_decode(Hc, geo, T, I, mu)
+    H = oracle.qc_parity_check(shifts, p)
+    rp, col = oracle.csr_rows(H)
+    frames = mu.reshape(T, c)
+    bp, bh, _, _ = oracle.sp_decode(rp, col, c, frames, max_iter=I)
+    nd = T - I + 1
+    assert decided[0].sum() == nd
+    assert np.allclose(post[0].reshape(T, c)[:nd], bp[:nd], atol=1e-12)
+    assert np.array_equal(hard[0].reshape(T, c)[:nd], bh[:nd])
+
+
+def test_ldpccc_noiseless_stream_decodes_to_zero():
+    J, L, p, I = 3, 6, 8, 4
+    shifts = synth.qc_shifts(J, L, p, seed=1)
+    T = 30
+    Hc, geo = oracle.ldpccc_unwrap(shifts, p, T)
+    mu = np.full((2, T * geo["c"]), 5.0, dtype=np.float32)
+    post, hard, decided, _ = oracle.ldpccc_decode(Hc, geo, T, I, mu)
+    assert decided.sum() == 2 * (T - I * 3 + 1)
+    assert not hard.any()
+
+
+def test_codeword_enumeration_helper():
+    """The null-space enumeration used by brute force agrees with exhaustive search (eq. ldpcc example H)."""
+    from helpers import codewords, codewords_exhaustive
+    H = np.array(read_sections("irregular_H_example.txt")[None], dtype=np.uint8)
+    a = {tuple(r) for r in codewords(H)}
+    b = {tuple(r) for r in codewords_exhaustive(H)}
+    assert a == b and len(a) == 2 ** (10 - np.linalg.matrix_rank(H))  # rank over GF(2) = rank over R here
+
+
+def test_sp_on_paper_irregular_example_with_cycles():
+    """Eq. (ldpcc) H has cycles: BP is not exact, but hard decisions of a clean frame are right and ok=1."""
+    H = np.array(read_sections("irregular_H_example.txt")[None], dtype=np.uint8)
+    rp, col = oracle.csr_rows(H)
+    from helpers import codewords
+    C = codewords(H)
+    cw = C[len(C) // 2]
+    mu = (4.0 * (1 - 2 * cw)).astype(np.float32)
+    mu[3] = -mu[3] * 0.25  # one weak wrong bit
+    post, hard, iters, ok = oracle.sp_decode(rp, col, 10, mu, max_iter=20, early_stop=True)
+    assert ok[0] == 1 and np.array_equal(hard[0], cw.astype(np.uint8))
