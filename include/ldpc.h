@@ -1,0 +1,149 @@
+/*
+ * ldpc.h -- C-ABI of the GB300 (sm_103a) batched belief-propagation decoders
+ * for quasi-cyclic LDPC block codes and the LDPC convolutional codes derived
+ * from them (Zhao & Lau, arXiv 1204.0334).
+ *
+ * Conventions for every call:
+ *  - Plain C types only.  Buffers are caller-owned.  Unless a parameter says
+ *    otherwise, a buffer may live in device memory or in host memory (pinned
+ *    or pageable); the library finds out with cudaPointerGetAttributes and
+ *    stages host buffers through its own device workspace.  Results written
+ *    to host buffers are valid once `stream` has been synchronized.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  All device work is enqueued on it; calls return without
+ *    waiting unless stated.
+ *  - Objects (ldpc_code, ldpccc) are owned by the library, created on the
+ *    current CUDA device and used on that device only.  One object must not
+ *    be used from two streams or threads at the same time: it owns the
+ *    workspace its calls use.
+ *  - Every call returns an ldpc_status; no exception crosses the ABI.  On an
+ *    error, ldpc_last_error() gives a thread-local description.
+ *  - Frames are laid out frame-major: element (f, n) of an [gamma][N] buffer
+ *    is at f*N + n.
+ */
+#ifndef LDPC_GB300_H
+#define LDPC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LDPC_OK = 0,
+    LDPC_EINVAL = 1,        /* bad argument: sizes, null pointers, shifts out of range */
+    LDPC_ENOMEM = 2,        /* device or host allocation failed */
+    LDPC_ECUDA = 3,         /* a CUDA runtime call failed (detail in ldpc_last_error) */
+    LDPC_ETIMEOUT = 4,      /* a bounded device-side wait ran out */
+    LDPC_EUNSUPPORTED = 5   /* valid request this build does not implement */
+} ldpc_status;
+
+typedef struct ldpc_code_s *ldpc_code;
+typedef struct ldpccc_s *ldpccc;
+
+/* Check-node rule. */
+enum {
+    LDPC_ALGO_SP = 0,   /* sum-product, eq. (bphs) of Algorithm 1, log-domain phi form in FP32 */
+    LDPC_ALGO_MS = 1,   /* integer min-sum over int8 messages (quantized LLRs, F fractional bits) */
+    LDPC_ALGO_NOMS = 2  /* normalized/offset min-sum with per-iteration, per-circulant (w, o) */
+};
+
+/* Storage type of the edge messages (arithmetic is FP32 for SP/NOMS, int32 for MS). */
+enum { LDPC_MSG_F32 = 0, LDPC_MSG_F16 = 1, LDPC_MSG_I8 = 2 };
+
+typedef struct {
+    int32_t max_iter;          /* I_max >= 1: iterations of Algorithm 1 */
+    int32_t early_stop;        /* 1: a frame stops at the first iteration i >= 1 whose hard
+                                  decisions satisfy every check; its outputs are those of i */
+    int32_t algo;              /* LDPC_ALGO_* */
+    int32_t msg;               /* LDPC_MSG_*; MS requires LDPC_MSG_I8, SP/NOMS take F32 or F16 */
+    float clip;                /* SP/NOMS: channel LLRs, messages and posteriors are clipped to
+                                  [-clip, clip] (default 30) */
+    int32_t frac_bits;         /* MS: q = clamp(rint(mu * 2^frac_bits), -127, 127) (default 2) */
+    const float *noms_params;  /* NOMS: device [max_iter][J*L][2] of (w, o); else NULL */
+    int32_t reserved[4];       /* must be zero */
+} ldpc_decode_opts;
+
+/* Defaults: max_iter 30, early_stop 0, SP, F32 messages, clip 30, frac_bits 2. */
+void ldpc_default_opts(ldpc_decode_opts *opts);
+
+const char *ldpc_status_str(ldpc_status s);
+/* Thread-local text of the last error raised in this thread ("" if none). */
+const char *ldpc_last_error(void);
+
+/*
+ * ldpc_code_create -- a (J, L) QC-LDPC code, eq. (qcH) of Sec. II-A.
+ *   shifts: host int32 [J][L] row-major; a_jl in [0, p) selects the circulant
+ *           whose row r has its one in column (r + a_jl) mod p (the identity
+ *           shifted right a_jl times); -1 selects the zero block (the "shift
+ *           number" convention of Sec. IV-B-1).  Copied; the caller keeps it.
+ *   J, L:   1 <= J <= 8, 1 <= L <= 32; p >= 1; J*L*p*... must fit in int32.
+ *   N = L p variables, M = J p checks, E = p * (number of non-zero blocks).
+ * Uses the current CUDA device.  Errors: LDPC_EINVAL (sizes, shift range,
+ * out == NULL), LDPC_ENOMEM.
+ */
+ldpc_status ldpc_code_create(const int32_t *shifts, int32_t J, int32_t L, int32_t p, ldpc_code *out);
+ldpc_status ldpc_code_destroy(ldpc_code code);
+/* N, M, E and the design information length K = N - M (any pointer may be NULL). */
+ldpc_status ldpc_code_dims(ldpc_code code, int64_t *N, int64_t *M, int64_t *E, int64_t *K);
+
+/*
+ * ldpc_decode -- Algorithm 1 (Sec. II-B) on gamma frames at once (the
+ * paper's Gamma-codeword batches, Sec. IV-A).
+ *   llr:   [gamma][N] float channel LLRs mu_n = ln P(c_n=0|y_n)/P(c_n=1|y_n).
+ *   post:  [gamma][N] float a-posteriori LLRs beta_n of eq. (bpd), or NULL.
+ *          SP/NOMS: clipped to +-clip.  MS: the integer posterior q + sum(alpha)
+ *          times 2^-frac_bits.
+ *   hard:  [gamma][N] uint8 hard decisions of eq. (hrddcs) (1 iff beta_n < 0), or NULL.
+ *   iters: [gamma] int32 iterations run per frame, or NULL.
+ *   ok:    [gamma] int32, 1 iff the hard decisions satisfy every check, or NULL.
+ * gamma >= 1 (any value; internally padded to the package width).
+ * Errors: LDPC_EINVAL (null code/llr, gamma < 1, bad opts), LDPC_EUNSUPPORTED
+ * (algo/msg pair not built), LDPC_ENOMEM, LDPC_ECUDA.
+ */
+ldpc_status ldpc_decode(ldpc_code code, const float *llr, int32_t gamma, const ldpc_decode_opts *opts,
+                        float *post, uint8_t *hard, int32_t *iters, int32_t *ok, void *stream);
+
+/*
+ * ldpc_channel -- the device-side channel of Sec. V (codeword and noise made
+ * on the GPU): the all-zero codeword sent as BPSK x = +1 over AWGN, Sec. II-B,
+ * y = 1 + sigma g, mu = 2 y / sigma^2, with sigma^2 = 1 / (2 R 10^(EbN0/10))
+ * and R = K/N the design rate.  g is Box-Muller on Philox4x32-10 words:
+ * bit n of frame F uses counter (n/4, F mod 2^32, F / 2^32, 0) under key
+ * (seed mod 2^32, seed / 2^32); word w -> u = (floor(w / 2^9) + 1/2) 2^-23;
+ * words (0,1) and (2,3) give the normals of bits 4q, 4q+1 and 4q+2, 4q+3 as
+ * (r cos 2 pi u', r sin 2 pi u'), r = sqrt(-2 ln u).
+ *   llr_out: [gamma][N] float, frames first_frame .. first_frame+gamma-1.
+ */
+ldpc_status ldpc_channel(ldpc_code code, double ebn0_db, uint64_t seed, uint64_t first_frame, int32_t gamma,
+                         float *llr_out, void *stream);
+
+typedef struct {
+    int64_t frames;        /* frames decoded */
+    int64_t frame_errors;  /* frames with >= 1 wrong bit (all N coded bits counted) */
+    int64_t bit_errors;    /* wrong coded bits */
+    int64_t iters_sum;     /* sum over frames of the iterations run */
+    int64_t undetected;    /* frames with ok = 1 but >= 1 wrong bit */
+    double seconds;        /* wall time of the call */
+} ldpc_ber_result;
+
+/*
+ * ldpc_ber_sim -- the Monte-Carlo protocol of Sec. V: fixed iteration cap,
+ * batches of gamma frames generated and decoded on the device, error counts
+ * reduced on the device; stop once frame_errors >= target_frame_errors (the
+ * paper uses 100) or frames >= max_frames.  Frames first_frame,
+ * first_frame+1, ... are drawn exactly as ldpc_channel draws them, so a run
+ * can be resumed from (seed, first_frame + out->frames) and partial results
+ * added.  Synchronizes `stream` once per batch to test the stop rule.
+ *   out: host pointer, filled on return.
+ */
+ldpc_status ldpc_ber_sim(ldpc_code code, double ebn0_db, uint64_t seed, uint64_t first_frame, int64_t max_frames,
+                         int64_t target_frame_errors, int32_t gamma, const ldpc_decode_opts *opts,
+                         ldpc_ber_result *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LDPC_GB300_H */

@@ -1,0 +1,211 @@
+"""Python binding of the GB300 LDPC library (``include/ldpc.h``).
+
+Argument marshalling only: every step of decoding runs in the CUDA kernels of
+``libldpc_gb300.so``.  PyTorch supplies device memory and streams.  There is no
+CPU fallback: importing works without the library (so the package can be
+inspected on a machine without a GPU), but every call raises if the shared
+library has not been built.
+
+The functions carry the C names (``ldpc_code_create``, ``ldpc_decode``,
+``ldpc_channel``, ``ldpc_ber_sim`` ...).  Tensors are passed by data pointer;
+``stream`` defaults to the current torch stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libldpc_gb300.so")
+
+ALGO_SP, ALGO_MS, ALGO_NOMS = 0, 1, 2
+MSG_F32, MSG_F16, MSG_I8 = 0, 1, 2
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "device wait timed out",
+          5: "unsupported"}
+
+
+class LdpcError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {detail}")
+        self.status = status
+
+
+class DecodeOpts(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int32), ("early_stop", ctypes.c_int32), ("algo", ctypes.c_int32),
+                ("msg", ctypes.c_int32), ("clip", ctypes.c_float), ("frac_bits", ctypes.c_int32),
+                ("noms_params", ctypes.c_void_p), ("reserved", ctypes.c_int32 * 4)]
+
+
+class BerResult(ctypes.Structure):
+    _fields_ = [("frames", ctypes.c_int64), ("frame_errors", ctypes.c_int64), ("bit_errors", ctypes.c_int64),
+                ("iters_sum", ctypes.c_int64), ("undetected", ctypes.c_int64), ("seconds", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+P = ctypes.c_void_p
+
+# (name, restype, argtypes) of every exported entry point
+_SIGNATURES = [
+    ("ldpc_default_opts", None, [P]),
+    ("ldpc_status_str", ctypes.c_char_p, [ctypes.c_int]),
+    ("ldpc_last_error", ctypes.c_char_p, []),
+    ("ldpc_code_create", ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P]),
+    ("ldpc_code_destroy", ctypes.c_int, [P]),
+    ("ldpc_code_dims", ctypes.c_int, [P, P, P, P, P]),
+    ("ldpc_decode", ctypes.c_int, [P, P, ctypes.c_int32, P, P, P, P, P, P]),
+    ("ldpc_channel", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, P, P]),
+    ("ldpc_ber_sim", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
+                                    ctypes.c_int64, ctypes.c_int32, P, P, P]),
+]
+
+
+def exported_names() -> list[str]:
+    return [n for n, _, _ in _SIGNATURES]
+
+
+def lib():
+    """The loaded shared library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_1204_0334_gb300.build.build() (nvcc, sm_103a)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in _SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise LdpcError(status, where, lib().ldpc_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def default_opts(**kw) -> DecodeOpts:
+    o = DecodeOpts()
+    lib().ldpc_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+# ----------------------------------------------------------------- C-named calls
+def ldpc_code_create(shifts, p: int) -> int:
+    """shifts: J x L integer matrix (-1 = zero block).  Returns the opaque handle."""
+    import numpy as np
+
+    a = np.ascontiguousarray(np.asarray(shifts, dtype=np.int32))
+    J, L = a.shape
+    h = ctypes.c_void_p()
+    _check(lib().ldpc_code_create(a.ctypes.data_as(P), J, L, p, ctypes.byref(h)), "ldpc_code_create")
+    return h.value
+
+
+def ldpc_code_destroy(code: int):
+    _check(lib().ldpc_code_destroy(code), "ldpc_code_destroy")
+
+
+def ldpc_code_dims(code: int) -> dict:
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(lib().ldpc_code_dims(code, *[ctypes.byref(x) for x in v]), "ldpc_code_dims")
+    return dict(zip(["N", "M", "E", "K"], [x.value for x in v]))
+
+
+def ldpc_decode(code: int, llr, opts: DecodeOpts, post=None, hard=None, iters=None, ok=None, stream=None):
+    gamma = llr.shape[0]
+    _check(lib().ldpc_decode(code, _ptr(llr), gamma, ctypes.byref(opts), _ptr(post), _ptr(hard), _ptr(iters),
+                             _ptr(ok), _stream(stream)), "ldpc_decode")
+
+
+def ldpc_channel(code: int, ebn0_db: float, seed: int, first_frame: int, out, stream=None):
+    _check(lib().ldpc_channel(code, ebn0_db, seed, first_frame, out.shape[0], _ptr(out), _stream(stream)),
+           "ldpc_channel")
+
+
+def ldpc_ber_sim(code: int, ebn0_db: float, seed: int, first_frame: int, max_frames: int, target_frame_errors: int,
+                 gamma: int, opts: DecodeOpts, stream=None) -> dict:
+    r = BerResult()
+    _check(lib().ldpc_ber_sim(code, ebn0_db, seed, first_frame, max_frames, target_frame_errors, gamma,
+                              ctypes.byref(opts), ctypes.byref(r), _stream(stream)), "ldpc_ber_sim")
+    return r.as_dict()
+
+
+# ----------------------------------------------------------------- convenience
+@dataclass
+class QCCode:
+    """Owning wrapper of an ldpc_code handle."""
+
+    shifts: object
+    p: int
+
+    def __post_init__(self):
+        self.handle = ldpc_code_create(self.shifts, self.p)
+        d = ldpc_code_dims(self.handle)
+        self.N, self.M, self.E, self.K = d["N"], d["M"], d["E"], d["K"]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ldpc_code_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def decode(self, llr, max_iter=30, early_stop=False, algo=ALGO_SP, msg=None, clip=30.0, frac_bits=2,
+               want_post=True, stream=None):
+        """Decode a [gamma][N] float32 tensor; returns (post, hard, iters, ok) on llr's device."""
+        import torch
+
+        if msg is None:
+            msg = MSG_I8 if algo == ALGO_MS else MSG_F32
+        gamma = llr.shape[0]
+        dev = llr.device
+        post = torch.empty((gamma, self.N), dtype=torch.float32, device=dev) if want_post else None
+        hard = torch.empty((gamma, self.N), dtype=torch.uint8, device=dev)
+        iters = torch.empty(gamma, dtype=torch.int32, device=dev)
+        ok = torch.empty(gamma, dtype=torch.int32, device=dev)
+        o = default_opts(max_iter=max_iter, early_stop=int(early_stop), algo=algo, msg=msg, clip=clip,
+                         frac_bits=frac_bits)
+        ldpc_decode(self.handle, llr.contiguous(), o, post, hard, iters, ok, stream)
+        return post, hard, iters, ok
+
+    def channel(self, ebn0_db, seed, first_frame, gamma, device="cuda", stream=None):
+        import torch
+
+        out = torch.empty((gamma, self.N), dtype=torch.float32, device=device)
+        ldpc_channel(self.handle, ebn0_db, seed, first_frame, out, stream)
+        return out
+
+    def ber_sim(self, ebn0_db, seed=1, first_frame=0, max_frames=4096, target_frame_errors=100, gamma=4096,
+                stream=None, **opt):
+        return ldpc_ber_sim(self.handle, ebn0_db, seed, first_frame, max_frames, target_frame_errors, gamma,
+                            default_opts(**opt), stream)

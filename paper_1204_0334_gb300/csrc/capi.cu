@@ -1,0 +1,314 @@
+// C-ABI entry points of the block-code decoder (include/ldpc.h).
+#include "ldpc_internal.cuh"
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+namespace ldpc {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+ldpc_status cuda_fail(cudaError_t e, const char *what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return LDPC_ECUDA;
+}
+
+int pointer_kind(const void *p) {
+    if (!p) return -1;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? 0 : 1;
+}
+
+static ldpc_status check_opts(const ldpc_code c, const ldpc_decode_opts *o) {
+    if (!o) {
+        set_error("opts is NULL");
+        return LDPC_EINVAL;
+    }
+    if (o->max_iter < 1 || o->max_iter > 100000) {
+        set_error("max_iter %d out of range [1, 100000]", o->max_iter);
+        return LDPC_EINVAL;
+    }
+    for (int i = 0; i < 4; ++i)
+        if (o->reserved[i]) {
+            set_error("reserved fields must be zero");
+            return LDPC_EINVAL;
+        }
+    if (o->algo == LDPC_ALGO_SP) {
+        if (o->msg != LDPC_MSG_F32 && o->msg != LDPC_MSG_F16) {
+            set_error("sum-product takes F32 or F16 messages");
+            return LDPC_EUNSUPPORTED;
+        }
+        if (!(o->clip > 0.0f) || !std::isfinite(o->clip) || o->clip > 60000.0f) {
+            set_error("clip must be finite, positive and representable in FP16 storage");
+            return LDPC_EINVAL;
+        }
+    } else if (o->algo == LDPC_ALGO_MS) {
+        if (o->msg != LDPC_MSG_I8) {
+            set_error("integer min-sum takes I8 messages");
+            return LDPC_EUNSUPPORTED;
+        }
+        if (o->frac_bits < 0 || o->frac_bits > 6) {
+            set_error("frac_bits %d out of range [0, 6]", o->frac_bits);
+            return LDPC_EINVAL;
+        }
+    } else if (o->algo == LDPC_ALGO_NOMS) {
+        set_error("NOMS decoding is exposed through ldpc_noms_forward");
+        return LDPC_EUNSUPPORTED;
+    } else {
+        set_error("unknown algo %d", o->algo);
+        return LDPC_EINVAL;
+    }
+    (void)c;
+    return LDPC_OK;
+}
+
+}  // namespace ldpc
+
+using namespace ldpc;
+
+extern "C" {
+
+void ldpc_default_opts(ldpc_decode_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->max_iter = 30;
+    o->early_stop = 0;
+    o->algo = LDPC_ALGO_SP;
+    o->msg = LDPC_MSG_F32;
+    o->clip = 30.0f;
+    o->frac_bits = 2;
+}
+
+const char *ldpc_status_str(ldpc_status s) {
+    switch (s) {
+        case LDPC_OK: return "ok";
+        case LDPC_EINVAL: return "invalid argument";
+        case LDPC_ENOMEM: return "out of memory";
+        case LDPC_ECUDA: return "CUDA error";
+        case LDPC_ETIMEOUT: return "device wait timed out";
+        case LDPC_EUNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char *ldpc_last_error(void) { return g_err; }
+
+ldpc_status ldpc_code_create(const int32_t *shifts, int32_t J, int32_t L, int32_t p, ldpc_code *out) {
+    if (!out) {
+        set_error("out is NULL");
+        return LDPC_EINVAL;
+    }
+    *out = nullptr;
+    if (!shifts || J < 1 || J > kMaxJ || L < 1 || L > kMaxL || p < 1) {
+        set_error("need shifts != NULL, 1 <= J <= %d, 1 <= L <= %d, p >= 1 (got J=%d L=%d p=%d)", kMaxJ, kMaxL, J, L,
+                  p);
+        return LDPC_EINVAL;
+    }
+    if ((int64_t)L * p > (1 << 26)) {
+        set_error("code too long: N = %lld", (long long)L * p);
+        return LDPC_EINVAL;
+    }
+    QcDesc d;
+    std::memset(&d, 0, sizeof(d));
+    d.J = J;
+    d.L = L;
+    d.p = p;
+    d.N = L * p;
+    d.M = J * p;
+    int e = 0, dcmax = 0;
+    for (int j = 0; j < kMaxJ * kMaxL; ++j) d.shift[j] = -1, d.eoff[j] = -1;
+    for (int j = 0; j < J; ++j) {
+        int dc = 0;
+        for (int l = 0; l < L; ++l) {
+            const int a = shifts[j * L + l];
+            if (a < -1 || a >= p) {
+                set_error("shift a[%d][%d] = %d outside {-1} u [0, %d)", j, l, a, p);
+                return LDPC_EINVAL;
+            }
+            d.shift[j * L + l] = a;
+            if (a >= 0) {
+                d.eoff[j * L + l] = e;
+                e += p;
+                ++dc;
+            }
+        }
+        dcmax = dc > dcmax ? dc : dcmax;
+    }
+    d.E = e;
+    // the kernels index by the block column, so the row degree bound is L
+    d.dc_max = L;
+    (void)dcmax;
+    ldpc_code c = new (std::nothrow) ldpc_code_s();
+    if (!c) {
+        set_error("host allocation failed");
+        return LDPC_ENOMEM;
+    }
+    c->d = d;
+    c->rate = 1.0 - (double)d.M / (double)d.N;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        c->device = 0;
+    }
+    *out = c;
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_code_destroy(ldpc_code c) {
+    if (!c) return LDPC_OK;
+    DecodeWs &w = c->ws;
+    cudaFree(w.msg);
+    cudaFree(w.mu);
+    cudaFree(w.post);
+    cudaFree(w.hw);
+    cudaFree(w.flags);
+    cudaFree(w.iters);
+    cudaFree(w.counters);
+    cudaFree(w.stage_llr);
+    cudaFree(w.stage_post);
+    cudaFree(w.stage_hard);
+    cudaFree(w.stage_i32);
+    delete c;
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_code_dims(ldpc_code c, int64_t *N, int64_t *M, int64_t *E, int64_t *K) {
+    if (!c) {
+        set_error("code is NULL");
+        return LDPC_EINVAL;
+    }
+    if (N) *N = c->d.N;
+    if (M) *M = c->d.M;
+    if (E) *E = c->d.E;
+    if (K) *K = (int64_t)c->d.N - c->d.M;
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_decode(ldpc_code c, const float *llr, int32_t gamma, const ldpc_decode_opts *opts, float *post,
+                        uint8_t *hard, int32_t *iters, int32_t *ok, void *stream) {
+    if (!c || !llr || gamma < 1) {
+        set_error("need code, llr and gamma >= 1");
+        return LDPC_EINVAL;
+    }
+    ldpc_status st = check_opts(c, opts);
+    if (st != LDPC_OK) return st;
+    const ldpc_decode_opts &o = *opts;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool host_in = pointer_kind(llr) == 1;
+    const bool host_out = (post && pointer_kind(post) == 1) || (hard && pointer_kind(hard) == 1) ||
+                          (iters && pointer_kind(iters) == 1) || (ok && pointer_kind(ok) == 1);
+    st = qc_ensure_workspace(c, (size_t)gamma, host_in || host_out);
+    if (st != LDPC_OK) return st;
+    DecodeWs &w = c->ws;
+    const size_t NB = (size_t)gamma * c->d.N;
+    const float *src = llr;
+    if (host_in) {
+        LDPC_CUDA_TRY(cudaMemcpyAsync(w.stage_llr, llr, NB * 4, cudaMemcpyHostToDevice, s));
+        src = w.stage_llr;
+    }
+    st = qc_pack_llr(c, src, gamma, o, s);
+    if (st != LDPC_OK) return st;
+    st = qc_decode_device(c, gamma, o, post != nullptr, s);
+    if (st != LDPC_OK) return st;
+    float *d_post = post && pointer_kind(post) == 1 ? w.stage_post : post;
+    uint8_t *d_hard = hard && pointer_kind(hard) == 1 ? w.stage_hard : hard;
+    int32_t *d_iters = iters && pointer_kind(iters) == 1 ? w.stage_i32 : iters;
+    int32_t *d_ok = ok && pointer_kind(ok) == 1 ? w.stage_i32 + w.gamma_cap : ok;
+    st = qc_unpack_outputs(c, gamma, o, d_post, d_hard, d_iters, d_ok, s);
+    if (st != LDPC_OK) return st;
+    if (d_post != post) LDPC_CUDA_TRY(cudaMemcpyAsync(post, d_post, NB * 4, cudaMemcpyDeviceToHost, s));
+    if (d_hard != hard) LDPC_CUDA_TRY(cudaMemcpyAsync(hard, d_hard, NB, cudaMemcpyDeviceToHost, s));
+    if (d_iters != iters) LDPC_CUDA_TRY(cudaMemcpyAsync(iters, d_iters, (size_t)gamma * 4, cudaMemcpyDeviceToHost, s));
+    if (d_ok != ok) LDPC_CUDA_TRY(cudaMemcpyAsync(ok, d_ok, (size_t)gamma * 4, cudaMemcpyDeviceToHost, s));
+    return LDPC_OK;
+}
+
+static double sigma_of(ldpc_code c, double ebn0_db) {
+    return std::sqrt(1.0 / (2.0 * c->rate * std::pow(10.0, ebn0_db / 10.0)));
+}
+
+ldpc_status ldpc_channel(ldpc_code c, double ebn0_db, uint64_t seed, uint64_t first_frame, int32_t gamma,
+                         float *llr_out, void *stream) {
+    if (!c || !llr_out || gamma < 1 || !std::isfinite(ebn0_db)) {
+        set_error("need code, llr_out, gamma >= 1 and a finite Eb/N0");
+        return LDPC_EINVAL;
+    }
+    if (!(c->rate > 0.0)) {
+        set_error("design rate K/N = %g is not positive", c->rate);
+        return LDPC_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool host_out = pointer_kind(llr_out) == 1;
+    float *dst = llr_out;
+    if (host_out) {
+        ldpc_status st = qc_ensure_workspace(c, (size_t)gamma, 1);
+        if (st != LDPC_OK) return st;
+        dst = c->ws.stage_llr;
+    }
+    ldpc_status st = qc_channel_frames(c, sigma_of(c, ebn0_db), seed, first_frame, gamma, dst, s);
+    if (st != LDPC_OK) return st;
+    if (host_out)
+        LDPC_CUDA_TRY(cudaMemcpyAsync(llr_out, dst, (size_t)gamma * c->d.N * 4, cudaMemcpyDeviceToHost, s));
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_ber_sim(ldpc_code c, double ebn0_db, uint64_t seed, uint64_t first_frame, int64_t max_frames,
+                         int64_t target_frame_errors, int32_t gamma, const ldpc_decode_opts *opts,
+                         ldpc_ber_result *out, void *stream) {
+    if (!c || !out || gamma < 1 || max_frames < 1 || !std::isfinite(ebn0_db)) {
+        set_error("need code, out, gamma >= 1, max_frames >= 1 and a finite Eb/N0");
+        return LDPC_EINVAL;
+    }
+    if (!(c->rate > 0.0)) {
+        set_error("design rate K/N = %g is not positive", c->rate);
+        return LDPC_EINVAL;
+    }
+    ldpc_status st = check_opts(c, opts);
+    if (st != LDPC_OK) return st;
+    const ldpc_decode_opts &o = *opts;
+    cudaStream_t s = (cudaStream_t)stream;
+    const auto t0 = std::chrono::steady_clock::now();
+    std::memset(out, 0, sizeof(*out));
+    st = qc_ensure_workspace(c, (size_t)gamma, 0);
+    if (st != LDPC_OK) return st;
+    const double sigma = sigma_of(c, ebn0_db);
+    LDPC_CUDA_TRY(cudaMemsetAsync(c->ws.counters, 0, 8 * sizeof(unsigned long long), s));
+    unsigned long long h[8];
+    int64_t done = 0;
+    while (done < max_frames) {
+        const int g = (int)((max_frames - done) < gamma ? (max_frames - done) : gamma);
+        st = qc_channel_packed(c, sigma, seed, first_frame + (uint64_t)done, g, o, s);
+        if (st != LDPC_OK) return st;
+        st = qc_decode_device(c, g, o, false, s);
+        if (st != LDPC_OK) return st;
+        st = qc_count_errors(c, g, o, s);
+        if (st != LDPC_OK) return st;
+        LDPC_CUDA_TRY(cudaMemcpyAsync(h, c->ws.counters, sizeof(h), cudaMemcpyDeviceToHost, s));
+        LDPC_CUDA_TRY(cudaStreamSynchronize(s));
+        done += g;
+        if ((int64_t)h[1] >= target_frame_errors) break;
+    }
+    out->frames = (int64_t)h[0];
+    out->frame_errors = (int64_t)h[1];
+    out->bit_errors = (int64_t)h[2];
+    out->iters_sum = (int64_t)h[3];
+    out->undetected = (int64_t)h[4];
+    out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return LDPC_OK;
+}
+
+}  // extern "C"

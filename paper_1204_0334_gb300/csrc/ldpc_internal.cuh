@@ -1,0 +1,91 @@
+// Internal declarations of the sm_103a LDPC library (not part of the C-ABI).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "ldpc.h"
+
+namespace ldpc {
+
+constexpr int kMaxJ = 8;
+constexpr int kMaxL = 32;
+
+// QC code description passed by value to every kernel (lives in the constant
+// parameter bank, so warp-uniform reads of shifts and block offsets are broadcasts).
+// Block (j, l) with shift a >= 0 owns p edges; edge k of the block joins check
+// j*p + ((k - a) mod p) and variable l*p + k ("variable-side" order), so both the
+// check pass and the variable pass address edges by arithmetic, not tables.
+struct QcDesc {
+    int J, L, p;
+    int N, M, E;        // variables, checks, edges
+    int dc_max;         // largest row degree over the block rows
+    int shift[kMaxJ * kMaxL];  // -1 = zero block
+    int eoff[kMaxJ * kMaxL];   // first edge of block (j, l), -1 for a zero block
+};
+
+// Device workspace of one code object, grown on demand.  Frames are grouped in
+// packages of W = 32 * V frames (V frames per lane, 4 bytes per lane per edge).
+struct DecodeWs {
+    size_t gamma_cap = 0;      // frames the buffers hold (multiple of 128)
+    size_t msg_bytes = 0;
+    void *msg = nullptr;       // [P][E][W] edge messages (one kind live at a time)
+    void *mu = nullptr;        // [P][N][W] channel LLRs (float, or int8 for MS)
+    float *post = nullptr;     // [P][N][W] posteriors (package layout)
+    uint32_t *hw = nullptr;    // [P][N][V] hard-decision words, bit = lane
+    uint32_t *flags = nullptr; // per package: done[V], unsat[2][V], valid[V], fin[V]
+    int32_t *iters = nullptr;  // [gamma_cap] in package order (frame f)
+    unsigned long long *counters = nullptr;  // [8] error counters (ber sim)
+    // host-buffer staging
+    float *stage_llr = nullptr;   // [gamma][N]
+    float *stage_post = nullptr;  // [gamma][N]
+    uint8_t *stage_hard = nullptr;
+    int32_t *stage_i32 = nullptr;  // [2][gamma]
+};
+
+}  // namespace ldpc
+
+struct ldpc_code_s {
+    ldpc::QcDesc d;
+    int device = 0;
+    double rate = 0.0;   // design rate K/N
+    ldpc::DecodeWs ws;
+};
+
+namespace ldpc {
+
+// thread-local error text
+void set_error(const char *fmt, ...);
+ldpc_status cuda_fail(cudaError_t e, const char *what);
+
+#define LDPC_CUDA_TRY(call)                                   \
+    do {                                                      \
+        cudaError_t _e = (call);                              \
+        if (_e != cudaSuccess) return ::ldpc::cuda_fail(_e, #call); \
+    } while (0)
+
+// 0: device pointer (or managed); 1: host pointer; -1: null
+int pointer_kind(const void *p);
+
+// sizes of the flags block per package
+inline int flags_per_package(int V) { return 5 * V; }
+
+// launchers implemented in qc_decode.cu
+ldpc_status qc_ensure_workspace(ldpc_code c, size_t gamma, int want_host_stage);
+ldpc_status qc_decode_device(ldpc_code c, int gamma, const ldpc_decode_opts &o, bool want_post,
+                             cudaStream_t s);
+ldpc_status qc_pack_llr(ldpc_code c, const float *llr, int gamma, const ldpc_decode_opts &o, cudaStream_t s);
+ldpc_status qc_unpack_outputs(ldpc_code c, int gamma, const ldpc_decode_opts &o, float *post, uint8_t *hard,
+                              int32_t *iters, int32_t *ok, cudaStream_t s);
+ldpc_status qc_channel_packed(ldpc_code c, double sigma, uint64_t seed, uint64_t first_frame, int gamma,
+                              const ldpc_decode_opts &o, cudaStream_t s);
+ldpc_status qc_channel_frames(ldpc_code c, double sigma, uint64_t seed, uint64_t first_frame, int gamma,
+                              float *out, cudaStream_t s);
+ldpc_status qc_count_errors(ldpc_code c, int gamma, const ldpc_decode_opts &o, cudaStream_t s);
+
+inline int lanes_per_word(int msg) { return msg == LDPC_MSG_F32 ? 1 : (msg == LDPC_MSG_F16 ? 2 : 4); }
+
+}  // namespace ldpc

@@ -1,0 +1,938 @@
+// Batched BP decoding of QC-LDPC codes on sm_103a (Algorithm 1, Sec. II-B),
+// with the device-side channel and error counting of the simulation (Sec. V).
+//
+// Data layout (HBM).  Frames are grouped in packages of W = 32*V frames; a lane
+// owns V consecutive frames and moves 4 bytes per edge (V = 1 float, V = 2
+// half, V = 4 int8), so every warp access to one edge is one 128-byte line --
+// the paper's Gamma-package idea (Sec. IV-A) at the width of a warp.
+//   msg [P][E][W]   edge messages; beta after the variable pass, alpha after the
+//                   check pass (one store per edge, Sec. IV-A)
+//   mu  [P][N][W]   channel LLRs (float; int8 for min-sum)
+//   hw  [P][N][V]   hard decisions, one 32-bit word per (variable, frame slot v)
+// Edge k of circulant block (j, l) belongs to variable l*p + k, so the check
+// pass of row j*p + r reads edge (r + a_jl) mod p of every block of row j and
+// the variable pass reads edge k of every block of column l: both are address
+// arithmetic on the shift table, with no index tables (LUT_c / LUT_v of Sec.
+// IV-A are not needed for QC codes).
+#include "ldpc_internal.cuh"
+
+#include <algorithm>
+#include <cstdio>
+
+namespace ldpc {
+
+constexpr int kWarps = 8;  // warps per block in the node kernels: 8 consecutive rows / variables
+
+// ---------------------------------------------------------------------------
+// phi(x) = -ln tanh(x/2) = ln((e^x + 1)/(e^x - 1)) = log1p(2 / expm1(x)), x >= 0.
+// phi(0) = +inf, phi(+inf) = 0, and phi is its own inverse, so eq. (bphs)
+// becomes alpha = sign * phi(sum of phi(|beta|) over the other edges).
+// Written with CUDA's expm1f / log1pf (about 1 ulp each) and a correctly
+// rounded reciprocal: errors of a few ulp here grow by two orders of magnitude
+// over 30 iterations on frames that do not converge.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float phi_f(float x) {
+    const float e = expm1f(x);
+    return log1pf(2.0f * __frcp_rn(e));
+}
+
+__device__ __forceinline__ float clipf(float x, float c) { return fminf(fmaxf(x, -c), c); }
+
+// lane word <-> V floats
+template <int V> struct Lane;
+template <> struct Lane<1> {
+    static __device__ __forceinline__ void unpack(uint32_t w, float *x) { x[0] = __uint_as_float(w); }
+    static __device__ __forceinline__ uint32_t pack(const float *x) { return __float_as_uint(x[0]); }
+};
+template <> struct Lane<2> {
+    static __device__ __forceinline__ void unpack(uint32_t w, float *x) {
+        __half2 h = *reinterpret_cast<__half2 *>(&w);
+        float2 f = __half22float2(h);
+        x[0] = f.x;
+        x[1] = f.y;
+    }
+    static __device__ __forceinline__ uint32_t pack(const float *x) {
+        __half2 h = __floats2half2_rn(x[0], x[1]);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+};
+
+// flags of one package (V words per field; bit = lane)
+struct PkgFlags {
+    uint32_t *base;
+    int V;
+    __device__ uint32_t *done() const { return base; }
+    __device__ uint32_t *unsat(int par) const { return base + (1 + par) * V; }
+    __device__ uint32_t *valid() const { return base + 3 * V; }
+    __device__ uint32_t *fin() const { return base + 4 * V; }
+};
+
+// ---------------------------------------------------------------------------
+// Check-node (horizontal) step, sum-product.  One warp = one check row of one
+// package; lane = V frames.  FIRST: the incoming messages are beta = mu (the
+// initialization of Algorithm 1 folded into the first read).  SYN: also XOR the
+// hard-decision words of the row's variables (the decisions of the previous
+// iteration) and flag frames whose check is violated.
+// Sums of phi over the other edges use prefix + suffix sums (the forward-
+// backward computation of Sec. IV-A), never "total minus own": that
+// subtraction loses the small terms when one input is unreliable.
+// ---------------------------------------------------------------------------
+template <int DCMAX, int V, bool FIRST, bool SYN>
+__global__ void __launch_bounds__(kWarps * 32)
+cn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict__ mu,
+             const uint32_t *__restrict__ hw, uint32_t *__restrict__ flags, float clip, int par) {
+    constexpr int W = 32 * V;
+    const int lane = threadIdx.x & 31;
+    const int m = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int pk = blockIdx.y;
+    if (m >= d.M) return;
+    PkgFlags F{flags + (size_t)pk * 5 * V, V};
+    bool lane_on = false, warp_on = false;
+    uint32_t act[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        act[v] = ~F.done()[v];
+        warp_on |= act[v] != 0;
+        lane_on |= (act[v] >> lane) & 1u;
+    }
+    if (!warp_on) return;
+
+    const int j = m / d.p;
+    const int r = m - j * d.p;
+    const int *sh = d.shift + j * d.L;
+    const int *eo = d.eoff + j * d.L;
+    float ph[DCMAX][V];
+    uint32_t neg[V];
+    uint32_t syn[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) neg[v] = 0u, syn[v] = 0u;
+
+#pragma unroll
+    for (int l = 0; l < DCMAX; ++l) {
+        const bool on = l < d.L && sh[l] >= 0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) ph[l][v] = 0.0f;
+        if (on) {
+            int k = r + sh[l];
+            if (k >= d.p) k -= d.p;
+            float x[V];
+            if (lane_on) {
+                if (FIRST) {
+                    const float *src = mu + ((size_t)pk * d.N + (size_t)l * d.p + k) * W + lane * V;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) x[v] = src[v];
+                } else {
+                    Lane<V>::unpack(msg[((size_t)pk * d.E + eo[l] + k) * 32 + lane], x);
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) x[v] = 1.0f;
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                ph[l][v] = phi_f(fabsf(x[v]));
+                neg[v] |= (x[v] < 0.0f ? 1u : 0u) << l;
+            }
+            if (SYN) {
+                const uint32_t *h = hw + ((size_t)pk * d.N + (size_t)l * d.p + k) * V;
+#pragma unroll
+                for (int v = 0; v < V; ++v) syn[v] ^= h[v];
+            }
+        }
+    }
+    if (SYN && lane == 0) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const uint32_t bad = syn[v] & act[v];
+            if (bad) atomicOr(F.unsat(par) + v, bad);
+        }
+    }
+    // prefix sums (in place in pre[]) then the backward sweep
+    float pre[DCMAX][V];
+    {
+        float acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = 0.0f;
+#pragma unroll
+        for (int l = 0; l < DCMAX; ++l)
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                pre[l][v] = acc[v];
+                acc[v] += ph[l][v];
+            }
+    }
+    uint32_t par_all[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) par_all[v] = __popc(neg[v]) & 1u;
+    float suf[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) suf[v] = 0.0f;
+#pragma unroll
+    for (int l = DCMAX - 1; l >= 0; --l) {
+        const bool on = l < d.L && sh[l] >= 0;
+        if (on && lane_on) {
+            int k = r + sh[l];
+            if (k >= d.p) k -= d.p;
+            float a[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const float mag = fminf(phi_f(pre[l][v] + suf[v]), clip);
+                const uint32_t s = par_all[v] ^ ((neg[v] >> l) & 1u);
+                a[v] = s ? -mag : mag;
+            }
+            msg[((size_t)pk * d.E + eo[l] + k) * 32 + lane] = Lane<V>::pack(a);
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) suf[v] += ph[l][v];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Variable-node (vertical) step + posterior + hard decision, eqs. (bpvs),
+// (bpd), (hrddcs).  One warp = one variable of one package.  STOP: frames whose
+// previous decisions satisfied every check (no flag raised by the check pass
+// that just ran) are frozen from now on: their outputs stay those of the
+// previous iteration, which is the early-stop rule.
+// ---------------------------------------------------------------------------
+template <int JMAX, int V, bool STOP, bool POST>
+__global__ void __launch_bounds__(kWarps * 32)
+vn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict__ mu, uint32_t *__restrict__ hw,
+             uint32_t *__restrict__ flags, float *__restrict__ post, int32_t *__restrict__ iters, float clip, int it,
+             int par) {
+    constexpr int W = 32 * V;
+    const int lane = threadIdx.x & 31;
+    const int n = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int pk = blockIdx.y;
+    if (n >= d.N) return;
+    PkgFlags F{flags + (size_t)pk * 5 * V, V};
+    uint32_t frozen[V];
+    bool warp_on = false, lane_on = false;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        uint32_t dn = F.done()[v];
+        if (STOP) {
+            const uint32_t newly = ~dn & ~F.unsat(par)[v];
+            if (n == 0 && lane == 0 && newly) {
+                // first warp of the package records the stop
+                F.done()[v] = dn | newly;
+                for (uint32_t b = newly; b; b &= b - 1) {
+                    const int ln = __ffs(b) - 1;
+                    iters[(size_t)pk * W + ln * V + v] = it - 1;
+                }
+            }
+            dn |= newly;
+        }
+        frozen[v] = dn;
+        warp_on |= ~dn != 0u;
+        lane_on |= ((~dn) >> lane) & 1u;
+    }
+    if (STOP && n == 0 && lane == 0) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) F.unsat(par ^ 1)[v] = 0u;
+    }
+    if (!warp_on) return;
+
+    const int l = n / d.p;
+    const int k = n - l * d.p;
+    float m[V];
+    {
+        const float *src = mu + ((size_t)pk * d.N + n) * W + lane * V;
+#pragma unroll
+        for (int v = 0; v < V; ++v) m[v] = lane_on ? src[v] : 1.0f;
+    }
+    float a[JMAX][V];
+    float tot[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) tot[v] = m[v];
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j) {
+        const bool on = j < d.J && d.shift[j * d.L + l] >= 0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) a[j][v] = 0.0f;
+        if (on && lane_on) {
+            Lane<V>::unpack(msg[((size_t)pk * d.E + d.eoff[j * d.L + l] + k) * 32 + lane], a[j]);
+#pragma unroll
+            for (int v = 0; v < V; ++v) tot[v] += a[j][v];
+        }
+    }
+    if (lane_on) {
+#pragma unroll
+        for (int j = 0; j < JMAX; ++j) {
+            const bool on = j < d.J && d.shift[j * d.L + l] >= 0;
+            if (!on) continue;
+            float b[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                float s = m[v];
+#pragma unroll
+                for (int j2 = 0; j2 < JMAX; ++j2)
+                    if (j2 != j) s += a[j2][v];
+                b[v] = clipf(s, clip);
+            }
+            msg[((size_t)pk * d.E + d.eoff[j * d.L + l] + k) * 32 + lane] = Lane<V>::pack(b);
+        }
+    }
+    float pst[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) pst[v] = clipf(tot[v], clip);
+    if (POST && lane_on) {
+        float *dst = post + ((size_t)pk * d.N + n) * W + lane * V;
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            if (!((frozen[v] >> lane) & 1u)) dst[v] = pst[v];
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const uint32_t bits = __ballot_sync(0xffffffffu, pst[v] < 0.0f);
+        if (lane == 0) {
+            uint32_t *h = hw + ((size_t)pk * d.N + n) * V + v;
+            *h = frozen[v] ? ((bits & ~frozen[v]) | (*h & frozen[v])) : bits;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Integer min-sum over int8 messages, 4 frames per lane in one 32-bit word,
+// evaluated with the byte-SIMD video instructions.  Check update:
+// |alpha_e| = min over the other edges = (|beta_e| == min1) ? min2 : min1 --
+// ties give min2 == min1, so no arg-min is needed; the sign is the parity of
+// the other signs (sign(0) = +).  Empty extrinsic set: 127.
+// ---------------------------------------------------------------------------
+template <int DCMAX, bool FIRST, bool SYN>
+__global__ void __launch_bounds__(kWarps * 32)
+cn_ms_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__restrict__ mu,
+             const uint32_t *__restrict__ hw, uint32_t *__restrict__ flags, int par) {
+    constexpr int V = 4;
+    const int lane = threadIdx.x & 31;
+    const int m = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int pk = blockIdx.y;
+    if (m >= d.M) return;
+    PkgFlags F{flags + (size_t)pk * 5 * V, V};
+    bool lane_on = false, warp_on = false;
+    uint32_t act[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        act[v] = ~F.done()[v];
+        warp_on |= act[v] != 0;
+        lane_on |= (act[v] >> lane) & 1u;
+    }
+    if (!warp_on) return;
+    const int j = m / d.p;
+    const int r = m - j * d.p;
+    const int *sh = d.shift + j * d.L;
+    const int *eo = d.eoff + j * d.L;
+    uint32_t ab[DCMAX], sg[DCMAX];
+    uint32_t min1 = 0x7f7f7f7fu, min2 = 0x7f7f7f7fu, sgn = 0u;
+    uint32_t syn[V] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int l = 0; l < DCMAX; ++l) {
+        const bool on = l < d.L && sh[l] >= 0;
+        ab[l] = 0u;
+        sg[l] = 0u;
+        if (on) {
+            int k = r + sh[l];
+            if (k >= d.p) k -= d.p;
+            uint32_t x = 0u;
+            if (lane_on) {
+                x = FIRST ? mu[((size_t)pk * d.N + (size_t)l * d.p + k) * 32 + lane]
+                          : msg[((size_t)pk * d.E + eo[l] + k) * 32 + lane];
+            }
+            const uint32_t a = __vabsss4(x);
+            sg[l] = x & 0x80808080u;
+            ab[l] = a;
+            sgn ^= sg[l];
+            min2 = __vminu4(min2, __vmaxu4(min1, a));
+            min1 = __vminu4(min1, a);
+            if (SYN) {
+                const uint32_t *h = hw + ((size_t)pk * d.N + (size_t)l * d.p + k) * V;
+#pragma unroll
+                for (int v = 0; v < V; ++v) syn[v] ^= h[v];
+            }
+        }
+    }
+    if (SYN && lane == 0) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const uint32_t bad = syn[v] & act[v];
+            if (bad) atomicOr(F.unsat(par) + v, bad);
+        }
+    }
+    if (!lane_on) return;
+#pragma unroll
+    for (int l = 0; l < DCMAX; ++l) {
+        const bool on = l < d.L && sh[l] >= 0;
+        if (!on) continue;
+        int k = r + sh[l];
+        if (k >= d.p) k -= d.p;
+        const uint32_t eq = __vcmpeq4(ab[l], min1);
+        const uint32_t mag = (min2 & eq) | (min1 & ~eq);
+        const uint32_t s = ((sgn ^ sg[l]) >> 7) & 0x01010101u;  // 1 where the output is negative
+        const uint32_t out = __vadd4(mag ^ (s * 0xffu), s);        // two's-complement negate where s
+        msg[((size_t)pk * d.E + eo[l] + k) * 32 + lane] = out;
+    }
+}
+
+__device__ __forceinline__ int sbyte(uint32_t w, int v) { return (int)(int8_t)(uint8_t)(w >> (8 * v)); }
+
+template <int JMAX, bool STOP, bool POST>
+__global__ void __launch_bounds__(kWarps * 32)
+vn_ms_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__restrict__ mu, uint32_t *__restrict__ hw,
+             uint32_t *__restrict__ flags, float *__restrict__ post, int32_t *__restrict__ iters, float lsb, int it,
+             int par) {
+    constexpr int V = 4, W = 128;
+    const int lane = threadIdx.x & 31;
+    const int n = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int pk = blockIdx.y;
+    if (n >= d.N) return;
+    PkgFlags F{flags + (size_t)pk * 5 * V, V};
+    uint32_t frozen[V];
+    bool warp_on = false, lane_on = false;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        uint32_t dn = F.done()[v];
+        if (STOP) {
+            const uint32_t newly = ~dn & ~F.unsat(par)[v];
+            if (n == 0 && lane == 0 && newly) {
+                F.done()[v] = dn | newly;
+                for (uint32_t b = newly; b; b &= b - 1) {
+                    const int ln = __ffs(b) - 1;
+                    iters[(size_t)pk * W + ln * V + v] = it - 1;
+                }
+            }
+            dn |= newly;
+        }
+        frozen[v] = dn;
+        warp_on |= ~dn != 0u;
+        lane_on |= ((~dn) >> lane) & 1u;
+    }
+    if (STOP && n == 0 && lane == 0) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) F.unsat(par ^ 1)[v] = 0u;
+    }
+    if (!warp_on) return;
+    const int l = n / d.p;
+    const int k = n - l * d.p;
+    const uint32_t qw = lane_on ? mu[((size_t)pk * d.N + n) * 32 + lane] : 0x01010101u;
+    uint32_t aw[JMAX];
+    int tot[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) tot[v] = sbyte(qw, v);
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j) {
+        const bool on = j < d.J && d.shift[j * d.L + l] >= 0;
+        aw[j] = 0u;
+        if (on && lane_on) {
+            aw[j] = msg[((size_t)pk * d.E + d.eoff[j * d.L + l] + k) * 32 + lane];
+#pragma unroll
+            for (int v = 0; v < V; ++v) tot[v] += sbyte(aw[j], v);
+        }
+    }
+    if (lane_on) {
+#pragma unroll
+        for (int j = 0; j < JMAX; ++j) {
+            const bool on = j < d.J && d.shift[j * d.L + l] >= 0;
+            if (!on) continue;
+            uint32_t out = 0u;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                int b = tot[v] - sbyte(aw[j], v);
+                b = b > 127 ? 127 : (b < -127 ? -127 : b);
+                out |= ((uint32_t)(uint8_t)(int8_t)b) << (8 * v);
+            }
+            msg[((size_t)pk * d.E + d.eoff[j * d.L + l] + k) * 32 + lane] = out;
+        }
+    }
+    if (POST && lane_on) {
+        float *dst = post + ((size_t)pk * d.N + n) * W + lane * V;
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            if (!((frozen[v] >> lane) & 1u)) dst[v] = (float)tot[v] * lsb;
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const uint32_t bits = __ballot_sync(0xffffffffu, tot[v] < 0);
+        if (lane == 0) {
+            uint32_t *h = hw + ((size_t)pk * d.N + n) * V + v;
+            *h = frozen[v] ? ((bits & ~frozen[v]) | (*h & frozen[v])) : bits;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Final syndrome of the last decisions (for ok), and the per-frame finish.
+// ---------------------------------------------------------------------------
+template <int V>
+__global__ void final_syndrome_kernel(const QcDesc d, const uint32_t *__restrict__ hw, uint32_t *__restrict__ flags,
+                                      int P) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int pk = blockIdx.y;
+    if (m >= d.M || pk >= P) return;
+    const int j = m / d.p, r = m - j * d.p;
+    uint32_t syn[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) syn[v] = 0u;
+    for (int l = 0; l < d.L; ++l) {
+        const int a = d.shift[j * d.L + l];
+        if (a < 0) continue;
+        int k = r + a;
+        if (k >= d.p) k -= d.p;
+        const uint32_t *h = hw + ((size_t)pk * d.N + (size_t)l * d.p + k) * V;
+#pragma unroll
+        for (int v = 0; v < V; ++v) syn[v] ^= h[v];
+    }
+    uint32_t *fin = flags + (size_t)pk * 5 * V + 4 * V;
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+        if (syn[v]) atomicOr(fin + v, syn[v]);
+}
+
+// flags init: done = ~valid (padding frames never run), unsat = 0, fin = 0
+__global__ void init_flags_kernel(uint32_t *flags, int P, int V, int gamma) {
+    const int pk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pk >= P) return;
+    uint32_t *b = flags + (size_t)pk * 5 * V;
+    const int W = 32 * V;
+    for (int v = 0; v < V; ++v) {
+        uint32_t valid = 0u;
+        for (int ln = 0; ln < 32; ++ln)
+            if (pk * W + ln * V + v < gamma) valid |= 1u << ln;
+        b[v] = ~valid;
+        b[V + v] = 0u;
+        b[2 * V + v] = 0u;
+        b[3 * V + v] = valid;
+        b[4 * V + v] = 0u;
+    }
+}
+
+// Per-frame finish: frames not stopped early ran max_iter iterations; ok = 1
+// iff the last decisions satisfy every check.  Results in package order
+// (frame f at iters[f], okv[f]).
+__global__ void finish_frames_kernel(const uint32_t *__restrict__ flags, int32_t *__restrict__ iters,
+                                     int32_t *__restrict__ okv, int gamma, int V, int max_iter) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= gamma) return;
+    const int W = 32 * V;
+    const int pk = f / W, ln = (f % W) / V, v = f % V;
+    const uint32_t *b = flags + (size_t)pk * 5 * V;
+    const bool stopped = (b[v] >> ln) & 1u;  // a valid frame with its done bit set stopped early
+    if (!stopped) iters[f] = max_iter;
+    okv[f] = ((b[4 * V + v] >> ln) & 1u) ? 0 : 1;
+}
+
+// ---------------------------------------------------------------------------
+// Frame-major [gamma][N] <-> package layout, through 32x32 shared-memory tiles.
+// ---------------------------------------------------------------------------
+template <typename Out>
+__global__ void pack_llr_kernel(const float *__restrict__ llr, Out *__restrict__ mu, int gamma, int N, int W,
+                                int frames_alloc, float clip, float qscale, float pad) {
+    __shared__ float tile[32][33];
+    const int f0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int i = ty; i < 32; i += blockDim.y) {
+        const int f = f0 + i, n = n0 + tx;
+        float x = pad;
+        if (f < gamma && n < N) x = llr[(size_t)f * N + n];
+        tile[i][tx] = x;
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += blockDim.y) {
+        const int n = n0 + i, f = f0 + tx;
+        if (n >= N || f >= frames_alloc) continue;
+        const float x = tile[tx][i];
+        const size_t idx = ((size_t)(f / W) * N + n) * W + (f % W);
+        if (sizeof(Out) == 1) {
+            float q = rintf(x * qscale);
+            q = fminf(fmaxf(q, -127.0f), 127.0f);
+            reinterpret_cast<int8_t *>(mu)[idx] = (int8_t)q;
+        } else {
+            reinterpret_cast<float *>(mu)[idx] = clipf(x, clip);
+        }
+    }
+}
+
+__global__ void unpack_post_kernel(const float *__restrict__ pk_post, float *__restrict__ post, int gamma, int N,
+                                   int W) {
+    __shared__ float tile[32][33];
+    const int f0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int i = ty; i < 32; i += blockDim.y) {
+        const int n = n0 + i, f = f0 + tx;
+        float x = 0.0f;
+        if (n < N && f < gamma) x = pk_post[((size_t)(f / W) * N + n) * W + (f % W)];
+        tile[i][tx] = x;
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += blockDim.y) {
+        const int f = f0 + i, n = n0 + tx;
+        if (f < gamma && n < N) post[(size_t)f * N + n] = tile[tx][i];
+    }
+}
+
+__global__ void unpack_hard_kernel(const uint32_t *__restrict__ hw, uint8_t *__restrict__ hard, int gamma, int N,
+                                   int V) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int W = 32 * V;
+    for (int f = blockIdx.y; f < gamma; f += gridDim.y) {
+        const int pk = f / W, ln = (f % W) / V, v = f % V;
+        hard[(size_t)f * N + n] = (uint8_t)((hw[((size_t)pk * N + n) * V + v] >> ln) & 1u);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Error counting for the all-zero codeword (Sec. V: errors counted after the
+// hard decisions; here on the device).  One block per package; lane = frame
+// bit; the warps split the variables.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+count_errors_kernel(const uint32_t *__restrict__ hw, const int32_t *__restrict__ okv,
+                    const int32_t *__restrict__ iters, unsigned long long *__restrict__ counters, int N, int V,
+                    int gamma) {
+    __shared__ int cnt[8][32];
+    const int pk = blockIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int W = 32 * V;
+    unsigned long long fr = 0, fe = 0, be = 0, is = 0, ud = 0;
+    for (int v = 0; v < V; ++v) {
+        int c = 0;
+        for (int n = w; n < N; n += 8) c += (hw[((size_t)pk * N + n) * V + v] >> lane) & 1u;
+        cnt[w][lane] = c;
+        __syncthreads();
+        if (w == 0) {
+            int tot = 0;
+            for (int i = 0; i < 8; ++i) tot += cnt[i][lane];
+            const int f = pk * W + lane * V + v;
+            if (f < gamma) {
+                const bool okf = okv[f] != 0;
+                fr += 1;
+                be += (unsigned long long)tot;
+                fe += tot > 0 ? 1 : 0;
+                ud += (tot > 0 && okf) ? 1 : 0;
+                is += (unsigned long long)iters[f];
+            }
+        }
+        __syncthreads();
+    }
+    if (w == 0) {
+        for (int o = 16; o > 0; o >>= 1) {
+            fr += __shfl_xor_sync(0xffffffffu, fr, o);
+            fe += __shfl_xor_sync(0xffffffffu, fe, o);
+            be += __shfl_xor_sync(0xffffffffu, be, o);
+            is += __shfl_xor_sync(0xffffffffu, is, o);
+            ud += __shfl_xor_sync(0xffffffffu, ud, o);
+        }
+        if (lane == 0) {
+            atomicAdd(counters + 0, fr);
+            atomicAdd(counters + 1, fe);
+            atomicAdd(counters + 2, be);
+            atomicAdd(counters + 3, is);
+            atomicAdd(counters + 4, ud);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Channel: Philox4x32-10 (Salmon et al., SC'11) + Box-Muller, all-zero codeword.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                              uint32_t k1, uint32_t *o) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    o[0] = c0;
+    o[1] = c1;
+    o[2] = c2;
+    o[3] = c3;
+}
+
+// four channel LLRs of bits 4q..4q+3 of frame F
+__device__ __forceinline__ void channel_quad(uint64_t seed, uint64_t F, int q, float sigma, float s2, float *mu4) {
+    uint32_t w[4];
+    philox4x32_10((uint32_t)q, (uint32_t)F, (uint32_t)(F >> 32), 0u, (uint32_t)seed, (uint32_t)(seed >> 32), w);
+#pragma unroll
+    for (int pr = 0; pr < 2; ++pr) {
+        const float u0 = ((float)(w[2 * pr] >> 9) + 0.5f) * 1.1920928955078125e-07f;
+        const float u1 = ((float)(w[2 * pr + 1] >> 9) + 0.5f) * 1.1920928955078125e-07f;
+        const float rr = sqrtf(-2.0f * logf(u0));
+        float sn, cs;
+        sincospif(2.0f * u1, &sn, &cs);
+        mu4[2 * pr] = s2 * (1.0f + sigma * (rr * cs));
+        mu4[2 * pr + 1] = s2 * (1.0f + sigma * (rr * sn));
+    }
+}
+
+// straight into the package layout; thread x = frame within the package, y = bit quad
+template <typename Out>
+__global__ void channel_packed_kernel(Out *__restrict__ mu, int N, int W, int gamma, int frames_alloc,
+                                      uint64_t seed, uint64_t first_frame, float sigma, float s2, float clip,
+                                      float qscale) {
+    const int fw = threadIdx.x;
+    const int pk = blockIdx.y;
+    const int q = blockIdx.x * blockDim.y + threadIdx.y;
+    const int f = pk * W + fw;
+    if (4 * q >= N || f >= frames_alloc) return;
+    float v4[4];
+    if (f < gamma) {
+        channel_quad(seed, first_frame + (uint64_t)f, q, sigma, s2, v4);
+    } else {
+        v4[0] = v4[1] = v4[2] = v4[3] = clip;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int n = 4 * q + e;
+        if (n >= N) break;
+        const size_t idx = ((size_t)pk * N + n) * W + fw;
+        if (sizeof(Out) == 1) {
+            float qv = rintf(v4[e] * qscale);
+            qv = fminf(fmaxf(qv, -127.0f), 127.0f);
+            reinterpret_cast<int8_t *>(mu)[idx] = (int8_t)qv;
+        } else {
+            reinterpret_cast<float *>(mu)[idx] = clipf(v4[e], clip);
+        }
+    }
+}
+
+__global__ void channel_frames_kernel(float *__restrict__ out, int N, int gamma, uint64_t seed, uint64_t first_frame,
+                                      float sigma, float s2) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (4 * q >= N) return;
+    for (int f = blockIdx.y; f < gamma; f += gridDim.y) {
+        float v4[4];
+        channel_quad(seed, first_frame + (uint64_t)f, q, sigma, s2, v4);
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (4 * q + e < N) out[(size_t)f * N + 4 * q + e] = v4[e];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+ldpc_status qc_ensure_workspace(ldpc_code c, size_t gamma, int want_host_stage) {
+    DecodeWs &w = c->ws;
+    const size_t need = round_up(gamma, 128);
+    const bool grow = need > w.gamma_cap;
+    const bool stage_missing = want_host_stage && !w.stage_llr;
+    if (!grow && !stage_missing) return LDPC_OK;
+    const size_t cap = grow ? need : w.gamma_cap;
+    if (grow) {
+        // synchronous reallocation (first use or a larger batch)
+        LDPC_CUDA_TRY(cudaDeviceSynchronize());
+        cudaFree(w.msg);
+        cudaFree(w.mu);
+        cudaFree(w.post);
+        cudaFree(w.hw);
+        cudaFree(w.flags);
+        cudaFree(w.iters);
+        cudaFree(w.counters);
+        cudaFree(w.stage_llr);
+        cudaFree(w.stage_post);
+        cudaFree(w.stage_hard);
+        cudaFree(w.stage_i32);
+        w = DecodeWs();
+        const size_t P32 = cap / 32;
+        if (cudaMalloc(&w.msg, (size_t)c->d.E * cap * 4) != cudaSuccess ||
+            cudaMalloc(&w.mu, (size_t)c->d.N * cap * 4) != cudaSuccess ||
+            cudaMalloc(&w.post, (size_t)c->d.N * cap * 4) != cudaSuccess ||
+            cudaMalloc(&w.hw, (size_t)c->d.N * P32 * 4) != cudaSuccess ||
+            cudaMalloc(&w.flags, P32 * 5 * 4) != cudaSuccess ||
+            cudaMalloc(&w.iters, cap * 2 * 4) != cudaSuccess ||
+            cudaMalloc(&w.counters, 8 * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("device allocation for %zu frames failed", cap);
+            return LDPC_ENOMEM;
+        }
+        w.gamma_cap = cap;
+        w.msg_bytes = (size_t)c->d.E * cap * 4;
+    }
+    if (want_host_stage && !w.stage_llr) {
+        if (cudaMalloc(&w.stage_llr, (size_t)c->d.N * cap * 4) != cudaSuccess ||
+            cudaMalloc(&w.stage_post, (size_t)c->d.N * cap * 4) != cudaSuccess ||
+            cudaMalloc(&w.stage_hard, (size_t)c->d.N * cap) != cudaSuccess ||
+            cudaMalloc(&w.stage_i32, cap * 2 * 4) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("device staging allocation for %zu frames failed", cap);
+            return LDPC_ENOMEM;
+        }
+    }
+    return LDPC_OK;
+}
+
+static int words_per_lane(const ldpc_decode_opts &o) { return lanes_per_word(o.msg); }
+
+ldpc_status qc_pack_llr(ldpc_code c, const float *llr, int gamma, const ldpc_decode_opts &o, cudaStream_t s) {
+    const int V = words_per_lane(o), W = 32 * V;
+    const int P = (gamma + W - 1) / W;
+    dim3 blk(32, 8), grd((c->d.N + 31) / 32, (P * W + 31) / 32);
+    if (o.algo == LDPC_ALGO_MS) {
+        pack_llr_kernel<int8_t><<<grd, blk, 0, s>>>(llr, (int8_t *)c->ws.mu, gamma, c->d.N, W, P * W, 0.0f,
+                                                    ldexpf(1.0f, o.frac_bits), 1e30f);
+    } else {
+        pack_llr_kernel<float><<<grd, blk, 0, s>>>(llr, (float *)c->ws.mu, gamma, c->d.N, W, P * W, o.clip, 1.0f,
+                                                   o.clip);
+    }
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
+template <int DCMAX, int V, bool FIRST, bool SYN>
+static void launch_cn_sp(ldpc_code c, int P, const ldpc_decode_opts &o, int par, cudaStream_t s) {
+    dim3 grd((c->d.M + kWarps - 1) / kWarps, P);
+    cn_sp_kernel<DCMAX, V, FIRST, SYN><<<grd, kWarps * 32, 0, s>>>(c->d, (uint32_t *)c->ws.msg,
+                                                                   (const float *)c->ws.mu, c->ws.hw, c->ws.flags,
+                                                                   o.clip, par);
+}
+template <int DCMAX, bool FIRST, bool SYN>
+static void launch_cn_ms(ldpc_code c, int P, int par, cudaStream_t s) {
+    dim3 grd((c->d.M + kWarps - 1) / kWarps, P);
+    cn_ms_kernel<DCMAX, FIRST, SYN><<<grd, kWarps * 32, 0, s>>>(c->d, (uint32_t *)c->ws.msg,
+                                                               (const uint32_t *)c->ws.mu, c->ws.hw, c->ws.flags,
+                                                               par);
+}
+
+template <int DCMAX>
+static void cn_dispatch(ldpc_code c, int P, const ldpc_decode_opts &o, bool first, bool syn, int par,
+                        cudaStream_t s) {
+    if (o.algo == LDPC_ALGO_MS) {
+        if (first) launch_cn_ms<DCMAX, true, false>(c, P, par, s);
+        else if (syn) launch_cn_ms<DCMAX, false, true>(c, P, par, s);
+        else launch_cn_ms<DCMAX, false, false>(c, P, par, s);
+    } else if (o.msg == LDPC_MSG_F16) {
+        if (first) launch_cn_sp<DCMAX, 2, true, false>(c, P, o, par, s);
+        else if (syn) launch_cn_sp<DCMAX, 2, false, true>(c, P, o, par, s);
+        else launch_cn_sp<DCMAX, 2, false, false>(c, P, o, par, s);
+    } else {
+        if (first) launch_cn_sp<DCMAX, 1, true, false>(c, P, o, par, s);
+        else if (syn) launch_cn_sp<DCMAX, 1, false, true>(c, P, o, par, s);
+        else launch_cn_sp<DCMAX, 1, false, false>(c, P, o, par, s);
+    }
+}
+
+template <int JMAX, bool STOP, bool POST>
+static void launch_vn(ldpc_code c, int P, const ldpc_decode_opts &o, int it, int par, cudaStream_t s) {
+    dim3 grd((c->d.N + kWarps - 1) / kWarps, P);
+    if (o.algo == LDPC_ALGO_MS) {
+        vn_ms_kernel<JMAX, STOP, POST><<<grd, kWarps * 32, 0, s>>>(
+            c->d, (uint32_t *)c->ws.msg, (const uint32_t *)c->ws.mu, c->ws.hw, c->ws.flags, c->ws.post,
+            c->ws.iters, ldexpf(1.0f, -o.frac_bits), it, par);
+    } else if (o.msg == LDPC_MSG_F16) {
+        vn_sp_kernel<JMAX, 2, STOP, POST><<<grd, kWarps * 32, 0, s>>>(c->d, (uint32_t *)c->ws.msg,
+                                                                      (const float *)c->ws.mu, c->ws.hw,
+                                                                      c->ws.flags, c->ws.post, c->ws.iters, o.clip,
+                                                                      it, par);
+    } else {
+        vn_sp_kernel<JMAX, 1, STOP, POST><<<grd, kWarps * 32, 0, s>>>(c->d, (uint32_t *)c->ws.msg,
+                                                                      (const float *)c->ws.mu, c->ws.hw,
+                                                                      c->ws.flags, c->ws.post, c->ws.iters, o.clip,
+                                                                      it, par);
+    }
+}
+
+template <int JMAX>
+static void vn_dispatch(ldpc_code c, int P, const ldpc_decode_opts &o, bool stop, bool post, int it, int par,
+                        cudaStream_t s) {
+    if (stop) {
+        if (post) launch_vn<JMAX, true, true>(c, P, o, it, par, s);
+        else launch_vn<JMAX, true, false>(c, P, o, it, par, s);
+    } else {
+        if (post) launch_vn<JMAX, false, true>(c, P, o, it, par, s);
+        else launch_vn<JMAX, false, false>(c, P, o, it, par, s);
+    }
+}
+
+ldpc_status qc_decode_device(ldpc_code c, int gamma, const ldpc_decode_opts &o, bool want_post, cudaStream_t s) {
+    const int V = words_per_lane(o), W = 32 * V;
+    const int P = (gamma + W - 1) / W;
+    init_flags_kernel<<<(P + 127) / 128, 128, 0, s>>>(c->ws.flags, P, V, gamma);
+    LDPC_CUDA_TRY(cudaMemsetAsync(c->ws.hw, 0, (size_t)P * c->d.N * V * 4, s));
+    const int dcm = c->d.dc_max;
+    for (int it = 1; it <= o.max_iter; ++it) {
+        const bool first = it == 1;
+        const bool syn = o.early_stop && it >= 2;
+        const int par = it & 1;
+        if (dcm <= 8) cn_dispatch<8>(c, P, o, first, syn, par, s);
+        else if (dcm <= 16) cn_dispatch<16>(c, P, o, first, syn, par, s);
+        else if (dcm <= 24) cn_dispatch<24>(c, P, o, first, syn, par, s);
+        else cn_dispatch<32>(c, P, o, first, syn, par, s);
+        if (c->d.J <= 4) vn_dispatch<4>(c, P, o, syn, want_post, it, par, s);
+        else vn_dispatch<8>(c, P, o, syn, want_post, it, par, s);
+    }
+    {
+        dim3 grd((c->d.M + 127) / 128, P);
+        if (V == 1) final_syndrome_kernel<1><<<grd, 128, 0, s>>>(c->d, c->ws.hw, c->ws.flags, P);
+        else if (V == 2) final_syndrome_kernel<2><<<grd, 128, 0, s>>>(c->d, c->ws.hw, c->ws.flags, P);
+        else final_syndrome_kernel<4><<<grd, 128, 0, s>>>(c->d, c->ws.hw, c->ws.flags, P);
+    }
+    finish_frames_kernel<<<(gamma + 255) / 256, 256, 0, s>>>(c->ws.flags, c->ws.iters,
+                                                             c->ws.iters + c->ws.gamma_cap, gamma, V, o.max_iter);
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
+ldpc_status qc_unpack_outputs(ldpc_code c, int gamma, const ldpc_decode_opts &o, float *post, uint8_t *hard,
+                              int32_t *iters, int32_t *ok, cudaStream_t s) {
+    const int V = words_per_lane(o), W = 32 * V;
+    if (iters) LDPC_CUDA_TRY(cudaMemcpyAsync(iters, c->ws.iters, (size_t)gamma * 4, cudaMemcpyDeviceToDevice, s));
+    if (ok)
+        LDPC_CUDA_TRY(cudaMemcpyAsync(ok, c->ws.iters + c->ws.gamma_cap, (size_t)gamma * 4, cudaMemcpyDeviceToDevice,
+                                      s));
+    if (post) {
+        dim3 blk(32, 8), grd((c->d.N + 31) / 32, (gamma + 31) / 32);
+        unpack_post_kernel<<<grd, blk, 0, s>>>(c->ws.post, post, gamma, c->d.N, W);
+    }
+    if (hard) {
+        dim3 grd((c->d.N + 255) / 256, gamma < 65535 ? gamma : 65535);
+        unpack_hard_kernel<<<grd, 256, 0, s>>>(c->ws.hw, hard, gamma, c->d.N, V);
+    }
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
+ldpc_status qc_channel_packed(ldpc_code c, double sigma, uint64_t seed, uint64_t first_frame, int gamma,
+                              const ldpc_decode_opts &o, cudaStream_t s) {
+    const int V = words_per_lane(o), W = 32 * V;
+    const int P = (gamma + W - 1) / W;
+    const int Q = (c->d.N + 3) / 4;
+    const int ty = 256 / W > 0 ? 256 / W : 1;
+    dim3 blk(W, ty), grd((Q + ty - 1) / ty, P);
+    const float fs = (float)sigma, s2 = (float)(2.0 / (sigma * sigma));
+    if (o.algo == LDPC_ALGO_MS)
+        channel_packed_kernel<int8_t><<<grd, blk, 0, s>>>((int8_t *)c->ws.mu, c->d.N, W, gamma, P * W, seed,
+                                                          first_frame, fs, s2, 1e30f, ldexpf(1.0f, o.frac_bits));
+    else
+        channel_packed_kernel<float><<<grd, blk, 0, s>>>((float *)c->ws.mu, c->d.N, W, gamma, P * W, seed,
+                                                         first_frame, fs, s2, o.clip, 1.0f);
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
+ldpc_status qc_channel_frames(ldpc_code c, double sigma, uint64_t seed, uint64_t first_frame, int gamma, float *out,
+                              cudaStream_t s) {
+    const int Q = (c->d.N + 3) / 4;
+    dim3 grd((Q + 127) / 128, gamma < 65535 ? gamma : 65535);
+    channel_frames_kernel<<<grd, 128, 0, s>>>(out, c->d.N, gamma, seed, first_frame, (float)sigma,
+                                              (float)(2.0 / (sigma * sigma)));
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
+ldpc_status qc_count_errors(ldpc_code c, int gamma, const ldpc_decode_opts &o, cudaStream_t s) {
+    const int V = words_per_lane(o), W = 32 * V;
+    const int P = (gamma + W - 1) / W;
+    count_errors_kernel<<<P, 256, 0, s>>>(c->ws.hw, c->ws.iters + c->ws.gamma_cap, c->ws.iters, c->ws.counters, c->d.N, V, gamma);
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
+}  // namespace ldpc

@@ -1,0 +1,66 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every symbol that
+include/*.h declares, and rejects bad arguments before touching a device."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1204_0334_gb300 import build as b
+
+    path = b.build()
+    return ctypes.CDLL(path)
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(ldpc\w*)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["ldpc_code_create", "ldpc_decode", "ldpc_channel", "ldpc_ber_sim"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header():
+    import paper_1204_0334_gb300 as pkg
+
+    assert set(pkg.exported_names()) <= set(declared_functions())
+    assert set(declared_functions()) <= set(pkg.exported_names())
+
+
+def test_validation_without_a_device(lib):
+    import paper_1204_0334_gb300 as pkg
+
+    pkg.lib()
+    with pytest.raises(pkg.LdpcError) as e:
+        pkg.ldpc_code_create(np.array([[0, 64]]), 64)  # shift out of [0, p)
+    assert e.value.status == 1 and "shift" in str(e.value)
+    with pytest.raises(pkg.LdpcError):
+        pkg.ldpc_code_create(np.array([[-2, 0]]), 64)
+    with pytest.raises(pkg.LdpcError):
+        pkg.ldpc_code_create(np.zeros((2, 40), dtype=np.int32), 8)  # L > 32
+    h = pkg.ldpc_code_create(np.array([[0, 1, -1], [2, -1, 3]]), 5)
+    d = pkg.ldpc_code_dims(h)
+    assert d == {"N": 15, "M": 10, "E": 20, "K": 5}
+    o = pkg.default_opts()
+    assert (o.max_iter, o.algo, o.msg, o.clip, o.frac_bits) == (30, 0, 0, 30.0, 2)
+    pkg.ldpc_code_destroy(h)
+    assert lib.ldpc_status_str(1) is not None

@@ -1,0 +1,270 @@
+"""GPU parity of the QC block-code decoder against the CPU oracle (through the C-ABI).
+
+Tolerances (FP32 sum-product against the FP64 oracle): every posterior within
+1e-4 * max(1, |oracle|) after clipping at +-30; hard decisions identical wherever
+|oracle posterior| >= 1e-3 (closer to zero the sign is decided by rounding);
+iteration counts and the ok flag identical.  Integer min-sum is bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import TREE_BASES, brute_force_llr
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1204_0334_gb300 as p
+
+    p.lib()
+    return p
+
+
+def _graph(shifts, p):
+    H = oracle.qc_parity_check(shifts, p)
+    rp, col = oracle.csr_rows(H)
+    return H, rp, col
+
+
+def _cmp_sp(post, hard, iters, ok, ref, label=""):
+    po, ho, io, oo = ref
+    p = post.cpu().numpy().astype(np.float64)
+    err = np.abs(p - po) / np.maximum(1.0, np.abs(po))
+    assert err.max() <= REL, f"{label} max rel deviation {err.max():.3e}"
+    sure = np.abs(po) >= 1e-3
+    h = hard.cpu().numpy()
+    assert np.array_equal(h[sure], ho[sure]), label
+    assert np.array_equal(iters.cpu().numpy(), io), label
+    assert np.array_equal(ok.cpu().numpy(), oo), label
+    return err.max()
+
+
+def test_cfg1_sum_product_parity(pkg):
+    """(3,6) QC code, p = 64 (n = 384), Eb/N0 = 2 dB, 32 frames, 30 iterations, no early stop."""
+    shifts = synth.qc_shifts(3, 6, 64, seed=1)
+    H, rp, col = _graph(shifts, 64)
+    code = pkg.QCCode(shifts, 64)
+    mu = synth.gaussian_llrs(32, code.N, seed=1001, ebn0_db=2.0, rate=0.5)
+    out = code.decode(torch.from_numpy(mu).cuda(), max_iter=30)
+    ref = oracle.sp_decode(rp, col, code.N, mu, 30)
+    _cmp_sp(*out, ref, "cfg1")
+
+
+@pytest.mark.parametrize("iters", [1, 2, 5])
+def test_sum_product_each_iteration(pkg, iters):
+    shifts = synth.qc_shifts(3, 6, 64, seed=1)
+    H, rp, col = _graph(shifts, 64)
+    code = pkg.QCCode(shifts, 64)
+    mu = synth.gaussian_llrs(64, code.N, seed=7, ebn0_db=1.0, rate=0.5)
+    out = code.decode(torch.from_numpy(mu).cuda(), max_iter=iters)
+    _cmp_sp(*out, oracle.sp_decode(rp, col, code.N, mu, iters), f"it{iters}")
+
+
+@pytest.mark.parametrize("gamma", [1, 31, 33, 100, 257])
+def test_ragged_frame_counts_early_stop(pkg, gamma):
+    """Frame counts that leave partial packages; early stop freezes each frame at its own iteration."""
+    shifts = synth.qc_shifts(4, 8, 37, seed=3)
+    H, rp, col = _graph(shifts, 37)
+    code = pkg.QCCode(shifts, 37)
+    mu = synth.gaussian_llrs(gamma, code.N, seed=gamma, ebn0_db=2.5, rate=0.5)
+    out = code.decode(torch.from_numpy(mu).cuda(), max_iter=25, early_stop=True)
+    ref = oracle.sp_decode(rp, col, code.N, mu, 25, early_stop=True, nthreads=8)
+    _cmp_sp(*out, ref, f"gamma{gamma}")
+    assert len(set(ref[2].tolist())) > 1 or gamma < 8  # frames stopped at different iterations
+
+
+def test_irregular_code_with_zero_blocks(pkg):
+    shifts = synth.qc_shifts(4, 12, 29, seed=5, zero_blocks=9)
+    assert (shifts < 0).sum() >= 9
+    H, rp, col = _graph(shifts, 29)
+    code = pkg.QCCode(shifts, 29)
+    mu = synth.gaussian_llrs(96, code.N, seed=2, ebn0_db=2.0, rate=1 - 4 / 12)
+    out = code.decode(torch.from_numpy(mu).cuda(), max_iter=12, early_stop=True)
+    _cmp_sp(*out, oracle.sp_decode(rp, col, code.N, mu, 12, early_stop=True, nthreads=8), "irregular")
+
+
+@pytest.mark.parametrize("name", sorted(TREE_BASES))
+def test_trees_exact_marginals(pkg, name):
+    """Cycle-free graphs (lifted by p = 2): the GPU posterior equals brute-force marginals within FP32 error."""
+    base = np.array(TREE_BASES[name])
+    code = pkg.QCCode(base, 2)
+    H = oracle.qc_parity_check(base, 2)
+    rng = np.random.default_rng(17)
+    mu = rng.normal(1.0, 1.5, size=(32, code.N)).astype(np.float32)
+    post, hard, _, _ = code.decode(torch.from_numpy(mu).cuda(), max_iter=12)
+    p = post.cpu().numpy()
+    for f in range(0, 32, 8):
+        want = brute_force_llr(H, mu[f])
+        assert np.allclose(p[f], want, rtol=1e-5, atol=1e-5), name
+
+
+def test_min_sum_bit_exact(pkg):
+    """int8 min-sum: posteriors, decisions, iteration counts and ok identical to the integer oracle."""
+    shifts = synth.qc_shifts(3, 6, 64, seed=1)
+    H, rp, col = _graph(shifts, 64)
+    code = pkg.QCCode(shifts, 64)
+    for seed, es, ebn0 in [(1, False, 2.0), (2, True, 2.5), (3, True, 1.0)]:
+        mu = synth.gaussian_llrs(200, code.N, seed=seed, ebn0_db=ebn0, rate=0.5)
+        post, hard, iters, ok = code.decode(torch.from_numpy(mu).cuda(), max_iter=20, early_stop=es,
+                                            algo=pkg.ALGO_MS)
+        po, ho, io, oo = oracle.ms_decode(rp, col, code.N, mu, 20, early_stop=es, nthreads=8)
+        assert np.array_equal(post.cpu().numpy(), po.astype(np.float32) * 0.25)
+        assert np.array_equal(hard.cpu().numpy(), ho)
+        assert np.array_equal(iters.cpu().numpy(), io)
+        assert np.array_equal(ok.cpu().numpy(), oo)
+
+
+def test_min_sum_saturation_and_ties(pkg):
+    """Coarse LLR grid (exact ties, zeros, values beyond the int8 range), irregular code."""
+    shifts = synth.qc_shifts(4, 8, 16, seed=6, zero_blocks=3)
+    H, rp, col = _graph(shifts, 16)
+    code = pkg.QCCode(shifts, 16)
+    mu = synth.integer_llrs(130, code.N, seed=4, lo=-200, hi=200, scale=0.25)
+    post, hard, iters, ok = code.decode(torch.from_numpy(mu).cuda(), max_iter=9, early_stop=True, algo=pkg.ALGO_MS)
+    po, ho, io, oo = oracle.ms_decode(rp, col, code.N, mu, 9, early_stop=True)
+    assert np.array_equal(post.cpu().numpy(), po.astype(np.float32) * 0.25)
+    assert np.array_equal(hard.cpu().numpy(), ho)
+    assert np.array_equal(iters.cpu().numpy(), io) and np.array_equal(ok.cpu().numpy(), oo)
+
+
+def test_fp16_storage_deviation(pkg):
+    """FP16 message storage (FP32 arithmetic): decisions of clean frames agree; LLR error reported, bounded."""
+    shifts = synth.qc_shifts(3, 6, 64, seed=1)
+    H, rp, col = _graph(shifts, 64)
+    code = pkg.QCCode(shifts, 64)
+    mu = synth.gaussian_llrs(256, code.N, seed=9, ebn0_db=2.5, rate=0.5)
+    post, hard, iters, ok = code.decode(torch.from_numpy(mu).cuda(), max_iter=30, early_stop=True,
+                                        msg=pkg.MSG_F16)
+    po, ho, io, oo = oracle.sp_decode(rp, col, code.N, mu, 30, early_stop=True, nthreads=8)
+    okg = ok.cpu().numpy()
+    both = (okg == 1) & (oo == 1)
+    assert both.sum() >= 0.95 * oo.sum()
+    assert np.array_equal(hard.cpu().numpy()[both], ho[both])
+    # one iteration: the only error is the FP16 rounding of the stored messages
+    post1 = code.decode(torch.from_numpy(mu).cuda(), max_iter=1, msg=pkg.MSG_F16)[0].cpu().numpy()
+    p1 = oracle.sp_decode(rp, col, code.N, mu, 1)[0]
+    assert np.max(np.abs(post1 - p1) / np.maximum(1, np.abs(p1))) < 4e-3
+
+
+def test_host_buffers(pkg):
+    """Host (pageable and pinned) inputs and outputs are staged through the device workspace."""
+    shifts = synth.qc_shifts(3, 6, 64, seed=1)
+    H, rp, col = _graph(shifts, 64)
+    code = pkg.QCCode(shifts, 64)
+    mu = synth.gaussian_llrs(40, code.N, seed=12, ebn0_db=2.0, rate=0.5)
+    ref = oracle.sp_decode(rp, col, code.N, mu, 10)
+    for pin in (False, True):
+        llr = torch.from_numpy(mu)
+        if pin:
+            llr = llr.pin_memory()
+        post = torch.empty((40, code.N), dtype=torch.float32, pin_memory=pin)
+        hard = torch.empty((40, code.N), dtype=torch.uint8, pin_memory=pin)
+        iters = torch.empty(40, dtype=torch.int32, pin_memory=pin)
+        ok = torch.empty(40, dtype=torch.int32, pin_memory=pin)
+        o = pkg.default_opts(max_iter=10)
+        pkg.ldpc_decode(code.handle, llr, o, post, hard, iters, ok)
+        torch.cuda.synchronize()
+        _cmp_sp(post, hard, iters, ok, ref, f"host pin={pin}")
+
+
+def test_channel_matches_oracle(pkg):
+    """Philox4x32-10 + Box-Muller on the device equals the oracle's double-precision channel to FP32 error."""
+    shifts = synth.qc_shifts(3, 6, 64, seed=1)
+    code = pkg.QCCode(shifts, 64)
+    for ebn0, first in [(2.0, 0), (4.5, 123456789012)]:
+        out = code.channel(ebn0, seed=77, first_frame=first, gamma=50).cpu().numpy().astype(np.float64)
+        sigma = oracle.sigma_from_ebn0(ebn0, 0.5)
+        mu, g = oracle.channel_awgn(77, first, 50, code.N, sigma, return_g=True)
+        mu64 = 2 * (1 + sigma * g) / sigma**2
+        s2 = 2 / sigma**2
+        tol = s2 * (8e-7 * sigma * np.abs(g) + 2.4e-7 * (1 + np.abs(1 + sigma * g))) + 1.2e-7 * np.abs(mu64)
+        assert np.all(np.abs(out - mu64) <= tol + 1e-7)
+
+
+def test_ber_sim_counts_match_oracle(pkg):
+    """Device channel + decode + device error count equals the oracle's counts on the same frames."""
+    shifts = synth.qc_shifts(3, 6, 64, seed=1)
+    H, rp, col = _graph(shifts, 64)
+    code = pkg.QCCode(shifts, 64)
+    sigma = oracle.sigma_from_ebn0(1.75, 0.5)
+    res = code.ber_sim(1.75, seed=5, first_frame=10, max_frames=300, target_frame_errors=10 ** 9, gamma=128,
+                       max_iter=20, early_stop=1)
+    assert res["frames"] == 300
+    mu = oracle.channel_awgn(5, 10, 300, code.N, sigma)
+    po, ho, io, oo = oracle.sp_decode(rp, col, code.N, mu, 20, early_stop=True, nthreads=8)
+    errs = ho.sum(axis=1)
+    marginal = (np.abs(po) < 1e-2).any(axis=1)  # frames whose outcome rounding could change
+    want = {"frame_errors": int((errs > 0).sum()), "bit_errors": int(errs.sum()), "iters_sum": int(io.sum()),
+            "undetected": int(((errs > 0) & (oo == 1)).sum())}
+    slack = int(marginal.sum())
+    assert abs(res["frame_errors"] - want["frame_errors"]) <= slack
+    if slack == 0:
+        for k, v in want.items():
+            assert res[k] == v, (k, res[k], v)
+    assert want["frame_errors"] > 0
+
+
+def test_ber_sim_stops_after_target_errors(pkg):
+    shifts = synth.qc_shifts(3, 6, 64, seed=1)
+    code = pkg.QCCode(shifts, 64)
+    res = code.ber_sim(0.5, seed=1, max_frames=10 ** 6, target_frame_errors=100, gamma=256, max_iter=10)
+    assert res["frame_errors"] >= 100 and res["frames"] % 256 == 0 and res["frames"] <= 10 ** 6
+
+
+def test_resume_adds_up(pkg):
+    """A run split at a frame boundary gives the counts of the whole run (counter-based channel)."""
+    shifts = synth.qc_shifts(3, 6, 64, seed=1)
+    code = pkg.QCCode(shifts, 64)
+    kw = dict(target_frame_errors=10 ** 9, gamma=64, max_iter=15, early_stop=1)
+    whole = code.ber_sim(1.5, seed=3, first_frame=0, max_frames=256, **kw)
+    a = code.ber_sim(1.5, seed=3, first_frame=0, max_frames=128, **kw)
+    b = code.ber_sim(1.5, seed=3, first_frame=128, max_frames=128, **kw)
+    for k in ("frames", "frame_errors", "bit_errors", "iters_sum", "undetected"):
+        assert whole[k] == a[k] + b[k], k
+
+
+def test_full_size_code_sampled_parity(pkg):
+    """n = 18360 (4 x 24, p = 765) at the benchmark's launch configuration (4096 frames, early stop):
+    sampled frames against the oracle; every frame flagged ok satisfies H c = 0."""
+    import scipy.sparse as sp
+
+    shifts = synth.qc_shifts(4, 24, 765, seed=2)
+    H, rp, col = _graph(shifts, 765)
+    code = pkg.QCCode(shifts, 765)
+    gamma = 4096
+    mu = synth.gaussian_llrs(gamma, code.N, seed=31, ebn0_db=3.0, rate=20 / 24)
+    post, hard, iters, ok = code.decode(torch.from_numpy(mu).cuda(), max_iter=30, early_stop=True)
+    idx = np.linspace(0, gamma - 1, 24).astype(int)
+    ref = oracle.sp_decode(rp, col, code.N, mu[idx], 30, early_stop=True, nthreads=16)
+    _cmp_sp(post[idx], hard[idx], iters[idx], ok[idx], ref, "n=18360")
+    Hs = sp.csr_matrix(H.astype(np.int64))
+    hh = hard.cpu().numpy().astype(np.int64)
+    syn = (Hs @ hh.T) % 2
+    okg = ok.cpu().numpy()
+    assert np.array_equal(okg == 1, ~syn.any(axis=0))
+    it = iters.cpu().numpy()
+    assert it.min() >= 1 and it.max() <= 30
+
+
+def test_invalid_arguments(pkg):
+    with pytest.raises(pkg.LdpcError) as e:
+        pkg.ldpc_code_create(np.array([[0, 70]]), 64)
+    assert e.value.status == 1
+    with pytest.raises(pkg.LdpcError):
+        pkg.ldpc_code_create(np.zeros((9, 4)), 4)
+    code = pkg.QCCode(synth.qc_shifts(3, 6, 8, seed=1), 8)
+    x = torch.zeros((4, code.N), device="cuda")
+    with pytest.raises(pkg.LdpcError) as e:
+        pkg.ldpc_decode(code.handle, x, pkg.default_opts(max_iter=0))
+    assert e.value.status == 1
+    with pytest.raises(pkg.LdpcError) as e:
+        pkg.ldpc_decode(code.handle, x, pkg.default_opts(algo=pkg.ALGO_MS, msg=pkg.MSG_F32))
+    assert e.value.status == 5
