@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 LDPC decoder.
+
+Workload (one step = one batch through the whole block-code path):
+  QC-LDPC 4 x 24, p = 765 (n = 18360, K = N - M = 15300 design information bits),
+  seeded shifts, 4096 frames per batch, all-zero codeword over BPSK/AWGN at
+  Eb/N0 = 3.5 dB generated on the device (Philox + Box-Muller), sum-product with
+  FP32 messages, at most 30 iterations with syndrome early stop, device-side
+  error counting; one ldpc_ber_sim call per step.
+
+Metric: decoded information Mbit/s = frames * 15300 / seconds (whole job over
+all ranks).  Ranks decode disjoint frame ranges (weak scaling, no collective on
+the data path; the only collectives are the timing barrier and max).
+
+--impl reference runs the CPU oracle (FP64, OpenMP over frames) on the host
+cores on a bounded sample of the same workload and prints the same JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+J, L, P_CIRC, SHIFT_SEED = 4, 24, 765, 2
+N_BITS = L * P_CIRC
+K_INFO = N_BITS - J * P_CIRC  # 15300
+E_EDGES = J * L * P_CIRC
+METRIC = "decoded info Mbit/s (n=18360, 30 iters) at BER matching FP64 oracle"
+
+
+def args_parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ebn0", type=float, default=3.5)
+    ap.add_argument("--gamma", type=int, default=4096)
+    ap.add_argument("--iters", type=int, default=30)
+    ap.add_argument("--msg", default="f32", choices=["f32", "f16", "i8"])
+    ap.add_argument("--no-early-stop", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU seconds of the oracle baseline")
+    ap.add_argument("--seed", type=int, default=20120403)
+    return ap.parse_args()
+
+
+def workload_name(a) -> str:
+    es = "early-stop" if not a.no_early_stop else "fixed"
+    return f"QC-LDPC 4x24 p=765 n=18360, {a.gamma} frames/batch, {a.iters} iters {es}, Eb/N0 {a.ebn0} dB, {a.msg} msgs"
+
+
+def load_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                    power.append(float(f[3]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s, p in zip(sm, power) if p >= 0.5 * max(power)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_sample(a, nframes: int, threads: int, first_frame: int):
+    """Channel + FP64 decode + error count of nframes on the host cores; returns (seconds, iters, errors)."""
+    import numpy as np
+    import oracle
+    import synth
+
+    shifts = synth.qc_shifts(J, L, P_CIRC, seed=SHIFT_SEED)
+    if not hasattr(oracle_sample, "graph"):
+        H = oracle.qc_parity_check(shifts, P_CIRC)
+        oracle_sample.graph = oracle.csr_rows(H)
+    rp, col = oracle_sample.graph
+    sigma = oracle.sigma_from_ebn0(a.ebn0, K_INFO / N_BITS)
+    t0 = time.perf_counter()
+    mu = oracle.channel_awgn(a.seed, first_frame, nframes, N_BITS, sigma)
+    _, hard, iters, ok = oracle.sp_decode(rp, col, N_BITS, mu, a.iters, early_stop=not a.no_early_stop,
+                                          nthreads=threads)
+    errs = int(hard.sum())
+    dt = time.perf_counter() - t0
+    return dt, int(np.asarray(iters).sum()), errs
+
+
+def cpu_baseline(a) -> dict:
+    threads = os.cpu_count() or 1
+    n = max(threads, 16)
+    dt, it, _ = oracle_sample(a, n, threads, first_frame=1 << 50)
+    while dt < a.cpu_seconds * 0.5 and n < 4096:
+        n = int(min(4096, max(2 * n, n * a.cpu_seconds / max(dt, 1e-3))))
+        n = max(threads, (n // threads) * threads)
+        dt, it, _ = oracle_sample(a, n, threads, first_frame=1 << 50)
+    return {"value": n * K_INFO / dt / 1e6, "unit": "Mbit/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n} frames of the same workload (channel + FP64 sum-product, {it / n:.2f} mean iters) "
+                      f"on {threads} host threads, {dt:.1f} s"}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    # size each step to a few seconds of host work
+    t, _, _ = oracle_sample(a, threads, threads, first_frame=1 << 52)
+    per = max(threads, int(round(4.0 / max(t, 1e-3))) * threads)
+    per = min(per, 2048)
+    for w in range(a.warmup):
+        oracle_sample(a, threads, threads, first_frame=(1 << 52) + (w + 1) * 4096)
+    total_t, frames, iters = 0.0, 0, 0
+    for s in range(a.steps):
+        dt, it, _ = oracle_sample(a, per, threads, first_frame=(1 << 53) + s * per)
+        total_t += dt
+        frames += per
+        iters += it
+    value = frames * K_INFO / total_t / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mbit/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_t / a.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "frames_per_step": per, "mean_iters": iters / frames},
+            "cpu_baseline": {"value": value, "unit": "Mbit/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{per} frames per step, {a.steps} steps"},
+            "e2e": {"value": value, "unit": "Mbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU
+def run_ours(a):
+    import torch
+
+    import synth
+    import paper_1204_0334_gb300 as pkg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    shifts = synth.qc_shifts(J, L, P_CIRC, seed=SHIFT_SEED)
+    code = pkg.QCCode(shifts, P_CIRC)
+    msg = {"f32": pkg.MSG_F32, "f16": pkg.MSG_F16, "i8": pkg.MSG_I8}[a.msg]
+    algo = pkg.ALGO_MS if a.msg == "i8" else pkg.ALGO_SP
+    opts = pkg.default_opts(max_iter=a.iters, early_stop=0 if a.no_early_stop else 1, algo=algo, msg=msg)
+    s_msg = {"f32": 4, "f16": 2, "i8": 1}[a.msg]
+    s_mu = 1 if a.msg == "i8" else 4
+    base = (rank << 40) + (1 << 36)
+
+    def step(i, o=opts, gamma=a.gamma):
+        return pkg.ldpc_ber_sim(code.handle, a.ebn0, a.seed, base + i * gamma, gamma, 1 << 60, gamma, o, stream)
+
+    for w in range(a.warmup):
+        step(-1 - w)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = str(local)
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    time.sleep(0.3)
+    pkg.ldpc_profile_enable(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    res = [step(i) for i in range(a.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    prof = pkg.ldpc_profile_read()
+    pkg.ldpc_profile_enable(False)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    frames = sum(r["frames"] for r in res)
+    iters_sum = sum(r["iters_sum"] for r in res)
+    fe = sum(r["frame_errors"] for r in res)
+    be = sum(r["bit_errors"] for r in res)
+    if dist:
+        t = torch.tensor([frames, iters_sum, fe, be], dtype=torch.float64, device=dev)
+        dist.all_reduce(t)
+        frames, iters_sum, fe, be = [int(x) for x in t.tolist()]
+    value = frames * K_INFO / (ms / 1e3) / 1e6
+
+    # roofline of the check-node kernel: algorithmic bytes = read + write of every edge message of every
+    # frame-iteration the algorithm runs (the iterations each frame needed)
+    local_iters = sum(r["iters_sum"] for r in res)
+    cn_bytes = 2.0 * E_EDGES * s_msg * local_iters
+    cn_s = prof["cn_ms"] / 1e3
+    peaks = load_peaks()
+    peak = peaks.get("hbm_gbs", 6800.0)
+    roof = {"bound": "hbm", "kernel": "cn_sp_kernel" if algo == pkg.ALGO_SP else "cn_ms_kernel",
+            "achieved": cn_bytes / cn_s / 1e9 if cn_s > 0 else None, "peak": peak, "unit": "GB/s",
+            "frac": (cn_bytes / cn_s / 1e9) / peak if cn_s > 0 else None, "traffic": None,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback",
+            "cn_launches": prof["cn_launches"], "cn_ms_avg": prof["cn_ms"] / max(1, prof["cn_launches"]),
+            "vn_ms_avg": prof["vn_ms"] / max(1, prof["vn_launches"]),
+            "path_bytes_per_frame_iter": 4 * E_EDGES * s_msg + N_BITS * s_mu + N_BITS // 8,
+            "path_achieved_gbs": (4 * E_EDGES * s_msg + N_BITS * s_mu + N_BITS / 8) * local_iters / (ms / 1e3) / 1e9}
+    line = {"metric": METRIC, "value": value, "unit": "Mbit/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "i8" if a.msg == "i8" else "f32", "data": "synthetic",
+            "config": {"workload": workload_name(a), "gamma": a.gamma, "iters_cap": a.iters,
+                       "early_stop": not a.no_early_stop, "ebn0_db": a.ebn0, "msg": a.msg,
+                       "l2": "inputs larger than L2 (message store %.2f GB per batch)" % (
+                           E_EDGES * s_msg * a.gamma / 1e9)},
+            "frames": frames, "mean_iters": iters_sum / frames, "fer": fe / frames, "ber": be / (frames * N_BITS),
+            "frames_per_s": frames / (ms / 1e3), "roofline": roof, "clocks": clk,
+            "gpu_launches": prof["launches"]}
+
+    if not a.no_variants:
+        line["variants"] = variants(a, pkg, code, stream, opts)
+    line["e2e"] = e2e(a, pkg, code, stream, opts)
+    if rank == 0 and world == 1:
+        line["cpu_baseline"] = cpu_baseline(a)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    code.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def variants(a, pkg, code, stream, opts) -> dict:
+    """Secondary figures on the same batch (not the headline): other message types, no early stop."""
+    import torch
+
+    out = {}
+    cases = [("f32_fixed30", dict(early_stop=0, algo=pkg.ALGO_SP, msg=pkg.MSG_F32)),
+             ("f16_early_stop", dict(early_stop=1, algo=pkg.ALGO_SP, msg=pkg.MSG_F16)),
+             ("i8_minsum_early_stop", dict(early_stop=1, algo=pkg.ALGO_MS, msg=pkg.MSG_I8)),
+             ("i8_minsum_fixed30", dict(early_stop=0, algo=pkg.ALGO_MS, msg=pkg.MSG_I8))]
+    for name, kw in cases:
+        o = pkg.default_opts(max_iter=a.iters, **kw)
+        base = (7 << 44)
+        pkg.ldpc_ber_sim(code.handle, a.ebn0, a.seed, base, a.gamma, 1 << 60, a.gamma, o, stream)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k = 3
+        ev0.record(stream)
+        rs = [pkg.ldpc_ber_sim(code.handle, a.ebn0, a.seed, base + (i + 1) * a.gamma, a.gamma, 1 << 60, a.gamma, o,
+                               stream) for i in range(k)]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        fr = sum(r["frames"] for r in rs)
+        out[name] = {"value": fr * K_INFO / (ms / 1e3) / 1e6, "unit": "Mbit/s", "ms_per_step": ms / k,
+                     "mean_iters": sum(r["iters_sum"] for r in rs) / fr,
+                     "fer": sum(r["frame_errors"] for r in rs) / fr}
+    return out
+
+
+def e2e(a, pkg, code, stream, opts) -> dict:
+    """Same metric through ldpc_decode with pinned HOST buffers: LLRs copied in, hard decisions copied out."""
+    import torch
+
+    gamma = a.gamma
+    llr_dev = torch.empty((gamma, code.N), dtype=torch.float32, device="cuda")
+    pkg.ldpc_channel(code.handle, a.ebn0, a.seed, 3 << 44, llr_dev, stream)
+    llr = llr_dev.cpu().pin_memory()
+    del llr_dev
+    hard = torch.empty((gamma, code.N), dtype=torch.uint8).pin_memory()
+    iters = torch.empty(gamma, dtype=torch.int32).pin_memory()
+    ok = torch.empty(gamma, dtype=torch.int32).pin_memory()
+    o = opts
+    pkg.ldpc_decode(code.handle, llr, o, None, hard, iters, ok, stream)
+    torch.cuda.synchronize()
+    k = 3
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(k):
+        pkg.ldpc_decode(code.handle, llr, o, None, hard, iters, ok, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    return {"value": gamma * k * K_INFO / (ms / 1e3) / 1e6, "unit": "Mbit/s",
+            "h2d_bytes_per_step": gamma * code.N * 4, "d2h_bytes_per_step": gamma * code.N + 2 * gamma * 4,
+            "ms_per_step": ms / k, "call": "ldpc_decode(host llr [gamma][N] f32 -> host hard [gamma][N] u8)"}
+
+
+def main():
+    a = args_parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

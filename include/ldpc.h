@@ -143,6 +143,26 @@ ldpc_status ldpc_ber_sim(ldpc_code code, double ebn0_db, uint64_t seed, uint64_t
                          int64_t target_frame_errors, int32_t gamma, const ldpc_decode_opts *opts,
                          ldpc_ber_result *out, void *stream);
 
+/*
+ * Measurement aid (the paper has no counterpart; its timings are wall-clock
+ * totals, Sec. V).  While enabled, each check-node and variable-node kernel
+ * launch of the block-code decoder is bracketed by CUDA events on its own
+ * stream.  ldpc_profile_read synchronizes those events and returns the summed
+ * device time per kind.  `launches` counts every kernel this library has
+ * launched since the last ldpc_profile_enable call, enabled or not.
+ * Not thread-safe; enable/read from the thread that issues the decodes.
+ */
+typedef struct {
+    int64_t launches;     /* all kernels launched by the library */
+    int64_t cn_launches;  /* timed check-node launches */
+    double cn_ms;         /* their summed device time */
+    int64_t vn_launches;  /* timed variable-node launches */
+    double vn_ms;
+} ldpc_profile;
+
+ldpc_status ldpc_profile_enable(int32_t on);  /* resets all counters */
+ldpc_status ldpc_profile_read(ldpc_profile *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -60,6 +60,8 @@ _SIGNATURES = [
     ("ldpc_channel", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, P, P]),
     ("ldpc_ber_sim", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
                                     ctypes.c_int64, ctypes.c_int32, P, P, P]),
+    ("ldpc_profile_enable", ctypes.c_int, [ctypes.c_int32]),
+    ("ldpc_profile_read", ctypes.c_int, [P]),
 ]
 
 
@@ -154,6 +156,21 @@ def ldpc_ber_sim(code: int, ebn0_db: float, seed: int, first_frame: int, max_fra
     _check(lib().ldpc_ber_sim(code, ebn0_db, seed, first_frame, max_frames, target_frame_errors, gamma,
                               ctypes.byref(opts), ctypes.byref(r), _stream(stream)), "ldpc_ber_sim")
     return r.as_dict()
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("cn_launches", ctypes.c_int64), ("cn_ms", ctypes.c_double),
+                ("vn_launches", ctypes.c_int64), ("vn_ms", ctypes.c_double)]
+
+
+def ldpc_profile_enable(on: bool = True):
+    _check(lib().ldpc_profile_enable(int(on)), "ldpc_profile_enable")
+
+
+def ldpc_profile_read() -> dict:
+    r = Profile()
+    _check(lib().ldpc_profile_read(ctypes.byref(r)), "ldpc_profile_read")
+    return {k: getattr(r, k) for k, _ in Profile._fields_}
 
 
 # ----------------------------------------------------------------- convenience

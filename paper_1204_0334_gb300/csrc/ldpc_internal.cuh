@@ -89,3 +89,12 @@ ldpc_status qc_count_errors(ldpc_code c, int gamma, const ldpc_decode_opts &o, c
 inline int lanes_per_word(int msg) { return msg == LDPC_MSG_F32 ? 1 : (msg == LDPC_MSG_F16 ? 2 : 4); }
 
 }  // namespace ldpc
+
+namespace ldpc {
+// launch accounting and optional per-launch event timing (profile.cu)
+void count_launch(int n = 1);
+bool profiling();
+// kind 0 = check node, 1 = variable node; returns a slot for prof_end (or -1)
+int prof_begin(int kind, cudaStream_t s);
+void prof_end(int slot, cudaStream_t s);
+}  // namespace ldpc

@@ -775,6 +775,7 @@ ldpc_status qc_pack_llr(ldpc_code c, const float *llr, int gamma, const ldpc_dec
     const int V = words_per_lane(o), W = 32 * V;
     const int P = (gamma + W - 1) / W;
     dim3 blk(32, 8), grd((c->d.N + 31) / 32, (P * W + 31) / 32);
+    count_launch();
     if (o.algo == LDPC_ALGO_MS) {
         pack_llr_kernel<int8_t><<<grd, blk, 0, s>>>(llr, (int8_t *)c->ws.mu, gamma, c->d.N, W, P * W, 0.0f,
                                                     ldexpf(1.0f, o.frac_bits), 1e30f);
@@ -855,18 +856,24 @@ ldpc_status qc_decode_device(ldpc_code c, int gamma, const ldpc_decode_opts &o, 
     const int V = words_per_lane(o), W = 32 * V;
     const int P = (gamma + W - 1) / W;
     init_flags_kernel<<<(P + 127) / 128, 128, 0, s>>>(c->ws.flags, P, V, gamma);
+    count_launch(3);  // init, final syndrome, finish
     LDPC_CUDA_TRY(cudaMemsetAsync(c->ws.hw, 0, (size_t)P * c->d.N * V * 4, s));
     const int dcm = c->d.dc_max;
     for (int it = 1; it <= o.max_iter; ++it) {
         const bool first = it == 1;
         const bool syn = o.early_stop && it >= 2;
         const int par = it & 1;
+        const int slot_cn = prof_begin(0, s);
         if (dcm <= 8) cn_dispatch<8>(c, P, o, first, syn, par, s);
         else if (dcm <= 16) cn_dispatch<16>(c, P, o, first, syn, par, s);
         else if (dcm <= 24) cn_dispatch<24>(c, P, o, first, syn, par, s);
         else cn_dispatch<32>(c, P, o, first, syn, par, s);
+        prof_end(slot_cn, s);
+        const int slot_vn = prof_begin(1, s);
         if (c->d.J <= 4) vn_dispatch<4>(c, P, o, syn, want_post, it, par, s);
         else vn_dispatch<8>(c, P, o, syn, want_post, it, par, s);
+        prof_end(slot_vn, s);
+        count_launch(2);
     }
     {
         dim3 grd((c->d.M + 127) / 128, P);
@@ -889,10 +896,12 @@ ldpc_status qc_unpack_outputs(ldpc_code c, int gamma, const ldpc_decode_opts &o,
                                       s));
     if (post) {
         dim3 blk(32, 8), grd((c->d.N + 31) / 32, (gamma + 31) / 32);
+        count_launch();
         unpack_post_kernel<<<grd, blk, 0, s>>>(c->ws.post, post, gamma, c->d.N, W);
     }
     if (hard) {
         dim3 grd((c->d.N + 255) / 256, gamma < 65535 ? gamma : 65535);
+        count_launch();
         unpack_hard_kernel<<<grd, 256, 0, s>>>(c->ws.hw, hard, gamma, c->d.N, V);
     }
     LDPC_CUDA_TRY(cudaGetLastError());
@@ -907,6 +916,7 @@ ldpc_status qc_channel_packed(ldpc_code c, double sigma, uint64_t seed, uint64_t
     const int ty = 256 / W > 0 ? 256 / W : 1;
     dim3 blk(W, ty), grd((Q + ty - 1) / ty, P);
     const float fs = (float)sigma, s2 = (float)(2.0 / (sigma * sigma));
+    count_launch();
     if (o.algo == LDPC_ALGO_MS)
         channel_packed_kernel<int8_t><<<grd, blk, 0, s>>>((int8_t *)c->ws.mu, c->d.N, W, gamma, P * W, seed,
                                                           first_frame, fs, s2, 1e30f, ldexpf(1.0f, o.frac_bits));
@@ -921,6 +931,7 @@ ldpc_status qc_channel_frames(ldpc_code c, double sigma, uint64_t seed, uint64_t
                               cudaStream_t s) {
     const int Q = (c->d.N + 3) / 4;
     dim3 grd((Q + 127) / 128, gamma < 65535 ? gamma : 65535);
+    count_launch();
     channel_frames_kernel<<<grd, 128, 0, s>>>(out, c->d.N, gamma, seed, first_frame, (float)sigma,
                                               (float)(2.0 / (sigma * sigma)));
     LDPC_CUDA_TRY(cudaGetLastError());
@@ -930,6 +941,7 @@ ldpc_status qc_channel_frames(ldpc_code c, double sigma, uint64_t seed, uint64_t
 ldpc_status qc_count_errors(ldpc_code c, int gamma, const ldpc_decode_opts &o, cudaStream_t s) {
     const int V = words_per_lane(o), W = 32 * V;
     const int P = (gamma + W - 1) / W;
+    count_launch();
     count_errors_kernel<<<P, 256, 0, s>>>(c->ws.hw, c->ws.iters + c->ws.gamma_cap, c->ws.iters, c->ws.counters, c->d.N, V, gamma);
     LDPC_CUDA_TRY(cudaGetLastError());
     return LDPC_OK;
