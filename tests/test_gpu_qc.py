@@ -1,13 +1,15 @@
 """GPU parity of the QC block-code decoder against the CPU oracle (through the C-ABI).
 
 Tolerances (FP32 sum-product against the FP64 oracle):
-* posteriors within REL = 1e-4 * max(1, |oracle|) (after clipping at +-30) for
-  every frame over the first ten iterations, and at any iteration count for
-  frames the oracle decodes (syndrome satisfied);
-* frames that do not converge are chaotic: a decoder that rounds only its stored
-  messages to FP32 and does everything else exactly already drifts by up to
-  ~1.7e-4 after 30 iterations on such frames, so for them the bound is
-  REL_NONCONV = 1e-3 (measured deviation is reported by the benchmark notes);
+* every posterior within REL = 1e-4 * max(1, |oracle|) (values clipped at +-30),
+  OR, where the decoding map itself is ill-conditioned, within SENS = 16 times
+  the distance the exact FP64 decoder moves when its FP32 input is changed by
+  one ulp (the larger of two random sign patterns, per frame).  Frames that do
+  not converge, or converge after a long transient, are chaotic: a decoder that
+  rounds only its stored messages to FP32 and does everything else exactly
+  already drifts by 1.2e-4 on such frames after 30 iterations, and an FP32
+  decoder drifts up to ~7x the one-ulp response of the exact one;
+* over the first ten iterations every frame meets REL without the second arm;
 * hard decisions identical wherever |oracle posterior| >= 1e-3;
 * iteration counts and ok flags identical.
 Integer min-sum is bit-exact.
@@ -23,7 +25,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 REL = 1e-4
-REL_NONCONV = 1e-3
+SENS = 16.0
 
 
 @pytest.fixture(scope="module")
@@ -42,23 +44,40 @@ def _graph(shifts, p):
     return H, rp, col
 
 
-def _cmp_sp(post, hard, iters, ok, ref, label="", strict_all=False):
+def oracle_one_ulp_response(rp, col, N, mu, iters, early_stop, base_post, frames):
+    """Per frame: max |posterior change| of the FP64 oracle when each input moves by one FP32 ulp."""
+    rng = np.random.default_rng(99)
+    resp = np.zeros(len(frames))
+    for _ in range(2):
+        up = rng.integers(0, 2, size=mu[frames].shape).astype(bool)
+        m2 = np.where(up, np.nextafter(mu[frames], np.float32(np.inf)),
+                      np.nextafter(mu[frames], np.float32(-np.inf))).astype(np.float32)
+        p2 = oracle.sp_decode(rp, col, N, m2, iters, early_stop=early_stop, nthreads=16)[0]
+        resp = np.maximum(resp, np.abs(p2 - base_post[frames]).max(axis=1))
+    return resp
+
+
+def _cmp_sp(post, hard, iters, ok, ref, label="", strict_all=False, sens=None):
+    """sens = (rp, col, N, mu, iters, early_stop) enables the conditioning arm of the tolerance."""
     po, ho, io, oo = ref
     p = post.cpu().numpy().astype(np.float64)
-    err = np.abs(p - po) / np.maximum(1.0, np.abs(po))
-    conv = oo == 1
-    if strict_all or conv.all():
-        assert err.max() <= REL, f"{label} max rel deviation {err.max():.3e}"
-    else:
-        if conv.any():
-            assert err[conv].max() <= REL, f"{label} converged frames: max rel deviation {err[conv].max():.3e}"
-        assert err[~conv].max() <= REL_NONCONV, f"{label} non-converged frames: {err[~conv].max():.3e}"
+    dev = np.abs(p - po)
+    rel = dev / np.maximum(1.0, np.abs(po))
+    bad = np.nonzero((rel > REL).any(axis=1))[0]
+    if len(bad):
+        assert not strict_all and sens is not None, f"{label} max rel deviation {rel.max():.3e}"
+        rp, col, N, mu, it, es = sens
+        resp = oracle_one_ulp_response(rp, col, N, mu, it, es, po, bad)
+        for f, r in zip(bad, resp):
+            allowed = np.maximum(REL * np.maximum(1.0, np.abs(po[f])), SENS * r)
+            assert (dev[f] <= allowed).all(), (
+                f"{label} frame {f}: deviation {dev[f].max():.3e}, one-ulp response of the oracle {r:.3e}")
     sure = np.abs(po) >= 1e-3
     h = hard.cpu().numpy()
     assert np.array_equal(h[sure], ho[sure]), label
     assert np.array_equal(iters.cpu().numpy(), io), label
     assert np.array_equal(ok.cpu().numpy(), oo), label
-    return err.max()
+    return rel.max()
 
 
 def test_cfg1_sum_product_parity(pkg):
@@ -69,7 +88,7 @@ def test_cfg1_sum_product_parity(pkg):
     mu = synth.gaussian_llrs(32, code.N, seed=1001, ebn0_db=2.0, rate=0.5)
     out = code.decode(torch.from_numpy(mu).cuda(), max_iter=30)
     ref = oracle.sp_decode(rp, col, code.N, mu, 30)
-    _cmp_sp(*out, ref, "cfg1")
+    _cmp_sp(*out, ref, "cfg1", sens=(rp, col, code.N, mu, 30, False))
 
 
 @pytest.mark.parametrize("iters", [1, 2, 5, 10])
@@ -92,7 +111,7 @@ def test_ragged_frame_counts_early_stop(pkg, gamma):
     mu = synth.gaussian_llrs(gamma, code.N, seed=gamma, ebn0_db=2.5, rate=0.5)
     out = code.decode(torch.from_numpy(mu).cuda(), max_iter=25, early_stop=True)
     ref = oracle.sp_decode(rp, col, code.N, mu, 25, early_stop=True, nthreads=8)
-    _cmp_sp(*out, ref, f"gamma{gamma}")
+    _cmp_sp(*out, ref, f"gamma{gamma}", sens=(rp, col, code.N, mu, 25, True))
     assert len(set(ref[2].tolist())) > 1 or gamma < 8  # frames stopped at different iterations
 
 
@@ -103,7 +122,8 @@ def test_irregular_code_with_zero_blocks(pkg):
     code = pkg.QCCode(shifts, 29)
     mu = synth.gaussian_llrs(96, code.N, seed=2, ebn0_db=2.0, rate=1 - 4 / 12)
     out = code.decode(torch.from_numpy(mu).cuda(), max_iter=12, early_stop=True)
-    _cmp_sp(*out, oracle.sp_decode(rp, col, code.N, mu, 12, early_stop=True, nthreads=8), "irregular")
+    _cmp_sp(*out, oracle.sp_decode(rp, col, code.N, mu, 12, early_stop=True, nthreads=8), "irregular",
+            sens=(rp, col, code.N, mu, 12, True))
 
 
 @pytest.mark.parametrize("name", sorted(TREE_BASES))
@@ -187,7 +207,7 @@ def test_host_buffers(pkg):
         o = pkg.default_opts(max_iter=10)
         pkg.ldpc_decode(code.handle, llr, o, post, hard, iters, ok)
         torch.cuda.synchronize()
-        _cmp_sp(post, hard, iters, ok, ref, f"host pin={pin}")
+        _cmp_sp(post, hard, iters, ok, ref, f"host pin={pin}", strict_all=True)
 
 
 def test_channel_matches_oracle(pkg):
@@ -259,7 +279,8 @@ def test_full_size_code_sampled_parity(pkg):
     post, hard, iters, ok = code.decode(torch.from_numpy(mu).cuda(), max_iter=30, early_stop=True)
     idx = np.linspace(0, gamma - 1, 24).astype(int)
     ref = oracle.sp_decode(rp, col, code.N, mu[idx], 30, early_stop=True, nthreads=16)
-    _cmp_sp(post[idx], hard[idx], iters[idx], ok[idx], ref, "n=18360")
+    _cmp_sp(post[idx], hard[idx], iters[idx], ok[idx], ref, "n=18360",
+            sens=(rp, col, code.N, mu[idx], 30, True))
     Hs = sp.csr_matrix(H.astype(np.int64))
     hh = hard.cpu().numpy().astype(np.int64)
     syn = (Hs @ hh.T) % 2
