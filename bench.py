@@ -49,6 +49,8 @@ def args_parse():
     ap.add_argument("--msg", default="f32", choices=["f32", "f16", "i8"])
     ap.add_argument("--no-early-stop", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU seconds of the oracle baseline")
     ap.add_argument("--seed", type=int, default=20120403)
     return ap.parse_args()
@@ -287,8 +289,9 @@ def run_ours(a):
 
     if not a.no_variants:
         line["variants"] = variants(a, pkg, code, stream, opts)
-    line["e2e"] = e2e(a, pkg, code, stream, opts)
-    if rank == 0 and world == 1:
+    if not a.no_e2e:
+        line["e2e"] = e2e(a, pkg, code, stream, opts)
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a)
     if rank == 0:
         print(json.dumps(line), flush=True)
