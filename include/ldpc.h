@@ -144,6 +144,16 @@ ldpc_status ldpc_ber_sim(ldpc_code code, double ebn0_db, uint64_t seed, uint64_t
                          ldpc_ber_result *out, void *stream);
 
 /*
+ * ldpc_phi_eval -- the check-node transform of the sum-product rule on its own:
+ * phi(x) = -ln tanh(x/2) for x >= 0, with which eq. (bphs) reads
+ * alpha = prod(sign) * phi(sum_{n' != n} phi(|beta_n'|)) (phi is its own inverse).
+ * Exposed so that its accuracy can be checked against the definition.
+ *   x, y: device float [n]; variant 0 = the decoder's SFU-based evaluation,
+ *   variant 1 = CUDA's expm1f/log1pf form.  Errors: LDPC_EINVAL.
+ */
+ldpc_status ldpc_phi_eval(const float *x, float *y, int64_t n, int32_t variant, void *stream);
+
+/*
  * Measurement aid (the paper has no counterpart; its timings are wall-clock
  * totals, Sec. V).  While enabled, each check-node and variable-node kernel
  * launch of the block-code decoder is bracketed by CUDA events on its own

@@ -60,6 +60,7 @@ _SIGNATURES = [
     ("ldpc_channel", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, P, P]),
     ("ldpc_ber_sim", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
                                     ctypes.c_int64, ctypes.c_int32, P, P, P]),
+    ("ldpc_phi_eval", ctypes.c_int, [P, P, ctypes.c_int64, ctypes.c_int32, P]),
     ("ldpc_profile_enable", ctypes.c_int, [ctypes.c_int32]),
     ("ldpc_profile_read", ctypes.c_int, [P]),
 ]
@@ -156,6 +157,15 @@ def ldpc_ber_sim(code: int, ebn0_db: float, seed: int, first_frame: int, max_fra
     _check(lib().ldpc_ber_sim(code, ebn0_db, seed, first_frame, max_frames, target_frame_errors, gamma,
                               ctypes.byref(opts), ctypes.byref(r), _stream(stream)), "ldpc_ber_sim")
     return r.as_dict()
+
+
+def ldpc_phi_eval(x, variant: int = 0, stream=None):
+    """phi(x) = -ln tanh(x/2) evaluated on the device by the decoder's kernel code."""
+    import torch
+
+    y = torch.empty_like(x)
+    _check(lib().ldpc_phi_eval(_ptr(x), _ptr(y), x.numel(), variant, _stream(stream)), "ldpc_phi_eval")
+    return y
 
 
 class Profile(ctypes.Structure):

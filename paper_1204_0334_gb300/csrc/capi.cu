@@ -311,4 +311,17 @@ ldpc_status ldpc_ber_sim(ldpc_code c, double ebn0_db, uint64_t seed, uint64_t fi
     return LDPC_OK;
 }
 
+ldpc_status ldpc_phi_eval(const float *x, float *y, int64_t n, int32_t variant, void *stream) {
+    if (!x || !y || n < 0 || n > (int64_t)1 << 30 || (variant != 0 && variant != 1)) {
+        set_error("need device x, y, 0 <= n <= 2^30 and variant 0 or 1");
+        return LDPC_EINVAL;
+    }
+    if (pointer_kind(x) != 0 || pointer_kind(y) != 0) {
+        set_error("ldpc_phi_eval takes device buffers");
+        return LDPC_EINVAL;
+    }
+    if (n == 0) return LDPC_OK;
+    return phi_eval(x, y, (int)n, variant, (cudaStream_t)stream);
+}
+
 }  // extern "C"

@@ -86,6 +86,8 @@ ldpc_status qc_channel_frames(ldpc_code c, double sigma, uint64_t seed, uint64_t
                               float *out, cudaStream_t s);
 ldpc_status qc_count_errors(ldpc_code c, int gamma, const ldpc_decode_opts &o, cudaStream_t s);
 
+ldpc_status phi_eval(const float *x, float *y, int n, int variant, cudaStream_t s);
+
 inline int lanes_per_word(int msg) { return msg == LDPC_MSG_F32 ? 1 : (msg == LDPC_MSG_F16 ? 2 : 4); }
 
 }  // namespace ldpc

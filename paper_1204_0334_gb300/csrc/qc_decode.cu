@@ -24,16 +24,60 @@ namespace ldpc {
 constexpr int kWarps = 8;  // warps per block in the node kernels: 8 consecutive rows / variables
 
 // ---------------------------------------------------------------------------
-// phi(x) = -ln tanh(x/2) = ln((e^x + 1)/(e^x - 1)) = log1p(2 / expm1(x)), x >= 0.
-// phi(0) = +inf, phi(+inf) = 0, and phi is its own inverse, so eq. (bphs)
-// becomes alpha = sign * phi(sum of phi(|beta|) over the other edges).
-// Written with CUDA's expm1f / log1pf (about 1 ulp each) and a correctly
-// rounded reciprocal: errors of a few ulp here grow by two orders of magnitude
-// over 30 iterations on frames that do not converge.
+// phi(x) = -ln tanh(x/2) = ln((1 + e^-x)/(1 - e^-x)), x >= 0; phi(0) = +inf,
+// phi(+inf) = 0, and phi is its own inverse, so eq. (bphs) becomes
+// alpha = sign * phi(sum of phi(|beta|) over the other edges).
+//
+// Errors of a few ulp here grow by two orders of magnitude over 30 iterations
+// on frames that do not converge, and phi is evaluated twice per edge, so it
+// has to be both accurate and cheap.  Two regimes, both evaluated and selected
+// (no divergence):
+//  x >= 3/2:  phi = 2 atanh(t), t = e^-x <= 0.223, written 2 t S(t^2) with
+//             S(v) = atanh(sqrt v)/sqrt v; t from the SFU exp2 with the
+//             rounding error of x*log2(e) carried to first order.
+//  x <  3/2:  phi = -ln(x/2) + G(x^2/4), G(u) = -ln(tanh(sqrt u)/sqrt u); the
+//             log from the SFU log2, G a polynomial.
+// S and G are degree-3 / degree-5 polynomials fitted here (weighted least
+// squares converging to the minimax fit) to 7e-9 relative / 7e-9 absolute on
+// their intervals; the remaining error is that of the SFU approximations.
+// phi_ref keeps CUDA's expm1f/log1pf form (about 2-3 ulp, several times
+// slower) for verification through ldpc_phi_eval.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float phi_f(float x) {
+__device__ __forceinline__ float phi_ref(float x) {
     const float e = expm1f(x);
     return log1pf(2.0f * __frcp_rn(e));
+}
+
+__device__ __forceinline__ float ex2_approx(float a) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ float lg2_approx(float a) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+
+__device__ __forceinline__ float phi_f(float x) {
+    x = fminf(x, 100.0f);  // e^-100 flushes to 0; keeps inf - inf out of the error term
+    // x >= 1.5
+    const float L2E = 1.44269502f, L2E_LO = 1.92596299e-8f, LN2 = 0.693147182f;
+    const float a = -x * L2E;
+    float alo = fmaf(-x, L2E, -a);
+    alo = fmaf(-x, L2E_LO, alo);
+    const float t0 = ex2_approx(a);
+    const float t = fmaf(t0, alo * LN2, t0);
+    const float v = t * t;
+    const float w = 2.0f * t;
+    const float phiA = fmaf(w, v * fmaf(fmaf(0.15412693f, v, 0.19966834f), v, 0.33333607f), w);
+    // x < 1.5
+    const float y = 0.5f * x;
+    const float u = y * y;
+    const float G = u * fmaf(fmaf(fmaf(fmaf(0.00130455f, u, -0.00623973f), u, 0.02174386f), u, -0.07776314f), u,
+                             0.33333278f);
+    const float phiB = fmaf(lg2_approx(y), -LN2, G);
+    return x < 1.5f ? phiB : phiA;
 }
 
 __device__ __forceinline__ float clipf(float x, float c) { return fminf(fmaxf(x, -c), c); }
@@ -101,6 +145,10 @@ cn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict
     const int r = m - j * d.p;
     const int *sh = d.shift + j * d.L;
     const int *eo = d.eoff + j * d.L;
+    // package-relative bases; offsets below stay in 32 bits (E * 32 < 2^31)
+    uint32_t *pmsg = msg + (size_t)pk * d.E * 32 + lane;
+    const float *pmu = mu + (size_t)pk * d.N * W + lane * V;
+    const uint32_t *phw = hw + (size_t)pk * d.N * V;
     float ph[DCMAX][V];
     uint32_t neg[V];
     uint32_t syn[V];
@@ -115,14 +163,14 @@ cn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict
         if (on) {
             int k = r + sh[l];
             if (k >= d.p) k -= d.p;
+            const int n = l * d.p + k;
             float x[V];
             if (lane_on) {
                 if (FIRST) {
-                    const float *src = mu + ((size_t)pk * d.N + (size_t)l * d.p + k) * W + lane * V;
 #pragma unroll
-                    for (int v = 0; v < V; ++v) x[v] = src[v];
+                    for (int v = 0; v < V; ++v) x[v] = pmu[n * W + v];
                 } else {
-                    Lane<V>::unpack(msg[((size_t)pk * d.E + eo[l] + k) * 32 + lane], x);
+                    Lane<V>::unpack(pmsg[(eo[l] + k) * 32], x);
                 }
             } else {
 #pragma unroll
@@ -134,9 +182,8 @@ cn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict
                 neg[v] |= (x[v] < 0.0f ? 1u : 0u) << l;
             }
             if (SYN) {
-                const uint32_t *h = hw + ((size_t)pk * d.N + (size_t)l * d.p + k) * V;
 #pragma unroll
-                for (int v = 0; v < V; ++v) syn[v] ^= h[v];
+                for (int v = 0; v < V; ++v) syn[v] ^= phw[n * V + v];
             }
         }
     }
@@ -147,7 +194,7 @@ cn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict
             if (bad) atomicOr(F.unsat(par) + v, bad);
         }
     }
-    // prefix sums (in place in pre[]) then the backward sweep
+    // prefix sums, then the backward sweep adds the suffix sums
     float pre[DCMAX][V];
     {
         float acc[V];
@@ -180,7 +227,7 @@ cn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict
                 const uint32_t s = par_all[v] ^ ((neg[v] >> l) & 1u);
                 a[v] = s ? -mag : mag;
             }
-            msg[((size_t)pk * d.E + eo[l] + k) * 32 + lane] = Lane<V>::pack(a);
+            pmsg[(eo[l] + k) * 32] = Lane<V>::pack(a);
         }
 #pragma unroll
         for (int v = 0; v < V; ++v) suf[v] += ph[l][v];
@@ -194,99 +241,125 @@ cn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict
 // that just ran) are frozen from now on: their outputs stay those of the
 // previous iteration, which is the early-stop rule.
 // ---------------------------------------------------------------------------
+constexpr int kVnPerWarp = 4;  // variables per warp in the variable-node kernels (more bytes in flight)
+
+// Frozen-frame bookkeeping shared by the variable-node kernels: frames whose
+// previous decisions satisfied every check stop here (STOP); the first warp of
+// the package records it.  Returns the frozen mask per frame slot.
+template <int V, bool STOP>
+__device__ __forceinline__ void vn_frozen(PkgFlags F, bool first_warp, int lane, int it, int par,
+                                          int32_t *__restrict__ iters, int pk, uint32_t *frozen) {
+    constexpr int W = 32 * V;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        uint32_t dn = F.done()[v];
+        if (STOP) {
+            const uint32_t newly = ~dn & ~F.unsat(par)[v];
+            if (first_warp && lane == 0) {
+                if (newly) {
+                    F.done()[v] = dn | newly;
+                    for (uint32_t b = newly; b; b &= b - 1) {
+                        const int ln = __ffs(b) - 1;
+                        iters[(size_t)pk * W + ln * V + v] = it - 1;
+                    }
+                }
+                F.unsat(par ^ 1)[v] = 0u;  // cleared for the next check pass
+            }
+            dn |= newly;
+        }
+        frozen[v] = dn;
+    }
+}
+
 template <int JMAX, int V, bool STOP, bool POST>
 __global__ void __launch_bounds__(kWarps * 32)
 vn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict__ mu, uint32_t *__restrict__ hw,
              uint32_t *__restrict__ flags, float *__restrict__ post, int32_t *__restrict__ iters, float clip, int it,
              int par) {
     constexpr int W = 32 * V;
+    constexpr int NV = kVnPerWarp;
     const int lane = threadIdx.x & 31;
-    const int n = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int warp = threadIdx.x >> 5;
+    const int n0 = blockIdx.x * kWarps * NV + warp;  // this warp: n0 + i * kWarps, i < NV
     const int pk = blockIdx.y;
-    if (n >= d.N) return;
+    if (n0 >= d.N) return;
     PkgFlags F{flags + (size_t)pk * 5 * V, V};
     uint32_t frozen[V];
+    vn_frozen<V, STOP>(F, n0 == 0, lane, it, par, iters, pk, frozen);
     bool warp_on = false, lane_on = false;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        uint32_t dn = F.done()[v];
-        if (STOP) {
-            const uint32_t newly = ~dn & ~F.unsat(par)[v];
-            if (n == 0 && lane == 0 && newly) {
-                // first warp of the package records the stop
-                F.done()[v] = dn | newly;
-                for (uint32_t b = newly; b; b &= b - 1) {
-                    const int ln = __ffs(b) - 1;
-                    iters[(size_t)pk * W + ln * V + v] = it - 1;
-                }
-            }
-            dn |= newly;
-        }
-        frozen[v] = dn;
-        warp_on |= ~dn != 0u;
-        lane_on |= ((~dn) >> lane) & 1u;
-    }
-    if (STOP && n == 0 && lane == 0) {
-#pragma unroll
-        for (int v = 0; v < V; ++v) F.unsat(par ^ 1)[v] = 0u;
+        warp_on |= ~frozen[v] != 0u;
+        lane_on |= ((~frozen[v]) >> lane) & 1u;
     }
     if (!warp_on) return;
+    uint32_t *pmsg = msg + (size_t)pk * d.E * 32 + lane;
+    const float *pmu = mu + (size_t)pk * d.N * W + lane * V;
 
-    const int l = n / d.p;
-    const int k = n - l * d.p;
-    float m[V];
-    {
-        const float *src = mu + ((size_t)pk * d.N + n) * W + lane * V;
+    float m[NV][V];
+    float a[NV][JMAX][V];
+    int eidx[NV][JMAX];
+    // all loads of the warp's variables first
 #pragma unroll
-        for (int v = 0; v < V; ++v) m[v] = lane_on ? src[v] : 1.0f;
-    }
-    float a[JMAX][V];
-    float tot[V];
+    for (int i = 0; i < NV; ++i) {
+        const int n = n0 + i * kWarps;
+        const bool nok = n < d.N;
+        const int l = nok ? n / d.p : 0;
+        const int k = n - l * d.p;
 #pragma unroll
-    for (int v = 0; v < V; ++v) tot[v] = m[v];
-#pragma unroll
-    for (int j = 0; j < JMAX; ++j) {
-        const bool on = j < d.J && d.shift[j * d.L + l] >= 0;
-#pragma unroll
-        for (int v = 0; v < V; ++v) a[j][v] = 0.0f;
-        if (on && lane_on) {
-            Lane<V>::unpack(msg[((size_t)pk * d.E + d.eoff[j * d.L + l] + k) * 32 + lane], a[j]);
-#pragma unroll
-            for (int v = 0; v < V; ++v) tot[v] += a[j][v];
-        }
-    }
-    if (lane_on) {
+        for (int v = 0; v < V; ++v) m[i][v] = (nok && lane_on) ? pmu[n * W + v] : 1.0f;
 #pragma unroll
         for (int j = 0; j < JMAX; ++j) {
-            const bool on = j < d.J && d.shift[j * d.L + l] >= 0;
-            if (!on) continue;
-            float b[V];
+            const bool on = nok && j < d.J && d.shift[j * d.L + l] >= 0;
+            eidx[i][j] = on ? (d.eoff[j * d.L + l] + k) * 32 : -1;
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                float s = m[v];
-#pragma unroll
-                for (int j2 = 0; j2 < JMAX; ++j2)
-                    if (j2 != j) s += a[j2][v];
-                b[v] = clipf(s, clip);
-            }
-            msg[((size_t)pk * d.E + d.eoff[j * d.L + l] + k) * 32 + lane] = Lane<V>::pack(b);
+            for (int v = 0; v < V; ++v) a[i][j][v] = 0.0f;
+            if (on && lane_on) Lane<V>::unpack(pmsg[eidx[i][j]], a[i][j]);
         }
     }
-    float pst[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) pst[v] = clipf(tot[v], clip);
-    if (POST && lane_on) {
-        float *dst = post + ((size_t)pk * d.N + n) * W + lane * V;
+    for (int i = 0; i < NV; ++i) {
+        const int n = n0 + i * kWarps;
+        float tot[V];
 #pragma unroll
-        for (int v = 0; v < V; ++v)
-            if (!((frozen[v] >> lane) & 1u)) dst[v] = pst[v];
-    }
+        for (int v = 0; v < V; ++v) {
+            tot[v] = m[i][v];
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-        const uint32_t bits = __ballot_sync(0xffffffffu, pst[v] < 0.0f);
-        if (lane == 0) {
-            uint32_t *h = hw + ((size_t)pk * d.N + n) * V + v;
-            *h = frozen[v] ? ((bits & ~frozen[v]) | (*h & frozen[v])) : bits;
+            for (int j = 0; j < JMAX; ++j) tot[v] += a[i][j][v];
+        }
+        if (lane_on) {
+#pragma unroll
+            for (int j = 0; j < JMAX; ++j) {
+                if (eidx[i][j] < 0) continue;
+                float b[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    float s = m[i][v];
+#pragma unroll
+                    for (int j2 = 0; j2 < JMAX; ++j2)
+                        if (j2 != j) s += a[i][j2][v];
+                    b[v] = clipf(s, clip);
+                }
+                pmsg[eidx[i][j]] = Lane<V>::pack(b);
+            }
+        }
+        if (n >= d.N) continue;  // warp-uniform
+        float pst[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) pst[v] = clipf(tot[v], clip);
+        if (POST && lane_on) {
+            float *dst = post + ((size_t)pk * d.N + n) * W + lane * V;
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                if (!((frozen[v] >> lane) & 1u)) dst[v] = pst[v];
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const uint32_t bits = __ballot_sync(0xffffffffu, pst[v] < 0.0f);
+            if (lane == 0) {
+                uint32_t *h = hw + ((size_t)pk * d.N + n) * V + v;
+                *h = frozen[v] ? ((bits & ~frozen[v]) | (*h & frozen[v])) : bits;
+            }
         }
     }
 }
@@ -380,80 +453,78 @@ vn_ms_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__restr
              uint32_t *__restrict__ flags, float *__restrict__ post, int32_t *__restrict__ iters, float lsb, int it,
              int par) {
     constexpr int V = 4, W = 128;
+    constexpr int NV = kVnPerWarp;
     const int lane = threadIdx.x & 31;
-    const int n = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int warp = threadIdx.x >> 5;
+    const int n0 = blockIdx.x * kWarps * NV + warp;
     const int pk = blockIdx.y;
-    if (n >= d.N) return;
+    if (n0 >= d.N) return;
     PkgFlags F{flags + (size_t)pk * 5 * V, V};
     uint32_t frozen[V];
+    vn_frozen<V, STOP>(F, n0 == 0, lane, it, par, iters, pk, frozen);
     bool warp_on = false, lane_on = false;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        uint32_t dn = F.done()[v];
-        if (STOP) {
-            const uint32_t newly = ~dn & ~F.unsat(par)[v];
-            if (n == 0 && lane == 0 && newly) {
-                F.done()[v] = dn | newly;
-                for (uint32_t b = newly; b; b &= b - 1) {
-                    const int ln = __ffs(b) - 1;
-                    iters[(size_t)pk * W + ln * V + v] = it - 1;
-                }
-            }
-            dn |= newly;
-        }
-        frozen[v] = dn;
-        warp_on |= ~dn != 0u;
-        lane_on |= ((~dn) >> lane) & 1u;
-    }
-    if (STOP && n == 0 && lane == 0) {
-#pragma unroll
-        for (int v = 0; v < V; ++v) F.unsat(par ^ 1)[v] = 0u;
+        warp_on |= ~frozen[v] != 0u;
+        lane_on |= ((~frozen[v]) >> lane) & 1u;
     }
     if (!warp_on) return;
-    const int l = n / d.p;
-    const int k = n - l * d.p;
-    const uint32_t qw = lane_on ? mu[((size_t)pk * d.N + n) * 32 + lane] : 0x01010101u;
-    uint32_t aw[JMAX];
-    int tot[V];
+    uint32_t *pmsg = msg + (size_t)pk * d.E * 32 + lane;
+    const uint32_t *pmu = mu + (size_t)pk * d.N * 32 + lane;
+    uint32_t qw[NV], aw[NV][JMAX];
+    int eidx[NV][JMAX];
 #pragma unroll
-    for (int v = 0; v < V; ++v) tot[v] = sbyte(qw, v);
-#pragma unroll
-    for (int j = 0; j < JMAX; ++j) {
-        const bool on = j < d.J && d.shift[j * d.L + l] >= 0;
-        aw[j] = 0u;
-        if (on && lane_on) {
-            aw[j] = msg[((size_t)pk * d.E + d.eoff[j * d.L + l] + k) * 32 + lane];
-#pragma unroll
-            for (int v = 0; v < V; ++v) tot[v] += sbyte(aw[j], v);
-        }
-    }
-    if (lane_on) {
+    for (int i = 0; i < NV; ++i) {
+        const int n = n0 + i * kWarps;
+        const bool nok = n < d.N;
+        const int l = nok ? n / d.p : 0;
+        const int k = n - l * d.p;
+        qw[i] = (nok && lane_on) ? pmu[n * 32] : 0x01010101u;
 #pragma unroll
         for (int j = 0; j < JMAX; ++j) {
-            const bool on = j < d.J && d.shift[j * d.L + l] >= 0;
-            if (!on) continue;
-            uint32_t out = 0u;
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                int b = tot[v] - sbyte(aw[j], v);
-                b = b > 127 ? 127 : (b < -127 ? -127 : b);
-                out |= ((uint32_t)(uint8_t)(int8_t)b) << (8 * v);
-            }
-            msg[((size_t)pk * d.E + d.eoff[j * d.L + l] + k) * 32 + lane] = out;
+            const bool on = nok && j < d.J && d.shift[j * d.L + l] >= 0;
+            eidx[i][j] = on ? (d.eoff[j * d.L + l] + k) * 32 : -1;
+            aw[i][j] = (on && lane_on) ? pmsg[eidx[i][j]] : 0u;
         }
     }
-    if (POST && lane_on) {
-        float *dst = post + ((size_t)pk * d.N + n) * W + lane * V;
 #pragma unroll
-        for (int v = 0; v < V; ++v)
-            if (!((frozen[v] >> lane) & 1u)) dst[v] = (float)tot[v] * lsb;
-    }
+    for (int i = 0; i < NV; ++i) {
+        const int n = n0 + i * kWarps;
+        int tot[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-        const uint32_t bits = __ballot_sync(0xffffffffu, tot[v] < 0);
-        if (lane == 0) {
-            uint32_t *h = hw + ((size_t)pk * d.N + n) * V + v;
-            *h = frozen[v] ? ((bits & ~frozen[v]) | (*h & frozen[v])) : bits;
+        for (int v = 0; v < V; ++v) {
+            tot[v] = sbyte(qw[i], v);
+#pragma unroll
+            for (int j = 0; j < JMAX; ++j) tot[v] += sbyte(aw[i][j], v);
+        }
+        if (lane_on) {
+#pragma unroll
+            for (int j = 0; j < JMAX; ++j) {
+                if (eidx[i][j] < 0) continue;
+                uint32_t out = 0u;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    int b = tot[v] - sbyte(aw[i][j], v);
+                    b = b > 127 ? 127 : (b < -127 ? -127 : b);
+                    out |= ((uint32_t)(uint8_t)(int8_t)b) << (8 * v);
+                }
+                pmsg[eidx[i][j]] = out;
+            }
+        }
+        if (n >= d.N) continue;
+        if (POST && lane_on) {
+            float *dst = post + ((size_t)pk * d.N + n) * W + lane * V;
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                if (!((frozen[v] >> lane) & 1u)) dst[v] = (float)tot[v] * lsb;
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const uint32_t bits = __ballot_sync(0xffffffffu, tot[v] < 0);
+            if (lane == 0) {
+                uint32_t *h = hw + ((size_t)pk * d.N + n) * V + v;
+                *h = frozen[v] ? ((bits & ~frozen[v]) | (*h & frozen[v])) : bits;
+            }
         }
     }
 }
@@ -714,6 +785,20 @@ __global__ void channel_frames_kernel(float *__restrict__ out, int N, int gamma,
     }
 }
 
+// the check-node transform on its own, for verification (ldpc_phi_eval)
+__global__ void phi_eval_kernel(const float *__restrict__ x, float *__restrict__ y, int n, int variant) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        y[i] = variant == 0 ? phi_f(x[i]) : phi_ref(x[i]);
+}
+
+ldpc_status phi_eval(const float *x, float *y, int n, int variant, cudaStream_t s) {
+    const int blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+    count_launch();
+    phi_eval_kernel<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(x, y, n, variant);
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -822,7 +907,7 @@ static void cn_dispatch(ldpc_code c, int P, const ldpc_decode_opts &o, bool firs
 
 template <int JMAX, bool STOP, bool POST>
 static void launch_vn(ldpc_code c, int P, const ldpc_decode_opts &o, int it, int par, cudaStream_t s) {
-    dim3 grd((c->d.N + kWarps - 1) / kWarps, P);
+    dim3 grd((c->d.N + kWarps * kVnPerWarp - 1) / (kWarps * kVnPerWarp), P);
     if (o.algo == LDPC_ALGO_MS) {
         vn_ms_kernel<JMAX, STOP, POST><<<grd, kWarps * 32, 0, s>>>(
             c->d, (uint32_t *)c->ws.msg, (const uint32_t *)c->ws.mu, c->ws.hw, c->ws.flags, c->ws.post,

@@ -304,3 +304,19 @@ def test_invalid_arguments(pkg):
     with pytest.raises(pkg.LdpcError) as e:
         pkg.ldpc_decode(code.handle, x, pkg.default_opts(algo=pkg.ALGO_MS, msg=pkg.MSG_F32))
     assert e.value.status == 5
+
+
+def test_phi_transform_accuracy(pkg):
+    """phi(x) = -ln tanh(x/2) as the kernels evaluate it, against the FP64 definition: a few ulp over [0, 30]
+    and over small arguments down to 1e-12 (the output side sees sums of tiny phi values)."""
+    x = np.concatenate([np.linspace(0, 30, 1 << 20), np.logspace(-12, 1.5, 1 << 18)]).astype(np.float32)
+    x = x[x > 0]
+    ref = np.log1p(2.0 / np.expm1(x.astype(np.float64)))
+    ulp = np.spacing(ref.astype(np.float32)).astype(np.float64)
+    for variant, bound in [(0, 4.0), (1, 4.0)]:
+        y = pkg.ldpc_phi_eval(torch.from_numpy(x).cuda(), variant).cpu().numpy().astype(np.float64)
+        err = np.abs(y - ref) / ulp
+        print(f"phi variant {variant}: max {err.max():.2f} ulp, mean {err.mean():.3f} ulp")
+        assert err.max() <= bound, (variant, err.max(), x[err.argmax()])
+    y0 = pkg.ldpc_phi_eval(torch.tensor([0.0, float("inf")], device="cuda"), 0).cpu().numpy()
+    assert y0[0] == np.inf and y0[1] == 0.0
