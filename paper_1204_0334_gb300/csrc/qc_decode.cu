@@ -5,8 +5,10 @@
 // owns V consecutive frames and moves 4 bytes per edge (V = 1 float, V = 2
 // half, V = 4 int8), so every warp access to one edge is one 128-byte line --
 // the paper's Gamma-package idea (Sec. IV-A) at the width of a warp.
-//   msg [P][E][W]   edge messages; beta after the variable pass, alpha after the
-//                   check pass (one store per edge, Sec. IV-A)
+//   msg [P][E][W]   edge messages, one store per edge (Sec. IV-A): alpha after
+//                   the check pass; after the variable pass beta (F16) or, for
+//                   F32 storage, sign(beta) * phi(|beta|), the form the check
+//                   pass sums (so each pass evaluates phi once per edge)
 //   mu  [P][N][W]   channel LLRs (float; int8 for min-sum)
 //   hw  [P][N][V]   hard decisions, one 32-bit word per (variable, frame slot v)
 // Edge k of circulant block (j, l) belongs to variable l*p + k, so the check
@@ -32,13 +34,14 @@ constexpr int kWarps = 8;  // warps per block in the node kernels: 8 consecutive
 // on frames that do not converge, and phi is evaluated twice per edge, so it
 // has to be both accurate and cheap.  Two regimes, both evaluated and selected
 // (no divergence):
-//  x >= 3/2:  phi = 2 atanh(t), t = e^-x <= 0.223, written 2 t S(t^2) with
-//             S(v) = atanh(sqrt v)/sqrt v; t from the SFU exp2 with the
-//             rounding error of x*log2(e) carried to first order.
-//  x <  3/2:  phi = -ln(x/2) + G(x^2/4), G(u) = -ln(tanh(sqrt u)/sqrt u); the
-//             log from the SFU log2, G a polynomial.
-// S and G are degree-3 / degree-5 polynomials fitted here (weighted least
-// squares converging to the minimax fit) to 7e-9 relative / 7e-9 absolute on
+//  x >= 1:  phi = 2 atanh(t), t = e^-x <= 0.368, written 2 t S(t^2) with
+//           S(v) = atanh(sqrt v)/sqrt v; t from the SFU exp2 with the
+//           rounding error of x*log2(e) carried to first order.
+//  x <  1:  phi = -ln(x/2) + G(x^2/4), G(u) = -ln(tanh(sqrt u)/sqrt u); the
+//           log from the SFU log2 (its argument stays below 1/2, where the
+//           approximation has a relative error bound), G a polynomial.
+// S - 1 and G are degree-4 polynomials fitted here (weighted least squares
+// converging to the minimax fit) to 1.3e-8 relative / 3.8e-9 absolute on
 // their intervals; the remaining error is that of the SFU approximations.
 // phi_ref keeps CUDA's expm1f/log1pf form (about 2-3 ulp, several times
 // slower) for verification through ldpc_phi_eval.
@@ -61,7 +64,7 @@ __device__ __forceinline__ float lg2_approx(float a) {
 
 __device__ __forceinline__ float phi_f(float x) {
     x = fminf(x, 100.0f);  // e^-100 flushes to 0; keeps inf - inf out of the error term
-    // x >= 1.5
+    // x >= 1: t = e^-x from exp2 of the split product -x*log2(e)
     const float L2E = 1.44269502f, L2E_LO = 1.92596299e-8f, LN2 = 0.693147182f;
     const float a = -x * L2E;
     float alo = fmaf(-x, L2E, -a);
@@ -70,14 +73,14 @@ __device__ __forceinline__ float phi_f(float x) {
     const float t = fmaf(t0, alo * LN2, t0);
     const float v = t * t;
     const float w = 2.0f * t;
-    const float phiA = fmaf(w, v * fmaf(fmaf(0.15412693f, v, 0.19966834f), v, 0.33333607f), w);
-    // x < 1.5
+    const float sv = v * fmaf(fmaf(fmaf(0.147845685f, v, 0.138392285f), v, 0.200207084f), v, 0.333330393f);
+    const float phiA = fmaf(w, sv, w);
+    // x < 1: -ln(y) with y = x/2 < 1/2, where the log2 approximation is relative-accurate
     const float y = 0.5f * x;
     const float u = y * y;
-    const float G = u * fmaf(fmaf(fmaf(fmaf(0.00130455f, u, -0.00623973f), u, 0.02174386f), u, -0.07776314f), u,
-                             0.33333278f);
+    const float G = u * fmaf(fmaf(fmaf(-0.00555368373f, u, 0.0216362253f), u, -0.0777590200f), u, 0.333332866f);
     const float phiB = fmaf(lg2_approx(y), -LN2, G);
-    return x < 1.5f ? phiB : phiA;
+    return x < 1.0f ? phiB : phiA;
 }
 
 __device__ __forceinline__ float clipf(float x, float c) { return fminf(fmaxf(x, -c), c); }
@@ -121,7 +124,7 @@ struct PkgFlags {
 // backward computation of Sec. IV-A), never "total minus own": that
 // subtraction loses the small terms when one input is unreliable.
 // ---------------------------------------------------------------------------
-template <int DCMAX, int V, bool FIRST, bool SYN>
+template <int DCMAX, int V, bool FIRST, bool SYN, bool XF>
 __global__ void __launch_bounds__(kWarps * 32)
 cn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict__ mu,
              const uint32_t *__restrict__ hw, uint32_t *__restrict__ flags, float clip, int par) {
@@ -155,6 +158,8 @@ cn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict
 #pragma unroll
     for (int v = 0; v < V; ++v) neg[v] = 0u, syn[v] = 0u;
 
+    // incoming messages: beta (FIRST: beta = mu) or, with XF, the stored
+    // transform sign(beta) * phi(|beta|) written by the variable pass
 #pragma unroll
     for (int l = 0; l < DCMAX; ++l) {
         const bool on = l < d.L && sh[l] >= 0;
@@ -165,20 +170,15 @@ cn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict
             if (k >= d.p) k -= d.p;
             const int n = l * d.p + k;
             float x[V];
-            if (lane_on) {
-                if (FIRST) {
+            if (FIRST) {
 #pragma unroll
-                    for (int v = 0; v < V; ++v) x[v] = pmu[n * W + v];
-                } else {
-                    Lane<V>::unpack(pmsg[(eo[l] + k) * 32], x);
-                }
+                for (int v = 0; v < V; ++v) x[v] = pmu[n * W + v];
             } else {
-#pragma unroll
-                for (int v = 0; v < V; ++v) x[v] = 1.0f;
+                Lane<V>::unpack(pmsg[(eo[l] + k) * 32], x);
             }
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                ph[l][v] = phi_f(fabsf(x[v]));
+                ph[l][v] = (XF && !FIRST) ? fabsf(x[v]) : phi_f(fabsf(x[v]));
                 neg[v] |= (x[v] < 0.0f ? 1u : 0u) << l;
             }
             if (SYN) {
@@ -217,7 +217,7 @@ cn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict
 #pragma unroll
     for (int l = DCMAX - 1; l >= 0; --l) {
         const bool on = l < d.L && sh[l] >= 0;
-        if (on && lane_on) {
+        if (on) {
             int k = r + sh[l];
             if (k >= d.p) k -= d.p;
             float a[V];
@@ -227,20 +227,13 @@ cn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict
                 const uint32_t s = par_all[v] ^ ((neg[v] >> l) & 1u);
                 a[v] = s ? -mag : mag;
             }
-            pmsg[(eo[l] + k) * 32] = Lane<V>::pack(a);
+            if (lane_on) pmsg[(eo[l] + k) * 32] = Lane<V>::pack(a);
         }
 #pragma unroll
         for (int v = 0; v < V; ++v) suf[v] += ph[l][v];
     }
 }
 
-// ---------------------------------------------------------------------------
-// Variable-node (vertical) step + posterior + hard decision, eqs. (bpvs),
-// (bpd), (hrddcs).  One warp = one variable of one package.  STOP: frames whose
-// previous decisions satisfied every check (no flag raised by the check pass
-// that just ran) are frozen from now on: their outputs stay those of the
-// previous iteration, which is the early-stop rule.
-// ---------------------------------------------------------------------------
 constexpr int kVnPerWarp = 4;  // variables per warp in the variable-node kernels (more bytes in flight)
 
 // Frozen-frame bookkeeping shared by the variable-node kernels: frames whose
@@ -271,7 +264,7 @@ __device__ __forceinline__ void vn_frozen(PkgFlags F, bool first_warp, int lane,
     }
 }
 
-template <int JMAX, int V, bool STOP, bool POST>
+template <int JMAX, int V, bool STOP, bool POST, bool XF>
 __global__ void __launch_bounds__(kWarps * 32)
 vn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict__ mu, uint32_t *__restrict__ hw,
              uint32_t *__restrict__ flags, float *__restrict__ post, int32_t *__restrict__ iters, float clip, int it,
@@ -339,6 +332,11 @@ vn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict
                     for (int j2 = 0; j2 < JMAX; ++j2)
                         if (j2 != j) s += a[i][j2][v];
                     b[v] = clipf(s, clip);
+                    if (XF) {
+                        // the check pass needs phi(|beta|): evaluate it here, from the unrounded beta
+                        const float f = phi_f(fabsf(b[v]));
+                        b[v] = b[v] < 0.0f ? -f : f;
+                    }
                 }
                 pmsg[eidx[i][j]] = Lane<V>::pack(b);
             }
@@ -875,7 +873,9 @@ ldpc_status qc_pack_llr(ldpc_code c, const float *llr, int gamma, const ldpc_dec
 template <int DCMAX, int V, bool FIRST, bool SYN>
 static void launch_cn_sp(ldpc_code c, int P, const ldpc_decode_opts &o, int par, cudaStream_t s) {
     dim3 grd((c->d.M + kWarps - 1) / kWarps, P);
-    cn_sp_kernel<DCMAX, V, FIRST, SYN><<<grd, kWarps * 32, 0, s>>>(c->d, (uint32_t *)c->ws.msg,
+    // F32 storage carries sign(beta) * phi(|beta|) between the passes; F16 carries beta
+    // (its range cannot hold phi of reliable messages)
+    cn_sp_kernel<DCMAX, V, FIRST, SYN, V == 1><<<grd, kWarps * 32, 0, s>>>(c->d, (uint32_t *)c->ws.msg,
                                                                    (const float *)c->ws.mu, c->ws.hw, c->ws.flags,
                                                                    o.clip, par);
 }
@@ -913,12 +913,12 @@ static void launch_vn(ldpc_code c, int P, const ldpc_decode_opts &o, int it, int
             c->d, (uint32_t *)c->ws.msg, (const uint32_t *)c->ws.mu, c->ws.hw, c->ws.flags, c->ws.post,
             c->ws.iters, ldexpf(1.0f, -o.frac_bits), it, par);
     } else if (o.msg == LDPC_MSG_F16) {
-        vn_sp_kernel<JMAX, 2, STOP, POST><<<grd, kWarps * 32, 0, s>>>(c->d, (uint32_t *)c->ws.msg,
+        vn_sp_kernel<JMAX, 2, STOP, POST, false><<<grd, kWarps * 32, 0, s>>>(c->d, (uint32_t *)c->ws.msg,
                                                                       (const float *)c->ws.mu, c->ws.hw,
                                                                       c->ws.flags, c->ws.post, c->ws.iters, o.clip,
                                                                       it, par);
     } else {
-        vn_sp_kernel<JMAX, 1, STOP, POST><<<grd, kWarps * 32, 0, s>>>(c->d, (uint32_t *)c->ws.msg,
+        vn_sp_kernel<JMAX, 1, STOP, POST, true><<<grd, kWarps * 32, 0, s>>>(c->d, (uint32_t *)c->ws.msg,
                                                                       (const float *)c->ws.mu, c->ws.hw,
                                                                       c->ws.flags, c->ws.post, c->ws.iters, o.clip,
                                                                       it, par);
