@@ -178,6 +178,7 @@ ldpc_status ldpc_code_destroy(ldpc_code c) {
     cudaFree(w.flags);
     cudaFree(w.iters);
     cudaFree(w.counters);
+    cudaFree(w.act);
     cudaFree(w.stage_llr);
     cudaFree(w.stage_post);
     cudaFree(w.stage_hard);

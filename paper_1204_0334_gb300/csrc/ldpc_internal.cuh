@@ -39,6 +39,7 @@ struct DecodeWs {
     uint32_t *flags = nullptr; // per package: done[V], unsat[2][V], valid[V], fin[V]
     int32_t *iters = nullptr;  // [gamma_cap] in package order (frame f)
     unsigned long long *counters = nullptr;  // [8] error counters (ber sim)
+    int *act = nullptr;        // [1 + P]: count, then the packages with a frame still running
     // host-buffer staging
     float *stage_llr = nullptr;   // [gamma][N]
     float *stage_post = nullptr;  // [gamma][N]
@@ -87,6 +88,11 @@ ldpc_status qc_channel_frames(ldpc_code c, double sigma, uint64_t seed, uint64_t
 ldpc_status qc_count_errors(ldpc_code c, int gamma, const ldpc_decode_opts &o, cudaStream_t s);
 
 ldpc_status phi_eval(const float *x, float *y, int n, int variant, cudaStream_t s);
+// pipelined node passes (qc_pipe.cu)
+ldpc_status qc_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, bool syn, int par, cudaStream_t s);
+ldpc_status qc_vn_pipe(ldpc_code c, const ldpc_decode_opts &o, bool stop, bool post, int it, int par,
+                       cudaStream_t s);
+ldpc_status qc_compact(ldpc_code c, int P, int V, cudaStream_t s);
 
 inline int lanes_per_word(int msg) { return msg == LDPC_MSG_F32 ? 1 : (msg == LDPC_MSG_F16 ? 2 : 4); }
 

@@ -17,102 +17,12 @@
 // arithmetic on the shift table, with no index tables (LUT_c / LUT_v of Sec.
 // IV-A are not needed for QC codes).
 #include "ldpc_internal.cuh"
+#include "qc_device.cuh"
 
 #include <algorithm>
 #include <cstdio>
 
 namespace ldpc {
-
-constexpr int kWarps = 8;  // warps per block in the node kernels: 8 consecutive rows / variables
-
-// ---------------------------------------------------------------------------
-// phi(x) = -ln tanh(x/2) = ln((1 + e^-x)/(1 - e^-x)), x >= 0; phi(0) = +inf,
-// phi(+inf) = 0, and phi is its own inverse, so eq. (bphs) becomes
-// alpha = sign * phi(sum of phi(|beta|) over the other edges).
-//
-// Errors of a few ulp here grow by two orders of magnitude over 30 iterations
-// on frames that do not converge, and phi is evaluated twice per edge, so it
-// has to be both accurate and cheap.  Two regimes, both evaluated and selected
-// (no divergence):
-//  x >= 1:  phi = 2 atanh(t), t = e^-x <= 0.368, written 2 t S(t^2) with
-//           S(v) = atanh(sqrt v)/sqrt v; t from the SFU exp2 with the
-//           rounding error of x*log2(e) carried to first order.
-//  x <  1:  phi = -ln(x/2) + G(x^2/4), G(u) = -ln(tanh(sqrt u)/sqrt u); the
-//           log from the SFU log2 (its argument stays below 1/2, where the
-//           approximation has a relative error bound), G a polynomial.
-// S - 1 and G are degree-4 polynomials fitted here (weighted least squares
-// converging to the minimax fit) to 1.3e-8 relative / 3.8e-9 absolute on
-// their intervals; the remaining error is that of the SFU approximations.
-// phi_ref keeps CUDA's expm1f/log1pf form (about 2-3 ulp, several times
-// slower) for verification through ldpc_phi_eval.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float phi_ref(float x) {
-    const float e = expm1f(x);
-    return log1pf(2.0f * __frcp_rn(e));
-}
-
-__device__ __forceinline__ float ex2_approx(float a) {
-    float r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
-    return r;
-}
-__device__ __forceinline__ float lg2_approx(float a) {
-    float r;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
-    return r;
-}
-
-__device__ __forceinline__ float phi_f(float x) {
-    x = fminf(x, 100.0f);  // e^-100 flushes to 0; keeps inf - inf out of the error term
-    // x >= 1: t = e^-x from exp2 of the split product -x*log2(e)
-    const float L2E = 1.44269502f, L2E_LO = 1.92596299e-8f, LN2 = 0.693147182f;
-    const float a = -x * L2E;
-    float alo = fmaf(-x, L2E, -a);
-    alo = fmaf(-x, L2E_LO, alo);
-    const float t0 = ex2_approx(a);
-    const float t = fmaf(t0, alo * LN2, t0);
-    const float v = t * t;
-    const float w = 2.0f * t;
-    const float sv = v * fmaf(fmaf(fmaf(0.147845685f, v, 0.138392285f), v, 0.200207084f), v, 0.333330393f);
-    const float phiA = fmaf(w, sv, w);
-    // x < 1: -ln(y) with y = x/2 < 1/2, where the log2 approximation is relative-accurate
-    const float y = 0.5f * x;
-    const float u = y * y;
-    const float G = u * fmaf(fmaf(fmaf(-0.00555368373f, u, 0.0216362253f), u, -0.0777590200f), u, 0.333332866f);
-    const float phiB = fmaf(lg2_approx(y), -LN2, G);
-    return x < 1.0f ? phiB : phiA;
-}
-
-__device__ __forceinline__ float clipf(float x, float c) { return fminf(fmaxf(x, -c), c); }
-
-// lane word <-> V floats
-template <int V> struct Lane;
-template <> struct Lane<1> {
-    static __device__ __forceinline__ void unpack(uint32_t w, float *x) { x[0] = __uint_as_float(w); }
-    static __device__ __forceinline__ uint32_t pack(const float *x) { return __float_as_uint(x[0]); }
-};
-template <> struct Lane<2> {
-    static __device__ __forceinline__ void unpack(uint32_t w, float *x) {
-        __half2 h = *reinterpret_cast<__half2 *>(&w);
-        float2 f = __half22float2(h);
-        x[0] = f.x;
-        x[1] = f.y;
-    }
-    static __device__ __forceinline__ uint32_t pack(const float *x) {
-        __half2 h = __floats2half2_rn(x[0], x[1]);
-        return *reinterpret_cast<uint32_t *>(&h);
-    }
-};
-
-// flags of one package (V words per field; bit = lane)
-struct PkgFlags {
-    uint32_t *base;
-    int V;
-    __device__ uint32_t *done() const { return base; }
-    __device__ uint32_t *unsat(int par) const { return base + (1 + par) * V; }
-    __device__ uint32_t *valid() const { return base + 3 * V; }
-    __device__ uint32_t *fin() const { return base + 4 * V; }
-};
 
 // ---------------------------------------------------------------------------
 // Check-node (horizontal) step, sum-product.  One warp = one check row of one
@@ -234,134 +144,6 @@ cn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict
     }
 }
 
-constexpr int kVnPerWarp = 4;  // variables per warp in the variable-node kernels (more bytes in flight)
-
-// Frozen-frame bookkeeping shared by the variable-node kernels: frames whose
-// previous decisions satisfied every check stop here (STOP); the first warp of
-// the package records it.  Returns the frozen mask per frame slot.
-template <int V, bool STOP>
-__device__ __forceinline__ void vn_frozen(PkgFlags F, bool first_warp, int lane, int it, int par,
-                                          int32_t *__restrict__ iters, int pk, uint32_t *frozen) {
-    constexpr int W = 32 * V;
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-        uint32_t dn = F.done()[v];
-        if (STOP) {
-            const uint32_t newly = ~dn & ~F.unsat(par)[v];
-            if (first_warp && lane == 0) {
-                if (newly) {
-                    F.done()[v] = dn | newly;
-                    for (uint32_t b = newly; b; b &= b - 1) {
-                        const int ln = __ffs(b) - 1;
-                        iters[(size_t)pk * W + ln * V + v] = it - 1;
-                    }
-                }
-                F.unsat(par ^ 1)[v] = 0u;  // cleared for the next check pass
-            }
-            dn |= newly;
-        }
-        frozen[v] = dn;
-    }
-}
-
-template <int JMAX, int V, bool STOP, bool POST, bool XF>
-__global__ void __launch_bounds__(kWarps * 32)
-vn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict__ mu, uint32_t *__restrict__ hw,
-             uint32_t *__restrict__ flags, float *__restrict__ post, int32_t *__restrict__ iters, float clip, int it,
-             int par) {
-    constexpr int W = 32 * V;
-    constexpr int NV = kVnPerWarp;
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int n0 = blockIdx.x * kWarps * NV + warp;  // this warp: n0 + i * kWarps, i < NV
-    const int pk = blockIdx.y;
-    if (n0 >= d.N) return;
-    PkgFlags F{flags + (size_t)pk * 5 * V, V};
-    uint32_t frozen[V];
-    vn_frozen<V, STOP>(F, n0 == 0, lane, it, par, iters, pk, frozen);
-    bool warp_on = false, lane_on = false;
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-        warp_on |= ~frozen[v] != 0u;
-        lane_on |= ((~frozen[v]) >> lane) & 1u;
-    }
-    if (!warp_on) return;
-    uint32_t *pmsg = msg + (size_t)pk * d.E * 32 + lane;
-    const float *pmu = mu + (size_t)pk * d.N * W + lane * V;
-
-    float m[NV][V];
-    float a[NV][JMAX][V];
-    int eidx[NV][JMAX];
-    // all loads of the warp's variables first
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        const int n = n0 + i * kWarps;
-        const bool nok = n < d.N;
-        const int l = nok ? n / d.p : 0;
-        const int k = n - l * d.p;
-#pragma unroll
-        for (int v = 0; v < V; ++v) m[i][v] = (nok && lane_on) ? pmu[n * W + v] : 1.0f;
-#pragma unroll
-        for (int j = 0; j < JMAX; ++j) {
-            const bool on = nok && j < d.J && d.shift[j * d.L + l] >= 0;
-            eidx[i][j] = on ? (d.eoff[j * d.L + l] + k) * 32 : -1;
-#pragma unroll
-            for (int v = 0; v < V; ++v) a[i][j][v] = 0.0f;
-            if (on && lane_on) Lane<V>::unpack(pmsg[eidx[i][j]], a[i][j]);
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        const int n = n0 + i * kWarps;
-        float tot[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            tot[v] = m[i][v];
-#pragma unroll
-            for (int j = 0; j < JMAX; ++j) tot[v] += a[i][j][v];
-        }
-        if (lane_on) {
-#pragma unroll
-            for (int j = 0; j < JMAX; ++j) {
-                if (eidx[i][j] < 0) continue;
-                float b[V];
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    float s = m[i][v];
-#pragma unroll
-                    for (int j2 = 0; j2 < JMAX; ++j2)
-                        if (j2 != j) s += a[i][j2][v];
-                    b[v] = clipf(s, clip);
-                    if (XF) {
-                        // the check pass needs phi(|beta|): evaluate it here, from the unrounded beta
-                        const float f = phi_f(fabsf(b[v]));
-                        b[v] = b[v] < 0.0f ? -f : f;
-                    }
-                }
-                pmsg[eidx[i][j]] = Lane<V>::pack(b);
-            }
-        }
-        if (n >= d.N) continue;  // warp-uniform
-        float pst[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) pst[v] = clipf(tot[v], clip);
-        if (POST && lane_on) {
-            float *dst = post + ((size_t)pk * d.N + n) * W + lane * V;
-#pragma unroll
-            for (int v = 0; v < V; ++v)
-                if (!((frozen[v] >> lane) & 1u)) dst[v] = pst[v];
-        }
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const uint32_t bits = __ballot_sync(0xffffffffu, pst[v] < 0.0f);
-            if (lane == 0) {
-                uint32_t *h = hw + ((size_t)pk * d.N + n) * V + v;
-                *h = frozen[v] ? ((bits & ~frozen[v]) | (*h & frozen[v])) : bits;
-            }
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Integer min-sum over int8 messages, 4 frames per lane in one 32-bit word,
 // evaluated with the byte-SIMD video instructions.  Check update:
@@ -443,89 +225,6 @@ cn_ms_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__restr
     }
 }
 
-__device__ __forceinline__ int sbyte(uint32_t w, int v) { return (int)(int8_t)(uint8_t)(w >> (8 * v)); }
-
-template <int JMAX, bool STOP, bool POST>
-__global__ void __launch_bounds__(kWarps * 32)
-vn_ms_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__restrict__ mu, uint32_t *__restrict__ hw,
-             uint32_t *__restrict__ flags, float *__restrict__ post, int32_t *__restrict__ iters, float lsb, int it,
-             int par) {
-    constexpr int V = 4, W = 128;
-    constexpr int NV = kVnPerWarp;
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int n0 = blockIdx.x * kWarps * NV + warp;
-    const int pk = blockIdx.y;
-    if (n0 >= d.N) return;
-    PkgFlags F{flags + (size_t)pk * 5 * V, V};
-    uint32_t frozen[V];
-    vn_frozen<V, STOP>(F, n0 == 0, lane, it, par, iters, pk, frozen);
-    bool warp_on = false, lane_on = false;
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-        warp_on |= ~frozen[v] != 0u;
-        lane_on |= ((~frozen[v]) >> lane) & 1u;
-    }
-    if (!warp_on) return;
-    uint32_t *pmsg = msg + (size_t)pk * d.E * 32 + lane;
-    const uint32_t *pmu = mu + (size_t)pk * d.N * 32 + lane;
-    uint32_t qw[NV], aw[NV][JMAX];
-    int eidx[NV][JMAX];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        const int n = n0 + i * kWarps;
-        const bool nok = n < d.N;
-        const int l = nok ? n / d.p : 0;
-        const int k = n - l * d.p;
-        qw[i] = (nok && lane_on) ? pmu[n * 32] : 0x01010101u;
-#pragma unroll
-        for (int j = 0; j < JMAX; ++j) {
-            const bool on = nok && j < d.J && d.shift[j * d.L + l] >= 0;
-            eidx[i][j] = on ? (d.eoff[j * d.L + l] + k) * 32 : -1;
-            aw[i][j] = (on && lane_on) ? pmsg[eidx[i][j]] : 0u;
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        const int n = n0 + i * kWarps;
-        int tot[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            tot[v] = sbyte(qw[i], v);
-#pragma unroll
-            for (int j = 0; j < JMAX; ++j) tot[v] += sbyte(aw[i][j], v);
-        }
-        if (lane_on) {
-#pragma unroll
-            for (int j = 0; j < JMAX; ++j) {
-                if (eidx[i][j] < 0) continue;
-                uint32_t out = 0u;
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    int b = tot[v] - sbyte(aw[i][j], v);
-                    b = b > 127 ? 127 : (b < -127 ? -127 : b);
-                    out |= ((uint32_t)(uint8_t)(int8_t)b) << (8 * v);
-                }
-                pmsg[eidx[i][j]] = out;
-            }
-        }
-        if (n >= d.N) continue;
-        if (POST && lane_on) {
-            float *dst = post + ((size_t)pk * d.N + n) * W + lane * V;
-#pragma unroll
-            for (int v = 0; v < V; ++v)
-                if (!((frozen[v] >> lane) & 1u)) dst[v] = (float)tot[v] * lsb;
-        }
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const uint32_t bits = __ballot_sync(0xffffffffu, tot[v] < 0);
-            if (lane == 0) {
-                uint32_t *h = hw + ((size_t)pk * d.N + n) * V + v;
-                *h = frozen[v] ? ((bits & ~frozen[v]) | (*h & frozen[v])) : bits;
-            }
-        }
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Final syndrome of the last decisions (for ok), and the per-frame finish.
@@ -819,6 +518,7 @@ ldpc_status qc_ensure_workspace(ldpc_code c, size_t gamma, int want_host_stage) 
         cudaFree(w.flags);
         cudaFree(w.iters);
         cudaFree(w.counters);
+        cudaFree(w.act);
         cudaFree(w.stage_llr);
         cudaFree(w.stage_post);
         cudaFree(w.stage_hard);
@@ -831,7 +531,8 @@ ldpc_status qc_ensure_workspace(ldpc_code c, size_t gamma, int want_host_stage) 
             cudaMalloc(&w.hw, (size_t)c->d.N * P32 * 4) != cudaSuccess ||
             cudaMalloc(&w.flags, P32 * 5 * 4) != cudaSuccess ||
             cudaMalloc(&w.iters, cap * 2 * 4) != cudaSuccess ||
-            cudaMalloc(&w.counters, 8 * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaMalloc(&w.counters, 8 * sizeof(unsigned long long)) != cudaSuccess ||
+            cudaMalloc(&w.act, (P32 + 1) * sizeof(int)) != cudaSuccess) {
             cudaGetLastError();
             set_error("device allocation for %zu frames failed", cap);
             return LDPC_ENOMEM;
@@ -905,60 +606,40 @@ static void cn_dispatch(ldpc_code c, int P, const ldpc_decode_opts &o, bool firs
     }
 }
 
-template <int JMAX, bool STOP, bool POST>
-static void launch_vn(ldpc_code c, int P, const ldpc_decode_opts &o, int it, int par, cudaStream_t s) {
-    dim3 grd((c->d.N + kWarps * kVnPerWarp - 1) / (kWarps * kVnPerWarp), P);
-    if (o.algo == LDPC_ALGO_MS) {
-        vn_ms_kernel<JMAX, STOP, POST><<<grd, kWarps * 32, 0, s>>>(
-            c->d, (uint32_t *)c->ws.msg, (const uint32_t *)c->ws.mu, c->ws.hw, c->ws.flags, c->ws.post,
-            c->ws.iters, ldexpf(1.0f, -o.frac_bits), it, par);
-    } else if (o.msg == LDPC_MSG_F16) {
-        vn_sp_kernel<JMAX, 2, STOP, POST, false><<<grd, kWarps * 32, 0, s>>>(c->d, (uint32_t *)c->ws.msg,
-                                                                      (const float *)c->ws.mu, c->ws.hw,
-                                                                      c->ws.flags, c->ws.post, c->ws.iters, o.clip,
-                                                                      it, par);
-    } else {
-        vn_sp_kernel<JMAX, 1, STOP, POST, true><<<grd, kWarps * 32, 0, s>>>(c->d, (uint32_t *)c->ws.msg,
-                                                                      (const float *)c->ws.mu, c->ws.hw,
-                                                                      c->ws.flags, c->ws.post, c->ws.iters, o.clip,
-                                                                      it, par);
-    }
-}
-
-template <int JMAX>
-static void vn_dispatch(ldpc_code c, int P, const ldpc_decode_opts &o, bool stop, bool post, int it, int par,
-                        cudaStream_t s) {
-    if (stop) {
-        if (post) launch_vn<JMAX, true, true>(c, P, o, it, par, s);
-        else launch_vn<JMAX, true, false>(c, P, o, it, par, s);
-    } else {
-        if (post) launch_vn<JMAX, false, true>(c, P, o, it, par, s);
-        else launch_vn<JMAX, false, false>(c, P, o, it, par, s);
-    }
-}
-
 ldpc_status qc_decode_device(ldpc_code c, int gamma, const ldpc_decode_opts &o, bool want_post, cudaStream_t s) {
     const int V = words_per_lane(o), W = 32 * V;
     const int P = (gamma + W - 1) / W;
     init_flags_kernel<<<(P + 127) / 128, 128, 0, s>>>(c->ws.flags, P, V, gamma);
-    count_launch(3);  // init, final syndrome, finish
     LDPC_CUDA_TRY(cudaMemsetAsync(c->ws.hw, 0, (size_t)P * c->d.N * V * 4, s));
+    ldpc_status st = qc_compact(c, P, V, s);  // every package starts active
+    if (st != LDPC_OK) return st;
+    count_launch(4);  // init, compact, final syndrome, finish
     const int dcm = c->d.dc_max;
     for (int it = 1; it <= o.max_iter; ++it) {
-        const bool first = it == 1;
         const bool syn = o.early_stop && it >= 2;
         const int par = it & 1;
         const int slot_cn = prof_begin(0, s);
-        if (dcm <= 8) cn_dispatch<8>(c, P, o, first, syn, par, s);
-        else if (dcm <= 16) cn_dispatch<16>(c, P, o, first, syn, par, s);
-        else if (dcm <= 24) cn_dispatch<24>(c, P, o, first, syn, par, s);
-        else cn_dispatch<32>(c, P, o, first, syn, par, s);
+        if (it == 1) {
+            // beta = mu: the first check pass reads the channel LLRs
+            if (dcm <= 8) cn_dispatch<8>(c, P, o, true, false, par, s);
+            else if (dcm <= 16) cn_dispatch<16>(c, P, o, true, false, par, s);
+            else if (dcm <= 24) cn_dispatch<24>(c, P, o, true, false, par, s);
+            else cn_dispatch<32>(c, P, o, true, false, par, s);
+        } else {
+            st = qc_cn_pipe(c, o, syn, par, s);
+            if (st != LDPC_OK) return st;
+        }
         prof_end(slot_cn, s);
         const int slot_vn = prof_begin(1, s);
-        if (c->d.J <= 4) vn_dispatch<4>(c, P, o, syn, want_post, it, par, s);
-        else vn_dispatch<8>(c, P, o, syn, want_post, it, par, s);
+        st = qc_vn_pipe(c, o, syn, want_post, it, par, s);
+        if (st != LDPC_OK) return st;
         prof_end(slot_vn, s);
         count_launch(2);
+        if (o.early_stop && it < o.max_iter) {
+            st = qc_compact(c, P, V, s);
+            if (st != LDPC_OK) return st;
+            count_launch();
+        }
     }
     {
         dim3 grd((c->d.M + 127) / 128, P);

@@ -1,0 +1,103 @@
+// Device helpers shared by the QC decoder kernels: the check-node transform
+// phi, lane-word packing of V frames, and the per-package flag layout.
+#pragma once
+
+#include "ldpc_internal.cuh"
+
+namespace ldpc {
+
+constexpr int kWarps = 8;  // warps per block in the node kernels: 8 consecutive rows / variables
+
+// ---------------------------------------------------------------------------
+// phi(x) = -ln tanh(x/2) = ln((1 + e^-x)/(1 - e^-x)), x >= 0; phi(0) = +inf,
+// phi(+inf) = 0, and phi is its own inverse, so eq. (bphs) becomes
+// alpha = sign * phi(sum of phi(|beta|) over the other edges).
+//
+// Errors of a few ulp here grow by two orders of magnitude over 30 iterations
+// on frames that do not converge, and phi is evaluated twice per edge, so it
+// has to be both accurate and cheap.  Two regimes, both evaluated and selected
+// (no divergence):
+//  x >= 1:  phi = 2 atanh(t), t = e^-x <= 0.368, written 2 t S(t^2) with
+//           S(v) = atanh(sqrt v)/sqrt v; t from the SFU exp2 with the
+//           rounding error of x*log2(e) carried to first order.
+//  x <  1:  phi = -ln(x/2) + G(x^2/4), G(u) = -ln(tanh(sqrt u)/sqrt u); the
+//           log from the SFU log2 (its argument stays below 1/2, where the
+//           approximation has a relative error bound), G a polynomial.
+// S - 1 and G are degree-4 polynomials fitted here (weighted least squares
+// converging to the minimax fit) to 1.3e-8 relative / 3.8e-9 absolute on
+// their intervals; the remaining error is that of the SFU approximations.
+// phi_ref keeps CUDA's expm1f/log1pf form (about 2-3 ulp, several times
+// slower) for verification through ldpc_phi_eval.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float phi_ref(float x) {
+    const float e = expm1f(x);
+    return log1pf(2.0f * __frcp_rn(e));
+}
+
+__device__ __forceinline__ float ex2_approx(float a) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ float lg2_approx(float a) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+
+__device__ __forceinline__ float phi_f(float x) {
+    x = fminf(x, 100.0f);  // e^-100 flushes to 0; keeps inf - inf out of the error term
+    // x >= 1: t = e^-x from exp2 of the split product -x*log2(e)
+    const float L2E = 1.44269502f, L2E_LO = 1.92596299e-8f, LN2 = 0.693147182f;
+    const float a = -x * L2E;
+    float alo = fmaf(-x, L2E, -a);
+    alo = fmaf(-x, L2E_LO, alo);
+    const float t0 = ex2_approx(a);
+    const float t = fmaf(t0, alo * LN2, t0);
+    const float v = t * t;
+    const float w = 2.0f * t;
+    const float sv = v * fmaf(fmaf(fmaf(0.147845685f, v, 0.138392285f), v, 0.200207084f), v, 0.333330393f);
+    const float phiA = fmaf(w, sv, w);
+    // x < 1: -ln(y) with y = x/2 < 1/2, where the log2 approximation is relative-accurate
+    const float y = 0.5f * x;
+    const float u = y * y;
+    const float G = u * fmaf(fmaf(fmaf(-0.00555368373f, u, 0.0216362253f), u, -0.0777590200f), u, 0.333332866f);
+    const float phiB = fmaf(lg2_approx(y), -LN2, G);
+    return x < 1.0f ? phiB : phiA;
+}
+
+__device__ __forceinline__ float clipf(float x, float c) { return fminf(fmaxf(x, -c), c); }
+
+// lane word <-> V floats
+template <int V> struct Lane;
+template <> struct Lane<1> {
+    static __device__ __forceinline__ void unpack(uint32_t w, float *x) { x[0] = __uint_as_float(w); }
+    static __device__ __forceinline__ uint32_t pack(const float *x) { return __float_as_uint(x[0]); }
+};
+template <> struct Lane<2> {
+    static __device__ __forceinline__ void unpack(uint32_t w, float *x) {
+        __half2 h = *reinterpret_cast<__half2 *>(&w);
+        float2 f = __half22float2(h);
+        x[0] = f.x;
+        x[1] = f.y;
+    }
+    static __device__ __forceinline__ uint32_t pack(const float *x) {
+        __half2 h = __floats2half2_rn(x[0], x[1]);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+};
+
+// flags of one package (V words per field; bit = lane)
+struct PkgFlags {
+    uint32_t *base;
+    int V;
+    __device__ uint32_t *done() const { return base; }
+    __device__ uint32_t *unsat(int par) const { return base + (1 + par) * V; }
+    __device__ uint32_t *valid() const { return base + 3 * V; }
+    __device__ uint32_t *fin() const { return base + 4 * V; }
+};
+
+
+__device__ __forceinline__ int sbyte(uint32_t w, int v) { return (int)(int8_t)(uint8_t)(w >> (8 * v)); }
+
+}  // namespace ldpc

@@ -1,0 +1,588 @@
+// Software-pipelined check-node and variable-node passes (Algorithm 1,
+// horizontal and vertical steps) for the QC block-code decoder.
+//
+// The node passes stream the message store through HBM.  Each warp needs the
+// 128-byte packages of 24 edges (check pass) or of 4 variables x J edges plus
+// their channel LLRs (variable pass) before it can compute, and then spends a
+// long stretch on arithmetic: with one work item per warp the SM runs out of
+// bytes in flight.  Here warps are persistent: each walks a strided list of
+// work items and keeps the packages of the next kStages-1 items in flight in
+// its own shared-memory ring, copied with cp.async (16 bytes per lane,
+// completion tracked by cp.async groups -- hardware waits, no spinning), while
+// it computes the current item out of shared memory.  Results go straight to
+// global memory (in place, Sec. IV-A).  Only packages with a frame still
+// running are visited: a compaction pass after each variable pass lists them.
+#include "qc_device.cuh"
+
+#include <mutex>
+#include <unordered_map>
+
+namespace ldpc {
+
+constexpr int kStages = 3;
+constexpr int kNV = 4;  // consecutive variables per variable-pass work item
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int DCMAX, int V, bool SYN>
+struct CnStage {
+    static constexpr int SEG = DCMAX * 32;          // edge packages, [l][32 words]
+    static constexpr int HW = SYN ? DCMAX * V : 0;  // hard-decision words of the row's variables
+    static constexpr int FL = SEG + HW;             // done words
+    static constexpr int WORDS = (FL + V + 3) & ~3;
+};
+
+// ---------------------------------------------------------------------------
+// check pass (iterations >= 2): sum-product (MS = false) or integer min-sum
+// ---------------------------------------------------------------------------
+template <int DCMAX, int V, bool SYN, bool XF, bool MS>
+__global__ void __launch_bounds__(kWarps * 32)
+cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__restrict__ hw,
+               uint32_t *__restrict__ flags, const int *__restrict__ act, float clip, int par) {
+    using St = CnStage<DCMAX, V, SYN>;
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ int s_sh[kMaxJ * kMaxL], s_eo[kMaxJ * kMaxL];
+    for (int i = threadIdx.x; i < d.J * d.L; i += blockDim.x) {
+        s_sh[i] = d.shift[i];
+        s_eo[i] = d.eoff[i];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *ring = smem + warp * kStages * St::WORDS;
+    // work items (package, check row); the host keeps packages * rows below 2^31
+    const int total = act[0] * d.M;
+    const int *list = act + 1;
+    const int GW = gridDim.x * kWarps;
+    int item = blockIdx.x * kWarps + warp;
+
+    auto issue = [&](int it, int slot) {
+        if (it < total) {
+            const int a = it / d.M;
+            const int m = it - a * d.M;
+            const int pk = __ldg(list + a);
+            const int j = m / d.p, r = m - j * d.p;
+            const uint32_t *gmsg = msg + (size_t)pk * d.E * 32;
+            uint32_t *dst = ring + slot * St::WORDS;
+            const int g = lane >> 3, sub = lane & 7;
+#pragma unroll
+            for (int q = 0; q < DCMAX / 4; ++q) {
+                const int l = 4 * q + g;
+                if (l < d.L) {
+                    const int sh = s_sh[j * d.L + l];
+                    if (sh >= 0) {
+                        int k = r + sh;
+                        if (k >= d.p) k -= d.p;
+                        cp_async16(dst + l * 32 + sub * 4, gmsg + (size_t)(s_eo[j * d.L + l] + k) * 32 + sub * 4);
+                    }
+                }
+            }
+            if (SYN) {
+                for (int w = lane; w < DCMAX * V; w += 32) {
+                    const int l = w / V, v = w - l * V;
+                    if (l < d.L) {
+                        const int sh = s_sh[j * d.L + l];
+                        if (sh >= 0) {
+                            int k = r + sh;
+                            if (k >= d.p) k -= d.p;
+                            cp_async4(dst + St::SEG + w, hw + ((size_t)pk * d.N + (size_t)l * d.p + k) * V + v);
+                        }
+                    }
+                }
+            }
+            if (lane < V) cp_async4(dst + St::FL + lane, flags + (size_t)pk * 5 * V + lane);
+        }
+        cp_async_commit();
+    };
+
+#pragma unroll
+    for (int s = 0; s < kStages - 1; ++s) issue(item + s * GW, s);
+    int slot = 0;
+    for (; item < total; item += GW) {
+        issue(item + (kStages - 1) * GW, (slot + kStages - 1) % kStages);
+        cp_async_wait<kStages - 1>();
+        __syncwarp();
+        const uint32_t *S = ring + slot * St::WORDS;
+        const int a = item / d.M;
+        const int m = item - a * d.M;
+        const int pk = __ldg(list + a);
+        const int j = m / d.p, r = m - j * d.p;
+        uint32_t *gmsg = msg + (size_t)pk * d.E * 32 + lane;
+        uint32_t actv[V];
+        bool lane_on = false;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            actv[v] = ~S[St::FL + v];
+            lane_on |= (actv[v] >> lane) & 1u;
+        }
+        uint32_t syn[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) syn[v] = 0u;
+        if constexpr (!MS) {
+            float ph[DCMAX][V];
+            uint32_t neg[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) neg[v] = 0u;
+#pragma unroll
+            for (int l = 0; l < DCMAX; ++l) {
+                const bool on = l < d.L && s_sh[j * d.L + l] >= 0;
+#pragma unroll
+                for (int v = 0; v < V; ++v) ph[l][v] = 0.0f;
+                if (on) {
+                    float x[V];
+                    Lane<V>::unpack(S[l * 32 + lane], x);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        ph[l][v] = XF ? fabsf(x[v]) : phi_f(fabsf(x[v]));
+                        neg[v] |= (x[v] < 0.0f ? 1u : 0u) << l;
+                        if (SYN) syn[v] ^= S[St::SEG + l * V + v];
+                    }
+                }
+            }
+            float pre[DCMAX][V];
+            {
+                float acc[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] = 0.0f;
+#pragma unroll
+                for (int l = 0; l < DCMAX; ++l)
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        pre[l][v] = acc[v];
+                        acc[v] += ph[l][v];
+                    }
+            }
+            uint32_t par_all[V];
+            float suf[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) par_all[v] = __popc(neg[v]) & 1u, suf[v] = 0.0f;
+#pragma unroll
+            for (int l = DCMAX - 1; l >= 0; --l) {
+                const int sh = l < d.L ? s_sh[j * d.L + l] : -1;
+                if (sh >= 0) {
+                    int k = r + sh;
+                    if (k >= d.p) k -= d.p;
+                    float out[V];
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const float mag = fminf(phi_f(pre[l][v] + suf[v]), clip);
+                        out[v] = (par_all[v] ^ ((neg[v] >> l) & 1u)) ? -mag : mag;
+                    }
+                    if (lane_on) gmsg[(size_t)(s_eo[j * d.L + l] + k) * 32] = Lane<V>::pack(out);
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v) suf[v] += ph[l][v];
+            }
+        } else {
+            // min-sum, 4 frames per lane word (V == 4)
+            uint32_t ab[DCMAX], sg[DCMAX];
+            uint32_t min1 = 0x7f7f7f7fu, min2 = 0x7f7f7f7fu, sgn = 0u;
+#pragma unroll
+            for (int l = 0; l < DCMAX; ++l) {
+                const bool on = l < d.L && s_sh[j * d.L + l] >= 0;
+                ab[l] = 0u;
+                sg[l] = 0u;
+                if (on) {
+                    const uint32_t x = S[l * 32 + lane];
+                    const uint32_t av = __vabsss4(x);
+                    sg[l] = x & 0x80808080u;
+                    ab[l] = av;
+                    sgn ^= sg[l];
+                    min2 = __vminu4(min2, __vmaxu4(min1, av));
+                    min1 = __vminu4(min1, av);
+                    if (SYN) {
+#pragma unroll
+                        for (int v = 0; v < V; ++v) syn[v] ^= S[St::SEG + l * V + v];
+                    }
+                }
+            }
+            if (lane_on) {
+#pragma unroll
+                for (int l = 0; l < DCMAX; ++l) {
+                    const int sh = l < d.L ? s_sh[j * d.L + l] : -1;
+                    if (sh < 0) continue;
+                    int k = r + sh;
+                    if (k >= d.p) k -= d.p;
+                    const uint32_t eq = __vcmpeq4(ab[l], min1);
+                    const uint32_t mag = (min2 & eq) | (min1 & ~eq);
+                    const uint32_t sneg = ((sgn ^ sg[l]) >> 7) & 0x01010101u;
+                    gmsg[(size_t)(s_eo[j * d.L + l] + k) * 32] = __vadd4(mag ^ (sneg * 0xffu), sneg);
+                }
+            }
+        }
+        if (SYN && lane == 0) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const uint32_t bad = syn[v] & actv[v];
+                if (bad) atomicOr(flags + (size_t)pk * 5 * V + (1 + par) * V + v, bad);
+            }
+        }
+        __syncwarp();
+        slot = (slot + 1) % kStages;
+    }
+    cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
+// variable pass: eqs. (bpvs), (bpd), (hrddcs) on kNV consecutive variables
+// ---------------------------------------------------------------------------
+template <int JMAX, int V, bool STOP, bool MS>
+struct VnStage {
+    static constexpr int MUW = MS ? 32 : 32 * V;     // channel-LLR words per variable
+    static constexpr int MU = 0;
+    static constexpr int AL = kNV * MUW;             // [i][j][32] edge packages
+    static constexpr int HW = AL + kNV * JMAX * 32;  // old hard words [i][V]
+    static constexpr int FL = HW + kNV * V;          // done[V], unsat[V]
+    static constexpr int WORDS = (FL + 2 * V + 3) & ~3;
+};
+
+template <int JMAX, int V, bool STOP, bool POST, bool XF, bool MS>
+__global__ void __launch_bounds__(kWarps * 32)
+vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__restrict__ mu, uint32_t *__restrict__ hw,
+               uint32_t *__restrict__ flags, float *__restrict__ post, int32_t *__restrict__ iters,
+               const int *__restrict__ act, float clip, float lsb, int it, int par) {
+    using St = VnStage<JMAX, V, STOP, MS>;
+    constexpr int W = 32 * V;
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ int s_sh[kMaxJ * kMaxL], s_eo[kMaxJ * kMaxL];
+    for (int i = threadIdx.x; i < d.J * d.L; i += blockDim.x) {
+        s_sh[i] = d.shift[i];
+        s_eo[i] = d.eoff[i];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *ring = smem + warp * kStages * St::WORDS;
+    const int G = (d.N + kNV - 1) / kNV;
+    const int total = act[0] * G;  // work items (package, group of kNV variables)
+    const int *list = act + 1;
+    const int GW = gridDim.x * kWarps;
+    int item = blockIdx.x * kWarps + warp;
+    constexpr int MU_SEGS = St::MUW / 32;
+    constexpr int NSEG = kNV * (MU_SEGS + JMAX);
+
+    auto issue = [&](int itm, int slot) {
+        if (itm < total) {
+            const int a = itm / G;
+            const int g = itm - a * G;
+            const int pk = __ldg(list + a);
+            uint32_t *dst = ring + slot * St::WORDS;
+            const uint32_t *gmsg = msg + (size_t)pk * d.E * 32;
+            const uint32_t *gmu = mu + (size_t)pk * d.N * St::MUW;
+            const int grp = lane >> 3, sub = lane & 7;
+            for (int s0 = 0; s0 < NSEG; s0 += 4) {
+                const int s = s0 + grp;
+                if (s < kNV * MU_SEGS) {
+                    const int i = s / MU_SEGS, h = s - i * MU_SEGS;
+                    const int n = g * kNV + i;
+                    if (n < d.N)
+                        cp_async16(dst + St::MU + i * St::MUW + h * 32 + sub * 4,
+                                   gmu + (size_t)n * St::MUW + h * 32 + sub * 4);
+                } else if (s < NSEG) {
+                    const int t = s - kNV * MU_SEGS;
+                    const int i = t / JMAX, jj = t - i * JMAX;
+                    const int n = g * kNV + i;
+                    if (n < d.N && jj < d.J) {
+                        const int l = n / d.p, k = n - l * d.p;
+                        const int sh = s_sh[jj * d.L + l];
+                        if (sh >= 0)
+                            cp_async16(dst + St::AL + (i * JMAX + jj) * 32 + sub * 4,
+                                       gmsg + (size_t)(s_eo[jj * d.L + l] + k) * 32 + sub * 4);
+                    }
+                }
+            }
+            if (lane < kNV * V) {
+                const int i = lane / V, v = lane - i * V;
+                const int n = g * kNV + i;
+                if (n < d.N) cp_async4(dst + St::HW + lane, hw + ((size_t)pk * d.N + n) * V + v);
+            } else if (lane >= 32 - 2 * V) {
+                const int q = lane - (32 - 2 * V);  // 0..2V-1: done[V], unsat[par][V]
+                const int off = q < V ? q : (1 + par) * V + (q - V);
+                cp_async4(dst + St::FL + q, flags + (size_t)pk * 5 * V + off);
+            }
+        }
+        cp_async_commit();
+    };
+
+#pragma unroll
+    for (int s = 0; s < kStages - 1; ++s) issue(item + s * GW, s);
+    int slot = 0;
+    for (; item < total; item += GW) {
+        issue(item + (kStages - 1) * GW, (slot + kStages - 1) % kStages);
+        cp_async_wait<kStages - 1>();
+        __syncwarp();
+        const uint32_t *S = ring + slot * St::WORDS;
+        const int a = item / G;
+        const int g = item - a * G;
+        const int pk = __ldg(list + a);
+        uint32_t *gmsg = msg + (size_t)pk * d.E * 32 + lane;
+        // frames stopped so far, and the ones whose last decisions satisfied every check
+        uint32_t frozen[V];
+        bool lane_on = false;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            uint32_t dn = S[St::FL + v];
+            if (STOP) {
+                const uint32_t newly = ~dn & ~S[St::FL + V + v];
+                if (g == 0 && lane == 0) {
+                    uint32_t *F = flags + (size_t)pk * 5 * V;
+                    if (newly) {
+                        F[v] = dn | newly;
+                        for (uint32_t b = newly; b; b &= b - 1) {
+                            const int ln = __ffs(b) - 1;
+                            iters[(size_t)pk * W + ln * V + v] = it - 1;
+                        }
+                    }
+                    F[(1 + (par ^ 1)) * V + v] = 0u;  // cleared for the next check pass
+                }
+                dn |= newly;
+            }
+            frozen[v] = dn;
+            lane_on |= ((~dn) >> lane) & 1u;
+        }
+#pragma unroll
+        for (int i = 0; i < kNV; ++i) {
+            const int n = g * kNV + i;
+            if (n >= d.N) break;  // warp-uniform
+            const int l = n / d.p, k = n - l * d.p;
+            uint32_t outb[V];
+            if constexpr (!MS) {
+                float m[V], aj[JMAX][V], tot[V];
+                const float *mf = reinterpret_cast<const float *>(S + St::MU + i * St::MUW) + lane * V;
+#pragma unroll
+                for (int v = 0; v < V; ++v) m[v] = mf[v], tot[v] = mf[v];
+#pragma unroll
+                for (int jj = 0; jj < JMAX; ++jj) {
+                    const bool on = jj < d.J && s_sh[jj * d.L + l] >= 0;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) aj[jj][v] = 0.0f;
+                    if (on) {
+                        Lane<V>::unpack(S[St::AL + (i * JMAX + jj) * 32 + lane], aj[jj]);
+#pragma unroll
+                        for (int v = 0; v < V; ++v) tot[v] += aj[jj][v];
+                    }
+                }
+                if (lane_on) {
+#pragma unroll
+                    for (int jj = 0; jj < JMAX; ++jj) {
+                        const int sh = jj < d.J ? s_sh[jj * d.L + l] : -1;
+                        if (sh < 0) continue;
+                        float b[V];
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            float s = m[v];
+#pragma unroll
+                            for (int j2 = 0; j2 < JMAX; ++j2)
+                                if (j2 != jj) s += aj[j2][v];
+                            b[v] = clipf(s, clip);
+                            if (XF) {
+                                // the check pass sums phi(|beta|): evaluate it here, from the unrounded beta
+                                const float f = phi_f(fabsf(b[v]));
+                                b[v] = b[v] < 0.0f ? -f : f;
+                            }
+                        }
+                        gmsg[(size_t)(s_eo[jj * d.L + l] + k) * 32] = Lane<V>::pack(b);
+                    }
+                }
+                float pst[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) pst[v] = clipf(tot[v], clip);
+                if (POST && lane_on) {
+                    float *dst = post + ((size_t)pk * d.N + n) * W + lane * V;
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        if (!((frozen[v] >> lane) & 1u)) dst[v] = pst[v];
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v) outb[v] = __ballot_sync(0xffffffffu, pst[v] < 0.0f);
+            } else {
+                const uint32_t qw = S[St::MU + i * St::MUW + lane];
+                uint32_t aw[JMAX];
+                int tot[4];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) tot[v] = sbyte(qw, v);
+#pragma unroll
+                for (int jj = 0; jj < JMAX; ++jj) {
+                    const bool on = jj < d.J && s_sh[jj * d.L + l] >= 0;
+                    aw[jj] = on ? S[St::AL + (i * JMAX + jj) * 32 + lane] : 0u;
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) tot[v] += sbyte(aw[jj], v);
+                }
+                if (lane_on) {
+#pragma unroll
+                    for (int jj = 0; jj < JMAX; ++jj) {
+                        const int sh = jj < d.J ? s_sh[jj * d.L + l] : -1;
+                        if (sh < 0) continue;
+                        uint32_t o = 0u;
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            int b = tot[v] - sbyte(aw[jj], v);
+                            b = b > 127 ? 127 : (b < -127 ? -127 : b);
+                            o |= ((uint32_t)(uint8_t)(int8_t)b) << (8 * v);
+                        }
+                        gmsg[(size_t)(s_eo[jj * d.L + l] + k) * 32] = o;
+                    }
+                }
+                if (POST && lane_on) {
+                    float *dst = post + ((size_t)pk * d.N + n) * W + lane * V;
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        if (!((frozen[v] >> lane) & 1u)) dst[v] = (float)tot[v] * lsb;
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v) outb[v] = __ballot_sync(0xffffffffu, tot[v] < 0);
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const uint32_t old = S[St::HW + i * V + v];
+                    hw[((size_t)pk * d.N + n) * V + v] = (outb[v] & ~frozen[v]) | (old & frozen[v]);
+                }
+            }
+        }
+        __syncwarp();
+        slot = (slot + 1) % kStages;
+    }
+    cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
+// list of packages with at least one frame still running: act[0] = count,
+// act[1..] = package indices (one block)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) compact_kernel(const uint32_t *__restrict__ flags, int P, int V,
+                                                       int *__restrict__ act) {
+    __shared__ int wsum[32];
+    __shared__ int s_base;
+    if (threadIdx.x == 0) s_base = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int p0 = 0; p0 < P; p0 += blockDim.x) {
+        const int pk = p0 + threadIdx.x;
+        bool on = false;
+        if (pk < P)
+            for (int v = 0; v < V; ++v) on |= ~flags[(size_t)pk * 5 * V + v] != 0u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, on);
+        if (lane == 0) wsum[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, all = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            if (w < warp) before += wsum[w];
+            all += wsum[w];
+        }
+        const int base = s_base;
+        if (on) act[1 + base + before + __popc(bal & ((1u << lane) - 1u))] = pk;
+        __syncthreads();
+        if (threadIdx.x == 0) s_base = base + all;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) act[0] = s_base;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_occ_mu;
+std::unordered_map<const void *, int> g_occ;  // kernel -> resident blocks per SM
+int g_sms = 0;
+
+template <typename K>
+int persistent_blocks(K kernel, size_t smem) {
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    const void *key = (const void *)kernel;
+    auto f = g_occ.find(key);
+    if (f != g_occ.end()) return f->second * g_sms;
+    if (!g_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sms <= 0) g_sms = 1;
+    }
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int bps = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, kWarps * 32, smem);
+    if (bps < 1) bps = 1;
+    g_occ[key] = bps;
+    return bps * g_sms;
+}
+}  // namespace
+
+template <int DCMAX, int V, bool SYN, bool XF, bool MS>
+static void launch_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int par, cudaStream_t s) {
+    auto k = cn_pipe_kernel<DCMAX, V, SYN, XF, MS>;
+    const size_t smem = (size_t)kWarps * kStages * CnStage<DCMAX, V, SYN>::WORDS * 4;
+    const int blocks = persistent_blocks(k, smem);
+    k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, c->ws.hw, c->ws.flags, c->ws.act, o.clip, par);
+}
+
+template <int DCMAX>
+static void cn_pipe_dispatch(ldpc_code c, const ldpc_decode_opts &o, bool syn, int par, cudaStream_t s) {
+    if (o.algo == LDPC_ALGO_MS) {
+        if (syn) launch_cn_pipe<DCMAX, 4, true, false, true>(c, o, par, s);
+        else launch_cn_pipe<DCMAX, 4, false, false, true>(c, o, par, s);
+    } else if (o.msg == LDPC_MSG_F16) {
+        if (syn) launch_cn_pipe<DCMAX, 2, true, false, false>(c, o, par, s);
+        else launch_cn_pipe<DCMAX, 2, false, false, false>(c, o, par, s);
+    } else {
+        if (syn) launch_cn_pipe<DCMAX, 1, true, true, false>(c, o, par, s);
+        else launch_cn_pipe<DCMAX, 1, false, true, false>(c, o, par, s);
+    }
+}
+
+ldpc_status qc_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, bool syn, int par, cudaStream_t s) {
+    const int dcm = c->d.dc_max;
+    if (dcm <= 8) cn_pipe_dispatch<8>(c, o, syn, par, s);
+    else if (dcm <= 16) cn_pipe_dispatch<16>(c, o, syn, par, s);
+    else if (dcm <= 24) cn_pipe_dispatch<24>(c, o, syn, par, s);
+    else cn_pipe_dispatch<32>(c, o, syn, par, s);
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
+template <int JMAX, int V, bool STOP, bool POST, bool XF, bool MS>
+static void launch_vn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, int par, cudaStream_t s) {
+    auto k = vn_pipe_kernel<JMAX, V, STOP, POST, XF, MS>;
+    const size_t smem = (size_t)kWarps * kStages * VnStage<JMAX, V, STOP, MS>::WORDS * 4;
+    const int blocks = persistent_blocks(k, smem);
+    k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, (const uint32_t *)c->ws.mu, c->ws.hw,
+                                        c->ws.flags, c->ws.post, c->ws.iters, c->ws.act, o.clip,
+                                        ldexpf(1.0f, -o.frac_bits), it, par);
+}
+
+template <int JMAX, bool STOP, bool POST>
+static void vn_pipe_dispatch(ldpc_code c, const ldpc_decode_opts &o, int it, int par, cudaStream_t s) {
+    if (o.algo == LDPC_ALGO_MS) launch_vn_pipe<JMAX, 4, STOP, POST, false, true>(c, o, it, par, s);
+    else if (o.msg == LDPC_MSG_F16) launch_vn_pipe<JMAX, 2, STOP, POST, false, false>(c, o, it, par, s);
+    else launch_vn_pipe<JMAX, 1, STOP, POST, true, false>(c, o, it, par, s);
+}
+
+ldpc_status qc_vn_pipe(ldpc_code c, const ldpc_decode_opts &o, bool stop, bool post, int it, int par,
+                       cudaStream_t s) {
+    if (c->d.J <= 4) {
+        if (stop) post ? vn_pipe_dispatch<4, true, true>(c, o, it, par, s) : vn_pipe_dispatch<4, true, false>(c, o, it, par, s);
+        else post ? vn_pipe_dispatch<4, false, true>(c, o, it, par, s) : vn_pipe_dispatch<4, false, false>(c, o, it, par, s);
+    } else {
+        if (stop) post ? vn_pipe_dispatch<8, true, true>(c, o, it, par, s) : vn_pipe_dispatch<8, true, false>(c, o, it, par, s);
+        else post ? vn_pipe_dispatch<8, false, true>(c, o, it, par, s) : vn_pipe_dispatch<8, false, false>(c, o, it, par, s);
+    }
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
+ldpc_status qc_compact(ldpc_code c, int P, int V, cudaStream_t s) {
+    compact_kernel<<<1, 1024, 0, s>>>(c->ws.flags, P, V, c->ws.act);
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
+}  // namespace ldpc
