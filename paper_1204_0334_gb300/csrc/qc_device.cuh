@@ -45,9 +45,8 @@ __device__ __forceinline__ float lg2_approx(float a) {
     return r;
 }
 
-__device__ __forceinline__ float phi_f(float x) {
+__device__ __forceinline__ float phi_hi(float x) {  // x >= 1 (and +inf)
     x = fminf(x, 100.0f);  // e^-100 flushes to 0; keeps inf - inf out of the error term
-    // x >= 1: t = e^-x from exp2 of the split product -x*log2(e)
     const float L2E = 1.44269502f, L2E_LO = 1.92596299e-8f, LN2 = 0.693147182f;
     const float a = -x * L2E;
     float alo = fmaf(-x, L2E, -a);
@@ -57,13 +56,31 @@ __device__ __forceinline__ float phi_f(float x) {
     const float v = t * t;
     const float w = 2.0f * t;
     const float sv = v * fmaf(fmaf(fmaf(0.147845685f, v, 0.138392285f), v, 0.200207084f), v, 0.333330393f);
-    const float phiA = fmaf(w, sv, w);
-    // x < 1: -ln(y) with y = x/2 < 1/2, where the log2 approximation is relative-accurate
+    return fmaf(w, sv, w);
+}
+
+__device__ __forceinline__ float phi_lo(float x) {  // 0 <= x < 1
+    const float LN2 = 0.693147182f;
     const float y = 0.5f * x;
     const float u = y * y;
     const float G = u * fmaf(fmaf(fmaf(-0.00555368373f, u, 0.0216362253f), u, -0.0777590200f), u, 0.333332866f);
-    const float phiB = fmaf(lg2_approx(y), -LN2, G);
-    return x < 1.0f ? phiB : phiA;
+    return fmaf(lg2_approx(y), -LN2, G);
+}
+
+// any lanes, no warp-level assumptions
+__device__ __forceinline__ float phi_f(float x) {
+    const float hi = phi_hi(x), lo = phi_lo(x);
+    return x < 1.0f ? lo : hi;
+}
+
+// same values; must be called by all 32 lanes together: when the whole warp
+// is in one regime (the usual case) only that regime is evaluated
+__device__ __forceinline__ float phi_warp(float x) {
+    const bool lo = x < 1.0f;
+    const unsigned b = __ballot_sync(0xffffffffu, lo);
+    if (b == 0u) return phi_hi(x);
+    if (b == 0xffffffffu) return phi_lo(x);
+    return lo ? phi_lo(x) : phi_hi(x);
 }
 
 __device__ __forceinline__ float clipf(float x, float c) { return fminf(fmaxf(x, -c), c); }

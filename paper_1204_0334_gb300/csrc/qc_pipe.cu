@@ -38,15 +38,17 @@ __device__ __forceinline__ void cp_async_wait() {
 template <int DCMAX, int V, bool SYN>
 struct CnStage {
     static constexpr int SEG = DCMAX * 32;          // edge packages, [l][32 words]
-    static constexpr int HW = SYN ? DCMAX * V : 0;  // hard-decision words of the row's variables
-    static constexpr int FL = SEG + HW;             // done words
+    static constexpr int OFF = SEG;                 // [l]: package offset of the edge in words / 32, or -1
+    static constexpr int HW = OFF + DCMAX;          // hard-decision words of the row's variables
+    static constexpr int FL = HW + (SYN ? DCMAX * V : 0);  // done words
     static constexpr int WORDS = (FL + V + 3) & ~3;
 };
 
 // ---------------------------------------------------------------------------
-// check pass (iterations >= 2): sum-product (MS = false) or integer min-sum
+// check pass (iterations >= 2): sum-product (MS = false) or integer min-sum.
+// REG: every block of the row is present and L == DCMAX (regular QC code).
 // ---------------------------------------------------------------------------
-template <int DCMAX, int V, bool SYN, bool XF, bool MS>
+template <int DCMAX, int V, bool SYN, bool XF, bool MS, bool REG>
 __global__ void __launch_bounds__(kWarps * 32)
 cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__restrict__ hw,
                uint32_t *__restrict__ flags, const int *__restrict__ act, float clip, int par) {
@@ -74,29 +76,29 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
             const int j = m / d.p, r = m - j * d.p;
             const uint32_t *gmsg = msg + (size_t)pk * d.E * 32;
             uint32_t *dst = ring + slot * St::WORDS;
+            int *off = reinterpret_cast<int *>(dst + St::OFF);
             const int g = lane >> 3, sub = lane & 7;
 #pragma unroll
             for (int q = 0; q < DCMAX / 4; ++q) {
                 const int l = 4 * q + g;
-                if (l < d.L) {
-                    const int sh = s_sh[j * d.L + l];
-                    if (sh >= 0) {
-                        int k = r + sh;
-                        if (k >= d.p) k -= d.p;
-                        cp_async16(dst + l * 32 + sub * 4, gmsg + (size_t)(s_eo[j * d.L + l] + k) * 32 + sub * 4);
-                    }
+                const int sh = (REG || l < d.L) ? s_sh[j * d.L + l] : -1;
+                int o = -1;
+                if (REG || sh >= 0) {
+                    int k = r + sh;
+                    if (k >= d.p) k -= d.p;
+                    o = s_eo[j * d.L + l] + k;
+                    cp_async16(dst + l * 32 + sub * 4, gmsg + (size_t)o * 32 + sub * 4);
                 }
+                if (sub == 0) off[l] = o;
             }
             if (SYN) {
                 for (int w = lane; w < DCMAX * V; w += 32) {
                     const int l = w / V, v = w - l * V;
-                    if (l < d.L) {
-                        const int sh = s_sh[j * d.L + l];
-                        if (sh >= 0) {
-                            int k = r + sh;
-                            if (k >= d.p) k -= d.p;
-                            cp_async4(dst + St::SEG + w, hw + ((size_t)pk * d.N + (size_t)l * d.p + k) * V + v);
-                        }
+                    const int sh = (REG || l < d.L) ? s_sh[j * d.L + l] : -1;
+                    if (REG || sh >= 0) {
+                        int k = r + sh;
+                        if (k >= d.p) k -= d.p;
+                        cp_async4(dst + St::HW + w, hw + ((size_t)pk * d.N + (size_t)l * d.p + k) * V + v);
                     }
                 }
             }
@@ -113,10 +115,8 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
         cp_async_wait<kStages - 1>();
         __syncwarp();
         const uint32_t *S = ring + slot * St::WORDS;
-        const int a = item / d.M;
-        const int m = item - a * d.M;
-        const int pk = __ldg(list + a);
-        const int j = m / d.p, r = m - j * d.p;
+        const int *off = reinterpret_cast<const int *>(S + St::OFF);
+        const int pk = __ldg(list + item / d.M);
         uint32_t *gmsg = msg + (size_t)pk * d.E * 32 + lane;
         uint32_t actv[V];
         bool lane_on = false;
@@ -135,17 +135,16 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
             for (int v = 0; v < V; ++v) neg[v] = 0u;
 #pragma unroll
             for (int l = 0; l < DCMAX; ++l) {
-                const bool on = l < d.L && s_sh[j * d.L + l] >= 0;
 #pragma unroll
                 for (int v = 0; v < V; ++v) ph[l][v] = 0.0f;
-                if (on) {
+                if (REG || off[l] >= 0) {
                     float x[V];
                     Lane<V>::unpack(S[l * 32 + lane], x);
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
-                        ph[l][v] = XF ? fabsf(x[v]) : phi_f(fabsf(x[v]));
+                        ph[l][v] = XF ? fabsf(x[v]) : phi_warp(fabsf(x[v]));
                         neg[v] |= (x[v] < 0.0f ? 1u : 0u) << l;
-                        if (SYN) syn[v] ^= S[St::SEG + l * V + v];
+                        if (SYN) syn[v] ^= S[St::HW + l * V + v];
                     }
                 }
             }
@@ -168,17 +167,15 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
             for (int v = 0; v < V; ++v) par_all[v] = __popc(neg[v]) & 1u, suf[v] = 0.0f;
 #pragma unroll
             for (int l = DCMAX - 1; l >= 0; --l) {
-                const int sh = l < d.L ? s_sh[j * d.L + l] : -1;
-                if (sh >= 0) {
-                    int k = r + sh;
-                    if (k >= d.p) k -= d.p;
+                const int o = off[l];
+                if (REG || o >= 0) {
                     float out[V];
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
-                        const float mag = fminf(phi_f(pre[l][v] + suf[v]), clip);
+                        const float mag = fminf(phi_warp(pre[l][v] + suf[v]), clip);
                         out[v] = (par_all[v] ^ ((neg[v] >> l) & 1u)) ? -mag : mag;
                     }
-                    if (lane_on) gmsg[(size_t)(s_eo[j * d.L + l] + k) * 32] = Lane<V>::pack(out);
+                    if (lane_on) gmsg[(size_t)o * 32] = Lane<V>::pack(out);
                 }
 #pragma unroll
                 for (int v = 0; v < V; ++v) suf[v] += ph[l][v];
@@ -189,10 +186,9 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
             uint32_t min1 = 0x7f7f7f7fu, min2 = 0x7f7f7f7fu, sgn = 0u;
 #pragma unroll
             for (int l = 0; l < DCMAX; ++l) {
-                const bool on = l < d.L && s_sh[j * d.L + l] >= 0;
                 ab[l] = 0u;
                 sg[l] = 0u;
-                if (on) {
+                if (REG || off[l] >= 0) {
                     const uint32_t x = S[l * 32 + lane];
                     const uint32_t av = __vabsss4(x);
                     sg[l] = x & 0x80808080u;
@@ -202,21 +198,19 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
                     min1 = __vminu4(min1, av);
                     if (SYN) {
 #pragma unroll
-                        for (int v = 0; v < V; ++v) syn[v] ^= S[St::SEG + l * V + v];
+                        for (int v = 0; v < V; ++v) syn[v] ^= S[St::HW + l * V + v];
                     }
                 }
             }
             if (lane_on) {
 #pragma unroll
                 for (int l = 0; l < DCMAX; ++l) {
-                    const int sh = l < d.L ? s_sh[j * d.L + l] : -1;
-                    if (sh < 0) continue;
-                    int k = r + sh;
-                    if (k >= d.p) k -= d.p;
+                    const int o = off[l];
+                    if (!REG && o < 0) continue;
                     const uint32_t eq = __vcmpeq4(ab[l], min1);
                     const uint32_t mag = (min2 & eq) | (min1 & ~eq);
                     const uint32_t sneg = ((sgn ^ sg[l]) >> 7) & 0x01010101u;
-                    gmsg[(size_t)(s_eo[j * d.L + l] + k) * 32] = __vadd4(mag ^ (sneg * 0xffu), sneg);
+                    gmsg[(size_t)o * 32] = __vadd4(mag ^ (sneg * 0xffu), sneg);
                 }
             }
         }
@@ -234,7 +228,8 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
 }
 
 // ---------------------------------------------------------------------------
-// variable pass: eqs. (bpvs), (bpd), (hrddcs) on kNV consecutive variables
+// variable pass: eqs. (bpvs), (bpd), (hrddcs) on kNV consecutive variables.
+// REG: every block of the column is present and J == JMAX.
 // ---------------------------------------------------------------------------
 template <int JMAX, int V, bool STOP, bool MS>
 struct VnStage {
@@ -246,7 +241,7 @@ struct VnStage {
     static constexpr int WORDS = (FL + 2 * V + 3) & ~3;
 };
 
-template <int JMAX, int V, bool STOP, bool POST, bool XF, bool MS>
+template <int JMAX, int V, bool STOP, bool POST, bool XF, bool MS, bool REG>
 __global__ void __launch_bounds__(kWarps * 32)
 vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__restrict__ mu, uint32_t *__restrict__ hw,
                uint32_t *__restrict__ flags, float *__restrict__ post, int32_t *__restrict__ iters,
@@ -278,23 +273,27 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
             uint32_t *dst = ring + slot * St::WORDS;
             const uint32_t *gmsg = msg + (size_t)pk * d.E * 32;
             const uint32_t *gmu = mu + (size_t)pk * d.N * St::MUW;
+            const int n0 = g * kNV;
+            const int l0 = n0 / d.p, k0 = n0 - l0 * d.p;
             const int grp = lane >> 3, sub = lane & 7;
+#pragma unroll
             for (int s0 = 0; s0 < NSEG; s0 += 4) {
                 const int s = s0 + grp;
                 if (s < kNV * MU_SEGS) {
                     const int i = s / MU_SEGS, h = s - i * MU_SEGS;
-                    const int n = g * kNV + i;
+                    const int n = n0 + i;
                     if (n < d.N)
                         cp_async16(dst + St::MU + i * St::MUW + h * 32 + sub * 4,
                                    gmu + (size_t)n * St::MUW + h * 32 + sub * 4);
                 } else if (s < NSEG) {
                     const int t = s - kNV * MU_SEGS;
                     const int i = t / JMAX, jj = t - i * JMAX;
-                    const int n = g * kNV + i;
-                    if (n < d.N && jj < d.J) {
-                        const int l = n / d.p, k = n - l * d.p;
+                    const int n = n0 + i;
+                    int l = l0, k = k0 + i;
+                    if (k >= d.p) k -= d.p, ++l;
+                    if (n < d.N && (REG || jj < d.J)) {
                         const int sh = s_sh[jj * d.L + l];
-                        if (sh >= 0)
+                        if (REG || sh >= 0)
                             cp_async16(dst + St::AL + (i * JMAX + jj) * 32 + sub * 4,
                                        gmsg + (size_t)(s_eo[jj * d.L + l] + k) * 32 + sub * 4);
                     }
@@ -302,7 +301,7 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
             }
             if (lane < kNV * V) {
                 const int i = lane / V, v = lane - i * V;
-                const int n = g * kNV + i;
+                const int n = n0 + i;
                 if (n < d.N) cp_async4(dst + St::HW + lane, hw + ((size_t)pk * d.N + n) * V + v);
             } else if (lane >= 32 - 2 * V) {
                 const int q = lane - (32 - 2 * V);  // 0..2V-1: done[V], unsat[par][V]
@@ -349,11 +348,13 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
             frozen[v] = dn;
             lane_on |= ((~dn) >> lane) & 1u;
         }
+        const int n0 = g * kNV;
+        int l = n0 / d.p, k = n0 - l * d.p;
 #pragma unroll
-        for (int i = 0; i < kNV; ++i) {
-            const int n = g * kNV + i;
+        for (int i = 0; i < kNV; ++i, ++k) {
+            if (k >= d.p) k -= d.p, ++l;
+            const int n = n0 + i;
             if (n >= d.N) break;  // warp-uniform
-            const int l = n / d.p, k = n - l * d.p;
             uint32_t outb[V];
             if constexpr (!MS) {
                 float m[V], aj[JMAX][V], tot[V];
@@ -362,7 +363,7 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
                 for (int v = 0; v < V; ++v) m[v] = mf[v], tot[v] = mf[v];
 #pragma unroll
                 for (int jj = 0; jj < JMAX; ++jj) {
-                    const bool on = jj < d.J && s_sh[jj * d.L + l] >= 0;
+                    const bool on = REG || (jj < d.J && s_sh[jj * d.L + l] >= 0);
 #pragma unroll
                     for (int v = 0; v < V; ++v) aj[jj][v] = 0.0f;
                     if (on) {
@@ -371,27 +372,25 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
                         for (int v = 0; v < V; ++v) tot[v] += aj[jj][v];
                     }
                 }
-                if (lane_on) {
 #pragma unroll
-                    for (int jj = 0; jj < JMAX; ++jj) {
-                        const int sh = jj < d.J ? s_sh[jj * d.L + l] : -1;
-                        if (sh < 0) continue;
-                        float b[V];
+                for (int jj = 0; jj < JMAX; ++jj) {
+                    const int sh = (REG || jj < d.J) ? s_sh[jj * d.L + l] : -1;
+                    if (!REG && sh < 0) continue;  // warp-uniform
+                    float b[V];
 #pragma unroll
-                        for (int v = 0; v < V; ++v) {
-                            float s = m[v];
+                    for (int v = 0; v < V; ++v) {
+                        float s = m[v];
 #pragma unroll
-                            for (int j2 = 0; j2 < JMAX; ++j2)
-                                if (j2 != jj) s += aj[j2][v];
-                            b[v] = clipf(s, clip);
-                            if (XF) {
-                                // the check pass sums phi(|beta|): evaluate it here, from the unrounded beta
-                                const float f = phi_f(fabsf(b[v]));
-                                b[v] = b[v] < 0.0f ? -f : f;
-                            }
+                        for (int j2 = 0; j2 < JMAX; ++j2)
+                            if (j2 != jj) s += aj[j2][v];
+                        b[v] = clipf(s, clip);
+                        if (XF) {
+                            // the check pass sums phi(|beta|): evaluate it here, from the unrounded beta
+                            const float f = phi_warp(fabsf(b[v]));
+                            b[v] = b[v] < 0.0f ? -f : f;
                         }
-                        gmsg[(size_t)(s_eo[jj * d.L + l] + k) * 32] = Lane<V>::pack(b);
                     }
+                    if (lane_on) gmsg[(size_t)(s_eo[jj * d.L + l] + k) * 32] = Lane<V>::pack(b);
                 }
                 float pst[V];
 #pragma unroll
@@ -412,7 +411,7 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
                 for (int v = 0; v < 4; ++v) tot[v] = sbyte(qw, v);
 #pragma unroll
                 for (int jj = 0; jj < JMAX; ++jj) {
-                    const bool on = jj < d.J && s_sh[jj * d.L + l] >= 0;
+                    const bool on = REG || (jj < d.J && s_sh[jj * d.L + l] >= 0);
                     aw[jj] = on ? S[St::AL + (i * JMAX + jj) * 32 + lane] : 0u;
 #pragma unroll
                     for (int v = 0; v < 4; ++v) tot[v] += sbyte(aw[jj], v);
@@ -420,8 +419,8 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
                 if (lane_on) {
 #pragma unroll
                     for (int jj = 0; jj < JMAX; ++jj) {
-                        const int sh = jj < d.J ? s_sh[jj * d.L + l] : -1;
-                        if (sh < 0) continue;
+                        const int sh = (REG || jj < d.J) ? s_sh[jj * d.L + l] : -1;
+                        if (!REG && sh < 0) continue;
                         uint32_t o = 0u;
 #pragma unroll
                         for (int v = 0; v < 4; ++v) {
@@ -517,41 +516,51 @@ int persistent_blocks(K kernel, size_t smem) {
 }
 }  // namespace
 
-template <int DCMAX, int V, bool SYN, bool XF, bool MS>
+template <int DCMAX, int V, bool SYN, bool XF, bool MS, bool REG>
 static void launch_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int par, cudaStream_t s) {
-    auto k = cn_pipe_kernel<DCMAX, V, SYN, XF, MS>;
+    auto k = cn_pipe_kernel<DCMAX, V, SYN, XF, MS, REG>;
     const size_t smem = (size_t)kWarps * kStages * CnStage<DCMAX, V, SYN>::WORDS * 4;
     const int blocks = persistent_blocks(k, smem);
     k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, c->ws.hw, c->ws.flags, c->ws.act, o.clip, par);
 }
 
-template <int DCMAX>
+template <int DCMAX, bool REG>
 static void cn_pipe_dispatch(ldpc_code c, const ldpc_decode_opts &o, bool syn, int par, cudaStream_t s) {
     if (o.algo == LDPC_ALGO_MS) {
-        if (syn) launch_cn_pipe<DCMAX, 4, true, false, true>(c, o, par, s);
-        else launch_cn_pipe<DCMAX, 4, false, false, true>(c, o, par, s);
+        if (syn) launch_cn_pipe<DCMAX, 4, true, false, true, REG>(c, o, par, s);
+        else launch_cn_pipe<DCMAX, 4, false, false, true, REG>(c, o, par, s);
     } else if (o.msg == LDPC_MSG_F16) {
-        if (syn) launch_cn_pipe<DCMAX, 2, true, false, false>(c, o, par, s);
-        else launch_cn_pipe<DCMAX, 2, false, false, false>(c, o, par, s);
+        if (syn) launch_cn_pipe<DCMAX, 2, true, false, false, REG>(c, o, par, s);
+        else launch_cn_pipe<DCMAX, 2, false, false, false, REG>(c, o, par, s);
     } else {
-        if (syn) launch_cn_pipe<DCMAX, 1, true, true, false>(c, o, par, s);
-        else launch_cn_pipe<DCMAX, 1, false, true, false>(c, o, par, s);
+        if (syn) launch_cn_pipe<DCMAX, 1, true, true, false, REG>(c, o, par, s);
+        else launch_cn_pipe<DCMAX, 1, false, true, false, REG>(c, o, par, s);
     }
 }
 
+// a regular code whose row degree is exactly one of the compiled degrees
+static bool regular_rows(const QcDesc &d, int dcmax) {
+    if (d.L != dcmax) return false;
+    for (int i = 0; i < d.J * d.L; ++i)
+        if (d.shift[i] < 0) return false;
+    return true;
+}
+
 ldpc_status qc_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, bool syn, int par, cudaStream_t s) {
-    const int dcm = c->d.dc_max;
-    if (dcm <= 8) cn_pipe_dispatch<8>(c, o, syn, par, s);
-    else if (dcm <= 16) cn_pipe_dispatch<16>(c, o, syn, par, s);
-    else if (dcm <= 24) cn_pipe_dispatch<24>(c, o, syn, par, s);
-    else cn_pipe_dispatch<32>(c, o, syn, par, s);
+    const QcDesc &d = c->d;
+    if (regular_rows(d, 24)) cn_pipe_dispatch<24, true>(c, o, syn, par, s);
+    else if (regular_rows(d, 6)) cn_pipe_dispatch<8, false>(c, o, syn, par, s);
+    else if (d.L <= 8) cn_pipe_dispatch<8, false>(c, o, syn, par, s);
+    else if (d.L <= 16) cn_pipe_dispatch<16, false>(c, o, syn, par, s);
+    else if (d.L <= 24) cn_pipe_dispatch<24, false>(c, o, syn, par, s);
+    else cn_pipe_dispatch<32, false>(c, o, syn, par, s);
     LDPC_CUDA_TRY(cudaGetLastError());
     return LDPC_OK;
 }
 
-template <int JMAX, int V, bool STOP, bool POST, bool XF, bool MS>
+template <int JMAX, int V, bool STOP, bool POST, bool XF, bool MS, bool REG>
 static void launch_vn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, int par, cudaStream_t s) {
-    auto k = vn_pipe_kernel<JMAX, V, STOP, POST, XF, MS>;
+    auto k = vn_pipe_kernel<JMAX, V, STOP, POST, XF, MS, REG>;
     const size_t smem = (size_t)kWarps * kStages * VnStage<JMAX, V, STOP, MS>::WORDS * 4;
     const int blocks = persistent_blocks(k, smem);
     k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, (const uint32_t *)c->ws.mu, c->ws.hw,
@@ -559,22 +568,34 @@ static void launch_vn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, int p
                                         ldexpf(1.0f, -o.frac_bits), it, par);
 }
 
-template <int JMAX, bool STOP, bool POST>
+template <int JMAX, bool STOP, bool POST, bool REG>
 static void vn_pipe_dispatch(ldpc_code c, const ldpc_decode_opts &o, int it, int par, cudaStream_t s) {
-    if (o.algo == LDPC_ALGO_MS) launch_vn_pipe<JMAX, 4, STOP, POST, false, true>(c, o, it, par, s);
-    else if (o.msg == LDPC_MSG_F16) launch_vn_pipe<JMAX, 2, STOP, POST, false, false>(c, o, it, par, s);
-    else launch_vn_pipe<JMAX, 1, STOP, POST, true, false>(c, o, it, par, s);
+    if (o.algo == LDPC_ALGO_MS) launch_vn_pipe<JMAX, 4, STOP, POST, false, true, REG>(c, o, it, par, s);
+    else if (o.msg == LDPC_MSG_F16) launch_vn_pipe<JMAX, 2, STOP, POST, false, false, REG>(c, o, it, par, s);
+    else launch_vn_pipe<JMAX, 1, STOP, POST, true, false, REG>(c, o, it, par, s);
+}
+
+template <int JMAX, bool REG>
+static void vn_pipe_dispatch2(ldpc_code c, const ldpc_decode_opts &o, bool stop, bool post, int it, int par,
+                              cudaStream_t s) {
+    if (stop) {
+        if (post) vn_pipe_dispatch<JMAX, true, true, REG>(c, o, it, par, s);
+        else vn_pipe_dispatch<JMAX, true, false, REG>(c, o, it, par, s);
+    } else {
+        if (post) vn_pipe_dispatch<JMAX, false, true, REG>(c, o, it, par, s);
+        else vn_pipe_dispatch<JMAX, false, false, REG>(c, o, it, par, s);
+    }
 }
 
 ldpc_status qc_vn_pipe(ldpc_code c, const ldpc_decode_opts &o, bool stop, bool post, int it, int par,
                        cudaStream_t s) {
-    if (c->d.J <= 4) {
-        if (stop) post ? vn_pipe_dispatch<4, true, true>(c, o, it, par, s) : vn_pipe_dispatch<4, true, false>(c, o, it, par, s);
-        else post ? vn_pipe_dispatch<4, false, true>(c, o, it, par, s) : vn_pipe_dispatch<4, false, false>(c, o, it, par, s);
-    } else {
-        if (stop) post ? vn_pipe_dispatch<8, true, true>(c, o, it, par, s) : vn_pipe_dispatch<8, true, false>(c, o, it, par, s);
-        else post ? vn_pipe_dispatch<8, false, true>(c, o, it, par, s) : vn_pipe_dispatch<8, false, false>(c, o, it, par, s);
-    }
+    const QcDesc &d = c->d;
+    bool full = true;
+    for (int i = 0; i < d.J * d.L; ++i) full &= d.shift[i] >= 0;
+    if (full && d.J == 4) vn_pipe_dispatch2<4, true>(c, o, stop, post, it, par, s);
+    else if (full && d.J == 3) vn_pipe_dispatch2<3, true>(c, o, stop, post, it, par, s);
+    else if (d.J <= 4) vn_pipe_dispatch2<4, false>(c, o, stop, post, it, par, s);
+    else vn_pipe_dispatch2<8, false>(c, o, stop, post, it, par, s);
     LDPC_CUDA_TRY(cudaGetLastError());
     return LDPC_OK;
 }
