@@ -144,6 +144,44 @@ ldpc_status ldpc_ber_sim(ldpc_code code, double ebn0_db, uint64_t seed, uint64_t
                          ldpc_ber_result *out, void *stream);
 
 /*
+ * LDPC convolutional codes derived from a QC base (Sec. II-D): partition H_QC
+ * into Lambda x Lambda sub-blocks, Lambda = gcd(J, L), keep the lower part H^L
+ * and paste the strictly-upper part H^U below it, repeat down the diagonal.
+ * Frames carry c = (L/Lambda) p bits, check layers (J/Lambda) p checks, rate
+ * b/c with b = ((L-J)/Lambda) p, syndrome-former memory ms = Lambda - 1.
+ *
+ * ldpccc_create -- a pipelined decoder (Algorithm 2, Sec. II-E) with I
+ *   processors (one per iteration) for gamma independent code streams.  The
+ *   shifts follow ldpc_code_create (copied).  Device memory: a ring of
+ *   I*Lambda frames holding the channel LLRs and the J*c edge messages of each
+ *   frame for all streams (Sec. IV-B-1: I*E message units, E = J L p).
+ *   Lambda = 1 (gcd(J, L) = 1) is accepted: frames then decode independently
+ *   with I iterations.  Errors: LDPC_EINVAL, LDPC_ENOMEM.
+ */
+ldpc_status ldpccc_create(const int32_t *shifts, int32_t J, int32_t L, int32_t p, int32_t I, int32_t gamma,
+                          ldpccc *out);
+ldpc_status ldpccc_destroy(ldpccc cc);
+/* c, b, ms and Lambda of the derived code (any pointer may be NULL). */
+ldpc_status ldpccc_dims(ldpccc cc, int32_t *c, int32_t *b, int32_t *ms, int32_t *lambda);
+/* Empty the pipeline: the next window's first frame is frame 0 of every stream. */
+ldpc_status ldpccc_reset(ldpccc cc);
+/*
+ * ldpccc_decode_window -- T time slots of Algorithm 2: at each slot the next
+ * frame of every stream enters processor 1, the I check layers and then the I
+ * frames in the decoder are updated (eqs. ldpccc_bph, ldpccc_bpvs), and the
+ * frame leaving processor I is decided (eq. ldpccc_hrddcs).  Frame f is decided
+ * at slot f + I*Lambda - 1, so the first I*Lambda - 1 slots after a reset emit
+ * nothing; the decoder state carries over to the next call (continuous decoding).
+ *   llr:   [gamma][T][c] float channel LLRs of the T arriving frames (mu = 2y/sigma^2).
+ *   clip:  LLR clip (e.g. 30), applied to channel LLRs, messages and posteriors.
+ *   hard:  [gamma][T][c] uint8 or NULL: the decided frames, stream-major, frame q at [s][q][.].
+ *   post:  [gamma][T][c] float or NULL: their a-posteriori LLRs.
+ *   first_out: index of the first decided frame (or -1); n_out: number decided (host ints).
+ */
+ldpc_status ldpccc_decode_window(ldpccc cc, const float *llr, int32_t T, float clip, uint8_t *hard, float *post,
+                                 int64_t *first_out, int32_t *n_out, void *stream);
+
+/*
  * ldpc_phi_eval -- the check-node transform of the sum-product rule on its own:
  * phi(x) = -ln tanh(x/2) for x >= 0, with which eq. (bphs) reads
  * alpha = prod(sign) * phi(sum_{n' != n} phi(|beta_n'|)) (phi is its own inverse).

@@ -60,6 +60,12 @@ _SIGNATURES = [
     ("ldpc_channel", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, P, P]),
     ("ldpc_ber_sim", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
                                     ctypes.c_int64, ctypes.c_int32, P, P, P]),
+    ("ldpccc_create", ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_int32, P]),
+    ("ldpccc_destroy", ctypes.c_int, [P]),
+    ("ldpccc_dims", ctypes.c_int, [P, P, P, P, P]),
+    ("ldpccc_reset", ctypes.c_int, [P]),
+    ("ldpccc_decode_window", ctypes.c_int, [P, P, ctypes.c_int32, ctypes.c_float, P, P, P, P, P]),
     ("ldpc_phi_eval", ctypes.c_int, [P, P, ctypes.c_int64, ctypes.c_int32, P]),
     ("ldpc_profile_enable", ctypes.c_int, [ctypes.c_int32]),
     ("ldpc_profile_read", ctypes.c_int, [P]),
@@ -166,6 +172,71 @@ def ldpc_phi_eval(x, variant: int = 0, stream=None):
     y = torch.empty_like(x)
     _check(lib().ldpc_phi_eval(_ptr(x), _ptr(y), x.numel(), variant, _stream(stream)), "ldpc_phi_eval")
     return y
+
+
+def ldpccc_create(shifts, p: int, I: int, gamma: int) -> int:
+    import numpy as np
+
+    a = np.ascontiguousarray(np.asarray(shifts, dtype=np.int32))
+    J, L = a.shape
+    h = ctypes.c_void_p()
+    _check(lib().ldpccc_create(a.ctypes.data_as(P), J, L, p, I, gamma, ctypes.byref(h)), "ldpccc_create")
+    return h.value
+
+
+def ldpccc_destroy(cc: int):
+    _check(lib().ldpccc_destroy(cc), "ldpccc_destroy")
+
+
+def ldpccc_dims(cc: int) -> dict:
+    v = [ctypes.c_int32() for _ in range(4)]
+    _check(lib().ldpccc_dims(cc, *[ctypes.byref(x) for x in v]), "ldpccc_dims")
+    return dict(zip(["c", "b", "ms", "Lambda"], [x.value for x in v]))
+
+
+def ldpccc_reset(cc: int):
+    _check(lib().ldpccc_reset(cc), "ldpccc_reset")
+
+
+def ldpccc_decode_window(cc: int, llr, clip: float = 30.0, hard=None, post=None, stream=None):
+    """llr: [gamma][T][c] float32.  Returns (first decided frame or -1, number decided)."""
+    first = ctypes.c_int64()
+    n = ctypes.c_int32()
+    T = llr.shape[1]
+    _check(lib().ldpccc_decode_window(cc, _ptr(llr), T, clip, _ptr(hard), _ptr(post), ctypes.byref(first),
+                                      ctypes.byref(n), _stream(stream)), "ldpccc_decode_window")
+    return first.value, n.value
+
+
+class LDPCCC:
+    """Owning wrapper of an ldpccc handle."""
+
+    def __init__(self, shifts, p: int, I: int, gamma: int):
+        self.handle = ldpccc_create(shifts, p, I, gamma)
+        d = ldpccc_dims(self.handle)
+        self.c, self.b, self.ms, self.Lambda = d["c"], d["b"], d["ms"], d["Lambda"]
+        self.I, self.gamma = I, gamma
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ldpccc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def window(self, llr, clip=30.0, want_post=True, stream=None):
+        """llr: [gamma][T][c] tensor on the device.  Returns (first, n, hard[:, :n], post[:, :n])."""
+        import torch
+
+        g, T, c = llr.shape
+        hard = torch.empty((g, T, c), dtype=torch.uint8, device=llr.device)
+        post = torch.empty((g, T, c), dtype=torch.float32, device=llr.device) if want_post else None
+        first, n = ldpccc_decode_window(self.handle, llr.contiguous(), clip, hard, post, stream)
+        return first, n, hard[:, :n], (post[:, :n] if post is not None else None)
 
 
 class Profile(ctypes.Structure):
