@@ -55,6 +55,7 @@ def args_parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ldpccc", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU seconds of the oracle baseline")
     ap.add_argument("--seed", type=int, default=20120403)
     return ap.parse_args()
@@ -298,6 +299,8 @@ def run_ours(a):
         line["variants"] = variants(a, pkg, code, stream, opts)
     if not a.no_e2e:
         line["e2e"] = e2e(a, pkg, code, stream, opts)
+    if not a.no_ldpccc:
+        line["ldpccc"] = ldpccc_bench(a, pkg, stream)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a)
     if rank == 0:
@@ -334,6 +337,40 @@ def variants(a, pkg, code, stream, opts) -> dict:
                      "mean_iters": sum(r["iters_sum"] for r in rs) / fr,
                      "fer": sum(r["frame_errors"] for r in rs) / fr}
     return out
+
+
+def ldpccc_bench(a, pkg, stream) -> dict:
+    """Pipelined LDPCCC decoder (secondary workload): 3x6 QC base, p = 128 (Lambda = 3, c = 256, b = 128),
+    I = 30 processors, 1024 streams, Eb/N0 2.0 dB; frames generated on the device, then decoded window by window."""
+    import torch
+
+    import synth
+
+    J_, L_, p_, I_, g_ = 3, 6, 128, 30, 1024
+    cc = pkg.LDPCCC(synth.qc_shifts(J_, L_, p_, seed=3), p_, I_, g_)
+    T = 200
+    llr = cc.channel(2.0, a.seed, 0, T)
+    hard = torch.empty((g_, T, cc.c), dtype=torch.uint8, device="cuda")
+    pkg.ldpccc_decode_window(cc.handle, llr, 30.0, hard, None, stream)  # fills the pipeline
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    windows = 3
+    decided = 0
+    ev0.record(stream)
+    for w in range(windows):
+        pkg.ldpccc_channel(cc.handle, 2.0, a.seed, T * (w + 1), llr, stream)
+        _, n = pkg.ldpccc_decode_window(cc.handle, llr, 30.0, hard, None, stream)
+        decided += n
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    errs = int(hard[:, :decided // windows].sum().item())
+    cc.close()
+    slot_bytes = I_ * (4 * J_ * cc.c * 4 + cc.c * 4) + cc.c // 8  # per stream per slot: edges r/w twice, mu
+    return {"workload": "LDPCCC from 3x6 QC, p=128 (c=256, b=128, ms=2), I=30, 1024 streams, 2.0 dB",
+            "value": g_ * decided * cc.b / (ms / 1e3) / 1e6, "unit": "Mbit/s", "ms_per_slot": ms / (windows * T),
+            "achieved_gbs": g_ * slot_bytes * windows * T / (ms / 1e3) / 1e9,
+            "bit_errors_last_window": errs}
 
 
 def e2e(a, pkg, code, stream, opts) -> dict:

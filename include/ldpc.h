@@ -182,6 +182,17 @@ ldpc_status ldpccc_decode_window(ldpccc cc, const float *llr, int32_t T, float c
                                  int64_t *first_out, int32_t *n_out, void *stream);
 
 /*
+ * ldpccc_channel -- channel LLRs for frames first_frame .. first_frame+T-1 of
+ * every stream: all-zero frames over BPSK/AWGN (Sec. II-E: x = 1 - 2v, y = x + g,
+ * sigma^2 = 1 / (2 (b/c) 10^(EbN0/10))), mu = 2y/sigma^2.  Bit n of frame f of
+ * stream s uses Philox4x32-10 counter (n/4, f mod 2^32, s, 1) under key
+ * (seed mod 2^32, seed / 2^32), then Box-Muller as in ldpc_channel.
+ *   llr_out: device [gamma][T][c] float.
+ */
+ldpc_status ldpccc_channel(ldpccc cc, double ebn0_db, uint64_t seed, int64_t first_frame, int32_t T,
+                           float *llr_out, void *stream);
+
+/*
  * ldpc_phi_eval -- the check-node transform of the sum-product rule on its own:
  * phi(x) = -ln tanh(x/2) for x >= 0, with which eq. (bphs) reads
  * alpha = prod(sign) * phi(sum_{n' != n} phi(|beta_n'|)) (phi is its own inverse).

@@ -66,6 +66,7 @@ _SIGNATURES = [
     ("ldpccc_dims", ctypes.c_int, [P, P, P, P, P]),
     ("ldpccc_reset", ctypes.c_int, [P]),
     ("ldpccc_decode_window", ctypes.c_int, [P, P, ctypes.c_int32, ctypes.c_float, P, P, P, P, P]),
+    ("ldpccc_channel", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, P, P]),
     ("ldpc_phi_eval", ctypes.c_int, [P, P, ctypes.c_int64, ctypes.c_int32, P]),
     ("ldpc_profile_enable", ctypes.c_int, [ctypes.c_int32]),
     ("ldpc_profile_read", ctypes.c_int, [P]),
@@ -208,6 +209,11 @@ def ldpccc_decode_window(cc: int, llr, clip: float = 30.0, hard=None, post=None,
     return first.value, n.value
 
 
+def ldpccc_channel(cc: int, ebn0_db: float, seed: int, first_frame: int, out, stream=None):
+    _check(lib().ldpccc_channel(cc, ebn0_db, seed, first_frame, out.shape[1], _ptr(out), _stream(stream)),
+           "ldpccc_channel")
+
+
 class LDPCCC:
     """Owning wrapper of an ldpccc handle."""
 
@@ -227,6 +233,13 @@ class LDPCCC:
             self.close()
         except Exception:
             pass
+
+    def channel(self, ebn0_db, seed, first_frame, T, device="cuda", stream=None):
+        import torch
+
+        out = torch.empty((self.gamma, T, self.c), dtype=torch.float32, device=device)
+        ldpccc_channel(self.handle, ebn0_db, seed, first_frame, out, stream)
+        return out
 
     def window(self, llr, clip=30.0, want_post=True, stream=None):
         """llr: [gamma][T][c] tensor on the device.  Returns (first, n, hard[:, :n], post[:, :n])."""

@@ -25,6 +25,7 @@
 // straight from the ring: the edges of an arriving frame need no initial fill.
 #include "qc_device.cuh"
 
+#include <cmath>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -185,6 +186,26 @@ cc_vn_kernel(const QcDesc d, CcDesc g, uint32_t *__restrict__ msg, const float *
             if (hard) hard[o] = pst < 0.0f ? 1 : 0;
             if (post) post[o] = pst;
         }
+    }
+}
+
+// channel LLRs of frames first .. first+T-1 of every stream: all-zero frames over
+// BPSK/AWGN; bit n of frame f of stream s draws from Philox counter (n/4, f mod 2^32,
+// s, 1) under key (seed mod 2^32, seed / 2^32)
+__global__ void cc_channel_kernel(float *__restrict__ out, int gamma, int T, int c, long long first, uint64_t seed,
+                                  float sigma, float s2) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (4 * q >= c) return;
+    for (int st = blockIdx.y; st < gamma * T; st += gridDim.y) {
+        const int s = st / T, tt = st - s * T;
+        const uint64_t f = (uint64_t)(first + tt);
+        uint32_t w[4];
+        philox4x32_10((uint32_t)q, (uint32_t)f, (uint32_t)s, 1u, (uint32_t)seed, (uint32_t)(seed >> 32), w);
+        float v4[4];
+        box_muller_llr(w, sigma, s2, v4);
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (4 * q + e < c) out[((size_t)s * T + tt) * c + 4 * q + e] = v4[e];
     }
 }
 
@@ -350,6 +371,32 @@ ldpc_status ldpccc_decode_window(ldpccc cc, const float *llr, int32_t T, float c
     }
     *n_out = n;
     if (first_out) *first_out = n > 0 ? (first_dec > 0 ? first_dec : 0) : -1;
+    return LDPC_OK;
+}
+
+ldpc_status ldpccc_channel(ldpccc cc, double ebn0_db, uint64_t seed, int64_t first_frame, int32_t T,
+                           float *llr_out, void *stream) {
+    if (!cc || !llr_out || T < 1 || first_frame < 0 || !std::isfinite(ebn0_db)) {
+        set_error("need ldpccc, llr_out, T >= 1, first_frame >= 0 and a finite Eb/N0");
+        return LDPC_EINVAL;
+    }
+    if (pointer_kind(llr_out) != 0) {
+        set_error("ldpccc_channel writes device memory");
+        return LDPC_EINVAL;
+    }
+    const double R = (double)(cc->c - cc->cb) / cc->c;
+    if (!(R > 0.0)) {
+        set_error("rate b/c is not positive");
+        return LDPC_EINVAL;
+    }
+    const double sigma = std::sqrt(1.0 / (2.0 * R * std::pow(10.0, ebn0_db / 10.0)));
+    const int Q = (cc->c + 3) / 4;
+    const long long rows = (long long)cc->gamma * T;
+    dim3 grd((Q + 127) / 128, rows < 65535 ? (unsigned)rows : 65535u);
+    count_launch();
+    cc_channel_kernel<<<grd, 128, 0, (cudaStream_t)stream>>>(llr_out, cc->gamma, T, cc->c, first_frame, seed,
+                                                            (float)sigma, (float)(2.0 / (sigma * sigma)));
+    LDPC_CUDA_TRY(cudaGetLastError());
     return LDPC_OK;
 }
 

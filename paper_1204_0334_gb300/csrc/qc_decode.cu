@@ -402,42 +402,6 @@ count_errors_kernel(const uint32_t *__restrict__ hw, const int32_t *__restrict__
 // ---------------------------------------------------------------------------
 // Channel: Philox4x32-10 (Salmon et al., SC'11) + Box-Muller, all-zero codeword.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
-                                              uint32_t k1, uint32_t *o) {
-#pragma unroll
-    for (int round = 0; round < 10; ++round) {
-        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
-        c0 = n0;
-        c1 = lo1;
-        c2 = n2;
-        c3 = lo0;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    o[0] = c0;
-    o[1] = c1;
-    o[2] = c2;
-    o[3] = c3;
-}
-
-// four channel LLRs of bits 4q..4q+3 of frame F
-__device__ __forceinline__ void channel_quad(uint64_t seed, uint64_t F, int q, float sigma, float s2, float *mu4) {
-    uint32_t w[4];
-    philox4x32_10((uint32_t)q, (uint32_t)F, (uint32_t)(F >> 32), 0u, (uint32_t)seed, (uint32_t)(seed >> 32), w);
-#pragma unroll
-    for (int pr = 0; pr < 2; ++pr) {
-        const float u0 = ((float)(w[2 * pr] >> 9) + 0.5f) * 1.1920928955078125e-07f;
-        const float u1 = ((float)(w[2 * pr + 1] >> 9) + 0.5f) * 1.1920928955078125e-07f;
-        const float rr = sqrtf(-2.0f * logf(u0));
-        float sn, cs;
-        sincospif(2.0f * u1, &sn, &cs);
-        mu4[2 * pr] = s2 * (1.0f + sigma * (rr * cs));
-        mu4[2 * pr + 1] = s2 * (1.0f + sigma * (rr * sn));
-    }
-}
-
 // straight into the package layout; thread x = frame within the package, y = bit quad
 template <typename Out>
 __global__ void channel_packed_kernel(Out *__restrict__ mu, int N, int W, int gamma, int frames_alloc,

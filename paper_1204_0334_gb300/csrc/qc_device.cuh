@@ -115,6 +115,51 @@ struct PkgFlags {
 };
 
 
+// ---------------------------------------------------------------------------
+// Channel: Philox4x32-10 (Salmon et al., SC'11) + Box-Muller.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                              uint32_t k1, uint32_t *o) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    o[0] = c0;
+    o[1] = c1;
+    o[2] = c2;
+    o[3] = c3;
+}
+
+// words -> four channel LLRs: u = (floor(w / 2^9) + 1/2) 2^-23, Box-Muller pairs
+// (w0, w1) and (w2, w3), mu = (2 / sigma^2) (1 + sigma g) for the all-zero codeword
+__device__ __forceinline__ void box_muller_llr(const uint32_t *w, float sigma, float s2, float *mu4) {
+#pragma unroll
+    for (int pr = 0; pr < 2; ++pr) {
+        const float u0 = ((float)(w[2 * pr] >> 9) + 0.5f) * 1.1920928955078125e-07f;
+        const float u1 = ((float)(w[2 * pr + 1] >> 9) + 0.5f) * 1.1920928955078125e-07f;
+        const float rr = sqrtf(-2.0f * logf(u0));
+        float sn, cs;
+        sincospif(2.0f * u1, &sn, &cs);
+        mu4[2 * pr] = s2 * (1.0f + sigma * (rr * cs));
+        mu4[2 * pr + 1] = s2 * (1.0f + sigma * (rr * sn));
+    }
+}
+
+// four channel LLRs of bits 4q..4q+3 of frame F
+__device__ __forceinline__ void channel_quad(uint64_t seed, uint64_t F, int q, float sigma, float s2, float *mu4) {
+    uint32_t w[4];
+    philox4x32_10((uint32_t)q, (uint32_t)F, (uint32_t)(F >> 32), 0u, (uint32_t)seed, (uint32_t)(seed >> 32), w);
+    box_muller_llr(w, sigma, s2, mu4);
+}
+
 __device__ __forceinline__ int sbyte(uint32_t w, int v) { return (int)(int8_t)(uint8_t)(w >> (8 * v)); }
 
 }  // namespace ldpc
