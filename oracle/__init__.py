@@ -58,6 +58,8 @@ def _load():
         lib.or_sp_decode.argtypes = [i32, i32, P, P, i32, P, i32, i32, f64, i32, P, P, P, P, i32]
         lib.or_ms_decode.argtypes = [i32, i32, P, P, i32, P, i32, i32, i32, P, P, P, P, i32]
         lib.or_quantize.argtypes = [P, i32, i32, P]
+        lib.or_noms.argtypes = [i32, i32, P, P, P, i32, P, i32, P, i32, f64, P, P, i32]
+        lib.or_noms.restype = f64
         lib.or_ldpccc_decode.argtypes = [i32, i32, P, P, i32, i32, i32, i32, i32, i32, P, f64, P, P, P,
                                          P, i32, P, i32]
         _lib = lib
@@ -280,3 +282,35 @@ def ldpccc_decode(Hconv, geo: dict, T: int, I: int, mu, clip: float = 30.0, nthr
     if rc < 0:
         raise ValueError("or_ldpccc_decode rejected its arguments")
     return post, hard, decided, log[: min(int(log_n[0]), log_cap)]
+
+
+def circulant_index(row_ptr, col, p: int, L: int) -> np.ndarray:
+    """Circulant block j*L + l of every edge of a QC code (row m = j*p + r, column n = l*p + k)."""
+    row_ptr = np.asarray(row_ptr)
+    rows = np.repeat(np.arange(len(row_ptr) - 1), np.diff(row_ptr))
+    return ((rows // p) * L + (np.asarray(col) // p)).astype(np.int32)
+
+
+def noms(row_ptr, col, cblk, N: int, mu, T: int, params, clip: float = 30.0, want_grad: bool = False,
+         nthreads: int = 1):
+    """Normalized/offset min-sum over T iterations with params [T][ncirc][2] = (w, o).
+
+    Returns (loss, post^(T) [nfr][N], grad [T][ncirc][2] or None); loss is the mean over
+    iterations, bits and frames of softplus(-posterior) (BCE against the all-zero codeword).
+    """
+    lib = _load()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    cblk = np.ascontiguousarray(cblk, dtype=np.int32)
+    mu = np.ascontiguousarray(mu, dtype=np.float32)
+    if mu.ndim == 1:
+        mu = mu[None, :]
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    assert params.shape[0] == T and params.shape[2] == 2
+    ncirc = params.shape[1]
+    nfr = mu.shape[0]
+    post = np.zeros((nfr, N), dtype=np.float64)
+    grad = np.zeros_like(params) if want_grad else None
+    loss = lib.or_noms(len(row_ptr) - 1, N, _p(row_ptr), _p(col), _p(cblk), nfr, _p(mu), T, _p(params), ncirc,
+                       clip, _p(post), _p(grad) if want_grad else None, nthreads)
+    return loss, post, grad

@@ -489,3 +489,158 @@ int or_ldpccc_decode(int M, int N, const int *row_ptr, const int *col, int T, in
     or_graph_free(&g);
     return ndec;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Neural normalized/offset min-sum (NOMS).  The paper only cites reduced-    */
+/* complexity BP (Sec. II-B); this is the usual parameterized min-sum with a   */
+/* weight w and an offset o per iteration and per circulant block:            */
+/*   beta^(0)_e = clip(mu_v)                                                   */
+/*   alpha^(l)_e = s_e * max(w_{l,c(e)} * m_e - o_{l,c(e)}, 0),               */
+/*        m_e = min_{e' != e in the row} |beta^(l-1)_e'|,                      */
+/*        s_e = prod_{e' != e} sign(beta^(l-1)_e')   (sign(0) = +)             */
+/*   beta^(l)_e = clip(mu_v + sum_{e' != e in the column} alpha^(l)_e'),       */
+/*   post^(l)_v = mu_v + sum_e alpha^(l)_e                                    */
+/*   loss = 1/(T N nfr) sum_l sum_v softplus(-post^(l)_v)                     */
+/* (multi-loss over iterations, target = the all-zero codeword).  cblk[e] is  */
+/* the circulant index of edge e; params is [T][ncirc][2] = (w, o).           */
+/* The gradient is reverse mode written out by hand: through the arg-min edge */
+/* of each m_e (the lowest index among ties), through max(., 0) where it is   */
+/* positive, and through the clip where |beta| < clip; signs carry none.      */
+/* ------------------------------------------------------------------------ */
+static double or_softplus(double x)
+{
+    return x > 0 ? x + log1p(exp(-x)) : log1p(exp(x));
+}
+
+static double or_sigmoid(double x)
+{
+    return x >= 0 ? 1.0 / (1.0 + exp(-x)) : exp(x) / (1.0 + exp(x));
+}
+
+/* CN of one iteration; also returns, per edge, the arg-min edge, m_e, s_e and the active flag */
+static void or_noms_cn(const or_graph *g, const double *beta, const int *cblk, const double *par_l, double *alpha,
+                       int *amin, double *mval, double *sval, int *act)
+{
+    for (int m = 0; m < g->M; ++m) {
+        int e0 = g->row_ptr[m], e1 = g->row_ptr[m + 1];
+        for (int e = e0; e < e1; ++e) {
+            double best = INFINITY;
+            int arg = -1, neg = 0;
+            for (int e2 = e0; e2 < e1; ++e2) {
+                if (e2 == e) continue;
+                double a = fabs(beta[e2]);
+                if (a < best) { best = a; arg = e2; }
+                if (beta[e2] < 0.0) neg ^= 1;
+            }
+            double s = neg ? -1.0 : 1.0;
+            double w = par_l[2 * cblk[e]], o = par_l[2 * cblk[e] + 1];
+            double z = (arg < 0) ? INFINITY : w * best - o;
+            int on = z > 0.0;
+            alpha[e] = on ? s * z : 0.0;
+            if (arg < 0) alpha[e] = s * INFINITY;  /* empty set: the clip below bounds it */
+            amin[e] = arg; mval[e] = best; sval[e] = s; act[e] = on && arg >= 0;
+        }
+    }
+}
+
+static void or_noms_vn(const or_graph *g, const double *mu, const double *alpha, double clip, double *beta,
+                       double *raw, double *post)
+{
+    for (int n = 0; n < g->N; ++n) {
+        int v0 = g->vptr[n], dv = g->vptr[n + 1] - v0;
+        double tot = mu[n];
+        for (int k = 0; k < dv; ++k) tot += alpha[g->vedge[v0 + k]];
+        post[n] = tot;
+        for (int k = 0; k < dv; ++k) {
+            double s = mu[n];
+            for (int k2 = 0; k2 < dv; ++k2)
+                if (k2 != k) s += alpha[g->vedge[v0 + k2]];
+            raw[g->vedge[v0 + k]] = s;
+            beta[g->vedge[v0 + k]] = or_clip(s, clip);
+        }
+    }
+}
+
+/*
+ * or_noms: forward (and, if grad != NULL, backward) over nfr frames.
+ * post_out (nullable) receives post^(T) [nfr][N]; returns the loss.  grad is [T][ncirc][2],
+ * accumulated (the caller zeroes it).
+ */
+double or_noms(int M, int N, const int *row_ptr, const int *col, const int *cblk, int nfr, const float *mu_f,
+               int T, const double *params, int ncirc, double clip, double *post_out, double *grad, int nthreads)
+{
+    or_graph g;
+    if (T < 1 || or_graph_init(&g, M, N, row_ptr, col)) return NAN;
+    int E = g.E;
+    double Z = (double)T * N * nfr;
+    double loss = 0.0;
+    (void)ncirc;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1) reduction(+ : loss)
+    for (int f = 0; f < nfr; ++f) {
+        double *mu = malloc(sizeof(double) * N);
+        double *beta = malloc(sizeof(double) * (size_t)E * (T + 1)); /* beta^(0..T) */
+        double *raw = malloc(sizeof(double) * (size_t)E * (T + 1));
+        double *alpha = malloc(sizeof(double) * (size_t)E * T);
+        double *post = malloc(sizeof(double) * (size_t)N * T);
+        double *mval = malloc(sizeof(double) * (size_t)E * T), *sval = malloc(sizeof(double) * (size_t)E * T);
+        int *amin = malloc(sizeof(int) * (size_t)E * T), *act = malloc(sizeof(int) * (size_t)E * T);
+        double *gb = calloc((size_t)E, sizeof(double)), *ga = malloc(sizeof(double) * E);
+        double *gb_prev = malloc(sizeof(double) * E);
+        double lf = 0.0;
+        for (int n = 0; n < N; ++n) mu[n] = or_clip((double)mu_f[(size_t)f * N + n], clip);
+        for (int e = 0; e < E; ++e) beta[e] = mu[col[e]];
+        for (int l = 0; l < T; ++l) {
+            or_noms_cn(&g, beta + (size_t)l * E, cblk, params + (size_t)l * 2 * ncirc, alpha + (size_t)l * E,
+                       amin + (size_t)l * E, mval + (size_t)l * E, sval + (size_t)l * E, act + (size_t)l * E);
+            or_noms_vn(&g, mu, alpha + (size_t)l * E, clip, beta + (size_t)(l + 1) * E, raw + (size_t)(l + 1) * E,
+                       post + (size_t)l * N);
+            for (int n = 0; n < N; ++n) lf += or_softplus(-post[(size_t)l * N + n]);
+        }
+        if (post_out)
+            for (int n = 0; n < N; ++n) post_out[(size_t)f * N + n] = post[(size_t)(T - 1) * N + n];
+        loss += lf / Z;
+        if (grad) {
+            /* gb = adjoint of beta^(l) (zero for l = T) */
+            for (int l = T - 1; l >= 0; --l) {
+                const double *bl = beta + (size_t)l * E;                 /* input of CN l */
+                const double *rawn = raw + (size_t)(l + 1) * E;          /* VN l output, unclipped */
+                const double *pl = post + (size_t)l * N;
+                /* adjoint of alpha^(l) */
+                for (int n = 0; n < N; ++n) {
+                    int v0 = g.vptr[n], dv = g.vptr[n + 1] - v0;
+                    double dpost = -or_sigmoid(-pl[n]) / Z;
+                    for (int k = 0; k < dv; ++k) {
+                        double s = dpost;
+                        for (int k2 = 0; k2 < dv; ++k2) {
+                            if (k2 == k) continue;
+                            int e2 = g.vedge[v0 + k2];
+                            if (fabs(rawn[e2]) < clip) s += gb[e2];
+                        }
+                        ga[g.vedge[v0 + k]] = s;
+                    }
+                }
+                /* parameters and the adjoint of beta^(l) */
+                double *pg = grad ? grad + (size_t)l * 2 * ncirc : NULL;
+                for (int e = 0; e < E; ++e) gb_prev[e] = 0.0;
+                for (int e = 0; e < E; ++e) {
+                    if (!act[(size_t)l * E + e]) continue;
+                    double s = sval[(size_t)l * E + e], mv = mval[(size_t)l * E + e];
+                    int c = cblk[e];
+                    double w = params[(size_t)l * 2 * ncirc + 2 * c];
+#pragma omp atomic
+                    pg[2 * c] += ga[e] * s * mv;
+#pragma omp atomic
+                    pg[2 * c + 1] += -ga[e] * s;
+                    int a = amin[(size_t)l * E + e];
+                    double sb = bl[a] > 0 ? 1.0 : (bl[a] < 0 ? -1.0 : 0.0);
+                    gb_prev[a] += ga[e] * s * w * sb;
+                }
+                for (int e = 0; e < E; ++e) gb[e] = gb_prev[e];
+            }
+        }
+        free(mu); free(beta); free(raw); free(alpha); free(post); free(mval); free(sval); free(amin); free(act);
+        free(gb); free(ga); free(gb_prev);
+    }
+    or_graph_free(&g);
+    return loss;
+}

@@ -390,3 +390,44 @@ def test_sp_on_paper_irregular_example_with_cycles():
     mu[3] = -mu[3] * 0.25  # one weak wrong bit
     post, hard, iters, ok = oracle.sp_decode(rp, col, 10, mu, max_iter=20, early_stop=True)
     assert ok[0] == 1 and np.array_equal(hard[0], cw.astype(np.uint8))
+
+
+# ---------------------------------------------------------------- learned normalized/offset min-sum
+def _qc(J, L, p, seed):
+    shifts = synth.qc_shifts(J, L, p, seed=seed)
+    H = oracle.qc_parity_check(shifts, p)
+    rp, col = oracle.csr_rows(H)
+    return H, rp, col, oracle.circulant_index(rp, col, p, L)
+
+
+def test_noms_with_unit_weight_is_min_sum():
+    """w = 1, o = 0 reduces the NOMS rule to plain min-sum: equal to the integer oracle on the LLR grid."""
+    H, rp, col, cb = _qc(3, 6, 16, 4)
+    N = H.shape[1]
+    mu = synth.integer_llrs(6, N, seed=2, lo=-12, hi=12, scale=0.25)
+    T = 4
+    params = np.zeros((T, 18, 2))
+    params[:, :, 0] = 1.0
+    _, post, _ = oracle.noms(rp, col, cb, N, mu, T, params, clip=31.75)
+    mpost = oracle.ms_decode(rp, col, N, mu, T)[0]
+    assert np.array_equal(post, mpost * 0.25)
+
+
+def test_noms_gradient_matches_finite_differences():
+    """Hand-written reverse mode against central differences of the FP64 loss (away from ties and kinks)."""
+    H, rp, col, cb = _qc(3, 6, 8, 5)
+    N = H.shape[1]
+    mu = synth.gaussian_llrs(3, N, seed=6, ebn0_db=1.0, rate=0.5)
+    T = 3
+    rng = np.random.default_rng(7)
+    params = np.stack([rng.uniform(0.6, 1.0, (T, 18)), rng.uniform(0.0, 0.5, (T, 18))], axis=-1)
+    loss, _, grad = oracle.noms(rp, col, cb, N, mu, T, params, want_grad=True)
+    h = 1e-6
+    idx = [(0, 0, 0), (0, 5, 1), (1, 7, 0), (1, 17, 1), (2, 3, 0), (2, 11, 1), (0, 12, 0), (2, 0, 1)]
+    for t, c, k in idx:
+        pp, pm = params.copy(), params.copy()
+        pp[t, c, k] += h
+        pm[t, c, k] -= h
+        fd = (oracle.noms(rp, col, cb, N, mu, T, pp)[0] - oracle.noms(rp, col, cb, N, mu, T, pm)[0]) / (2 * h)
+        assert abs(fd - grad[t, c, k]) <= 1e-6 * max(1e-3, abs(fd)), (t, c, k, fd, grad[t, c, k])
+    assert np.abs(grad).max() > 0
