@@ -193,6 +193,34 @@ ldpc_status ldpccc_channel(ldpccc cc, double ebn0_db, uint64_t seed, int64_t fir
                            float *llr_out, void *stream);
 
 /*
+ * Learned normalized/offset min-sum (NOMS).  The paper cites reduced-complexity
+ * BP (Sec. II-B) without defining it; this is the parameterized min-sum
+ *   alpha_e = sign * max(w_{l,c(e)} * m_e - o_{l,c(e)}, 0),  m_e = min_{e' != e} |beta_e'|
+ * with one (w, o) per iteration l and circulant block c = j*L + l, used with
+ * the variable rule of eq. (bpvs) (clipped at +-clip) for T iterations.
+ * Inference: ldpc_decode / ldpc_ber_sim with opts.algo = LDPC_ALGO_NOMS and
+ * opts.noms_params = device [max_iter][J*L][2].
+ *
+ * ldpc_noms_forward -- training forward pass over B frames:
+ *   loss = 1/(T N B) sum over iterations l, bits n, frames of softplus(-post^(l)_n)
+ *   (BCE of every iteration's posterior against the all-zero codeword).
+ *   llr: device [B][N] float; params: device [T][J*L][2] float (w, o); msg: LDPC_MSG_F32
+ *   or LDPC_MSG_F16 storage of the saved messages; ckpt_every = k: the messages of every
+ *   k-th iteration are kept and the others recomputed in the backward pass;
+ *   loss: device float[1]; post: device [B][N] float (post^(T)) or NULL.
+ *   The code object keeps the state for the following ldpc_noms_backward.
+ * ldpc_noms_backward -- d loss / d params accumulated into grad (device [T][J*L][2],
+ *   the caller zeroes it).  Needs the forward of the same params on the same code
+ *   object just before.  Reverse mode written out by hand: through the arg-min edge
+ *   of each m_e (lowest index among ties), through max(., 0) where positive and
+ *   through the clip where inactive.
+ * Errors: LDPC_EINVAL (sizes, host pointers, backward without forward), LDPC_ENOMEM.
+ */
+ldpc_status ldpc_noms_forward(ldpc_code code, const float *llr, int32_t B, int32_t T, const float *params,
+                              int32_t msg, int32_t ckpt_every, float clip, float *loss, float *post, void *stream);
+ldpc_status ldpc_noms_backward(ldpc_code code, const float *params, float *grad, void *stream);
+
+/*
  * ldpc_phi_eval -- the check-node transform of the sum-product rule on its own:
  * phi(x) = -ln tanh(x/2) for x >= 0, with which eq. (bphs) reads
  * alpha = prod(sign) * phi(sum_{n' != n} phi(|beta_n'|)) (phi is its own inverse).

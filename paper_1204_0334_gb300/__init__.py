@@ -67,6 +67,9 @@ _SIGNATURES = [
     ("ldpccc_reset", ctypes.c_int, [P]),
     ("ldpccc_decode_window", ctypes.c_int, [P, P, ctypes.c_int32, ctypes.c_float, P, P, P, P, P]),
     ("ldpccc_channel", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, P, P]),
+    ("ldpc_noms_forward", ctypes.c_int, [P, P, ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_float, P, P, P]),
+    ("ldpc_noms_backward", ctypes.c_int, [P, P, P, P]),
     ("ldpc_phi_eval", ctypes.c_int, [P, P, ctypes.c_int64, ctypes.c_int32, P]),
     ("ldpc_profile_enable", ctypes.c_int, [ctypes.c_int32]),
     ("ldpc_profile_read", ctypes.c_int, [P]),
@@ -250,6 +253,24 @@ class LDPCCC:
         post = torch.empty((g, T, c), dtype=torch.float32, device=llr.device) if want_post else None
         first, n = ldpccc_decode_window(self.handle, llr.contiguous(), clip, hard, post, stream)
         return first, n, hard[:, :n], (post[:, :n] if post is not None else None)
+
+
+def ldpc_noms_forward(code: int, llr, params, msg: int = MSG_F32, ckpt_every: int = 1, clip: float = 30.0,
+                      want_post: bool = False, stream=None):
+    """Training forward pass; returns (loss tensor [1], post^(T) [B][N] or None)."""
+    import torch
+
+    B = llr.shape[0]
+    T = params.shape[0]
+    loss = torch.empty(1, dtype=torch.float32, device=llr.device)
+    post = torch.empty_like(llr) if want_post else None
+    _check(lib().ldpc_noms_forward(code, _ptr(llr), B, T, _ptr(params), msg, ckpt_every, clip, _ptr(loss),
+                                   _ptr(post), _stream(stream)), "ldpc_noms_forward")
+    return loss, post
+
+
+def ldpc_noms_backward(code: int, params, grad, stream=None):
+    _check(lib().ldpc_noms_backward(code, _ptr(params), _ptr(grad), _stream(stream)), "ldpc_noms_backward")
 
 
 class Profile(ctypes.Structure):

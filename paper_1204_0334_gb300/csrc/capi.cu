@@ -67,8 +67,18 @@ static ldpc_status check_opts(const ldpc_code c, const ldpc_decode_opts *o) {
             return LDPC_EINVAL;
         }
     } else if (o->algo == LDPC_ALGO_NOMS) {
-        set_error("NOMS decoding is exposed through ldpc_noms_forward");
-        return LDPC_EUNSUPPORTED;
+        if (o->msg != LDPC_MSG_F32 && o->msg != LDPC_MSG_F16) {
+            set_error("normalized/offset min-sum takes F32 or F16 messages");
+            return LDPC_EUNSUPPORTED;
+        }
+        if (!o->noms_params || pointer_kind(o->noms_params) != 0) {
+            set_error("NOMS needs device noms_params [max_iter][J*L][2]");
+            return LDPC_EINVAL;
+        }
+        if (!(o->clip > 0.0f) || !std::isfinite(o->clip) || o->clip > 60000.0f) {
+            set_error("clip must be finite, positive and representable in FP16 storage");
+            return LDPC_EINVAL;
+        }
     } else {
         set_error("unknown algo %d", o->algo);
         return LDPC_EINVAL;
@@ -183,6 +193,7 @@ ldpc_status ldpc_code_destroy(ldpc_code c) {
     cudaFree(w.stage_post);
     cudaFree(w.stage_hard);
     cudaFree(w.stage_i32);
+    noms_free(c->noms);
     delete c;
     return LDPC_OK;
 }

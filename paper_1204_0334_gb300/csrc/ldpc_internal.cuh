@@ -49,8 +49,11 @@ struct DecodeWs {
 
 }  // namespace ldpc
 
+struct ldpc_noms_state;  // training state of the learned min-sum (noms.cu)
+
 struct ldpc_code_s {
     ldpc::QcDesc d;
+    ldpc_noms_state *noms = nullptr;
     int device = 0;
     double rate = 0.0;   // design rate K/N
     ldpc::DecodeWs ws;
@@ -88,8 +91,9 @@ ldpc_status qc_channel_frames(ldpc_code c, double sigma, uint64_t seed, uint64_t
 ldpc_status qc_count_errors(ldpc_code c, int gamma, const ldpc_decode_opts &o, cudaStream_t s);
 
 ldpc_status phi_eval(const float *x, float *y, int n, int variant, cudaStream_t s);
+void noms_free(ldpc_noms_state *w);
 // pipelined node passes (qc_pipe.cu)
-ldpc_status qc_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, bool syn, int par, cudaStream_t s);
+ldpc_status qc_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, bool syn, int par, int it, cudaStream_t s);
 ldpc_status qc_vn_pipe(ldpc_code c, const ldpc_decode_opts &o, bool stop, bool post, int it, int par,
                        cudaStream_t s);
 ldpc_status qc_compact(ldpc_code c, int P, int V, cudaStream_t s);

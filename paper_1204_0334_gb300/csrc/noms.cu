@@ -1,0 +1,542 @@
+// Learned normalized/offset min-sum (NOMS): forward and backward kernels for
+// training the per-iteration, per-circulant weights and offsets, over T
+// unrolled flooding iterations of Algorithm 1 with the check rule
+//   alpha_e = s_e * max(w_{l,c(e)} * m_e - o_{l,c(e)}, 0),  m_e = min_{e' != e} |beta_e'|,
+// the variable rule of eq. (bpvs) with clipping, and the loss
+//   loss = 1/(T N B) sum_l sum_n softplus(-post^(l)_n)
+// (BCE of every iteration's posterior against the all-zero codeword).
+//
+// Layout: packages of 32 frames, one frame per lane, msg-like buffers
+// [P][E][32] (edge order of the block decoder: edge k of block (j, l) is
+// variable l*p + k).  Betas are kept at checkpoints every k iterations in the
+// storage type S (float or half); alphas and adjoints in float.  The backward
+// pass recomputes each segment of k iterations from its checkpoint.
+#include "qc_device.cuh"
+
+#include <algorithm>
+#include <vector>
+
+struct ldpc_noms_state {
+    int B = 0, T = 0, k = 1, P = 0, msg = LDPC_MSG_F32;
+    float clip = 30.0f;
+    size_t cap_frames = 0, cap_nck = 0, cap_seg = 0;
+    float *mu = nullptr;       // [P][N][32]
+    void *ping[2] = {nullptr, nullptr};  // non-checkpoint betas (S)
+    void *ckpt = nullptr;      // [nck][P][E][32] (S): beta^(k), beta^(2k), ...
+    void *seg = nullptr;       // [k][P][E][32] (S): recomputed betas of one segment
+    float *A = nullptr, *GA = nullptr, *GB = nullptr;  // [P][E][32]
+    float *postbuf = nullptr;  // [P][N][32]
+    double *acc = nullptr;     // loss accumulator
+    bool have_forward = false;
+    const float *params = nullptr;
+};
+
+namespace ldpc {
+
+template <typename S> struct Store;
+template <> struct Store<float> {
+    static __device__ __forceinline__ float ld(const float *p) { return *p; }
+    static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+};
+template <> struct Store<__half> {
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(*p); }
+    static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+};
+
+__device__ __forceinline__ float softplusf(float x) { return x > 0.0f ? x + log1pf(__expf(-x)) : log1pf(__expf(x)); }
+__device__ __forceinline__ float sigmoidf(float x) {
+    return x >= 0.0f ? 1.0f / (1.0f + __expf(-x)) : __expf(x) / (1.0f + __expf(x));
+}
+
+// beta^(l-1) of edge (block offset eo + k) and variable n, from mu (l = 1) or a store
+template <typename S, bool FROM_MU>
+__device__ __forceinline__ float nm_beta(const void *src, const QcDesc &d, int pk, int eidx, int n, int lane) {
+    if (FROM_MU) return reinterpret_cast<const float *>(src)[((size_t)pk * d.N + n) * 32 + lane];
+    return Store<S>::ld(reinterpret_cast<const S *>(src) + ((size_t)pk * d.E + eidx) * 32 + lane);
+}
+
+// ---------------------------------------------------------------------------
+// forward check step: alpha^(l) from beta^(l-1); one warp = one row of one package
+// ---------------------------------------------------------------------------
+template <int DCMAX, typename S, bool FROM_MU>
+__global__ void __launch_bounds__(kWarps * 32)
+nm_cn_fwd(const QcDesc d, const void *__restrict__ bin, float *__restrict__ A, const float *__restrict__ prm_l,
+          float clip, int P) {
+    const int lane = threadIdx.x & 31;
+    const int m = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int pk = blockIdx.y;
+    if (m >= d.M || pk >= P) return;
+    const int j = m / d.p, r = m - j * d.p;
+    float ab[DCMAX];
+    int eid[DCMAX];
+    uint32_t neg = 0u;
+    float mn1 = INFINITY, mn2 = INFINITY;
+#pragma unroll
+    for (int l = 0; l < DCMAX; ++l) {
+        ab[l] = INFINITY;
+        eid[l] = -1;
+        if (l >= d.L || d.shift[j * d.L + l] < 0) continue;
+        int k = r + d.shift[j * d.L + l];
+        if (k >= d.p) k -= d.p;
+        eid[l] = d.eoff[j * d.L + l] + k;
+        const float x = nm_beta<S, FROM_MU>(bin, d, pk, eid[l], l * d.p + k, lane);
+        ab[l] = fabsf(x);
+        neg |= (x < 0.0f ? 1u : 0u) << l;
+        mn2 = fminf(mn2, fmaxf(mn1, ab[l]));
+        mn1 = fminf(mn1, ab[l]);
+    }
+    const uint32_t par = __popc(neg) & 1u;
+    const float *prm = prm_l + (size_t)j * d.L * 2;
+#pragma unroll
+    for (int l = 0; l < DCMAX; ++l) {
+        if (eid[l] < 0) continue;
+        const float mv = ab[l] == mn1 ? mn2 : mn1;
+        const float mag = fminf(fmaxf(fmaf(__ldg(prm + 2 * l), mv, -__ldg(prm + 2 * l + 1)), 0.0f), clip);
+        A[((size_t)pk * d.E + eid[l]) * 32 + lane] = (par ^ ((neg >> l) & 1u)) ? -mag : mag;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// forward variable step: beta^(l) (clipped, stored as S), posterior, loss term
+// ---------------------------------------------------------------------------
+template <int JMAX, typename S>
+__global__ void __launch_bounds__(kWarps * 32)
+nm_vn_fwd(const QcDesc d, const float *__restrict__ A, const float *__restrict__ mu, S *__restrict__ bout,
+          double *__restrict__ acc, float *__restrict__ post, float zinv, float clip, int P, int B) {
+    __shared__ float red[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n = blockIdx.x * kWarps + warp;
+    const int pk = blockIdx.y;
+    float lsum = 0.0f;
+    if (n < d.N && pk < P) {
+        const int l = n / d.p, k = n - l * d.p;
+        const float mv = mu[((size_t)pk * d.N + n) * 32 + lane];
+        float a[JMAX];
+        int eid[JMAX];
+        float tot = mv;
+#pragma unroll
+        for (int j = 0; j < JMAX; ++j) {
+            a[j] = 0.0f;
+            eid[j] = -1;
+            if (j >= d.J || d.shift[j * d.L + l] < 0) continue;
+            eid[j] = d.eoff[j * d.L + l] + k;
+            a[j] = A[((size_t)pk * d.E + eid[j]) * 32 + lane];
+            tot += a[j];
+        }
+        if (bout) {
+#pragma unroll
+            for (int j = 0; j < JMAX; ++j) {
+                if (eid[j] < 0) continue;
+                float s = mv;
+#pragma unroll
+                for (int j2 = 0; j2 < JMAX; ++j2)
+                    if (j2 != j) s += a[j2];
+                Store<S>::st(bout + ((size_t)pk * d.E + eid[j]) * 32 + lane, clipf(s, clip));
+            }
+        }
+        if (post) post[((size_t)pk * d.N + n) * 32 + lane] = tot;
+        if (pk * 32 + lane < B) lsum = softplusf(-tot) * zinv;
+    }
+    if (acc) {
+        for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+        if (lane == 0) red[warp] = lsum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int w = 0; w < kWarps; ++w) s += red[w];
+            if (s != 0.0) atomicAdd(acc, s);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// backward variable step: adjoint of alpha^(l) from the loss at iteration l and
+// the adjoint of beta^(l) (zero at l = T), through the clip
+// ---------------------------------------------------------------------------
+template <int JMAX>
+__global__ void __launch_bounds__(kWarps * 32)
+nm_vn_bwd(const QcDesc d, const float *__restrict__ A, const float *__restrict__ mu, const float *__restrict__ GB,
+          float *__restrict__ GA, float zinv, float clip, int P, int B) {
+    const int lane = threadIdx.x & 31;
+    const int n = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int pk = blockIdx.y;
+    if (n >= d.N || pk >= P) return;
+    const int l = n / d.p, k = n - l * d.p;
+    const float mv = mu[((size_t)pk * d.N + n) * 32 + lane];
+    float a[JMAX], gbm[JMAX];
+    int eid[JMAX];
+    float tot = mv;
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j) {
+        a[j] = 0.0f;
+        eid[j] = -1;
+        if (j >= d.J || d.shift[j * d.L + l] < 0) continue;
+        eid[j] = d.eoff[j * d.L + l] + k;
+        a[j] = A[((size_t)pk * d.E + eid[j]) * 32 + lane];
+        tot += a[j];
+    }
+    // adjoint of beta^(l)_e, masked where the clip was active
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j) {
+        gbm[j] = 0.0f;
+        if (eid[j] < 0 || !GB) continue;
+        float s = mv;
+#pragma unroll
+        for (int j2 = 0; j2 < JMAX; ++j2)
+            if (j2 != j) s += a[j2];
+        if (fabsf(s) < clip) gbm[j] = GB[((size_t)pk * d.E + eid[j]) * 32 + lane];
+    }
+    const float dpost = (pk * 32 + lane < B) ? -sigmoidf(-tot) * zinv : 0.0f;
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j) {
+        if (eid[j] < 0) continue;
+        float g = dpost;
+#pragma unroll
+        for (int j2 = 0; j2 < JMAX; ++j2)
+            if (j2 != j) g += gbm[j2];
+        GA[((size_t)pk * d.E + eid[j]) * 32 + lane] = g;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// backward check step: parameter gradients of iteration l and the adjoint of
+// beta^(l-1).  m_e = |beta_{e*}| with e* the arg-min over the other edges
+// (lowest index among ties): e* = idx2 for e = idx1, else idx1; so only the
+// two smallest inputs of a row receive gradient.  Persistent blocks; parameter
+// sums in shared memory, flushed once per block.
+// ---------------------------------------------------------------------------
+template <int DCMAX, typename S, bool FROM_MU>
+__global__ void __launch_bounds__(kWarps * 32)
+nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict__ GA, const float *__restrict__ prm_l,
+          float *__restrict__ GB, float *__restrict__ grad_l, int P, int want_gb) {
+    __shared__ float sg[kMaxJ * kMaxL * 2];
+    for (int i = threadIdx.x; i < d.J * d.L * 2; i += blockDim.x) sg[i] = 0.0f;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long total = (long long)P * d.M;
+    for (long long item = (long long)blockIdx.x * kWarps + warp; item < total; item += (long long)gridDim.x * kWarps) {
+        const int pk = (int)(item / d.M), m = (int)(item - (long long)pk * d.M);
+        const int j = m / d.p, r = m - j * d.p;
+        float ab[DCMAX], sgn[DCMAX];
+        int eid[DCMAX];
+        uint32_t neg = 0u;
+        float mn1 = INFINITY, mn2 = INFINITY;
+        int i1 = -1, i2 = -1;
+#pragma unroll
+        for (int l = 0; l < DCMAX; ++l) {
+            ab[l] = INFINITY;
+            sgn[l] = 0.0f;
+            eid[l] = -1;
+            if (l >= d.L || d.shift[j * d.L + l] < 0) continue;
+            int k = r + d.shift[j * d.L + l];
+            if (k >= d.p) k -= d.p;
+            eid[l] = d.eoff[j * d.L + l] + k;
+            const float x = nm_beta<S, FROM_MU>(bin, d, pk, eid[l], l * d.p + k, lane);
+            ab[l] = fabsf(x);
+            sgn[l] = x > 0.0f ? 1.0f : (x < 0.0f ? -1.0f : 0.0f);
+            neg |= (x < 0.0f ? 1u : 0u) << l;
+            // strict < keeps the lowest index among ties
+            if (ab[l] < mn1) {
+                mn2 = mn1;
+                i2 = i1;
+                mn1 = ab[l];
+                i1 = l;
+            } else if (ab[l] < mn2) {
+                mn2 = ab[l];
+                i2 = l;
+            }
+        }
+        const uint32_t par = __popc(neg) & 1u;
+        const float *prm = prm_l + (size_t)j * d.L * 2;
+        float g1 = 0.0f, g2 = 0.0f;  // adjoints landing on edges i1 and i2
+#pragma unroll
+        for (int l = 0; l < DCMAX; ++l) {
+            float gw = 0.0f, go = 0.0f;
+            if (eid[l] >= 0) {
+                const float w = __ldg(prm + 2 * l), o = __ldg(prm + 2 * l + 1);
+                const bool first = l == i1;
+                const float mv = first ? mn2 : mn1;
+                const float s = (par ^ ((neg >> l) & 1u)) ? -1.0f : 1.0f;
+                const bool act = (first ? i2 : i1) >= 0 && fmaf(w, mv, -o) > 0.0f;
+                if (act) {
+                    const float ga = GA[((size_t)pk * d.E + eid[l]) * 32 + lane];
+                    gw = ga * s * mv;
+                    go = -ga * s;
+                    if (first) g2 += ga * s * w;
+                    else g1 += ga * s * w;
+                }
+            }
+            // warp sums of this circulant's two gradients
+            for (int of = 16; of > 0; of >>= 1) {
+                gw += __shfl_xor_sync(0xffffffffu, gw, of);
+                go += __shfl_xor_sync(0xffffffffu, go, of);
+            }
+            if (lane == 0 && eid[l] >= 0 && (gw != 0.0f || go != 0.0f)) {
+                atomicAdd(&sg[(j * d.L + l) * 2], gw);
+                atomicAdd(&sg[(j * d.L + l) * 2 + 1], go);
+            }
+        }
+        if (want_gb) {
+#pragma unroll
+            for (int l = 0; l < DCMAX; ++l) {
+                if (eid[l] < 0) continue;
+                float g = 0.0f;
+                if (l == i1) g = g1 * sgn[l];
+                else if (l == i2) g = g2 * sgn[l];
+                GB[((size_t)pk * d.E + eid[l]) * 32 + lane] = g;
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < d.J * d.L * 2; i += blockDim.x)
+        if (sg[i] != 0.0f) atomicAdd(grad_l + i, sg[i]);
+}
+
+__global__ void nm_loss_out(const double *acc, float *out) { *out = (float)*acc; }
+
+// ---------------------------------------------------------------------------
+// host orchestration
+// ---------------------------------------------------------------------------
+static size_t es(int msg) { return msg == LDPC_MSG_F16 ? 2 : 4; }
+
+static ldpc_status nm_alloc(ldpc_code c, ldpc_noms_state &w, size_t frames, size_t nck, size_t nseg) {
+    const size_t E = c->d.E, N = c->d.N;
+    const size_t fr = (frames + 31) / 32 * 32;
+    auto fail = [&]() {
+        cudaGetLastError();
+        set_error("NOMS workspace allocation failed");
+        return LDPC_ENOMEM;
+    };
+    if (fr > w.cap_frames) {
+        cudaDeviceSynchronize();
+        cudaFree(w.mu); cudaFree(w.ping[0]); cudaFree(w.ping[1]); cudaFree(w.A); cudaFree(w.GA); cudaFree(w.GB);
+        cudaFree(w.postbuf); cudaFree(w.ckpt); cudaFree(w.seg);
+        w.ckpt = w.seg = nullptr;
+        w.cap_nck = w.cap_seg = 0;
+        if (cudaMalloc(&w.mu, N * fr * 4) || cudaMalloc(&w.ping[0], E * fr * 4) || cudaMalloc(&w.ping[1], E * fr * 4) ||
+            cudaMalloc(&w.A, E * fr * 4) || cudaMalloc(&w.GA, E * fr * 4) || cudaMalloc(&w.GB, E * fr * 4) ||
+            cudaMalloc(&w.postbuf, N * fr * 4))
+            return fail();
+        if (!w.acc && cudaMalloc(&w.acc, sizeof(double))) return fail();
+        w.cap_frames = fr;
+    }
+    if (nck > w.cap_nck) {
+        cudaDeviceSynchronize();
+        cudaFree(w.ckpt);
+        if (cudaMalloc(&w.ckpt, nck * E * w.cap_frames * 4)) return fail();
+        w.cap_nck = nck;
+    }
+    if (nseg > w.cap_seg) {
+        cudaDeviceSynchronize();
+        cudaFree(w.seg);
+        if (cudaMalloc(&w.seg, nseg * E * w.cap_frames * 4)) return fail();
+        w.cap_seg = nseg;
+    }
+    return LDPC_OK;
+}
+
+template <typename S>
+static ldpc_status nm_step_fwd(ldpc_code c, ldpc_noms_state &w, int l, const void *bin, bool from_mu, void *bout,
+                               bool loss, float *post, cudaStream_t s) {
+    const QcDesc &d = c->d;
+    dim3 cg((d.M + kWarps - 1) / kWarps, w.P), vg((d.N + kWarps - 1) / kWarps, w.P);
+    const float *prm = w.params + (size_t)(l - 1) * d.J * d.L * 2;
+    const float zinv = (float)(1.0 / ((double)w.T * d.N * w.B));
+#define NM_CN(DC)                                                                                       \
+    do {                                                                                                \
+        if (from_mu) nm_cn_fwd<DC, S, true><<<cg, kWarps * 32, 0, s>>>(d, bin, w.A, prm, w.clip, w.P);  \
+        else nm_cn_fwd<DC, S, false><<<cg, kWarps * 32, 0, s>>>(d, bin, w.A, prm, w.clip, w.P);         \
+    } while (0)
+    if (d.L <= 8) NM_CN(8);
+    else if (d.L <= 16) NM_CN(16);
+    else if (d.L <= 24) NM_CN(24);
+    else NM_CN(32);
+#undef NM_CN
+    count_launch();
+    if (bout || loss || post) {
+        if (d.J <= 4)
+            nm_vn_fwd<4, S><<<vg, kWarps * 32, 0, s>>>(d, w.A, w.mu, (S *)bout, loss ? w.acc : nullptr, post, zinv,
+                                                       w.clip, w.P, w.B);
+        else
+            nm_vn_fwd<8, S><<<vg, kWarps * 32, 0, s>>>(d, w.A, w.mu, (S *)bout, loss ? w.acc : nullptr, post, zinv,
+                                                       w.clip, w.P, w.B);
+        count_launch();
+    }
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
+template <typename S>
+static void *ck(ldpc_code c, ldpc_noms_state &w, int idx) {  // checkpoint beta^(idx * k), idx >= 1
+    return (char *)w.ckpt + (size_t)(idx - 1) * c->d.E * w.cap_frames * sizeof(S);
+}
+template <typename S>
+static void *sg(ldpc_code c, ldpc_noms_state &w, int idx) {
+    return (char *)w.seg + (size_t)idx * c->d.E * w.cap_frames * sizeof(S);
+}
+
+template <typename S>
+static ldpc_status nm_forward(ldpc_code c, ldpc_noms_state &w, float *post_out, cudaStream_t s) {
+    LDPC_CUDA_TRY(cudaMemsetAsync(w.acc, 0, sizeof(double), s));
+    const void *prev = w.mu;
+    bool from_mu = true;
+    for (int l = 1; l <= w.T; ++l) {
+        void *out;
+        if (l == w.T) out = nullptr;  // beta^(T) is never used
+        else if (l % w.k == 0) out = ck<S>(c, w, l / w.k);
+        else out = w.ping[l & 1];
+        ldpc_status st = nm_step_fwd<S>(c, w, l, prev, from_mu, out, true, l == w.T ? w.postbuf : nullptr, s);
+        if (st != LDPC_OK) return st;
+        prev = out;
+        from_mu = false;
+    }
+    (void)post_out;
+    return LDPC_OK;
+}
+
+template <typename S>
+static ldpc_status nm_backward(ldpc_code c, ldpc_noms_state &w, float *grad, cudaStream_t s) {
+    const QcDesc &d = c->d;
+    dim3 vg((d.N + kWarps - 1) / kWarps, w.P);
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int cb_blocks = std::max(1, sms * 4);
+    const float zinv = (float)(1.0 / ((double)w.T * d.N * w.B));
+    int seg_base = -1;  // iterations seg_base+1 .. seg_base+k-1 recomputed into seg
+    for (int l = w.T; l >= 1; --l) {
+        // beta^(l-1): mu, a checkpoint, or a recomputed member of its segment
+        const int b = l - 1;
+        const void *bin;
+        bool from_mu = false;
+        if (b == 0) {
+            bin = w.mu;
+            from_mu = true;
+        } else if (b % w.k == 0) {
+            bin = ck<S>(c, w, b / w.k);
+        } else {
+            const int c0 = (b / w.k) * w.k;
+            if (seg_base != c0) {
+                const void *src = c0 == 0 ? (const void *)w.mu : ck<S>(c, w, c0 / w.k);
+                bool fm = c0 == 0;
+                for (int q = c0 + 1; q < std::min(c0 + w.k, w.T); ++q) {
+                    void *dst = sg<S>(c, w, q - c0 - 1);
+                    ldpc_status st = nm_step_fwd<S>(c, w, q, src, fm, dst, false, nullptr, s);
+                    if (st != LDPC_OK) return st;
+                    src = dst;
+                    fm = false;
+                }
+                seg_base = c0;
+            }
+            bin = sg<S>(c, w, b - c0 - 1);
+        }
+        // alpha^(l), then the adjoints
+        ldpc_status st = nm_step_fwd<S>(c, w, l, bin, from_mu, nullptr, false, nullptr, s);
+        if (st != LDPC_OK) return st;
+        if (d.J <= 4)
+            nm_vn_bwd<4><<<vg, kWarps * 32, 0, s>>>(d, w.A, w.mu, l == w.T ? nullptr : w.GB, w.GA, zinv, w.clip, w.P, w.B);
+        else
+            nm_vn_bwd<8><<<vg, kWarps * 32, 0, s>>>(d, w.A, w.mu, l == w.T ? nullptr : w.GB, w.GA, zinv, w.clip, w.P, w.B);
+        const float *prm = w.params + (size_t)(l - 1) * d.J * d.L * 2;
+        float *gl = grad + (size_t)(l - 1) * d.J * d.L * 2;
+        const int want_gb = l > 1;
+#define NM_CB(DC)                                                                                                  \
+    do {                                                                                                           \
+        if (from_mu) nm_cn_bwd<DC, S, true><<<cb_blocks, kWarps * 32, 0, s>>>(d, bin, w.GA, prm, w.GB, gl, w.P, want_gb); \
+        else nm_cn_bwd<DC, S, false><<<cb_blocks, kWarps * 32, 0, s>>>(d, bin, w.GA, prm, w.GB, gl, w.P, want_gb);        \
+    } while (0)
+        if (d.L <= 8) NM_CB(8);
+        else if (d.L <= 16) NM_CB(16);
+        else if (d.L <= 24) NM_CB(24);
+        else NM_CB(32);
+#undef NM_CB
+        count_launch(2);
+        LDPC_CUDA_TRY(cudaGetLastError());
+    }
+    return LDPC_OK;
+}
+
+// pack [B][N] -> [P][N][32] with clipping (qc_decode.cu)
+ldpc_status pack_frames_w32(const float *llr, float *dst, int gamma, int N, float clip, cudaStream_t s);
+ldpc_status unpack_frames_w32(const float *src, float *dst, int gamma, int N, cudaStream_t s);
+
+}  // namespace ldpc
+
+using namespace ldpc;
+
+extern "C" {
+
+ldpc_status ldpc_noms_forward(ldpc_code c, const float *llr, int32_t B, int32_t T, const float *params, int32_t msg,
+                              int32_t ckpt_every, float clip, float *loss, float *post, void *stream) {
+    if (!c || !llr || B < 1 || T < 1 || !params || !loss || ckpt_every < 1 || !(clip > 0.0f) || clip > 60000.0f ||
+        (msg != LDPC_MSG_F32 && msg != LDPC_MSG_F16)) {
+        set_error("need code, llr, B >= 1, T >= 1, params, loss, ckpt_every >= 1, 0 < clip <= 60000, F32/F16");
+        return LDPC_EINVAL;
+    }
+    if (pointer_kind(llr) != 0 || pointer_kind(params) != 0 || pointer_kind(loss) != 0 ||
+        (post && pointer_kind(post) != 0)) {
+        set_error("ldpc_noms_forward takes device buffers");
+        return LDPC_EINVAL;
+    }
+    if (!c->noms) {
+        c->noms = new (std::nothrow) ldpc_noms_state();
+        if (!c->noms) {
+            set_error("host allocation failed");
+            return LDPC_ENOMEM;
+        }
+    }
+    ldpc_noms_state &w = *c->noms;
+    const int nck = (T - 1) / ckpt_every;
+    ldpc_status st = nm_alloc(c, w, (size_t)B, (size_t)std::max(nck, 1), (size_t)std::max(ckpt_every - 1, 1));
+    if (st != LDPC_OK) return st;
+    w.B = B;
+    w.T = T;
+    w.k = ckpt_every;
+    w.P = (B + 31) / 32;
+    w.msg = msg;
+    w.clip = clip;
+    w.params = params;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = pack_frames_w32(llr, w.mu, B, c->d.N, clip, s);
+    if (st != LDPC_OK) return st;
+    st = msg == LDPC_MSG_F16 ? nm_forward<__half>(c, w, post, s) : nm_forward<float>(c, w, post, s);
+    if (st != LDPC_OK) return st;
+    nm_loss_out<<<1, 1, 0, s>>>(w.acc, loss);
+    count_launch();
+    if (post) {
+        st = unpack_frames_w32(w.postbuf, post, B, c->d.N, s);
+        if (st != LDPC_OK) return st;
+    }
+    w.have_forward = true;
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_noms_backward(ldpc_code c, const float *params, float *grad, void *stream) {
+    if (!c || !params || !grad) {
+        set_error("need code, params and grad");
+        return LDPC_EINVAL;
+    }
+    if (!c->noms || !c->noms->have_forward || c->noms->params != params) {
+        set_error("ldpc_noms_backward needs the matching ldpc_noms_forward on this code object first");
+        return LDPC_EINVAL;
+    }
+    if (pointer_kind(grad) != 0) {
+        set_error("grad must be device memory");
+        return LDPC_EINVAL;
+    }
+    ldpc_noms_state &w = *c->noms;
+    cudaStream_t s = (cudaStream_t)stream;
+    return w.msg == LDPC_MSG_F16 ? nm_backward<__half>(c, w, grad, s) : nm_backward<float>(c, w, grad, s);
+}
+
+}  // extern "C"
+
+namespace ldpc {
+void noms_free(ldpc_noms_state *w) {
+    if (!w) return;
+    cudaFree(w->mu); cudaFree(w->ping[0]); cudaFree(w->ping[1]); cudaFree(w->ckpt); cudaFree(w->seg);
+    cudaFree(w->A); cudaFree(w->GA); cudaFree(w->GB); cudaFree(w->postbuf); cudaFree(w->acc);
+    delete w;
+}
+}  // namespace ldpc

@@ -34,10 +34,11 @@ namespace ldpc {
 // backward computation of Sec. IV-A), never "total minus own": that
 // subtraction loses the small terms when one input is unreliable.
 // ---------------------------------------------------------------------------
-template <int DCMAX, int V, bool FIRST, bool SYN, bool XF>
+template <int DCMAX, int V, bool FIRST, bool SYN, bool XF, bool NOMS>
 __global__ void __launch_bounds__(kWarps * 32)
 cn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict__ mu,
-             const uint32_t *__restrict__ hw, uint32_t *__restrict__ flags, float clip, int par) {
+             const uint32_t *__restrict__ hw, uint32_t *__restrict__ flags, float clip, int par,
+             const float *__restrict__ nparams) {
     constexpr int W = 32 * V;
     const int lane = threadIdx.x & 31;
     const int m = blockIdx.x * kWarps + (threadIdx.x >> 5);
@@ -88,7 +89,7 @@ cn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict
             }
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                ph[l][v] = (XF && !FIRST) ? fabsf(x[v]) : phi_f(fabsf(x[v]));
+                ph[l][v] = (NOMS || (XF && !FIRST)) ? fabsf(x[v]) : phi_f(fabsf(x[v]));
                 neg[v] |= (x[v] < 0.0f ? 1u : 0u) << l;
             }
             if (SYN) {
@@ -104,6 +105,43 @@ cn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict
             if (bad) atomicOr(F.unsat(par) + v, bad);
         }
     }
+    uint32_t par_all[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) par_all[v] = __popc(neg[v]) & 1u;
+    if (NOMS) {
+        // normalized/offset min-sum: ph[] holds |beta|; alpha = sign * max(w * m - o, 0)
+        float mn1[V], mn2[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) mn1[v] = mn2[v] = INFINITY;
+#pragma unroll
+        for (int l = 0; l < DCMAX; ++l) {
+            const bool on = l < d.L && sh[l] >= 0;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                if (!on) ph[l][v] = INFINITY;
+                mn2[v] = fminf(mn2[v], fmaxf(mn1[v], ph[l][v]));
+                mn1[v] = fminf(mn1[v], ph[l][v]);
+            }
+        }
+        const float *prm = nparams + (size_t)j * d.L * 2;
+#pragma unroll
+        for (int l = 0; l < DCMAX; ++l) {
+            const bool on = l < d.L && sh[l] >= 0;
+            if (!on || !lane_on) continue;
+            int k = r + sh[l];
+            if (k >= d.p) k -= d.p;
+            const float w = __ldg(prm + 2 * l), ofs = __ldg(prm + 2 * l + 1);
+            float a[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const float m = ph[l][v] == mn1[v] ? mn2[v] : mn1[v];
+                const float mag = fminf(fmaxf(fmaf(w, m, -ofs), 0.0f), clip);
+                a[v] = (par_all[v] ^ ((neg[v] >> l) & 1u)) ? -mag : mag;
+            }
+            pmsg[(eo[l] + k) * 32] = Lane<V>::pack(a);
+        }
+        return;
+    }
     // prefix sums, then the backward sweep adds the suffix sums
     float pre[DCMAX][V];
     {
@@ -118,9 +156,6 @@ cn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict
                 acc[v] += ph[l][v];
             }
     }
-    uint32_t par_all[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) par_all[v] = __popc(neg[v]) & 1u;
     float suf[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) suf[v] = 0.0f;
@@ -446,6 +481,24 @@ __global__ void channel_frames_kernel(float *__restrict__ out, int N, int gamma,
     }
 }
 
+// [gamma][N] <-> [P][N][32] for the learned min-sum state (packages of 32 frames)
+ldpc_status pack_frames_w32(const float *llr, float *dst, int gamma, int N, float clip, cudaStream_t s) {
+    const int P = (gamma + 31) / 32;
+    dim3 blk(32, 8), grd((N + 31) / 32, P);
+    count_launch();
+    pack_llr_kernel<float><<<grd, blk, 0, s>>>(llr, dst, gamma, N, 32, P * 32, clip, 1.0f, clip);
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
+ldpc_status unpack_frames_w32(const float *src, float *dst, int gamma, int N, cudaStream_t s) {
+    dim3 blk(32, 8), grd((N + 31) / 32, (gamma + 31) / 32);
+    count_launch();
+    unpack_post_kernel<<<grd, blk, 0, s>>>(src, dst, gamma, N, 32);
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
 // the check-node transform on its own, for verification (ldpc_phi_eval)
 __global__ void phi_eval_kernel(const float *__restrict__ x, float *__restrict__ y, int n, int variant) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -535,14 +588,13 @@ ldpc_status qc_pack_llr(ldpc_code c, const float *llr, int gamma, const ldpc_dec
     return LDPC_OK;
 }
 
-template <int DCMAX, int V, bool FIRST, bool SYN>
-static void launch_cn_sp(ldpc_code c, int P, const ldpc_decode_opts &o, int par, cudaStream_t s) {
+template <int DCMAX, int V, bool NOMS>
+static void launch_cn_first(ldpc_code c, int P, const ldpc_decode_opts &o, cudaStream_t s) {
     dim3 grd((c->d.M + kWarps - 1) / kWarps, P);
-    // F32 storage carries sign(beta) * phi(|beta|) between the passes; F16 carries beta
-    // (its range cannot hold phi of reliable messages)
-    cn_sp_kernel<DCMAX, V, FIRST, SYN, V == 1><<<grd, kWarps * 32, 0, s>>>(c->d, (uint32_t *)c->ws.msg,
-                                                                   (const float *)c->ws.mu, c->ws.hw, c->ws.flags,
-                                                                   o.clip, par);
+    // F32 sum-product storage carries sign(beta) * phi(|beta|) between the passes; F16 and
+    // NOMS carry beta (FP16's range cannot hold phi of reliable messages)
+    cn_sp_kernel<DCMAX, V, true, false, V == 1 && !NOMS, NOMS><<<grd, kWarps * 32, 0, s>>>(
+        c->d, (uint32_t *)c->ws.msg, (const float *)c->ws.mu, c->ws.hw, c->ws.flags, o.clip, 0, o.noms_params);
 }
 template <int DCMAX, bool FIRST, bool SYN>
 static void launch_cn_ms(ldpc_code c, int P, int par, cudaStream_t s) {
@@ -553,21 +605,13 @@ static void launch_cn_ms(ldpc_code c, int P, int par, cudaStream_t s) {
 }
 
 template <int DCMAX>
-static void cn_dispatch(ldpc_code c, int P, const ldpc_decode_opts &o, bool first, bool syn, int par,
-                        cudaStream_t s) {
-    if (o.algo == LDPC_ALGO_MS) {
-        if (first) launch_cn_ms<DCMAX, true, false>(c, P, par, s);
-        else if (syn) launch_cn_ms<DCMAX, false, true>(c, P, par, s);
-        else launch_cn_ms<DCMAX, false, false>(c, P, par, s);
-    } else if (o.msg == LDPC_MSG_F16) {
-        if (first) launch_cn_sp<DCMAX, 2, true, false>(c, P, o, par, s);
-        else if (syn) launch_cn_sp<DCMAX, 2, false, true>(c, P, o, par, s);
-        else launch_cn_sp<DCMAX, 2, false, false>(c, P, o, par, s);
-    } else {
-        if (first) launch_cn_sp<DCMAX, 1, true, false>(c, P, o, par, s);
-        else if (syn) launch_cn_sp<DCMAX, 1, false, true>(c, P, o, par, s);
-        else launch_cn_sp<DCMAX, 1, false, false>(c, P, o, par, s);
-    }
+static void cn_first_dispatch(ldpc_code c, int P, const ldpc_decode_opts &o, cudaStream_t s) {
+    if (o.algo == LDPC_ALGO_MS) launch_cn_ms<DCMAX, true, false>(c, P, 0, s);
+    else if (o.algo == LDPC_ALGO_NOMS) {
+        if (o.msg == LDPC_MSG_F16) launch_cn_first<DCMAX, 2, true>(c, P, o, s);
+        else launch_cn_first<DCMAX, 1, true>(c, P, o, s);
+    } else if (o.msg == LDPC_MSG_F16) launch_cn_first<DCMAX, 2, false>(c, P, o, s);
+    else launch_cn_first<DCMAX, 1, false>(c, P, o, s);
 }
 
 ldpc_status qc_decode_device(ldpc_code c, int gamma, const ldpc_decode_opts &o, bool want_post, cudaStream_t s) {
@@ -585,12 +629,12 @@ ldpc_status qc_decode_device(ldpc_code c, int gamma, const ldpc_decode_opts &o, 
         const int slot_cn = prof_begin(0, s);
         if (it == 1) {
             // beta = mu: the first check pass reads the channel LLRs
-            if (dcm <= 8) cn_dispatch<8>(c, P, o, true, false, par, s);
-            else if (dcm <= 16) cn_dispatch<16>(c, P, o, true, false, par, s);
-            else if (dcm <= 24) cn_dispatch<24>(c, P, o, true, false, par, s);
-            else cn_dispatch<32>(c, P, o, true, false, par, s);
+            if (dcm <= 8) cn_first_dispatch<8>(c, P, o, s);
+            else if (dcm <= 16) cn_first_dispatch<16>(c, P, o, s);
+            else if (dcm <= 24) cn_first_dispatch<24>(c, P, o, s);
+            else cn_first_dispatch<32>(c, P, o, s);
         } else {
-            st = qc_cn_pipe(c, o, syn, par, s);
+            st = qc_cn_pipe(c, o, syn, par, it, s);
             if (st != LDPC_OK) return st;
         }
         prof_end(slot_cn, s);

@@ -20,6 +20,7 @@
 namespace ldpc {
 
 constexpr int kStages = 3;
+constexpr int kModeSP = 0, kModeMS = 1, kModeNOMS = 2;
 constexpr int kNV = 4;  // consecutive variables per variable-pass work item
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -48,10 +49,11 @@ struct CnStage {
 // check pass (iterations >= 2): sum-product (MS = false) or integer min-sum.
 // REG: every block of the row is present and L == DCMAX (regular QC code).
 // ---------------------------------------------------------------------------
-template <int DCMAX, int V, bool SYN, bool XF, bool MS, bool REG>
+template <int DCMAX, int V, bool SYN, bool XF, int MODE, bool REG>
 __global__ void __launch_bounds__(kWarps * 32)
 cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__restrict__ hw,
-               uint32_t *__restrict__ flags, const int *__restrict__ act, float clip, int par) {
+               uint32_t *__restrict__ flags, const int *__restrict__ act, float clip, int par,
+               const float *__restrict__ nparams) {
     using St = CnStage<DCMAX, V, SYN>;
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ int s_sh[kMaxJ * kMaxL], s_eo[kMaxJ * kMaxL];
@@ -128,7 +130,7 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
         uint32_t syn[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) syn[v] = 0u;
-        if constexpr (!MS) {
+        if constexpr (MODE == kModeSP) {
             float ph[DCMAX][V];
             uint32_t neg[V];
 #pragma unroll
@@ -179,6 +181,52 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
                 }
 #pragma unroll
                 for (int v = 0; v < V; ++v) suf[v] += ph[l][v];
+            }
+        } else if constexpr (MODE == kModeNOMS) {
+            // normalized/offset min-sum: alpha = sign * max(w * m - o, 0), (w, o) of this
+            // iteration and circulant (j, l); m = min over the other edges = (|beta| == min1 ? min2 : min1)
+            const int j = (item - (item / d.M) * d.M) / d.p;
+            const float *prm = nparams + (size_t)j * d.L * 2;
+            float ab[DCMAX][V], mn1[V], mn2[V];
+            uint32_t neg[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) mn1[v] = mn2[v] = INFINITY, neg[v] = 0u;
+#pragma unroll
+            for (int l = 0; l < DCMAX; ++l) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) ab[l][v] = INFINITY;
+                if (REG || off[l] >= 0) {
+                    float x[V];
+                    Lane<V>::unpack(S[l * 32 + lane], x);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const float a = fabsf(x[v]);
+                        ab[l][v] = a;
+                        neg[v] |= (x[v] < 0.0f ? 1u : 0u) << l;
+                        mn2[v] = fminf(mn2[v], fmaxf(mn1[v], a));
+                        mn1[v] = fminf(mn1[v], a);
+                        if (SYN) syn[v] ^= S[St::HW + l * V + v];
+                    }
+                }
+            }
+            uint32_t par_all[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) par_all[v] = __popc(neg[v]) & 1u;
+            if (lane_on) {
+#pragma unroll
+                for (int l = 0; l < DCMAX; ++l) {
+                    const int o = off[l];
+                    if (!REG && o < 0) continue;
+                    const float w = __ldg(prm + 2 * l), ofs = __ldg(prm + 2 * l + 1);
+                    float out[V];
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const float m = ab[l][v] == mn1[v] ? mn2[v] : mn1[v];
+                        const float mag = fminf(fmaxf(fmaf(w, m, -ofs), 0.0f), clip);
+                        out[v] = (par_all[v] ^ ((neg[v] >> l) & 1u)) ? -mag : mag;
+                    }
+                    gmsg[(size_t)o * 32] = Lane<V>::pack(out);
+                }
             }
         } else {
             // min-sum, 4 frames per lane word (V == 4)
@@ -516,25 +564,35 @@ int persistent_blocks(K kernel, size_t smem) {
 }
 }  // namespace
 
-template <int DCMAX, int V, bool SYN, bool XF, bool MS, bool REG>
-static void launch_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int par, cudaStream_t s) {
-    auto k = cn_pipe_kernel<DCMAX, V, SYN, XF, MS, REG>;
+template <int DCMAX, int V, bool SYN, bool XF, int MODE, bool REG>
+static void launch_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int par, int it, cudaStream_t s) {
+    auto k = cn_pipe_kernel<DCMAX, V, SYN, XF, MODE, REG>;
     const size_t smem = (size_t)kWarps * kStages * CnStage<DCMAX, V, SYN>::WORDS * 4;
     const int blocks = persistent_blocks(k, smem);
-    k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, c->ws.hw, c->ws.flags, c->ws.act, o.clip, par);
+    const float *np = o.noms_params ? o.noms_params + (size_t)(it - 1) * c->d.J * c->d.L * 2 : nullptr;
+    k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, c->ws.hw, c->ws.flags, c->ws.act, o.clip, par,
+                                        np);
 }
 
 template <int DCMAX, bool REG>
-static void cn_pipe_dispatch(ldpc_code c, const ldpc_decode_opts &o, bool syn, int par, cudaStream_t s) {
+static void cn_pipe_dispatch(ldpc_code c, const ldpc_decode_opts &o, bool syn, int par, int it, cudaStream_t s) {
     if (o.algo == LDPC_ALGO_MS) {
-        if (syn) launch_cn_pipe<DCMAX, 4, true, false, true, REG>(c, o, par, s);
-        else launch_cn_pipe<DCMAX, 4, false, false, true, REG>(c, o, par, s);
+        if (syn) launch_cn_pipe<DCMAX, 4, true, false, kModeMS, REG>(c, o, par, it, s);
+        else launch_cn_pipe<DCMAX, 4, false, false, kModeMS, REG>(c, o, par, it, s);
+    } else if (o.algo == LDPC_ALGO_NOMS) {
+        if (o.msg == LDPC_MSG_F16) {
+            if (syn) launch_cn_pipe<DCMAX, 2, true, false, kModeNOMS, REG>(c, o, par, it, s);
+            else launch_cn_pipe<DCMAX, 2, false, false, kModeNOMS, REG>(c, o, par, it, s);
+        } else {
+            if (syn) launch_cn_pipe<DCMAX, 1, true, false, kModeNOMS, REG>(c, o, par, it, s);
+            else launch_cn_pipe<DCMAX, 1, false, false, kModeNOMS, REG>(c, o, par, it, s);
+        }
     } else if (o.msg == LDPC_MSG_F16) {
-        if (syn) launch_cn_pipe<DCMAX, 2, true, false, false, REG>(c, o, par, s);
-        else launch_cn_pipe<DCMAX, 2, false, false, false, REG>(c, o, par, s);
+        if (syn) launch_cn_pipe<DCMAX, 2, true, false, kModeSP, REG>(c, o, par, it, s);
+        else launch_cn_pipe<DCMAX, 2, false, false, kModeSP, REG>(c, o, par, it, s);
     } else {
-        if (syn) launch_cn_pipe<DCMAX, 1, true, true, false, REG>(c, o, par, s);
-        else launch_cn_pipe<DCMAX, 1, false, true, false, REG>(c, o, par, s);
+        if (syn) launch_cn_pipe<DCMAX, 1, true, true, kModeSP, REG>(c, o, par, it, s);
+        else launch_cn_pipe<DCMAX, 1, false, true, kModeSP, REG>(c, o, par, it, s);
     }
 }
 
@@ -546,14 +604,13 @@ static bool regular_rows(const QcDesc &d, int dcmax) {
     return true;
 }
 
-ldpc_status qc_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, bool syn, int par, cudaStream_t s) {
+ldpc_status qc_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, bool syn, int par, int it, cudaStream_t s) {
     const QcDesc &d = c->d;
-    if (regular_rows(d, 24)) cn_pipe_dispatch<24, true>(c, o, syn, par, s);
-    else if (regular_rows(d, 6)) cn_pipe_dispatch<8, false>(c, o, syn, par, s);
-    else if (d.L <= 8) cn_pipe_dispatch<8, false>(c, o, syn, par, s);
-    else if (d.L <= 16) cn_pipe_dispatch<16, false>(c, o, syn, par, s);
-    else if (d.L <= 24) cn_pipe_dispatch<24, false>(c, o, syn, par, s);
-    else cn_pipe_dispatch<32, false>(c, o, syn, par, s);
+    if (regular_rows(d, 24)) cn_pipe_dispatch<24, true>(c, o, syn, par, it, s);
+    else if (d.L <= 8) cn_pipe_dispatch<8, false>(c, o, syn, par, it, s);
+    else if (d.L <= 16) cn_pipe_dispatch<16, false>(c, o, syn, par, it, s);
+    else if (d.L <= 24) cn_pipe_dispatch<24, false>(c, o, syn, par, it, s);
+    else cn_pipe_dispatch<32, false>(c, o, syn, par, it, s);
     LDPC_CUDA_TRY(cudaGetLastError());
     return LDPC_OK;
 }
@@ -572,6 +629,7 @@ template <int JMAX, bool STOP, bool POST, bool REG>
 static void vn_pipe_dispatch(ldpc_code c, const ldpc_decode_opts &o, int it, int par, cudaStream_t s) {
     if (o.algo == LDPC_ALGO_MS) launch_vn_pipe<JMAX, 4, STOP, POST, false, true, REG>(c, o, it, par, s);
     else if (o.msg == LDPC_MSG_F16) launch_vn_pipe<JMAX, 2, STOP, POST, false, false, REG>(c, o, it, par, s);
+    else if (o.algo == LDPC_ALGO_NOMS) launch_vn_pipe<JMAX, 1, STOP, POST, false, false, REG>(c, o, it, par, s);
     else launch_vn_pipe<JMAX, 1, STOP, POST, true, false, REG>(c, o, it, par, s);
 }
 

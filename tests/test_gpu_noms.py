@@ -1,0 +1,131 @@
+"""GPU parity of the learned normalized/offset min-sum: inference, loss, and the
+hand-written backward pass against the FP64 oracle gradient; checkpointing; and
+what training gains over plain min-sum (the same rule with w = 1, o = 0)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1204_0334_gb300 as p
+
+    p.lib()
+    return p
+
+
+def setup(J, L, p, seed):
+    shifts = synth.qc_shifts(J, L, p, seed=seed)
+    H = oracle.qc_parity_check(shifts, p)
+    rp, col = oracle.csr_rows(H)
+    return shifts, rp, col, oracle.circulant_index(rp, col, p, L)
+
+
+def rand_params(T, ncirc, seed):
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.uniform(0.6, 1.0, (T, ncirc)), rng.uniform(0.0, 0.6, (T, ncirc))], axis=-1).astype(
+        np.float32)
+
+
+def test_noms_inference_matches_oracle(pkg):
+    shifts, rp, col, cb = setup(4, 12, 31, 3)
+    code = pkg.QCCode(shifts, 31)
+    T = 8
+    prm = rand_params(T, 48, 1)
+    mu = synth.gaussian_llrs(100, code.N, seed=4, ebn0_db=2.5, rate=2 / 3)
+    o = pkg.default_opts(max_iter=T, algo=pkg.ALGO_NOMS, msg=pkg.MSG_F32)
+    prm_d = torch.from_numpy(prm).cuda()
+    o.noms_params = prm_d.data_ptr()
+    post = torch.empty((100, code.N), device="cuda")
+    hard = torch.empty((100, code.N), dtype=torch.uint8, device="cuda")
+    pkg.ldpc_decode(code.handle, torch.from_numpy(mu).cuda(), o, post, hard)
+    _, po, _ = oracle.noms(rp, col, cb, code.N, mu, T, prm.astype(np.float64), nthreads=8)
+    po = np.clip(po, -30, 30)
+    p = post.cpu().numpy()
+    assert np.max(np.abs(p - po) / np.maximum(1, np.abs(po))) < 1e-4
+    sure = np.abs(po) > 1e-3
+    assert np.array_equal(hard.cpu().numpy()[sure], (po < 0)[sure])
+
+
+@pytest.mark.parametrize("msg,ckpt", [(0, 1), (0, 3)])
+def test_noms_loss_and_gradient_match_oracle(pkg, msg, ckpt):
+    shifts, rp, col, cb = setup(3, 6, 32, 2)
+    code = pkg.QCCode(shifts, 32)
+    T, B = 5, 70
+    prm = rand_params(T, 18, 3)
+    mu = synth.gaussian_llrs(B, code.N, seed=5, ebn0_db=1.5, rate=0.5)
+    prm_d = torch.from_numpy(prm).cuda()
+    loss, post = pkg.ldpc_noms_forward(code.handle, torch.from_numpy(mu).cuda(), prm_d, msg, ckpt, 30.0, True)
+    grad = torch.zeros_like(prm_d)
+    pkg.ldpc_noms_backward(code.handle, prm_d, grad)
+    lo, po, go = oracle.noms(rp, col, cb, code.N, mu, T, prm.astype(np.float64), want_grad=True, nthreads=8)
+    assert abs(float(loss) - lo) <= 1e-5 * abs(lo)
+    assert np.max(np.abs(post.cpu().numpy() - po) / np.maximum(1, np.abs(po))) < 1e-4
+    g = grad.cpu().numpy().astype(np.float64)
+    scale = np.abs(go).max()
+    assert np.max(np.abs(g - go)) <= 1e-3 * scale, (np.max(np.abs(g - go)), scale)
+
+
+def test_noms_checkpointing_does_not_change_gradients(pkg):
+    shifts, rp, col, cb = setup(4, 8, 16, 6)
+    code = pkg.QCCode(shifts, 16)
+    T = 7
+    prm_d = torch.from_numpy(rand_params(T, 32, 8)).cuda()
+    llr = torch.from_numpy(synth.gaussian_llrs(96, code.N, seed=9, ebn0_db=2.0, rate=0.5)).cuda()
+    out = []
+    for k in (1, 2, 3, 7):
+        loss, _ = pkg.ldpc_noms_forward(code.handle, llr, prm_d, 0, k, 30.0)
+        g = torch.zeros_like(prm_d)
+        pkg.ldpc_noms_backward(code.handle, prm_d, g)
+        out.append((float(loss), g.cpu().numpy()))
+    for lk, gk in out[1:]:
+        assert lk == out[0][0]
+        assert np.allclose(gk, out[0][1], rtol=1e-5, atol=1e-9 * np.abs(out[0][1]).max())
+
+
+def test_noms_fp16_storage_gradient(pkg):
+    """FP16 storage of the saved messages: loss and gradient close to the FP64 oracle."""
+    shifts, rp, col, cb = setup(3, 6, 32, 2)
+    code = pkg.QCCode(shifts, 32)
+    T, B = 5, 64
+    prm = rand_params(T, 18, 4)
+    mu = synth.gaussian_llrs(B, code.N, seed=6, ebn0_db=1.5, rate=0.5)
+    prm_d = torch.from_numpy(prm).cuda()
+    loss, _ = pkg.ldpc_noms_forward(code.handle, torch.from_numpy(mu).cuda(), prm_d, pkg.MSG_F16, 2, 30.0)
+    grad = torch.zeros_like(prm_d)
+    pkg.ldpc_noms_backward(code.handle, prm_d, grad)
+    lo, _, go = oracle.noms(rp, col, cb, code.N, mu, T, prm.astype(np.float64), want_grad=True, nthreads=8)
+    assert abs(float(loss) - lo) <= 2e-3 * abs(lo)
+    g = grad.cpu().numpy()
+    assert np.linalg.norm(g - go) <= 5e-2 * np.linalg.norm(go)
+
+
+def test_backward_requires_forward(pkg):
+    code = pkg.QCCode(synth.qc_shifts(3, 6, 8, seed=1), 8)
+    prm = torch.ones((3, 18, 2), device="cuda")
+    with pytest.raises(pkg.LdpcError):
+        pkg.ldpc_noms_backward(code.handle, prm, torch.zeros_like(prm))
+
+
+def test_training_gains_over_plain_min_sum(pkg):
+    """A short training run (the simulator's own frames, Eb/N0 ~ U[2.5, 4.5]) lowers the loss and the
+    trained decoder makes fewer bit errors than the untrained rule (w = 1, o = 0, plain min-sum)."""
+    from paper_1204_0334_gb300 import noms
+
+    shifts = synth.qc_shifts(4, 24, 128, seed=2)
+    code = pkg.QCCode(shifts, 128)
+    T = 10
+    p0 = noms.init_params(T, 96)
+    params, losses = noms.train_noms(code, T=T, steps=60, batch=512, ebn0=(2.5, 4.5), lr=0.03, seed=3,
+                                     msg=pkg.MSG_F16, ckpt_every=2, params=p0)
+    assert np.mean(losses[-10:]) < 0.8 * np.mean(losses[:5])
+    base = noms.ber(code, p0, 3.5, frames=8192)
+    trained = noms.ber(code, params, 3.5, frames=8192)
+    assert trained["bit_errors"] < 0.5 * base["bit_errors"], (trained, base)
