@@ -94,7 +94,7 @@ def train_noms(code: QCCode, T: int = 10, steps: int = 200, batch: int = 1024, e
         opt.step()
         with torch.no_grad():
             p[..., 1].clamp_(min=0.0)
-        losses.append(float(loss))
+        losses.append(float(loss.detach()))
         if log and (it % max(1, steps // 10) == 0 or it == steps - 1):
             log(f"step {it}: loss {losses[-1]:.5f}")
     return p.detach(), losses

@@ -87,7 +87,8 @@ def test_noms_checkpointing_does_not_change_gradients(pkg):
         out.append((float(loss), g.cpu().numpy()))
     for lk, gk in out[1:]:
         assert lk == out[0][0]
-        assert np.allclose(gk, out[0][1], rtol=1e-5, atol=1e-9 * np.abs(out[0][1]).max())
+        # same values up to the order of the float atomic sums of the parameter gradients
+        assert np.allclose(gk, out[0][1], rtol=1e-5, atol=1e-6 * np.abs(out[0][1]).max())
 
 
 def test_noms_fp16_storage_gradient(pkg):
