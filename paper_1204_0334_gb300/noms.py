@@ -117,3 +117,94 @@ def ber(code: QCCode, params, ebn0_db: float, frames: int, seed: int = 99, gamma
     r["ber"] = r["bit_errors"] / (r["frames"] * code.N)
     r["fer"] = r["frame_errors"] / r["frames"]
     return r
+
+
+def clopper_pearson(k: int, n: int, conf: float = 0.95):
+    """Exact binomial confidence interval of a rate k/n."""
+    from scipy.stats import beta
+
+    a = 1.0 - conf
+    lo = 0.0 if k == 0 else float(beta.ppf(a / 2, k, n - k + 1))
+    hi = 1.0 if k == n else float(beta.ppf(1 - a / 2, k + 1, n - k))
+    return lo, hi
+
+
+def _timed_ber(code, opts, ebn0, frames, gamma, target_fe, seed=4242):
+    torch = _torch()
+    torch.cuda.synchronize()
+    r = ldpc_ber_sim(code.handle, ebn0, seed, 0, frames, target_fe, gamma, opts)
+    r["mbit_s"] = r["frames"] * code.K / r["seconds"] / 1e6
+    nb = r["frames"] * code.N
+    r["ber"] = r["bit_errors"] / nb
+    r["ber_ci95"] = clopper_pearson(r["bit_errors"], nb)
+    r["fer"] = r["frame_errors"] / r["frames"]
+    return r
+
+
+def evaluate(code, params, ebn0_points, frames=1 << 20, gamma=8192, target_fe=100, sp_iters=30):
+    """BER, 95% CI and Mbit/s of trained NOMS, untrained min-sum and sum-product at each Eb/N0."""
+    T = params.shape[0]
+    ncirc = params.shape[1]
+    plain = init_params(T, ncirc)
+    out = {}
+    for e in ebn0_points:
+        row = {}
+        o = default_opts(max_iter=sp_iters, early_stop=1, msg=MSG_F32)
+        row[f"sp{sp_iters}_f32"] = _timed_ber(code, o, e, frames, gamma, target_fe)
+        for name, prm in (("noms_trained", params), ("minsum_untrained", plain)):
+            o = default_opts(max_iter=T, early_stop=1, algo=ALGO_NOMS, msg=MSG_F16)
+            o.noms_params = prm.contiguous().data_ptr()
+            row[f"{name}_{T}it_f16"] = _timed_ber(code, o, e, frames, gamma, target_fe)
+        out[str(e)] = row
+    return out
+
+
+def main(argv=None):
+    import argparse
+    import json
+    import time
+
+    import numpy as np
+
+    torch = _torch()
+    ap = argparse.ArgumentParser(description="train the learned normalized/offset min-sum and compare it with "
+                                             "sum-product on a seeded QC code")
+    ap.add_argument("--J", type=int, default=4)
+    ap.add_argument("--L", type=int, default=24)
+    ap.add_argument("--p", type=int, default=765)
+    ap.add_argument("--shift-seed", type=int, default=2)
+    ap.add_argument("--T", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=256)
+    ap.add_argument("--batch", type=int, default=4096)
+    ap.add_argument("--lr", type=float, default=0.02)
+    ap.add_argument("--ebn0", type=float, nargs="*", default=[3.0, 3.25, 3.5])
+    ap.add_argument("--eval-frames", type=int, default=1 << 20)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args(argv)
+    import sys
+    import os
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import synth
+
+    code = QCCode(synth.qc_shifts(a.J, a.L, a.p, seed=a.shift_seed), a.p)
+    t0 = time.time()
+    params, losses = train_noms(code, T=a.T, steps=a.steps, batch=a.batch, lr=a.lr, log=print)
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    res = {"code": f"QC {a.J}x{a.L} p={a.p} n={code.N}", "T": a.T,
+           "training": {"frames": a.steps * a.batch, "seconds": train_s, "loss_first": losses[0],
+                        "loss_last": float(np.mean(losses[-10:]))},
+           "eval": evaluate(code, params, a.ebn0, frames=a.eval_frames),
+           "params_w_mean_per_iter": params[..., 0].mean(dim=1).tolist(),
+           "params_o_mean_per_iter": params[..., 1].mean(dim=1).tolist()}
+    print(json.dumps(res, indent=1))
+    if a.out:
+        with open(a.out, "w") as fh:
+            json.dump(res, fh, indent=1)
+
+
+if __name__ == "__main__":
+    main()
