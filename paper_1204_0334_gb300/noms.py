@@ -141,20 +141,32 @@ def _timed_ber(code, opts, ebn0, frames, gamma, target_fe, seed=4242):
     return r
 
 
-def evaluate(code, params, ebn0_points, frames=1 << 20, gamma=8192, target_fe=100, sp_iters=30):
-    """BER, 95% CI and Mbit/s of trained NOMS, untrained min-sum and sum-product at each Eb/N0."""
+def extend_params(params, iters: int):
+    """[iters][ncirc][2]: the trained rows, then the last trained row repeated for the later iterations."""
+    torch = _torch()
+    T = params.shape[0]
+    if iters <= T:
+        return params[:iters].contiguous()
+    return torch.cat([params, params[-1:].expand(iters - T, -1, -1)], dim=0).contiguous()
+
+
+def evaluate(code, params, ebn0_points, frames=1 << 20, gamma=8192, target_fe=100, sp_iters=30, long_iters=30):
+    """BER, 95% CI and Mbit/s at each Eb/N0 of: sum-product (sp_iters, FP32), the trained NOMS over its
+    T trained iterations and over long_iters (last trained row reused), and untrained min-sum (w=1, o=0)."""
     T = params.shape[0]
     ncirc = params.shape[1]
     plain = init_params(T, ncirc)
+    cases = [("noms_trained", params, T), ("noms_trained", extend_params(params, long_iters), long_iters),
+             ("minsum_untrained", plain, T)]
     out = {}
     for e in ebn0_points:
         row = {}
         o = default_opts(max_iter=sp_iters, early_stop=1, msg=MSG_F32)
         row[f"sp{sp_iters}_f32"] = _timed_ber(code, o, e, frames, gamma, target_fe)
-        for name, prm in (("noms_trained", params), ("minsum_untrained", plain)):
-            o = default_opts(max_iter=T, early_stop=1, algo=ALGO_NOMS, msg=MSG_F16)
+        for name, prm, it in cases:
+            o = default_opts(max_iter=it, early_stop=1, algo=ALGO_NOMS, msg=MSG_F16)
             o.noms_params = prm.contiguous().data_ptr()
-            row[f"{name}_{T}it_f16"] = _timed_ber(code, o, e, frames, gamma, target_fe)
+            row[f"{name}_{it}it_f16"] = _timed_ber(code, o, e, frames, gamma, target_fe)
         out[str(e)] = row
     return out
 
