@@ -107,6 +107,27 @@ ldpc_status ldpc_decode(ldpc_code code, const float *llr, int32_t gamma, const l
                         float *post, uint8_t *hard, int32_t *iters, int32_t *ok, void *stream);
 
 /*
+ * ldpc_decode_noalloc -- ldpc_decode for callers that cannot allocate device
+ * memory (for example code running under a stream capture that must not add
+ * allocation nodes, real-time loops that cannot afford a synchronous
+ * cudaMalloc, or processes whose device memory is reserved up front by another
+ * allocator).  The paper has no counterpart.  Same arguments and results as
+ * ldpc_decode, but every buffer must be device memory and the decoder's
+ * workspace comes from a fixed 16 MiB array inside the library (held on every
+ * GPU that loads it until the process exits); the call itself calls no
+ * cudaMalloc/cudaFree.  A decode of gamma frames needs about
+ * (4E + 8N + N/8) * gamma bytes (rounded up to 128 frames): requests beyond
+ * the array return LDPC_EINVAL with the size in ldpc_last_error().  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * All calls share the array, and each decode initializes what it reads, but
+ * calls whose GPU work overlaps (other streams or threads) race on it.
+ * Sum-product (F32/F16 storage) and integer min-sum; LDPC_EUNSUPPORTED for NOMS.
+ */
+ldpc_status ldpc_decode_noalloc(ldpc_code code, const float *llr, int32_t gamma, const ldpc_decode_opts *opts,
+                                float *post, uint8_t *hard, int32_t *iters, int32_t *ok, void *stream);
+
+/*
  * ldpc_channel -- the device-side channel of Sec. V (codeword and noise made
  * on the GPU): the all-zero codeword sent as BPSK x = +1 over AWGN, Sec. II-B,
  * y = 1 + sigma g, mu = 2 y / sigma^2, with sigma^2 = 1 / (2 R 10^(EbN0/10))

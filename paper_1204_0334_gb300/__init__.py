@@ -57,6 +57,7 @@ _SIGNATURES = [
     ("ldpc_code_destroy", ctypes.c_int, [P]),
     ("ldpc_code_dims", ctypes.c_int, [P, P, P, P, P]),
     ("ldpc_decode", ctypes.c_int, [P, P, ctypes.c_int32, P, P, P, P, P, P]),
+    ("ldpc_decode_noalloc", ctypes.c_int, [P, P, ctypes.c_int32, P, P, P, P, P, P]),
     ("ldpc_channel", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, P, P]),
     ("ldpc_ber_sim", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
                                     ctypes.c_int64, ctypes.c_int32, P, P, P]),
@@ -154,6 +155,13 @@ def ldpc_decode(code: int, llr, opts: DecodeOpts, post=None, hard=None, iters=No
     gamma = llr.shape[0]
     _check(lib().ldpc_decode(code, _ptr(llr), gamma, ctypes.byref(opts), _ptr(post), _ptr(hard), _ptr(iters),
                              _ptr(ok), _stream(stream)), "ldpc_decode")
+
+
+def ldpc_decode_noalloc(code: int, llr, opts: DecodeOpts, post=None, hard=None, iters=None, ok=None, stream=None):
+    """ldpc_decode with the library's fixed scratch instead of allocated workspace (device buffers only)."""
+    gamma = llr.shape[0]
+    _check(lib().ldpc_decode_noalloc(code, _ptr(llr), gamma, ctypes.byref(opts), _ptr(post), _ptr(hard),
+                                     _ptr(iters), _ptr(ok), _stream(stream)), "ldpc_decode_noalloc")
 
 
 def ldpc_channel(code: int, ebn0_db: float, seed: int, first_frame: int, out, stream=None):
