@@ -42,6 +42,7 @@ typedef enum {
 
 typedef struct ldpc_code_s *ldpc_code;
 typedef struct ldpccc_s *ldpccc;
+typedef struct ldpc_batch_s *ldpc_batch;
 
 /* Check-node rule. */
 enum {
@@ -126,6 +127,32 @@ ldpc_status ldpc_decode(ldpc_code code, const float *llr, int32_t gamma, const l
  */
 ldpc_status ldpc_decode_noalloc(ldpc_code code, const float *llr, int32_t gamma, const ldpc_decode_opts *opts,
                                 float *post, uint8_t *hard, int32_t *iters, int32_t *ok, void *stream);
+
+/*
+ * Heterogeneous batches (no paper counterpart; the paper decodes one code at a
+ * time, Sec. IV-A).  ldpc_batch_create plans a batch of ncodes QC codes (J <= 4,
+ * L <= 24), code i with gammas[i] frames, all decoded with the same options
+ * (sum-product with F32/F16 storage or integer min-sum; early stop as in
+ * opts).  The codes must outlive the batch.  The batch owns one device
+ * workspace for all codes.  ldpc_batch_decode runs Algorithm 1 on every code
+ * with a shared iteration loop: per iteration one check-pass and one
+ * variable-pass launch over the tiles (code, package, row/variable range) of
+ * every package that still has a running frame, listed again after each
+ * variable pass.  The loop is captured into a CUDA graph on the second call
+ * and replayed afterwards; the first call also tunes the tile sizes by timing
+ * three candidates on its frames (ldpc_batch_info reports the choice).
+ *   llr: host array of ncodes device pointers, [gammas[i]][N_i] float each.
+ *   hard / iters / ok: host arrays of ncodes device pointers (entries or the
+ *   arrays may be NULL): [gammas[i]][N_i] uint8, [gammas[i]] int32, int32.
+ * Errors: LDPC_EINVAL, LDPC_EUNSUPPORTED (NOMS, larger degrees), LDPC_ENOMEM.
+ */
+ldpc_status ldpc_batch_create(const ldpc_code *codes, int32_t ncodes, const int32_t *gammas,
+                              const ldpc_decode_opts *opts, ldpc_batch *out);
+ldpc_status ldpc_batch_decode(ldpc_batch batch, const float *const *llr, uint8_t *const *hard,
+                              int32_t *const *iters, int32_t *const *ok, void *stream);
+/* tile rows of the check pass, variable groups of the variable pass, tuning times (ms) of the 3 candidates */
+ldpc_status ldpc_batch_info(ldpc_batch batch, int32_t *tile_rows, int32_t *tile_groups, double *tune_ms3);
+ldpc_status ldpc_batch_destroy(ldpc_batch batch);
 
 /*
  * ldpc_channel -- the device-side channel of Sec. V (codeword and noise made

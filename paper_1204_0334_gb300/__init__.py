@@ -58,6 +58,10 @@ _SIGNATURES = [
     ("ldpc_code_dims", ctypes.c_int, [P, P, P, P, P]),
     ("ldpc_decode", ctypes.c_int, [P, P, ctypes.c_int32, P, P, P, P, P, P]),
     ("ldpc_decode_noalloc", ctypes.c_int, [P, P, ctypes.c_int32, P, P, P, P, P, P]),
+    ("ldpc_batch_create", ctypes.c_int, [P, ctypes.c_int32, P, P, P]),
+    ("ldpc_batch_decode", ctypes.c_int, [P, P, P, P, P, P]),
+    ("ldpc_batch_info", ctypes.c_int, [P, P, P, P]),
+    ("ldpc_batch_destroy", ctypes.c_int, [P]),
     ("ldpc_channel", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, P, P]),
     ("ldpc_ber_sim", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
                                     ctypes.c_int64, ctypes.c_int32, P, P, P]),
@@ -279,6 +283,42 @@ def ldpc_noms_forward(code: int, llr, params, msg: int = MSG_F32, ckpt_every: in
 
 def ldpc_noms_backward(code: int, params, grad, stream=None):
     _check(lib().ldpc_noms_backward(code, _ptr(params), _ptr(grad), _stream(stream)), "ldpc_noms_backward")
+
+
+def _ptr_array(ts):
+    arr = (ctypes.c_void_p * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = None if t is None else t.data_ptr()
+    return arr
+
+
+def ldpc_batch_create(codes, gammas, opts: DecodeOpts) -> int:
+    """codes: list of ldpc_code handles (or QCCode objects); gammas: frames per code."""
+    hs = (ctypes.c_void_p * len(codes))(*[getattr(c, "handle", c) for c in codes])
+    g = (ctypes.c_int32 * len(gammas))(*gammas)
+    h = ctypes.c_void_p()
+    _check(lib().ldpc_batch_create(hs, len(codes), g, ctypes.byref(opts), ctypes.byref(h)), "ldpc_batch_create")
+    return h.value
+
+
+def ldpc_batch_decode(batch: int, llrs, hards=None, iters=None, oks=None, stream=None):
+    """llrs / hards / iters / oks: lists (one device tensor per code) or None."""
+    la = _ptr_array(llrs)
+    ha = _ptr_array(hards) if hards is not None else None
+    ia = _ptr_array(iters) if iters is not None else None
+    oa = _ptr_array(oks) if oks is not None else None
+    _check(lib().ldpc_batch_decode(batch, la, ha, ia, oa, _stream(stream)), "ldpc_batch_decode")
+
+
+def ldpc_batch_info(batch: int) -> dict:
+    tr, tg = ctypes.c_int32(), ctypes.c_int32()
+    ms = (ctypes.c_double * 3)()
+    _check(lib().ldpc_batch_info(batch, ctypes.byref(tr), ctypes.byref(tg), ms), "ldpc_batch_info")
+    return {"tile_rows": tr.value, "tile_groups": tg.value, "tune_ms": list(ms)}
+
+
+def ldpc_batch_destroy(batch: int):
+    _check(lib().ldpc_batch_destroy(batch), "ldpc_batch_destroy")
 
 
 class Profile(ctypes.Structure):

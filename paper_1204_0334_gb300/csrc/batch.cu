@@ -1,0 +1,890 @@
+// Heterogeneous batches: many QC codes, each with its own number of frames,
+// decoded together (Algorithm 1 for every code, one shared iteration loop).
+//
+// Every code keeps the single-code layout (packages of W = 32*V frames,
+// msg [P][E][32], mu [P][N][W], hw [P][N][V], flags) inside one workspace.
+// Work is a list of tiles (code, package, first row or variable group, count):
+// after every variable pass a compaction kernel lists the tiles of the
+// packages that still have a running frame, across all codes, so one
+// persistent check-pass launch and one variable-pass launch per iteration
+// serve the whole batch and converged packages of any code drop out
+// (active-frame compaction at package granularity).  Warps stage each item's
+// 128-byte edge packages with cp.async into a shared-memory ring, as the
+// single-code passes do; codes are read from a device table (their shift and
+// edge-offset tables sit in global memory, cached in L1).
+//
+// The iteration loop (check pass, variable pass, compaction) is captured once
+// into a CUDA graph and replayed by later calls.  The first call tunes the tile
+// sizes (rows per check-pass tile, variable groups per variable-pass tile) by
+// timing a few iterations of each candidate on the call's own frames.
+#include "qc_device.cuh"
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+namespace ldpc {
+
+struct BCode {
+    int J, L, p, N, M, E, P, gamma, tab;
+    long long msg, mu, hw, flags, iters;  // offsets (words / ints) into the shared regions
+};
+
+struct BTile {
+    int code, pk, start, count;
+};
+
+constexpr int kBStages = 3;
+constexpr int kBDC = 24;  // largest row degree of a batch
+constexpr int kBJ = 4;    // largest column degree of a batch
+constexpr int kBNV = 4;   // variables per variable-pass item
+
+__device__ __forceinline__ uint32_t b_smem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void b_cp16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(b_smem(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void b_cp4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(b_smem(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void b_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void b_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int V, bool SYN, bool FIRST, bool MS>
+struct BCnStage {
+    static constexpr int MUW = MS ? 32 : 32 * V;     // words of one channel-LLR package
+    static constexpr int SEGW = FIRST ? MUW : 32;    // words per edge in the stage
+    static constexpr int SEG = kBDC * SEGW;
+    static constexpr int OFF = SEG;                  // [l]: edge offset in the package or -1
+    static constexpr int HW = OFF + kBDC;
+    static constexpr int FL = HW + (SYN ? kBDC * V : 0);
+    static constexpr int WORDS = (FL + V + 3) & ~3;
+};
+
+// ---------------------------------------------------------------------------
+// check pass over all codes (FIRST: beta = mu)
+// ---------------------------------------------------------------------------
+template <int V, bool SYN, bool XF, bool MS, bool FIRST>
+__global__ void __launch_bounds__(kWarps * 32)
+bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const int *__restrict__ eotab,
+           uint32_t *__restrict__ msg, const uint32_t *__restrict__ mu, const uint32_t *__restrict__ hw,
+           uint32_t *__restrict__ flags, const int *__restrict__ tcount, const BTile *__restrict__ tiles, int TR,
+           float clip, int par) {
+    using St = BCnStage<V, SYN, FIRST, MS>;
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *ring = smem + warp * kBStages * St::WORDS;
+    const int total = *tcount * TR;
+    const int GW = gridDim.x * kWarps;
+    int item = blockIdx.x * kWarps + warp;
+
+    auto issue = [&](int it, int slot) {
+        if (it < total) {
+            const BTile tl = tiles[it / TR];
+            const int ri = it - (it / TR) * TR;
+            if (ri < tl.count) {
+                const BCode C = codes[tl.code];
+                const int m = tl.start + ri;
+                const int j = m / C.p, r = m - j * C.p;
+                uint32_t *dst = ring + slot * St::WORDS;
+                int *off = reinterpret_cast<int *>(dst + St::OFF);
+                const uint32_t *gsrc = FIRST ? mu + C.mu + (size_t)tl.pk * C.N * St::MUW
+                                             : msg + C.msg + (size_t)tl.pk * C.E * 32;
+                const int g = lane >> 3, sub = lane & 7;
+#pragma unroll
+                for (int q = 0; q < kBDC / 4; ++q) {
+                    const int l = 4 * q + g;
+                    const int sh = l < C.L ? __ldg(shtab + C.tab + j * C.L + l) : -1;
+                    int o = -1;
+                    if (sh >= 0) {
+                        int k = r + sh;
+                        if (k >= C.p) k -= C.p;
+                        o = __ldg(eotab + C.tab + j * C.L + l) + k;
+                        if (FIRST) {
+                            const int n = l * C.p + k;
+#pragma unroll
+                            for (int h = 0; h < St::MUW / 32; ++h)
+                                b_cp16(dst + l * St::SEGW + h * 32 + sub * 4, gsrc + (size_t)n * St::MUW + h * 32 + sub * 4);
+                        } else {
+                            b_cp16(dst + l * 32 + sub * 4, gsrc + (size_t)o * 32 + sub * 4);
+                        }
+                    }
+                    if (sub == 0) off[l] = o;
+                }
+                if (SYN) {
+                    for (int w = lane; w < kBDC * V; w += 32) {
+                        const int l = w / V, v = w - l * V;
+                        const int sh = l < C.L ? __ldg(shtab + C.tab + j * C.L + l) : -1;
+                        if (sh >= 0) {
+                            int k = r + sh;
+                            if (k >= C.p) k -= C.p;
+                            b_cp4(dst + St::HW + w, hw + C.hw + ((size_t)tl.pk * C.N + (size_t)l * C.p + k) * V + v);
+                        }
+                    }
+                }
+                if (lane < V) b_cp4(dst + St::FL + lane, flags + C.flags + (size_t)tl.pk * 5 * V + lane);
+            }
+        }
+        b_commit();
+    };
+
+#pragma unroll
+    for (int s = 0; s < kBStages - 1; ++s) issue(item + s * GW, s);
+    int slot = 0;
+    for (; item < total; item += GW) {
+        issue(item + (kBStages - 1) * GW, (slot + kBStages - 1) % kBStages);
+        b_wait<kBStages - 1>();
+        __syncwarp();
+        const BTile tl = tiles[item / TR];
+        const int ri = item - (item / TR) * TR;
+        if (ri < tl.count) {
+            const BCode C = codes[tl.code];
+            const uint32_t *S = ring + slot * St::WORDS;
+            const int *off = reinterpret_cast<const int *>(S + St::OFF);
+            uint32_t *gmsg = msg + C.msg + (size_t)tl.pk * C.E * 32 + lane;
+            uint32_t actv[V], syn[V];
+            bool lane_on = false;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                actv[v] = ~S[St::FL + v];
+                lane_on |= (actv[v] >> lane) & 1u;
+                syn[v] = 0u;
+            }
+            if constexpr (!MS) {
+                float ph[kBDC][V];
+                uint32_t neg[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) neg[v] = 0u;
+#pragma unroll
+                for (int l = 0; l < kBDC; ++l) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) ph[l][v] = 0.0f;
+                    if (off[l] >= 0) {
+                        float x[V];
+                        if (FIRST) {
+                            const float *mf = reinterpret_cast<const float *>(S + l * St::SEGW) + lane * V;
+#pragma unroll
+                            for (int v = 0; v < V; ++v) x[v] = mf[v];
+                        } else {
+                            Lane<V>::unpack(S[l * 32 + lane], x);
+                        }
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            ph[l][v] = (XF && !FIRST) ? fabsf(x[v]) : phi_f(fabsf(x[v]));
+                            neg[v] |= (x[v] < 0.0f ? 1u : 0u) << l;
+                            if (SYN) syn[v] ^= S[St::HW + l * V + v];
+                        }
+                    }
+                }
+                float pre[kBDC][V];
+                {
+                    float acc[V];
+#pragma unroll
+                    for (int v = 0; v < V; ++v) acc[v] = 0.0f;
+#pragma unroll
+                    for (int l = 0; l < kBDC; ++l)
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            pre[l][v] = acc[v];
+                            acc[v] += ph[l][v];
+                        }
+                }
+                uint32_t par_all[V];
+                float suf[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) par_all[v] = __popc(neg[v]) & 1u, suf[v] = 0.0f;
+#pragma unroll
+                for (int l = kBDC - 1; l >= 0; --l) {
+                    const int o = off[l];
+                    if (o >= 0) {
+                        float out[V];
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            const float mag = fminf(phi_f(pre[l][v] + suf[v]), clip);
+                            out[v] = (par_all[v] ^ ((neg[v] >> l) & 1u)) ? -mag : mag;
+                        }
+                        if (lane_on) gmsg[(size_t)o * 32] = Lane<V>::pack(out);
+                    }
+#pragma unroll
+                    for (int v = 0; v < V; ++v) suf[v] += ph[l][v];
+                }
+            } else {
+                uint32_t ab[kBDC], sg[kBDC];
+                uint32_t min1 = 0x7f7f7f7fu, min2 = 0x7f7f7f7fu, sgn = 0u;
+#pragma unroll
+                for (int l = 0; l < kBDC; ++l) {
+                    ab[l] = 0u;
+                    sg[l] = 0u;
+                    if (off[l] >= 0) {
+                        const uint32_t x = S[l * St::SEGW + lane];
+                        const uint32_t av = __vabsss4(x);
+                        sg[l] = x & 0x80808080u;
+                        ab[l] = av;
+                        sgn ^= sg[l];
+                        min2 = __vminu4(min2, __vmaxu4(min1, av));
+                        min1 = __vminu4(min1, av);
+                        if (SYN) {
+#pragma unroll
+                            for (int v = 0; v < V; ++v) syn[v] ^= S[St::HW + l * V + v];
+                        }
+                    }
+                }
+                if (lane_on) {
+#pragma unroll
+                    for (int l = 0; l < kBDC; ++l) {
+                        const int o = off[l];
+                        if (o < 0) continue;
+                        const uint32_t eq = __vcmpeq4(ab[l], min1);
+                        const uint32_t mag = (min2 & eq) | (min1 & ~eq);
+                        const uint32_t sneg = ((sgn ^ sg[l]) >> 7) & 0x01010101u;
+                        gmsg[(size_t)o * 32] = __vadd4(mag ^ (sneg * 0xffu), sneg);
+                    }
+                }
+            }
+            if (SYN && lane == 0) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const uint32_t bad = syn[v] & actv[v];
+                    if (bad) atomicOr(flags + C.flags + (size_t)tl.pk * 5 * V + (1 + par) * V + v, bad);
+                }
+            }
+        }
+        __syncwarp();
+        slot = (slot + 1) % kBStages;
+    }
+    b_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
+// variable pass over all codes
+// ---------------------------------------------------------------------------
+template <int V, bool MS>
+struct BVnStage {
+    static constexpr int MUW = MS ? 32 : 32 * V;
+    static constexpr int MU = 0;
+    static constexpr int AL = kBNV * MUW;
+    static constexpr int HW = AL + kBNV * kBJ * 32;
+    static constexpr int FL = HW + kBNV * V;
+    static constexpr int WORDS = (FL + 2 * V + 3) & ~3;
+};
+
+template <int V, bool STOP, bool XF, bool MS>
+__global__ void __launch_bounds__(kWarps * 32)
+bvn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const int *__restrict__ eotab,
+           uint32_t *__restrict__ msg, const uint32_t *__restrict__ mu, uint32_t *__restrict__ hw,
+           uint32_t *__restrict__ flags, int32_t *__restrict__ iters, const int *__restrict__ tcount,
+           const BTile *__restrict__ tiles, int TG, float clip, int it, int par) {
+    using St = BVnStage<V, MS>;
+    constexpr int W = 32 * V;
+    constexpr int MU_SEGS = St::MUW / 32;
+    constexpr int NSEG = kBNV * (MU_SEGS + kBJ);
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *ring = smem + warp * kBStages * St::WORDS;
+    const int total = *tcount * TG;
+    const int GW = gridDim.x * kWarps;
+    int item = blockIdx.x * kWarps + warp;
+
+    auto issue = [&](int itm, int slot) {
+        if (itm < total) {
+            const BTile tl = tiles[itm / TG];
+            const int gi = itm - (itm / TG) * TG;
+            if (gi < tl.count) {
+                const BCode C = codes[tl.code];
+                const int n0 = (tl.start + gi) * kBNV;
+                const int l0 = n0 / C.p, k0 = n0 - l0 * C.p;
+                uint32_t *dst = ring + slot * St::WORDS;
+                const uint32_t *gmsg = msg + C.msg + (size_t)tl.pk * C.E * 32;
+                const uint32_t *gmu = mu + C.mu + (size_t)tl.pk * C.N * St::MUW;
+                const int grp = lane >> 3, sub = lane & 7;
+#pragma unroll
+                for (int s0 = 0; s0 < NSEG; s0 += 4) {
+                    const int s = s0 + grp;
+                    if (s < kBNV * MU_SEGS) {
+                        const int i = s / MU_SEGS, h = s - i * MU_SEGS;
+                        const int n = n0 + i;
+                        if (n < C.N)
+                            b_cp16(dst + St::MU + i * St::MUW + h * 32 + sub * 4,
+                                   gmu + (size_t)n * St::MUW + h * 32 + sub * 4);
+                    } else if (s < NSEG) {
+                        const int t = s - kBNV * MU_SEGS;
+                        const int i = t / kBJ, jj = t - i * kBJ;
+                        const int n = n0 + i;
+                        int l = l0, k = k0 + i;
+                        if (k >= C.p) k -= C.p, ++l;
+                        if (n < C.N && jj < C.J) {
+                            const int sh = __ldg(shtab + C.tab + jj * C.L + l);
+                            if (sh >= 0)
+                                b_cp16(dst + St::AL + (i * kBJ + jj) * 32 + sub * 4,
+                                       gmsg + (size_t)(__ldg(eotab + C.tab + jj * C.L + l) + k) * 32 + sub * 4);
+                        }
+                    }
+                }
+                if (lane < kBNV * V) {
+                    const int i = lane / V, v = lane - i * V;
+                    const int n = n0 + i;
+                    if (n < C.N) b_cp4(dst + St::HW + lane, hw + C.hw + ((size_t)tl.pk * C.N + n) * V + v);
+                } else if (lane >= 32 - 2 * V) {
+                    const int q = lane - (32 - 2 * V);
+                    const int off = q < V ? q : (1 + par) * V + (q - V);
+                    b_cp4(dst + St::FL + q, flags + C.flags + (size_t)tl.pk * 5 * V + off);
+                }
+            }
+        }
+        b_commit();
+    };
+
+#pragma unroll
+    for (int s = 0; s < kBStages - 1; ++s) issue(item + s * GW, s);
+    int slot = 0;
+    for (; item < total; item += GW) {
+        issue(item + (kBStages - 1) * GW, (slot + kBStages - 1) % kBStages);
+        b_wait<kBStages - 1>();
+        __syncwarp();
+        const BTile tl = tiles[item / TG];
+        const int gi = item - (item / TG) * TG;
+        if (gi < tl.count) {
+            const BCode C = codes[tl.code];
+            const uint32_t *S = ring + slot * St::WORDS;
+            const int pk = tl.pk;
+            const int g = tl.start + gi;
+            uint32_t *gmsg = msg + C.msg + (size_t)pk * C.E * 32 + lane;
+            uint32_t frozen[V];
+            bool lane_on = false;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                uint32_t dn = S[St::FL + v];
+                if (STOP) {
+                    const uint32_t newly = ~dn & ~S[St::FL + V + v];
+                    if (g == 0 && lane == 0) {
+                        uint32_t *F = flags + C.flags + (size_t)pk * 5 * V;
+                        if (newly) {
+                            F[v] = dn | newly;
+                            for (uint32_t b = newly; b; b &= b - 1) {
+                                const int ln = __ffs(b) - 1;
+                                iters[C.iters + (size_t)pk * W + ln * V + v] = it - 1;
+                            }
+                        }
+                        F[(1 + (par ^ 1)) * V + v] = 0u;
+                    }
+                    dn |= newly;
+                }
+                frozen[v] = dn;
+                lane_on |= ((~dn) >> lane) & 1u;
+            }
+            const int n0 = g * kBNV;
+            int l = n0 / C.p, k = n0 - l * C.p;
+#pragma unroll
+            for (int i = 0; i < kBNV; ++i, ++k) {
+                if (k >= C.p) k -= C.p, ++l;
+                const int n = n0 + i;
+                if (n >= C.N) break;
+                uint32_t outb[V];
+                if constexpr (!MS) {
+                    float m[V], aj[kBJ][V], tot[V];
+                    const float *mf = reinterpret_cast<const float *>(S + St::MU + i * St::MUW) + lane * V;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) m[v] = mf[v], tot[v] = mf[v];
+                    int eo[kBJ];
+#pragma unroll
+                    for (int jj = 0; jj < kBJ; ++jj) {
+                        eo[jj] = -1;
+#pragma unroll
+                        for (int v = 0; v < V; ++v) aj[jj][v] = 0.0f;
+                        if (jj < C.J && __ldg(shtab + C.tab + jj * C.L + l) >= 0) {
+                            eo[jj] = __ldg(eotab + C.tab + jj * C.L + l) + k;
+                            Lane<V>::unpack(S[St::AL + (i * kBJ + jj) * 32 + lane], aj[jj]);
+#pragma unroll
+                            for (int v = 0; v < V; ++v) tot[v] += aj[jj][v];
+                        }
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < kBJ; ++jj) {
+                        if (eo[jj] < 0) continue;
+                        float b[V];
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            float s = m[v];
+#pragma unroll
+                            for (int j2 = 0; j2 < kBJ; ++j2)
+                                if (j2 != jj) s += aj[j2][v];
+                            b[v] = clipf(s, clip);
+                            if (XF) {
+                                const float f = phi_f(fabsf(b[v]));
+                                b[v] = b[v] < 0.0f ? -f : f;
+                            }
+                        }
+                        if (lane_on) gmsg[(size_t)eo[jj] * 32] = Lane<V>::pack(b);
+                    }
+#pragma unroll
+                    for (int v = 0; v < V; ++v) outb[v] = __ballot_sync(0xffffffffu, clipf(tot[v], clip) < 0.0f);
+                } else {
+                    const uint32_t qw = S[St::MU + i * St::MUW + lane];
+                    uint32_t aw[kBJ];
+                    int eo[kBJ], tot[4];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) tot[v] = sbyte(qw, v);
+#pragma unroll
+                    for (int jj = 0; jj < kBJ; ++jj) {
+                        eo[jj] = -1;
+                        aw[jj] = 0u;
+                        if (jj < C.J && __ldg(shtab + C.tab + jj * C.L + l) >= 0) {
+                            eo[jj] = __ldg(eotab + C.tab + jj * C.L + l) + k;
+                            aw[jj] = S[St::AL + (i * kBJ + jj) * 32 + lane];
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) tot[v] += sbyte(aw[jj], v);
+                        }
+                    }
+                    if (lane_on) {
+#pragma unroll
+                        for (int jj = 0; jj < kBJ; ++jj) {
+                            if (eo[jj] < 0) continue;
+                            uint32_t o = 0u;
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) {
+                                int b = tot[v] - sbyte(aw[jj], v);
+                                b = b > 127 ? 127 : (b < -127 ? -127 : b);
+                                o |= ((uint32_t)(uint8_t)(int8_t)b) << (8 * v);
+                            }
+                            gmsg[(size_t)eo[jj] * 32] = o;
+                        }
+                    }
+#pragma unroll
+                    for (int v = 0; v < V; ++v) outb[v] = __ballot_sync(0xffffffffu, tot[v] < 0);
+                }
+                if (lane == 0) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const uint32_t old = S[St::HW + i * V + v];
+                        hw[C.hw + ((size_t)pk * C.N + n) * V + v] = (outb[v] & ~frozen[v]) | (old & frozen[v]);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        slot = (slot + 1) % kBStages;
+    }
+    b_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
+// tile lists of the packages with a running frame, over all codes
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024)
+btiles_kernel(const BCode *__restrict__ codes, const int *__restrict__ pair_code, const int *__restrict__ pair_pk,
+              int npairs, const uint32_t *__restrict__ flags, int V, int TR, int TG, int *__restrict__ cn_count,
+              BTile *__restrict__ cn_tiles, int *__restrict__ vn_count, BTile *__restrict__ vn_tiles, int first) {
+    __shared__ int ws_c[32], ws_v[32];
+    __shared__ int base_c, base_v;
+    if (threadIdx.x == 0) base_c = base_v = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int p0 = 0; p0 < npairs; p0 += blockDim.x) {
+        const int q = p0 + threadIdx.x;
+        int nc = 0, nv = 0, code = 0, pk = 0;
+        if (q < npairs) {
+            code = pair_code[q];
+            pk = pair_pk[q];
+            const BCode C = codes[code];
+            bool on = first != 0;
+            for (int v = 0; v < V && !on; ++v) on = ~flags[C.flags + (size_t)pk * 5 * V + v] != 0u;
+            if (on) {
+                nc = (C.M + TR - 1) / TR;
+                nv = ((C.N + kBNV - 1) / kBNV + TG - 1) / TG;
+            }
+        }
+        // inclusive warp scans of the tile counts
+        int sc = nc, sv = nv;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int a = __shfl_up_sync(0xffffffffu, sc, o), b = __shfl_up_sync(0xffffffffu, sv, o);
+            if (lane >= o) sc += a, sv += b;
+        }
+        if (lane == 31) ws_c[warp] = sc, ws_v[warp] = sv;
+        __syncthreads();
+        int pc = 0, pv = 0, tc = 0, tv = 0;
+        for (int w = 0; w < nw; ++w) {
+            if (w < warp) pc += ws_c[w], pv += ws_v[w];
+            tc += ws_c[w];
+            tv += ws_v[w];
+        }
+        const int oc = base_c + pc + sc - nc, ov = base_v + pv + sv - nv;
+        if (q < npairs) {
+            const BCode C = codes[code];
+            for (int t = 0; t < nc; ++t) {
+                const int start = t * TR;
+                cn_tiles[oc + t] = BTile{code, pk, start, min(TR, C.M - start)};
+            }
+            const int G = (C.N + kBNV - 1) / kBNV;
+            for (int t = 0; t < nv; ++t) {
+                const int start = t * TG;
+                vn_tiles[ov + t] = BTile{code, pk, start, min(TG, G - start)};
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) base_c += tc, base_v += tv;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *cn_count = base_c, *vn_count = base_v;
+}
+
+}  // namespace ldpc
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+using namespace ldpc;
+
+struct ldpc_batch_s {
+    int ncodes = 0, V = 1;
+    ldpc_decode_opts o;
+    std::vector<ldpc_code_s> views;  // per-code views into the shared workspace
+    std::vector<BCode> hcodes;
+    BCode *codes = nullptr;
+    int *shtab = nullptr, *eotab = nullptr;
+    int *pair_code = nullptr, *pair_pk = nullptr;
+    int npairs = 0;
+    int *counts = nullptr;  // [2]: cn, vn tile counts
+    BTile *cn_tiles = nullptr, *vn_tiles = nullptr;
+    size_t max_cn_tiles = 0, max_vn_tiles = 0;
+    void *msg = nullptr, *mu = nullptr;
+    uint32_t *hw = nullptr, *flags = nullptr;
+    int32_t *iters = nullptr;  // per code: [cap] iterations, then [cap] ok flags
+    float *post = nullptr;
+    int *act = nullptr;
+    size_t hw_words = 0, flags_words = 0, iters_total = 0;
+    int TR = 0, TG = 0;
+    bool tuned = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double tune_ms[3] = {0, 0, 0};
+};
+
+namespace ldpc {
+
+template <typename K>
+static int b_blocks(K kernel, size_t smem) {
+    int dev = 0, sms = 0, bps = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, kWarps * 32, smem);
+    return (bps < 1 ? 1 : bps) * (sms < 1 ? 1 : sms);
+}
+
+template <int V, bool XF, bool MS>
+static void b_cn(ldpc_batch b, bool first, bool syn, int par, cudaStream_t s) {
+#define B_CN(SYNV, FIRSTV)                                                                                          \
+    do {                                                                                                            \
+        auto k = bcn_kernel<V, SYNV, XF, MS, FIRSTV>;                                                               \
+        const size_t sm = (size_t)kWarps * kBStages * BCnStage<V, SYNV, FIRSTV, MS>::WORDS * 4;                     \
+        static int blocks = 0;                                                                                      \
+        if (!blocks) blocks = b_blocks(k, sm);                                                                      \
+        k<<<blocks, kWarps * 32, sm, s>>>(b->codes, b->shtab, b->eotab, (uint32_t *)b->msg, (const uint32_t *)b->mu, \
+                                          b->hw, b->flags, b->counts, b->cn_tiles, b->TR, b->o.clip, par);          \
+    } while (0)
+    if (first) B_CN(false, true);
+    else if (syn) B_CN(true, false);
+    else B_CN(false, false);
+#undef B_CN
+}
+
+template <int V, bool XF, bool MS>
+static void b_vn(ldpc_batch b, bool stop, int it, int par, cudaStream_t s) {
+#define B_VN(STOPV)                                                                                                  \
+    do {                                                                                                             \
+        auto k = bvn_kernel<V, STOPV, XF, MS>;                                                                       \
+        const size_t sm = (size_t)kWarps * kBStages * BVnStage<V, MS>::WORDS * 4;                                    \
+        static int blocks = 0;                                                                                       \
+        if (!blocks) blocks = b_blocks(k, sm);                                                                       \
+        k<<<blocks, kWarps * 32, sm, s>>>(b->codes, b->shtab, b->eotab, (uint32_t *)b->msg, (const uint32_t *)b->mu, \
+                                          b->hw, b->flags, b->iters, b->counts + 1, b->vn_tiles, b->TG, b->o.clip,  \
+                                          it, par);                                                                  \
+    } while (0)
+    if (stop) B_VN(true);
+    else B_VN(false);
+#undef B_VN
+}
+
+static void b_tiles(ldpc_batch b, bool first, cudaStream_t s) {
+    btiles_kernel<<<1, 1024, 0, s>>>(b->codes, b->pair_code, b->pair_pk, b->npairs, b->flags, b->V, b->TR, b->TG,
+                                     b->counts, b->cn_tiles, b->counts + 1, b->vn_tiles, first ? 1 : 0);
+}
+
+// one iteration of the shared loop
+static void b_iteration(ldpc_batch b, int it, cudaStream_t s) {
+    const bool first = it == 1, syn = b->o.early_stop && it >= 2;
+    const int par = it & 1;
+    if (b->o.algo == LDPC_ALGO_MS) {
+        b_cn<4, false, true>(b, first, syn, par, s);
+        b_vn<4, false, true>(b, syn, it, par, s);
+    } else if (b->o.msg == LDPC_MSG_F16) {
+        b_cn<2, false, false>(b, first, syn, par, s);
+        b_vn<2, false, false>(b, syn, it, par, s);
+    } else {
+        b_cn<1, true, false>(b, first, syn, par, s);
+        b_vn<1, true, false>(b, syn, it, par, s);
+    }
+    if (b->o.early_stop && it < b->o.max_iter) b_tiles(b, false, s);
+    count_launch(b->o.early_stop && it < b->o.max_iter ? 3 : 2);
+}
+
+static void b_loop(ldpc_batch b, int iters, cudaStream_t s) {
+    for (int it = 1; it <= iters; ++it) b_iteration(b, it, s);
+}
+
+}  // namespace ldpc
+
+// implemented in qc_decode.cu
+namespace ldpc {
+ldpc_status qc_init_flags(ldpc_code c, int gamma, int V, cudaStream_t s);
+ldpc_status qc_finish(ldpc_code c, int gamma, const ldpc_decode_opts &o, cudaStream_t s);
+}  // namespace ldpc
+
+extern "C" {
+
+ldpc_status ldpc_batch_create(const ldpc_code *codes, int32_t ncodes, const int32_t *gammas,
+                              const ldpc_decode_opts *opts, ldpc_batch *out) {
+    if (!out || !codes || !gammas || !opts || ncodes < 1 || ncodes > 4096) {
+        set_error("need codes, gammas, opts, out and 1 <= ncodes <= 4096");
+        return LDPC_EINVAL;
+    }
+    *out = nullptr;
+    const ldpc_decode_opts &o = *opts;
+    if (o.max_iter < 1 || o.max_iter > 100000 ||
+        !((o.algo == LDPC_ALGO_SP && (o.msg == LDPC_MSG_F32 || o.msg == LDPC_MSG_F16)) ||
+          (o.algo == LDPC_ALGO_MS && o.msg == LDPC_MSG_I8)) ||
+        !(o.clip > 0.0f) || o.clip > 60000.0f) {
+        set_error("batches take sum-product (F32/F16) or integer min-sum (I8), 1 <= max_iter, 0 < clip <= 60000");
+        return LDPC_EUNSUPPORTED;
+    }
+    ldpc_batch b = new (std::nothrow) ldpc_batch_s();
+    if (!b) {
+        set_error("host allocation failed");
+        return LDPC_ENOMEM;
+    }
+    b->ncodes = ncodes;
+    b->o = o;
+    b->V = lanes_per_word(o.msg);
+    const int V = b->V, W = 32 * V;
+    // sizes and offsets
+    size_t msg_w = 0, mu_w = 0, hw_w = 0, fl_w = 0, it_n = 0, post_n = 0;
+    std::vector<int> hsh, heo, pc, pp;
+    size_t max_ct = 0, max_vt = 0;
+    b->hcodes.resize(ncodes);
+    for (int i = 0; i < ncodes; ++i) {
+        const ldpc_code c = codes[i];
+        if (!c || gammas[i] < 1) {
+            delete b;
+            set_error("code %d is NULL or has gamma < 1", i);
+            return LDPC_EINVAL;
+        }
+        if (c->d.J > kBJ || c->d.L > kBDC) {
+            delete b;
+            set_error("code %d: batches take J <= %d and L <= %d", i, kBJ, kBDC);
+            return LDPC_EUNSUPPORTED;
+        }
+        const int P = (gammas[i] + W - 1) / W;
+        BCode &bc = b->hcodes[i];
+        bc.J = c->d.J; bc.L = c->d.L; bc.p = c->d.p; bc.N = c->d.N; bc.M = c->d.M; bc.E = c->d.E;
+        bc.P = P; bc.gamma = gammas[i];
+        bc.tab = (int)hsh.size();
+        for (int q = 0; q < c->d.J * c->d.L; ++q) hsh.push_back(c->d.shift[q]), heo.push_back(c->d.eoff[q]);
+        bc.msg = (long long)msg_w;
+        bc.mu = (long long)mu_w;
+        bc.hw = (long long)hw_w;
+        bc.flags = (long long)fl_w;
+        bc.iters = (long long)it_n;
+        msg_w += (size_t)P * c->d.E * 32;
+        mu_w += (size_t)P * c->d.N * (o.algo == LDPC_ALGO_MS ? 32 : W);
+        hw_w += (size_t)P * c->d.N * V;
+        fl_w += (size_t)P * 5 * V;
+        it_n += (size_t)P * W * 2;  // iterations, then ok flags (the single-code layout)
+        post_n += (size_t)P * c->d.N * W;
+        for (int pk = 0; pk < P; ++pk) pc.push_back(i), pp.push_back(pk);
+        max_ct += (size_t)P * c->d.M;                    // tiles of one row each at most
+        max_vt += (size_t)P * ((c->d.N + kBNV - 1) / kBNV);
+    }
+    b->npairs = (int)pc.size();
+    auto fail = [&](const char *what) {
+        cudaGetLastError();
+        ldpc_batch_destroy(b);
+        set_error("device allocation failed (%s)", what);
+        return LDPC_ENOMEM;
+    };
+    if (cudaMalloc(&b->msg, msg_w * 4)) return fail("messages");
+    if (cudaMalloc(&b->mu, mu_w * 4)) return fail("channel LLRs");
+    if (cudaMalloc(&b->hw, hw_w * 4)) return fail("hard words");
+    if (cudaMalloc(&b->flags, fl_w * 4)) return fail("flags");
+    if (cudaMalloc(&b->iters, it_n * 4)) return fail("iterations");
+    if (cudaMalloc(&b->codes, sizeof(BCode) * ncodes)) return fail("code table");
+    if (cudaMalloc(&b->shtab, hsh.size() * 4) || cudaMalloc(&b->eotab, heo.size() * 4)) return fail("shift tables");
+    if (cudaMalloc(&b->pair_code, pc.size() * 4) || cudaMalloc(&b->pair_pk, pp.size() * 4)) return fail("pairs");
+    if (cudaMalloc(&b->counts, 2 * sizeof(int))) return fail("counts");
+    if (cudaMalloc(&b->cn_tiles, max_ct * sizeof(BTile)) || cudaMalloc(&b->vn_tiles, max_vt * sizeof(BTile)))
+        return fail("tiles");
+    b->max_cn_tiles = max_ct;
+    b->max_vn_tiles = max_vt;
+    b->hw_words = hw_w;
+    b->flags_words = fl_w;
+    b->iters_total = it_n;
+    if (cudaMemcpy(b->codes, b->hcodes.data(), sizeof(BCode) * ncodes, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(b->shtab, hsh.data(), hsh.size() * 4, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(b->eotab, heo.data(), heo.size() * 4, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(b->pair_code, pc.data(), pc.size() * 4, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(b->pair_pk, pp.data(), pp.size() * 4, cudaMemcpyHostToDevice))
+        return fail("table upload");
+    // per-code views: the single-code pack / finish / unpack kernels run on them
+    b->views.resize(ncodes);
+    for (int i = 0; i < ncodes; ++i) {
+        ldpc_code_s &v = b->views[i];
+        const BCode &bc = b->hcodes[i];
+        v.d = codes[i]->d;
+        v.device = codes[i]->device;
+        v.rate = codes[i]->rate;
+        v.noms = nullptr;
+        v.ws.gamma_cap = (size_t)bc.P * W;
+        v.ws.msg = (uint32_t *)b->msg + bc.msg;
+        v.ws.mu = (uint32_t *)b->mu + bc.mu;
+        v.ws.hw = b->hw + bc.hw;
+        v.ws.flags = b->flags + bc.flags;
+        v.ws.iters = b->iters + bc.iters;  // ok flags follow at + gamma_cap
+        v.ws.post = nullptr;
+    }
+    *out = b;
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_batch_destroy(ldpc_batch b) {
+    if (!b) return LDPC_OK;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->msg); cudaFree(b->mu); cudaFree(b->hw); cudaFree(b->flags); cudaFree(b->iters);
+    cudaFree(b->codes); cudaFree(b->shtab); cudaFree(b->eotab); cudaFree(b->pair_code); cudaFree(b->pair_pk);
+    cudaFree(b->counts); cudaFree(b->cn_tiles); cudaFree(b->vn_tiles);
+    for (auto &v : b->views) v.ws = DecodeWs();  // borrowed
+    delete b;
+    return LDPC_OK;
+}
+
+}  // extern "C"
+
+namespace ldpc {
+
+// pack every code's frames and reset its state; the initial tile list covers every package
+static ldpc_status b_prepare(ldpc_batch b, const float *const *llr, cudaStream_t s) {
+    for (int i = 0; i < b->ncodes; ++i) {
+        ldpc_status st = qc_pack_llr(&b->views[i], llr[i], b->hcodes[i].gamma, b->o, s);
+        if (st != LDPC_OK) return st;
+        st = qc_init_flags(&b->views[i], b->hcodes[i].gamma, b->V, s);
+        if (st != LDPC_OK) return st;
+    }
+    LDPC_CUDA_TRY(cudaMemsetAsync(b->hw, 0, b->hw_words * 4, s));
+    b_tiles(b, true, s);
+    count_launch();
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
+// autotuner: rows per check-pass tile and variable groups per variable-pass tile
+static ldpc_status b_tune(ldpc_batch b, const float *const *llr, cudaStream_t s) {
+    const int cand[3][2] = {{16, 8}, {64, 32}, {256, 128}};
+    const int iters = b->o.max_iter < 3 ? b->o.max_iter : 3;
+    cudaEvent_t e0, e1;
+    LDPC_CUDA_TRY(cudaEventCreate(&e0));
+    LDPC_CUDA_TRY(cudaEventCreate(&e1));
+    double best = 1e30;
+    int bi = 1;
+    for (int q = 0; q < 3; ++q) {
+        b->TR = cand[q][0];
+        b->TG = cand[q][1];
+        ldpc_status st = b_prepare(b, llr, s);
+        if (st != LDPC_OK) return st;
+        b_loop(b, 1, s);  // warm-up of this configuration
+        st = b_prepare(b, llr, s);
+        if (st != LDPC_OK) return st;
+        LDPC_CUDA_TRY(cudaEventRecord(e0, s));
+        b_loop(b, iters, s);
+        LDPC_CUDA_TRY(cudaEventRecord(e1, s));
+        LDPC_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        LDPC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        b->tune_ms[q] = ms;
+        if (ms < best) best = ms, bi = q;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->TR = cand[bi][0];
+    b->TG = cand[bi][1];
+    b->tuned = true;
+    return LDPC_OK;
+}
+
+}  // namespace ldpc
+
+extern "C" {
+
+ldpc_status ldpc_batch_decode(ldpc_batch b, const float *const *llr, uint8_t *const *hard, int32_t *const *iters,
+                              int32_t *const *ok, void *stream) {
+    if (!b || !llr) {
+        set_error("need a batch and its llr pointer array");
+        return LDPC_EINVAL;
+    }
+    for (int i = 0; i < b->ncodes; ++i) {
+        if (!llr[i] || pointer_kind(llr[i]) != 0 || (hard && hard[i] && pointer_kind(hard[i]) != 0) ||
+            (iters && iters[i] && pointer_kind(iters[i]) != 0) || (ok && ok[i] && pointer_kind(ok[i]) != 0)) {
+            set_error("code %d: llr (and any outputs) must be device buffers", i);
+            return LDPC_EINVAL;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    ldpc_status st;
+    if (!b->tuned) {
+        st = b_tune(b, llr, s);
+        if (st != LDPC_OK) return st;
+    }
+    st = b_prepare(b, llr, s);
+    if (st != LDPC_OK) return st;
+    if (!b->exec) {
+        // the first run goes eagerly (kernel attributes get set), then the loop is captured
+        b_loop(b, b->o.max_iter, s);
+        LDPC_CUDA_TRY(cudaGetLastError());
+        cudaStream_t cs;
+        LDPC_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        LDPC_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        b_loop(b, b->o.max_iter, cs);
+        cudaError_t ce = cudaStreamEndCapture(cs, &b->graph);
+        cudaStreamDestroy(cs);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+        LDPC_CUDA_TRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    } else {
+        LDPC_CUDA_TRY(cudaGraphLaunch(b->exec, s));
+    }
+    for (int i = 0; i < b->ncodes; ++i) {
+        ldpc_code_s &v = b->views[i];
+        const int g = b->hcodes[i].gamma;
+        st = qc_finish(&v, g, b->o, s);
+        if (st != LDPC_OK) return st;
+        st = qc_unpack_outputs(&v, g, b->o, nullptr, hard ? hard[i] : nullptr, iters ? iters[i] : nullptr,
+                               ok ? ok[i] : nullptr, s);
+        if (st != LDPC_OK) return st;
+    }
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_batch_info(ldpc_batch b, int32_t *tile_rows, int32_t *tile_groups, double *tune_ms3) {
+    if (!b) {
+        set_error("batch is NULL");
+        return LDPC_EINVAL;
+    }
+    if (tile_rows) *tile_rows = b->TR;
+    if (tile_groups) *tile_groups = b->TG;
+    if (tune_ms3)
+        for (int q = 0; q < 3; ++q) tune_ms3[q] = b->tune_ms[q];
+    return LDPC_OK;
+}
+
+}  // extern "C"

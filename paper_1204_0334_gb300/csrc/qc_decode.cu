@@ -661,6 +661,30 @@ ldpc_status qc_decode_device(ldpc_code c, int gamma, const ldpc_decode_opts &o, 
     return LDPC_OK;
 }
 
+// flag words of a fresh decode of gamma frames (padding frames start stopped)
+ldpc_status qc_init_flags(ldpc_code c, int gamma, int V, cudaStream_t s) {
+    const int P = (gamma + 32 * V - 1) / (32 * V);
+    init_flags_kernel<<<(P + 127) / 128, 128, 0, s>>>(c->ws.flags, P, V, gamma);
+    count_launch();
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
+// syndrome of the last decisions, iteration counts and ok flags of every frame
+ldpc_status qc_finish(ldpc_code c, int gamma, const ldpc_decode_opts &o, cudaStream_t s) {
+    const int V = words_per_lane(o);
+    const int P = (gamma + 32 * V - 1) / (32 * V);
+    dim3 grd((c->d.M + 127) / 128, P);
+    if (V == 1) final_syndrome_kernel<1><<<grd, 128, 0, s>>>(c->d, c->ws.hw, c->ws.flags, P);
+    else if (V == 2) final_syndrome_kernel<2><<<grd, 128, 0, s>>>(c->d, c->ws.hw, c->ws.flags, P);
+    else final_syndrome_kernel<4><<<grd, 128, 0, s>>>(c->d, c->ws.hw, c->ws.flags, P);
+    finish_frames_kernel<<<(gamma + 255) / 256, 256, 0, s>>>(c->ws.flags, c->ws.iters, c->ws.iters + c->ws.gamma_cap,
+                                                             gamma, V, o.max_iter);
+    count_launch(2);
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
 ldpc_status qc_unpack_outputs(ldpc_code c, int gamma, const ldpc_decode_opts &o, float *post, uint8_t *hard,
                               int32_t *iters, int32_t *ok, cudaStream_t s) {
     const int V = words_per_lane(o), W = 32 * V;
