@@ -1,12 +1,13 @@
 #!/usr/bin/env python
 """Throughput benchmark of the GB300 LDPC decoder.
 
-Workload (one step = one batch through the whole block-code path):
+Workload (one step = one ldpc_ber_sim call through the whole block-code path):
   QC-LDPC 4 x 24, p = 765 (n = 18360, K = N - M = 15300 design information bits),
-  seeded shifts, 4096 frames per batch, all-zero codeword over BPSK/AWGN at
+  seeded shifts, 32768 frames per step decoded in 4096 frame slots (a slot takes
+  the next frame as soon as its frame stops), all-zero codeword over BPSK/AWGN at
   Eb/N0 = 3.5 dB generated on the device (Philox + Box-Muller), sum-product with
   FP32 messages, at most 30 iterations with syndrome early stop, device-side
-  error counting; one ldpc_ber_sim call per step.
+  error counting.
 
 Metric: decoded information Mbit/s = frames * 15300 / seconds (whole job over
 all ranks).  Ranks decode disjoint frame ranges (weak scaling, no collective on
@@ -36,9 +37,9 @@ K_INFO = N_BITS - J * P_CIRC  # 15300
 E_EDGES = J * L * P_CIRC
 METRIC = "decoded info Mbit/s (n=18360, 30 iters) at BER matching FP64 oracle"
 # DRAM bytes (read + write) per check-pass launch, measured with ncu
-# (gpu__time_duration / dram__bytes_{read,write}) on the default workload of this file
-# (FP32 messages, early stop, 3.5 dB); None whenever the kernels change until re-measured.
-CN_DRAM_BYTES_PER_LAUNCH = {"f32": 724.1e6}
+# (dram__bytes_{read,write}.sum) on the default workload of this file (FP32 messages,
+# early stop, 3.5 dB, 4096 slots); absent whenever the kernels change until re-measured.
+CN_DRAM_BYTES_PER_LAUNCH = {}
 
 
 def args_parse():
@@ -48,7 +49,8 @@ def args_parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ebn0", type=float, default=3.5)
-    ap.add_argument("--gamma", type=int, default=4096)
+    ap.add_argument("--gamma", type=int, default=4096, help="frame slots decoded together")
+    ap.add_argument("--frames", type=int, default=32768, help="frames simulated per step")
     ap.add_argument("--iters", type=int, default=30)
     ap.add_argument("--msg", default="f32", choices=["f32", "f16", "i8"])
     ap.add_argument("--no-early-stop", action="store_true")
@@ -64,7 +66,8 @@ def args_parse():
 
 def workload_name(a) -> str:
     es = "early-stop" if not a.no_early_stop else "fixed"
-    return f"QC-LDPC 4x24 p=765 n=18360, {a.gamma} frames/batch, {a.iters} iters {es}, Eb/N0 {a.ebn0} dB, {a.msg} msgs"
+    return (f"QC-LDPC 4x24 p=765 n=18360, {a.frames} frames/step in {a.gamma} slots, {a.iters} iters {es}, "
+            f"Eb/N0 {a.ebn0} dB, {a.msg} msgs")
 
 
 def load_peaks() -> dict:
@@ -222,8 +225,9 @@ def run_ours(a):
     s_mu = 1 if a.msg == "i8" else 4
     base = (rank << 40) + (1 << 36)
 
-    def step(i, o=opts, gamma=a.gamma):
-        return pkg.ldpc_ber_sim(code.handle, a.ebn0, a.seed, base + i * gamma, gamma, 1 << 60, gamma, o, stream)
+    def step(i, o=opts):
+        return pkg.ldpc_ber_sim(code.handle, a.ebn0, a.seed, base + i * a.frames, a.frames, 1 << 60, a.gamma, o,
+                                stream)
 
     for w in range(a.warmup):
         step(-1 - w)
@@ -278,7 +282,7 @@ def run_ours(a):
             "achieved": cn_bytes / cn_s / 1e9 if cn_s > 0 else None, "peak": peak, "unit": "GB/s",
             "frac": (cn_bytes / cn_s / 1e9) / peak if cn_s > 0 else None,
             "traffic": (CN_DRAM_BYTES_PER_LAUNCH.get(a.msg) if (not a.no_early_stop and a.gamma == 4096
-                                                                 and a.ebn0 == 3.5) else None),
+                                                                 and a.ebn0 == 3.5 and a.iters == 30) else None),
             "algorithmic_bytes_per_launch": cn_bytes / max(1, prof["cn_launches"]),
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback",
             "cn_launches": prof["cn_launches"], "cn_ms_avg": prof["cn_ms"] / max(1, prof["cn_launches"]),
@@ -288,9 +292,10 @@ def run_ours(a):
     line = {"metric": METRIC, "value": value, "unit": "Mbit/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "i8" if a.msg == "i8" else "f32", "data": "synthetic",
-            "config": {"workload": workload_name(a), "gamma": a.gamma, "iters_cap": a.iters,
+            "config": {"workload": workload_name(a), "slots": a.gamma, "frames_per_step": a.frames,
+                       "iters_cap": a.iters,
                        "early_stop": not a.no_early_stop, "ebn0_db": a.ebn0, "msg": a.msg,
-                       "l2": "inputs larger than L2 (message store %.2f GB per batch)" % (
+                       "l2": "inputs larger than L2 (message store %.2f GB)" % (
                            E_EDGES * s_msg * a.gamma / 1e9)},
             "frames": frames, "mean_iters": iters_sum / frames, "fer": fe / frames, "ber": be / (frames * N_BITS),
             "frames_per_s": frames / (ms / 1e3), "roofline": roof, "clocks": clk,
@@ -325,13 +330,13 @@ def variants(a, pkg, code, stream, opts) -> dict:
     for name, kw in cases:
         o = pkg.default_opts(max_iter=a.iters, **kw)
         base = (7 << 44)
-        pkg.ldpc_ber_sim(code.handle, a.ebn0, a.seed, base, a.gamma, 1 << 60, a.gamma, o, stream)
+        pkg.ldpc_ber_sim(code.handle, a.ebn0, a.seed, base, a.frames, 1 << 60, a.gamma, o, stream)
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         k = 3
         ev0.record(stream)
-        rs = [pkg.ldpc_ber_sim(code.handle, a.ebn0, a.seed, base + (i + 1) * a.gamma, a.gamma, 1 << 60, a.gamma, o,
-                               stream) for i in range(k)]
+        rs = [pkg.ldpc_ber_sim(code.handle, a.ebn0, a.seed, base + (i + 1) * a.frames, a.frames, 1 << 60, a.gamma,
+                               o, stream) for i in range(k)]
         ev1.record(stream)
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1)

@@ -50,10 +50,12 @@ struct DecodeWs {
 }  // namespace ldpc
 
 struct ldpc_noms_state;  // training state of the learned min-sum (noms.cu)
+struct ldpc_sim_state;   // frame slots of the continuous simulation (sim.cu)
 
 struct ldpc_code_s {
     ldpc::QcDesc d;
     ldpc_noms_state *noms = nullptr;
+    ldpc_sim_state *sim = nullptr;
     int device = 0;
     double rate = 0.0;   // design rate K/N
     ldpc::DecodeWs ws;
@@ -89,14 +91,23 @@ ldpc_status qc_channel_packed(ldpc_code c, double sigma, uint64_t seed, uint64_t
 ldpc_status qc_channel_frames(ldpc_code c, double sigma, uint64_t seed, uint64_t first_frame, int gamma,
                               float *out, cudaStream_t s);
 ldpc_status qc_count_errors(ldpc_code c, int gamma, const ldpc_decode_opts &o, cudaStream_t s);
+// syndrome of the hard decisions into flag word `word` (+v) of every package
+ldpc_status qc_syndrome(ldpc_code c, int P, int V, int word, cudaStream_t s);
 
 ldpc_status phi_eval(const float *x, float *y, int n, int variant, cudaStream_t s);
 void noms_free(ldpc_noms_state *w);
 // pipelined node passes (qc_pipe.cu)
-ldpc_status qc_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, bool syn, int par, int it, cudaStream_t s);
+ldpc_status qc_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, cudaStream_t s);
 ldpc_status qc_vn_pipe(ldpc_code c, const ldpc_decode_opts &o, bool stop, bool post, int it, int par,
                        cudaStream_t s);
-ldpc_status qc_compact(ldpc_code c, int P, int V, cudaStream_t s);
+// packages with a running frame; with sflags (continuous simulation) also those
+// with a retiring or new frame
+ldpc_status qc_compact(ldpc_code c, int P, int V, cudaStream_t s, const uint32_t *sflags = nullptr);
+// continuous simulation (sim.cu)
+void sim_free(ldpc_sim_state *st);
+ldpc_status qc_ber_sim_refill(ldpc_code c, double sigma, uint64_t seed, uint64_t first_frame, int64_t max_frames,
+                              int64_t target, int gamma, const ldpc_decode_opts &o, unsigned long long *h,
+                              cudaStream_t s);
 
 inline int lanes_per_word(int msg) { return msg == LDPC_MSG_F32 ? 1 : (msg == LDPC_MSG_F16 ? 2 : 4); }
 

@@ -262,31 +262,38 @@ cn_ms_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__restr
 
 
 // ---------------------------------------------------------------------------
-// Final syndrome of the last decisions (for ok), and the per-frame finish.
+// Syndrome of the current decisions, eq. (hrddcs) checked row by row: bit
+// `lane` of flag word `word + v` of a package is set when some check of frame
+// (lane, v) is unsatisfied.  One thread per check row; consecutive rows of a
+// block row read consecutive hard-decision words (a cyclic shift of one
+// column block), and a warp ORs its rows before one atomic per word.
 // ---------------------------------------------------------------------------
 template <int V>
-__global__ void final_syndrome_kernel(const QcDesc d, const uint32_t *__restrict__ hw, uint32_t *__restrict__ flags,
-                                      int P) {
+__global__ void syndrome_kernel(const QcDesc d, const uint32_t *__restrict__ hw, uint32_t *__restrict__ flags,
+                                int P, int word) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int pk = blockIdx.y;
-    if (m >= d.M || pk >= P) return;
-    const int j = m / d.p, r = m - j * d.p;
     uint32_t syn[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) syn[v] = 0u;
-    for (int l = 0; l < d.L; ++l) {
-        const int a = d.shift[j * d.L + l];
-        if (a < 0) continue;
-        int k = r + a;
-        if (k >= d.p) k -= d.p;
-        const uint32_t *h = hw + ((size_t)pk * d.N + (size_t)l * d.p + k) * V;
+    if (m < d.M && pk < P) {
+        const int j = m / d.p, r = m - j * d.p;
+        for (int l = 0; l < d.L; ++l) {
+            const int a = d.shift[j * d.L + l];
+            if (a < 0) continue;
+            int k = r + a;
+            if (k >= d.p) k -= d.p;
+            const uint32_t *h = hw + ((size_t)pk * d.N + (size_t)l * d.p + k) * V;
 #pragma unroll
-        for (int v = 0; v < V; ++v) syn[v] ^= h[v];
+            for (int v = 0; v < V; ++v) syn[v] ^= h[v];
+        }
     }
-    uint32_t *fin = flags + (size_t)pk * 5 * V + 4 * V;
+    uint32_t *out = flags + (size_t)pk * 5 * V + word;
 #pragma unroll
-    for (int v = 0; v < V; ++v)
-        if (syn[v]) atomicOr(fin + v, syn[v]);
+    for (int v = 0; v < V; ++v) {
+        const uint32_t any = __reduce_or_sync(0xffffffffu, syn[v]);
+        if (any && (threadIdx.x & 31) == 0) atomicOr(out + v, any);
+    }
 }
 
 // flags init: done = ~valid (padding frames never run), unsat = 0, fin = 0
@@ -614,6 +621,15 @@ static void cn_first_dispatch(ldpc_code c, int P, const ldpc_decode_opts &o, cud
     else launch_cn_first<DCMAX, 1, false>(c, P, o, s);
 }
 
+ldpc_status qc_syndrome(ldpc_code c, int P, int V, int word, cudaStream_t s) {
+    dim3 grd((c->d.M + 255) / 256, P);
+    if (V == 1) syndrome_kernel<1><<<grd, 256, 0, s>>>(c->d, c->ws.hw, c->ws.flags, P, word);
+    else if (V == 2) syndrome_kernel<2><<<grd, 256, 0, s>>>(c->d, c->ws.hw, c->ws.flags, P, word);
+    else syndrome_kernel<4><<<grd, 256, 0, s>>>(c->d, c->ws.hw, c->ws.flags, P, word);
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
 ldpc_status qc_decode_device(ldpc_code c, int gamma, const ldpc_decode_opts &o, bool want_post, cudaStream_t s) {
     const int V = words_per_lane(o), W = 32 * V;
     const int P = (gamma + W - 1) / W;
@@ -634,7 +650,13 @@ ldpc_status qc_decode_device(ldpc_code c, int gamma, const ldpc_decode_opts &o, 
             else if (dcm <= 24) cn_first_dispatch<24>(c, P, o, s);
             else cn_first_dispatch<32>(c, P, o, s);
         } else {
-            st = qc_cn_pipe(c, o, syn, par, it, s);
+            // C-11 stopping: the syndrome of the decisions after it-1 iterations, then the check pass
+            if (syn) {
+                st = qc_syndrome(c, P, V, (1 + par) * V, s);
+                if (st != LDPC_OK) return st;
+                count_launch();
+            }
+            st = qc_cn_pipe(c, o, it, s);
             if (st != LDPC_OK) return st;
         }
         prof_end(slot_cn, s);
@@ -649,12 +671,8 @@ ldpc_status qc_decode_device(ldpc_code c, int gamma, const ldpc_decode_opts &o, 
             count_launch();
         }
     }
-    {
-        dim3 grd((c->d.M + 127) / 128, P);
-        if (V == 1) final_syndrome_kernel<1><<<grd, 128, 0, s>>>(c->d, c->ws.hw, c->ws.flags, P);
-        else if (V == 2) final_syndrome_kernel<2><<<grd, 128, 0, s>>>(c->d, c->ws.hw, c->ws.flags, P);
-        else final_syndrome_kernel<4><<<grd, 128, 0, s>>>(c->d, c->ws.hw, c->ws.flags, P);
-    }
+    st = qc_syndrome(c, P, V, 4 * V, s);  // fin words: the last decisions
+    if (st != LDPC_OK) return st;
     finish_frames_kernel<<<(gamma + 255) / 256, 256, 0, s>>>(c->ws.flags, c->ws.iters,
                                                              c->ws.iters + c->ws.gamma_cap, gamma, V, o.max_iter);
     LDPC_CUDA_TRY(cudaGetLastError());
@@ -674,10 +692,8 @@ ldpc_status qc_init_flags(ldpc_code c, int gamma, int V, cudaStream_t s) {
 ldpc_status qc_finish(ldpc_code c, int gamma, const ldpc_decode_opts &o, cudaStream_t s) {
     const int V = words_per_lane(o);
     const int P = (gamma + 32 * V - 1) / (32 * V);
-    dim3 grd((c->d.M + 127) / 128, P);
-    if (V == 1) final_syndrome_kernel<1><<<grd, 128, 0, s>>>(c->d, c->ws.hw, c->ws.flags, P);
-    else if (V == 2) final_syndrome_kernel<2><<<grd, 128, 0, s>>>(c->d, c->ws.hw, c->ws.flags, P);
-    else final_syndrome_kernel<4><<<grd, 128, 0, s>>>(c->d, c->ws.hw, c->ws.flags, P);
+    ldpc_status st = qc_syndrome(c, P, V, 4 * V, s);
+    if (st != LDPC_OK) return st;
     finish_frames_kernel<<<(gamma + 255) / 256, 256, 0, s>>>(c->ws.flags, c->ws.iters, c->ws.iters + c->ws.gamma_cap,
                                                              gamma, V, o.max_iter);
     count_launch(2);

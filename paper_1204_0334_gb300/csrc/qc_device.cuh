@@ -160,6 +160,17 @@ __device__ __forceinline__ void channel_quad(uint64_t seed, uint64_t F, int q, f
     box_muller_llr(w, sigma, s2, mu4);
 }
 
+// arguments of the variable pass in continuous-simulation (refill) mode
+struct RefillArgs {
+    const uint32_t *sflags = nullptr;  // per package: retire[V], refill[V]
+    int *errs = nullptr;               // bit errors of the retiring frames, per slot
+};
+
 __device__ __forceinline__ int sbyte(uint32_t w, int v) { return (int)(int8_t)(uint8_t)(w >> (8 * v)); }
 
+}  // namespace ldpc
+
+namespace ldpc {
+// variable pass in refill mode (qc_pipe.cu); sum-product or min-sum, not NOMS
+ldpc_status qc_vn_refill(ldpc_code c, const ldpc_decode_opts &o, const RefillArgs &rf, cudaStream_t s);
 }  // namespace ldpc

@@ -36,25 +36,25 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-template <int DCMAX, int V, bool SYN>
+template <int DCMAX>
 struct CnStage {
-    static constexpr int SEG = DCMAX * 32;          // edge packages, [l][32 words]
-    static constexpr int OFF = SEG;                 // [l]: package offset of the edge in words / 32, or -1
-    static constexpr int HW = OFF + DCMAX;          // hard-decision words of the row's variables
-    static constexpr int FL = HW + (SYN ? DCMAX * V : 0);  // done words
-    static constexpr int WORDS = (FL + V + 3) & ~3;
+    static constexpr int SEG = DCMAX * 32;  // edge packages, [l][32 words]
+    static constexpr int FL = SEG;          // done words (V <= 4)
+    static constexpr int WORDS = SEG + 4;
 };
 
 // ---------------------------------------------------------------------------
-// check pass (iterations >= 2): sum-product (MS = false) or integer min-sum.
-// REG: every block of the row is present and L == DCMAX (regular QC code).
+// check pass (iterations >= 2): sum-product, learned normalized/offset
+// min-sum, or integer min-sum.  REG: every block of the row is present and
+// L == DCMAX (regular QC code).  The message offsets of an item's DCMAX edges
+// stay in registers (lane l holds edge l's, broadcast with a shuffle), so the
+// ring holds only message packages and three blocks of eight warps fit on an SM.
 // ---------------------------------------------------------------------------
-template <int DCMAX, int V, bool SYN, bool XF, int MODE, bool REG>
+template <int DCMAX, int V, bool XF, int MODE, bool REG>
 __global__ void __launch_bounds__(kWarps * 32)
-cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__restrict__ hw,
-               uint32_t *__restrict__ flags, const int *__restrict__ act, float clip, int par,
-               const float *__restrict__ nparams) {
-    using St = CnStage<DCMAX, V, SYN>;
+cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__restrict__ flags,
+               const int *__restrict__ act, float clip, const float *__restrict__ nparams) {
+    using St = CnStage<DCMAX>;
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ int s_sh[kMaxJ * kMaxL], s_eo[kMaxJ * kMaxL];
     for (int i = threadIdx.x; i < d.J * d.L; i += blockDim.x) {
@@ -70,7 +70,10 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
     const int GW = gridDim.x * kWarps;
     int item = blockIdx.x * kWarps + warp;
 
-    auto issue = [&](int it, int slot) {
+    // starts the copies of item `it` into ring slot `slot`; returns this lane's
+    // edge offset (lane l < DCMAX: edge l of the row, in 32-word packages; -1 if absent)
+    auto issue = [&](int it, int slot) -> int {
+        int mine = -1;
         if (it < total) {
             const int a = it / d.M;
             const int m = it - a * d.M;
@@ -78,75 +81,66 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
             const int j = m / d.p, r = m - j * d.p;
             const uint32_t *gmsg = msg + (size_t)pk * d.E * 32;
             uint32_t *dst = ring + slot * St::WORDS;
-            int *off = reinterpret_cast<int *>(dst + St::OFF);
             const int g = lane >> 3, sub = lane & 7;
 #pragma unroll
             for (int q = 0; q < DCMAX / 4; ++q) {
                 const int l = 4 * q + g;
                 const int sh = (REG || l < d.L) ? s_sh[j * d.L + l] : -1;
-                int o = -1;
                 if (REG || sh >= 0) {
                     int k = r + sh;
                     if (k >= d.p) k -= d.p;
-                    o = s_eo[j * d.L + l] + k;
-                    cp_async16(dst + l * 32 + sub * 4, gmsg + (size_t)o * 32 + sub * 4);
+                    cp_async16(dst + l * 32 + sub * 4, gmsg + (size_t)(s_eo[j * d.L + l] + k) * 32 + sub * 4);
                 }
-                if (sub == 0) off[l] = o;
             }
-            if (SYN) {
-                for (int w = lane; w < DCMAX * V; w += 32) {
-                    const int l = w / V, v = w - l * V;
-                    const int sh = (REG || l < d.L) ? s_sh[j * d.L + l] : -1;
-                    if (REG || sh >= 0) {
-                        int k = r + sh;
-                        if (k >= d.p) k -= d.p;
-                        cp_async4(dst + St::HW + w, hw + ((size_t)pk * d.N + (size_t)l * d.p + k) * V + v);
-                    }
+            if (lane < DCMAX && (REG || lane < d.L)) {
+                const int sh = s_sh[j * d.L + lane];
+                if (REG || sh >= 0) {
+                    int k = r + sh;
+                    if (k >= d.p) k -= d.p;
+                    mine = s_eo[j * d.L + lane] + k;
                 }
             }
             if (lane < V) cp_async4(dst + St::FL + lane, flags + (size_t)pk * 5 * V + lane);
         }
         cp_async_commit();
+        return mine;
     };
 
+    int offr[kStages];
 #pragma unroll
-    for (int s = 0; s < kStages - 1; ++s) issue(item + s * GW, s);
+    for (int s = 0; s < kStages - 1; ++s) offr[s] = issue(item + s * GW, s);
     int slot = 0;
     for (; item < total; item += GW) {
-        issue(item + (kStages - 1) * GW, (slot + kStages - 1) % kStages);
+        offr[kStages - 1] = issue(item + (kStages - 1) * GW, (slot + kStages - 1) % kStages);
         cp_async_wait<kStages - 1>();
         __syncwarp();
         const uint32_t *S = ring + slot * St::WORDS;
-        const int *off = reinterpret_cast<const int *>(S + St::OFF);
+        const int myoff = offr[0];
+#pragma unroll
+        for (int s = 0; s < kStages - 1; ++s) offr[s] = offr[s + 1];
         const int pk = __ldg(list + item / d.M);
         uint32_t *gmsg = msg + (size_t)pk * d.E * 32 + lane;
-        uint32_t actv[V];
         bool lane_on = false;
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            actv[v] = ~S[St::FL + v];
-            lane_on |= (actv[v] >> lane) & 1u;
-        }
-        uint32_t syn[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) syn[v] = 0u;
+        for (int v = 0; v < V; ++v) lane_on |= ((~S[St::FL + v]) >> lane) & 1u;
         if constexpr (MODE == kModeSP) {
-            float ph[DCMAX][V];
-            uint32_t neg[V];
+            // xs: signed terms sign(beta) * phi(|beta|) (XF: as stored by the variable pass);
+            // the output sign is the XOR of the other edges' sign bits
+            float xs[DCMAX][V];
+            uint32_t sgn[V];
 #pragma unroll
-            for (int v = 0; v < V; ++v) neg[v] = 0u;
+            for (int v = 0; v < V; ++v) sgn[v] = 0u;
 #pragma unroll
             for (int l = 0; l < DCMAX; ++l) {
 #pragma unroll
-                for (int v = 0; v < V; ++v) ph[l][v] = 0.0f;
-                if (REG || off[l] >= 0) {
+                for (int v = 0; v < V; ++v) xs[l][v] = 0.0f;
+                if (REG || (l < d.L && __shfl_sync(0xffffffffu, myoff, l) >= 0)) {
                     float x[V];
                     Lane<V>::unpack(S[l * 32 + lane], x);
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
-                        ph[l][v] = XF ? fabsf(x[v]) : phi_warp(fabsf(x[v]));
-                        neg[v] |= (x[v] < 0.0f ? 1u : 0u) << l;
-                        if (SYN) syn[v] ^= S[St::HW + l * V + v];
+                        xs[l][v] = XF ? x[v] : copysignf(phi_warp(fabsf(x[v])), x[v]);
+                        sgn[v] ^= __float_as_uint(x[v]);
                     }
                 }
             }
@@ -160,27 +154,27 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
                         pre[l][v] = acc[v];
-                        acc[v] += ph[l][v];
+                        acc[v] += fabsf(xs[l][v]);
                     }
             }
-            uint32_t par_all[V];
             float suf[V];
 #pragma unroll
-            for (int v = 0; v < V; ++v) par_all[v] = __popc(neg[v]) & 1u, suf[v] = 0.0f;
+            for (int v = 0; v < V; ++v) suf[v] = 0.0f;
 #pragma unroll
             for (int l = DCMAX - 1; l >= 0; --l) {
-                const int o = off[l];
+                const int o = __shfl_sync(0xffffffffu, myoff, l);
                 if (REG || o >= 0) {
                     float out[V];
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
                         const float mag = fminf(phi_warp(pre[l][v] + suf[v]), clip);
-                        out[v] = (par_all[v] ^ ((neg[v] >> l) & 1u)) ? -mag : mag;
+                        out[v] = __uint_as_float(__float_as_uint(mag) |
+                                                 ((sgn[v] ^ __float_as_uint(xs[l][v])) & 0x80000000u));
                     }
                     if (lane_on) gmsg[(size_t)o * 32] = Lane<V>::pack(out);
                 }
 #pragma unroll
-                for (int v = 0; v < V; ++v) suf[v] += ph[l][v];
+                for (int v = 0; v < V; ++v) suf[v] += fabsf(xs[l][v]);
             }
         } else if constexpr (MODE == kModeNOMS) {
             // normalized/offset min-sum: alpha = sign * max(w * m - o, 0), (w, o) of this
@@ -195,38 +189,38 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
             for (int l = 0; l < DCMAX; ++l) {
 #pragma unroll
                 for (int v = 0; v < V; ++v) ab[l][v] = INFINITY;
-                if (REG || off[l] >= 0) {
-                    float x[V];
-                    Lane<V>::unpack(S[l * 32 + lane], x);
+                if (REG || l < d.L) {
+                    const int o = __shfl_sync(0xffffffffu, myoff, l);
+                    if (REG || o >= 0) {
+                        float x[V];
+                        Lane<V>::unpack(S[l * 32 + lane], x);
 #pragma unroll
-                    for (int v = 0; v < V; ++v) {
-                        const float a = fabsf(x[v]);
-                        ab[l][v] = a;
-                        neg[v] |= (x[v] < 0.0f ? 1u : 0u) << l;
-                        mn2[v] = fminf(mn2[v], fmaxf(mn1[v], a));
-                        mn1[v] = fminf(mn1[v], a);
-                        if (SYN) syn[v] ^= S[St::HW + l * V + v];
+                        for (int v = 0; v < V; ++v) {
+                            const float a = fabsf(x[v]);
+                            ab[l][v] = a;
+                            neg[v] |= (x[v] < 0.0f ? 1u : 0u) << l;
+                            mn2[v] = fminf(mn2[v], fmaxf(mn1[v], a));
+                            mn1[v] = fminf(mn1[v], a);
+                        }
                     }
                 }
             }
             uint32_t par_all[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) par_all[v] = __popc(neg[v]) & 1u;
-            if (lane_on) {
 #pragma unroll
-                for (int l = 0; l < DCMAX; ++l) {
-                    const int o = off[l];
-                    if (!REG && o < 0) continue;
-                    const float w = __ldg(prm + 2 * l), ofs = __ldg(prm + 2 * l + 1);
-                    float out[V];
+            for (int l = 0; l < DCMAX; ++l) {
+                const int o = __shfl_sync(0xffffffffu, myoff, l);
+                if (!REG && o < 0) continue;
+                const float w = __ldg(prm + 2 * l), ofs = __ldg(prm + 2 * l + 1);
+                float out[V];
 #pragma unroll
-                    for (int v = 0; v < V; ++v) {
-                        const float m = ab[l][v] == mn1[v] ? mn2[v] : mn1[v];
-                        const float mag = fminf(fmaxf(fmaf(w, m, -ofs), 0.0f), clip);
-                        out[v] = (par_all[v] ^ ((neg[v] >> l) & 1u)) ? -mag : mag;
-                    }
-                    gmsg[(size_t)o * 32] = Lane<V>::pack(out);
+                for (int v = 0; v < V; ++v) {
+                    const float m = ab[l][v] == mn1[v] ? mn2[v] : mn1[v];
+                    const float mag = fminf(fmaxf(fmaf(w, m, -ofs), 0.0f), clip);
+                    out[v] = (par_all[v] ^ ((neg[v] >> l) & 1u)) ? -mag : mag;
                 }
+                if (lane_on) gmsg[(size_t)o * 32] = Lane<V>::pack(out);
             }
         } else {
             // min-sum, 4 frames per lane word (V == 4)
@@ -236,37 +230,27 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
             for (int l = 0; l < DCMAX; ++l) {
                 ab[l] = 0u;
                 sg[l] = 0u;
-                if (REG || off[l] >= 0) {
-                    const uint32_t x = S[l * 32 + lane];
-                    const uint32_t av = __vabsss4(x);
-                    sg[l] = x & 0x80808080u;
-                    ab[l] = av;
-                    sgn ^= sg[l];
-                    min2 = __vminu4(min2, __vmaxu4(min1, av));
-                    min1 = __vminu4(min1, av);
-                    if (SYN) {
-#pragma unroll
-                        for (int v = 0; v < V; ++v) syn[v] ^= S[St::HW + l * V + v];
+                if (REG || l < d.L) {
+                    const int o = __shfl_sync(0xffffffffu, myoff, l);
+                    if (REG || o >= 0) {
+                        const uint32_t x = S[l * 32 + lane];
+                        const uint32_t av = __vabsss4(x);
+                        sg[l] = x & 0x80808080u;
+                        ab[l] = av;
+                        sgn ^= sg[l];
+                        min2 = __vminu4(min2, __vmaxu4(min1, av));
+                        min1 = __vminu4(min1, av);
                     }
                 }
             }
-            if (lane_on) {
 #pragma unroll
-                for (int l = 0; l < DCMAX; ++l) {
-                    const int o = off[l];
-                    if (!REG && o < 0) continue;
-                    const uint32_t eq = __vcmpeq4(ab[l], min1);
-                    const uint32_t mag = (min2 & eq) | (min1 & ~eq);
-                    const uint32_t sneg = ((sgn ^ sg[l]) >> 7) & 0x01010101u;
-                    gmsg[(size_t)o * 32] = __vadd4(mag ^ (sneg * 0xffu), sneg);
-                }
-            }
-        }
-        if (SYN && lane == 0) {
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const uint32_t bad = syn[v] & actv[v];
-                if (bad) atomicOr(flags + (size_t)pk * 5 * V + (1 + par) * V + v, bad);
+            for (int l = 0; l < DCMAX; ++l) {
+                const int o = __shfl_sync(0xffffffffu, myoff, l);
+                if (!REG && o < 0) continue;
+                const uint32_t eq = __vcmpeq4(ab[l], min1);
+                const uint32_t mag = (min2 & eq) | (min1 & ~eq);
+                const uint32_t sneg = ((sgn ^ sg[l]) >> 7) & 0x01010101u;
+                if (lane_on) gmsg[(size_t)o * 32] = __vadd4(mag ^ (sneg * 0xffu), sneg);
             }
         }
         __syncwarp();
@@ -279,22 +263,23 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
 // variable pass: eqs. (bpvs), (bpd), (hrddcs) on kNV consecutive variables.
 // REG: every block of the column is present and J == JMAX.
 // ---------------------------------------------------------------------------
-template <int JMAX, int V, bool STOP, bool MS>
+template <int JMAX, int V, bool STOP, bool MS, bool REFILL = false>
 struct VnStage {
     static constexpr int MUW = MS ? 32 : 32 * V;     // channel-LLR words per variable
     static constexpr int MU = 0;
     static constexpr int AL = kNV * MUW;             // [i][j][32] edge packages
     static constexpr int HW = AL + kNV * JMAX * 32;  // old hard words [i][V]
-    static constexpr int FL = HW + kNV * V;          // done[V], unsat[V]
-    static constexpr int WORDS = (FL + 2 * V + 3) & ~3;
+    static constexpr int FL = HW + kNV * V;          // done[V], unsat[V] (refill: idle, retire, refill)
+    static constexpr int NFL = REFILL ? 3 * V : 2 * V;
+    static constexpr int WORDS = (FL + NFL + 3) & ~3;
 };
 
-template <int JMAX, int V, bool STOP, bool POST, bool XF, bool MS, bool REG>
+template <int JMAX, int V, bool STOP, bool POST, bool XF, bool MS, bool REG, bool REFILL = false>
 __global__ void __launch_bounds__(kWarps * 32)
-vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__restrict__ mu, uint32_t *__restrict__ hw,
+vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict__ mu, uint32_t *__restrict__ hw,
                uint32_t *__restrict__ flags, float *__restrict__ post, int32_t *__restrict__ iters,
-               const int *__restrict__ act, float clip, float lsb, int it, int par) {
-    using St = VnStage<JMAX, V, STOP, MS>;
+               const int *__restrict__ act, float clip, float lsb, int it, int par, RefillArgs rf) {
+    using St = VnStage<JMAX, V, STOP, MS, REFILL>;
     constexpr int W = 32 * V;
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ int s_sh[kMaxJ * kMaxL], s_eo[kMaxJ * kMaxL];
@@ -351,10 +336,17 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
                 const int i = lane / V, v = lane - i * V;
                 const int n = n0 + i;
                 if (n < d.N) cp_async4(dst + St::HW + lane, hw + ((size_t)pk * d.N + n) * V + v);
-            } else if (lane >= 32 - 2 * V) {
-                const int q = lane - (32 - 2 * V);  // 0..2V-1: done[V], unsat[par][V]
-                const int off = q < V ? q : (1 + par) * V + (q - V);
-                cp_async4(dst + St::FL + q, flags + (size_t)pk * 5 * V + off);
+            } else if (lane >= 32 - St::NFL) {
+                const int q = lane - (32 - St::NFL);
+                if (REFILL) {
+                    // idle[V] (the done words), retire[V], refill[V]
+                    if (q < V) cp_async4(dst + St::FL + q, flags + (size_t)pk * 5 * V + q);
+                    else cp_async4(dst + St::FL + q, rf.sflags + (size_t)pk * 2 * V + (q - V));
+                } else {
+                    // done[V], unsat[par][V]
+                    const int off = q < V ? q : (1 + par) * V + (q - V);
+                    cp_async4(dst + St::FL + q, flags + (size_t)pk * 5 * V + off);
+                }
             }
         }
         cp_async_commit();
@@ -373,10 +365,19 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
         const int pk = __ldg(list + a);
         uint32_t *gmsg = msg + (size_t)pk * d.E * 32 + lane;
         // frames stopped so far, and the ones whose last decisions satisfied every check
-        uint32_t frozen[V];
+        uint32_t frozen[V], refill[V], retire[V];
         bool lane_on = false;
+        if (REFILL) {
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
+            for (int v = 0; v < V; ++v) {
+                retire[v] = S[St::FL + V + v];
+                refill[v] = S[St::FL + 2 * V + v];
+                frozen[v] = S[St::FL + v] | retire[v];
+                lane_on |= ((~frozen[v] | refill[v]) >> lane) & 1u;
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < V && !REFILL; ++v) {
             uint32_t dn = S[St::FL + v];
             if (STOP) {
                 const uint32_t newly = ~dn & ~S[St::FL + V + v];
@@ -397,6 +398,31 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
             lane_on |= ((~dn) >> lane) & 1u;
         }
         const int n0 = g * kNV;
+        // refill: a new frame's channel LLRs are already in the channel store
+        bool any_refill = false;
+        uint32_t rmask = 0u;  // min-sum: byte mask of the new frames in the lane word
+        if (REFILL) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                any_refill |= refill[v] != 0u;
+                if ((refill[v] >> lane) & 1u) rmask |= 0xffu << (8 * v);
+            }
+            // errors of the frames retiring now: their last decisions are the staged hard words
+            bool any_retire = false;
+#pragma unroll
+            for (int v = 0; v < V; ++v) any_retire |= retire[v] != 0u;
+            if (any_retire) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    if (!((retire[v] >> lane) & 1u)) continue;
+                    int cnt = 0;
+#pragma unroll
+                    for (int i = 0; i < kNV; ++i)
+                        if (n0 + i < d.N) cnt += (S[St::HW + i * V + v] >> lane) & 1u;
+                    if (cnt) atomicAdd(rf.errs + (size_t)pk * W + lane * V + v, cnt);
+                }
+            }
+        }
         int l = n0 / d.p, k = n0 - l * d.p;
 #pragma unroll
         for (int i = 0; i < kNV; ++i, ++k) {
@@ -432,6 +458,8 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
                         for (int j2 = 0; j2 < JMAX; ++j2)
                             if (j2 != jj) s += aj[j2][v];
                         b[v] = clipf(s, clip);
+                        // a new frame starts from beta = mu (initialization of Algorithm 1)
+                        if (REFILL && any_refill && ((refill[v] >> lane) & 1u)) b[v] = m[v];
                         if (XF) {
                             // the check pass sums phi(|beta|): evaluate it here, from the unrounded beta
                             const float f = phi_warp(fabsf(b[v]));
@@ -443,6 +471,11 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
                 float pst[V];
 #pragma unroll
                 for (int v = 0; v < V; ++v) pst[v] = clipf(tot[v], clip);
+                if (REFILL && any_refill) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        if ((refill[v] >> lane) & 1u) pst[v] = m[v];
+                }
                 if (POST && lane_on) {
                     float *dst = post + ((size_t)pk * d.N + n) * W + lane * V;
 #pragma unroll
@@ -464,6 +497,11 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
 #pragma unroll
                     for (int v = 0; v < 4; ++v) tot[v] += sbyte(aw[jj], v);
                 }
+                if (REFILL && any_refill && rmask) {
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+                        if ((rmask >> (8 * v)) & 1u) tot[v] = sbyte(qw, v);
+                }
                 if (lane_on) {
 #pragma unroll
                     for (int jj = 0; jj < JMAX; ++jj) {
@@ -473,6 +511,7 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
 #pragma unroll
                         for (int v = 0; v < 4; ++v) {
                             int b = tot[v] - sbyte(aw[jj], v);
+                            if (REFILL && any_refill && ((rmask >> (8 * v)) & 1u)) b = sbyte(qw, v);
                             b = b > 127 ? 127 : (b < -127 ? -127 : b);
                             o |= ((uint32_t)(uint8_t)(int8_t)b) << (8 * v);
                         }
@@ -492,7 +531,8 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     const uint32_t old = S[St::HW + i * V + v];
-                    hw[((size_t)pk * d.N + n) * V + v] = (outb[v] & ~frozen[v]) | (old & frozen[v]);
+                    const uint32_t keep = REFILL ? (frozen[v] & ~refill[v]) : frozen[v];
+                    hw[((size_t)pk * d.N + n) * V + v] = (outb[v] & ~keep) | (old & keep);
                 }
             }
         }
@@ -506,7 +546,8 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
 // list of packages with at least one frame still running: act[0] = count,
 // act[1..] = package indices (one block)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) compact_kernel(const uint32_t *__restrict__ flags, int P, int V,
+__global__ void __launch_bounds__(1024) compact_kernel(const uint32_t *__restrict__ flags,
+                                                       const uint32_t *__restrict__ sflags, int P, int V,
                                                        int *__restrict__ act) {
     __shared__ int wsum[32];
     __shared__ int s_base;
@@ -517,7 +558,10 @@ __global__ void __launch_bounds__(1024) compact_kernel(const uint32_t *__restric
         const int pk = p0 + threadIdx.x;
         bool on = false;
         if (pk < P)
-            for (int v = 0; v < V; ++v) on |= ~flags[(size_t)pk * 5 * V + v] != 0u;
+            for (int v = 0; v < V; ++v) {
+                on |= ~flags[(size_t)pk * 5 * V + v] != 0u;
+                if (sflags) on |= sflags[(size_t)pk * 2 * V + v] != 0u;  // retiring frames
+            }
         const uint32_t bal = __ballot_sync(0xffffffffu, on);
         if (lane == 0) wsum[warp] = __popc(bal);
         __syncthreads();
@@ -564,35 +608,25 @@ int persistent_blocks(K kernel, size_t smem) {
 }
 }  // namespace
 
-template <int DCMAX, int V, bool SYN, bool XF, int MODE, bool REG>
-static void launch_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int par, int it, cudaStream_t s) {
-    auto k = cn_pipe_kernel<DCMAX, V, SYN, XF, MODE, REG>;
-    const size_t smem = (size_t)kWarps * kStages * CnStage<DCMAX, V, SYN>::WORDS * 4;
+template <int DCMAX, int V, bool XF, int MODE, bool REG>
+static void launch_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, cudaStream_t s) {
+    auto k = cn_pipe_kernel<DCMAX, V, XF, MODE, REG>;
+    const size_t smem = (size_t)kWarps * kStages * CnStage<DCMAX>::WORDS * 4;
     const int blocks = persistent_blocks(k, smem);
     const float *np = o.noms_params ? o.noms_params + (size_t)(it - 1) * c->d.J * c->d.L * 2 : nullptr;
-    k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, c->ws.hw, c->ws.flags, c->ws.act, o.clip, par,
-                                        np);
+    k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, c->ws.flags, c->ws.act, o.clip, np);
 }
 
 template <int DCMAX, bool REG>
-static void cn_pipe_dispatch(ldpc_code c, const ldpc_decode_opts &o, bool syn, int par, int it, cudaStream_t s) {
-    if (o.algo == LDPC_ALGO_MS) {
-        if (syn) launch_cn_pipe<DCMAX, 4, true, false, kModeMS, REG>(c, o, par, it, s);
-        else launch_cn_pipe<DCMAX, 4, false, false, kModeMS, REG>(c, o, par, it, s);
-    } else if (o.algo == LDPC_ALGO_NOMS) {
-        if (o.msg == LDPC_MSG_F16) {
-            if (syn) launch_cn_pipe<DCMAX, 2, true, false, kModeNOMS, REG>(c, o, par, it, s);
-            else launch_cn_pipe<DCMAX, 2, false, false, kModeNOMS, REG>(c, o, par, it, s);
-        } else {
-            if (syn) launch_cn_pipe<DCMAX, 1, true, false, kModeNOMS, REG>(c, o, par, it, s);
-            else launch_cn_pipe<DCMAX, 1, false, false, kModeNOMS, REG>(c, o, par, it, s);
-        }
+static void cn_pipe_dispatch(ldpc_code c, const ldpc_decode_opts &o, int it, cudaStream_t s) {
+    if (o.algo == LDPC_ALGO_MS) launch_cn_pipe<DCMAX, 4, false, kModeMS, REG>(c, o, it, s);
+    else if (o.algo == LDPC_ALGO_NOMS) {
+        if (o.msg == LDPC_MSG_F16) launch_cn_pipe<DCMAX, 2, false, kModeNOMS, REG>(c, o, it, s);
+        else launch_cn_pipe<DCMAX, 1, false, kModeNOMS, REG>(c, o, it, s);
     } else if (o.msg == LDPC_MSG_F16) {
-        if (syn) launch_cn_pipe<DCMAX, 2, true, false, kModeSP, REG>(c, o, par, it, s);
-        else launch_cn_pipe<DCMAX, 2, false, false, kModeSP, REG>(c, o, par, it, s);
+        launch_cn_pipe<DCMAX, 2, false, kModeSP, REG>(c, o, it, s);
     } else {
-        if (syn) launch_cn_pipe<DCMAX, 1, true, true, kModeSP, REG>(c, o, par, it, s);
-        else launch_cn_pipe<DCMAX, 1, false, true, kModeSP, REG>(c, o, par, it, s);
+        launch_cn_pipe<DCMAX, 1, true, kModeSP, REG>(c, o, it, s);
     }
 }
 
@@ -604,25 +638,25 @@ static bool regular_rows(const QcDesc &d, int dcmax) {
     return true;
 }
 
-ldpc_status qc_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, bool syn, int par, int it, cudaStream_t s) {
+ldpc_status qc_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, cudaStream_t s) {
     const QcDesc &d = c->d;
-    if (regular_rows(d, 24)) cn_pipe_dispatch<24, true>(c, o, syn, par, it, s);
-    else if (d.L <= 8) cn_pipe_dispatch<8, false>(c, o, syn, par, it, s);
-    else if (d.L <= 16) cn_pipe_dispatch<16, false>(c, o, syn, par, it, s);
-    else if (d.L <= 24) cn_pipe_dispatch<24, false>(c, o, syn, par, it, s);
-    else cn_pipe_dispatch<32, false>(c, o, syn, par, it, s);
+    if (regular_rows(d, 24)) cn_pipe_dispatch<24, true>(c, o, it, s);
+    else if (d.L <= 8) cn_pipe_dispatch<8, false>(c, o, it, s);
+    else if (d.L <= 16) cn_pipe_dispatch<16, false>(c, o, it, s);
+    else if (d.L <= 24) cn_pipe_dispatch<24, false>(c, o, it, s);
+    else cn_pipe_dispatch<32, false>(c, o, it, s);
     LDPC_CUDA_TRY(cudaGetLastError());
     return LDPC_OK;
 }
 
 template <int JMAX, int V, bool STOP, bool POST, bool XF, bool MS, bool REG>
 static void launch_vn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, int par, cudaStream_t s) {
-    auto k = vn_pipe_kernel<JMAX, V, STOP, POST, XF, MS, REG>;
+    auto k = vn_pipe_kernel<JMAX, V, STOP, POST, XF, MS, REG, false>;
     const size_t smem = (size_t)kWarps * kStages * VnStage<JMAX, V, STOP, MS>::WORDS * 4;
     const int blocks = persistent_blocks(k, smem);
-    k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, (const uint32_t *)c->ws.mu, c->ws.hw,
-                                        c->ws.flags, c->ws.post, c->ws.iters, c->ws.act, o.clip,
-                                        ldexpf(1.0f, -o.frac_bits), it, par);
+    k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, (uint32_t *)c->ws.mu, c->ws.hw, c->ws.flags,
+                                        c->ws.post, c->ws.iters, c->ws.act, o.clip, ldexpf(1.0f, -o.frac_bits), it,
+                                        par, RefillArgs{});
 }
 
 template <int JMAX, bool STOP, bool POST, bool REG>
@@ -658,8 +692,42 @@ ldpc_status qc_vn_pipe(ldpc_code c, const ldpc_decode_opts &o, bool stop, bool p
     return LDPC_OK;
 }
 
-ldpc_status qc_compact(ldpc_code c, int P, int V, cudaStream_t s) {
-    compact_kernel<<<1, 1024, 0, s>>>(c->ws.flags, P, V, c->ws.act);
+ldpc_status qc_compact(ldpc_code c, int P, int V, cudaStream_t s, const uint32_t *sflags) {
+    compact_kernel<<<1, 1024, 0, s>>>(c->ws.flags, sflags, P, V, c->ws.act);
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
+}  // namespace ldpc
+
+namespace ldpc {
+
+// variable pass of the continuous simulation: no early-stop bookkeeping (the
+// retire kernel owns the flag words), no posteriors
+template <int JMAX, int V, bool XF, bool MS, bool REG>
+static void launch_vn_refill(ldpc_code c, const ldpc_decode_opts &o, const RefillArgs &rf, cudaStream_t s) {
+    auto k = vn_pipe_kernel<JMAX, V, false, false, XF, MS, REG, true>;
+    const size_t smem = (size_t)kWarps * kStages * VnStage<JMAX, V, false, MS, true>::WORDS * 4;
+    const int blocks = persistent_blocks(k, smem);
+    k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, (uint32_t *)c->ws.mu, c->ws.hw, c->ws.flags,
+                                        nullptr, nullptr, c->ws.act, o.clip, ldexpf(1.0f, -o.frac_bits), 0, 0, rf);
+}
+
+template <int JMAX, bool REG>
+static void vn_refill_dispatch(ldpc_code c, const ldpc_decode_opts &o, const RefillArgs &rf, cudaStream_t s) {
+    if (o.algo == LDPC_ALGO_MS) launch_vn_refill<JMAX, 4, false, true, REG>(c, o, rf, s);
+    else if (o.msg == LDPC_MSG_F16) launch_vn_refill<JMAX, 2, false, false, REG>(c, o, rf, s);
+    else launch_vn_refill<JMAX, 1, true, false, REG>(c, o, rf, s);
+}
+
+ldpc_status qc_vn_refill(ldpc_code c, const ldpc_decode_opts &o, const RefillArgs &rf, cudaStream_t s) {
+    const QcDesc &d = c->d;
+    bool full = true;
+    for (int i = 0; i < d.J * d.L; ++i) full &= d.shift[i] >= 0;
+    if (full && d.J == 4) vn_refill_dispatch<4, true>(c, o, rf, s);
+    else if (full && d.J == 3) vn_refill_dispatch<3, true>(c, o, rf, s);
+    else if (d.J <= 4) vn_refill_dispatch<4, false>(c, o, rf, s);
+    else vn_refill_dispatch<8, false>(c, o, rf, s);
     LDPC_CUDA_TRY(cudaGetLastError());
     return LDPC_OK;
 }

@@ -248,10 +248,54 @@ def test_ber_sim_counts_match_oracle(pkg):
 
 
 def test_ber_sim_stops_after_target_errors(pkg):
+    """Once the target is met no new frame starts and the frames in flight finish: the frames counted are
+    exactly ids 0 .. frames-1, so a run capped at that many frames (no target) gives the same counts."""
     shifts = synth.qc_shifts(3, 6, 64, seed=1)
     code = pkg.QCCode(shifts, 64)
     res = code.ber_sim(0.5, seed=1, max_frames=10 ** 6, target_frame_errors=100, gamma=256, max_iter=10)
-    assert res["frame_errors"] >= 100 and res["frames"] % 256 == 0 and res["frames"] <= 10 ** 6
+    assert 100 <= res["frame_errors"] and res["frames"] < 10 ** 6
+    # beyond the target: frames in flight (256 slots), the step that crossed it (tallies and refills)
+    assert res["frame_errors"] <= 100 + 3 * 256
+    again = code.ber_sim(0.5, seed=1, max_frames=res["frames"], target_frame_errors=10 ** 9, gamma=256, max_iter=10)
+    for k in ("frames", "frame_errors", "bit_errors", "iters_sum", "undetected"):
+        assert again[k] == res[k], k
+
+
+@pytest.mark.parametrize("algo,msg,exact", [("sp", "f32", True), ("ms", "i8", True), ("sp", "f16", False)])
+def test_ber_sim_refill_equals_batch_decode(pkg, algo, msg, exact):
+    """The continuous simulator (slots refilled as frames stop, several frames per slot) gives every frame
+    the decisions, iteration count and ok flag of the batch decoder on the same channel frames."""
+    A = {"sp": pkg.ALGO_SP, "ms": pkg.ALGO_MS}[algo]
+    M = {"f32": pkg.MSG_F32, "f16": pkg.MSG_F16, "i8": pkg.MSG_I8}[msg]
+    shifts = synth.qc_shifts(4, 12, 96, seed=7)
+    code = pkg.QCCode(shifts, 96)
+    frames, first, ebn0 = 1500, 77, 2.0
+    res = code.ber_sim(ebn0, seed=11, first_frame=first, max_frames=frames, target_frame_errors=10 ** 9, gamma=256,
+                       max_iter=25, early_stop=1, algo=A, msg=M)
+    llr = code.channel(ebn0, 11, first, frames)
+    _, hard, iters, ok = code.decode(llr, max_iter=25, early_stop=True, algo=A, msg=M, want_post=False)
+    errs = hard.sum(dim=1).cpu().numpy().astype(np.int64)
+    okn = ok.cpu().numpy()
+    want = {"frames": frames, "frame_errors": int((errs > 0).sum()), "bit_errors": int(errs.sum()),
+            "iters_sum": int(iters.cpu().numpy().sum()), "undetected": int(((errs > 0) & (okn == 1)).sum())}
+    assert want["frame_errors"] > 0 and want["frames"] - want["frame_errors"] > 0
+    if exact:
+        for k, v in want.items():
+            assert res[k] == v, (k, res[k], v)
+    else:
+        # FP16 messages: the batch decoder's first check pass reads the FP32 channel LLRs, the continuous
+        # one their FP16 rounding (beta = mu stored as a message); totals agree statistically
+        assert res["frames"] == frames
+        assert abs(res["frame_errors"] - want["frame_errors"]) <= max(3, 0.05 * want["frame_errors"])
+        assert abs(res["iters_sum"] - want["iters_sum"]) <= 0.02 * want["iters_sum"]
+
+
+def test_ber_sim_no_early_stop_runs_max_iter(pkg):
+    shifts = synth.qc_shifts(3, 6, 64, seed=1)
+    code = pkg.QCCode(shifts, 64)
+    res = code.ber_sim(2.0, seed=4, max_frames=700, target_frame_errors=10 ** 9, gamma=128, max_iter=7,
+                       early_stop=0)
+    assert res["frames"] == 700 and res["iters_sum"] == 7 * 700
 
 
 def test_resume_adds_up(pkg):
