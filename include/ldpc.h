@@ -179,12 +179,20 @@ typedef struct {
 
 /*
  * ldpc_ber_sim -- the Monte-Carlo protocol of Sec. V: fixed iteration cap,
- * batches of gamma frames generated and decoded on the device, error counts
- * reduced on the device; stop once frame_errors >= target_frame_errors (the
- * paper uses 100) or frames >= max_frames.  Frames first_frame,
- * first_frame+1, ... are drawn exactly as ldpc_channel draws them, so a run
- * can be resumed from (seed, first_frame + out->frames) and partial results
- * added.  Synchronizes `stream` once per batch to test the stop rule.
+ * frames generated and decoded on the device, error counts reduced on the
+ * device.  Sum-product and min-sum run continuously: gamma frame slots
+ * (rounded up to whole packages of 32 V frames), and a slot takes the next
+ * frame in the step after its frame stops (C-11 syndrome check after >= 1
+ * iterations when opts->early_stop, or the iteration cap), so each frame
+ * gets exactly the iterations and decisions that ldpc_decode gives it.
+ * Once frame_errors >= target_frame_errors (the paper uses 100) no new frame
+ * starts and the frames in flight finish; at most max_frames frames start.
+ * The frames counted are always first_frame .. first_frame + out->frames - 1,
+ * drawn exactly as ldpc_channel draws them, so a run can be resumed from
+ * (seed, first_frame + out->frames) and partial results added.  Learned NOMS
+ * (parameters per iteration) runs in batches of gamma frames and tests the
+ * stop rule after each batch.  Blocks the calling thread until the run ends
+ * (it reads the totals every two steps).
  *   out: host pointer, filled on return.
  */
 ldpc_status ldpc_ber_sim(ldpc_code code, double ebn0_db, uint64_t seed, uint64_t first_frame, int64_t max_frames,
