@@ -97,7 +97,10 @@ ldpc_status qc_syndrome(ldpc_code c, int P, int V, int word, cudaStream_t s);
 ldpc_status phi_eval(const float *x, float *y, int n, int variant, cudaStream_t s);
 void noms_free(ldpc_noms_state *w);
 // pipelined node passes (qc_pipe.cu)
-ldpc_status qc_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, cudaStream_t s);
+// fresh (continuous simulation, else NULL): per package [2V] words, bits V..2V-1 mark
+// frames that entered their slot this step; their outgoing messages are set to 0
+ldpc_status qc_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, cudaStream_t s,
+                       const uint32_t *fresh = nullptr);
 ldpc_status qc_vn_pipe(ldpc_code c, const ldpc_decode_opts &o, bool stop, bool post, int it, int par,
                        cudaStream_t s);
 // packages with a running frame; with sflags (continuous simulation) also those

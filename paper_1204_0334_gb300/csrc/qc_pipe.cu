@@ -6,7 +6,7 @@
 // their channel LLRs (variable pass) before it can compute, and then spends a
 // long stretch on arithmetic: with one work item per warp the SM runs out of
 // bytes in flight.  Here warps are persistent: each walks a strided list of
-// work items and keeps the packages of the next kStages-1 items in flight in
+// work items and keeps the packages of its next items in flight in
 // its own shared-memory ring, copied with cp.async (16 bytes per lane,
 // completion tracked by cp.async groups -- hardware waits, no spinning), while
 // it computes the current item out of shared memory.  Results go straight to
@@ -19,7 +19,14 @@
 
 namespace ldpc {
 
-constexpr int kStages = 3;
+#ifndef LDPC_CN_STAGES
+#define LDPC_CN_STAGES 3
+#endif
+#ifndef LDPC_VN_STAGES
+#define LDPC_VN_STAGES 3
+#endif
+constexpr int kCnStages = LDPC_CN_STAGES;  // ring slots per warp, check pass
+constexpr int kVnStages = LDPC_VN_STAGES;  // ring slots per warp, variable pass
 constexpr int kModeSP = 0, kModeMS = 1, kModeNOMS = 2;
 constexpr int kNV = 4;  // consecutive variables per variable-pass work item
 
@@ -39,8 +46,8 @@ __device__ __forceinline__ void cp_async_wait() {
 template <int DCMAX>
 struct CnStage {
     static constexpr int SEG = DCMAX * 32;  // edge packages, [l][32 words]
-    static constexpr int FL = SEG;          // done words (V <= 4)
-    static constexpr int WORDS = SEG + 4;
+    static constexpr int FL = SEG;          // done words [V], fresh-frame words [V] (V <= 4)
+    static constexpr int WORDS = SEG + 8;
 };
 
 // ---------------------------------------------------------------------------
@@ -53,7 +60,8 @@ struct CnStage {
 template <int DCMAX, int V, bool XF, int MODE, bool REG>
 __global__ void __launch_bounds__(kWarps * 32)
 cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__restrict__ flags,
-               const int *__restrict__ act, float clip, const float *__restrict__ nparams) {
+               const uint32_t *__restrict__ fresh, const int *__restrict__ act, float clip,
+               const float *__restrict__ nparams) {
     using St = CnStage<DCMAX>;
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ int s_sh[kMaxJ * kMaxL], s_eo[kMaxJ * kMaxL];
@@ -63,7 +71,7 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *ring = smem + warp * kStages * St::WORDS;
+    uint32_t *ring = smem + warp * kCnStages * St::WORDS;
     // work items (package, check row); the host keeps packages * rows below 2^31
     const int total = act[0] * d.M;
     const int *list = act + 1;
@@ -101,28 +109,37 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
                 }
             }
             if (lane < V) cp_async4(dst + St::FL + lane, flags + (size_t)pk * 5 * V + lane);
+            else if (fresh && lane < 2 * V) cp_async4(dst + St::FL + lane, fresh + (size_t)pk * 2 * V + lane);
         }
         cp_async_commit();
         return mine;
     };
 
-    int offr[kStages];
+    int offr[kCnStages];
 #pragma unroll
-    for (int s = 0; s < kStages - 1; ++s) offr[s] = issue(item + s * GW, s);
+    for (int s = 0; s < kCnStages - 1; ++s) offr[s] = issue(item + s * GW, s);
     int slot = 0;
     for (; item < total; item += GW) {
-        offr[kStages - 1] = issue(item + (kStages - 1) * GW, (slot + kStages - 1) % kStages);
-        cp_async_wait<kStages - 1>();
+        offr[kCnStages - 1] = issue(item + (kCnStages - 1) * GW, (slot + kCnStages - 1) % kCnStages);
+        cp_async_wait<kCnStages - 1>();
         __syncwarp();
         const uint32_t *S = ring + slot * St::WORDS;
         const int myoff = offr[0];
 #pragma unroll
-        for (int s = 0; s < kStages - 1; ++s) offr[s] = offr[s + 1];
+        for (int s = 0; s < kCnStages - 1; ++s) offr[s] = offr[s + 1];
         const int pk = __ldg(list + item / d.M);
         uint32_t *gmsg = msg + (size_t)pk * d.E * 32 + lane;
         bool lane_on = false;
+        // frames that entered their slot this step (continuous simulation): alpha = 0, so the
+        // variable pass that follows starts them at beta = mu (initialization of Alg. 1)
+        bool fr[V];
+        uint32_t frmask = 0u;
 #pragma unroll
-        for (int v = 0; v < V; ++v) lane_on |= ((~S[St::FL + v]) >> lane) & 1u;
+        for (int v = 0; v < V; ++v) {
+            lane_on |= ((~S[St::FL + v]) >> lane) & 1u;
+            fr[v] = fresh && ((S[St::FL + V + v] >> lane) & 1u);
+            if (fr[v]) frmask |= 0xffu << (8 * v);
+        }
         if constexpr (MODE == kModeSP) {
             // xs: signed terms sign(beta) * phi(|beta|) (XF: as stored by the variable pass);
             // the output sign is the XOR of the other edges' sign bits
@@ -170,6 +187,7 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
                         const float mag = fminf(phi_warp(pre[l][v] + suf[v]), clip);
                         out[v] = __uint_as_float(__float_as_uint(mag) |
                                                  ((sgn[v] ^ __float_as_uint(xs[l][v])) & 0x80000000u));
+                        if (fr[v]) out[v] = 0.0f;
                     }
                     if (lane_on) gmsg[(size_t)o * 32] = Lane<V>::pack(out);
                 }
@@ -219,6 +237,7 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
                     const float m = ab[l][v] == mn1[v] ? mn2[v] : mn1[v];
                     const float mag = fminf(fmaxf(fmaf(w, m, -ofs), 0.0f), clip);
                     out[v] = (par_all[v] ^ ((neg[v] >> l) & 1u)) ? -mag : mag;
+                    if (fr[v]) out[v] = 0.0f;
                 }
                 if (lane_on) gmsg[(size_t)o * 32] = Lane<V>::pack(out);
             }
@@ -250,11 +269,11 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
                 const uint32_t eq = __vcmpeq4(ab[l], min1);
                 const uint32_t mag = (min2 & eq) | (min1 & ~eq);
                 const uint32_t sneg = ((sgn ^ sg[l]) >> 7) & 0x01010101u;
-                if (lane_on) gmsg[(size_t)o * 32] = __vadd4(mag ^ (sneg * 0xffu), sneg);
+                if (lane_on) gmsg[(size_t)o * 32] = __vadd4(mag ^ (sneg * 0xffu), sneg) & ~frmask;
             }
         }
         __syncwarp();
-        slot = (slot + 1) % kStages;
+        slot = (slot + 1) % kCnStages;
     }
     cp_async_wait<0>();
 }
@@ -263,14 +282,14 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
 // variable pass: eqs. (bpvs), (bpd), (hrddcs) on kNV consecutive variables.
 // REG: every block of the column is present and J == JMAX.
 // ---------------------------------------------------------------------------
-template <int JMAX, int V, bool STOP, bool MS, bool REFILL = false>
+template <int JMAX, int V, bool STOP, bool MS>
 struct VnStage {
     static constexpr int MUW = MS ? 32 : 32 * V;     // channel-LLR words per variable
     static constexpr int MU = 0;
     static constexpr int AL = kNV * MUW;             // [i][j][32] edge packages
     static constexpr int HW = AL + kNV * JMAX * 32;  // old hard words [i][V]
-    static constexpr int FL = HW + kNV * V;          // done[V], unsat[V] (refill: idle, retire, refill)
-    static constexpr int NFL = REFILL ? 3 * V : 2 * V;
+    static constexpr int FL = HW + kNV * V;          // done[V], then unsat[V] (continuous simulation: retire[V])
+    static constexpr int NFL = 2 * V;
     static constexpr int WORDS = (FL + NFL + 3) & ~3;
 };
 
@@ -279,7 +298,7 @@ __global__ void __launch_bounds__(kWarps * 32)
 vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict__ mu, uint32_t *__restrict__ hw,
                uint32_t *__restrict__ flags, float *__restrict__ post, int32_t *__restrict__ iters,
                const int *__restrict__ act, float clip, float lsb, int it, int par, RefillArgs rf) {
-    using St = VnStage<JMAX, V, STOP, MS, REFILL>;
+    using St = VnStage<JMAX, V, STOP, MS>;
     constexpr int W = 32 * V;
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ int s_sh[kMaxJ * kMaxL], s_eo[kMaxJ * kMaxL];
@@ -289,7 +308,7 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *ring = smem + warp * kStages * St::WORDS;
+    uint32_t *ring = smem + warp * kVnStages * St::WORDS;
     const int G = (d.N + kNV - 1) / kNV;
     const int total = act[0] * G;  // work items (package, group of kNV variables)
     const int *list = act + 1;
@@ -339,7 +358,7 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
             } else if (lane >= 32 - St::NFL) {
                 const int q = lane - (32 - St::NFL);
                 if (REFILL) {
-                    // idle[V] (the done words), retire[V], refill[V]
+                    // done[V] (slots without a running frame), retire[V]
                     if (q < V) cp_async4(dst + St::FL + q, flags + (size_t)pk * 5 * V + q);
                     else cp_async4(dst + St::FL + q, rf.sflags + (size_t)pk * 2 * V + (q - V));
                 } else {
@@ -353,11 +372,11 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
     };
 
 #pragma unroll
-    for (int s = 0; s < kStages - 1; ++s) issue(item + s * GW, s);
+    for (int s = 0; s < kVnStages - 1; ++s) issue(item + s * GW, s);
     int slot = 0;
     for (; item < total; item += GW) {
-        issue(item + (kStages - 1) * GW, (slot + kStages - 1) % kStages);
-        cp_async_wait<kStages - 1>();
+        issue(item + (kVnStages - 1) * GW, (slot + kVnStages - 1) % kVnStages);
+        cp_async_wait<kVnStages - 1>();
         __syncwarp();
         const uint32_t *S = ring + slot * St::WORDS;
         const int a = item / G;
@@ -365,15 +384,14 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
         const int pk = __ldg(list + a);
         uint32_t *gmsg = msg + (size_t)pk * d.E * 32 + lane;
         // frames stopped so far, and the ones whose last decisions satisfied every check
-        uint32_t frozen[V], refill[V], retire[V];
+        uint32_t frozen[V], retire[V];
         bool lane_on = false;
         if (REFILL) {
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 retire[v] = S[St::FL + V + v];
-                refill[v] = S[St::FL + 2 * V + v];
-                frozen[v] = S[St::FL + v] | retire[v];
-                lane_on |= ((~frozen[v] | refill[v]) >> lane) & 1u;
+                frozen[v] = S[St::FL + v];
+                lane_on |= ((~frozen[v]) >> lane) & 1u;
             }
         }
 #pragma unroll
@@ -398,16 +416,9 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
             lane_on |= ((~dn) >> lane) & 1u;
         }
         const int n0 = g * kNV;
-        // refill: a new frame's channel LLRs are already in the channel store
-        bool any_refill = false;
-        uint32_t rmask = 0u;  // min-sum: byte mask of the new frames in the lane word
         if (REFILL) {
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                any_refill |= refill[v] != 0u;
-                if ((refill[v] >> lane) & 1u) rmask |= 0xffu << (8 * v);
-            }
-            // errors of the frames retiring now: their last decisions are the staged hard words
+            // wrong bits of the frames that retired this step: their last decisions are the staged
+            // hard words (a new frame in the same slot writes its first decisions below)
             bool any_retire = false;
 #pragma unroll
             for (int v = 0; v < V; ++v) any_retire |= retire[v] != 0u;
@@ -458,8 +469,6 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
                         for (int j2 = 0; j2 < JMAX; ++j2)
                             if (j2 != jj) s += aj[j2][v];
                         b[v] = clipf(s, clip);
-                        // a new frame starts from beta = mu (initialization of Algorithm 1)
-                        if (REFILL && any_refill && ((refill[v] >> lane) & 1u)) b[v] = m[v];
                         if (XF) {
                             // the check pass sums phi(|beta|): evaluate it here, from the unrounded beta
                             const float f = phi_warp(fabsf(b[v]));
@@ -471,11 +480,6 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
                 float pst[V];
 #pragma unroll
                 for (int v = 0; v < V; ++v) pst[v] = clipf(tot[v], clip);
-                if (REFILL && any_refill) {
-#pragma unroll
-                    for (int v = 0; v < V; ++v)
-                        if ((refill[v] >> lane) & 1u) pst[v] = m[v];
-                }
                 if (POST && lane_on) {
                     float *dst = post + ((size_t)pk * d.N + n) * W + lane * V;
 #pragma unroll
@@ -497,11 +501,6 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
 #pragma unroll
                     for (int v = 0; v < 4; ++v) tot[v] += sbyte(aw[jj], v);
                 }
-                if (REFILL && any_refill && rmask) {
-#pragma unroll
-                    for (int v = 0; v < 4; ++v)
-                        if ((rmask >> (8 * v)) & 1u) tot[v] = sbyte(qw, v);
-                }
                 if (lane_on) {
 #pragma unroll
                     for (int jj = 0; jj < JMAX; ++jj) {
@@ -511,7 +510,6 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
 #pragma unroll
                         for (int v = 0; v < 4; ++v) {
                             int b = tot[v] - sbyte(aw[jj], v);
-                            if (REFILL && any_refill && ((rmask >> (8 * v)) & 1u)) b = sbyte(qw, v);
                             b = b > 127 ? 127 : (b < -127 ? -127 : b);
                             o |= ((uint32_t)(uint8_t)(int8_t)b) << (8 * v);
                         }
@@ -531,13 +529,12 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     const uint32_t old = S[St::HW + i * V + v];
-                    const uint32_t keep = REFILL ? (frozen[v] & ~refill[v]) : frozen[v];
-                    hw[((size_t)pk * d.N + n) * V + v] = (outb[v] & ~keep) | (old & keep);
+                    hw[((size_t)pk * d.N + n) * V + v] = (outb[v] & ~frozen[v]) | (old & frozen[v]);
                 }
             }
         }
         __syncwarp();
-        slot = (slot + 1) % kStages;
+        slot = (slot + 1) % kVnStages;
     }
     cp_async_wait<0>();
 }
@@ -609,24 +606,24 @@ int persistent_blocks(K kernel, size_t smem) {
 }  // namespace
 
 template <int DCMAX, int V, bool XF, int MODE, bool REG>
-static void launch_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, cudaStream_t s) {
+static void launch_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, const uint32_t *fresh, cudaStream_t s) {
     auto k = cn_pipe_kernel<DCMAX, V, XF, MODE, REG>;
-    const size_t smem = (size_t)kWarps * kStages * CnStage<DCMAX>::WORDS * 4;
+    const size_t smem = (size_t)kWarps * kCnStages * CnStage<DCMAX>::WORDS * 4;
     const int blocks = persistent_blocks(k, smem);
     const float *np = o.noms_params ? o.noms_params + (size_t)(it - 1) * c->d.J * c->d.L * 2 : nullptr;
-    k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, c->ws.flags, c->ws.act, o.clip, np);
+    k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, c->ws.flags, fresh, c->ws.act, o.clip, np);
 }
 
 template <int DCMAX, bool REG>
-static void cn_pipe_dispatch(ldpc_code c, const ldpc_decode_opts &o, int it, cudaStream_t s) {
-    if (o.algo == LDPC_ALGO_MS) launch_cn_pipe<DCMAX, 4, false, kModeMS, REG>(c, o, it, s);
+static void cn_pipe_dispatch(ldpc_code c, const ldpc_decode_opts &o, int it, const uint32_t *fresh, cudaStream_t s) {
+    if (o.algo == LDPC_ALGO_MS) launch_cn_pipe<DCMAX, 4, false, kModeMS, REG>(c, o, it, fresh, s);
     else if (o.algo == LDPC_ALGO_NOMS) {
-        if (o.msg == LDPC_MSG_F16) launch_cn_pipe<DCMAX, 2, false, kModeNOMS, REG>(c, o, it, s);
-        else launch_cn_pipe<DCMAX, 1, false, kModeNOMS, REG>(c, o, it, s);
+        if (o.msg == LDPC_MSG_F16) launch_cn_pipe<DCMAX, 2, false, kModeNOMS, REG>(c, o, it, fresh, s);
+        else launch_cn_pipe<DCMAX, 1, false, kModeNOMS, REG>(c, o, it, fresh, s);
     } else if (o.msg == LDPC_MSG_F16) {
-        launch_cn_pipe<DCMAX, 2, false, kModeSP, REG>(c, o, it, s);
+        launch_cn_pipe<DCMAX, 2, false, kModeSP, REG>(c, o, it, fresh, s);
     } else {
-        launch_cn_pipe<DCMAX, 1, true, kModeSP, REG>(c, o, it, s);
+        launch_cn_pipe<DCMAX, 1, true, kModeSP, REG>(c, o, it, fresh, s);
     }
 }
 
@@ -638,13 +635,13 @@ static bool regular_rows(const QcDesc &d, int dcmax) {
     return true;
 }
 
-ldpc_status qc_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, cudaStream_t s) {
+ldpc_status qc_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, cudaStream_t s, const uint32_t *fresh) {
     const QcDesc &d = c->d;
-    if (regular_rows(d, 24)) cn_pipe_dispatch<24, true>(c, o, it, s);
-    else if (d.L <= 8) cn_pipe_dispatch<8, false>(c, o, it, s);
-    else if (d.L <= 16) cn_pipe_dispatch<16, false>(c, o, it, s);
-    else if (d.L <= 24) cn_pipe_dispatch<24, false>(c, o, it, s);
-    else cn_pipe_dispatch<32, false>(c, o, it, s);
+    if (regular_rows(d, 24)) cn_pipe_dispatch<24, true>(c, o, it, fresh, s);
+    else if (d.L <= 8) cn_pipe_dispatch<8, false>(c, o, it, fresh, s);
+    else if (d.L <= 16) cn_pipe_dispatch<16, false>(c, o, it, fresh, s);
+    else if (d.L <= 24) cn_pipe_dispatch<24, false>(c, o, it, fresh, s);
+    else cn_pipe_dispatch<32, false>(c, o, it, fresh, s);
     LDPC_CUDA_TRY(cudaGetLastError());
     return LDPC_OK;
 }
@@ -652,7 +649,7 @@ ldpc_status qc_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, cudaStrea
 template <int JMAX, int V, bool STOP, bool POST, bool XF, bool MS, bool REG>
 static void launch_vn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, int par, cudaStream_t s) {
     auto k = vn_pipe_kernel<JMAX, V, STOP, POST, XF, MS, REG, false>;
-    const size_t smem = (size_t)kWarps * kStages * VnStage<JMAX, V, STOP, MS>::WORDS * 4;
+    const size_t smem = (size_t)kWarps * kVnStages * VnStage<JMAX, V, STOP, MS>::WORDS * 4;
     const int blocks = persistent_blocks(k, smem);
     k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, (uint32_t *)c->ws.mu, c->ws.hw, c->ws.flags,
                                         c->ws.post, c->ws.iters, c->ws.act, o.clip, ldexpf(1.0f, -o.frac_bits), it,
@@ -707,7 +704,7 @@ namespace ldpc {
 template <int JMAX, int V, bool XF, bool MS, bool REG>
 static void launch_vn_refill(ldpc_code c, const ldpc_decode_opts &o, const RefillArgs &rf, cudaStream_t s) {
     auto k = vn_pipe_kernel<JMAX, V, false, false, XF, MS, REG, true>;
-    const size_t smem = (size_t)kWarps * kStages * VnStage<JMAX, V, false, MS, true>::WORDS * 4;
+    const size_t smem = (size_t)kWarps * kVnStages * VnStage<JMAX, V, false, MS>::WORDS * 4;
     const int blocks = persistent_blocks(k, smem);
     k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, (uint32_t *)c->ws.mu, c->ws.hw, c->ws.flags,
                                         nullptr, nullptr, c->ws.act, o.clip, ldexpf(1.0f, -o.frac_bits), 0, 0, rf);

@@ -7,20 +7,24 @@
 // Here every lane of the package layout is a frame slot.  One step of the
 // simulation is
 //
-//   syndrome of the current decisions (eq. (hrddcs)), then the check pass
+//   syndrome: of every slot's decisions so far (eq. (hrddcs))
 //   retire:   a frame whose decisions after a >= 1 iterations satisfy every
 //             check (C-11 stopping), or that has run max_iter iterations,
 //             leaves its slot; the next frame id takes the slot
-//   compact:  the packages with a running, retiring or new frame
+//   compact:  the packages with a running or retiring frame
 //   channel:  the new frames' channel LLRs (Philox + Box-Muller with the
-//             counter of ldpc_channel), written into the slots' channel store
-//   variable pass: running frames update as usual; a retiring frame's wrong
-//             bits are counted from its last decisions; a new frame's messages
-//             start at beta = mu (initialization of Alg. 1)
+//             counter of ldpc_channel) into the slots' channel store
+//   check pass: one iteration of every running frame; a new frame's
+//             outgoing messages are set to 0
+//   variable pass: one iteration of every running frame (a new frame gets
+//             beta = mu + 0 = mu, the initialization of Alg. 1, and its
+//             first check pass comes in the next step); it also counts a
+//             retired frame's wrong bits from its last decisions before the
+//             new frame's overwrite them
 //
-// so each frame runs exactly the iterations the batch decoder would give it,
-// with the same decisions, while the slots stay busy.  The retire kernel of the
-// next step adds the retired frames' counts to the totals.  Frame ids are
+// so each frame runs exactly the iterations the batch decoder gives it, with
+// the same decisions, while the slots stay busy.  The retire
+// kernel of the next step adds the retired frames' counts to the totals.  Frame ids are
 // handed out in order from a device counter, so the frames simulated are
 // always first_frame .. first_frame + frames - 1 (the set does not depend on
 // which slot a frame lands in).  Once the frame-error target is met no new
@@ -175,6 +179,8 @@ __global__ void sim_retire_kernel(uint32_t *__restrict__ flags, uint32_t *__rest
     }
     const unsigned long long idx = base + (unsigned long long)__popc(want & ((1u << lane) - 1u));
     const bool fill = ((want >> lane) & 1u) && idx < limit;
+    // iterations completed at the next step's retire kernel (a new frame's first step only
+    // initializes its messages)
     if (fill) {
         fid[slot] = first_frame + idx;
         a = 0;
@@ -267,20 +273,13 @@ ldpc_status qc_ber_sim_refill(ldpc_code c, double sigma, uint64_t seed, uint64_t
     const unsigned long long tgt = target < 0 ? 0ull : (unsigned long long)target;
     const int rblocks = (P * V * 32 + 255) / 256;
 
-    auto step = [&](bool check) -> ldpc_status {
-        if (check) {
-            // syndrome of the decisions so far (unsat words), then the check pass
-            ldpc_status e = qc_syndrome(c, P, V, V, s);
-            if (e != LDPC_OK) return e;
-            const int slot_cn = prof_begin(0, s);
-            e = qc_cn_pipe(c, o, 1, s);
-            if (e != LDPC_OK) return e;
-            prof_end(slot_cn, s);
-        }
+    auto step = [&]() -> ldpc_status {
+        ldpc_status e = qc_syndrome(c, P, V, V, s);  // unsat words
+        if (e != LDPC_OK) return e;
         sim_retire_kernel<<<rblocks, 256, 0, s>>>(c->ws.flags, S->sflags, S->fid, S->errs, S->age, S->pend, S->next,
                                                   S->rlist, S->rcount, c->ws.counters, P, V, o.max_iter,
                                                   o.early_stop, first_frame, limit, tgt, parity);
-        ldpc_status e = qc_compact(c, P, V, s, S->sflags);
+        e = qc_compact(c, P, V, s, S->sflags);
         if (e != LDPC_OK) return e;
         if (i8)
             sim_channel_kernel<true><<<cblocks, 256, 0, s>>>(c->ws.mu, S->rlist, S->rcount, S->fid, c->d.N, W, parity,
@@ -289,16 +288,18 @@ ldpc_status qc_ber_sim_refill(ldpc_code c, double sigma, uint64_t seed, uint64_t
             sim_channel_kernel<false><<<cblocks, 256, 0, s>>>(c->ws.mu, S->rlist, S->rcount, S->fid, c->d.N, W,
                                                               parity, seed, fsig, s2, o.clip, 1.0f);
         parity ^= 1;
+        const int slot_cn = prof_begin(0, s);
+        e = qc_cn_pipe(c, o, 1, s, S->sflags);
+        if (e != LDPC_OK) return e;
+        prof_end(slot_cn, s);
         const int slot_vn = prof_begin(1, s);
         e = qc_vn_refill(c, o, rf, s);
         if (e != LDPC_OK) return e;
         prof_end(slot_vn, s);
-        count_launch(check ? 6 : 4);
+        count_launch(6);
         return LDPC_OK;
     };
 
-    st = step(false);  // the first frames enter every slot
-    if (st != LDPC_OK) return st;
     // Steps are queued in chunks; after each chunk the totals and the number of
     // active packages are copied to pinned memory and the previous chunk's copy
     // is read, so the device always has a chunk queued while the host checks.
@@ -311,7 +312,7 @@ ldpc_status qc_ber_sim_refill(ldpc_code c, double sigma, uint64_t seed, uint64_t
     bool have_prev = false;
     for (;;) {
         for (int i = 0; i < kChunk; ++i) {
-            st = step(true);
+            st = step();
             if (st != LDPC_OK) return st;
         }
         steps += kChunk;
