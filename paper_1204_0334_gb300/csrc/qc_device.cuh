@@ -67,20 +67,12 @@ __device__ __forceinline__ float phi_lo(float x) {  // 0 <= x < 1
     return fmaf(lg2_approx(y), -LN2, G);
 }
 
-// any lanes, no warp-level assumptions
+// Both regimes evaluated and selected: no branch.  (Voting per warp to
+// evaluate one regime only costs more than it saves once the frames of a
+// warp are at different iterations, as in the continuous simulation.)
 __device__ __forceinline__ float phi_f(float x) {
     const float hi = phi_hi(x), lo = phi_lo(x);
     return x < 1.0f ? lo : hi;
-}
-
-// same values; must be called by all 32 lanes together: when the whole warp
-// is in one regime (the usual case) only that regime is evaluated
-__device__ __forceinline__ float phi_warp(float x) {
-    const bool lo = x < 1.0f;
-    const unsigned b = __ballot_sync(0xffffffffu, lo);
-    if (b == 0u) return phi_hi(x);
-    if (b == 0xffffffffu) return phi_lo(x);
-    return lo ? phi_lo(x) : phi_hi(x);
 }
 
 __device__ __forceinline__ float clipf(float x, float c) { return fminf(fmaxf(x, -c), c); }

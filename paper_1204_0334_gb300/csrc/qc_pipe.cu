@@ -156,7 +156,7 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
                     Lane<V>::unpack(S[l * 32 + lane], x);
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
-                        xs[l][v] = XF ? x[v] : copysignf(phi_warp(fabsf(x[v])), x[v]);
+                        xs[l][v] = XF ? x[v] : copysignf(phi_f(fabsf(x[v])), x[v]);
                         sgn[v] ^= __float_as_uint(x[v]);
                     }
                 }
@@ -184,7 +184,7 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
                     float out[V];
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
-                        const float mag = fminf(phi_warp(pre[l][v] + suf[v]), clip);
+                        const float mag = fminf(phi_f(pre[l][v] + suf[v]), clip);
                         out[v] = __uint_as_float(__float_as_uint(mag) |
                                                  ((sgn[v] ^ __float_as_uint(xs[l][v])) & 0x80000000u));
                         if (fr[v]) out[v] = 0.0f;
@@ -471,7 +471,7 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
                         b[v] = clipf(s, clip);
                         if (XF) {
                             // the check pass sums phi(|beta|): evaluate it here, from the unrounded beta
-                            const float f = phi_warp(fabsf(b[v]));
+                            const float f = phi_f(fabsf(b[v]));
                             b[v] = b[v] < 0.0f ? -f : f;
                         }
                     }
