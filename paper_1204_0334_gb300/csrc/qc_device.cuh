@@ -45,8 +45,10 @@ __device__ __forceinline__ float lg2_approx(float a) {
     return r;
 }
 
-__device__ __forceinline__ float phi_hi(float x) {  // x >= 1 (and +inf)
-    x = fminf(x, 100.0f);  // e^-100 flushes to 0; keeps inf - inf out of the error term
+// x >= 1 and finite (CLAMP: x may also be +inf)
+template <bool CLAMP = true>
+__device__ __forceinline__ float phi_hi(float x) {
+    if (CLAMP) x = fminf(x, 100.0f);  // e^-100 flushes to 0; keeps inf - inf out of the error term
     const float L2E = 1.44269502f, L2E_LO = 1.92596299e-8f, LN2 = 0.693147182f;
     const float a = -x * L2E;
     float alo = fmaf(-x, L2E, -a);
@@ -73,6 +75,15 @@ __device__ __forceinline__ float phi_lo(float x) {  // 0 <= x < 1
 __device__ __forceinline__ float phi_f(float x) {
     const float hi = phi_hi(x), lo = phi_lo(x);
     return x < 1.0f ? lo : hi;
+}
+// the same for finite x (no clamp)
+__device__ __forceinline__ float phi_fin(float x) {
+    const float hi = phi_hi<false>(x), lo = phi_lo(x);
+    return x < 1.0f ? lo : hi;
+}
+// |y| with the sign bit of s
+__device__ __forceinline__ float with_sign_of(float y, float s) {
+    return __uint_as_float(__float_as_uint(y) | (__float_as_uint(s) & 0x80000000u));
 }
 
 __device__ __forceinline__ float clipf(float x, float c) { return fminf(fmaxf(x, -c), c); }

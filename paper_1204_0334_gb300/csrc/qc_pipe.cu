@@ -133,11 +133,12 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
         // frames that entered their slot this step (continuous simulation): alpha = 0, so the
         // variable pass that follows starts them at beta = mu (initialization of Alg. 1)
         bool fr[V];
-        uint32_t frmask = 0u;
+        uint32_t frmask = 0u, keep[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             lane_on |= ((~S[St::FL + v]) >> lane) & 1u;
             fr[v] = fresh && ((S[St::FL + V + v] >> lane) & 1u);
+            keep[v] = fr[v] ? 0u : 0xffffffffu;
             if (fr[v]) frmask |= 0xffu << (8 * v);
         }
         if constexpr (MODE == kModeSP) {
@@ -185,9 +186,10 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
                         const float mag = fminf(phi_f(pre[l][v] + suf[v]), clip);
-                        out[v] = __uint_as_float(__float_as_uint(mag) |
-                                                 ((sgn[v] ^ __float_as_uint(xs[l][v])) & 0x80000000u));
-                        if (fr[v]) out[v] = 0.0f;
+                        // |alpha| with the XOR of the other edges' signs; 0 for a frame that has just
+                        // entered its slot
+                        out[v] = __uint_as_float(
+                            (__float_as_uint(mag) | ((sgn[v] ^ __float_as_uint(xs[l][v])) & 0x80000000u)) & keep[v]);
                     }
                     if (lane_on) gmsg[(size_t)o * 32] = Lane<V>::pack(out);
                 }
@@ -468,11 +470,12 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
 #pragma unroll
                         for (int j2 = 0; j2 < JMAX; ++j2)
                             if (j2 != jj) s += aj[j2][v];
-                        b[v] = clipf(s, clip);
                         if (XF) {
-                            // the check pass sums phi(|beta|): evaluate it here, from the unrounded beta
-                            const float f = phi_f(fabsf(b[v]));
-                            b[v] = b[v] < 0.0f ? -f : f;
+                            // the check pass sums phi(|beta|): evaluate it here, from the unrounded
+                            // beta (|clip(s)| = min(|s|, clip)), and keep beta's sign
+                            b[v] = with_sign_of(phi_fin(fminf(fabsf(s), clip)), s);
+                        } else {
+                            b[v] = clipf(s, clip);
                         }
                     }
                     if (lane_on) gmsg[(size_t)(s_eo[jj * d.L + l] + k) * 32] = Lane<V>::pack(b);
