@@ -3,7 +3,7 @@
 
 Workload (one step = one ldpc_ber_sim call through the whole block-code path):
   QC-LDPC 4 x 24, p = 765 (n = 18360, K = N - M = 15300 design information bits),
-  seeded shifts, 32768 frames per step decoded in 4096 frame slots (a slot takes
+  seeded shifts, 131072 frames per step decoded in 4096 frame slots (a slot takes
   the next frame as soon as its frame stops), all-zero codeword over BPSK/AWGN at
   Eb/N0 = 3.5 dB generated on the device (Philox + Box-Muller), sum-product with
   FP32 messages, at most 30 iterations with syndrome early stop, device-side
@@ -50,7 +50,7 @@ def args_parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ebn0", type=float, default=3.5)
     ap.add_argument("--gamma", type=int, default=4096, help="frame slots decoded together")
-    ap.add_argument("--frames", type=int, default=32768, help="frames simulated per step")
+    ap.add_argument("--frames", type=int, default=131072, help="frames simulated per step")
     ap.add_argument("--iters", type=int, default=30)
     ap.add_argument("--msg", default="f32", choices=["f32", "f16", "i8"])
     ap.add_argument("--no-early-stop", action="store_true")
