@@ -295,7 +295,8 @@ struct VnStage {
     static constexpr int WORDS = (FL + NFL + 3) & ~3;
 };
 
-template <int JMAX, int V, bool STOP, bool POST, bool XF, bool MS, bool REG, bool REFILL = false>
+// EVEN: N is a multiple of kNV (every item has kNV variables)
+template <int JMAX, int V, bool STOP, bool POST, bool XF, bool MS, bool REG, bool REFILL = false, bool EVEN = false>
 __global__ void __launch_bounds__(kWarps * 32)
 vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict__ mu, uint32_t *__restrict__ hw,
                uint32_t *__restrict__ flags, float *__restrict__ post, int32_t *__restrict__ iters,
@@ -317,7 +318,6 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
     const int GW = gridDim.x * kWarps;
     int item = blockIdx.x * kWarps + warp;
     constexpr int MU_SEGS = St::MUW / 32;
-    constexpr int NSEG = kNV * (MU_SEGS + JMAX);
 
     auto issue = [&](int itm, int slot) {
         if (itm < total) {
@@ -330,33 +330,35 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
             const int n0 = g * kNV;
             const int l0 = n0 / d.p, k0 = n0 - l0 * d.p;
             const int grp = lane >> 3, sub = lane & 7;
+            // channel LLRs: kNV * MU_SEGS segments of 32 words, one per group of 8 lanes and pass
 #pragma unroll
-            for (int s0 = 0; s0 < NSEG; s0 += 4) {
+            for (int s0 = 0; s0 < kNV * MU_SEGS; s0 += 4) {
                 const int s = s0 + grp;
-                if (s < kNV * MU_SEGS) {
-                    const int i = s / MU_SEGS, h = s - i * MU_SEGS;
-                    const int n = n0 + i;
-                    if (n < d.N)
+                const int i = s / MU_SEGS, h = s - i * MU_SEGS;
+                const int n = n0 + i;
+                if ((kNV * MU_SEGS) % 4 == 0 || s < kNV * MU_SEGS)
+                    if (EVEN || n < d.N)
                         cp_async16(dst + St::MU + i * St::MUW + h * 32 + sub * 4,
                                    gmu + (size_t)n * St::MUW + h * 32 + sub * 4);
-                } else if (s < NSEG) {
-                    const int t = s - kNV * MU_SEGS;
-                    const int i = t / JMAX, jj = t - i * JMAX;
-                    const int n = n0 + i;
-                    int l = l0, k = k0 + i;
-                    if (k >= d.p) k -= d.p, ++l;
-                    if (n < d.N && (REG || jj < d.J)) {
-                        const int sh = s_sh[jj * d.L + l];
-                        if (REG || sh >= 0)
-                            cp_async16(dst + St::AL + (i * JMAX + jj) * 32 + sub * 4,
-                                       gmsg + (size_t)(s_eo[jj * d.L + l] + k) * 32 + sub * 4);
-                    }
+            }
+            // edge packages: kNV * JMAX of them
+#pragma unroll
+            for (int t0 = 0; t0 < kNV * JMAX; t0 += 4) {
+                const int t = t0 + grp;
+                const int i = t / JMAX, jj = t - i * JMAX;
+                const int n = n0 + i;
+                int l = l0, k = k0 + i;
+                if (k >= d.p) k -= d.p, ++l;
+                if (((kNV * JMAX) % 4 == 0 || t < kNV * JMAX) && (EVEN || n < d.N) && (REG || jj < d.J)) {
+                    if (REG || s_sh[jj * d.L + l] >= 0)
+                        cp_async16(dst + St::AL + (i * JMAX + jj) * 32 + sub * 4,
+                                   gmsg + (size_t)(s_eo[jj * d.L + l] + k) * 32 + sub * 4);
                 }
             }
             if (lane < kNV * V) {
                 const int i = lane / V, v = lane - i * V;
                 const int n = n0 + i;
-                if (n < d.N) cp_async4(dst + St::HW + lane, hw + ((size_t)pk * d.N + n) * V + v);
+                if (EVEN || n < d.N) cp_async4(dst + St::HW + lane, hw + ((size_t)pk * d.N + n) * V + v);
             } else if (lane >= 32 - St::NFL) {
                 const int q = lane - (32 - St::NFL);
                 if (REFILL) {
@@ -431,7 +433,7 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
                     int cnt = 0;
 #pragma unroll
                     for (int i = 0; i < kNV; ++i)
-                        if (n0 + i < d.N) cnt += (S[St::HW + i * V + v] >> lane) & 1u;
+                        if (EVEN || n0 + i < d.N) cnt += (S[St::HW + i * V + v] >> lane) & 1u;
                     if (cnt) atomicAdd(rf.errs + (size_t)pk * W + lane * V + v, cnt);
                 }
             }
@@ -441,7 +443,7 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
         for (int i = 0; i < kNV; ++i, ++k) {
             if (k >= d.p) k -= d.p, ++l;
             const int n = n0 + i;
-            if (n >= d.N) break;  // warp-uniform
+            if (!EVEN && n >= d.N) break;  // warp-uniform
             uint32_t outb[V];
             if constexpr (!MS) {
                 float m[V], aj[JMAX][V], tot[V];
@@ -651,7 +653,8 @@ ldpc_status qc_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, cudaStrea
 
 template <int JMAX, int V, bool STOP, bool POST, bool XF, bool MS, bool REG>
 static void launch_vn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, int par, cudaStream_t s) {
-    auto k = vn_pipe_kernel<JMAX, V, STOP, POST, XF, MS, REG, false>;
+    auto k = (REG && c->d.N % kNV == 0) ? vn_pipe_kernel<JMAX, V, STOP, POST, XF, MS, REG, false, REG>
+                                        : vn_pipe_kernel<JMAX, V, STOP, POST, XF, MS, REG, false, false>;
     const size_t smem = (size_t)kWarps * kVnStages * VnStage<JMAX, V, STOP, MS>::WORDS * 4;
     const int blocks = persistent_blocks(k, smem);
     k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, (uint32_t *)c->ws.mu, c->ws.hw, c->ws.flags,
@@ -706,7 +709,8 @@ namespace ldpc {
 // retire kernel owns the flag words), no posteriors
 template <int JMAX, int V, bool XF, bool MS, bool REG>
 static void launch_vn_refill(ldpc_code c, const ldpc_decode_opts &o, const RefillArgs &rf, cudaStream_t s) {
-    auto k = vn_pipe_kernel<JMAX, V, false, false, XF, MS, REG, true>;
+    auto k = (REG && c->d.N % kNV == 0) ? vn_pipe_kernel<JMAX, V, false, false, XF, MS, REG, true, REG>
+                                        : vn_pipe_kernel<JMAX, V, false, false, XF, MS, REG, true, false>;
     const size_t smem = (size_t)kWarps * kVnStages * VnStage<JMAX, V, false, MS>::WORDS * 4;
     const int blocks = persistent_blocks(k, smem);
     k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, (uint32_t *)c->ws.mu, c->ws.hw, c->ws.flags,
