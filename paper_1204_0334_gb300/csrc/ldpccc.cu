@@ -25,6 +25,7 @@
 // straight from the ring: the edges of an arriving frame need no initial fill.
 #include "qc_device.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <new>
 #include <numeric>
@@ -73,120 +74,324 @@ __global__ void cc_enter_kernel(const float *__restrict__ llr, float *__restrict
     }
 }
 
-// check pass of slot t over the I processors' layers; one warp = one check row of one package
-template <int DCMAX>
-__global__ void __launch_bounds__(kWarps * 32)
-cc_cn_kernel(const QcDesc d, CcDesc g, uint32_t *__restrict__ msg, const float *__restrict__ mu, long long t,
-             float clip) {
-    const int lane = threadIdx.x & 31;
-    const int row_all = blockIdx.x * kWarps + (threadIdx.x >> 5);  // over I * cb
-    const int pk = blockIdx.y;
-    if (row_all >= g.I * g.cb) return;
-    const int i = row_all / g.cb, row = row_all - i * g.cb;
-    const long long R = t - (long long)i * g.lam;
-    if (R < 0) return;
-    const int a = mod_pos(R, g.lam);
-    const int jj = row / d.p, r = row - jj * d.p;
-    const int j = a * g.Jb + jj;
-    const bool proc1 = i == 0;
-    float ph[DCMAX];
-    size_t addr[DCMAX];
-    uint32_t neg = 0u;
-#pragma unroll
-    for (int l = 0; l < DCMAX; ++l) {
-        ph[l] = 0.0f;
-        addr[l] = ~(size_t)0;
-        if (l >= d.L) continue;
-        const int sh = d.shift[j * d.L + l];
-        if (sh < 0) continue;
-        const int b = l / g.Lb, ll = l - b * g.Lb;
-        const long long F = R - mod_pos(a - b, g.lam);
-        if (F < 0) continue;
-        int k = r + sh;
-        if (k >= d.p) k -= d.p;
-        const int slot = mod_pos(F, g.ring);
-        const size_t e = (size_t)(j * g.Lb + ll) * d.p + k;
-        addr[l] = (((size_t)slot * g.P + pk) * g.Ef + e) * 32 + lane;
-        float x;
-        if (proc1) {
-            x = mu[(((size_t)slot * g.P + pk) * g.c + (size_t)ll * d.p + k) * 32 + lane];
-            ph[l] = phi_f(fabsf(x));
-        } else {
-            x = __uint_as_float(msg[addr[l]]);
-            ph[l] = fabsf(x);  // the variable pass stored sign(beta) * phi(|beta|)
-        }
-        neg |= (x < 0.0f ? 1u : 0u) << l;
-    }
-    float pre[DCMAX];
-    float acc = 0.0f;
-#pragma unroll
-    for (int l = 0; l < DCMAX; ++l) {
-        pre[l] = acc;
-        acc += ph[l];
-    }
-    const uint32_t par = __popc(neg) & 1u;
-    float suf = 0.0f;
-#pragma unroll
-    for (int l = DCMAX - 1; l >= 0; --l) {
-        if (addr[l] != ~(size_t)0) {
-            const float mag = fminf(phi_f(pre[l] + suf), clip);
-            msg[addr[l]] = __float_as_uint((par ^ ((neg >> l) & 1u)) ? -mag : mag);
-        }
-        suf += ph[l];
-    }
+constexpr int kCcStages = 3;  // ring slots per warp
+// consecutive check rows per check-pass work item: up to 32 edges (one lane each)
+__host__ __device__ constexpr int cc_rows(int dcmax) { return dcmax <= 8 ? 4 : (dcmax <= 16 ? 2 : 1); }
+constexpr int kCcNV = 4;      // consecutive variables per variable-pass work item
+
+__device__ __forceinline__ int wrap_lam(int x, int lam) { return x < 0 ? x + lam : x; }
+
+// Exact n / d for 0 <= n < 2^32 and a divisor d >= 1 fixed for a launch: the multiply-high
+// method of Granlund and Montgomery, "Division by invariant integers using multiplication"
+// (PLDI 1994, Fig. 4.1): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+// t = mulhi(m, n), q = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0).
+struct FastDiv {
+    uint32_t d, m;
+    int s1, s2;
+};
+static FastDiv fast_div(uint32_t d) {
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    FastDiv f;
+    f.d = d;
+    f.m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l > 1 ? l - 1 : 0;
+    return f;
+}
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f) {
+    const uint32_t t = __umulhi(n, f.m);
+    return (t + ((n - t) >> f.s1)) >> f.s2;
 }
 
-// variable pass of slot t over the I processors' frames; one warp = one variable of one package.
-// The frame leaving processor I gets its posterior and hard decision (output index q).
-template <int JMAX>
+// per-slot constants: t clamped to 2^30 (only compared with frame lags below I*Lambda + Lambda),
+// t mod ring, layer type a = t mod Lambda, and the variable pass's frame type (t - ms) mod Lambda
+struct SlotC {
+    int t, tm, a, bv;
+};
+
+// launch geometry: item counts and their divisors
+struct CcGeo {
+    FastDiv RB, Jb, P, G, p;  // row blocks per block row, Jb, packages, variable groups, p
+};
+
+// Check pass of slot t over processors 0 .. n_i - 1 (layers R = t - i*Lambda >= 0).  Work
+// items are (processor, package, block row, cc_rows(DCMAX) consecutive rows); persistent warps walk
+// them with the items' cc_rows(DCMAX) * DCMAX 128-byte edge packages copied into the warp's shared
+// ring by cp.async two items ahead.  The layer's type a = t mod Lambda is the same for every
+// processor, so base column l meets frame F = R - ((a - l / Lb) mod Lambda) in ring slot
+// (t mod ring - i*Lambda - that lag) mod ring.  Processor 1 reads its edges' beta = mu from
+// the channel ring (no frame has had a variable pass yet); the others read
+// sign(beta) * phi(|beta|) as the variable pass stored it.
+template <int DCMAX>
 __global__ void __launch_bounds__(kWarps * 32)
-cc_vn_kernel(const QcDesc d, CcDesc g, uint32_t *__restrict__ msg, const float *__restrict__ mu, long long t,
-             float clip, int gamma, int T_out, int q_out, uint8_t *__restrict__ hard, float *__restrict__ post) {
-    const int lane = threadIdx.x & 31;
-    const int var_all = blockIdx.x * kWarps + (threadIdx.x >> 5);  // over I * c
-    const int pk = blockIdx.y;
-    if (var_all >= g.I * g.c) return;
-    const int i = var_all / g.c, v = var_all - i * g.c;
-    const long long F = t - (long long)i * g.lam - g.ms;
-    if (F < 0) return;
-    const int b = mod_pos(F, g.lam);
-    const int slot = mod_pos(F, g.ring);
-    const int ll = v / d.p, k = v - ll * d.p;
-    const int l = b * g.Lb + ll;
-    const float m = mu[(((size_t)slot * g.P + pk) * g.c + v) * 32 + lane];
-    float a[JMAX];
-    size_t addr[JMAX];
-    float tot = m;
-#pragma unroll
-    for (int j = 0; j < JMAX; ++j) {
-        a[j] = 0.0f;
-        addr[j] = ~(size_t)0;
-        if (j >= d.J || d.shift[j * d.L + l] < 0) continue;
-        const size_t e = (size_t)(j * g.Lb + ll) * d.p + k;
-        addr[j] = (((size_t)slot * g.P + pk) * g.Ef + e) * 32 + lane;
-        a[j] = __uint_as_float(msg[addr[j]]);
-        tot += a[j];
-    }
-#pragma unroll
-    for (int j = 0; j < JMAX; ++j) {
-        if (addr[j] == ~(size_t)0) continue;
-        float s = m;
-#pragma unroll
-        for (int j2 = 0; j2 < JMAX; ++j2)
-            if (j2 != j) s += a[j2];
-        const float bt = clipf(s, clip);
-        const float f = phi_f(fabsf(bt));
-        msg[addr[j]] = __float_as_uint(bt < 0.0f ? -f : f);
-    }
-    if (i == g.I - 1 && q_out >= 0) {
-        const float pst = clipf(tot, clip);
-        const int s = pk * 32 + lane;
-        if (s < gamma) {
-            const size_t o = ((size_t)s * T_out + q_out) * g.c + v;
-            if (hard) hard[o] = pst < 0.0f ? 1 : 0;
-            if (post) post[o] = pst;
+cc_cn_pipe_kernel(const QcDesc d, CcDesc g, CcGeo q, uint32_t *__restrict__ msg, const float *__restrict__ mu,
+                  SlotC sc, float clip, int n_i) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ int s_sh[kMaxJ * kMaxL], s_eb[kMaxJ * kMaxL], s_ll[kMaxL], s_dl[kMaxL];
+    for (int x = threadIdx.x; x < d.J * d.L; x += blockDim.x) {
+        const int j = x / d.L, l = x - j * d.L;
+        const int b = l / g.Lb, ll = l - b * g.Lb;
+        s_sh[x] = d.shift[x];
+        s_eb[x] = (j * g.Lb + ll) * d.p;  // first edge of block (j, l) within a frame
+        if (j == 0) {
+            s_ll[l] = ll;
+            s_dl[l] = wrap_lam(sc.a - b, g.lam);  // frame lag of base column l
         }
     }
+    __syncthreads();
+    constexpr int ROWS = cc_rows(DCMAX);
+    constexpr int NE = ROWS * DCMAX;  // edges of an item
+    constexpr int WORDS = NE * 32;
+    static_assert(NE <= 32, "one lane per edge of an item");
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *ring = smem + warp * kCcStages * WORDS;
+    const int per_i = (int)(q.P.d * q.Jb.d * q.RB.d);
+    const int total = n_i * per_i;  // the host keeps I * P * cb below 2^31
+    const int GW = gridDim.x * kWarps;
+    int item = blockIdx.x * kWarps + warp;
+
+    struct Item {
+        int i, pk, j, r0;
+    };
+    auto geo = [&](int it) {
+        Item o;
+        uint32_t x = (uint32_t)it;
+        const uint32_t x1 = fdiv(x, q.RB);
+        o.r0 = (int)(x - x1 * q.RB.d) * ROWS;
+        const uint32_t x2 = fdiv(x1, q.Jb);
+        const int jj = (int)(x1 - x2 * q.Jb.d);
+        const uint32_t x3 = fdiv(x2, q.P);
+        o.pk = (int)(x2 - x3 * q.P.d);
+        o.i = (int)x3;
+        o.j = sc.a * g.Jb + jj;
+        return o;
+    };
+    // package line read for edge e = rr * DCMAX + l of an item (channel ring for processor 1)
+    // and the message line written, or -1 where the edge is absent
+    auto edge = [&](const Item &o, int e, int &src, int &dstl) {
+        src = dstl = -1;
+        const int rr = e / DCMAX, l = e - rr * DCMAX;
+        const int r = o.r0 + rr;
+        if (l >= d.L || r >= d.p) return;
+        const int sh = s_sh[o.j * d.L + l];
+        if (sh < 0) return;
+        const int back = o.i * g.lam + s_dl[l];  // t - F
+        if (back > sc.t) return;                 // frame not yet arrived
+        int k = r + sh;
+        if (k >= d.p) k -= d.p;
+        int fs = sc.tm - back;
+        if (fs < 0) fs += g.ring;
+        dstl = (fs * g.P + o.pk) * g.Ef + s_eb[o.j * d.L + l] + k;
+        src = o.i == 0 ? (fs * g.P + o.pk) * g.c + s_ll[l] * d.p + k : dstl;
+    };
+
+    auto issue = [&](int it, int slot) -> int {
+        int mine = -1;
+        if (it < total) {
+            const Item o = geo(it);
+            uint32_t *dst = ring + slot * WORDS;
+            const uint32_t *base = o.i == 0 ? reinterpret_cast<const uint32_t *>(mu) : msg;
+            const int grp = lane >> 3, sub = lane & 7;
+#pragma unroll
+            for (int e0 = 0; e0 < NE; e0 += 4) {
+                const int e = e0 + grp;
+                int src = -1, dl;
+                if (NE % 4 == 0 || e < NE) edge(o, e, src, dl);
+                if (src >= 0) cp_async16(dst + e * 32 + sub * 4, base + (size_t)src * 32 + sub * 4);
+            }
+            if (lane < NE) {
+                int src;
+                edge(o, lane, src, mine);
+            }
+        }
+        cp_async_commit();
+        return mine;
+    };
+
+    int offr[kCcStages];
+#pragma unroll
+    for (int s = 0; s < kCcStages - 1; ++s) offr[s] = issue(item + s * GW, s);
+    int slot = 0;
+    for (; item < total; item += GW) {
+        offr[kCcStages - 1] = issue(item + (kCcStages - 1) * GW, (slot + kCcStages - 1) % kCcStages);
+        cp_async_wait<kCcStages - 1>();
+        __syncwarp();
+        const uint32_t *S = ring + slot * WORDS;
+        const int myoff = offr[0];
+#pragma unroll
+        for (int s = 0; s < kCcStages - 1; ++s) offr[s] = offr[s + 1];
+        const bool p1 = item < per_i;  // processor 1 (warp-uniform)
+#pragma unroll
+        for (int rr = 0; rr < ROWS; ++rr) {
+            float xs[DCMAX];
+            uint32_t sgn = 0u, pres = 0u;
+#pragma unroll
+            for (int l = 0; l < DCMAX; ++l) {
+                xs[l] = 0.0f;
+                if (__shfl_sync(0xffffffffu, myoff, rr * DCMAX + l) >= 0) {
+                    xs[l] = __uint_as_float(S[(rr * DCMAX + l) * 32 + lane]);
+                    sgn ^= __float_as_uint(xs[l]);
+                    pres |= 1u << l;
+                }
+            }
+            if (pres == 0u) continue;  // row past p (warp-uniform)
+            if (p1) {  // channel LLRs: transform here (absent edges stay 0)
+#pragma unroll
+                for (int l = 0; l < DCMAX; ++l)
+                    if ((pres >> l) & 1u) xs[l] = with_sign_of(phi_f(fabsf(xs[l])), xs[l]);
+            }
+            float pre[DCMAX];
+            float acc = 0.0f;
+#pragma unroll
+            for (int l = 0; l < DCMAX; ++l) {
+                pre[l] = acc;
+                acc += fabsf(xs[l]);
+            }
+            float suf = 0.0f;
+#pragma unroll
+            for (int l = DCMAX - 1; l >= 0; --l) {
+                const int o = __shfl_sync(0xffffffffu, myoff, rr * DCMAX + l);
+                if (o >= 0) {
+                    const float mag = fminf(phi_f(pre[l] + suf), clip);
+                    msg[(size_t)o * 32 + lane] =
+                        __float_as_uint(mag) | ((sgn ^ __float_as_uint(xs[l])) & 0x80000000u);
+                }
+                suf += fabsf(xs[l]);
+            }
+        }
+        __syncwarp();
+        slot = (slot + 1) % kCcStages;
+    }
+    cp_async_wait<0>();
+}
+
+// Variable pass of slot t over processors 0 .. n_i - 1 (frames F = t - i*Lambda - ms >= 0);
+// items are (processor, package, kCcNV consecutive variables).  Every processor's frame has
+// type b = (t - ms) mod Lambda and sits in ring slot (t mod ring - i*Lambda - ms) mod ring.
+// The frame leaving processor I (i = I - 1) gets its posterior and hard decision at output
+// position q_out.
+template <int JMAX>
+__global__ void __launch_bounds__(kWarps * 32)
+cc_vn_pipe_kernel(const QcDesc d, CcDesc g, CcGeo q, uint32_t *__restrict__ msg, const float *__restrict__ mu,
+                  SlotC sc, float clip, int n_i, int gamma, int T_out, int q_out, uint8_t *__restrict__ hard,
+                  float *__restrict__ post) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ int s_sh[kMaxJ * kMaxL];
+    for (int x = threadIdx.x; x < d.J * d.L; x += blockDim.x) s_sh[x] = d.shift[x];
+    __syncthreads();
+    constexpr int MU = 0, AL = kCcNV * 32, WORDS = AL + kCcNV * JMAX * 32;
+    static_assert(kCcNV == 4 && kCcNV * JMAX <= 32, "item layout");
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *ring = smem + warp * kCcStages * WORDS;
+    const int per_i = (int)(q.P.d * q.G.d);
+    const int total = n_i * per_i;
+    const int GW = gridDim.x * kWarps;
+    int item = blockIdx.x * kWarps + warp;
+
+    struct Geo {
+        int i, pk, v0, fs, ll0, k0;
+    };
+    auto geo = [&](int it) {
+        Geo o;
+        uint32_t x = (uint32_t)it;
+        const uint32_t x1 = fdiv(x, q.G);
+        o.v0 = (int)(x - x1 * q.G.d) * kCcNV;
+        const uint32_t x2 = fdiv(x1, q.P);
+        o.pk = (int)(x1 - x2 * q.P.d);
+        o.i = (int)x2;
+        int fs = sc.tm - o.i * g.lam - g.ms;
+        if (fs < 0) fs += g.ring;
+        if (fs < 0) fs += g.ring;
+        o.fs = fs;
+        o.ll0 = (int)fdiv((uint32_t)o.v0, q.p);
+        o.k0 = o.v0 - o.ll0 * d.p;
+        return o;
+    };
+    // message line of edge (variable v0 + iv of the item's frame, block row j), or -1
+    auto eline = [&](const Geo &o, int iv, int j) -> int {
+        if (o.v0 + iv >= g.c || j >= d.J) return -1;
+        int ll = o.ll0, k = o.k0 + iv;
+        if (k >= d.p) k -= d.p, ++ll;
+        if (s_sh[j * d.L + sc.bv * g.Lb + ll] < 0) return -1;
+        return (o.fs * g.P + o.pk) * g.Ef + (j * g.Lb + ll) * d.p + k;
+    };
+
+    auto issue = [&](int it, int slot) -> int {
+        int mine = -1;
+        if (it < total) {
+            const Geo o = geo(it);
+            uint32_t *dst = ring + slot * WORDS;
+            const int grp = lane >> 3, sub = lane & 7;
+            if (o.v0 + grp < g.c)  // one channel line per lane group
+                cp_async16(dst + MU + grp * 32 + sub * 4,
+                           reinterpret_cast<const uint32_t *>(mu) +
+                               ((size_t)(o.fs * g.P + o.pk) * g.c + o.v0 + grp) * 32 + sub * 4);
+#pragma unroll
+            for (int qq = 0; qq < JMAX; ++qq) {
+                const int tt = 4 * qq + grp;  // (variable tt / JMAX, row tt % JMAX)
+                const int e = eline(o, tt / JMAX, tt % JMAX);
+                if (e >= 0) cp_async16(dst + AL + tt * 32 + sub * 4, msg + (size_t)e * 32 + sub * 4);
+            }
+            if (lane < kCcNV * JMAX) mine = eline(o, lane / JMAX, lane % JMAX);
+        }
+        cp_async_commit();
+        return mine;
+    };
+
+    int offr[kCcStages];
+#pragma unroll
+    for (int s = 0; s < kCcStages - 1; ++s) offr[s] = issue(item + s * GW, s);
+    int slot = 0;
+    for (; item < total; item += GW) {
+        offr[kCcStages - 1] = issue(item + (kCcStages - 1) * GW, (slot + kCcStages - 1) % kCcStages);
+        cp_async_wait<kCcStages - 1>();
+        __syncwarp();
+        const uint32_t *S = ring + slot * WORDS;
+        const int myoff = offr[0];
+#pragma unroll
+        for (int s = 0; s < kCcStages - 1; ++s) offr[s] = offr[s + 1];
+        const uint32_t x1 = fdiv((uint32_t)item, q.G);
+        const int v0 = (int)((uint32_t)item - x1 * q.G.d) * kCcNV;
+        const uint32_t x2 = fdiv(x1, q.P);
+        const int pk = (int)(x1 - x2 * q.P.d);
+        const bool out_here = (int)x2 == g.I - 1 && q_out >= 0;
+        const int sidx = pk * 32 + lane;
+#pragma unroll
+        for (int iv = 0; iv < kCcNV; ++iv) {
+            const int v = v0 + iv;
+            if (v >= g.c) break;  // warp-uniform
+            const float m = __uint_as_float(S[MU + iv * 32 + lane]);
+            float a[JMAX];
+            int e[JMAX];
+            float tot = m;
+#pragma unroll
+            for (int j = 0; j < JMAX; ++j) {
+                e[j] = __shfl_sync(0xffffffffu, myoff, iv * JMAX + j);
+                a[j] = e[j] >= 0 ? __uint_as_float(S[AL + (iv * JMAX + j) * 32 + lane]) : 0.0f;
+                tot += a[j];
+            }
+#pragma unroll
+            for (int j = 0; j < JMAX; ++j) {
+                if (e[j] < 0) continue;  // warp-uniform
+                float sm = m;
+#pragma unroll
+                for (int j2 = 0; j2 < JMAX; ++j2)
+                    if (j2 != j) sm += a[j2];
+                // store sign(beta) * phi(|beta|), beta = clip(sm)
+                msg[(size_t)e[j] * 32 + lane] = __float_as_uint(with_sign_of(phi_fin(fminf(fabsf(sm), clip)), sm));
+            }
+            if (out_here && sidx < gamma) {
+                const float pst = clipf(tot, clip);
+                const size_t oi = ((size_t)sidx * T_out + q_out) * g.c + v;
+                if (hard) hard[oi] = pst < 0.0f ? 1 : 0;
+                if (post) post[oi] = pst;
+            }
+        }
+        __syncwarp();
+        slot = (slot + 1) % kCcStages;
+    }
+    cp_async_wait<0>();
 }
 
 // channel LLRs of frames first .. first+T-1 of every stream: all-zero frames over
@@ -211,6 +416,44 @@ __global__ void cc_channel_kernel(float *__restrict__ out, int gamma, int T, int
 
 static CcDesc cc_desc(const ldpccc_s *cc) {
     return CcDesc{cc->lam, cc->Jb, cc->Lb, cc->c, cc->cb, cc->ms, cc->I, cc->P, cc->ring, cc->d.J * cc->c};
+}
+
+static SlotC slot_consts(const ldpccc_s *cc, long long t) {
+    SlotC c;
+    c.t = (int)std::min<long long>(t, 1ll << 30);
+    c.tm = (int)(t % cc->ring);
+    c.a = (int)(t % cc->lam);
+    c.bv = (int)(((t - cc->ms) % cc->lam + cc->lam) % cc->lam);
+    return c;
+}
+
+static CcGeo cc_geo(const ldpccc_s *cc, int rows) {
+    CcGeo q;
+    q.RB = fast_div((uint32_t)((cc->d.p + rows - 1) / rows));
+    q.Jb = fast_div((uint32_t)cc->Jb);
+    q.P = fast_div((uint32_t)cc->P);
+    q.G = fast_div((uint32_t)((cc->c + kCcNV - 1) / kCcNV));
+    q.p = fast_div((uint32_t)cc->d.p);
+    return q;
+}
+
+template <int DCMAX>
+static void cc_cn_launch(const ldpccc_s *cc, const CcDesc &g, long long t, float clip, int n_i, cudaStream_t s) {
+    auto k = cc_cn_pipe_kernel<DCMAX>;
+    const size_t smem = (size_t)kWarps * kCcStages * cc_rows(DCMAX) * DCMAX * 32 * 4;
+    const int blocks = persistent_blocks(k, smem);
+    k<<<blocks, kWarps * 32, smem, s>>>(cc->d, g, cc_geo(cc, cc_rows(DCMAX)), cc->msg, cc->mu, slot_consts(cc, t), clip,
+                                        n_i);
+}
+
+template <int JMAX>
+static void cc_vn_launch(const ldpccc_s *cc, const CcDesc &g, long long t, float clip, int n_i, int T_out, int q,
+                         uint8_t *hard, float *post, cudaStream_t s) {
+    auto k = cc_vn_pipe_kernel<JMAX>;
+    const size_t smem = (size_t)kWarps * kCcStages * (kCcNV + kCcNV * JMAX) * 32 * 4;
+    const int blocks = persistent_blocks(k, smem);
+    k<<<blocks, kWarps * 32, smem, s>>>(cc->d, g, cc_geo(cc, 1), cc->msg, cc->mu, slot_consts(cc, t), clip, n_i,
+                                        cc->gamma, T_out, q, hard, post);
 }
 
 }  // namespace ldpc
@@ -251,6 +494,13 @@ ldpc_status ldpccc_create(const int32_t *shifts, int32_t J, int32_t L, int32_t p
     cc->gamma = gamma;
     cc->P = (gamma + 31) / 32;
     cc->ring = I * cc->lam;
+    // the passes index 128-byte package lines and work items with 32-bit integers
+    if ((long long)cc->ring * cc->P * J * cc->c >= (1ll << 31) || (long long)I * cc->P * J * cc->c >= (1ll << 31)) {
+        delete cc;
+        set_error("I * Lambda * ceil(gamma / 32) * J * c = %lld package lines exceeds 2^31",
+                  (long long)I * std::gcd(J, L) * ((gamma + 31) / 32) * J * (L / std::gcd(J, L)) * (long long)p);
+        return LDPC_EINVAL;
+    }
     cudaGetDevice(&cc->device);
     const size_t mu_b = (size_t)cc->ring * cc->P * cc->c * 32 * 4;
     const size_t msg_b = (size_t)cc->ring * cc->P * J * cc->c * 32 * 4;
@@ -340,23 +590,26 @@ ldpc_status ldpccc_decode_window(ldpccc cc, const float *llr, int32_t T, float c
     int n = 0;
     const int dcm = cc->d.L;
     dim3 eblk(32, 8), egrd((cc->c + 31) / 32, cc->P);
-    dim3 cgrd((cc->I * cc->cb + kWarps - 1) / kWarps, cc->P);
-    dim3 vgrd((cc->I * cc->c + kWarps - 1) / kWarps, cc->P);
     for (int tt = 0; tt < T; ++tt) {
         const long long t = t0 + tt;
         cc_enter_kernel<<<egrd, eblk, 0, s>>>(src, cc->mu, g, cc->gamma, T, tt, t, clip);
-        if (dcm <= 8) cc_cn_kernel<8><<<cgrd, kWarps * 32, 0, s>>>(cc->d, g, cc->msg, cc->mu, t, clip);
-        else if (dcm <= 16) cc_cn_kernel<16><<<cgrd, kWarps * 32, 0, s>>>(cc->d, g, cc->msg, cc->mu, t, clip);
-        else if (dcm <= 24) cc_cn_kernel<24><<<cgrd, kWarps * 32, 0, s>>>(cc->d, g, cc->msg, cc->mu, t, clip);
-        else cc_cn_kernel<32><<<cgrd, kWarps * 32, 0, s>>>(cc->d, g, cc->msg, cc->mu, t, clip);
+        // processors whose layer (check pass) / frame (variable pass) exists yet
+        const int n_cn = (int)std::min<long long>(cc->I, t / cc->lam + 1);
+        const int n_vn = t < cc->ms ? 0 : (int)std::min<long long>(cc->I, (t - cc->ms) / cc->lam + 1);
+        if (dcm <= 4) cc_cn_launch<4>(cc, g, t, clip, n_cn, s);
+        else if (dcm <= 6) cc_cn_launch<6>(cc, g, t, clip, n_cn, s);
+        else if (dcm <= 8) cc_cn_launch<8>(cc, g, t, clip, n_cn, s);
+        else if (dcm <= 16) cc_cn_launch<16>(cc, g, t, clip, n_cn, s);
+        else cc_cn_launch<32>(cc, g, t, clip, n_cn, s);
         const long long Fd = t - (long long)cc->ring + 1;  // frame decided at this slot
         const int q = Fd >= 0 ? (int)(Fd - (first_dec > 0 ? first_dec : 0)) : -1;
         if (q >= 0) ++n;
-        if (cc->d.J <= 4)
-            cc_vn_kernel<4><<<vgrd, kWarps * 32, 0, s>>>(cc->d, g, cc->msg, cc->mu, t, clip, cc->gamma, T, q, dh, dp);
-        else
-            cc_vn_kernel<8><<<vgrd, kWarps * 32, 0, s>>>(cc->d, g, cc->msg, cc->mu, t, clip, cc->gamma, T, q, dh, dp);
-        count_launch(3);
+        if (n_vn > 0) {
+            if (cc->d.J == 3) cc_vn_launch<3>(cc, g, t, clip, n_vn, T, q, dh, dp, s);
+            else if (cc->d.J <= 4) cc_vn_launch<4>(cc, g, t, clip, n_vn, T, q, dh, dp, s);
+            else cc_vn_launch<8>(cc, g, t, clip, n_vn, T, q, dh, dp, s);
+        }
+        count_launch(n_vn > 0 ? 3 : 2);
     }
     LDPC_CUDA_TRY(cudaGetLastError());
     cc->t = t0 + T;

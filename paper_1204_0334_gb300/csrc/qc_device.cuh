@@ -4,6 +4,9 @@
 
 #include "ldpc_internal.cuh"
 
+#include <mutex>
+#include <unordered_map>
+
 namespace ldpc {
 
 constexpr int kWarps = 8;  // warps per block in the node kernels: 8 consecutive rows / variables
@@ -161,6 +164,47 @@ __device__ __forceinline__ void channel_quad(uint64_t seed, uint64_t F, int q, f
     uint32_t w[4];
     philox4x32_10((uint32_t)q, (uint32_t)F, (uint32_t)(F >> 32), 0u, (uint32_t)seed, (uint32_t)(seed >> 32), w);
     box_muller_llr(w, sigma, s2, mu4);
+}
+
+// ---------------------------------------------------------------------------
+// asynchronous global -> shared copies (cp.async; completion by groups)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// blocks of a persistent launch: resident blocks per SM (occupancy API, cached per
+// kernel) times the SM count; also raises the kernel's dynamic shared-memory limit
+template <typename K>
+int persistent_blocks(K kernel, size_t smem) {
+    static std::mutex mu;
+    static std::unordered_map<const void *, int> cache;  // kernel -> resident blocks per SM
+    static int sms = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    const void *key = (const void *)kernel;
+    auto f = cache.find(key);
+    if (f != cache.end()) return f->second * sms;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int bps = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, kWarps * 32, smem);
+    if (bps < 1) bps = 1;
+    cache[key] = bps;
+    return bps * sms;
 }
 
 // arguments of the variable pass in continuous-simulation (refill) mode

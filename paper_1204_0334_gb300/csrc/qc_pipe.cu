@@ -14,8 +14,6 @@
 // running are visited: a compaction pass after each variable pass lists them.
 #include "qc_device.cuh"
 
-#include <mutex>
-#include <unordered_map>
 
 namespace ldpc {
 
@@ -29,19 +27,6 @@ constexpr int kCnStages = LDPC_CN_STAGES;  // ring slots per warp, check pass
 constexpr int kVnStages = LDPC_VN_STAGES;  // ring slots per warp, variable pass
 constexpr int kModeSP = 0, kModeMS = 1, kModeNOMS = 2;
 constexpr int kNV = 4;  // consecutive variables per variable-pass work item
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
 
 template <int DCMAX>
 struct CnStage {
@@ -584,31 +569,6 @@ __global__ void __launch_bounds__(1024) compact_kernel(const uint32_t *__restric
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-namespace {
-std::mutex g_occ_mu;
-std::unordered_map<const void *, int> g_occ;  // kernel -> resident blocks per SM
-int g_sms = 0;
-
-template <typename K>
-int persistent_blocks(K kernel, size_t smem) {
-    std::lock_guard<std::mutex> lk(g_occ_mu);
-    const void *key = (const void *)kernel;
-    auto f = g_occ.find(key);
-    if (f != g_occ.end()) return f->second * g_sms;
-    if (!g_sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (g_sms <= 0) g_sms = 1;
-    }
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int bps = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, kWarps * 32, smem);
-    if (bps < 1) bps = 1;
-    g_occ[key] = bps;
-    return bps * g_sms;
-}
-}  // namespace
 
 template <int DCMAX, int V, bool XF, int MODE, bool REG>
 static void launch_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, const uint32_t *fresh, cudaStream_t s) {
