@@ -211,6 +211,7 @@ int persistent_blocks(K kernel, size_t smem) {
 struct RefillArgs {
     const uint32_t *sflags = nullptr;  // per package: retire[V], refill[V]
     int *errs = nullptr;               // bit errors of the retiring frames, per slot
+    const void *mu = nullptr;          // channel LLRs, frame-major [P][W][N rounded up to 4]
 };
 
 __device__ __forceinline__ int sbyte(uint32_t w, int v) { return (int)(int8_t)(uint8_t)(w >> (8 * v)); }

@@ -288,6 +288,7 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
                const int *__restrict__ act, float clip, float lsb, int it, int par, RefillArgs rf) {
     using St = VnStage<JMAX, V, STOP, MS>;
     constexpr int W = 32 * V;
+    static_assert(kNV == 4, "items of 4 variables: 16-byte channel rows, 4-byte lane words");
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ int s_sh[kMaxJ * kMaxL], s_eo[kMaxJ * kMaxL];
     for (int i = threadIdx.x; i < d.J * d.L; i += blockDim.x) {
@@ -315,16 +316,32 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
             const int n0 = g * kNV;
             const int l0 = n0 / d.p, k0 = n0 - l0 * d.p;
             const int grp = lane >> 3, sub = lane & 7;
-            // channel LLRs: kNV * MU_SEGS segments of 32 words, one per group of 8 lanes and pass
+            if (REFILL) {
+                // continuous simulation: frame-major channel LLRs [P][W][N4] (rows padded to a
+                // multiple of 4): each lane copies its V frames' kNV values, [lane][v][kNV] in the ring
+                const size_t N4 = (size_t)((d.N + 3) & ~3);
 #pragma unroll
-            for (int s0 = 0; s0 < kNV * MU_SEGS; s0 += 4) {
-                const int s = s0 + grp;
-                const int i = s / MU_SEGS, h = s - i * MU_SEGS;
-                const int n = n0 + i;
-                if ((kNV * MU_SEGS) % 4 == 0 || s < kNV * MU_SEGS)
-                    if (EVEN || n < d.N)
-                        cp_async16(dst + St::MU + i * St::MUW + h * 32 + sub * 4,
-                                   gmu + (size_t)n * St::MUW + h * 32 + sub * 4);
+                for (int v = 0; v < V; ++v) {
+                    const size_t row = (size_t)pk * W + lane * V + v;
+                    if constexpr (MS)
+                        cp_async4(dst + St::MU + lane * 4 + v,
+                                  reinterpret_cast<const uint8_t *>(rf.mu) + row * N4 + n0);
+                    else
+                        cp_async16(dst + St::MU + (lane * V + v) * 4,
+                                   reinterpret_cast<const float *>(rf.mu) + row * N4 + n0);
+                }
+            } else {
+                // channel LLRs: kNV * MU_SEGS segments of 32 words, one per group of 8 lanes and pass
+#pragma unroll
+                for (int s0 = 0; s0 < kNV * MU_SEGS; s0 += 4) {
+                    const int s = s0 + grp;
+                    const int i = s / MU_SEGS, h = s - i * MU_SEGS;
+                    const int n = n0 + i;
+                    if ((kNV * MU_SEGS) % 4 == 0 || s < kNV * MU_SEGS)
+                        if (EVEN || n < d.N)
+                            cp_async16(dst + St::MU + i * St::MUW + h * 32 + sub * 4,
+                                       gmu + (size_t)n * St::MUW + h * 32 + sub * 4);
+                }
             }
             // edge packages: kNV * JMAX of them
 #pragma unroll
@@ -423,6 +440,27 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
                 }
             }
         }
+        // continuous simulation: this lane's channel values, frame-major in the ring
+        float mr[MS ? 1 : V][kNV];
+        uint32_t qr[kNV];
+        if constexpr (REFILL) {
+            if constexpr (MS) {
+                // words v: the kNV bytes of frame v; transpose to words i: frames 0..3 of variable i
+                const uint4 wv = *reinterpret_cast<const uint4 *>(S + St::MU + lane * 4);
+                const uint32_t a01 = __byte_perm(wv.x, wv.y, 0x5140), a23 = __byte_perm(wv.z, wv.w, 0x5140);
+                const uint32_t b01 = __byte_perm(wv.x, wv.y, 0x7362), b23 = __byte_perm(wv.z, wv.w, 0x7362);
+                qr[0] = __byte_perm(a01, a23, 0x5410);
+                qr[1] = __byte_perm(a01, a23, 0x7632);
+                qr[2] = __byte_perm(b01, b23, 0x5410);
+                qr[3] = __byte_perm(b01, b23, 0x7632);
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const float4 f = *reinterpret_cast<const float4 *>(S + St::MU + (lane * V + v) * 4);
+                    mr[v][0] = f.x, mr[v][1] = f.y, mr[v][2] = f.z, mr[v][3] = f.w;
+                }
+            }
+        }
         int l = n0 / d.p, k = n0 - l * d.p;
 #pragma unroll
         for (int i = 0; i < kNV; ++i, ++k) {
@@ -434,7 +472,10 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
                 float m[V], aj[JMAX][V], tot[V];
                 const float *mf = reinterpret_cast<const float *>(S + St::MU + i * St::MUW) + lane * V;
 #pragma unroll
-                for (int v = 0; v < V; ++v) m[v] = mf[v], tot[v] = mf[v];
+                for (int v = 0; v < V; ++v) {
+                    m[v] = REFILL ? mr[v][i] : mf[v];
+                    tot[v] = m[v];
+                }
 #pragma unroll
                 for (int jj = 0; jj < JMAX; ++jj) {
                     const bool on = REG || (jj < d.J && s_sh[jj * d.L + l] >= 0);
@@ -479,7 +520,7 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
 #pragma unroll
                 for (int v = 0; v < V; ++v) outb[v] = __ballot_sync(0xffffffffu, pst[v] < 0.0f);
             } else {
-                const uint32_t qw = S[St::MU + i * St::MUW + lane];
+                const uint32_t qw = REFILL ? qr[i] : S[St::MU + i * St::MUW + lane];
                 uint32_t aw[JMAX];
                 int tot[4];
 #pragma unroll

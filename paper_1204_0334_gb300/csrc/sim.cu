@@ -41,6 +41,8 @@ struct ldpc_sim_state {
     int *errs = nullptr;                  // [slots] wrong bits of the frame retired last step
     int *age = nullptr;                   // [slots] iterations completed by the slot's frame
     int *pend = nullptr;                  // [slots] 2 * iterations + ok of the frame retired last step, or -1
+    void *mu = nullptr;                   // channel LLRs, frame-major [slots][N rounded up to 4]
+    size_t mu_bytes = 0;
     int *rlist = nullptr;                 // [slots] slots refilled this step
     int *rcount = nullptr;                // [2] entries of rlist, by step parity
     unsigned long long *next = nullptr;   // next frame index to hand out
@@ -57,6 +59,7 @@ void sim_free(ldpc_sim_state *st) {
     cudaFree(st->errs);
     cudaFree(st->age);
     cudaFree(st->pend);
+    cudaFree(st->mu);
     cudaFree(st->rlist);
     cudaFree(st->rcount);
     cudaFree(st->next);
@@ -70,7 +73,8 @@ namespace {
 
 ldpc_status sim_ensure(ldpc_code c, size_t slots) {
     ldpc_sim_state *&st = c->sim;
-    if (st && st->slots >= slots) return LDPC_OK;
+    const size_t mu_bytes = slots * (size_t)((c->d.N + 3) & ~3) * 4;
+    if (st && st->slots >= slots && st->mu_bytes >= mu_bytes) return LDPC_OK;
     LDPC_CUDA_TRY(cudaDeviceSynchronize());
     sim_free(st);
     st = new ldpc_sim_state();
@@ -79,6 +83,7 @@ ldpc_status sim_ensure(ldpc_code c, size_t slots) {
         cudaMalloc(&st->errs, slots * 4) != cudaSuccess || cudaMalloc(&st->age, slots * 4) != cudaSuccess ||
         cudaMalloc(&st->pend, slots * 4) != cudaSuccess || cudaMalloc(&st->next, 8) != cudaSuccess ||
         cudaMalloc(&st->rlist, slots * 4) != cudaSuccess || cudaMalloc(&st->rcount, 2 * 4) != cudaSuccess ||
+        cudaMalloc(&st->mu, mu_bytes) != cudaSuccess ||
         cudaHostAlloc(&st->host, 2 * 16 * 8, cudaHostAllocDefault) != cudaSuccess ||
         cudaEventCreateWithFlags(&st->ev[0], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&st->ev[1], cudaEventDisableTiming) != cudaSuccess) {
@@ -89,6 +94,7 @@ ldpc_status sim_ensure(ldpc_code c, size_t slots) {
         return LDPC_ENOMEM;
     }
     st->slots = slots;
+    st->mu_bytes = mu_bytes;
     return LDPC_OK;
 }
 
@@ -204,38 +210,37 @@ __global__ void sim_retire_kernel(uint32_t *__restrict__ flags, uint32_t *__rest
     }
 }
 
-// Channel LLRs of the frames that entered a slot this step, in the package
-// layout of the channel store: clipped floats, or int8 quantized with qscale
-// (as the batch path's channel kernel writes them).  Consecutive threads take
-// consecutive list entries for one group of 4 bits, so a warp's stores land
-// in few lines.
+// Channel LLRs of the frames that entered a slot this step, frame-major
+// ([slot][N4], N4 = N rounded up to 4): clipped floats, or int8 quantized with
+// qscale (as the batch path's channel kernel rounds them).  Consecutive threads
+// take consecutive groups of 4 bits of one frame, so each warp writes whole lines.
 template <bool I8>
 __global__ void sim_channel_kernel(void *__restrict__ mu, const int *__restrict__ rlist,
-                                   const int *__restrict__ rcount, const uint64_t *__restrict__ fid, int N, int W,
+                                   const int *__restrict__ rcount, const uint64_t *__restrict__ fid, int N,
                                    int parity, uint64_t seed, float sigma, float s2, float clip, float qscale) {
     const int cnt = rcount[parity];
     if (cnt == 0) return;
     const int Q = (N + 3) / 4;
+    const size_t N4 = (size_t)Q * 4;
     const long long total = (long long)cnt * Q;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
-        const int q = (int)(i / cnt);
-        const int r = (int)(i - (long long)q * cnt);
+        const int r = (int)(i / Q);
+        const int q = (int)(i - (long long)r * Q);
         const int slot = rlist[r];
-        const int pk = slot / W, w = slot - pk * W;
         float x[4];
         channel_quad(seed, fid[slot], q, sigma, s2, x);
+        if (I8) {
+            uint32_t w = 0u;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int n = 4 * q + e;
-            if (n >= N) break;
-            const size_t idx = ((size_t)pk * N + n) * W + w;
-            if (I8) {
+            for (int e = 0; e < 4; ++e) {
                 const float v = fminf(fmaxf(rintf(x[e] * qscale), -127.0f), 127.0f);
-                reinterpret_cast<int8_t *>(mu)[idx] = (int8_t)v;
-            } else {
-                reinterpret_cast<float *>(mu)[idx] = clipf(x[e], clip);
+                w |= (uint32_t)(uint8_t)(int8_t)v << (8 * e);
             }
+            reinterpret_cast<uint32_t *>(mu)[((size_t)slot * N4 + 4 * q) / 4] = w;
+        } else {
+            reinterpret_cast<float4 *>(mu)[((size_t)slot * N4 + 4 * q) / 4] =
+                make_float4(clipf(x[0], clip), clipf(x[1], clip), clipf(x[2], clip), clipf(x[3], clip));
         }
     }
 }
@@ -262,6 +267,7 @@ ldpc_status qc_ber_sim_refill(ldpc_code c, double sigma, uint64_t seed, uint64_t
     RefillArgs rf;
     rf.sflags = S->sflags;
     rf.errs = S->errs;
+    rf.mu = S->mu;
     const float fsig = (float)sigma, s2 = (float)(2.0 / (sigma * sigma));
     const bool i8 = o.algo == LDPC_ALGO_MS;
     int sms = 0, dev = 0;
@@ -282,11 +288,11 @@ ldpc_status qc_ber_sim_refill(ldpc_code c, double sigma, uint64_t seed, uint64_t
         e = qc_compact(c, P, V, s, S->sflags);
         if (e != LDPC_OK) return e;
         if (i8)
-            sim_channel_kernel<true><<<cblocks, 256, 0, s>>>(c->ws.mu, S->rlist, S->rcount, S->fid, c->d.N, W, parity,
-                                                             seed, fsig, s2, 1e30f, ldexpf(1.0f, o.frac_bits));
+            sim_channel_kernel<true><<<cblocks, 256, 0, s>>>(S->mu, S->rlist, S->rcount, S->fid, c->d.N, parity, seed,
+                                                             fsig, s2, 1e30f, ldexpf(1.0f, o.frac_bits));
         else
-            sim_channel_kernel<false><<<cblocks, 256, 0, s>>>(c->ws.mu, S->rlist, S->rcount, S->fid, c->d.N, W,
-                                                              parity, seed, fsig, s2, o.clip, 1.0f);
+            sim_channel_kernel<false><<<cblocks, 256, 0, s>>>(S->mu, S->rlist, S->rcount, S->fid, c->d.N, parity,
+                                                              seed, fsig, s2, o.clip, 1.0f);
         parity ^= 1;
         const int slot_cn = prof_begin(0, s);
         e = qc_cn_pipe(c, o, 1, s, S->sflags);
