@@ -36,10 +36,11 @@ N_BITS = L * P_CIRC
 K_INFO = N_BITS - J * P_CIRC  # 15300
 E_EDGES = J * L * P_CIRC
 METRIC = "decoded info Mbit/s (n=18360, 30 iters) at BER matching FP64 oracle"
-# DRAM bytes (read + write) per check-pass launch, measured with ncu
-# (dram__bytes_{read,write}.sum) on the default workload of this file (FP32 messages,
-# early stop, 3.5 dB, 4096 slots); absent whenever the kernels change until re-measured.
-CN_DRAM_BYTES_PER_LAUNCH = {}
+# DRAM bytes (read + write) per check-pass launch, averaged over the launches of one
+# default-size call, measured with ncu (dram__bytes_{read,write}.sum) on the default
+# workload of this file (FP32 messages, early stop, 3.5 dB, 4096 slots, 131072 frames);
+# absent whenever the check pass changes until re-measured.
+CN_DRAM_BYTES_PER_LAUNCH = {"f32": 2277.5e6}
 
 
 def args_parse():
@@ -282,7 +283,8 @@ def run_ours(a):
             "achieved": cn_bytes / cn_s / 1e9 if cn_s > 0 else None, "peak": peak, "unit": "GB/s",
             "frac": (cn_bytes / cn_s / 1e9) / peak if cn_s > 0 else None,
             "traffic": (CN_DRAM_BYTES_PER_LAUNCH.get(a.msg) if (not a.no_early_stop and a.gamma == 4096
-                                                                 and a.ebn0 == 3.5 and a.iters == 30) else None),
+                                                                 and a.ebn0 == 3.5 and a.iters == 30
+                                                                 and a.frames == 131072) else None),
             "algorithmic_bytes_per_launch": cn_bytes / max(1, prof["cn_launches"]),
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback",
             "cn_launches": prof["cn_launches"], "cn_ms_avg": prof["cn_ms"] / max(1, prof["cn_launches"]),
