@@ -279,7 +279,7 @@ def run_ours(a):
     cn_s = prof["cn_ms"] / 1e3
     peaks = load_peaks()
     peak = peaks.get("hbm_gbs", 6800.0)
-    roof = {"bound": "hbm", "kernel": "cn_sp_kernel" if algo == pkg.ALGO_SP else "cn_ms_kernel",
+    roof = {"bound": "hbm", "kernel": "cn_pipe_kernel (" + ("sum-product" if algo == pkg.ALGO_SP else "min-sum") + ")",
             "achieved": cn_bytes / cn_s / 1e9 if cn_s > 0 else None, "peak": peak, "unit": "GB/s",
             "frac": (cn_bytes / cn_s / 1e9) / peak if cn_s > 0 else None,
             "traffic": (CN_DRAM_BYTES_PER_LAUNCH.get(a.msg) if (not a.no_early_stop and a.gamma == 4096
