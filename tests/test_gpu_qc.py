@@ -290,6 +290,42 @@ def test_ber_sim_refill_equals_batch_decode(pkg, algo, msg, exact):
         assert abs(res["iters_sum"] - want["iters_sum"]) <= 0.02 * want["iters_sum"]
 
 
+def _batch_counts(pkg, code, ebn0, seed, first, frames, **kw):
+    llr = code.channel(ebn0, seed, first, frames)
+    _, hard, iters, ok = code.decode(llr, want_post=False, **kw)
+    errs = hard.sum(dim=1).cpu().numpy().astype(np.int64)
+    okn = ok.cpu().numpy()
+    return {"frames": frames, "frame_errors": int((errs > 0).sum()), "bit_errors": int(errs.sum()),
+            "iters_sum": int(iters.cpu().numpy().sum()), "undetected": int(((errs > 0) & (okn == 1)).sum())}
+
+
+@pytest.mark.parametrize("case", ["fewer_frames_than_slots", "high_frame_ids", "one_iteration", "ragged_slots",
+                                  "min_sum_fixed"])
+def test_ber_sim_edge_cases_equal_batch_decode(pkg, case):
+    """Continuous simulation at its edges: fewer frames than slots, frame ids above 2^32 (the Philox
+    counter's high word), a single iteration, a slot count that is not a multiple of the package width,
+    integer min-sum without early stop -- always the batch decoder's counts on the same frames."""
+    shifts = synth.qc_shifts(3, 6, 64, seed=1)
+    code = pkg.QCCode(shifts, 64)
+    algo, msg, max_iter, early = pkg.ALGO_SP, pkg.MSG_F32, 12, True
+    frames, first, gamma, ebn0 = 300, 3, 128, 1.5
+    if case == "fewer_frames_than_slots":
+        frames, gamma = 50, 256
+    elif case == "high_frame_ids":
+        first = (1 << 32) + 5
+    elif case == "one_iteration":
+        max_iter = 1
+    elif case == "ragged_slots":
+        gamma = 100
+    elif case == "min_sum_fixed":
+        algo, msg, max_iter, early = pkg.ALGO_MS, pkg.MSG_I8, 9, False
+    res = code.ber_sim(ebn0, seed=21, first_frame=first, max_frames=frames, target_frame_errors=10 ** 9,
+                       gamma=gamma, max_iter=max_iter, early_stop=int(early), algo=algo, msg=msg)
+    want = _batch_counts(pkg, code, ebn0, 21, first, frames, max_iter=max_iter, early_stop=early, algo=algo, msg=msg)
+    for k, v in want.items():
+        assert res[k] == v, (case, k, res[k], v)
+
+
 def test_ber_sim_no_early_stop_runs_max_iter(pkg):
     shifts = synth.qc_shifts(3, 6, 64, seed=1)
     code = pkg.QCCode(shifts, 64)
