@@ -162,6 +162,9 @@ ldpc_status ldpc_code_create(const int32_t *shifts, int32_t J, int32_t L, int32_
     d.E = e;
     // the kernels index by the block column, so the row degree bound is L
     d.dc_max = L;
+    d.divM = fast_div((uint32_t)d.M);
+    d.divP = fast_div((uint32_t)d.p);
+    d.divG = fast_div((uint32_t)((d.N + 3) / 4));
     (void)dcmax;
     ldpc_code c = new (std::nothrow) ldpc_code_s();
     if (!c) {

@@ -14,6 +14,24 @@ namespace ldpc {
 constexpr int kMaxJ = 8;
 constexpr int kMaxL = 32;
 
+// Exact n / d for 0 <= n < 2^32 and a divisor d >= 1 fixed for a launch: the multiply-high
+// method of Granlund and Montgomery, "Division by invariant integers using multiplication"
+// (PLDI 1994, Fig. 4.1): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+// t = mulhi(m, n), q = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0).
+struct FastDiv {
+    uint32_t d, m;
+    int s1, s2;
+};
+inline FastDiv fast_div(uint32_t d) {
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    FastDiv f;
+    f.d = d;
+    f.m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l > 1 ? l - 1 : 0;
+    return f;
+}
 // QC code description passed by value to every kernel (lives in the constant
 // parameter bank, so warp-uniform reads of shifts and block offsets are broadcasts).
 // Block (j, l) with shift a >= 0 owns p edges; edge k of the block joins check
@@ -25,6 +43,7 @@ struct QcDesc {
     int dc_max;         // largest row degree over the block rows
     int shift[kMaxJ * kMaxL];  // -1 = zero block
     int eoff[kMaxJ * kMaxL];   // first edge of block (j, l), -1 for a zero block
+    FastDiv divM, divP, divG;  // n / M, n / p and n / ceil(N / 4) (work-item decomposition)
 };
 
 // Device workspace of one code object, grown on demand.  Frames are grouped in

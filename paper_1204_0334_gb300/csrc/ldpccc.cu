@@ -81,29 +81,6 @@ constexpr int kCcNV = 4;      // consecutive variables per variable-pass work it
 
 __device__ __forceinline__ int wrap_lam(int x, int lam) { return x < 0 ? x + lam : x; }
 
-// Exact n / d for 0 <= n < 2^32 and a divisor d >= 1 fixed for a launch: the multiply-high
-// method of Granlund and Montgomery, "Division by invariant integers using multiplication"
-// (PLDI 1994, Fig. 4.1): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
-// t = mulhi(m, n), q = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0).
-struct FastDiv {
-    uint32_t d, m;
-    int s1, s2;
-};
-static FastDiv fast_div(uint32_t d) {
-    int l = 0;
-    while ((1ull << l) < d) ++l;
-    FastDiv f;
-    f.d = d;
-    f.m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
-    f.s1 = l < 1 ? l : 1;
-    f.s2 = l > 1 ? l - 1 : 0;
-    return f;
-}
-__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f) {
-    const uint32_t t = __umulhi(n, f.m);
-    return (t + ((n - t) >> f.s1)) >> f.s2;
-}
-
 // per-slot constants: t clamped to 2^30 (only compared with frame lags below I*Lambda + Lambda),
 // t mod ring, layer type a = t mod Lambda, and the variable pass's frame type (t - ms) mod Lambda
 struct SlotC {

@@ -207,6 +207,12 @@ int persistent_blocks(K kernel, size_t smem) {
     return bps * sms;
 }
 
+// n / d for a divisor fixed at launch (FastDiv, ldpc_internal.cuh)
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f) {
+    const uint32_t t = __umulhi(n, f.m);
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
 // arguments of the variable pass in continuous-simulation (refill) mode
 struct RefillArgs {
     const uint32_t *sflags = nullptr;  // per package: retire[V], refill[V]

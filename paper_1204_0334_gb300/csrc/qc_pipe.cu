@@ -68,10 +68,10 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
     auto issue = [&](int it, int slot) -> int {
         int mine = -1;
         if (it < total) {
-            const int a = it / d.M;
+            const int a = (int)fdiv((uint32_t)it, d.divM);
             const int m = it - a * d.M;
             const int pk = __ldg(list + a);
-            const int j = m / d.p, r = m - j * d.p;
+            const int j = (int)fdiv((uint32_t)m, d.divP), r = m - j * d.p;
             const uint32_t *gmsg = msg + (size_t)pk * d.E * 32;
             uint32_t *dst = ring + slot * St::WORDS;
             const int g = lane >> 3, sub = lane & 7;
@@ -112,7 +112,7 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
         const int myoff = offr[0];
 #pragma unroll
         for (int s = 0; s < kCnStages - 1; ++s) offr[s] = offr[s + 1];
-        const int pk = __ldg(list + item / d.M);
+        const int pk = __ldg(list + fdiv((uint32_t)item, d.divM));
         uint32_t *gmsg = msg + (size_t)pk * d.E * 32 + lane;
         bool lane_on = false;
         // frames that entered their slot this step (continuous simulation): alpha = 0, so the
@@ -184,7 +184,7 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
         } else if constexpr (MODE == kModeNOMS) {
             // normalized/offset min-sum: alpha = sign * max(w * m - o, 0), (w, o) of this
             // iteration and circulant (j, l); m = min over the other edges = (|beta| == min1 ? min2 : min1)
-            const int j = (item - (item / d.M) * d.M) / d.p;
+            const int j = (int)fdiv((uint32_t)(item - (int)fdiv((uint32_t)item, d.divM) * d.M), d.divP);
             const float *prm = nparams + (size_t)j * d.L * 2;
             float ab[DCMAX][V], mn1[V], mn2[V];
             uint32_t neg[V];
@@ -305,16 +305,19 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
     int item = blockIdx.x * kWarps + warp;
     constexpr int MU_SEGS = St::MUW / 32;
 
-    auto issue = [&](int itm, int slot) {
+    // starts the copies of item itm into ring slot `slot`; returns this lane's edge offset
+    // (lane t < kNV * JMAX: edge (variable t / JMAX, block row t % JMAX), -1 if absent)
+    auto issue = [&](int itm, int slot) -> int {
+        int mine = -1;
         if (itm < total) {
-            const int a = itm / G;
+            const int a = (int)fdiv((uint32_t)itm, d.divG);
             const int g = itm - a * G;
             const int pk = __ldg(list + a);
             uint32_t *dst = ring + slot * St::WORDS;
             const uint32_t *gmsg = msg + (size_t)pk * d.E * 32;
             const uint32_t *gmu = mu + (size_t)pk * d.N * St::MUW;
             const int n0 = g * kNV;
-            const int l0 = n0 / d.p, k0 = n0 - l0 * d.p;
+            const int l0 = (int)fdiv((uint32_t)n0, d.divP), k0 = n0 - l0 * d.p;
             const int grp = lane >> 3, sub = lane & 7;
             if (REFILL) {
                 // continuous simulation: frame-major channel LLRs [P][W][N4] (rows padded to a
@@ -357,6 +360,13 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
                                    gmsg + (size_t)(s_eo[jj * d.L + l] + k) * 32 + sub * 4);
                 }
             }
+            if (lane < kNV * JMAX) {
+                const int i = lane / JMAX, jj = lane - i * JMAX;
+                int l = l0, k = k0 + i;
+                if (k >= d.p) k -= d.p, ++l;
+                if ((EVEN || n0 + i < d.N) && (REG || (jj < d.J && s_sh[jj * d.L + l] >= 0)))
+                    mine = s_eo[jj * d.L + l] + k;
+            }
             if (lane < kNV * V) {
                 const int i = lane / V, v = lane - i * V;
                 const int n = n0 + i;
@@ -375,17 +385,22 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
             }
         }
         cp_async_commit();
+        return mine;
     };
 
+    int offr[kVnStages];
 #pragma unroll
-    for (int s = 0; s < kVnStages - 1; ++s) issue(item + s * GW, s);
+    for (int s = 0; s < kVnStages - 1; ++s) offr[s] = issue(item + s * GW, s);
     int slot = 0;
     for (; item < total; item += GW) {
-        issue(item + (kVnStages - 1) * GW, (slot + kVnStages - 1) % kVnStages);
+        offr[kVnStages - 1] = issue(item + (kVnStages - 1) * GW, (slot + kVnStages - 1) % kVnStages);
         cp_async_wait<kVnStages - 1>();
         __syncwarp();
         const uint32_t *S = ring + slot * St::WORDS;
-        const int a = item / G;
+        const int myoff = offr[0];
+#pragma unroll
+        for (int s = 0; s < kVnStages - 1; ++s) offr[s] = offr[s + 1];
+        const int a = (int)fdiv((uint32_t)item, d.divG);
         const int g = item - a * G;
         const int pk = __ldg(list + a);
         uint32_t *gmsg = msg + (size_t)pk * d.E * 32 + lane;
@@ -461,12 +476,14 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
                 }
             }
         }
-        int l = n0 / d.p, k = n0 - l * d.p;
 #pragma unroll
-        for (int i = 0; i < kNV; ++i, ++k) {
-            if (k >= d.p) k -= d.p, ++l;
+        for (int i = 0; i < kNV; ++i) {
             const int n = n0 + i;
             if (!EVEN && n >= d.N) break;  // warp-uniform
+            // the item's edge offsets (-1: absent), warp-uniform
+            int eo[JMAX];
+#pragma unroll
+            for (int jj = 0; jj < JMAX; ++jj) eo[jj] = __shfl_sync(0xffffffffu, myoff, i * JMAX + jj);
             uint32_t outb[V];
             if constexpr (!MS) {
                 float m[V], aj[JMAX][V], tot[V];
@@ -478,7 +495,7 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
                 }
 #pragma unroll
                 for (int jj = 0; jj < JMAX; ++jj) {
-                    const bool on = REG || (jj < d.J && s_sh[jj * d.L + l] >= 0);
+                    const bool on = REG || eo[jj] >= 0;
 #pragma unroll
                     for (int v = 0; v < V; ++v) aj[jj][v] = 0.0f;
                     if (on) {
@@ -489,8 +506,7 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
                 }
 #pragma unroll
                 for (int jj = 0; jj < JMAX; ++jj) {
-                    const int sh = (REG || jj < d.J) ? s_sh[jj * d.L + l] : -1;
-                    if (!REG && sh < 0) continue;  // warp-uniform
+                    if (!REG && eo[jj] < 0) continue;  // warp-uniform
                     float b[V];
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
@@ -506,7 +522,7 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
                             b[v] = clipf(s, clip);
                         }
                     }
-                    if (lane_on) gmsg[(size_t)(s_eo[jj * d.L + l] + k) * 32] = Lane<V>::pack(b);
+                    if (lane_on) gmsg[(size_t)eo[jj] * 32] = Lane<V>::pack(b);
                 }
                 float pst[V];
 #pragma unroll
@@ -527,7 +543,7 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
                 for (int v = 0; v < 4; ++v) tot[v] = sbyte(qw, v);
 #pragma unroll
                 for (int jj = 0; jj < JMAX; ++jj) {
-                    const bool on = REG || (jj < d.J && s_sh[jj * d.L + l] >= 0);
+                    const bool on = REG || eo[jj] >= 0;
                     aw[jj] = on ? S[St::AL + (i * JMAX + jj) * 32 + lane] : 0u;
 #pragma unroll
                     for (int v = 0; v < 4; ++v) tot[v] += sbyte(aw[jj], v);
@@ -535,8 +551,7 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
                 if (lane_on) {
 #pragma unroll
                     for (int jj = 0; jj < JMAX; ++jj) {
-                        const int sh = (REG || jj < d.J) ? s_sh[jj * d.L + l] : -1;
-                        if (!REG && sh < 0) continue;
+                        if (!REG && eo[jj] < 0) continue;
                         uint32_t o = 0u;
 #pragma unroll
                         for (int v = 0; v < 4; ++v) {
@@ -544,7 +559,7 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
                             b = b > 127 ? 127 : (b < -127 ? -127 : b);
                             o |= ((uint32_t)(uint8_t)(int8_t)b) << (8 * v);
                         }
-                        gmsg[(size_t)(s_eo[jj * d.L + l] + k) * 32] = o;
+                        gmsg[(size_t)eo[jj] * 32] = o;
                     }
                 }
                 if (POST && lane_on) {
