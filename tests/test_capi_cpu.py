@@ -64,3 +64,19 @@ def test_validation_without_a_device(lib):
     assert (o.max_iter, o.algo, o.msg, o.clip, o.frac_bits) == (30, 0, 0, 30.0, 2)
     pkg.ldpc_code_destroy(h)
     assert lib.ldpc_status_str(1) is not None
+
+
+def test_ldpccc_rejects_sizes_beyond_32_bit_indexing(lib):
+    """The window decoder indexes 128-byte package lines with 32-bit integers: a ring of
+    I * Lambda frames of ceil(gamma / 32) packages with J * c edges each must stay below 2^31
+    lines, and the request is refused before any device memory is touched."""
+    import paper_1204_0334_gb300 as pkg
+
+    pkg.lib()
+    shifts = np.array([[0, 1, 2, 3, 4, 5], [1, 2, 3, 4, 5, 0], [2, 3, 4, 5, 0, 1]])
+    with pytest.raises(pkg.LdpcError) as e:
+        pkg.ldpccc_create(shifts, 4096, 4000, 1 << 20)  # 12000 * 32768 * 3 * 8192 lines
+    assert e.value.status == 1 and "2^31" in str(e.value)
+    with pytest.raises(pkg.LdpcError) as e:
+        pkg.ldpccc_create(shifts, 64, 0, 32)  # no processors
+    assert e.value.status == 1
