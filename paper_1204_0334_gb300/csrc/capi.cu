@@ -301,36 +301,9 @@ ldpc_status ldpc_ber_sim(ldpc_code c, double ebn0_db, uint64_t seed, uint64_t fi
     std::memset(out, 0, sizeof(*out));
     const double sigma = sigma_of(c, ebn0_db);
     unsigned long long h[8];
-    if (o.algo != LDPC_ALGO_NOMS) {
-        // continuous simulation: slots refilled as frames stop
-        st = qc_ber_sim_refill(c, sigma, seed, first_frame, max_frames, target_frame_errors, gamma, o, h, s);
-        if (st != LDPC_OK) return st;
-        out->frames = (int64_t)h[0];
-        out->frame_errors = (int64_t)h[1];
-        out->bit_errors = (int64_t)h[2];
-        out->iters_sum = (int64_t)h[3];
-        out->undetected = (int64_t)h[4];
-        out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        return LDPC_OK;
-    }
-    // learned NOMS: parameters depend on the iteration, so frames run in batches of gamma
-    st = qc_ensure_workspace(c, (size_t)gamma, 0);
+    // continuous simulation: slots refilled as frames stop
+    st = qc_ber_sim_refill(c, sigma, seed, first_frame, max_frames, target_frame_errors, gamma, o, h, s);
     if (st != LDPC_OK) return st;
-    LDPC_CUDA_TRY(cudaMemsetAsync(c->ws.counters, 0, 8 * sizeof(unsigned long long), s));
-    int64_t done = 0;
-    while (done < max_frames) {
-        const int g = (int)((max_frames - done) < gamma ? (max_frames - done) : gamma);
-        st = qc_channel_packed(c, sigma, seed, first_frame + (uint64_t)done, g, o, s);
-        if (st != LDPC_OK) return st;
-        st = qc_decode_device(c, g, o, false, s);
-        if (st != LDPC_OK) return st;
-        st = qc_count_errors(c, g, o, s);
-        if (st != LDPC_OK) return st;
-        LDPC_CUDA_TRY(cudaMemcpyAsync(h, c->ws.counters, sizeof(h), cudaMemcpyDeviceToHost, s));
-        LDPC_CUDA_TRY(cudaStreamSynchronize(s));
-        done += g;
-        if ((int64_t)h[1] >= target_frame_errors) break;
-    }
     out->frames = (int64_t)h[0];
     out->frame_errors = (int64_t)h[1];
     out->bit_errors = (int64_t)h[2];

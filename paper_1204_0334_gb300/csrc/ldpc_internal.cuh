@@ -105,11 +105,8 @@ ldpc_status qc_decode_device(ldpc_code c, int gamma, const ldpc_decode_opts &o, 
 ldpc_status qc_pack_llr(ldpc_code c, const float *llr, int gamma, const ldpc_decode_opts &o, cudaStream_t s);
 ldpc_status qc_unpack_outputs(ldpc_code c, int gamma, const ldpc_decode_opts &o, float *post, uint8_t *hard,
                               int32_t *iters, int32_t *ok, cudaStream_t s);
-ldpc_status qc_channel_packed(ldpc_code c, double sigma, uint64_t seed, uint64_t first_frame, int gamma,
-                              const ldpc_decode_opts &o, cudaStream_t s);
 ldpc_status qc_channel_frames(ldpc_code c, double sigma, uint64_t seed, uint64_t first_frame, int gamma,
                               float *out, cudaStream_t s);
-ldpc_status qc_count_errors(ldpc_code c, int gamma, const ldpc_decode_opts &o, cudaStream_t s);
 // syndrome of the hard decisions into flag word `word` (+v) of every package
 ldpc_status qc_syndrome(ldpc_code c, int P, int V, int word, cudaStream_t s);
 
@@ -118,8 +115,10 @@ void noms_free(ldpc_noms_state *w);
 // pipelined node passes (qc_pipe.cu)
 // fresh (continuous simulation, else NULL): per package [2V] words, bits V..2V-1 mark
 // frames that entered their slot this step; their outgoing messages are set to 0
+// ages (continuous simulation, learned min-sum): per slot, the iteration each frame runs in
+// this pass (1-based); its parameter row is ages - 1, clamped to [0, max_iter)
 ldpc_status qc_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, cudaStream_t s,
-                       const uint32_t *fresh = nullptr);
+                       const uint32_t *fresh = nullptr, const int *ages = nullptr);
 ldpc_status qc_vn_pipe(ldpc_code c, const ldpc_decode_opts &o, bool stop, bool post, int it, int par,
                        cudaStream_t s);
 // packages with a running frame; with sflags (continuous simulation) also those

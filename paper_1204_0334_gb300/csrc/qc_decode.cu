@@ -390,91 +390,10 @@ __global__ void unpack_hard_kernel(const uint32_t *__restrict__ hw, uint8_t *__r
 }
 
 // ---------------------------------------------------------------------------
-// Error counting for the all-zero codeword (Sec. V: errors counted after the
-// hard decisions; here on the device).  One block per package; lane = frame
-// bit; the warps split the variables.
+// Channel (Sec. V: codeword and noise made on the GPU): all-zero codeword,
+// BPSK, AWGN; Philox4x32-10 (Salmon et al., SC'11) + Box-Muller, frame-major
+// output [gamma][N] for ldpc_channel.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-count_errors_kernel(const uint32_t *__restrict__ hw, const int32_t *__restrict__ okv,
-                    const int32_t *__restrict__ iters, unsigned long long *__restrict__ counters, int N, int V,
-                    int gamma) {
-    __shared__ int cnt[8][32];
-    const int pk = blockIdx.x;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int W = 32 * V;
-    unsigned long long fr = 0, fe = 0, be = 0, is = 0, ud = 0;
-    for (int v = 0; v < V; ++v) {
-        int c = 0;
-        for (int n = w; n < N; n += 8) c += (hw[((size_t)pk * N + n) * V + v] >> lane) & 1u;
-        cnt[w][lane] = c;
-        __syncthreads();
-        if (w == 0) {
-            int tot = 0;
-            for (int i = 0; i < 8; ++i) tot += cnt[i][lane];
-            const int f = pk * W + lane * V + v;
-            if (f < gamma) {
-                const bool okf = okv[f] != 0;
-                fr += 1;
-                be += (unsigned long long)tot;
-                fe += tot > 0 ? 1 : 0;
-                ud += (tot > 0 && okf) ? 1 : 0;
-                is += (unsigned long long)iters[f];
-            }
-        }
-        __syncthreads();
-    }
-    if (w == 0) {
-        for (int o = 16; o > 0; o >>= 1) {
-            fr += __shfl_xor_sync(0xffffffffu, fr, o);
-            fe += __shfl_xor_sync(0xffffffffu, fe, o);
-            be += __shfl_xor_sync(0xffffffffu, be, o);
-            is += __shfl_xor_sync(0xffffffffu, is, o);
-            ud += __shfl_xor_sync(0xffffffffu, ud, o);
-        }
-        if (lane == 0) {
-            atomicAdd(counters + 0, fr);
-            atomicAdd(counters + 1, fe);
-            atomicAdd(counters + 2, be);
-            atomicAdd(counters + 3, is);
-            atomicAdd(counters + 4, ud);
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Channel: Philox4x32-10 (Salmon et al., SC'11) + Box-Muller, all-zero codeword.
-// ---------------------------------------------------------------------------
-// straight into the package layout; thread x = frame within the package, y = bit quad
-template <typename Out>
-__global__ void channel_packed_kernel(Out *__restrict__ mu, int N, int W, int gamma, int frames_alloc,
-                                      uint64_t seed, uint64_t first_frame, float sigma, float s2, float clip,
-                                      float qscale) {
-    const int fw = threadIdx.x;
-    const int pk = blockIdx.y;
-    const int q = blockIdx.x * blockDim.y + threadIdx.y;
-    const int f = pk * W + fw;
-    if (4 * q >= N || f >= frames_alloc) return;
-    float v4[4];
-    if (f < gamma) {
-        channel_quad(seed, first_frame + (uint64_t)f, q, sigma, s2, v4);
-    } else {
-        v4[0] = v4[1] = v4[2] = v4[3] = clip;
-    }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const int n = 4 * q + e;
-        if (n >= N) break;
-        const size_t idx = ((size_t)pk * N + n) * W + fw;
-        if (sizeof(Out) == 1) {
-            float qv = rintf(v4[e] * qscale);
-            qv = fminf(fmaxf(qv, -127.0f), 127.0f);
-            reinterpret_cast<int8_t *>(mu)[idx] = (int8_t)qv;
-        } else {
-            reinterpret_cast<float *>(mu)[idx] = clipf(v4[e], clip);
-        }
-    }
-}
-
 __global__ void channel_frames_kernel(float *__restrict__ out, int N, int gamma, uint64_t seed, uint64_t first_frame,
                                       float sigma, float s2) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -722,25 +641,6 @@ ldpc_status qc_unpack_outputs(ldpc_code c, int gamma, const ldpc_decode_opts &o,
     return LDPC_OK;
 }
 
-ldpc_status qc_channel_packed(ldpc_code c, double sigma, uint64_t seed, uint64_t first_frame, int gamma,
-                              const ldpc_decode_opts &o, cudaStream_t s) {
-    const int V = words_per_lane(o), W = 32 * V;
-    const int P = (gamma + W - 1) / W;
-    const int Q = (c->d.N + 3) / 4;
-    const int ty = 256 / W > 0 ? 256 / W : 1;
-    dim3 blk(W, ty), grd((Q + ty - 1) / ty, P);
-    const float fs = (float)sigma, s2 = (float)(2.0 / (sigma * sigma));
-    count_launch();
-    if (o.algo == LDPC_ALGO_MS)
-        channel_packed_kernel<int8_t><<<grd, blk, 0, s>>>((int8_t *)c->ws.mu, c->d.N, W, gamma, P * W, seed,
-                                                          first_frame, fs, s2, 1e30f, ldexpf(1.0f, o.frac_bits));
-    else
-        channel_packed_kernel<float><<<grd, blk, 0, s>>>((float *)c->ws.mu, c->d.N, W, gamma, P * W, seed,
-                                                         first_frame, fs, s2, o.clip, 1.0f);
-    LDPC_CUDA_TRY(cudaGetLastError());
-    return LDPC_OK;
-}
-
 ldpc_status qc_channel_frames(ldpc_code c, double sigma, uint64_t seed, uint64_t first_frame, int gamma, float *out,
                               cudaStream_t s) {
     const int Q = (c->d.N + 3) / 4;
@@ -752,13 +652,5 @@ ldpc_status qc_channel_frames(ldpc_code c, double sigma, uint64_t seed, uint64_t
     return LDPC_OK;
 }
 
-ldpc_status qc_count_errors(ldpc_code c, int gamma, const ldpc_decode_opts &o, cudaStream_t s) {
-    const int V = words_per_lane(o), W = 32 * V;
-    const int P = (gamma + W - 1) / W;
-    count_launch();
-    count_errors_kernel<<<P, 256, 0, s>>>(c->ws.hw, c->ws.iters + c->ws.gamma_cap, c->ws.iters, c->ws.counters, c->d.N, V, gamma);
-    LDPC_CUDA_TRY(cudaGetLastError());
-    return LDPC_OK;
-}
 
 }  // namespace ldpc

@@ -183,27 +183,33 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // blocks of a persistent launch: resident blocks per SM (occupancy API, cached per
-// kernel) times the SM count; also raises the kernel's dynamic shared-memory limit
+// kernel and dynamic shared-memory size) times the SM count; also raises the kernel's
+// dynamic shared-memory limit to the largest size requested so far
 template <typename K>
 int persistent_blocks(K kernel, size_t smem) {
     static std::mutex mu;
-    static std::unordered_map<const void *, int> cache;  // kernel -> resident blocks per SM
+    static std::unordered_map<const void *, size_t> limit;         // kernel -> attribute set
+    static std::unordered_map<const void *, std::unordered_map<size_t, int>> cache;  // -> blocks per SM
     static int sms = 0;
     std::lock_guard<std::mutex> lk(mu);
     const void *key = (const void *)kernel;
-    auto f = cache.find(key);
-    if (f != cache.end()) return f->second * sms;
+    auto &per = cache[key];
+    auto f = per.find(smem);
+    if (f != per.end()) return f->second * sms;
     if (!sms) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 1;
     }
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > limit[key]) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        limit[key] = smem;
+    }
     int bps = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, kWarps * 32, smem);
     if (bps < 1) bps = 1;
-    cache[key] = bps;
+    per[smem] = bps;
     return bps * sms;
 }
 

@@ -27,6 +27,7 @@ constexpr int kCnStages = LDPC_CN_STAGES;  // ring slots per warp, check pass
 constexpr int kVnStages = LDPC_VN_STAGES;  // ring slots per warp, variable pass
 constexpr int kModeSP = 0, kModeMS = 1, kModeNOMS = 2;
 constexpr int kNV = 4;  // consecutive variables per variable-pass work item
+constexpr int kNomsSmemTable = 48 << 10;  // largest learned-parameter table kept in shared memory
 
 template <int DCMAX>
 struct CnStage {
@@ -46,17 +47,32 @@ template <int DCMAX, int V, bool XF, int MODE, bool REG>
 __global__ void __launch_bounds__(kWarps * 32)
 cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__restrict__ flags,
                const uint32_t *__restrict__ fresh, const int *__restrict__ act, float clip,
-               const float *__restrict__ nparams) {
+               const float *__restrict__ nparams, const int *__restrict__ ages, int T) {
     using St = CnStage<DCMAX>;
+    // learned min-sum with frames at different iterations (continuous simulation): each lane's
+    // frames pick their own parameter row from their iteration counts, staged after the packages
+    constexpr int W = 32 * V;
+    constexpr int RW = St::WORDS + (MODE == kModeNOMS ? W : 0);
+    // the parameter table [T][J*L] (w, o) in shared memory after the rings, rows padded to
+    // S = 1 mod 16 pairs so that lanes reading different rows fall in different banks
+    const int PS = ((d.J * d.L + 14) / 16) * 16 + 1;
+    const bool prm_smem = MODE == kModeNOMS && ages && T * PS * 8 <= kNomsSmemTable;
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ int s_sh[kMaxJ * kMaxL], s_eo[kMaxJ * kMaxL];
     for (int i = threadIdx.x; i < d.J * d.L; i += blockDim.x) {
         s_sh[i] = d.shift[i];
         s_eo[i] = d.eoff[i];
     }
+    float2 *s_prm = reinterpret_cast<float2 *>(smem + kWarps * kCnStages * RW);
+    if (prm_smem) {
+        for (int x = threadIdx.x; x < T * d.J * d.L; x += blockDim.x) {
+            const int row = x / (d.J * d.L), c = x - row * (d.J * d.L);
+            s_prm[row * PS + c] = reinterpret_cast<const float2 *>(nparams)[x];
+        }
+    }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *ring = smem + warp * kCnStages * St::WORDS;
+    uint32_t *ring = smem + warp * kCnStages * RW;
     // work items (package, check row); the host keeps packages * rows below 2^31
     const int total = act[0] * d.M;
     const int *list = act + 1;
@@ -73,8 +89,13 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
             const int pk = __ldg(list + a);
             const int j = (int)fdiv((uint32_t)m, d.divP), r = m - j * d.p;
             const uint32_t *gmsg = msg + (size_t)pk * d.E * 32;
-            uint32_t *dst = ring + slot * St::WORDS;
+            uint32_t *dst = ring + slot * RW;
             const int g = lane >> 3, sub = lane & 7;
+            if (MODE == kModeNOMS && ages) {
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    cp_async4(dst + St::WORDS + lane * V + v, ages + (size_t)pk * W + lane * V + v);
+            }
 #pragma unroll
             for (int q = 0; q < DCMAX / 4; ++q) {
                 const int l = 4 * q + g;
@@ -108,7 +129,7 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
         offr[kCnStages - 1] = issue(item + (kCnStages - 1) * GW, (slot + kCnStages - 1) % kCnStages);
         cp_async_wait<kCnStages - 1>();
         __syncwarp();
-        const uint32_t *S = ring + slot * St::WORDS;
+        const uint32_t *S = ring + slot * RW;
         const int myoff = offr[0];
 #pragma unroll
         for (int s = 0; s < kCnStages - 1; ++s) offr[s] = offr[s + 1];
@@ -185,7 +206,15 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
             // normalized/offset min-sum: alpha = sign * max(w * m - o, 0), (w, o) of this
             // iteration and circulant (j, l); m = min over the other edges = (|beta| == min1 ? min2 : min1)
             const int j = (int)fdiv((uint32_t)(item - (int)fdiv((uint32_t)item, d.divM) * d.M), d.divP);
-            const float *prm = nparams + (size_t)j * d.L * 2;
+            // parameter rows: this launch's iteration, or per frame (row = iterations run - 1)
+            const float2 *prm[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                int row = 0;
+                if (ages) row = min(max((int)S[St::WORDS + lane * V + v] - 1, 0), T - 1);
+                prm[v] = prm_smem ? s_prm + row * PS + j * d.L
+                                  : reinterpret_cast<const float2 *>(nparams) + ((size_t)row * d.J + j) * d.L;
+            }
             float ab[DCMAX][V], mn1[V], mn2[V];
             uint32_t neg[V];
 #pragma unroll
@@ -217,12 +246,12 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
             for (int l = 0; l < DCMAX; ++l) {
                 const int o = __shfl_sync(0xffffffffu, myoff, l);
                 if (!REG && o < 0) continue;
-                const float w = __ldg(prm + 2 * l), ofs = __ldg(prm + 2 * l + 1);
                 float out[V];
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
+                    const float2 wo = prm_smem ? prm[v][l] : __ldg(prm[v] + l);
                     const float m = ab[l][v] == mn1[v] ? mn2[v] : mn1[v];
-                    const float mag = fminf(fmaxf(fmaf(w, m, -ofs), 0.0f), clip);
+                    const float mag = fminf(fmaxf(fmaf(wo.x, m, -wo.y), 0.0f), clip);
                     out[v] = (par_all[v] ^ ((neg[v] >> l) & 1u)) ? -mag : mag;
                     if (fr[v]) out[v] = 0.0f;
                 }
@@ -627,24 +656,35 @@ __global__ void __launch_bounds__(1024) compact_kernel(const uint32_t *__restric
 // ---------------------------------------------------------------------------
 
 template <int DCMAX, int V, bool XF, int MODE, bool REG>
-static void launch_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, const uint32_t *fresh, cudaStream_t s) {
+static void launch_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, const uint32_t *fresh, const int *ages,
+                           cudaStream_t s) {
     auto k = cn_pipe_kernel<DCMAX, V, XF, MODE, REG>;
-    const size_t smem = (size_t)kWarps * kCnStages * CnStage<DCMAX>::WORDS * 4;
+    size_t smem = (size_t)kWarps * kCnStages * (CnStage<DCMAX>::WORDS + (MODE == kModeNOMS ? 32 * V : 0)) * 4;
+    if (MODE == kModeNOMS && ages) {
+        const int PS = ((c->d.J * c->d.L + 14) / 16) * 16 + 1;
+        const size_t tb = (size_t)o.max_iter * PS * 8;
+        if (tb <= (size_t)kNomsSmemTable) smem += tb;
+    }
     const int blocks = persistent_blocks(k, smem);
-    const float *np = o.noms_params ? o.noms_params + (size_t)(it - 1) * c->d.J * c->d.L * 2 : nullptr;
-    k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, c->ws.flags, fresh, c->ws.act, o.clip, np);
+    // per-frame rows (ages): the whole table; else this iteration's row
+    const float *np = !o.noms_params ? nullptr
+                      : ages ? o.noms_params
+                             : o.noms_params + (size_t)(it - 1) * c->d.J * c->d.L * 2;
+    k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, c->ws.flags, fresh, c->ws.act, o.clip, np,
+                                        ages, o.max_iter);
 }
 
 template <int DCMAX, bool REG>
-static void cn_pipe_dispatch(ldpc_code c, const ldpc_decode_opts &o, int it, const uint32_t *fresh, cudaStream_t s) {
-    if (o.algo == LDPC_ALGO_MS) launch_cn_pipe<DCMAX, 4, false, kModeMS, REG>(c, o, it, fresh, s);
+static void cn_pipe_dispatch(ldpc_code c, const ldpc_decode_opts &o, int it, const uint32_t *fresh, const int *ages,
+                             cudaStream_t s) {
+    if (o.algo == LDPC_ALGO_MS) launch_cn_pipe<DCMAX, 4, false, kModeMS, REG>(c, o, it, fresh, ages, s);
     else if (o.algo == LDPC_ALGO_NOMS) {
-        if (o.msg == LDPC_MSG_F16) launch_cn_pipe<DCMAX, 2, false, kModeNOMS, REG>(c, o, it, fresh, s);
-        else launch_cn_pipe<DCMAX, 1, false, kModeNOMS, REG>(c, o, it, fresh, s);
+        if (o.msg == LDPC_MSG_F16) launch_cn_pipe<DCMAX, 2, false, kModeNOMS, REG>(c, o, it, fresh, ages, s);
+        else launch_cn_pipe<DCMAX, 1, false, kModeNOMS, REG>(c, o, it, fresh, ages, s);
     } else if (o.msg == LDPC_MSG_F16) {
-        launch_cn_pipe<DCMAX, 2, false, kModeSP, REG>(c, o, it, fresh, s);
+        launch_cn_pipe<DCMAX, 2, false, kModeSP, REG>(c, o, it, fresh, ages, s);
     } else {
-        launch_cn_pipe<DCMAX, 1, true, kModeSP, REG>(c, o, it, fresh, s);
+        launch_cn_pipe<DCMAX, 1, true, kModeSP, REG>(c, o, it, fresh, ages, s);
     }
 }
 
@@ -656,13 +696,14 @@ static bool regular_rows(const QcDesc &d, int dcmax) {
     return true;
 }
 
-ldpc_status qc_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, cudaStream_t s, const uint32_t *fresh) {
+ldpc_status qc_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, cudaStream_t s, const uint32_t *fresh,
+                       const int *ages) {
     const QcDesc &d = c->d;
-    if (regular_rows(d, 24)) cn_pipe_dispatch<24, true>(c, o, it, fresh, s);
-    else if (d.L <= 8) cn_pipe_dispatch<8, false>(c, o, it, fresh, s);
-    else if (d.L <= 16) cn_pipe_dispatch<16, false>(c, o, it, fresh, s);
-    else if (d.L <= 24) cn_pipe_dispatch<24, false>(c, o, it, fresh, s);
-    else cn_pipe_dispatch<32, false>(c, o, it, fresh, s);
+    if (regular_rows(d, 24)) cn_pipe_dispatch<24, true>(c, o, it, fresh, ages, s);
+    else if (d.L <= 8) cn_pipe_dispatch<8, false>(c, o, it, fresh, ages, s);
+    else if (d.L <= 16) cn_pipe_dispatch<16, false>(c, o, it, fresh, ages, s);
+    else if (d.L <= 24) cn_pipe_dispatch<24, false>(c, o, it, fresh, ages, s);
+    else cn_pipe_dispatch<32, false>(c, o, it, fresh, ages, s);
     LDPC_CUDA_TRY(cudaGetLastError());
     return LDPC_OK;
 }
@@ -737,6 +778,7 @@ template <int JMAX, bool REG>
 static void vn_refill_dispatch(ldpc_code c, const ldpc_decode_opts &o, const RefillArgs &rf, cudaStream_t s) {
     if (o.algo == LDPC_ALGO_MS) launch_vn_refill<JMAX, 4, false, true, REG>(c, o, rf, s);
     else if (o.msg == LDPC_MSG_F16) launch_vn_refill<JMAX, 2, false, false, REG>(c, o, rf, s);
+    else if (o.algo == LDPC_ALGO_NOMS) launch_vn_refill<JMAX, 1, false, false, REG>(c, o, rf, s);
     else launch_vn_refill<JMAX, 1, true, false, REG>(c, o, rf, s);
 }
 

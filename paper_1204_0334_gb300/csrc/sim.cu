@@ -295,7 +295,7 @@ ldpc_status qc_ber_sim_refill(ldpc_code c, double sigma, uint64_t seed, uint64_t
                                                               seed, fsig, s2, o.clip, 1.0f);
         parity ^= 1;
         const int slot_cn = prof_begin(0, s);
-        e = qc_cn_pipe(c, o, 1, s, S->sflags);
+        e = qc_cn_pipe(c, o, 1, s, S->sflags, o.algo == LDPC_ALGO_NOMS ? S->age : nullptr);
         if (e != LDPC_OK) return e;
         prof_end(slot_cn, s);
         const int slot_vn = prof_begin(1, s);

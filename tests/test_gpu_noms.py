@@ -130,3 +130,35 @@ def test_training_gains_over_plain_min_sum(pkg):
     base = noms.ber(code, p0, 3.5, frames=8192)
     trained = noms.ber(code, params, 3.5, frames=8192)
     assert trained["bit_errors"] < 0.5 * base["bit_errors"], (trained, base)
+
+
+@pytest.mark.parametrize("msg,exact", [("f32", True), ("f16", False)])
+def test_noms_ber_sim_equals_batch_decode(pkg, msg, exact):
+    """The continuous simulation runs frames at different iterations side by side; each frame must still
+    use the parameter row of its own iteration: counts equal those of the batch decoder on the same
+    channel frames (FP16: statistically, the batch decoder's first pass reads the FP32 channel LLRs)."""
+    shifts, rp, col, cb = setup(3, 6, 64, 1)
+    code = pkg.QCCode(shifts, 64)
+    T, frames, gamma, ebn0, seed, first = 9, 900, 128, 1.75, 31, 7
+    prm = torch.from_numpy(rand_params(T, 18, 4)).cuda()
+    M = pkg.MSG_F32 if msg == "f32" else pkg.MSG_F16
+    o = pkg.default_opts(max_iter=T, early_stop=1, algo=pkg.ALGO_NOMS, msg=M)
+    o.noms_params = prm.data_ptr()
+    res = pkg.ldpc_ber_sim(code.handle, ebn0, seed, first, frames, 10 ** 9, gamma, o)
+    llr = code.channel(ebn0, seed, first, frames)
+    hard = torch.empty((frames, code.N), dtype=torch.uint8, device="cuda")
+    iters = torch.empty(frames, dtype=torch.int32, device="cuda")
+    ok = torch.empty(frames, dtype=torch.int32, device="cuda")
+    pkg.ldpc_decode(code.handle, llr, o, None, hard, iters, ok)
+    errs = hard.sum(dim=1).cpu().numpy().astype(np.int64)
+    okn = ok.cpu().numpy()
+    want = {"frames": frames, "frame_errors": int((errs > 0).sum()), "bit_errors": int(errs.sum()),
+            "iters_sum": int(iters.cpu().numpy().sum()), "undetected": int(((errs > 0) & (okn == 1)).sum())}
+    assert 0 < want["frame_errors"] < frames
+    if exact:
+        for k, v in want.items():
+            assert res[k] == v, (k, res[k], v)
+    else:
+        assert res["frames"] == frames
+        assert abs(res["frame_errors"] - want["frame_errors"]) <= max(3, 0.05 * want["frame_errors"])
+        assert abs(res["iters_sum"] - want["iters_sum"]) <= 0.03 * want["iters_sum"]
