@@ -174,8 +174,10 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                         }
 #pragma unroll
                         for (int v = 0; v < V; ++v) {
-                            ph[l][v] = (XF && !FIRST) ? fabsf(x[v]) : phi_f(fabsf(x[v]));
-                            neg[v] |= (x[v] < 0.0f ? 1u : 0u) << l;
+                            ph[l][v] = (XF && !FIRST) ? fabsf(x[v]) * XfScale<V>::load : phi_f(fabsf(x[v]));
+                            // the sign bit: a transformed FP16 message of a strongly negative beta
+                            // may round to -0
+                            neg[v] |= (__float_as_uint(x[v]) >> 31) << l;
                             if (SYN) syn[v] ^= S[St::HW + l * V + v];
                         }
                     }
@@ -414,7 +416,7 @@ bvn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                                 if (j2 != jj) s += aj[j2][v];
                             b[v] = clipf(s, clip);
                             if (XF) {
-                                const float f = phi_f(fabsf(b[v]));
+                                const float f = phi_f(fabsf(b[v])) * XfScale<V>::store;
                                 b[v] = b[v] < 0.0f ? -f : f;
                             }
                         }
@@ -622,8 +624,8 @@ static void b_iteration(ldpc_batch b, int it, cudaStream_t s) {
         b_cn<4, false, true>(b, first, syn, par, s);
         b_vn<4, false, true>(b, syn, it, par, s);
     } else if (b->o.msg == LDPC_MSG_F16) {
-        b_cn<2, false, false>(b, first, syn, par, s);
-        b_vn<2, false, false>(b, syn, it, par, s);
+        b_cn<2, true, false>(b, first, syn, par, s);
+        b_vn<2, true, false>(b, syn, it, par, s);
     } else {
         b_cn<1, true, false>(b, first, syn, par, s);
         b_vn<1, true, false>(b, syn, it, par, s);

@@ -84,6 +84,21 @@ __device__ __forceinline__ float phi_fin(float x) {
     const float hi = phi_hi<false>(x), lo = phi_lo(x);
     return x < 1.0f ? lo : hi;
 }
+// Transformed message storage (the variable pass stores what the check pass sums):
+// FP32 keeps sign(beta) * phi(|beta|); FP16 keeps it scaled by 2^12, so that the
+// normal range of halves covers phi of |beta| in [2.3e-7, 18.7] -- a larger phi
+// (|beta| ~ 0) overflows to inf, whose check-pass sum gives the other edges
+// alpha = phi(inf) = 0, the limit of an erased input; a smaller one (|beta| > 18.7)
+// keeps fewer digits and flushes to 0 past |beta| ~ 25.6, the limit of a certain input.
+template <int V>
+struct XfScale {
+    static constexpr float store = 1.0f, load = 1.0f;
+};
+template <>
+struct XfScale<2> {
+    static constexpr float store = 4096.0f, load = 1.0f / 4096.0f;
+};
+
 // |y| with the sign bit of s
 __device__ __forceinline__ float with_sign_of(float y, float s) {
     return __uint_as_float(__float_as_uint(y) | (__float_as_uint(s) & 0x80000000u));

@@ -163,7 +163,7 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
                     Lane<V>::unpack(S[l * 32 + lane], x);
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
-                        xs[l][v] = XF ? x[v] : copysignf(phi_f(fabsf(x[v])), x[v]);
+                        xs[l][v] = XF ? x[v] * XfScale<V>::load : copysignf(phi_f(fabsf(x[v])), x[v]);
                         sgn[v] ^= __float_as_uint(x[v]);
                     }
                 }
@@ -546,7 +546,7 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
                         if (XF) {
                             // the check pass sums phi(|beta|): evaluate it here, from the unrounded
                             // beta (|clip(s)| = min(|s|, clip)), and keep beta's sign
-                            b[v] = with_sign_of(phi_fin(fminf(fabsf(s), clip)), s);
+                            b[v] = with_sign_of(phi_fin(fminf(fabsf(s), clip)) * XfScale<V>::store, s);
                         } else {
                             b[v] = clipf(s, clip);
                         }
@@ -682,7 +682,7 @@ static void cn_pipe_dispatch(ldpc_code c, const ldpc_decode_opts &o, int it, con
         if (o.msg == LDPC_MSG_F16) launch_cn_pipe<DCMAX, 2, false, kModeNOMS, REG>(c, o, it, fresh, ages, s);
         else launch_cn_pipe<DCMAX, 1, false, kModeNOMS, REG>(c, o, it, fresh, ages, s);
     } else if (o.msg == LDPC_MSG_F16) {
-        launch_cn_pipe<DCMAX, 2, false, kModeSP, REG>(c, o, it, fresh, ages, s);
+        launch_cn_pipe<DCMAX, 2, true, kModeSP, REG>(c, o, it, fresh, ages, s);
     } else {
         launch_cn_pipe<DCMAX, 1, true, kModeSP, REG>(c, o, it, fresh, ages, s);
     }
@@ -721,9 +721,12 @@ static void launch_vn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, int p
 
 template <int JMAX, bool STOP, bool POST, bool REG>
 static void vn_pipe_dispatch(ldpc_code c, const ldpc_decode_opts &o, int it, int par, cudaStream_t s) {
+    // sum-product stores transformed messages; learned min-sum (NOMS) needs beta itself
     if (o.algo == LDPC_ALGO_MS) launch_vn_pipe<JMAX, 4, STOP, POST, false, true, REG>(c, o, it, par, s);
-    else if (o.msg == LDPC_MSG_F16) launch_vn_pipe<JMAX, 2, STOP, POST, false, false, REG>(c, o, it, par, s);
+    else if (o.algo == LDPC_ALGO_NOMS && o.msg == LDPC_MSG_F16)
+        launch_vn_pipe<JMAX, 2, STOP, POST, false, false, REG>(c, o, it, par, s);
     else if (o.algo == LDPC_ALGO_NOMS) launch_vn_pipe<JMAX, 1, STOP, POST, false, false, REG>(c, o, it, par, s);
+    else if (o.msg == LDPC_MSG_F16) launch_vn_pipe<JMAX, 2, STOP, POST, true, false, REG>(c, o, it, par, s);
     else launch_vn_pipe<JMAX, 1, STOP, POST, true, false, REG>(c, o, it, par, s);
 }
 
@@ -777,8 +780,9 @@ static void launch_vn_refill(ldpc_code c, const ldpc_decode_opts &o, const Refil
 template <int JMAX, bool REG>
 static void vn_refill_dispatch(ldpc_code c, const ldpc_decode_opts &o, const RefillArgs &rf, cudaStream_t s) {
     if (o.algo == LDPC_ALGO_MS) launch_vn_refill<JMAX, 4, false, true, REG>(c, o, rf, s);
-    else if (o.msg == LDPC_MSG_F16) launch_vn_refill<JMAX, 2, false, false, REG>(c, o, rf, s);
+    else if (o.algo == LDPC_ALGO_NOMS && o.msg == LDPC_MSG_F16) launch_vn_refill<JMAX, 2, false, false, REG>(c, o, rf, s);
     else if (o.algo == LDPC_ALGO_NOMS) launch_vn_refill<JMAX, 1, false, false, REG>(c, o, rf, s);
+    else if (o.msg == LDPC_MSG_F16) launch_vn_refill<JMAX, 2, true, false, REG>(c, o, rf, s);
     else launch_vn_refill<JMAX, 1, true, false, REG>(c, o, rf, s);
 }
 
