@@ -69,7 +69,7 @@ struct BCnStage {
 // check pass over all codes (FIRST: beta = mu)
 // ---------------------------------------------------------------------------
 template <int V, bool SYN, bool XF, bool MS, bool FIRST>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, 2)  // two blocks of eight warps per SM
 bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const int *__restrict__ eotab,
            uint32_t *__restrict__ msg, const uint32_t *__restrict__ mu, const uint32_t *__restrict__ hw,
            uint32_t *__restrict__ flags, const int *__restrict__ tcount, const BTile *__restrict__ tiles, int TR,
