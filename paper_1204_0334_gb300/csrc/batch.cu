@@ -291,7 +291,10 @@ bvn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
     const int GW = gridDim.x * kWarps;
     int item = blockIdx.x * kWarps + warp;
 
-    auto issue = [&](int itm, int slot) {
+    // starts the copies of item itm; returns this lane's edge offset (lane t < kBNV * kBJ:
+    // edge (variable t / kBJ, block row t % kBJ) of the item, -1 if absent)
+    auto issue = [&](int itm, int slot) -> int {
+        int mine = -1;
         if (itm < total) {
             const BTile tl = tiles[itm / TG];
             const int gi = itm - (itm / TG) * TG;
@@ -326,6 +329,13 @@ bvn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                         }
                     }
                 }
+                if (lane < kBNV * kBJ) {
+                    const int i = lane / kBJ, jj = lane - i * kBJ;
+                    int l = l0, k = k0 + i;
+                    if (k >= C.p) k -= C.p, ++l;
+                    if (n0 + i < C.N && jj < C.J && __ldg(shtab + C.tab + jj * C.L + l) >= 0)
+                        mine = __ldg(eotab + C.tab + jj * C.L + l) + k;
+                }
                 if (lane < kBNV * V) {
                     const int i = lane / V, v = lane - i * V;
                     const int n = n0 + i;
@@ -338,15 +348,20 @@ bvn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
             }
         }
         b_commit();
+        return mine;
     };
 
+    int offr[kBStages];
 #pragma unroll
-    for (int s = 0; s < kBStages - 1; ++s) issue(item + s * GW, s);
+    for (int s = 0; s < kBStages - 1; ++s) offr[s] = issue(item + s * GW, s);
     int slot = 0;
     for (; item < total; item += GW) {
-        issue(item + (kBStages - 1) * GW, (slot + kBStages - 1) % kBStages);
+        offr[kBStages - 1] = issue(item + (kBStages - 1) * GW, (slot + kBStages - 1) % kBStages);
         b_wait<kBStages - 1>();
         __syncwarp();
+        const int myoff = offr[0];
+#pragma unroll
+        for (int s = 0; s < kBStages - 1; ++s) offr[s] = offr[s + 1];
         const BTile tl = tiles[item / TG];
         const int gi = item - (item / TG) * TG;
         if (gi < tl.count) {
@@ -379,26 +394,24 @@ bvn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                 lane_on |= ((~dn) >> lane) & 1u;
             }
             const int n0 = g * kBNV;
-            int l = n0 / C.p, k = n0 - l * C.p;
 #pragma unroll
-            for (int i = 0; i < kBNV; ++i, ++k) {
-                if (k >= C.p) k -= C.p, ++l;
+            for (int i = 0; i < kBNV; ++i) {
                 const int n = n0 + i;
                 if (n >= C.N) break;
+                int eo[kBJ];  // the item's edge offsets, -1 absent (warp-uniform)
+#pragma unroll
+                for (int jj = 0; jj < kBJ; ++jj) eo[jj] = __shfl_sync(0xffffffffu, myoff, i * kBJ + jj);
                 uint32_t outb[V];
                 if constexpr (!MS) {
                     float m[V], aj[kBJ][V], tot[V];
                     const float *mf = reinterpret_cast<const float *>(S + St::MU + i * St::MUW) + lane * V;
 #pragma unroll
                     for (int v = 0; v < V; ++v) m[v] = mf[v], tot[v] = mf[v];
-                    int eo[kBJ];
 #pragma unroll
                     for (int jj = 0; jj < kBJ; ++jj) {
-                        eo[jj] = -1;
 #pragma unroll
                         for (int v = 0; v < V; ++v) aj[jj][v] = 0.0f;
-                        if (jj < C.J && __ldg(shtab + C.tab + jj * C.L + l) >= 0) {
-                            eo[jj] = __ldg(eotab + C.tab + jj * C.L + l) + k;
+                        if (eo[jj] >= 0) {
                             Lane<V>::unpack(S[St::AL + (i * kBJ + jj) * 32 + lane], aj[jj]);
 #pragma unroll
                             for (int v = 0; v < V; ++v) tot[v] += aj[jj][v];
@@ -427,15 +440,13 @@ bvn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                 } else {
                     const uint32_t qw = S[St::MU + i * St::MUW + lane];
                     uint32_t aw[kBJ];
-                    int eo[kBJ], tot[4];
+                    int tot[4];
 #pragma unroll
                     for (int v = 0; v < 4; ++v) tot[v] = sbyte(qw, v);
 #pragma unroll
                     for (int jj = 0; jj < kBJ; ++jj) {
-                        eo[jj] = -1;
                         aw[jj] = 0u;
-                        if (jj < C.J && __ldg(shtab + C.tab + jj * C.L + l) >= 0) {
-                            eo[jj] = __ldg(eotab + C.tab + jj * C.L + l) + k;
+                        if (eo[jj] >= 0) {
                             aw[jj] = S[St::AL + (i * kBJ + jj) * 32 + lane];
 #pragma unroll
                             for (int v = 0; v < 4; ++v) tot[v] += sbyte(aw[jj], v);
