@@ -59,8 +59,7 @@ struct BCnStage {
     static constexpr int MUW = MS ? 32 : 32 * V;     // words of one channel-LLR package
     static constexpr int SEGW = FIRST ? MUW : 32;    // words per edge in the stage
     static constexpr int SEG = kBDC * SEGW;
-    static constexpr int OFF = SEG;                  // [l]: edge offset in the package or -1
-    static constexpr int HW = OFF + kBDC;
+    static constexpr int HW = SEG;
     static constexpr int FL = HW + (SYN ? kBDC * V : 0);
     static constexpr int WORDS = (FL + V + 3) & ~3;
 };
@@ -82,7 +81,10 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
     const int GW = gridDim.x * kWarps;
     int item = blockIdx.x * kWarps + warp;
 
-    auto issue = [&](int it, int slot) {
+    // starts the copies of item it; returns this lane's edge offset (lane l < kBDC: edge l of
+    // the row in 32-word packages, -1 if absent)
+    auto issue = [&](int it, int slot) -> int {
+        int mine = -1;
         if (it < total) {
             const BTile tl = tiles[it / TR];
             const int ri = it - (it / TR) * TR;
@@ -91,7 +93,6 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                 const int m = tl.start + ri;
                 const int j = m / C.p, r = m - j * C.p;
                 uint32_t *dst = ring + slot * St::WORDS;
-                int *off = reinterpret_cast<int *>(dst + St::OFF);
                 const uint32_t *gsrc = FIRST ? mu + C.mu + (size_t)tl.pk * C.N * St::MUW
                                              : msg + C.msg + (size_t)tl.pk * C.E * 32;
                 const int g = lane >> 3, sub = lane & 7;
@@ -113,7 +114,14 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                             b_cp16(dst + l * 32 + sub * 4, gsrc + (size_t)o * 32 + sub * 4);
                         }
                     }
-                    if (sub == 0) off[l] = o;
+                }
+                if (lane < kBDC && lane < C.L) {
+                    const int sh = __ldg(shtab + C.tab + j * C.L + lane);
+                    if (sh >= 0) {
+                        int k = r + sh;
+                        if (k >= C.p) k -= C.p;
+                        mine = __ldg(eotab + C.tab + j * C.L + lane) + k;
+                    }
                 }
                 if (SYN) {
                     for (int w = lane; w < kBDC * V; w += 32) {
@@ -130,21 +138,25 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
             }
         }
         b_commit();
+        return mine;
     };
 
+    int offr[kBStages];
 #pragma unroll
-    for (int s = 0; s < kBStages - 1; ++s) issue(item + s * GW, s);
+    for (int s = 0; s < kBStages - 1; ++s) offr[s] = issue(item + s * GW, s);
     int slot = 0;
     for (; item < total; item += GW) {
-        issue(item + (kBStages - 1) * GW, (slot + kBStages - 1) % kBStages);
+        offr[kBStages - 1] = issue(item + (kBStages - 1) * GW, (slot + kBStages - 1) % kBStages);
         b_wait<kBStages - 1>();
         __syncwarp();
+        const int myoff = offr[0];
+#pragma unroll
+        for (int s = 0; s < kBStages - 1; ++s) offr[s] = offr[s + 1];
         const BTile tl = tiles[item / TR];
         const int ri = item - (item / TR) * TR;
         if (ri < tl.count) {
             const BCode C = codes[tl.code];
             const uint32_t *S = ring + slot * St::WORDS;
-            const int *off = reinterpret_cast<const int *>(S + St::OFF);
             uint32_t *gmsg = msg + C.msg + (size_t)tl.pk * C.E * 32 + lane;
             uint32_t actv[V], syn[V];
             bool lane_on = false;
@@ -163,7 +175,7 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                 for (int l = 0; l < kBDC; ++l) {
 #pragma unroll
                     for (int v = 0; v < V; ++v) ph[l][v] = 0.0f;
-                    if (off[l] >= 0) {
+                    if (__shfl_sync(0xffffffffu, myoff, l) >= 0) {
                         float x[V];
                         if (FIRST) {
                             const float *mf = reinterpret_cast<const float *>(S + l * St::SEGW) + lane * V;
@@ -201,7 +213,7 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                 for (int v = 0; v < V; ++v) par_all[v] = __popc(neg[v]) & 1u, suf[v] = 0.0f;
 #pragma unroll
                 for (int l = kBDC - 1; l >= 0; --l) {
-                    const int o = off[l];
+                    const int o = __shfl_sync(0xffffffffu, myoff, l);
                     if (o >= 0) {
                         float out[V];
 #pragma unroll
@@ -221,7 +233,7 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                 for (int l = 0; l < kBDC; ++l) {
                     ab[l] = 0u;
                     sg[l] = 0u;
-                    if (off[l] >= 0) {
+                    if (__shfl_sync(0xffffffffu, myoff, l) >= 0) {
                         const uint32_t x = S[l * St::SEGW + lane];
                         const uint32_t av = __vabsss4(x);
                         sg[l] = x & 0x80808080u;
@@ -235,16 +247,14 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                         }
                     }
                 }
-                if (lane_on) {
 #pragma unroll
-                    for (int l = 0; l < kBDC; ++l) {
-                        const int o = off[l];
-                        if (o < 0) continue;
-                        const uint32_t eq = __vcmpeq4(ab[l], min1);
-                        const uint32_t mag = (min2 & eq) | (min1 & ~eq);
-                        const uint32_t sneg = ((sgn ^ sg[l]) >> 7) & 0x01010101u;
-                        gmsg[(size_t)o * 32] = __vadd4(mag ^ (sneg * 0xffu), sneg);
-                    }
+                for (int l = 0; l < kBDC; ++l) {
+                    const int o = __shfl_sync(0xffffffffu, myoff, l);
+                    if (o < 0) continue;  // warp-uniform
+                    const uint32_t eq = __vcmpeq4(ab[l], min1);
+                    const uint32_t mag = (min2 & eq) | (min1 & ~eq);
+                    const uint32_t sneg = ((sgn ^ sg[l]) >> 7) & 0x01010101u;
+                    if (lane_on) gmsg[(size_t)o * 32] = __vadd4(mag ^ (sneg * 0xffu), sneg);
                 }
             }
             if (SYN && lane == 0) {
