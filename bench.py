@@ -224,11 +224,11 @@ def run_ours(a):
     opts = pkg.default_opts(max_iter=a.iters, early_stop=0 if a.no_early_stop else 1, algo=algo, msg=msg)
     s_msg = {"f32": 4, "f16": 2, "i8": 1}[a.msg]
     s_mu = 1 if a.msg == "i8" else 4
-    base = (rank << 40) + (1 << 36)
+    from paper_1204_0334_gb300 import shard
 
     def step(i, o=opts):
-        return pkg.ldpc_ber_sim(code.handle, a.ebn0, a.seed, base + i * a.frames, a.frames, 1 << 60, a.gamma, o,
-                                stream)
+        return pkg.ldpc_ber_sim(code.handle, a.ebn0, a.seed, shard.first_frame(rank, i, a.frames), a.frames, 1 << 60,
+                                a.gamma, o, stream)
 
     for w in range(a.warmup):
         step(-1 - w)
@@ -258,18 +258,9 @@ def run_ours(a):
     prof = pkg.ldpc_profile_read()
     pkg.ldpc_profile_enable(False)
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    frames = sum(r["frames"] for r in res)
-    iters_sum = sum(r["iters_sum"] for r in res)
-    fe = sum(r["frame_errors"] for r in res)
-    be = sum(r["bit_errors"] for r in res)
-    if dist:
-        t = torch.tensor([frames, iters_sum, fe, be], dtype=torch.float64, device=dev)
-        dist.all_reduce(t)
-        frames, iters_sum, fe, be = [int(x) for x in t.tolist()]
+    ms = shard.max_over_ranks(ms, dist, dev)
+    tot = shard.merge_counts(res, dist, dev)
+    frames, iters_sum, fe, be = tot["frames"], tot["iters_sum"], tot["frame_errors"], tot["bit_errors"]
     value = frames * K_INFO / (ms / 1e3) / 1e6
 
     # roofline of the check-node kernel: algorithmic bytes = read + write of every edge message of every
