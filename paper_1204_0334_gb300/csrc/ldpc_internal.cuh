@@ -121,9 +121,8 @@ ldpc_status qc_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, cudaStrea
                        const uint32_t *fresh = nullptr, const int *ages = nullptr);
 ldpc_status qc_vn_pipe(ldpc_code c, const ldpc_decode_opts &o, bool stop, bool post, int it, int par,
                        cudaStream_t s);
-// packages with a running frame; with sflags (continuous simulation) also those
-// with a retiring or new frame
-ldpc_status qc_compact(ldpc_code c, int P, int V, cudaStream_t s, const uint32_t *sflags = nullptr);
+// packages with a running frame
+ldpc_status qc_compact(ldpc_code c, int P, int V, cudaStream_t s);
 // continuous simulation (sim.cu)
 void sim_free(ldpc_sim_state *st);
 ldpc_status qc_ber_sim_refill(ldpc_code c, double sigma, uint64_t seed, uint64_t first_frame, int64_t max_frames,

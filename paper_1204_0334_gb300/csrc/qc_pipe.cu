@@ -619,7 +619,7 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
 // act[1..] = package indices (one block)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) compact_kernel(const uint32_t *__restrict__ flags,
-                                                       const uint32_t *__restrict__ sflags, int P, int V,
+                                                       int P, int V,
                                                        int *__restrict__ act) {
     __shared__ int wsum[32];
     __shared__ int s_base;
@@ -630,10 +630,7 @@ __global__ void __launch_bounds__(1024) compact_kernel(const uint32_t *__restric
         const int pk = p0 + threadIdx.x;
         bool on = false;
         if (pk < P)
-            for (int v = 0; v < V; ++v) {
-                on |= ~flags[(size_t)pk * 5 * V + v] != 0u;
-                if (sflags) on |= sflags[(size_t)pk * 2 * V + v] != 0u;  // retiring frames
-            }
+            for (int v = 0; v < V; ++v) on |= ~flags[(size_t)pk * 5 * V + v] != 0u;
         const uint32_t bal = __ballot_sync(0xffffffffu, on);
         if (lane == 0) wsum[warp] = __popc(bal);
         __syncthreads();
@@ -755,8 +752,8 @@ ldpc_status qc_vn_pipe(ldpc_code c, const ldpc_decode_opts &o, bool stop, bool p
     return LDPC_OK;
 }
 
-ldpc_status qc_compact(ldpc_code c, int P, int V, cudaStream_t s, const uint32_t *sflags) {
-    compact_kernel<<<1, 1024, 0, s>>>(c->ws.flags, sflags, P, V, c->ws.act);
+ldpc_status qc_compact(ldpc_code c, int P, int V, cudaStream_t s) {
+    compact_kernel<<<1, 1024, 0, s>>>(c->ws.flags, P, V, c->ws.act);
     LDPC_CUDA_TRY(cudaGetLastError());
     return LDPC_OK;
 }

@@ -45,6 +45,7 @@ struct ldpc_sim_state {
     size_t mu_bytes = 0;
     int *rlist = nullptr;                 // [slots] slots refilled this step
     int *rcount = nullptr;                // [2] entries of rlist, by step parity
+    unsigned int *tickets = nullptr;      // [P + 1]: finished blocks per package, finished packages
     unsigned long long *next = nullptr;   // next frame index to hand out
     unsigned long long *host = nullptr;   // pinned [2][16]: counters, active packages
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -62,6 +63,7 @@ void sim_free(ldpc_sim_state *st) {
     cudaFree(st->mu);
     cudaFree(st->rlist);
     cudaFree(st->rcount);
+    cudaFree(st->tickets);
     cudaFree(st->next);
     if (st->host) cudaFreeHost(st->host);
     for (auto &e : st->ev)
@@ -83,6 +85,7 @@ ldpc_status sim_ensure(ldpc_code c, size_t slots) {
         cudaMalloc(&st->errs, slots * 4) != cudaSuccess || cudaMalloc(&st->age, slots * 4) != cudaSuccess ||
         cudaMalloc(&st->pend, slots * 4) != cudaSuccess || cudaMalloc(&st->next, 8) != cudaSuccess ||
         cudaMalloc(&st->rlist, slots * 4) != cudaSuccess || cudaMalloc(&st->rcount, 2 * 4) != cudaSuccess ||
+        cudaMalloc(&st->tickets, (slots / 32 + 2) * 4) != cudaSuccess ||
         cudaMalloc(&st->mu, mu_bytes) != cudaSuccess ||
         cudaHostAlloc(&st->host, 2 * 16 * 8, cudaHostAllocDefault) != cudaSuccess ||
         cudaEventCreateWithFlags(&st->ev[0], cudaEventDisableTiming) != cudaSuccess ||
@@ -102,7 +105,7 @@ ldpc_status sim_ensure(ldpc_code c, size_t slots) {
 
 // every slot empty, nothing pending, counters zero
 __global__ void sim_init_kernel(uint32_t *flags, int *errs, int *age, int *pend, unsigned long long *next,
-                                int *rcount, unsigned long long *counters, int P, int V) {
+                                int *rcount, unsigned int *tickets, unsigned long long *counters, int P, int V) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int slots = P * 32 * V;
     if (i < slots) {
@@ -117,33 +120,38 @@ __global__ void sim_init_kernel(uint32_t *flags, int *errs, int *age, int *pend,
     if (i < 8) counters[i] = 0ull;
     if (i == 0) *next = 0ull;
     if (i < 2) rcount[i] = 0;
+    if (i <= P) tickets[i] = 0u;
 }
 
-// One warp per (package, word v); lane = slot.  Tallies the frames retired by
-// the previous step, retires the frames that stop now and refills slots.
-__global__ void sim_retire_kernel(uint32_t *__restrict__ flags, uint32_t *__restrict__ sflags,
-                                  uint64_t *__restrict__ fid, int *__restrict__ errs, int *__restrict__ age,
-                                  int *__restrict__ pend, unsigned long long *__restrict__ next,
-                                  int *__restrict__ rlist, int *__restrict__ rcount,
-                                  unsigned long long *counters, int P, int V, int max_iter, int early_stop,
-                                  unsigned long long first_frame, unsigned long long limit,
-                                  unsigned long long target, int parity) {
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (gw == 0 && lane == 0) rcount[parity ^ 1] = 0;  // the next step's list
-    if (gw >= P * V) return;  // warp-uniform
-    const int pk = gw / V, v = gw - pk * V;
+// arguments of the step's check kernel
+struct SimArgs {
+    const uint32_t *hw;
+    uint32_t *flags, *sflags;
+    uint64_t *fid;
+    int *errs, *age, *pend;
+    unsigned long long *next, *counters;
+    int *rlist, *rcount, *act;
+    unsigned int *tickets;  // [P]: finished syndrome blocks per package; [P]: finished packages
+    int P, max_iter, early_stop, parity;
+    unsigned long long first_frame, limit, target;
+};
+
+// One warp per (package, word v); lane = slot.  Tallies the frames retired by the
+// previous step, retires the frames that stop now and refills slots.  Flag words written
+// by other blocks of this launch are read past L1.
+template <int V>
+__device__ void retire_word(const SimArgs &sa, int pk, int v, int lane) {
     const size_t slot = (size_t)pk * 32 * V + lane * V + v;
-    uint32_t *F = flags + (size_t)pk * 5 * V;
-    const uint32_t D = F[v], U = F[V + v];
+    uint32_t *F = sa.flags + (size_t)pk * 5 * V;
+    const uint32_t D = __ldcg(F + v), U = __ldcg(F + V + v);
 
     // frames retired by the previous step: their wrong bits were counted by its variable pass
-    const int pr = pend[slot];
+    const int pr = sa.pend[slot];
     unsigned long long fr = 0, fe = 0, be = 0, is = 0, ud = 0;
     if (pr >= 0) {
-        const int e = errs[slot];
-        errs[slot] = 0;
-        pend[slot] = -1;
+        const int e = sa.errs[slot];
+        sa.errs[slot] = 0;
+        sa.pend[slot] = -1;
         fr = 1;
         be = (unsigned long long)e;
         fe = e > 0;
@@ -160,53 +168,135 @@ __global__ void sim_retire_kernel(uint32_t *__restrict__ flags, uint32_t *__rest
             ud += __shfl_xor_sync(0xffffffffu, ud, o);
         }
         if (lane == 0) {
-            atomicAdd(counters + 0, fr);
-            if (fe) atomicAdd(counters + 1, fe);
-            if (be) atomicAdd(counters + 2, be);
-            atomicAdd(counters + 3, is);
-            if (ud) atomicAdd(counters + 4, ud);
+            atomicAdd(sa.counters + 0, fr);
+            if (fe) atomicAdd(sa.counters + 1, fe);
+            if (be) atomicAdd(sa.counters + 2, be);
+            atomicAdd(sa.counters + 3, is);
+            if (ud) atomicAdd(sa.counters + 4, ud);
         }
     }
 
-    // the check pass just computed the syndrome of the decisions after a iterations
+    // the syndrome of the decisions after a iterations was just computed
     const bool running = !((D >> lane) & 1u);
-    int a = age[slot];
+    int a = sa.age[slot];
     const bool sat = !((U >> lane) & 1u);
-    const bool ret = running && ((early_stop && a >= 1 && sat) || a >= max_iter);
-    if (ret) pend[slot] = 2 * a + (sat ? 1 : 0);
+    const bool ret = running && ((sa.early_stop && a >= 1 && sat) || a >= sa.max_iter);
+    if (ret) sa.pend[slot] = 2 * a + (sat ? 1 : 0);
 
-    // refill: no new frame once the frame-error target is met (read from earlier steps' totals)
-    const bool stop = *(volatile unsigned long long *)(counters + 1) >= target;
+    // refill: no new frame once the frame-error target is met (read from earlier totals)
+    const bool stop = *(volatile unsigned long long *)(sa.counters + 1) >= sa.target;
     const uint32_t want = __ballot_sync(0xffffffffu, (!running || ret) && !stop);
     unsigned long long base = 0;
     if (want) {
-        if (lane == 0) base = atomicAdd(next, (unsigned long long)__popc(want));
+        if (lane == 0) base = atomicAdd(sa.next, (unsigned long long)__popc(want));
         base = __shfl_sync(0xffffffffu, base, 0);
     }
     const unsigned long long idx = base + (unsigned long long)__popc(want & ((1u << lane) - 1u));
-    const bool fill = ((want >> lane) & 1u) && idx < limit;
-    // iterations completed at the next step's retire kernel (a new frame's first step only
+    const bool fill = ((want >> lane) & 1u) && idx < sa.limit;
+    // iterations completed at the next step's check (a new frame's first step only
     // initializes its messages)
     if (fill) {
-        fid[slot] = first_frame + idx;
+        sa.fid[slot] = sa.first_frame + idx;
         a = 0;
     } else if (running && !ret) {
         a += 1;
     }
-    age[slot] = a;
+    sa.age[slot] = a;
     const uint32_t retw = __ballot_sync(0xffffffffu, ret);
     const uint32_t fillw = __ballot_sync(0xffffffffu, fill);
     if (fillw) {
         int rb = 0;
-        if (lane == 0) rb = atomicAdd(rcount + parity, __popc(fillw));
+        if (lane == 0) rb = atomicAdd(sa.rcount + sa.parity, __popc(fillw));
         rb = __shfl_sync(0xffffffffu, rb, 0);
-        if (fill) rlist[rb + __popc(fillw & ((1u << lane) - 1u))] = (int)slot;
+        if (fill) sa.rlist[rb + __popc(fillw & ((1u << lane) - 1u))] = (int)slot;
     }
     if (lane == 0) {
         F[v] = (D | retw) & ~fillw;
-        F[V + v] = 0u;  // set again by the next check pass
-        sflags[(size_t)pk * 2 * V + v] = retw;
-        sflags[(size_t)pk * 2 * V + V + v] = fillw;
+        F[V + v] = 0u;  // set again by the next syndrome
+        sa.sflags[(size_t)pk * 2 * V + v] = retw;
+        sa.sflags[(size_t)pk * 2 * V + V + v] = fillw;
+    }
+}
+
+// The step's check kernel: hard-decision syndrome (eq. hrddcs), per-frame stop and refill,
+// and the list of active packages, in one launch.  Block (x, pk) checks rows 256x ..
+// 256x + 255 of package pk against the packed decisions and ORs the unsatisfied frames
+// into the package's unsat words; the last block to finish a package (atomic ticket after
+// a fence) retires and refills that package's slots; the last package to finish lists the
+// packages with a running or retiring frame (act[0] = count, act[1..]) for the passes.
+// Nothing waits: a block either continues with the later stage or returns.
+template <int V>
+__global__ void __launch_bounds__(256) sim_check_kernel(const QcDesc d, SimArgs sa) {
+    __shared__ int s_last;
+    __shared__ int s_wsum[8];
+    __shared__ int s_base;
+    const int pk = blockIdx.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    {
+        const int m = blockIdx.x * blockDim.x + threadIdx.x;
+        uint32_t syn[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) syn[v] = 0u;
+        if (m < d.M) {
+            const int j = (int)fdiv((uint32_t)m, d.divP), r = m - j * d.p;
+            for (int l = 0; l < d.L; ++l) {
+                const int a = d.shift[j * d.L + l];
+                if (a < 0) continue;
+                int k = r + a;
+                if (k >= d.p) k -= d.p;
+                const uint32_t *h = sa.hw + ((size_t)pk * d.N + (size_t)l * d.p + k) * V;
+#pragma unroll
+                for (int v = 0; v < V; ++v) syn[v] ^= h[v];
+            }
+        }
+        uint32_t *unsat = sa.flags + (size_t)pk * 5 * V + V;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const uint32_t any = __reduce_or_sync(0xffffffffu, syn[v]);
+            if (any && lane == 0) atomicOr(unsat + v, any);
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(sa.tickets + pk, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (warp < V) retire_word<V>(sa, pk, warp, lane);
+    if (threadIdx.x == 0) sa.tickets[pk] = 0u;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(sa.tickets + sa.P, 1u) == (unsigned)sa.P - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // compaction over all packages
+    if (threadIdx.x == 0) s_base = 0;
+    __syncthreads();
+    for (int p0 = 0; p0 < sa.P; p0 += blockDim.x) {
+        const int q = p0 + threadIdx.x;
+        bool on = false;
+        if (q < sa.P)
+            for (int v = 0; v < V; ++v)
+                on |= (~__ldcg(sa.flags + (size_t)q * 5 * V + v) | __ldcg(sa.sflags + (size_t)q * 2 * V + v)) != 0u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, on);
+        if (lane == 0) s_wsum[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, all = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            if (w < warp) before += s_wsum[w];
+            all += s_wsum[w];
+        }
+        const int base = s_base;
+        if (on) sa.act[1 + base + before + __popc(bal & ((1u << lane) - 1u))] = q;
+        __syncthreads();
+        if (threadIdx.x == 0) s_base = base + all;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        sa.act[0] = s_base;
+        sa.rcount[sa.parity ^ 1] = 0;  // the next step's list of new frames
+        sa.tickets[sa.P] = 0u;
     }
 }
 
@@ -261,7 +351,7 @@ ldpc_status qc_ber_sim_refill(ldpc_code c, double sigma, uint64_t seed, uint64_t
     {
         const int n = (int)(slots > (size_t)P * 5 * V ? slots : (size_t)P * 5 * V);
         sim_init_kernel<<<(n + 255) / 256, 256, 0, s>>>(c->ws.flags, S->errs, S->age, S->pend, S->next,
-                                                        S->rcount, c->ws.counters, P, V);
+                                                        S->rcount, S->tickets, c->ws.counters, P, V);
         count_launch();
     }
     RefillArgs rf;
@@ -277,16 +367,35 @@ ldpc_status qc_ber_sim_refill(ldpc_code c, double sigma, uint64_t seed, uint64_t
     int parity = 0;
     const unsigned long long limit = (unsigned long long)max_frames;
     const unsigned long long tgt = target < 0 ? 0ull : (unsigned long long)target;
-    const int rblocks = (P * V * 32 + 255) / 256;
+
+    SimArgs sa;
+    sa.hw = c->ws.hw;
+    sa.flags = c->ws.flags;
+    sa.sflags = S->sflags;
+    sa.fid = S->fid;
+    sa.errs = S->errs;
+    sa.age = S->age;
+    sa.pend = S->pend;
+    sa.next = S->next;
+    sa.counters = c->ws.counters;
+    sa.rlist = S->rlist;
+    sa.rcount = S->rcount;
+    sa.act = c->ws.act;
+    sa.tickets = S->tickets;
+    sa.P = P;
+    sa.max_iter = o.max_iter;
+    sa.early_stop = o.early_stop;
+    sa.first_frame = first_frame;
+    sa.limit = limit;
+    sa.target = tgt;
+    const dim3 cgrd((c->d.M + 255) / 256, P);
 
     auto step = [&]() -> ldpc_status {
-        ldpc_status e = qc_syndrome(c, P, V, V, s);  // unsat words
-        if (e != LDPC_OK) return e;
-        sim_retire_kernel<<<rblocks, 256, 0, s>>>(c->ws.flags, S->sflags, S->fid, S->errs, S->age, S->pend, S->next,
-                                                  S->rlist, S->rcount, c->ws.counters, P, V, o.max_iter,
-                                                  o.early_stop, first_frame, limit, tgt, parity);
-        e = qc_compact(c, P, V, s, S->sflags);
-        if (e != LDPC_OK) return e;
+        sa.parity = parity;
+        if (V == 1) sim_check_kernel<1><<<cgrd, 256, 0, s>>>(c->d, sa);
+        else if (V == 2) sim_check_kernel<2><<<cgrd, 256, 0, s>>>(c->d, sa);
+        else sim_check_kernel<4><<<cgrd, 256, 0, s>>>(c->d, sa);
+        ldpc_status e = LDPC_OK;
         if (i8)
             sim_channel_kernel<true><<<cblocks, 256, 0, s>>>(S->mu, S->rlist, S->rcount, S->fid, c->d.N, parity, seed,
                                                              fsig, s2, 1e30f, ldexpf(1.0f, o.frac_bits));
@@ -302,7 +411,7 @@ ldpc_status qc_ber_sim_refill(ldpc_code c, double sigma, uint64_t seed, uint64_t
         e = qc_vn_refill(c, o, rf, s);
         if (e != LDPC_OK) return e;
         prof_end(slot_vn, s);
-        count_launch(6);
+        count_launch(4);
         return LDPC_OK;
     };
 
