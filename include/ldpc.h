@@ -86,6 +86,22 @@ const char *ldpc_last_error(void);
  * out == NULL), LDPC_ENOMEM.
  */
 ldpc_status ldpc_code_create(const int32_t *shifts, int32_t J, int32_t L, int32_t p, ldpc_code *out);
+/*
+ * ldpc_code_create_sparse -- a general (not quasi-cyclic) LDPC code given by its
+ * parity-check matrix H (Sec. II-A), for decoders that gather through index tables as
+ * the paper's LUT_c / LUT_v do (Sec. IV-A) instead of circulant address arithmetic.
+ *   row_ptr: host int32 [M + 1], col_idx: host int32 [E] -- H in compressed-row form:
+ *            the ones of check m sit in columns col_idx[row_ptr[m] .. row_ptr[m+1]),
+ *            strictly increasing within a row; edges are numbered row by row (the
+ *            paper's order, eq. simpleH).  Copied; the caller keeps them.
+ *   Limits: 1 <= M, N; every row degree in [1, 32]; every column degree in [0, 8];
+ *   E * 32 < 2^31.
+ * ldpc_decode, ldpc_decode_noalloc and ldpc_channel accept the code; ldpc_ber_sim,
+ * the learned min-sum, heterogeneous batches and LDPCCC derivation take QC codes only
+ * (LDPC_EUNSUPPORTED).  Errors: LDPC_EINVAL (sizes, indices, degrees), LDPC_ENOMEM.
+ */
+ldpc_status ldpc_code_create_sparse(int32_t M, int32_t N, const int32_t *row_ptr, const int32_t *col_idx,
+                                    ldpc_code *out);
 ldpc_status ldpc_code_destroy(ldpc_code code);
 /* N, M, E and the design information length K = N - M (any pointer may be NULL). */
 ldpc_status ldpc_code_dims(ldpc_code code, int64_t *N, int64_t *M, int64_t *E, int64_t *K);

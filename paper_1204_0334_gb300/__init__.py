@@ -54,6 +54,7 @@ _SIGNATURES = [
     ("ldpc_status_str", ctypes.c_char_p, [ctypes.c_int]),
     ("ldpc_last_error", ctypes.c_char_p, []),
     ("ldpc_code_create", ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P]),
+    ("ldpc_code_create_sparse", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, P, P, P]),
     ("ldpc_code_destroy", ctypes.c_int, [P]),
     ("ldpc_code_dims", ctypes.c_int, [P, P, P, P, P]),
     ("ldpc_decode", ctypes.c_int, [P, P, ctypes.c_int32, P, P, P, P, P, P]),
@@ -142,6 +143,18 @@ def ldpc_code_create(shifts, p: int) -> int:
     J, L = a.shape
     h = ctypes.c_void_p()
     _check(lib().ldpc_code_create(a.ctypes.data_as(P), J, L, p, ctypes.byref(h)), "ldpc_code_create")
+    return h.value
+
+
+def ldpc_code_create_sparse(row_ptr, col_idx, N: int) -> int:
+    """A general LDPC code from H in compressed-row form (row_ptr [M+1], col_idx [E]).  Returns the handle."""
+    import numpy as np
+
+    rp = np.ascontiguousarray(np.asarray(row_ptr, dtype=np.int32))
+    ci = np.ascontiguousarray(np.asarray(col_idx, dtype=np.int32))
+    h = ctypes.c_void_p()
+    _check(lib().ldpc_code_create_sparse(len(rp) - 1, N, rp.ctypes.data_as(P), ci.ctypes.data_as(P), ctypes.byref(h)),
+           "ldpc_code_create_sparse")
     return h.value
 
 
@@ -389,3 +402,13 @@ class QCCode:
                 stream=None, **opt):
         return ldpc_ber_sim(self.handle, ebn0_db, seed, first_frame, max_frames, target_frame_errors, gamma,
                             default_opts(**opt), stream)
+
+
+class SparseCode(QCCode):
+    """Owning wrapper of a general (index-table) code: H in compressed-row form."""
+
+    def __init__(self, row_ptr, col_idx, N: int):
+        self.row_ptr, self.col_idx = row_ptr, col_idx
+        self.handle = ldpc_code_create_sparse(row_ptr, col_idx, N)
+        d = ldpc_code_dims(self.handle)
+        self.N, self.M, self.E, self.K = d["N"], d["M"], d["E"], d["K"]

@@ -676,6 +676,11 @@ ldpc_status ldpc_batch_create(const ldpc_code *codes, int32_t ncodes, const int3
         return LDPC_EINVAL;
     }
     *out = nullptr;
+    for (int i = 0; i < ncodes; ++i)
+        if (!codes[i] || codes[i]->sparse) {
+            set_error("code %d: batches take QC codes", i);
+            return codes[i] ? LDPC_EUNSUPPORTED : LDPC_EINVAL;
+        }
     const ldpc_decode_opts &o = *opts;
     if (o.max_iter < 1 || o.max_iter > 100000 ||
         !((o.algo == LDPC_ALGO_SP && (o.msg == LDPC_MSG_F32 || o.msg == LDPC_MSG_F16)) ||

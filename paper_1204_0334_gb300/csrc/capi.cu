@@ -1,12 +1,14 @@
 // C-ABI entry points of the block-code decoder (include/ldpc.h).
 #include "ldpc_internal.cuh"
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 namespace ldpc {
 
@@ -42,6 +44,10 @@ static ldpc_status check_opts(const ldpc_code c, const ldpc_decode_opts *o) {
     if (o->max_iter < 1 || o->max_iter > 100000) {
         set_error("max_iter %d out of range [1, 100000]", o->max_iter);
         return LDPC_EINVAL;
+    }
+    if (c && c->sparse && o->algo == LDPC_ALGO_NOMS) {
+        set_error("the learned min-sum takes QC codes (parameters per circulant)");
+        return LDPC_EUNSUPPORTED;
     }
     for (int i = 0; i < 4; ++i)
         if (o->reserved[i]) {
@@ -198,7 +204,98 @@ ldpc_status ldpc_code_destroy(ldpc_code c) {
     cudaFree(w.stage_i32);
     noms_free(c->noms);
     sim_free(c->sim);
+    cudaFree(c->sp_mem);
     delete c;
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_code_create_sparse(int32_t M, int32_t N, const int32_t *row_ptr, const int32_t *col_idx,
+                                    ldpc_code *out) {
+    if (!out || !row_ptr || !col_idx || M < 1 || N < 1) {
+        set_error("need out, row_ptr, col_idx, M >= 1 and N >= 1");
+        return LDPC_EINVAL;
+    }
+    *out = nullptr;
+    if (row_ptr[0] != 0) {
+        set_error("row_ptr[0] = %d, expected 0", row_ptr[0]);
+        return LDPC_EINVAL;
+    }
+    int dc_max = 0;
+    for (int m = 0; m < M; ++m) {
+        const int a = row_ptr[m], b = row_ptr[m + 1];
+        if (b - a < 1 || b - a > 32) {
+            set_error("row %d has degree %d outside [1, 32]", m, b - a);
+            return LDPC_EINVAL;
+        }
+        dc_max = std::max(dc_max, b - a);
+        for (int e = a; e < b; ++e) {
+            if (col_idx[e] < 0 || col_idx[e] >= N || (e > a && col_idx[e] <= col_idx[e - 1])) {
+                set_error("row %d: column indices must increase within [0, %d)", m, N);
+                return LDPC_EINVAL;
+            }
+        }
+    }
+    const long long E = row_ptr[M];
+    if (E * 32 >= (1ll << 31)) {
+        set_error("E = %lld edges: E * 32 must stay below 2^31", E);
+        return LDPC_EINVAL;
+    }
+    // each variable's edges (rows increase because edges are numbered row by row)
+    std::vector<int> cptr(N + 1, 0), cedge((size_t)E);
+    for (long long e = 0; e < E; ++e) ++cptr[col_idx[e] + 1];
+    int dv_max = 0;
+    for (int n = 0; n < N; ++n) {
+        dv_max = std::max(dv_max, cptr[n + 1]);
+        cptr[n + 1] += cptr[n];
+    }
+    if (dv_max > 8) {
+        set_error("a column has degree %d > 8", dv_max);
+        return LDPC_EINVAL;
+    }
+    {
+        std::vector<int> fill(cptr.begin(), cptr.end() - 1);
+        for (long long e = 0; e < E; ++e) cedge[(size_t)fill[col_idx[e]]++] = (int)e;
+    }
+    ldpc_code c = new (std::nothrow) ldpc_code_s();
+    if (!c) {
+        set_error("host allocation failed");
+        return LDPC_ENOMEM;
+    }
+    std::memset(&c->d, 0, sizeof(c->d));
+    c->d.N = N;
+    c->d.M = M;
+    c->d.E = (int)E;
+    c->d.dc_max = dc_max;
+    c->d.divM = fast_div((uint32_t)M);
+    c->d.divP = fast_div(1u);
+    c->d.divG = fast_div((uint32_t)((N + 3) / 4));
+    c->sparse = true;
+    c->rate = 1.0 - (double)M / (double)N;
+    const size_t words = (size_t)(M + 1) + (size_t)E + (size_t)(N + 1) + (size_t)E;
+    if (cudaGetDevice(&c->device) != cudaSuccess || cudaMalloc(&c->sp_mem, words * 4) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        set_error("device allocation of the index tables failed");
+        return LDPC_ENOMEM;
+    }
+    int *dm = (int *)c->sp_mem;
+    cudaError_t ce = cudaMemcpy(dm, row_ptr, (size_t)(M + 1) * 4, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(dm + M + 1, col_idx, (size_t)E * 4, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(dm + M + 1 + E, cptr.data(), (size_t)(N + 1) * 4, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpy(dm + M + 1 + E + N + 1, cedge.data(), (size_t)E * 4, cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+        cudaFree(c->sp_mem);
+        delete c;
+        return cuda_fail(ce, "cudaMemcpy(index tables)");
+    }
+    c->sp.rp = dm;
+    c->sp.col = dm + M + 1;
+    c->sp.cptr = dm + M + 1 + E;
+    c->sp.cedge = dm + M + 1 + E + N + 1;
+    c->sp.dc_max = dc_max;
+    c->sp.dv_max = dv_max;
+    *out = c;
     return LDPC_OK;
 }
 
@@ -292,6 +389,10 @@ ldpc_status ldpc_ber_sim(ldpc_code c, double ebn0_db, uint64_t seed, uint64_t fi
     if (!(c->rate > 0.0)) {
         set_error("design rate K/N = %g is not positive", c->rate);
         return LDPC_EINVAL;
+    }
+    if (c->sparse) {
+        set_error("ldpc_ber_sim takes QC codes; decode a general code with ldpc_channel + ldpc_decode");
+        return LDPC_EUNSUPPORTED;
     }
     ldpc_status st = check_opts(c, opts);
     if (st != LDPC_OK) return st;

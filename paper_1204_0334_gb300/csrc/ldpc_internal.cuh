@@ -71,8 +71,23 @@ struct DecodeWs {
 struct ldpc_noms_state;  // training state of the learned min-sum (noms.cu)
 struct ldpc_sim_state;   // frame slots of the continuous simulation (sim.cu)
 
+namespace ldpc {
+// index tables of a general sparse code (device memory): H in compressed-row form with
+// edges numbered row by row, and each variable's edges (compressed-column form)
+struct SparseTab {
+    const int *rp = nullptr;     // [M + 1] first edge of each row
+    const int *col = nullptr;    // [E] variable of each edge
+    const int *cptr = nullptr;   // [N + 1] first entry of each variable in cedge
+    const int *cedge = nullptr;  // [E] edges of each variable, in increasing row order
+    int dc_max = 0, dv_max = 0;  // largest row / column degree
+};
+}  // namespace ldpc
+
 struct ldpc_code_s {
-    ldpc::QcDesc d;
+    ldpc::QcDesc d;           // QC description; for a sparse code only N, M, E are set (J = 0)
+    bool sparse = false;
+    ldpc::SparseTab sp;       // sparse code: the index tables
+    void *sp_mem = nullptr;   // their device allocation
     ldpc_noms_state *noms = nullptr;
     ldpc_sim_state *sim = nullptr;
     int device = 0;
@@ -123,6 +138,13 @@ ldpc_status qc_vn_pipe(ldpc_code c, const ldpc_decode_opts &o, bool stop, bool p
                        cudaStream_t s);
 // packages with a running frame
 ldpc_status qc_compact(ldpc_code c, int P, int V, cudaStream_t s);
+// general (index-table) codes (qc_pipe.cu, sparse.cu)
+ldpc_status qc_cn_pipe_sparse(ldpc_code c, const ldpc_decode_opts &o, cudaStream_t s);
+ldpc_status qc_vn_pipe_sparse(ldpc_code c, const ldpc_decode_opts &o, bool stop, bool post, int it, int par,
+                              cudaStream_t s);
+ldpc_status sparse_decode_device(ldpc_code c, int gamma, const ldpc_decode_opts &o, bool want_post, cudaStream_t s);
+ldpc_status qc_init_flags(ldpc_code c, int gamma, int V, cudaStream_t s);
+ldpc_status qc_finish_frames(ldpc_code c, int gamma, const ldpc_decode_opts &o, cudaStream_t s);
 // continuous simulation (sim.cu)
 void sim_free(ldpc_sim_state *st);
 ldpc_status qc_ber_sim_refill(ldpc_code c, double sigma, uint64_t seed, uint64_t first_frame, int64_t max_frames,

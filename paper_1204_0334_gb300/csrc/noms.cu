@@ -478,6 +478,10 @@ ldpc_status ldpc_noms_forward(ldpc_code c, const float *llr, int32_t B, int32_t 
         set_error("ldpc_noms_forward takes device buffers");
         return LDPC_EINVAL;
     }
+    if (c->sparse) {
+        set_error("the learned min-sum takes QC codes (parameters per circulant)");
+        return LDPC_EUNSUPPORTED;
+    }
     if (!c->noms) {
         c->noms = new (std::nothrow) ldpc_noms_state();
         if (!c->noms) {

@@ -550,6 +550,7 @@ ldpc_status qc_syndrome(ldpc_code c, int P, int V, int word, cudaStream_t s) {
 }
 
 ldpc_status qc_decode_device(ldpc_code c, int gamma, const ldpc_decode_opts &o, bool want_post, cudaStream_t s) {
+    if (c->sparse) return sparse_decode_device(c, gamma, o, want_post, s);
     const int V = words_per_lane(o), W = 32 * V;
     const int P = (gamma + W - 1) / W;
     init_flags_kernel<<<(P + 127) / 128, 128, 0, s>>>(c->ws.flags, P, V, gamma);
@@ -608,6 +609,16 @@ ldpc_status qc_init_flags(ldpc_code c, int gamma, int V, cudaStream_t s) {
 }
 
 // syndrome of the last decisions, iteration counts and ok flags of every frame
+// iteration counts and ok flags of every frame from the flag words (the fin words must hold
+// the syndrome of the last decisions)
+ldpc_status qc_finish_frames(ldpc_code c, int gamma, const ldpc_decode_opts &o, cudaStream_t s) {
+    finish_frames_kernel<<<(gamma + 255) / 256, 256, 0, s>>>(c->ws.flags, c->ws.iters, c->ws.iters + c->ws.gamma_cap,
+                                                             gamma, words_per_lane(o), o.max_iter);
+    count_launch();
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
 ldpc_status qc_finish(ldpc_code c, int gamma, const ldpc_decode_opts &o, cudaStream_t s) {
     const int V = words_per_lane(o);
     const int P = (gamma + 32 * V - 1) / (32 * V);

@@ -43,11 +43,14 @@ struct CnStage {
 // stay in registers (lane l holds edge l's, broadcast with a shuffle), so the
 // ring holds only message packages and three blocks of eight warps fit on an SM.
 // ---------------------------------------------------------------------------
-template <int DCMAX, int V, bool XF, int MODE, bool REG>
+// SPARSE: a general code (index tables; edges of a row are consecutive)
+template <int DCMAX, int V, bool XF, int MODE, bool REG, bool SPARSE = false>
 __global__ void __launch_bounds__(kWarps * 32)
 cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__restrict__ flags,
                const uint32_t *__restrict__ fresh, const int *__restrict__ act, float clip,
-               const float *__restrict__ nparams, const int *__restrict__ ages, int T) {
+               const float *__restrict__ nparams, const int *__restrict__ ages, int T, SparseTab tab) {
+    static_assert(!(SPARSE && (REG || MODE == kModeNOMS)), "general codes: irregular rows, no learned min-sum");
+    const int LB = SPARSE ? DCMAX : d.L;  // bound of the edge index within a row
     using St = CnStage<DCMAX>;
     // learned min-sum with frames at different iterations (continuous simulation): each lane's
     // frames pick their own parameter row from their iteration counts, staged after the packages
@@ -87,10 +90,22 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
             const int a = (int)fdiv((uint32_t)it, d.divM);
             const int m = it - a * d.M;
             const int pk = __ldg(list + a);
-            const int j = (int)fdiv((uint32_t)m, d.divP), r = m - j * d.p;
             const uint32_t *gmsg = msg + (size_t)pk * d.E * 32;
             uint32_t *dst = ring + slot * RW;
             const int g = lane >> 3, sub = lane & 7;
+            if constexpr (SPARSE) {
+                const int e0 = __ldg(tab.rp + m), deg = __ldg(tab.rp + m + 1) - e0;
+#pragma unroll
+                for (int q = 0; q < DCMAX / 4; ++q) {
+                    const int l = 4 * q + g;
+                    if (l < deg) cp_async16(dst + l * 32 + sub * 4, gmsg + (size_t)(e0 + l) * 32 + sub * 4);
+                }
+                if (lane < deg) mine = e0 + lane;
+                if (lane < V) cp_async4(dst + St::FL + lane, flags + (size_t)pk * 5 * V + lane);
+                cp_async_commit();
+                return mine;
+            }
+            const int j = (int)fdiv((uint32_t)m, d.divP), r = m - j * d.p;
             if (MODE == kModeNOMS && ages) {
 #pragma unroll
                 for (int v = 0; v < V; ++v)
@@ -158,7 +173,7 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
             for (int l = 0; l < DCMAX; ++l) {
 #pragma unroll
                 for (int v = 0; v < V; ++v) xs[l][v] = 0.0f;
-                if (REG || (l < d.L && __shfl_sync(0xffffffffu, myoff, l) >= 0)) {
+                if (REG || (l < LB && __shfl_sync(0xffffffffu, myoff, l) >= 0)) {
                     float x[V];
                     Lane<V>::unpack(S[l * 32 + lane], x);
 #pragma unroll
@@ -223,7 +238,7 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
             for (int l = 0; l < DCMAX; ++l) {
 #pragma unroll
                 for (int v = 0; v < V; ++v) ab[l][v] = INFINITY;
-                if (REG || l < d.L) {
+                if (REG || l < LB) {
                     const int o = __shfl_sync(0xffffffffu, myoff, l);
                     if (REG || o >= 0) {
                         float x[V];
@@ -265,7 +280,7 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
             for (int l = 0; l < DCMAX; ++l) {
                 ab[l] = 0u;
                 sg[l] = 0u;
-                if (REG || l < d.L) {
+                if (REG || l < LB) {
                     const int o = __shfl_sync(0xffffffffu, myoff, l);
                     if (REG || o >= 0) {
                         const uint32_t x = S[l * 32 + lane];
@@ -310,11 +325,14 @@ struct VnStage {
 };
 
 // EVEN: N is a multiple of kNV (every item has kNV variables)
-template <int JMAX, int V, bool STOP, bool POST, bool XF, bool MS, bool REG, bool REFILL = false, bool EVEN = false>
+// SPARSE: a general code (each variable's edges from index tables)
+template <int JMAX, int V, bool STOP, bool POST, bool XF, bool MS, bool REG, bool REFILL = false, bool EVEN = false,
+          bool SPARSE = false>
 __global__ void __launch_bounds__(kWarps * 32)
 vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict__ mu, uint32_t *__restrict__ hw,
                uint32_t *__restrict__ flags, float *__restrict__ post, int32_t *__restrict__ iters,
-               const int *__restrict__ act, float clip, float lsb, int it, int par, RefillArgs rf) {
+               const int *__restrict__ act, float clip, float lsb, int it, int par, RefillArgs rf, SparseTab tab) {
+    static_assert(!(SPARSE && (REG || REFILL)), "general codes: irregular columns, batch decoding");
     using St = VnStage<JMAX, V, STOP, MS>;
     constexpr int W = 32 * V;
     static_assert(kNV == 4, "items of 4 variables: 16-byte channel rows, 4-byte lane words");
@@ -375,21 +393,39 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
                                        gmu + (size_t)n * St::MUW + h * 32 + sub * 4);
                 }
             }
-            // edge packages: kNV * JMAX of them
+            if constexpr (SPARSE) {
+                // each variable's edges from the tables: lane t < kNV * JMAX looks up edge t % JMAX
+                // of variable t / JMAX; the lane groups copy the packages
+                if (lane < kNV * JMAX) {
+                    const int i = lane / JMAX, jj = lane - i * JMAX;
+                    const int n = n0 + i;
+                    if (n < d.N) {
+                        const int c0 = __ldg(tab.cptr + n), deg = __ldg(tab.cptr + n + 1) - c0;
+                        if (jj < deg) mine = __ldg(tab.cedge + c0 + jj);
+                    }
+                }
 #pragma unroll
-            for (int t0 = 0; t0 < kNV * JMAX; t0 += 4) {
-                const int t = t0 + grp;
-                const int i = t / JMAX, jj = t - i * JMAX;
-                const int n = n0 + i;
-                int l = l0, k = k0 + i;
-                if (k >= d.p) k -= d.p, ++l;
-                if (((kNV * JMAX) % 4 == 0 || t < kNV * JMAX) && (EVEN || n < d.N) && (REG || jj < d.J)) {
-                    if (REG || s_sh[jj * d.L + l] >= 0)
-                        cp_async16(dst + St::AL + (i * JMAX + jj) * 32 + sub * 4,
-                                   gmsg + (size_t)(s_eo[jj * d.L + l] + k) * 32 + sub * 4);
+                for (int t0 = 0; t0 < kNV * JMAX; t0 += 4) {
+                    const int e = __shfl_sync(0xffffffffu, mine, t0 + grp);
+                    if (e >= 0) cp_async16(dst + St::AL + (t0 + grp) * 32 + sub * 4, gmsg + (size_t)e * 32 + sub * 4);
+                }
+            } else {
+                // edge packages: kNV * JMAX of them
+#pragma unroll
+                for (int t0 = 0; t0 < kNV * JMAX; t0 += 4) {
+                    const int t = t0 + grp;
+                    const int i = t / JMAX, jj = t - i * JMAX;
+                    const int n = n0 + i;
+                    int l = l0, k = k0 + i;
+                    if (k >= d.p) k -= d.p, ++l;
+                    if (((kNV * JMAX) % 4 == 0 || t < kNV * JMAX) && (EVEN || n < d.N) && (REG || jj < d.J)) {
+                        if (REG || s_sh[jj * d.L + l] >= 0)
+                            cp_async16(dst + St::AL + (i * JMAX + jj) * 32 + sub * 4,
+                                       gmsg + (size_t)(s_eo[jj * d.L + l] + k) * 32 + sub * 4);
+                    }
                 }
             }
-            if (lane < kNV * JMAX) {
+            if (!SPARSE && lane < kNV * JMAX) {
                 const int i = lane / JMAX, jj = lane - i * JMAX;
                 int l = l0, k = k0 + i;
                 if (k >= d.p) k -= d.p, ++l;
@@ -668,7 +704,7 @@ static void launch_cn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, const
                       : ages ? o.noms_params
                              : o.noms_params + (size_t)(it - 1) * c->d.J * c->d.L * 2;
     k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, c->ws.flags, fresh, c->ws.act, o.clip, np,
-                                        ages, o.max_iter);
+                                        ages, o.max_iter, SparseTab());
 }
 
 template <int DCMAX, bool REG>
@@ -713,7 +749,7 @@ static void launch_vn_pipe(ldpc_code c, const ldpc_decode_opts &o, int it, int p
     const int blocks = persistent_blocks(k, smem);
     k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, (uint32_t *)c->ws.mu, c->ws.hw, c->ws.flags,
                                         c->ws.post, c->ws.iters, c->ws.act, o.clip, ldexpf(1.0f, -o.frac_bits), it,
-                                        par, RefillArgs{});
+                                        par, RefillArgs{}, SparseTab());
 }
 
 template <int JMAX, bool STOP, bool POST, bool REG>
@@ -771,7 +807,8 @@ static void launch_vn_refill(ldpc_code c, const ldpc_decode_opts &o, const Refil
     const size_t smem = (size_t)kWarps * kVnStages * VnStage<JMAX, V, false, MS>::WORDS * 4;
     const int blocks = persistent_blocks(k, smem);
     k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, (uint32_t *)c->ws.mu, c->ws.hw, c->ws.flags,
-                                        nullptr, nullptr, c->ws.act, o.clip, ldexpf(1.0f, -o.frac_bits), 0, 0, rf);
+                                        nullptr, nullptr, c->ws.act, o.clip, ldexpf(1.0f, -o.frac_bits), 0, 0, rf,
+                                        SparseTab());
 }
 
 template <int JMAX, bool REG>
@@ -791,6 +828,76 @@ ldpc_status qc_vn_refill(ldpc_code c, const ldpc_decode_opts &o, const RefillArg
     else if (full && d.J == 3) vn_refill_dispatch<3, true>(c, o, rf, s);
     else if (d.J <= 4) vn_refill_dispatch<4, false>(c, o, rf, s);
     else vn_refill_dispatch<8, false>(c, o, rf, s);
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
+}  // namespace ldpc
+
+namespace ldpc {
+
+// ---------------------------------------------------------------------------
+// general (index-table) codes: the same passes with table-driven copy stages
+// ---------------------------------------------------------------------------
+template <int DCMAX, int V, bool XF, int MODE>
+static void launch_cn_sparse(ldpc_code c, const ldpc_decode_opts &o, cudaStream_t s) {
+    auto k = cn_pipe_kernel<DCMAX, V, XF, MODE, false, true>;
+    const size_t smem = (size_t)kWarps * kCnStages * CnStage<DCMAX>::WORDS * 4;
+    const int blocks = persistent_blocks(k, smem);
+    k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, c->ws.flags, nullptr, c->ws.act, o.clip,
+                                        nullptr, nullptr, 0, c->sp);
+}
+
+template <int DCMAX>
+static void cn_sparse_dispatch(ldpc_code c, const ldpc_decode_opts &o, cudaStream_t s) {
+    if (o.algo == LDPC_ALGO_MS) launch_cn_sparse<DCMAX, 4, false, kModeMS>(c, o, s);
+    else if (o.msg == LDPC_MSG_F16) launch_cn_sparse<DCMAX, 2, true, kModeSP>(c, o, s);
+    else launch_cn_sparse<DCMAX, 1, true, kModeSP>(c, o, s);
+}
+
+ldpc_status qc_cn_pipe_sparse(ldpc_code c, const ldpc_decode_opts &o, cudaStream_t s) {
+    const int dc = c->sp.dc_max;
+    if (dc <= 8) cn_sparse_dispatch<8>(c, o, s);
+    else if (dc <= 16) cn_sparse_dispatch<16>(c, o, s);
+    else if (dc <= 24) cn_sparse_dispatch<24>(c, o, s);
+    else cn_sparse_dispatch<32>(c, o, s);
+    LDPC_CUDA_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
+template <int JMAX, int V, bool STOP, bool POST, bool XF, bool MS>
+static void launch_vn_sparse(ldpc_code c, const ldpc_decode_opts &o, int it, int par, cudaStream_t s) {
+    auto k = vn_pipe_kernel<JMAX, V, STOP, POST, XF, MS, false, false, false, true>;
+    const size_t smem = (size_t)kWarps * kVnStages * VnStage<JMAX, V, STOP, MS>::WORDS * 4;
+    const int blocks = persistent_blocks(k, smem);
+    k<<<blocks, kWarps * 32, smem, s>>>(c->d, (uint32_t *)c->ws.msg, (uint32_t *)c->ws.mu, c->ws.hw, c->ws.flags,
+                                        c->ws.post, c->ws.iters, c->ws.act, o.clip, ldexpf(1.0f, -o.frac_bits), it,
+                                        par, RefillArgs{}, c->sp);
+}
+
+template <int JMAX, bool STOP, bool POST>
+static void vn_sparse_dispatch(ldpc_code c, const ldpc_decode_opts &o, int it, int par, cudaStream_t s) {
+    if (o.algo == LDPC_ALGO_MS) launch_vn_sparse<JMAX, 4, STOP, POST, false, true>(c, o, it, par, s);
+    else if (o.msg == LDPC_MSG_F16) launch_vn_sparse<JMAX, 2, STOP, POST, true, false>(c, o, it, par, s);
+    else launch_vn_sparse<JMAX, 1, STOP, POST, true, false>(c, o, it, par, s);
+}
+
+template <int JMAX>
+static void vn_sparse_dispatch2(ldpc_code c, const ldpc_decode_opts &o, bool stop, bool post, int it, int par,
+                                cudaStream_t s) {
+    if (stop) {
+        if (post) vn_sparse_dispatch<JMAX, true, true>(c, o, it, par, s);
+        else vn_sparse_dispatch<JMAX, true, false>(c, o, it, par, s);
+    } else {
+        if (post) vn_sparse_dispatch<JMAX, false, true>(c, o, it, par, s);
+        else vn_sparse_dispatch<JMAX, false, false>(c, o, it, par, s);
+    }
+}
+
+ldpc_status qc_vn_pipe_sparse(ldpc_code c, const ldpc_decode_opts &o, bool stop, bool post, int it, int par,
+                              cudaStream_t s) {
+    if (c->sp.dv_max <= 4) vn_sparse_dispatch2<4>(c, o, stop, post, it, par, s);
+    else vn_sparse_dispatch2<8>(c, o, stop, post, it, par, s);
     LDPC_CUDA_TRY(cudaGetLastError());
     return LDPC_OK;
 }

@@ -91,3 +91,35 @@ def mixed_codes(ncodes: int, seed: int, p_min: int = 32, p_max: int = 765, n_min
         p = max(min(p, n_max // L), -(-n_min // L))
         out.append((J, L, p, qc_shifts(J, L, p, seed * 1000 + i)))
     return out
+
+
+def random_ldpc(N: int, M: int, seed: int, var_degrees=(2, 3, 3, 4, 6), max_row: int = 32):
+    """A random irregular LDPC code (inputs only): variable degrees drawn from var_degrees, edges
+    matched to checks by the configuration model with check degrees as equal as possible, repeated
+    edges and over-full rows redrawn.  Returns (row_ptr [M+1], col_idx [E]) of H in compressed-row
+    form, columns increasing within each row; every check gets at least two variables."""
+    rng = np.random.default_rng(seed)
+    dv = rng.choice(np.asarray(var_degrees), size=N)
+    for _ in range(100):
+        rows = [set() for _ in range(M)]
+        ok = True
+        order = rng.permutation(N)
+        for n in order:
+            # the least-loaded checks first, random among equals
+            load = np.array([len(r) for r in rows]) + rng.random(M)
+            for m in np.argsort(load)[: int(dv[n])]:
+                if len(rows[m]) >= max_row:
+                    ok = False
+                    break
+                rows[m].add(int(n))
+            if not ok:
+                break
+        if ok and all(len(r) >= 2 for r in rows):
+            break
+    row_ptr = np.zeros(M + 1, dtype=np.int32)
+    cols = []
+    for m, r in enumerate(rows):
+        c = sorted(r)
+        cols += c
+        row_ptr[m + 1] = row_ptr[m] + len(c)
+    return row_ptr, np.asarray(cols, dtype=np.int32)

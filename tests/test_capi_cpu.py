@@ -80,3 +80,25 @@ def test_ldpccc_rejects_sizes_beyond_32_bit_indexing(lib):
     with pytest.raises(pkg.LdpcError) as e:
         pkg.ldpccc_create(shifts, 64, 0, 32)  # no processors
     assert e.value.status == 1
+
+
+def test_sparse_code_validation_without_a_device(lib):
+    """Malformed compressed-row input is refused before any device memory is touched."""
+    import paper_1204_0334_gb300 as pkg
+
+    pkg.lib()
+    cases = [([1, 2], [0], 4),                  # row_ptr[0] != 0
+             ([0, 2, 3], [1, 0, 2], 4),         # columns not increasing within a row
+             ([0, 2, 4], [0, 1, 2, 9], 4),      # column out of range
+             ([0, 2, 2], [0, 1], 4),            # empty row
+             ([0, 33], list(range(33)), 40)]    # row degree above 32
+    for rp, col, N in cases:
+        with pytest.raises(pkg.LdpcError) as e:
+            pkg.ldpc_code_create_sparse(rp, col, N)
+        assert e.value.status == 1, (rp, col)
+    # a column of degree 9
+    rp = [2 * m for m in range(10)]
+    col = [c for m in range(9) for c in (0, m + 1)]
+    with pytest.raises(pkg.LdpcError) as e:
+        pkg.ldpc_code_create_sparse(rp, col, 12)
+    assert e.value.status == 1 and "degree" in str(e.value)
