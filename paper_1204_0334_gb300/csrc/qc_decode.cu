@@ -25,31 +25,29 @@
 namespace ldpc {
 
 // ---------------------------------------------------------------------------
-// Check-node (horizontal) step, sum-product.  One warp = one check row of one
-// package; lane = V frames.  FIRST: the incoming messages are beta = mu (the
-// initialization of Algorithm 1 folded into the first read).  SYN: also XOR the
-// hard-decision words of the row's variables (the decisions of the previous
-// iteration) and flag frames whose check is violated.
+// First check-node (horizontal) step, sum-product.  One warp = one check row of
+// one package; lane = V frames.  The incoming messages are beta = mu: the
+// initialization of Algorithm 1 folded into the first read, so no beta is ever
+// written for iteration 0.  Later iterations run the pipelined pass (qc_pipe.cu).
 // Sums of phi over the other edges use prefix + suffix sums (the forward-
 // backward computation of Sec. IV-A), never "total minus own": that
 // subtraction loses the small terms when one input is unreliable.
 // ---------------------------------------------------------------------------
-template <int DCMAX, int V, bool FIRST, bool SYN, bool XF, bool NOMS>
+template <int DCMAX, int V, bool NOMS>
 __global__ void __launch_bounds__(kWarps * 32)
-cn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict__ mu,
-             const uint32_t *__restrict__ hw, uint32_t *__restrict__ flags, float clip, int par,
-             const float *__restrict__ nparams) {
+cn_sp_first_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict__ mu,
+                   const uint32_t *__restrict__ flags, float clip, const float *__restrict__ nparams) {
     constexpr int W = 32 * V;
     const int lane = threadIdx.x & 31;
     const int m = blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int pk = blockIdx.y;
     if (m >= d.M) return;
-    PkgFlags F{flags + (size_t)pk * 5 * V, V};
+    const uint32_t *done = flags + (size_t)pk * 5 * V;
     bool lane_on = false, warp_on = false;
     uint32_t act[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        act[v] = ~F.done()[v];
+        act[v] = ~done[v];
         warp_on |= act[v] != 0;
         lane_on |= (act[v] >> lane) & 1u;
     }
@@ -62,15 +60,12 @@ cn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict
     // package-relative bases; offsets below stay in 32 bits (E * 32 < 2^31)
     uint32_t *pmsg = msg + (size_t)pk * d.E * 32 + lane;
     const float *pmu = mu + (size_t)pk * d.N * W + lane * V;
-    const uint32_t *phw = hw + (size_t)pk * d.N * V;
     float ph[DCMAX][V];
     uint32_t neg[V];
-    uint32_t syn[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) neg[v] = 0u, syn[v] = 0u;
+    for (int v = 0; v < V; ++v) neg[v] = 0u;
 
-    // incoming messages: beta (FIRST: beta = mu) or, with XF, the stored
-    // transform sign(beta) * phi(|beta|) written by the variable pass
+    // incoming messages beta = mu
 #pragma unroll
     for (int l = 0; l < DCMAX; ++l) {
         const bool on = l < d.L && sh[l] >= 0;
@@ -81,28 +76,13 @@ cn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict
             if (k >= d.p) k -= d.p;
             const int n = l * d.p + k;
             float x[V];
-            if (FIRST) {
 #pragma unroll
-                for (int v = 0; v < V; ++v) x[v] = pmu[n * W + v];
-            } else {
-                Lane<V>::unpack(pmsg[(eo[l] + k) * 32], x);
-            }
+            for (int v = 0; v < V; ++v) x[v] = pmu[n * W + v];
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                ph[l][v] = (NOMS || (XF && !FIRST)) ? fabsf(x[v]) : phi_f(fabsf(x[v]));
+                ph[l][v] = NOMS ? fabsf(x[v]) : phi_f(fabsf(x[v]));
                 neg[v] |= (x[v] < 0.0f ? 1u : 0u) << l;
             }
-            if (SYN) {
-#pragma unroll
-                for (int v = 0; v < V; ++v) syn[v] ^= phw[n * V + v];
-            }
-        }
-    }
-    if (SYN && lane == 0) {
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const uint32_t bad = syn[v] & act[v];
-            if (bad) atomicOr(F.unsat(par) + v, bad);
         }
     }
     uint32_t par_all[V];
@@ -184,23 +164,24 @@ cn_sp_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__restrict
 // evaluated with the byte-SIMD video instructions.  Check update:
 // |alpha_e| = min over the other edges = (|beta_e| == min1) ? min2 : min1 --
 // ties give min2 == min1, so no arg-min is needed; the sign is the parity of
-// the other signs (sign(0) = +).  Empty extrinsic set: 127.
+// the other signs (sign(0) = +).  Empty extrinsic set: 127.  First iteration
+// only (beta = mu); later iterations run the pipelined pass (qc_pipe.cu).
 // ---------------------------------------------------------------------------
-template <int DCMAX, bool FIRST, bool SYN>
+template <int DCMAX>
 __global__ void __launch_bounds__(kWarps * 32)
-cn_ms_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__restrict__ mu,
-             const uint32_t *__restrict__ hw, uint32_t *__restrict__ flags, int par) {
+cn_ms_first_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__restrict__ mu,
+                   const uint32_t *__restrict__ flags) {
     constexpr int V = 4;
     const int lane = threadIdx.x & 31;
     const int m = blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int pk = blockIdx.y;
     if (m >= d.M) return;
-    PkgFlags F{flags + (size_t)pk * 5 * V, V};
+    const uint32_t *done = flags + (size_t)pk * 5 * V;
     bool lane_on = false, warp_on = false;
     uint32_t act[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        act[v] = ~F.done()[v];
+        act[v] = ~done[v];
         warp_on |= act[v] != 0;
         lane_on |= (act[v] >> lane) & 1u;
     }
@@ -211,7 +192,6 @@ cn_ms_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__restr
     const int *eo = d.eoff + j * d.L;
     uint32_t ab[DCMAX], sg[DCMAX];
     uint32_t min1 = 0x7f7f7f7fu, min2 = 0x7f7f7f7fu, sgn = 0u;
-    uint32_t syn[V] = {0u, 0u, 0u, 0u};
 #pragma unroll
     for (int l = 0; l < DCMAX; ++l) {
         const bool on = l < d.L && sh[l] >= 0;
@@ -221,28 +201,13 @@ cn_ms_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__restr
             int k = r + sh[l];
             if (k >= d.p) k -= d.p;
             uint32_t x = 0u;
-            if (lane_on) {
-                x = FIRST ? mu[((size_t)pk * d.N + (size_t)l * d.p + k) * 32 + lane]
-                          : msg[((size_t)pk * d.E + eo[l] + k) * 32 + lane];
-            }
+            if (lane_on) x = mu[((size_t)pk * d.N + (size_t)l * d.p + k) * 32 + lane];
             const uint32_t a = __vabsss4(x);
             sg[l] = x & 0x80808080u;
             ab[l] = a;
             sgn ^= sg[l];
             min2 = __vminu4(min2, __vmaxu4(min1, a));
             min1 = __vminu4(min1, a);
-            if (SYN) {
-                const uint32_t *h = hw + ((size_t)pk * d.N + (size_t)l * d.p + k) * V;
-#pragma unroll
-                for (int v = 0; v < V; ++v) syn[v] ^= h[v];
-            }
-        }
-    }
-    if (SYN && lane == 0) {
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const uint32_t bad = syn[v] & act[v];
-            if (bad) atomicOr(F.unsat(par) + v, bad);
         }
     }
     if (!lane_on) return;
@@ -519,20 +484,19 @@ static void launch_cn_first(ldpc_code c, int P, const ldpc_decode_opts &o, cudaS
     dim3 grd((c->d.M + kWarps - 1) / kWarps, P);
     // F32 sum-product storage carries sign(beta) * phi(|beta|) between the passes; F16 and
     // NOMS carry beta (FP16's range cannot hold phi of reliable messages)
-    cn_sp_kernel<DCMAX, V, true, false, V == 1 && !NOMS, NOMS><<<grd, kWarps * 32, 0, s>>>(
-        c->d, (uint32_t *)c->ws.msg, (const float *)c->ws.mu, c->ws.hw, c->ws.flags, o.clip, 0, o.noms_params);
+    cn_sp_first_kernel<DCMAX, V, NOMS><<<grd, kWarps * 32, 0, s>>>(
+        c->d, (uint32_t *)c->ws.msg, (const float *)c->ws.mu, c->ws.flags, o.clip, o.noms_params);
 }
-template <int DCMAX, bool FIRST, bool SYN>
-static void launch_cn_ms(ldpc_code c, int P, int par, cudaStream_t s) {
+template <int DCMAX>
+static void launch_cn_ms_first(ldpc_code c, int P, cudaStream_t s) {
     dim3 grd((c->d.M + kWarps - 1) / kWarps, P);
-    cn_ms_kernel<DCMAX, FIRST, SYN><<<grd, kWarps * 32, 0, s>>>(c->d, (uint32_t *)c->ws.msg,
-                                                               (const uint32_t *)c->ws.mu, c->ws.hw, c->ws.flags,
-                                                               par);
+    cn_ms_first_kernel<DCMAX><<<grd, kWarps * 32, 0, s>>>(c->d, (uint32_t *)c->ws.msg,
+                                                         (const uint32_t *)c->ws.mu, c->ws.flags);
 }
 
 template <int DCMAX>
 static void cn_first_dispatch(ldpc_code c, int P, const ldpc_decode_opts &o, cudaStream_t s) {
-    if (o.algo == LDPC_ALGO_MS) launch_cn_ms<DCMAX, true, false>(c, P, 0, s);
+    if (o.algo == LDPC_ALGO_MS) launch_cn_ms_first<DCMAX>(c, P, s);
     else if (o.algo == LDPC_ALGO_NOMS) {
         if (o.msg == LDPC_MSG_F16) launch_cn_first<DCMAX, 2, true>(c, P, o, s);
         else launch_cn_first<DCMAX, 1, true>(c, P, o, s);
