@@ -54,6 +54,8 @@ def _load():
         lib.or_philox4x32_10.restype = None
         lib.or_channel_awgn.argtypes = [u64, u64, i32, i32, f64, u32, P, P]
         lib.or_channel_awgn.restype = None
+        lib.or_channel_awgn_cw.argtypes = [u64, u64, i32, i32, f64, u32, P, P, P]
+        lib.or_channel_awgn_cw.restype = None
         lib.or_variable_edges.argtypes = [i32, i32, P, P, P, P]
         lib.or_sp_decode.argtypes = [i32, i32, P, P, i32, P, i32, i32, f64, i32, P, P, P, P, i32]
         lib.or_ms_decode.argtypes = [i32, i32, P, P, i32, P, i32, i32, i32, P, P, P, P, i32]
@@ -187,13 +189,120 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 
 def channel_awgn(seed: int, first_frame: int, nfr: int, N: int, sigma: float, tag: int = 0,
-                 return_g: bool = False):
-    """mu[nfr][N] (float32) of the all-zero codeword over BPSK/AWGN."""
+                 return_g: bool = False, cw=None):
+    """mu[nfr][N] (float32) over BPSK/AWGN: the all-zero codeword, or cw[nfr][N] (0/1) when given."""
     lib = _load()
     mu = np.zeros((nfr, N), dtype=np.float32)
     g = np.zeros((nfr, N), dtype=np.float64) if return_g else None
-    lib.or_channel_awgn(seed, first_frame, nfr, N, sigma, tag, _p(mu), _p(g) if return_g else None)
+    if cw is None:
+        lib.or_channel_awgn(seed, first_frame, nfr, N, sigma, tag, _p(mu), _p(g) if return_g else None)
+    else:
+        c = np.ascontiguousarray(cw, dtype=np.uint8)
+        assert c.shape == (nfr, N)
+        lib.or_channel_awgn_cw(seed, first_frame, nfr, N, sigma, tag, _p(c), _p(mu), _p(g) if return_g else None)
     return (mu, g) if return_g else mu
+
+
+# --------------------------------------------------------------------------
+# Systematic encoding (the transmitted codewords of Sec. V)
+# --------------------------------------------------------------------------
+def _columns_as_ints(H) -> tuple[list[int], int, int]:
+    """Column n of H as the integer sum over rows m with H[m, n] = 1 of 2^m."""
+    import scipy.sparse as sp
+
+    Hc = sp.csc_matrix(H)
+    Hc.sort_indices()
+    M, N = Hc.shape
+    cols = []
+    for n in range(N):
+        v = 0
+        for m, val in zip(Hc.indices[Hc.indptr[n]:Hc.indptr[n + 1]], Hc.data[Hc.indptr[n]:Hc.indptr[n + 1]]):
+            if int(val) & 1:
+                v ^= 1 << int(m)
+        cols.append(v)
+    return cols, M, N
+
+
+class Encoder:
+    """Systematic encoder of the code {c : H c = 0 over GF(2)}.
+
+    Information set (a definition, not a search heuristic): scanning columns
+    from n = N - 1 down to 0, column n is a PARITY position when it is not in
+    the GF(2) span of the columns to its right, and an INFORMATION position
+    otherwise.  The parity columns form a basis of H's column space, so
+    k = N - rank(H) and, for every u in {0,1}^k, exactly one codeword c has
+    c[info[j]] = u[j] (info in increasing order).
+
+    Built by inserting the columns, right to left, into a GF(2) basis kept by
+    leading row bit; each basis vector remembers which parity columns it is
+    the sum of (only with ``track`` = True: needed to encode, not for the
+    information set).
+    """
+
+    def __init__(self, H, track: bool = True):
+        self.cols, self.M, self.N = _columns_as_ints(H)
+        self.track = track
+        self.basis: dict[int, tuple[int, int]] = {}
+        parity = []
+        for n in range(self.N - 1, -1, -1):
+            v, comb = self.cols[n], (1 << n) if track else 0
+            while v:
+                lead = v.bit_length() - 1
+                if lead not in self.basis:
+                    break
+                bv, bc = self.basis[lead]
+                v ^= bv
+                comb ^= bc
+            if v:
+                self.basis[v.bit_length() - 1] = (v, comb)
+                parity.append(n)
+        self.parity = np.array(sorted(parity), dtype=np.int64)
+        is_par = np.zeros(self.N, dtype=bool)
+        is_par[self.parity] = True
+        self.info = np.nonzero(~is_par)[0].astype(np.int64)
+        self.k = len(self.info)
+        self.rank = len(self.parity)
+
+    def encode(self, u) -> np.ndarray:
+        """c[nfr][N] (uint8) for information bits u[nfr][k]: c[info] = u and H c = 0."""
+        assert self.track, "built with track=False"
+        u = np.atleast_2d(np.asarray(u, dtype=np.uint8))
+        out = np.zeros((u.shape[0], self.N), dtype=np.uint8)
+        for f in range(u.shape[0]):
+            s = 0  # syndrome of the information part
+            for j in np.nonzero(u[f] & 1)[0]:
+                s ^= self.cols[int(self.info[j])]
+            # s lies in the span of the parity columns: express it in the basis
+            comb = 0
+            while s:
+                bv, bc = self.basis[s.bit_length() - 1]
+                s ^= bv
+                comb ^= bc
+            out[f, self.info] = u[f] & 1
+            n = 0
+            while comb:
+                if comb & 1:
+                    out[f, n] = 1
+                comb >>= 1
+                n += 1
+        return out
+
+
+def info_bits(seed: int, first_frame: int, nfr: int, k: int) -> np.ndarray:
+    """u[nfr][k] (uint8): information bit j of frame F is bit j mod 32 of word
+    (j / 32) mod 4 of Philox4x32-10 at counter (j / 128, F_lo, F_hi, 1) under key
+    (seed_lo, seed_hi) -- the channel's counters carry 0 in the last word."""
+    key = np.array([seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF], dtype=np.uint32)
+    u = np.zeros((nfr, k), dtype=np.uint8)
+    for f in range(nfr):
+        F = first_frame + f
+        for q in range((k + 127) // 128):
+            w = philox4x32_10([q, F & 0xFFFFFFFF, (F >> 32) & 0xFFFFFFFF, 1], key)
+            # bit j of the 128 = bit j mod 32 of word j / 32 (little-endian bytes, LSB first)
+            bits = np.unpackbits(w.astype("<u4").view(np.uint8), bitorder="little")
+            n = min(k, 128 * q + 128) - 128 * q
+            u[f, 128 * q:128 * q + n] = bits[:n]
+    return u
 
 
 # --------------------------------------------------------------------------

@@ -15,8 +15,8 @@
  *
  * Contents
  *   or_philox4x32_10   counter-based generator (Salmon et al., SC'11)
- *   or_channel_awgn    BPSK over AWGN, all-zero codeword, channel LLR
- *                      (Sec. II-B: x = 1 - 2c, y = x + g, mu = 2y/sigma^2)
+ *   or_channel_awgn    BPSK over AWGN, channel LLR (Sec. II-B: x = 1 - 2c,
+ *   or_channel_awgn_cw y = x + g, mu = 2y/sigma^2), all-zero or given codeword
  *   or_sp_decode       sum-product BP, Algorithm 1 (eqs. bphs, bpvs, bpd,
  *                      hrddcs), phi-form or literal tanh-form check update
  *   or_ms_decode       integer min-sum (fixed-point variant of the CN rule)
@@ -71,15 +71,16 @@ static double or_uniform(uint32_t x)
 }
 
 /*
- * Channel of Sec. II-B for the all-zero codeword: x_n = 1 - 2*0 = +1,
- * y_n = x_n + sigma*g_n with g_n standard normal, mu_n = 2 y_n / sigma^2.
+ * Channel of Sec. II-B: BPSK x_n = 1 - 2 c_n, y_n = x_n + sigma*g_n with g_n
+ * standard normal, mu_n = 2 y_n / sigma^2.  cw (row-major [nfr][N], 0/1) is
+ * the transmitted codeword; NULL sends the all-zero codeword (x_n = +1).
  * g_n comes from Box-Muller on two Philox uniforms.  Bit n of frame F uses
  * counter (n/4, F_lo, F_hi, tag) under key (seed_lo, seed_hi); the four words
  * give the normals of bits 4q..4q+3 as two Box-Muller pairs.
  * mu is rounded to binary32 at the end; g_out (if non-NULL) receives g.
  */
-void or_channel_awgn(uint64_t seed, uint64_t first_frame, int nfr, int N, double sigma,
-                     uint32_t tag, float *mu_out, double *g_out)
+void or_channel_awgn_cw(uint64_t seed, uint64_t first_frame, int nfr, int N, double sigma,
+                        uint32_t tag, const uint8_t *cw, float *mu_out, double *g_out)
 {
     const double two_pi = 6.283185307179586476925286766559;
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
@@ -100,13 +101,20 @@ void or_channel_awgn(uint64_t seed, uint64_t first_frame, int nfr, int N, double
             for (int e = 0; e < 4; ++e) {
                 int n = 4 * q + e;
                 if (n >= N) break;
-                double y = 1.0 + sigma * g[e];
+                double x = (cw && cw[(size_t)f * N + n]) ? -1.0 : 1.0;
+                double y = x + sigma * g[e];
                 double mu = 2.0 * y / (sigma * sigma);
                 mu_out[(size_t)f * N + n] = (float)mu;
                 if (g_out) g_out[(size_t)f * N + n] = g[e];
             }
         }
     }
+}
+
+void or_channel_awgn(uint64_t seed, uint64_t first_frame, int nfr, int N, double sigma,
+                     uint32_t tag, float *mu_out, double *g_out)
+{
+    or_channel_awgn_cw(seed, first_frame, nfr, N, sigma, tag, NULL, mu_out, g_out);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -431,3 +431,72 @@ def test_noms_gradient_matches_finite_differences():
         fd = (oracle.noms(rp, col, cb, N, mu, T, pp)[0] - oracle.noms(rp, col, cb, N, mu, T, pm)[0]) / (2 * h)
         assert abs(fd - grad[t, c, k]) <= 1e-6 * max(1e-3, abs(fd)), (t, c, k, fd, grad[t, c, k])
     assert np.abs(grad).max() > 0
+
+
+# --------------------------------------------------------------------------
+# Systematic encoder (the transmitted codewords of Sec. V)
+# --------------------------------------------------------------------------
+def _span_rank(vectors) -> int:
+    """GF(2) rank by brute force: the span of r independent vectors has 2^r elements."""
+    span = {0}
+    for v in vectors:
+        span |= {x ^ v for x in span}
+    return len(span).bit_length() - 1
+
+
+def _small_parity_checks():
+    rng = np.random.default_rng(31)
+    Hs = [(rng.random((5, 10)) < 0.4).astype(np.uint8)]
+    Hs.append(oracle.qc_parity_check(synth.qc_shifts(2, 4, 3, seed=3), 3))  # rank-deficient (2 block rows)
+    H = (rng.random((4, 11)) < 0.5).astype(np.uint8)
+    H[2] = 0                    # an empty check
+    H[:, 7] = H[:, 9]           # two equal columns
+    H[:, 10] = 0                # a variable in no check
+    Hs.append(H)
+    Hs.append(np.array(read_sections("irregular_H_example.txt")[None], dtype=np.uint8))
+    return Hs
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_encoder_matches_brute_force(case):
+    """Information set by its definition (column n is parity iff it raises the rank of the columns to its
+    right), k = N - rank, and encoding is the bijection onto the null space with c[info] = u."""
+    from helpers import codewords_exhaustive
+    H = _small_parity_checks()[case]
+    M, N = H.shape
+    enc = oracle.Encoder(H)
+    cols = [sum(int(H[m, n]) << m for m in range(M)) for n in range(N)]
+    parity = [n for n in range(N) if _span_rank(cols[n:]) > _span_rank(cols[n + 1:])]
+    assert list(enc.parity) == parity
+    assert list(enc.info) == [n for n in range(N) if n not in parity]
+    C = {tuple(r) for r in codewords_exhaustive(H)}
+    assert len(C) == 2 ** enc.k and enc.k == N - _span_rank(cols)
+    U = np.array([[(x >> j) & 1 for j in range(enc.k)] for x in range(2 ** enc.k)], dtype=np.uint8)
+    c = enc.encode(U)
+    assert np.array_equal(c[:, enc.info], U)
+    assert {tuple(r) for r in c} == C
+
+
+def test_encoder_on_qc_code_rank_and_checks():
+    """A J x L QC code with every block present has rank at most J p - (J - 1) (each block row sums to the
+    all-ones row); encoded words of the 3 x 6, p = 64 code satisfy every check."""
+    shifts = synth.qc_shifts(3, 6, 64, seed=1)
+    H = oracle.qc_parity_check(shifts, 64)
+    enc = oracle.Encoder(H)
+    assert enc.rank <= 3 * 64 - 2 and enc.k == 384 - enc.rank
+    u = (np.random.default_rng(4).random((6, enc.k)) < 0.5).astype(np.uint8)
+    c = enc.encode(u)
+    assert not syndrome(H, c).any() and np.array_equal(c[:, enc.info], u)
+
+
+def test_channel_with_codeword_shifts_by_bpsk_symbol():
+    """Sec. II-B with x = 1 - 2c: a one bit moves y by -2, so mu(c) = mu(0) - 4 c / sigma^2 (same noise)."""
+    N, nfr, sigma = 37, 3, 0.8
+    cw = (np.random.default_rng(2).random((nfr, N)) < 0.5).astype(np.uint8)
+    m0, g0 = oracle.channel_awgn(9, 100, nfr, N, sigma, return_g=True)
+    m1, g1 = oracle.channel_awgn(9, 100, nfr, N, sigma, return_g=True, cw=cw)
+    assert np.array_equal(g0, g1)
+    x = 1.0 - 2.0 * cw.astype(np.float64)
+    want = (2.0 * (x + sigma * g0) / (sigma * sigma)).astype(np.float32)
+    assert np.array_equal(m1, want)
+    assert np.allclose(m1.astype(np.float64) - m0, -4.0 * cw.astype(np.float64) / sigma**2, atol=1e-5)
