@@ -322,7 +322,10 @@ def variants(a, pkg, code, stream, opts) -> dict:
     cases = [("f32_fixed30", dict(early_stop=0, algo=pkg.ALGO_SP, msg=pkg.MSG_F32)),
              ("f16_early_stop", dict(early_stop=1, algo=pkg.ALGO_SP, msg=pkg.MSG_F16)),
              ("i8_minsum_early_stop", dict(early_stop=1, algo=pkg.ALGO_MS, msg=pkg.MSG_I8)),
-             ("i8_minsum_fixed30", dict(early_stop=0, algo=pkg.ALGO_MS, msg=pkg.MSG_I8))]
+             ("i8_minsum_fixed30", dict(early_stop=0, algo=pkg.ALGO_MS, msg=pkg.MSG_I8)),
+             # random codewords encoded on the device (errors over the information bits)
+             ("f32_random_codewords", dict(early_stop=1, algo=pkg.ALGO_SP, msg=pkg.MSG_F32,
+                                           codewords=pkg.CODEWORDS_RANDOM))]
     for name, kw in cases:
         o = pkg.default_opts(max_iter=a.iters, **kw)
         base = (7 << 44)

@@ -64,8 +64,13 @@ typedef struct {
                                   [-clip, clip] (default 30) */
     int32_t frac_bits;         /* MS: q = clamp(rint(mu * 2^frac_bits), -127, 127) (default 2) */
     const float *noms_params;  /* NOMS: device [max_iter][J*L][2] of (w, o); else NULL */
-    int32_t reserved[4];       /* must be zero */
+    int32_t codewords;         /* ldpc_ber_sim only: LDPC_CODEWORDS_ZERO (default) or
+                                  LDPC_CODEWORDS_RANDOM; the other calls ignore it */
+    int32_t reserved[3];       /* must be zero */
 } ldpc_decode_opts;
+
+/* Transmitted codewords of ldpc_ber_sim. */
+enum { LDPC_CODEWORDS_ZERO = 0, LDPC_CODEWORDS_RANDOM = 1 };
 
 /* Defaults: max_iter 30, early_stop 0, SP, F32 messages, clip 30, frac_bits 2. */
 void ldpc_default_opts(ldpc_decode_opts *opts);
@@ -184,10 +189,46 @@ ldpc_status ldpc_batch_destroy(ldpc_batch batch);
 ldpc_status ldpc_channel(ldpc_code code, double ebn0_db, uint64_t seed, uint64_t first_frame, int32_t gamma,
                          float *llr_out, void *stream);
 
+/*
+ * Systematic encoding: the transmitted codewords of Sec. V, made on the device.
+ *
+ * Information set.  Scanning the columns of H from n = N-1 down to 0, column n
+ * is a parity position when it is not in the GF(2) span of the columns to its
+ * right, else an information position.  The parity columns are a basis of
+ * H's column space, so k = N - rank(H) >= K = N - M, and for every u in
+ * {0,1}^k exactly one codeword c (H c = 0) has c[info_pos[j]] = u[j], with
+ * info_pos increasing.  The encoder is built on the host by Gauss-Jordan
+ * elimination over GF(2) the first time a call below needs it (O(M^2 N / 64)
+ * word operations: about a second for n = 18360); each frame's parity bits are
+ * then a dense GF(2) matrix-vector product on the device.
+ *
+ * ldpc_code_info_set -- k and, when info_pos != NULL, the k information
+ *   positions (host int32 [k]).  Host-only work; no device memory is touched.
+ * ldpc_encode -- cw[f] = the codeword of info[f] (device uint8 [gamma][k]; bit
+ *   = byte & 1) into device uint8 [gamma][N] (0/1).  info may be NULL when k = 0.
+ * ldpc_random_codewords -- the codewords ldpc_ber_sim sends with
+ *   LDPC_CODEWORDS_RANDOM: information bit j of frame F is bit j mod 32 of word
+ *   (j/32) mod 4 of Philox4x32-10 at counter (j/128, F mod 2^32, F / 2^32, 1)
+ *   under key (seed mod 2^32, seed / 2^32) (the channel's counters carry 0 in
+ *   the last word); frames first_frame .. first_frame+gamma-1.  info (device
+ *   uint8 [gamma][k]) may be NULL; cw as in ldpc_encode.
+ * ldpc_channel_codewords -- ldpc_channel with the codeword cw (device uint8
+ *   [gamma][N], 0/1) sent as BPSK x = 1 - 2c: mu = 2 (x + sigma g) / sigma^2
+ *   with the same g, so an all-zero cw reproduces ldpc_channel exactly.
+ * All pointers but info_pos are device pointers (host pointers: LDPC_EINVAL).
+ */
+ldpc_status ldpc_code_info_set(ldpc_code code, int64_t *k, int32_t *info_pos);
+ldpc_status ldpc_encode(ldpc_code code, const uint8_t *info, int32_t gamma, uint8_t *cw, void *stream);
+ldpc_status ldpc_random_codewords(ldpc_code code, uint64_t seed, uint64_t first_frame, int32_t gamma,
+                                  uint8_t *info, uint8_t *cw, void *stream);
+ldpc_status ldpc_channel_codewords(ldpc_code code, double ebn0_db, uint64_t seed, uint64_t first_frame,
+                                   int32_t gamma, const uint8_t *cw, float *llr_out, void *stream);
+
 typedef struct {
     int64_t frames;        /* frames decoded */
-    int64_t frame_errors;  /* frames with >= 1 wrong bit (all N coded bits counted) */
-    int64_t bit_errors;    /* wrong coded bits */
+    int64_t frame_errors;  /* frames with >= 1 wrong bit (all N coded bits counted; with
+                              LDPC_CODEWORDS_RANDOM the k information bits) */
+    int64_t bit_errors;    /* wrong coded bits (LDPC_CODEWORDS_RANDOM: wrong information bits) */
     int64_t iters_sum;     /* sum over frames of the iterations run */
     int64_t undetected;    /* frames with ok = 1 but >= 1 wrong bit */
     double seconds;        /* wall time of the call */
@@ -196,19 +237,21 @@ typedef struct {
 /*
  * ldpc_ber_sim -- the Monte-Carlo protocol of Sec. V: fixed iteration cap,
  * frames generated and decoded on the device, error counts reduced on the
- * device.  Sum-product and min-sum run continuously: gamma frame slots
- * (rounded up to whole packages of 32 V frames), and a slot takes the next
- * frame in the step after its frame stops (C-11 syndrome check after >= 1
- * iterations when opts->early_stop, or the iteration cap), so each frame
- * gets exactly the iterations and decisions that ldpc_decode gives it.
+ * device.  The decoders run continuously: gamma frame slots (rounded up to
+ * whole packages of 32 V frames), and a slot takes the next frame in the
+ * step after its frame stops (C-11 syndrome check after >= 1 iterations when
+ * opts->early_stop, or the iteration cap), so each frame gets exactly the
+ * iterations and decisions that ldpc_decode gives it (learned NOMS: each
+ * frame's iteration i uses parameter row i).
  * Once frame_errors >= target_frame_errors (the paper uses 100) no new frame
  * starts and the frames in flight finish; at most max_frames frames start.
  * The frames counted are always first_frame .. first_frame + out->frames - 1,
- * drawn exactly as ldpc_channel draws them, so a run can be resumed from
- * (seed, first_frame + out->frames) and partial results added.  Learned NOMS
- * (parameters per iteration) runs in batches of gamma frames and tests the
- * stop rule after each batch.  Blocks the calling thread until the run ends
- * (it reads the totals every two steps).
+ * drawn exactly as ldpc_channel draws them (opts->codewords =
+ * LDPC_CODEWORDS_RANDOM: as ldpc_random_codewords and ldpc_channel_codewords
+ * draw them, errors counted over the information bits), so a run can be
+ * resumed from (seed, first_frame + out->frames) and partial results added.
+ * Blocks the calling thread until the run ends (it reads the totals every
+ * two steps).
  *   out: host pointer, filled on return.
  */
 ldpc_status ldpc_ber_sim(ldpc_code code, double ebn0_db, uint64_t seed, uint64_t first_frame, int64_t max_frames,

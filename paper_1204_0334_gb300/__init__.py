@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(HERE, "libldpc_gb300.so")
 
 ALGO_SP, ALGO_MS, ALGO_NOMS = 0, 1, 2
 MSG_F32, MSG_F16, MSG_I8 = 0, 1, 2
+CODEWORDS_ZERO, CODEWORDS_RANDOM = 0, 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "device wait timed out",
           5: "unsupported"}
 
@@ -34,7 +35,7 @@ class LdpcError(RuntimeError):
 class DecodeOpts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("early_stop", ctypes.c_int32), ("algo", ctypes.c_int32),
                 ("msg", ctypes.c_int32), ("clip", ctypes.c_float), ("frac_bits", ctypes.c_int32),
-                ("noms_params", ctypes.c_void_p), ("reserved", ctypes.c_int32 * 4)]
+                ("noms_params", ctypes.c_void_p), ("codewords", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class BerResult(ctypes.Structure):
@@ -66,6 +67,11 @@ _SIGNATURES = [
     ("ldpc_channel", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, P, P]),
     ("ldpc_ber_sim", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
                                     ctypes.c_int64, ctypes.c_int32, P, P, P]),
+    ("ldpc_code_info_set", ctypes.c_int, [P, P, P]),
+    ("ldpc_encode", ctypes.c_int, [P, P, ctypes.c_int32, P, P]),
+    ("ldpc_random_codewords", ctypes.c_int, [P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, P, P, P]),
+    ("ldpc_channel_codewords", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32,
+                                              P, P, P]),
     ("ldpccc_create", ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                      ctypes.c_int32, P]),
     ("ldpccc_destroy", ctypes.c_int, [P]),
@@ -192,6 +198,34 @@ def ldpc_ber_sim(code: int, ebn0_db: float, seed: int, first_frame: int, max_fra
     _check(lib().ldpc_ber_sim(code, ebn0_db, seed, first_frame, max_frames, target_frame_errors, gamma,
                               ctypes.byref(opts), ctypes.byref(r), _stream(stream)), "ldpc_ber_sim")
     return r.as_dict()
+
+
+def ldpc_code_info_set(code: int):
+    """(k, info_pos): the code's dimension and its information positions (numpy int32 [k])."""
+    import numpy as np
+
+    k = ctypes.c_int64()
+    _check(lib().ldpc_code_info_set(code, ctypes.byref(k), None), "ldpc_code_info_set")
+    pos = np.zeros(k.value, dtype=np.int32)
+    if k.value:
+        _check(lib().ldpc_code_info_set(code, ctypes.byref(k), pos.ctypes.data_as(ctypes.c_void_p)),
+               "ldpc_code_info_set")
+    return k.value, pos
+
+
+def ldpc_encode(code: int, info, cw, stream=None):
+    """cw[gamma][N] (uint8, device) = codewords of info[gamma][k] (uint8, device)."""
+    _check(lib().ldpc_encode(code, _ptr(info), cw.shape[0], _ptr(cw), _stream(stream)), "ldpc_encode")
+
+
+def ldpc_random_codewords(code: int, seed: int, first_frame: int, cw, info=None, stream=None):
+    _check(lib().ldpc_random_codewords(code, seed, first_frame, cw.shape[0], _ptr(info), _ptr(cw), _stream(stream)),
+           "ldpc_random_codewords")
+
+
+def ldpc_channel_codewords(code: int, ebn0_db: float, seed: int, first_frame: int, cw, out, stream=None):
+    _check(lib().ldpc_channel_codewords(code, ebn0_db, seed, first_frame, out.shape[0], _ptr(cw), _ptr(out),
+                                        _stream(stream)), "ldpc_channel_codewords")
 
 
 def ldpc_phi_eval(x, variant: int = 0, stream=None):
@@ -396,6 +430,34 @@ class QCCode:
 
         out = torch.empty((gamma, self.N), dtype=torch.float32, device=device)
         ldpc_channel(self.handle, ebn0_db, seed, first_frame, out, stream)
+        return out
+
+    def info_set(self):
+        """(k, info_pos) of the systematic encoder."""
+        return ldpc_code_info_set(self.handle)
+
+    def encode(self, info, stream=None):
+        import torch
+
+        cw = torch.empty((info.shape[0], self.N), dtype=torch.uint8, device=info.device)
+        ldpc_encode(self.handle, info.contiguous(), cw, stream)
+        return cw
+
+    def random_codewords(self, seed, first_frame, gamma, device="cuda", want_info=True, stream=None):
+        """(info[gamma][k], cw[gamma][N]) as uint8 device tensors (info None unless want_info)."""
+        import torch
+
+        k, _ = self.info_set()
+        cw = torch.empty((gamma, self.N), dtype=torch.uint8, device=device)
+        info = torch.empty((gamma, k), dtype=torch.uint8, device=device) if want_info and k else None
+        ldpc_random_codewords(self.handle, seed, first_frame, cw, info, stream)
+        return info, cw
+
+    def channel_codewords(self, ebn0_db, seed, first_frame, cw, stream=None):
+        import torch
+
+        out = torch.empty((cw.shape[0], self.N), dtype=torch.float32, device=cw.device)
+        ldpc_channel_codewords(self.handle, ebn0_db, seed, first_frame, cw.contiguous(), out, stream)
         return out
 
     def ber_sim(self, ebn0_db, seed=1, first_frame=0, max_frames=4096, target_frame_errors=100, gamma=4096,

@@ -23,6 +23,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <memory>
 #include <vector>
 
 namespace ldpc {
@@ -564,7 +565,8 @@ using namespace ldpc;
 struct ldpc_batch_s {
     int ncodes = 0, V = 1;
     ldpc_decode_opts o;
-    std::vector<ldpc_code_s> views;  // per-code views into the shared workspace
+    std::unique_ptr<ldpc_code_s[]> views;  // per-code views into the shared workspace
+    int nviews = 0;
     std::vector<BCode> hcodes;
     BCode *codes = nullptr;
     int *shtab = nullptr, *eotab = nullptr;
@@ -766,7 +768,9 @@ ldpc_status ldpc_batch_create(const ldpc_code *codes, int32_t ncodes, const int3
         cudaMemcpy(b->pair_pk, pp.data(), pp.size() * 4, cudaMemcpyHostToDevice))
         return fail("table upload");
     // per-code views: the single-code pack / finish / unpack kernels run on them
-    b->views.resize(ncodes);
+    b->views.reset(new (std::nothrow) ldpc_code_s[ncodes]);
+    if (!b->views) return fail("host allocation");
+    b->nviews = ncodes;
     for (int i = 0; i < ncodes; ++i) {
         ldpc_code_s &v = b->views[i];
         const BCode &bc = b->hcodes[i];
@@ -793,7 +797,7 @@ ldpc_status ldpc_batch_destroy(ldpc_batch b) {
     cudaFree(b->msg); cudaFree(b->mu); cudaFree(b->hw); cudaFree(b->flags); cudaFree(b->iters);
     cudaFree(b->codes); cudaFree(b->shtab); cudaFree(b->eotab); cudaFree(b->pair_code); cudaFree(b->pair_pk);
     cudaFree(b->counts); cudaFree(b->cn_tiles); cudaFree(b->vn_tiles);
-    for (auto &v : b->views) v.ws = DecodeWs();  // borrowed
+    for (int i = 0; i < b->nviews; ++i) b->views[i].ws = DecodeWs();  // borrowed
     delete b;
     return LDPC_OK;
 }

@@ -26,6 +26,10 @@ ldpc_status cuda_fail(cudaError_t e, const char *what) {
     return LDPC_ECUDA;
 }
 
+double channel_sigma(const ldpc_code c, double ebn0_db) {
+    return std::sqrt(1.0 / (2.0 * c->rate * std::pow(10.0, ebn0_db / 10.0)));
+}
+
 int pointer_kind(const void *p) {
     if (!p) return -1;
     cudaPointerAttributes a;
@@ -49,7 +53,11 @@ static ldpc_status check_opts(const ldpc_code c, const ldpc_decode_opts *o) {
         set_error("the learned min-sum takes QC codes (parameters per circulant)");
         return LDPC_EUNSUPPORTED;
     }
-    for (int i = 0; i < 4; ++i)
+    if (o->codewords != LDPC_CODEWORDS_ZERO && o->codewords != LDPC_CODEWORDS_RANDOM) {
+        set_error("codewords must be LDPC_CODEWORDS_ZERO or LDPC_CODEWORDS_RANDOM (got %d)", o->codewords);
+        return LDPC_EINVAL;
+    }
+    for (int i = 0; i < 3; ++i)
         if (o->reserved[i]) {
             set_error("reserved fields must be zero");
             return LDPC_EINVAL;
@@ -204,6 +212,7 @@ ldpc_status ldpc_code_destroy(ldpc_code c) {
     cudaFree(w.stage_i32);
     noms_free(c->noms);
     sim_free(c->sim);
+    enc_free(c->enc);
     cudaFree(c->sp_mem);
     delete c;
     return LDPC_OK;
@@ -295,6 +304,8 @@ ldpc_status ldpc_code_create_sparse(int32_t M, int32_t N, const int32_t *row_ptr
     c->sp.cedge = dm + M + 1 + E + N + 1;
     c->sp.dc_max = dc_max;
     c->sp.dv_max = dv_max;
+    c->h_rp.assign(row_ptr, row_ptr + M + 1);
+    c->h_col.assign(col_idx, col_idx + E);
     *out = c;
     return LDPC_OK;
 }
@@ -350,9 +361,6 @@ ldpc_status ldpc_decode(ldpc_code c, const float *llr, int32_t gamma, const ldpc
     return LDPC_OK;
 }
 
-static double sigma_of(ldpc_code c, double ebn0_db) {
-    return std::sqrt(1.0 / (2.0 * c->rate * std::pow(10.0, ebn0_db / 10.0)));
-}
 
 ldpc_status ldpc_channel(ldpc_code c, double ebn0_db, uint64_t seed, uint64_t first_frame, int32_t gamma,
                          float *llr_out, void *stream) {
@@ -372,7 +380,7 @@ ldpc_status ldpc_channel(ldpc_code c, double ebn0_db, uint64_t seed, uint64_t fi
         if (st != LDPC_OK) return st;
         dst = c->ws.stage_llr;
     }
-    ldpc_status st = qc_channel_frames(c, sigma_of(c, ebn0_db), seed, first_frame, gamma, dst, s);
+    ldpc_status st = qc_channel_frames(c, channel_sigma(c, ebn0_db), seed, first_frame, gamma, dst, s);
     if (st != LDPC_OK) return st;
     if (host_out)
         LDPC_CUDA_TRY(cudaMemcpyAsync(llr_out, dst, (size_t)gamma * c->d.N * 4, cudaMemcpyDeviceToHost, s));
@@ -400,7 +408,7 @@ ldpc_status ldpc_ber_sim(ldpc_code c, double ebn0_db, uint64_t seed, uint64_t fi
     cudaStream_t s = (cudaStream_t)stream;
     const auto t0 = std::chrono::steady_clock::now();
     std::memset(out, 0, sizeof(*out));
-    const double sigma = sigma_of(c, ebn0_db);
+    const double sigma = channel_sigma(c, ebn0_db);
     unsigned long long h[8];
     // continuous simulation: slots refilled as frames stop
     st = qc_ber_sim_refill(c, sigma, seed, first_frame, max_frames, target_frame_errors, gamma, o, h, s);

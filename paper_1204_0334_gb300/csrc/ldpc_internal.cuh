@@ -5,7 +5,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <string>
+#include <vector>
 
 #include "ldpc.h"
 
@@ -70,6 +72,7 @@ struct DecodeWs {
 
 struct ldpc_noms_state;  // training state of the learned min-sum (noms.cu)
 struct ldpc_sim_state;   // frame slots of the continuous simulation (sim.cu)
+struct ldpc_encoder_s;   // systematic encoder (encode.cu)
 
 namespace ldpc {
 // index tables of a general sparse code (device memory): H in compressed-row form with
@@ -90,6 +93,9 @@ struct ldpc_code_s {
     void *sp_mem = nullptr;   // their device allocation
     ldpc_noms_state *noms = nullptr;
     ldpc_sim_state *sim = nullptr;
+    ldpc_encoder_s *enc = nullptr;   // built on first use, under enc_mu
+    std::mutex enc_mu;
+    std::vector<int> h_rp, h_col;    // sparse code: H in compressed-row form (host copy)
     int device = 0;
     double rate = 0.0;   // design rate K/N
     ldpc::DecodeWs ws;
@@ -109,6 +115,8 @@ ldpc_status cuda_fail(cudaError_t e, const char *what);
 
 // 0: device pointer (or managed); 1: host pointer; -1: null
 int pointer_kind(const void *p);
+// noise level of Eb/N0 (dB) at the code's design rate: sigma^2 = 1 / (2 R 10^(EbN0/10))
+double channel_sigma(const ldpc_code c, double ebn0_db);
 
 // sizes of the flags block per package
 inline int flags_per_package(int V) { return 5 * V; }
@@ -150,6 +158,22 @@ void sim_free(ldpc_sim_state *st);
 ldpc_status qc_ber_sim_refill(ldpc_code c, double sigma, uint64_t seed, uint64_t first_frame, int64_t max_frames,
                               int64_t target, int gamma, const ldpc_decode_opts &o, unsigned long long *h,
                               cudaStream_t s);
+
+// systematic encoder (encode.cu)
+void enc_free(ldpc_encoder_s *e);
+// host part (information set, parity matrix); no device memory
+ldpc_status enc_build_host(ldpc_code c);
+// device tables and a sliced-codeword scratch for `groups` groups of 32 frames
+ldpc_status enc_ensure_device(ldpc_code c, size_t groups);
+int64_t enc_k(const ldpc_code c);
+int enc_words(const ldpc_code c);  // ceil(N / 32): words of a frame-major codeword row
+// continuous simulation with random codewords: wrong information bits of the frames that
+// retire this step (from the staged decisions, before a new frame's overwrite them), and
+// the codewords of the frames that enter a slot (frame-major rows cwf[slot][enc_words])
+ldpc_status enc_sim_errors(ldpc_code c, int P, int V, const uint32_t *sflags, const uint32_t *cwf, int *errs,
+                           cudaStream_t s);
+ldpc_status enc_sim_codewords(ldpc_code c, int slots, const int *rlist, const int *rcount, int parity,
+                              const uint64_t *fid, uint64_t seed, uint32_t *cwf, cudaStream_t s);
 
 inline int lanes_per_word(int msg) { return msg == LDPC_MSG_F32 ? 1 : (msg == LDPC_MSG_F16 ? 2 : 4); }
 

@@ -161,7 +161,9 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t
 
 // words -> four channel LLRs: u = (floor(w / 2^9) + 1/2) 2^-23, Box-Muller pairs
 // (w0, w1) and (w2, w3), mu = (2 / sigma^2) (1 + sigma g) for the all-zero codeword
-__device__ __forceinline__ void box_muller_llr(const uint32_t *w, float sigma, float s2, float *mu4) {
+// bit e of `bits` is the code bit c of LLR e: BPSK x = 1 - 2c (all-zero codeword: bits = 0)
+__device__ __forceinline__ void box_muller_llr(const uint32_t *w, float sigma, float s2, float *mu4,
+                                               uint32_t bits = 0u) {
 #pragma unroll
     for (int pr = 0; pr < 2; ++pr) {
         const float u0 = ((float)(w[2 * pr] >> 9) + 0.5f) * 1.1920928955078125e-07f;
@@ -169,16 +171,19 @@ __device__ __forceinline__ void box_muller_llr(const uint32_t *w, float sigma, f
         const float rr = sqrtf(-2.0f * logf(u0));
         float sn, cs;
         sincospif(2.0f * u1, &sn, &cs);
-        mu4[2 * pr] = s2 * (1.0f + sigma * (rr * cs));
-        mu4[2 * pr + 1] = s2 * (1.0f + sigma * (rr * sn));
+        const float x0 = ((bits >> (2 * pr)) & 1u) ? -1.0f : 1.0f;
+        const float x1 = ((bits >> (2 * pr + 1)) & 1u) ? -1.0f : 1.0f;
+        mu4[2 * pr] = s2 * (x0 + sigma * (rr * cs));
+        mu4[2 * pr + 1] = s2 * (x1 + sigma * (rr * sn));
     }
 }
 
-// four channel LLRs of bits 4q..4q+3 of frame F
-__device__ __forceinline__ void channel_quad(uint64_t seed, uint64_t F, int q, float sigma, float s2, float *mu4) {
+// four channel LLRs of bits 4q..4q+3 of frame F (code bits in `bits`, LSB = bit 4q)
+__device__ __forceinline__ void channel_quad(uint64_t seed, uint64_t F, int q, float sigma, float s2, float *mu4,
+                                             uint32_t bits = 0u) {
     uint32_t w[4];
     philox4x32_10((uint32_t)q, (uint32_t)F, (uint32_t)(F >> 32), 0u, (uint32_t)seed, (uint32_t)(seed >> 32), w);
-    box_muller_llr(w, sigma, s2, mu4);
+    box_muller_llr(w, sigma, s2, mu4, bits);
 }
 
 // ---------------------------------------------------------------------------

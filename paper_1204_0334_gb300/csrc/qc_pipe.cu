@@ -508,7 +508,7 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
             bool any_retire = false;
 #pragma unroll
             for (int v = 0; v < V; ++v) any_retire |= retire[v] != 0u;
-            if (any_retire) {
+            if (any_retire && rf.errs != nullptr) {  // NULL: counted against sent codewords elsewhere
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     if (!((retire[v] >> lane) & 1u)) continue;

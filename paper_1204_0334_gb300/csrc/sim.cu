@@ -29,6 +29,11 @@
 // always first_frame .. first_frame + frames - 1 (the set does not depend on
 // which slot a frame lands in).  Once the frame-error target is met no new
 // frame starts and the frames in flight finish.
+//
+// With random codewords (encode.cu) the step also counts the retiring frames'
+// wrong information bits against their codewords (right after the check, from
+// the decisions the variable pass would otherwise count) and encodes the new
+// frames' codewords before the channel sends them.
 #include "qc_device.cuh"
 
 #include <chrono>
@@ -45,6 +50,8 @@ struct ldpc_sim_state {
     size_t mu_bytes = 0;
     int *rlist = nullptr;                 // [slots] slots refilled this step
     int *rcount = nullptr;                // [2] entries of rlist, by step parity
+    uint32_t *cwf = nullptr;              // random codewords: [slots][ceil(N / 32)] the slot's codeword bits
+    size_t cwf_slots = 0;
     unsigned int *tickets = nullptr;      // [P + 1]: finished blocks per package, finished packages
     unsigned long long *next = nullptr;   // next frame index to hand out
     unsigned long long *host = nullptr;   // pinned [2][16]: counters, active packages
@@ -63,6 +70,7 @@ void sim_free(ldpc_sim_state *st) {
     cudaFree(st->mu);
     cudaFree(st->rlist);
     cudaFree(st->rcount);
+    cudaFree(st->cwf);
     cudaFree(st->tickets);
     cudaFree(st->next);
     if (st->host) cudaFreeHost(st->host);
@@ -304,10 +312,12 @@ __global__ void __launch_bounds__(256) sim_check_kernel(const QcDesc d, SimArgs 
 // ([slot][N4], N4 = N rounded up to 4): clipped floats, or int8 quantized with
 // qscale (as the batch path's channel kernel rounds them).  Consecutive threads
 // take consecutive groups of 4 bits of one frame, so each warp writes whole lines.
-template <bool I8>
+// CW: the slot's codeword (row cwf[slot][NW]) is sent, else the all-zero word.
+template <bool I8, bool CW>
 __global__ void sim_channel_kernel(void *__restrict__ mu, const int *__restrict__ rlist,
                                    const int *__restrict__ rcount, const uint64_t *__restrict__ fid, int N,
-                                   int parity, uint64_t seed, float sigma, float s2, float clip, float qscale) {
+                                   int parity, uint64_t seed, float sigma, float s2, float clip, float qscale,
+                                   const uint32_t *__restrict__ cwf, int NW) {
     const int cnt = rcount[parity];
     if (cnt == 0) return;
     const int Q = (N + 3) / 4;
@@ -319,7 +329,8 @@ __global__ void sim_channel_kernel(void *__restrict__ mu, const int *__restrict_
         const int q = (int)(i - (long long)r * Q);
         const int slot = rlist[r];
         float x[4];
-        channel_quad(seed, fid[slot], q, sigma, s2, x);
+        const uint32_t bits = CW ? (cwf[(size_t)slot * NW + (q >> 3)] >> (4 * (q & 7))) & 15u : 0u;
+        channel_quad(seed, fid[slot], q, sigma, s2, x, bits);
         if (I8) {
             uint32_t w = 0u;
 #pragma unroll
@@ -354,9 +365,29 @@ ldpc_status qc_ber_sim_refill(ldpc_code c, double sigma, uint64_t seed, uint64_t
                                                         S->rcount, S->tickets, c->ws.counters, P, V);
         count_launch();
     }
+    // random codewords: the encoder and each slot's codeword row
+    const bool cw = o.codewords == LDPC_CODEWORDS_RANDOM;
+    const int NW = enc_words(c);
+    if (cw) {
+        st = enc_ensure_device(c, slots / 32);
+        if (st != LDPC_OK) return st;
+        if (S->cwf_slots < slots) {
+            LDPC_CUDA_TRY(cudaDeviceSynchronize());
+            cudaFree(S->cwf);
+            S->cwf = nullptr;
+            S->cwf_slots = 0;
+            if (cudaMalloc(&S->cwf, slots * (size_t)NW * 4) != cudaSuccess) {
+                cudaGetLastError();
+                S->cwf = nullptr;
+                set_error("device allocation of %zu codeword rows failed", slots);
+                return LDPC_ENOMEM;
+            }
+            S->cwf_slots = slots;
+        }
+    }
     RefillArgs rf;
     rf.sflags = S->sflags;
-    rf.errs = S->errs;
+    rf.errs = cw ? nullptr : S->errs;  // with codewords the errors are counted against them
     rf.mu = S->mu;
     const float fsig = (float)sigma, s2 = (float)(2.0 / (sigma * sigma));
     const bool i8 = o.algo == LDPC_ALGO_MS;
@@ -396,12 +427,26 @@ ldpc_status qc_ber_sim_refill(ldpc_code c, double sigma, uint64_t seed, uint64_t
         else if (V == 2) sim_check_kernel<2><<<cgrd, 256, 0, s>>>(c->d, sa);
         else sim_check_kernel<4><<<cgrd, 256, 0, s>>>(c->d, sa);
         ldpc_status e = LDPC_OK;
-        if (i8)
-            sim_channel_kernel<true><<<cblocks, 256, 0, s>>>(S->mu, S->rlist, S->rcount, S->fid, c->d.N, parity, seed,
-                                                             fsig, s2, 1e30f, ldexpf(1.0f, o.frac_bits));
+        if (cw) {
+            // wrong information bits of the frames retiring now, then the new frames' codewords
+            e = enc_sim_errors(c, P, V, S->sflags, S->cwf, S->errs, s);
+            if (e != LDPC_OK) return e;
+            e = enc_sim_codewords(c, (int)slots, S->rlist, S->rcount, parity, S->fid, seed, S->cwf, s);
+            if (e != LDPC_OK) return e;
+        }
+        const float qs = ldexpf(1.0f, o.frac_bits);
+        if (i8 && cw)
+            sim_channel_kernel<true, true><<<cblocks, 256, 0, s>>>(S->mu, S->rlist, S->rcount, S->fid, c->d.N, parity,
+                                                                   seed, fsig, s2, 1e30f, qs, S->cwf, NW);
+        else if (i8)
+            sim_channel_kernel<true, false><<<cblocks, 256, 0, s>>>(S->mu, S->rlist, S->rcount, S->fid, c->d.N,
+                                                                    parity, seed, fsig, s2, 1e30f, qs, nullptr, 0);
+        else if (cw)
+            sim_channel_kernel<false, true><<<cblocks, 256, 0, s>>>(S->mu, S->rlist, S->rcount, S->fid, c->d.N,
+                                                                    parity, seed, fsig, s2, o.clip, 1.0f, S->cwf, NW);
         else
-            sim_channel_kernel<false><<<cblocks, 256, 0, s>>>(S->mu, S->rlist, S->rcount, S->fid, c->d.N, parity,
-                                                              seed, fsig, s2, o.clip, 1.0f);
+            sim_channel_kernel<false, false><<<cblocks, 256, 0, s>>>(S->mu, S->rlist, S->rcount, S->fid, c->d.N,
+                                                                     parity, seed, fsig, s2, o.clip, 1.0f, nullptr, 0);
         parity ^= 1;
         const int slot_cn = prof_begin(0, s);
         e = qc_cn_pipe(c, o, 1, s, S->sflags, o.algo == LDPC_ALGO_NOMS ? S->age : nullptr);

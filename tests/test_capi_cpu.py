@@ -8,6 +8,8 @@ import re
 import numpy as np
 import pytest
 
+import synth
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -102,3 +104,41 @@ def test_sparse_code_validation_without_a_device(lib):
     with pytest.raises(pkg.LdpcError) as e:
         pkg.ldpc_code_create_sparse(rp, col, 12)
     assert e.value.status == 1 and "degree" in str(e.value)
+
+
+@pytest.mark.parametrize("J,L,p,seed,zero_blocks", [(3, 6, 64, 1, 0), (4, 24, 32, 3, 0), (4, 12, 40, 7, 5),
+                                                    (4, 24, 765, 2, 0)])
+def test_information_set_matches_oracle(lib, J, L, p, seed, zero_blocks):
+    """The encoder's information set is built on the host (no device memory): it equals the oracle's
+    greedy right-to-left column basis complement, including the rank deficiency of QC codes and zero
+    blocks, up to the full 4 x 24, p = 765 code."""
+    import scipy.sparse as sp
+
+    import oracle
+    import paper_1204_0334_gb300 as pkg
+
+    shifts = synth.qc_shifts(J, L, p, seed=seed, zero_blocks=zero_blocks)
+    h = pkg.ldpc_code_create(shifts, p)
+    try:
+        k, pos = pkg.ldpc_code_info_set(h)
+    finally:
+        pkg.ldpc_code_destroy(h)
+    enc = oracle.Encoder(sp.csr_matrix(oracle.qc_parity_check(shifts, p)), track=False)
+    assert k == enc.k >= L * p - J * p
+    assert np.array_equal(pos, enc.info)
+
+
+def test_codeword_options_validated(lib):
+    import paper_1204_0334_gb300 as pkg
+
+    pkg.lib()
+    o = pkg.default_opts()
+    assert o.codewords == pkg.CODEWORDS_ZERO and list(o.reserved) == [0, 0, 0]
+    h = pkg.ldpc_code_create(np.array([[0, 1, 2, 3], [1, 3, 0, 2]]), 8)
+    try:
+        for bad in (dict(codewords=2), dict(codewords=-1)):
+            with pytest.raises(pkg.LdpcError) as e:
+                pkg.ldpc_ber_sim(h, 2.0, 1, 0, 64, 10, 64, pkg.default_opts(**bad), stream=0)
+            assert e.value.status == 1 and "codewords" in str(e.value)
+    finally:
+        pkg.ldpc_code_destroy(h)
