@@ -55,6 +55,8 @@ def args_parse():
     ap.add_argument("--iters", type=int, default=30)
     ap.add_argument("--msg", default="f32", choices=["f32", "f16", "i8"])
     ap.add_argument("--no-early-stop", action="store_true")
+    ap.add_argument("--codewords", default="zero", choices=["zero", "random"],
+                    help="transmitted codewords: all-zero (the paper's protocol) or random, encoded on the device")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -68,8 +70,9 @@ def args_parse():
 
 def workload_name(a) -> str:
     es = "early-stop" if not a.no_early_stop else "fixed"
+    cw = ", random codewords" if getattr(a, "codewords", "zero") == "random" else ""
     return (f"QC-LDPC 4x24 p=765 n=18360, {a.frames} frames/step in {a.gamma} slots, {a.iters} iters {es}, "
-            f"Eb/N0 {a.ebn0} dB, {a.msg} msgs")
+            f"Eb/N0 {a.ebn0} dB, {a.msg} msgs{cw}")
 
 
 def load_peaks() -> dict:
@@ -222,7 +225,8 @@ def run_ours(a):
     code = pkg.QCCode(shifts, P_CIRC)
     msg = {"f32": pkg.MSG_F32, "f16": pkg.MSG_F16, "i8": pkg.MSG_I8}[a.msg]
     algo = pkg.ALGO_MS if a.msg == "i8" else pkg.ALGO_SP
-    opts = pkg.default_opts(max_iter=a.iters, early_stop=0 if a.no_early_stop else 1, algo=algo, msg=msg)
+    opts = pkg.default_opts(max_iter=a.iters, early_stop=0 if a.no_early_stop else 1, algo=algo, msg=msg,
+                            codewords=pkg.CODEWORDS_RANDOM if a.codewords == "random" else pkg.CODEWORDS_ZERO)
     s_msg = {"f32": 4, "f16": 2, "i8": 1}[a.msg]
     s_mu = 1 if a.msg == "i8" else 4
     from paper_1204_0334_gb300 import shard

@@ -74,11 +74,14 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t w, int lane) {
 }
 
 // information bits -> sliced words sl[g][j], j < k.  Block (g, y), warp w: chunk c = 8y + w.
-__global__ void __launch_bounds__(256) enc_slice_kernel(EncSrc src, int64_t k, int kc, uint32_t *__restrict__ sl,
-                                                        int N) {
+// Blocks y = 0 also clear the group's parity words, which the parity pass accumulates.
+__global__ void __launch_bounds__(256) enc_slice_kernel(EncSrc src, int64_t k, int kc, int rank,
+                                                        uint32_t *__restrict__ sl, int N) {
     const int g = blockIdx.x;
     const int cnt = src.count();
     if (32 * g >= cnt) return;
+    if (blockIdx.y == 0)
+        for (int i = threadIdx.x; i < rank; i += blockDim.x) sl[(size_t)g * N + k + i] = 0u;
     const int lane = threadIdx.x & 31;
     const int c = blockIdx.y * 8 + (threadIdx.x >> 5);
     if (c >= kc) return;
@@ -103,7 +106,9 @@ __global__ void __launch_bounds__(256) enc_slice_kernel(EncSrc src, int64_t k, i
     if (32 * (int64_t)c + lane < k) sl[(size_t)g * N + 32 * c + lane] = x;
 }
 
-// parity words sl[g][k + i] = XOR_j A[i][j] U_j.  Block (g, y): rows 512y .. 512y + 511.
+// parity words sl[g][k + i] ^= XOR_j A[i][j] U_j over the stages of block z.  Block (g, y, z):
+// rows 512y .. 512y + 511, stages (128 information bits each) z, z + gridDim.z, ...; the
+// partial sums of the z-blocks meet in the (cleared) parity words through atomic XOR.
 __global__ void __launch_bounds__(256) enc_parity_kernel(EncSrc src, const uint32_t *__restrict__ At, int rpad,
                                                          int64_t k, int rank, int kc, uint32_t *__restrict__ sl,
                                                          int N) {
@@ -115,8 +120,18 @@ __global__ void __launch_bounds__(256) enc_parity_kernel(EncSrc src, const uint3
     const uint32_t *U = sl + (size_t)g * N;
     uint32_t acc0 = 0u, acc1 = 0u;
     const int ns = (kc + 3) / 4;
-    for (int s = 0; s < ns; ++s) {
-        uint32_t(*T)[16] = tab[s & 1];
+    int buf = 0;
+    for (int s = blockIdx.z; s < ns; s += gridDim.z, buf ^= 1) {
+        // this stage's rows of A first: their latency overlaps the table build and the barrier
+        uint32_t a0[4], a1[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int c = 4 * s + q < kc ? 4 * s + q : kc - 1;  // columns past kc are zero
+            a0[q] = __ldg(At + (size_t)c * rpad + r0);
+            a1[q] = __ldg(At + (size_t)c * rpad + r1);
+            if (4 * s + q >= kc) a0[q] = a1[q] = 0u;
+        }
+        uint32_t(*T)[16] = tab[buf];
         // entry (t, v) = XOR of U_j, j = 128 s + 4 t + b over the set bits b of v
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -130,24 +145,19 @@ __global__ void __launch_bounds__(256) enc_parity_kernel(EncSrc src, const uint3
             }
             T[t][v] = x;
         }
+        // the other table is free: every thread has passed the previous barrier, so the
+        // stage that read it is done
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int c = 4 * s + q;
-            if (c >= kc) break;
-            const uint32_t a0 = __ldg(At + (size_t)c * rpad + r0);
-            const uint32_t a1 = __ldg(At + (size_t)c * rpad + r1);
+        for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
-                acc0 ^= T[8 * q + t][(a0 >> (4 * t)) & 15u];
-                acc1 ^= T[8 * q + t][(a1 >> (4 * t)) & 15u];
+                acc0 ^= T[8 * q + t][(a0[q] >> (4 * t)) & 15u];
+                acc1 ^= T[8 * q + t][(a1[q] >> (4 * t)) & 15u];
             }
-        }
-        // the next stage writes the other table; the one after waits for this stage's
-        // readers at the next barrier
     }
-    if (r0 < rank) sl[(size_t)g * N + k + r0] = acc0;
-    if (r1 < rank) sl[(size_t)g * N + k + r1] = acc1;
+    if (r0 < rank && acc0) atomicXor(sl + (size_t)g * N + k + r0, acc0);
+    if (r1 < rank && acc1) atomicXor(sl + (size_t)g * N + k + r1, acc1);
 }
 
 // where a pack writes
@@ -198,11 +208,22 @@ __global__ void __launch_bounds__(256) enc_errors_kernel(const uint32_t *__restr
     const bool mine = (ret >> lane) & 1u;
     const size_t slot = (size_t)pk * 32 * V + (size_t)lane * V + v;
     int cnt = 0;
-    for (int c = blockIdx.y * 8 + (threadIdx.x >> 5); c < NW; c += gridDim.y * 8) {
-        const int n = 32 * c + lane;
-        const uint32_t h = n < N ? hw[((size_t)pk * N + n) * V + v] : 0u;
-        const uint32_t dec = transpose32(h, lane);  // lane b: decisions at 32c .. 32c+31 of slot b
-        if (mine) cnt += __popc((dec ^ cwf[slot * NW + c]) & imask[c]);
+    const int stride = gridDim.y * 8;
+    // four chunks per round: their loads are issued together
+    for (int c0 = blockIdx.y * 8 + (threadIdx.x >> 5); c0 < NW; c0 += 4 * stride) {
+        uint32_t h[4], w[4], m[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int c = c0 + i * stride, n = 32 * c + lane;
+            h[i] = c < NW && n < N ? hw[((size_t)pk * N + n) * V + v] : 0u;
+            w[i] = c < NW && mine ? cwf[slot * NW + c] : 0u;
+            m[i] = c < NW ? imask[c] : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t dec = transpose32(h[i], lane);  // lane b: decisions at 32c .. 32c+31 of slot b
+            cnt += __popc((dec ^ w[i]) & m[i]);
+        }
     }
     if (mine && cnt) atomicAdd(errs + slot, cnt);
 }
@@ -247,13 +268,18 @@ void parity_rows(const ldpc_code c, std::vector<uint64_t> &R, int W) {
 ldpc_status launch_encode(ldpc_code c, const EncSrc &src, int groups, cudaStream_t s) {
     ldpc_encoder_s *e = c->enc;
     const int N = e->N;
-    if (e->kc > 0) {
-        enc_slice_kernel<<<dim3(groups, (e->kc + 7) / 8), 256, 0, s>>>(src, e->k, e->kc, e->sl, N);
-        count_launch();
+    if (e->kc == 0) {
+        // k = 0: the only codeword is zero
+        LDPC_CUDA_TRY(cudaMemsetAsync(e->sl, 0, (size_t)groups * N * 4, s));
+        return LDPC_OK;
     }
+    enc_slice_kernel<<<dim3(groups, (e->kc + 7) / 8), 256, 0, s>>>(src, e->k, e->kc, e->rank, e->sl, N);
+    count_launch();
     if (e->rank > 0) {
-        enc_parity_kernel<<<dim3(groups, e->rpad / kEncRows), 256, 0, s>>>(src, e->d_At, e->rpad, e->k, e->rank,
-                                                                           e->kc, e->sl, N);
+        // split the stages so that each block runs about 16 of them
+        const int ns = (e->kc + 3) / 4, zs = std::min(16, (ns + 15) / 16);
+        enc_parity_kernel<<<dim3(groups, e->rpad / kEncRows, zs), 256, 0, s>>>(src, e->d_At, e->rpad, e->k,
+                                                                               e->rank, e->kc, e->sl, N);
         count_launch();
     }
     LDPC_CUDA_TRY(cudaGetLastError());
