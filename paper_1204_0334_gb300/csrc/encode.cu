@@ -3,20 +3,27 @@
 //
 // Information set: scanning the columns of H from n = N-1 down to 0, column n
 // is a parity position when it is not in the GF(2) span of the columns to its
-// right.  Gauss-Jordan elimination with the columns taken in that order finds
-// exactly these pivots; the reduced rows then read
-//     c[par_pos[i]] = sum_j A[i][j] u[j]   (GF(2)),  u[j] = c[info_pos[j]],
-// with A the rank x k block of the reduced rows at the information columns.
+// right.  Gauss-Jordan elimination of [H | I_M] with the columns of H taken in
+// that order finds exactly these pivots, and the rows i < rank of the right
+// block give T with T H = [rows of the reduced H]: for a codeword c,
+//     c[par_pos[i]] = sum_m T[i][m] s[m]   (GF(2)),   s = H_info u,
+// u[j] = c[info_pos[j]], H_info the columns of H at the information positions.
+// s is sparse work (the edges of the information columns); T is rank x M, so
+// the dense part is M / k times smaller than the rank x k generator block.
 //
 // Device layout.  Frames are processed in groups of 32, bit-sliced: word x of a
 // group holds bit x of its 32 frames (bit b = frame b), the form the decoder's
-// hard-decision words already take.  Per group the scratch row sl[g][N] holds
-// the k information words (index j) and then the rank parity words (k + i).
-//   slice:  information bits -> sliced words (32 ballots per 32 bits)
-//   parity: acc_i ^= A[i][j] * U_j over j, four bits at a time through 16-entry
-//           tables of the XORs of 4 consecutive U_j (the "four Russians" idea),
-//           one row per thread, A read as column-chunk-major words (coalesced)
-//   pack:   sliced words -> frame-major bits or bytes (32 ballots per 32 bits)
+// hard-decision words already take.  Per group the scratch row sl[g][N + M]
+// holds the k information words (index j), the rank parity words (k + i) and
+// the M syndrome words (N + m).
+//   slice:    information bits -> sliced words (32 ballots per 32 bits)
+//   syndrome: s_m = XOR of U_j over the information columns of row m
+//   parity:   acc_i ^= T[i][m] * s_m over m, four bits at a time through
+//             16-entry tables of the XORs of 4 consecutive s_m (the "four
+//             Russians" idea), two rows per thread, T read as column-chunk-major
+//             words (coalesced); the check range is split over blocks, which
+//             meet through atomic XOR
+//   pack:     sliced words -> frame-major bits or bytes (32 ballots per 32 bits)
 #include "ldpc_internal.cuh"
 #include "qc_device.cuh"
 
@@ -31,14 +38,17 @@ struct ldpc_encoder_s {
     int rank = 0;
     std::vector<int32_t> info_pos;  // [k] increasing
     std::vector<int32_t> par_pos;   // [rank] pivot column of reduced row i
-    std::vector<uint32_t> At;       // [kc4][rpad] word (c, i) = A[i][32c .. 32c+31], bit t = A[i][32c+t]
-    int kc = 0, kc4 = 0, rpad = 0, NW = 0;
+    std::vector<uint32_t> Tt;       // [mc4][rpad] word (c, i): bit t = T[i][32c + t]
+    std::vector<int32_t> hrp, hj;   // rows of H_info: information indices of row m in hj[hrp[m] .. hrp[m+1])
+    int mc = 0, mc4 = 0, kc = 0, rpad = 0, NW = 0;
+    size_t ld = 0;                  // scratch words per group: N + M
     // device
     void *dmem = nullptr;
-    const uint32_t *d_At = nullptr;
+    const uint32_t *d_Tt = nullptr;
+    const int *d_hrp = nullptr, *d_hj = nullptr;
     const int *d_src = nullptr;        // [N] scratch index of position n: j (information) or k + i (parity)
     const uint32_t *d_imask = nullptr; // [NW] bit n: information position
-    uint32_t *sl = nullptr;            // [groups][N] sliced codeword words
+    uint32_t *sl = nullptr;            // [groups][ld] sliced words
     size_t sl_groups = 0;
 };
 
@@ -76,12 +86,12 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t w, int lane) {
 // information bits -> sliced words sl[g][j], j < k.  Block (g, y), warp w: chunk c = 8y + w.
 // Blocks y = 0 also clear the group's parity words, which the parity pass accumulates.
 __global__ void __launch_bounds__(256) enc_slice_kernel(EncSrc src, int64_t k, int kc, int rank,
-                                                        uint32_t *__restrict__ sl, int N) {
+                                                        uint32_t *__restrict__ sl, size_t ld) {
     const int g = blockIdx.x;
     const int cnt = src.count();
     if (32 * g >= cnt) return;
     if (blockIdx.y == 0)
-        for (int i = threadIdx.x; i < rank; i += blockDim.x) sl[(size_t)g * N + k + i] = 0u;
+        for (int i = threadIdx.x; i < rank; i += blockDim.x) sl[(size_t)g * ld + k + i] = 0u;
     const int lane = threadIdx.x & 31;
     const int c = blockIdx.y * 8 + (threadIdx.x >> 5);
     if (c >= kc) return;
@@ -103,36 +113,49 @@ __global__ void __launch_bounds__(256) enc_slice_kernel(EncSrc src, int64_t k, i
         }
     }
     const uint32_t x = transpose32(w, lane);
-    if (32 * (int64_t)c + lane < k) sl[(size_t)g * N + 32 * c + lane] = x;
+    if (32 * (int64_t)c + lane < k) sl[(size_t)g * ld + 32 * c + lane] = x;
 }
 
-// parity words sl[g][k + i] ^= XOR_j A[i][j] U_j over the stages of block z.  Block (g, y, z):
-// rows 512y .. 512y + 511, stages (128 information bits each) z, z + gridDim.z, ...; the
-// partial sums of the z-blocks meet in the (cleared) parity words through atomic XOR.
-__global__ void __launch_bounds__(256) enc_parity_kernel(EncSrc src, const uint32_t *__restrict__ At, int rpad,
-                                                         int64_t k, int rank, int kc, uint32_t *__restrict__ sl,
-                                                         int N) {
+// syndrome of the information part, s_m = XOR_j U_j over the information columns of row m.
+// Block (g, y): rows 256y .. 256y + 255.
+__global__ void __launch_bounds__(256) enc_syndrome_kernel(EncSrc src, const int *__restrict__ hrp,
+                                                           const int *__restrict__ hj, int M, int N,
+                                                           uint32_t *__restrict__ sl, size_t ld) {
+    const int g = blockIdx.x;
+    if (32 * g >= src.count()) return;
+    const int m = blockIdx.y * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    uint32_t *row = sl + (size_t)g * ld;
+    uint32_t x = 0u;
+    for (int e = hrp[m]; e < hrp[m + 1]; ++e) x ^= row[hj[e]];
+    row[N + m] = x;
+}
+
+// parity words sl[g][k + i] ^= XOR_m T[i][m] s_m over the stages of block z (128 checks per
+// stage).  Block (g, y, z): rows 512y .. 512y + 511, stages z, z + gridDim.z, ...; the partial
+// sums of the z-blocks meet in the (cleared) parity words through atomic XOR.
+__global__ void __launch_bounds__(256) enc_parity_kernel(EncSrc src, const uint32_t *__restrict__ Tt, int rpad,
+                                                         int M, int mc, int N, int64_t k, int rank,
+                                                         uint32_t *__restrict__ sl, size_t ld) {
     __shared__ uint32_t tab[2][32][16];
     const int g = blockIdx.x;
     if (32 * g >= src.count()) return;
     const int tid = threadIdx.x;
     const int r0 = blockIdx.y * kEncRows + tid, r1 = r0 + 256;
-    const uint32_t *U = sl + (size_t)g * N;
+    const uint32_t *S = sl + (size_t)g * ld + N;
     uint32_t acc0 = 0u, acc1 = 0u;
-    const int ns = (kc + 3) / 4;
+    const int ns = (mc + 3) / 4;
     int buf = 0;
-    for (int s = blockIdx.z; s < ns; s += gridDim.z, buf ^= 1) {
-        // this stage's rows of A first: their latency overlaps the table build and the barrier
+    for (int st = blockIdx.z; st < ns; st += gridDim.z, buf ^= 1) {
+        // this stage's words of T first: their latency overlaps the table build and the barrier
         uint32_t a0[4], a1[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int c = 4 * s + q < kc ? 4 * s + q : kc - 1;  // columns past kc are zero
-            a0[q] = __ldg(At + (size_t)c * rpad + r0);
-            a1[q] = __ldg(At + (size_t)c * rpad + r1);
-            if (4 * s + q >= kc) a0[q] = a1[q] = 0u;
+        for (int q = 0; q < 4; ++q) {  // chunks past mc are zero (the table is padded to mc4)
+            a0[q] = __ldg(Tt + (size_t)(4 * st + q) * rpad + r0);
+            a1[q] = __ldg(Tt + (size_t)(4 * st + q) * rpad + r1);
         }
         uint32_t(*T)[16] = tab[buf];
-        // entry (t, v) = XOR of U_j, j = 128 s + 4 t + b over the set bits b of v
+        // entry (t, v) = XOR of s_m, m = 128 st + 4 t + b over the set bits b of v
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int e = tid + 256 * h;
@@ -140,8 +163,8 @@ __global__ void __launch_bounds__(256) enc_parity_kernel(EncSrc src, const uint3
             uint32_t x = 0u;
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const int64_t j = 128 * (int64_t)s + 4 * t + b;
-                if (((v >> b) & 1) && j < k) x ^= __ldg(U + j);
+                const int m = 128 * st + 4 * t + b;
+                if (((v >> b) & 1) && m < M) x ^= S[m];
             }
             T[t][v] = x;
         }
@@ -156,8 +179,8 @@ __global__ void __launch_bounds__(256) enc_parity_kernel(EncSrc src, const uint3
                 acc1 ^= T[8 * q + t][(a1[q] >> (4 * t)) & 15u];
             }
     }
-    if (r0 < rank && acc0) atomicXor(sl + (size_t)g * N + k + r0, acc0);
-    if (r1 < rank && acc1) atomicXor(sl + (size_t)g * N + k + r1, acc1);
+    if (r0 < rank && acc0) atomicXor(sl + (size_t)g * ld + k + r0, acc0);
+    if (r1 < rank && acc1) atomicXor(sl + (size_t)g * ld + k + r1, acc1);
 }
 
 // where a pack writes
@@ -170,7 +193,7 @@ struct EncDst {
 
 // sliced words -> per-frame bits.  Positions x < len: codeword positions (src != NULL,
 // word sl[g][src[x]]) or information bits (src == NULL, word sl[g][x]).
-__global__ void __launch_bounds__(256) enc_pack_kernel(EncSrc fs, const uint32_t *__restrict__ sl, int N,
+__global__ void __launch_bounds__(256) enc_pack_kernel(EncSrc fs, const uint32_t *__restrict__ sl, size_t ld,
                                                        const int *__restrict__ srcidx, int len, EncDst dst) {
     const int g = blockIdx.x;
     const int cnt = fs.count();
@@ -180,7 +203,7 @@ __global__ void __launch_bounds__(256) enc_pack_kernel(EncSrc fs, const uint32_t
     if (32 * c >= len) return;
     const int x = 32 * c + lane;
     uint32_t w = 0u;
-    if (x < len) w = sl[(size_t)g * N + (srcidx ? srcidx[x] : x)];
+    if (x < len) w = sl[(size_t)g * ld + (srcidx ? srcidx[x] : x)];
     const uint32_t bits = transpose32(w, lane);  // lane b: positions 32c .. 32c+31 of frame b
     const int f = 32 * g + lane;
     if (f >= cnt) return;
@@ -194,7 +217,9 @@ __global__ void __launch_bounds__(256) enc_pack_kernel(EncSrc fs, const uint32_t
 }
 
 // wrong information bits of the frames retiring in package word (pk, v): their decisions
-// are the staged hard words hw[pk][n][v] (bit = lane), their codewords the rows cwf[slot]
+// are the staged hard words hw[pk][n][v] (bit = lane), their codewords the rows cwf[slot].
+// Lane L holds the word of variable 32c + L; for each retiring lane b one ballot of bit b
+// gives that frame's decisions at 32c .. 32c+31.
 template <int V>
 __global__ void __launch_bounds__(256) enc_errors_kernel(const uint32_t *__restrict__ hw,
                                                          const uint32_t *__restrict__ sflags,
@@ -211,18 +236,24 @@ __global__ void __launch_bounds__(256) enc_errors_kernel(const uint32_t *__restr
     const int stride = gridDim.y * 8;
     // four chunks per round: their loads are issued together
     for (int c0 = blockIdx.y * 8 + (threadIdx.x >> 5); c0 < NW; c0 += 4 * stride) {
-        uint32_t h[4], w[4], m[4];
+        uint32_t h[4], w[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int c = c0 + i * stride, n = 32 * c + lane;
             h[i] = c < NW && n < N ? hw[((size_t)pk * N + n) * V + v] : 0u;
-            w[i] = c < NW && mine ? cwf[slot * NW + c] : 0u;
-            m[i] = c < NW ? imask[c] : 0u;
+            w[i] = c < NW && mine ? cwf[slot * NW + c] & imask[c] : 0u;
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const uint32_t dec = transpose32(h[i], lane);  // lane b: decisions at 32c .. 32c+31 of slot b
-            cnt += __popc((dec ^ w[i]) & m[i]);
+            const int c = c0 + i * stride;
+            const uint32_t m = c < NW ? imask[c] : 0u;
+            uint32_t mydec = 0u;
+            for (uint32_t r = ret; r; r &= r - 1) {  // warp-uniform loop over the retiring lanes
+                const int b = __ffs(r) - 1;
+                const uint32_t d = __ballot_sync(0xffffffffu, (h[i] >> b) & 1u);
+                mydec = lane == b ? d : mydec;
+            }
+            cnt += __popc((mydec & m) ^ w[i]);
         }
     }
     if (mine && cnt) atomicAdd(errs + slot, cnt);
@@ -267,20 +298,21 @@ void parity_rows(const ldpc_code c, std::vector<uint64_t> &R, int W) {
 
 ldpc_status launch_encode(ldpc_code c, const EncSrc &src, int groups, cudaStream_t s) {
     ldpc_encoder_s *e = c->enc;
-    const int N = e->N;
     if (e->kc == 0) {
         // k = 0: the only codeword is zero
-        LDPC_CUDA_TRY(cudaMemsetAsync(e->sl, 0, (size_t)groups * N * 4, s));
+        LDPC_CUDA_TRY(cudaMemsetAsync(e->sl, 0, (size_t)groups * e->ld * 4, s));
         return LDPC_OK;
     }
-    enc_slice_kernel<<<dim3(groups, (e->kc + 7) / 8), 256, 0, s>>>(src, e->k, e->kc, e->rank, e->sl, N);
+    enc_slice_kernel<<<dim3(groups, (e->kc + 7) / 8), 256, 0, s>>>(src, e->k, e->kc, e->rank, e->sl, e->ld);
     count_launch();
     if (e->rank > 0) {
-        // split the stages so that each block runs about 16 of them
-        const int ns = (e->kc + 3) / 4, zs = std::min(16, (ns + 15) / 16);
-        enc_parity_kernel<<<dim3(groups, e->rpad / kEncRows, zs), 256, 0, s>>>(src, e->d_At, e->rpad, e->k,
-                                                                               e->rank, e->kc, e->sl, N);
-        count_launch();
+        enc_syndrome_kernel<<<dim3(groups, (e->M + 255) / 256), 256, 0, s>>>(src, e->d_hrp, e->d_hj, e->M, e->N,
+                                                                            e->sl, e->ld);
+        // split the stages so that each block runs about 4 of them
+        const int ns = (e->mc + 3) / 4, zs = std::min(16, (ns + 3) / 4);
+        enc_parity_kernel<<<dim3(groups, e->rpad / kEncRows, zs), 256, 0, s>>>(
+            src, e->d_Tt, e->rpad, e->M, e->mc, e->N, e->k, e->rank, e->sl, e->ld);
+        count_launch(2);
     }
     LDPC_CUDA_TRY(cudaGetLastError());
     return LDPC_OK;
@@ -290,7 +322,7 @@ ldpc_status launch_pack(ldpc_code c, const EncSrc &src, int groups, const int *s
                         cudaStream_t s) {
     if (len <= 0) return LDPC_OK;
     const int chunks = (len + 31) / 32;
-    enc_pack_kernel<<<dim3(groups, (chunks + 7) / 8), 256, 0, s>>>(src, c->enc->sl, c->enc->N, srcidx, len, dst);
+    enc_pack_kernel<<<dim3(groups, (chunks + 7) / 8), 256, 0, s>>>(src, c->enc->sl, c->enc->ld, srcidx, len, dst);
     count_launch();
     LDPC_CUDA_TRY(cudaGetLastError());
     return LDPC_OK;
@@ -312,8 +344,16 @@ ldpc_status enc_build_host(ldpc_code c) {
     std::lock_guard<std::mutex> lock(c->enc_mu);
     if (c->enc) return LDPC_OK;
     const int M = c->d.M, N = c->d.N, W = (N + 63) / 64;
-    std::vector<uint64_t> R;
-    parity_rows(c, R, W);
+    std::vector<uint64_t> H0;
+    parity_rows(c, H0, W);
+    // [H | I_M] by rows, W2 words each
+    const int W2 = (N + M + 63) / 64;
+    std::vector<uint64_t> R((size_t)M * W2, 0ull);
+    for (int m = 0; m < M; ++m) {
+        std::copy(H0.begin() + (size_t)m * W, H0.begin() + (size_t)(m + 1) * W, R.begin() + (size_t)m * W2);
+        const int b = N + m;
+        R[(size_t)m * W2 + (b >> 6)] |= 1ull << (b & 63);
+    }
     // Gauss-Jordan over GF(2), pivot columns taken from n = N-1 down to 0
     std::vector<int32_t> piv;
     int rank = 0;
@@ -321,16 +361,16 @@ ldpc_status enc_build_host(ldpc_code c) {
         const int w = n >> 6;
         const uint64_t b = 1ull << (n & 63);
         int r = rank;
-        while (r < M && !(R[(size_t)r * W + w] & b)) ++r;
+        while (r < M && !(R[(size_t)r * W2 + w] & b)) ++r;
         if (r == M) continue;
-        if (r != rank) std::swap_ranges(R.begin() + (size_t)r * W, R.begin() + (size_t)(r + 1) * W,
-                                        R.begin() + (size_t)rank * W);
-        const uint64_t *pr = R.data() + (size_t)rank * W;
+        if (r != rank) std::swap_ranges(R.begin() + (size_t)r * W2, R.begin() + (size_t)(r + 1) * W2,
+                                        R.begin() + (size_t)rank * W2);
+        const uint64_t *pr = R.data() + (size_t)rank * W2;
         for (int q = 0; q < M; ++q) {
             if (q == rank) continue;
-            uint64_t *x = R.data() + (size_t)q * W;
+            uint64_t *x = R.data() + (size_t)q * W2;
             if (x[w] & b)
-                for (int t = 0; t < W; ++t) x[t] ^= pr[t];
+                for (int t = 0; t < W2; ++t) x[t] ^= pr[t];
         }
         piv.push_back(n);
         ++rank;
@@ -355,21 +395,33 @@ ldpc_status enc_build_host(ldpc_code c) {
         }
     e->k = (int64_t)e->info_pos.size();
     e->kc = (int)((e->k + 31) / 32);
-    e->kc4 = (e->kc + 3) / 4 * 4;
+    e->mc = (M + 31) / 32;
+    e->mc4 = (e->mc + 3) / 4 * 4;
     e->rpad = (rank + kEncRows - 1) / kEncRows * kEncRows;
     e->NW = (N + 31) / 32;
-    e->At.assign((size_t)e->kc4 * e->rpad, 0u);
+    e->ld = (size_t)N + (size_t)M;
+    // T: the identity block of the reduced rows, column-chunk-major
+    e->Tt.assign((size_t)e->mc4 * e->rpad, 0u);
     for (int i = 0; i < rank; ++i) {
-        const uint64_t *row = R.data() + (size_t)i * W;
+        const uint64_t *row = R.data() + (size_t)i * W2;
+        for (int m = 0; m < M; ++m) {
+            const int bit = N + m;
+            if ((row[bit >> 6] >> (bit & 63)) & 1ull) e->Tt[(size_t)(m >> 5) * e->rpad + i] |= 1u << (m & 31);
+        }
+    }
+    // H_info by rows
+    e->hrp.assign(M + 1, 0);
+    for (int m = 0; m < M; ++m) {
+        const uint64_t *row = H0.data() + (size_t)m * W;
         for (int w = 0; w < W; ++w) {
             uint64_t x = row[w];
             while (x) {
                 const int n = 64 * w + __builtin_ctzll(x);
                 x &= x - 1;
-                const int j = idx[n];
-                if (j >= 0) e->At[(size_t)(j >> 5) * e->rpad + i] |= 1u << (j & 31);
+                if (idx[n] >= 0) e->hj.push_back(idx[n]);
             }
         }
+        e->hrp[m + 1] = (int)e->hj.size();
     }
     c->enc = e;
     return LDPC_OK;
@@ -380,13 +432,14 @@ ldpc_status enc_ensure_device(ldpc_code c, size_t groups) {
     if (st != LDPC_OK) return st;
     std::lock_guard<std::mutex> lock(c->enc_mu);
     ldpc_encoder_s *e = c->enc;
-    const int N = e->N;
+    const int N = e->N, M = e->M;
     if (!e->dmem) {
-        const size_t at_words = e->At.size(), bytes = (at_words + (size_t)N + (size_t)e->NW) * 4;
+        const size_t nt = e->Tt.size(), nj = e->hj.size();
+        const size_t words = nt + (size_t)(M + 1) + nj + (size_t)N + (size_t)e->NW;
         void *mem = nullptr;
-        if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+        if (cudaMalloc(&mem, words * 4) != cudaSuccess) {
             cudaGetLastError();
-            set_error("device allocation of the encoder tables (%zu bytes) failed", bytes);
+            set_error("device allocation of the encoder tables (%zu bytes) failed", words * 4);
             return LDPC_ENOMEM;
         }
         std::vector<int> src(N);
@@ -398,25 +451,29 @@ ldpc_status enc_ensure_device(ldpc_code c, size_t groups) {
         }
         for (int i = 0; i < e->rank; ++i) src[e->par_pos[i]] = (int)(e->k + i);
         uint32_t *base = (uint32_t *)mem;
-        cudaError_t ce = cudaMemcpy(base, e->At.data(), at_words * 4, cudaMemcpyHostToDevice);
-        if (ce == cudaSuccess) ce = cudaMemcpy(base + at_words, src.data(), (size_t)N * 4, cudaMemcpyHostToDevice);
-        if (ce == cudaSuccess)
-            ce = cudaMemcpy(base + at_words + N, imask.data(), (size_t)e->NW * 4, cudaMemcpyHostToDevice);
+        uint32_t *p_hrp = base + nt, *p_hj = p_hrp + M + 1, *p_src = p_hj + nj, *p_im = p_src + N;
+        cudaError_t ce = cudaMemcpy(base, e->Tt.data(), nt * 4, cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess) ce = cudaMemcpy(p_hrp, e->hrp.data(), (size_t)(M + 1) * 4, cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess && nj) ce = cudaMemcpy(p_hj, e->hj.data(), nj * 4, cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess) ce = cudaMemcpy(p_src, src.data(), (size_t)N * 4, cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess) ce = cudaMemcpy(p_im, imask.data(), (size_t)e->NW * 4, cudaMemcpyHostToDevice);
         if (ce != cudaSuccess) {
             cudaFree(mem);
             return cuda_fail(ce, "cudaMemcpy(encoder tables)");
         }
         e->dmem = mem;
-        e->d_At = base;
-        e->d_src = (const int *)(base + at_words);
-        e->d_imask = base + at_words + N;
+        e->d_Tt = base;
+        e->d_hrp = (const int *)p_hrp;
+        e->d_hj = (const int *)p_hj;
+        e->d_src = (const int *)p_src;
+        e->d_imask = p_im;
     }
     if (groups > e->sl_groups) {
         LDPC_CUDA_TRY(cudaDeviceSynchronize());
         cudaFree(e->sl);
         e->sl = nullptr;
         e->sl_groups = 0;
-        if (cudaMalloc(&e->sl, groups * (size_t)N * 4) != cudaSuccess) {
+        if (cudaMalloc(&e->sl, groups * e->ld * 4) != cudaSuccess) {
             cudaGetLastError();
             e->sl = nullptr;
             set_error("device allocation of the encoder scratch (%zu groups) failed", groups);
