@@ -393,6 +393,46 @@ def ldpccc_decode(Hconv, geo: dict, T: int, I: int, mu, clip: float = 30.0, nthr
     return post, hard, decided, log[: min(int(log_n[0]), log_cap)]
 
 
+def ldpccc_tanner_geometry(shifts, p: int) -> dict:
+    """Frames of p time instants: c = L p bits, J p checks per layer, memory 1 frame (0 if
+    every delay is 0); "delay" is the largest shift, the code's memory in time instants."""
+    shifts = np.asarray(shifts, dtype=np.int64)
+    J, L = shifts.shape
+    amax = int(shifts.max()) if (shifts >= 0).any() else 0
+    return {"Lambda": 1, "ms": 1 if amax > 0 else 0, "c": L * p, "cb": J * p, "b": (L - J) * p, "delay": amax}
+
+
+def ldpccc_tanner(shifts, p: int, T: int):
+    """H_[0,T) of the time-invariant LDPCCC whose polynomial parity-check matrix has entries
+    D^{a_jl} (a_jl = -1: no entry): check j at time instant t involves bit l at instant t - a_jl,
+    instants before 0 do not exist.  Instant t = F p + tau belongs to frame F; bit (l, tau) of
+    frame F is column F c + l p + tau, check (j, tau) of layer F is row F cb + j p + tau.
+    """
+    import scipy.sparse as sp
+
+    shifts = np.asarray(shifts, dtype=np.int64)
+    J, L = shifts.shape
+    geo = ldpccc_tanner_geometry(shifts, p)
+    c, cb = geo["c"], geo["cb"]
+    rows, cols = [], []
+    for j in range(J):
+        for l in range(L):
+            a = int(shifts[j, l])
+            if a < 0:
+                continue
+            t = np.arange(T * p, dtype=np.int64)  # check instants
+            tb = t - a                             # bit instants
+            keep = tb >= 0
+            t, tb = t[keep], tb[keep]
+            rows.append((t // p) * cb + j * p + t % p)
+            cols.append((tb // p) * c + l * p + tb % p)
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    Hc = sp.csr_matrix((np.ones(len(rows), dtype=np.uint8), (rows, cols)), shape=(T * cb, T * c))
+    Hc.sort_indices()
+    return Hc, geo
+
+
 def circulant_index(row_ptr, col, p: int, L: int) -> np.ndarray:
     """Circulant block j*L + l of every edge of a QC code (row m = j*p + r, column n = l*p + k)."""
     row_ptr = np.asarray(row_ptr)

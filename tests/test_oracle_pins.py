@@ -500,3 +500,70 @@ def test_channel_with_codeword_shifts_by_bpsk_symbol():
     want = (2.0 * (x + sigma * g0) / (sigma * sigma)).astype(np.float32)
     assert np.array_equal(m1, want)
     assert np.allclose(m1.astype(np.float64) - m0, -4.0 * cw.astype(np.float64) / sigma**2, atol=1e-5)
+
+
+# --------------------------------------------------------------------------
+# Time-invariant LDPCCC with delays D^{a_jl} (the Tanner unwrapping of a QC base)
+# --------------------------------------------------------------------------
+def test_tanner_ldpccc_folds_to_qc_code():
+    """Reading every bit instant modulo p (tail-biting one frame) turns a complete check layer into the
+    QC code whose circulants have the negated shifts: check tau of block row j meets bit tau - a."""
+    J, L, p, T = 3, 6, 16, 5
+    shifts = synth.qc_shifts(J, L, p, seed=12, zero_blocks=2)
+    Hc, geo = oracle.ldpccc_tanner(shifts, p, T)
+    c, cb = geo["c"], geo["cb"]
+    assert (c, cb, geo["ms"], geo["delay"]) == (L * p, J * p, 1, int(shifts.max()))
+    neg = np.where(shifts >= 0, (-shifts) % p, -1)
+    want = oracle.qc_parity_check(neg, p)
+    for F in range(1, T):  # layer 0 lacks the edges to instants before 0
+        layer = Hc[F * cb:(F + 1) * cb].tocoo()
+        folded = np.zeros((cb, c), dtype=np.uint8)
+        folded[layer.row, layer.col % c] = 1
+        assert np.array_equal(folded, want)
+        assert layer.col.min() >= (F - 1) * c and layer.col.max() < (F + 1) * c  # memory one frame
+
+
+def test_tanner_ldpccc_delays_are_the_shifts():
+    """Check j at instant t involves bit l at instant t - a_jl: the instant differences of each row are the
+    row's shifts, so the syndrome-former memory in instants is the largest shift."""
+    J, L, p, T = 3, 6, 16, 4
+    shifts = synth.qc_shifts(J, L, p, seed=3)
+    Hc, geo = oracle.ldpccc_tanner(shifts, p, T)
+    c, cb = geo["c"], geo["cb"]
+    for row in range(cb * T):
+        F, rem = divmod(row, cb)
+        j, tau = divmod(rem, p)
+        t = F * p + tau
+        cols = Hc.indices[Hc.indptr[row]:Hc.indptr[row + 1]]
+        got = sorted((int(col % c) // p, t - ((col // c) * p + (col % c) % p)) for col in cols)
+        want = sorted((l, int(shifts[j, l])) for l in range(L) if shifts[j, l] >= 0 and t - shifts[j, l] >= 0)
+        assert got == want
+    assert geo["delay"] == int(shifts.max())
+
+
+def test_tanner_ldpccc_zero_delays_is_block_decoding():
+    """All delays 0: frames decouple (ms = 0) and I processors equal I iterations of Algorithm 1 on the
+    block code with identity circulants."""
+    J, L, p, I, T = 3, 6, 5, 4, 10
+    shifts = np.zeros((J, L), dtype=np.int64)
+    Hc, geo = oracle.ldpccc_tanner(shifts, p, T)
+    assert geo["ms"] == 0
+    c = geo["c"]
+    mu = synth.gaussian_llrs(1, T * c, seed=4, ebn0_db=2.0, rate=0.5)[0]
+    post, hard, decided, _ = oracle.ldpccc_decode(Hc, geo, T, I, mu)
+    rp, col = oracle.csr_rows(oracle.qc_parity_check(shifts, p))
+    bp, bh, _, _ = oracle.sp_decode(rp, col, c, mu.reshape(T, c), max_iter=I)
+    nd = T - I + 1
+    assert decided[0].sum() == nd
+    assert np.allclose(post[0].reshape(T, c)[:nd], bp[:nd], atol=1e-12)
+    assert np.array_equal(hard[0].reshape(T, c)[:nd], bh[:nd])
+
+
+def test_tanner_ldpccc_noiseless_stream_decodes_to_zero():
+    J, L, p, I, T = 3, 6, 8, 4, 20
+    shifts = synth.qc_shifts(J, L, p, seed=1)
+    Hc, geo = oracle.ldpccc_tanner(shifts, p, T)
+    mu = np.full((2, T * geo["c"]), 5.0, dtype=np.float32)
+    post, hard, decided, _ = oracle.ldpccc_decode(Hc, geo, T, I, mu)
+    assert decided.sum() == 2 * (T - I * 2 + 1)
+    assert not hard.any()
