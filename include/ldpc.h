@@ -275,8 +275,22 @@ ldpc_status ldpc_ber_sim(ldpc_code code, double ebn0_db, uint64_t seed, uint64_t
  */
 ldpc_status ldpccc_create(const int32_t *shifts, int32_t J, int32_t L, int32_t p, int32_t I, int32_t gamma,
                           ldpccc *out);
+/*
+ * ldpccc_create_tanner -- the same pipelined decoder for the time-invariant
+ * LDPCCC whose polynomial parity-check matrix is [D^{a_jl}] (the unwrapping of
+ * a QC base with its shifts as delays, Tanner et al. 2004, which Sec. II-D
+ * cites as another construction without specifying it): check j
+ * at time instant t involves bit l at instant t - a_jl (a_jl = -1: none), so
+ * the syndrome-former memory in instants is the largest shift.  Frames are p
+ * instants (c = L p bits, layers of J p checks, b = (L - J) p), which makes the
+ * code a memory-1 LDPCCC (ms = 1; 0 when every shift is 0) with one frame type
+ * (ldpccc_dims reports Lambda = 1); every other call behaves as for
+ * ldpccc_create, with Lambda read as ms + 1 in the slot arithmetic.
+ */
+ldpc_status ldpccc_create_tanner(const int32_t *shifts, int32_t J, int32_t L, int32_t p, int32_t I, int32_t gamma,
+                                 ldpccc *out);
 ldpc_status ldpccc_destroy(ldpccc cc);
-/* c, b, ms and Lambda of the derived code (any pointer may be NULL). */
+/* c, b, ms and Lambda (the period in frames) of the code (any pointer may be NULL). */
 ldpc_status ldpccc_dims(ldpccc cc, int32_t *c, int32_t *b, int32_t *ms, int32_t *lambda);
 /* Empty the pipeline: the next window's first frame is frame 0 of every stream. */
 ldpc_status ldpccc_reset(ldpccc cc);
@@ -285,7 +299,7 @@ ldpc_status ldpccc_reset(ldpccc cc);
  * frame of every stream enters processor 1, the I check layers and then the I
  * frames in the decoder are updated (eqs. ldpccc_bph, ldpccc_bpvs), and the
  * frame leaving processor I is decided (eq. ldpccc_hrddcs).  Frame f is decided
- * at slot f + I*Lambda - 1, so the first I*Lambda - 1 slots after a reset emit
+ * at slot f + I*(ms+1) - 1, so the first I*(ms+1) - 1 slots after a reset emit
  * nothing; the decoder state carries over to the next call (continuous decoding).
  *   llr:   [gamma][T][c] float channel LLRs of the T arriving frames (mu = 2y/sigma^2).
  *   clip:  LLR clip (e.g. 30), applied to channel LLRs, messages and posteriors.

@@ -74,6 +74,8 @@ _SIGNATURES = [
                                               P, P, P]),
     ("ldpccc_create", ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                      ctypes.c_int32, P]),
+    ("ldpccc_create_tanner", ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_int32, P]),
     ("ldpccc_destroy", ctypes.c_int, [P]),
     ("ldpccc_dims", ctypes.c_int, [P, P, P, P, P]),
     ("ldpccc_reset", ctypes.c_int, [P]),
@@ -247,6 +249,18 @@ def ldpccc_create(shifts, p: int, I: int, gamma: int) -> int:
     return h.value
 
 
+def ldpccc_create_tanner(shifts, p: int, I: int, gamma: int) -> int:
+    """Time-invariant LDPCCC with delays D^{a_jl}; frames of p time instants."""
+    import numpy as np
+
+    a = np.ascontiguousarray(np.asarray(shifts, dtype=np.int32))
+    J, L = a.shape
+    h = ctypes.c_void_p()
+    _check(lib().ldpccc_create_tanner(a.ctypes.data_as(P), J, L, p, I, gamma, ctypes.byref(h)),
+           "ldpccc_create_tanner")
+    return h.value
+
+
 def ldpccc_destroy(cc: int):
     _check(lib().ldpccc_destroy(cc), "ldpccc_destroy")
 
@@ -279,8 +293,9 @@ def ldpccc_channel(cc: int, ebn0_db: float, seed: int, first_frame: int, out, st
 class LDPCCC:
     """Owning wrapper of an ldpccc handle."""
 
-    def __init__(self, shifts, p: int, I: int, gamma: int):
-        self.handle = ldpccc_create(shifts, p, I, gamma)
+    def __init__(self, shifts, p: int, I: int, gamma: int, tanner: bool = False):
+        """tanner: the time-invariant code with delays D^{a_jl} instead of the Sec. II-D unwrapping."""
+        self.handle = (ldpccc_create_tanner if tanner else ldpccc_create)(shifts, p, I, gamma)
         d = ldpccc_dims(self.handle)
         self.c, self.b, self.ms, self.Lambda = d["c"], d["b"], d["ms"], d["Lambda"]
         self.I, self.gamma = I, gamma

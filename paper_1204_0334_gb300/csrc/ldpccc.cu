@@ -14,6 +14,12 @@
 // layers go in one check-pass launch and all I frames in one variable-pass
 // launch (Sec. IV-B-3: "processed in parallel").
 //
+// Time-invariant variant (ldpccc_create_tanner): the polynomial parity-check matrix
+// [D^{a_jl}] -- check j at time instant t meets bit l at instant t - a_jl.  Frames of
+// p instants (c = L p, layers of J p checks, one frame type) give a memory-1 code: check
+// (j, tau) of layer R meets bit (l, tau - a) of frame R when tau >= a, else bit
+// (l, tau - a + p) of frame R - 1.  Algorithm 2 runs unchanged with ms = 1.
+//
 // Memory (the "moving processors" of Sec. IV-B-2: relabelling, no copies).
 // Frame F lives in ring slot F mod (I*Lambda) from its arrival until its
 // decision; its channel LLRs in mu[slot][P][c][32] and its J*c edge messages in
@@ -33,7 +39,9 @@
 
 struct ldpccc_s {
     ldpc::QcDesc d;          // base code
-    int lam, Jb, Lb, c, cb, ms, I, gamma, P, ring;
+    int lam, Jb, Lb, c, cb, ms, I, gamma, P, ring;  // lam: frames between processors (ms + 1)
+    int types = 1;           // frame / layer types (period): Lambda, or 1 for the time-invariant code
+    int tanner = 0;          // 1: delays D^{a_jl} instead of the sub-block unwrapping
     int device = 0;
     long long t = 0;         // next slot (= index of the next frame to enter)
     float *mu = nullptr;     // [ring][P][c][32]
@@ -48,6 +56,7 @@ namespace ldpc {
 
 struct CcDesc {
     int lam, Jb, Lb, c, cb, ms, I, P, ring, Ef;
+    int tanner;  // per-edge frame lag from the row and the delay (time-invariant code)
 };
 
 __device__ __forceinline__ int mod_pos(long long x, int m) {
@@ -153,10 +162,16 @@ cc_cn_pipe_kernel(const QcDesc d, CcDesc g, CcGeo q, uint32_t *__restrict__ msg,
         if (l >= d.L || r >= d.p) return;
         const int sh = s_sh[o.j * d.L + l];
         if (sh < 0) return;
-        const int back = o.i * g.lam + s_dl[l];  // t - F
-        if (back > sc.t) return;                 // frame not yet arrived
-        int k = r + sh;
-        if (k >= d.p) k -= d.p;
+        int back = o.i * g.lam + s_dl[l];  // t - F
+        int k;
+        if (g.tanner) {  // bit instant tau - a, in the previous frame when negative
+            k = r - sh;
+            if (k < 0) k += d.p, ++back;
+        } else {
+            k = r + sh;
+            if (k >= d.p) k -= d.p;
+        }
+        if (back > sc.t) return;  // frame not yet arrived
         int fs = sc.tm - back;
         if (fs < 0) fs += g.ring;
         dstl = (fs * g.P + o.pk) * g.Ef + s_eb[o.j * d.L + l] + k;
@@ -392,15 +407,16 @@ __global__ void cc_channel_kernel(float *__restrict__ out, int gamma, int T, int
 }
 
 static CcDesc cc_desc(const ldpccc_s *cc) {
-    return CcDesc{cc->lam, cc->Jb, cc->Lb, cc->c, cc->cb, cc->ms, cc->I, cc->P, cc->ring, cc->d.J * cc->c};
+    return CcDesc{cc->lam, cc->Jb, cc->Lb, cc->c, cc->cb, cc->ms, cc->I, cc->P, cc->ring, cc->d.J * cc->c,
+                  cc->tanner};
 }
 
 static SlotC slot_consts(const ldpccc_s *cc, long long t) {
     SlotC c;
     c.t = (int)std::min<long long>(t, 1ll << 30);
     c.tm = (int)(t % cc->ring);
-    c.a = (int)(t % cc->lam);
-    c.bv = (int)(((t - cc->ms) % cc->lam + cc->lam) % cc->lam);
+    c.a = (int)(t % cc->types);
+    c.bv = (int)(((t - cc->ms) % cc->types + cc->types) % cc->types);
     return c;
 }
 
@@ -439,8 +455,8 @@ using namespace ldpc;
 
 extern "C" {
 
-ldpc_status ldpccc_create(const int32_t *shifts, int32_t J, int32_t L, int32_t p, int32_t I, int32_t gamma,
-                          ldpccc *out) {
+static ldpc_status cc_create(const int32_t *shifts, int32_t J, int32_t L, int32_t p, int32_t I, int32_t gamma,
+                             bool tanner, ldpccc *out) {
     if (!out) {
         set_error("out is NULL");
         return LDPC_EINVAL;
@@ -461,21 +477,33 @@ ldpc_status ldpccc_create(const int32_t *shifts, int32_t J, int32_t L, int32_t p
     }
     cc->d = base->d;
     ldpc_code_destroy(base);
-    cc->lam = std::gcd(J, L);
-    cc->Jb = J / cc->lam;
-    cc->Lb = L / cc->lam;
+    if (tanner) {
+        int amax = 0;
+        for (int x = 0; x < J * L; ++x) amax = std::max(amax, (int)shifts[x]);
+        cc->tanner = 1;
+        cc->types = 1;
+        cc->Jb = J;
+        cc->Lb = L;
+        cc->ms = amax > 0 ? 1 : 0;
+        cc->lam = cc->ms + 1;
+    } else {
+        cc->types = std::gcd(J, L);
+        cc->Jb = J / cc->types;
+        cc->Lb = L / cc->types;
+        cc->ms = cc->types - 1;
+        cc->lam = cc->types;
+    }
     cc->c = cc->Lb * p;
     cc->cb = cc->Jb * p;
-    cc->ms = cc->lam - 1;
     cc->I = I;
     cc->gamma = gamma;
     cc->P = (gamma + 31) / 32;
     cc->ring = I * cc->lam;
     // the passes index 128-byte package lines and work items with 32-bit integers
     if ((long long)cc->ring * cc->P * J * cc->c >= (1ll << 31) || (long long)I * cc->P * J * cc->c >= (1ll << 31)) {
+        const long long lines = (long long)cc->ring * cc->P * J * cc->c;
         delete cc;
-        set_error("I * Lambda * ceil(gamma / 32) * J * c = %lld package lines exceeds 2^31",
-                  (long long)I * std::gcd(J, L) * ((gamma + 31) / 32) * J * (L / std::gcd(J, L)) * (long long)p);
+        set_error("I * (ms + 1) * ceil(gamma / 32) * J * c = %lld package lines exceeds 2^31", lines);
         return LDPC_EINVAL;
     }
     cudaGetDevice(&cc->device);
@@ -491,6 +519,16 @@ ldpc_status ldpccc_create(const int32_t *shifts, int32_t J, int32_t L, int32_t p
     }
     *out = cc;
     return LDPC_OK;
+}
+
+ldpc_status ldpccc_create(const int32_t *shifts, int32_t J, int32_t L, int32_t p, int32_t I, int32_t gamma,
+                          ldpccc *out) {
+    return cc_create(shifts, J, L, p, I, gamma, false, out);
+}
+
+ldpc_status ldpccc_create_tanner(const int32_t *shifts, int32_t J, int32_t L, int32_t p, int32_t I, int32_t gamma,
+                                 ldpccc *out) {
+    return cc_create(shifts, J, L, p, I, gamma, true, out);
 }
 
 ldpc_status ldpccc_destroy(ldpccc cc) {
@@ -512,7 +550,7 @@ ldpc_status ldpccc_dims(ldpccc cc, int32_t *c, int32_t *b, int32_t *ms, int32_t 
     if (c) *c = cc->c;
     if (b) *b = cc->c - cc->cb;
     if (ms) *ms = cc->ms;
-    if (lambda) *lambda = cc->lam;
+    if (lambda) *lambda = cc->types;
     return LDPC_OK;
 }
 

@@ -297,8 +297,6 @@ __global__ void nm_loss_out(const double *acc, float *out) { *out = (float)*acc;
 // ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
-static size_t es(int msg) { return msg == LDPC_MSG_F16 ? 2 : 4; }
-
 static ldpc_status nm_alloc(ldpc_code c, ldpc_noms_state &w, size_t frames, size_t nck, size_t nseg) {
     const size_t E = c->d.E, N = c->d.N;
     const size_t fr = (frames + 31) / 32 * 32;

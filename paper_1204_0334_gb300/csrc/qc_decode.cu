@@ -88,7 +88,7 @@ cn_sp_first_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__re
     uint32_t par_all[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) par_all[v] = __popc(neg[v]) & 1u;
-    if (NOMS) {
+    if constexpr (NOMS) {
         // normalized/offset min-sum: ph[] holds |beta|; alpha = sign * max(w * m - o, 0)
         float mn1[V], mn2[V];
 #pragma unroll
@@ -121,41 +121,42 @@ cn_sp_first_kernel(const QcDesc d, uint32_t *__restrict__ msg, const float *__re
             pmsg[(eo[l] + k) * 32] = Lane<V>::pack(a);
         }
         return;
-    }
-    // prefix sums, then the backward sweep adds the suffix sums
-    float pre[DCMAX][V];
-    {
-        float acc[V];
+    } else {
+        // prefix sums, then the backward sweep adds the suffix sums
+        float pre[DCMAX][V];
+        {
+            float acc[V];
 #pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] = 0.0f;
+            for (int v = 0; v < V; ++v) acc[v] = 0.0f;
 #pragma unroll
-        for (int l = 0; l < DCMAX; ++l)
+            for (int l = 0; l < DCMAX; ++l)
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                pre[l][v] = acc[v];
-                acc[v] += ph[l][v];
-            }
-    }
-    float suf[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) suf[v] = 0.0f;
-#pragma unroll
-    for (int l = DCMAX - 1; l >= 0; --l) {
-        const bool on = l < d.L && sh[l] >= 0;
-        if (on) {
-            int k = r + sh[l];
-            if (k >= d.p) k -= d.p;
-            float a[V];
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const float mag = fminf(phi_f(pre[l][v] + suf[v]), clip);
-                const uint32_t s = par_all[v] ^ ((neg[v] >> l) & 1u);
-                a[v] = s ? -mag : mag;
-            }
-            if (lane_on) pmsg[(eo[l] + k) * 32] = Lane<V>::pack(a);
+                for (int v = 0; v < V; ++v) {
+                    pre[l][v] = acc[v];
+                    acc[v] += ph[l][v];
+                }
         }
+        float suf[V];
 #pragma unroll
-        for (int v = 0; v < V; ++v) suf[v] += ph[l][v];
+        for (int v = 0; v < V; ++v) suf[v] = 0.0f;
+#pragma unroll
+        for (int l = DCMAX - 1; l >= 0; --l) {
+            const bool on = l < d.L && sh[l] >= 0;
+            if (on) {
+                int k = r + sh[l];
+                if (k >= d.p) k -= d.p;
+                float a[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const float mag = fminf(phi_f(pre[l][v] + suf[v]), clip);
+                    const uint32_t s = par_all[v] ^ ((neg[v] >> l) & 1u);
+                    a[v] = s ? -mag : mag;
+                }
+                if (lane_on) pmsg[(eo[l] + k) * 32] = Lane<V>::pack(a);
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) suf[v] += ph[l][v];
+        }
     }
 }
 

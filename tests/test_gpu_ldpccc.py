@@ -28,10 +28,10 @@ def pkg():
     return p
 
 
-def run_gpu(pkg, shifts, p, I, mu, windows):
+def run_gpu(pkg, shifts, p, I, mu, windows, tanner=False):
     """mu: [gamma][T][c] numpy; windows: list of window lengths summing to T."""
     g, T, c = mu.shape
-    cc = pkg.LDPCCC(shifts, p, I, g)
+    cc = pkg.LDPCCC(shifts, p, I, g, tanner=tanner)
     assert cc.c == c
     hard = np.zeros((g, T, c), dtype=np.uint8)
     post = np.zeros((g, T, c), dtype=np.float32)
@@ -49,15 +49,15 @@ def run_gpu(pkg, shifts, p, I, mu, windows):
     return hard, post, decided
 
 
-def run_oracle(shifts, p, I, mu):
+def run_oracle(shifts, p, I, mu, tanner=False):
     g, T, c = mu.shape
-    Hc, geo = oracle.ldpccc_unwrap(shifts, p, T)
+    Hc, geo = (oracle.ldpccc_tanner if tanner else oracle.ldpccc_unwrap)(shifts, p, T)
     po, ho, dec, _ = oracle.ldpccc_decode(Hc, geo, T, I, mu.reshape(g, T * c), nthreads=8)
     return Hc, geo, po.reshape(g, T, c), ho.reshape(g, T, c), dec
 
 
-def compare(shifts, p, I, mu, hard, post, decided, label):
-    Hc, geo, po, ho, dec = run_oracle(shifts, p, I, mu)
+def compare(shifts, p, I, mu, hard, post, decided, label, tanner=False):
+    Hc, geo, po, ho, dec = run_oracle(shifts, p, I, mu, tanner)
     g, T, c = mu.shape
     assert np.array_equal(dec[0].astype(bool), decided), label
     sel = decided
@@ -68,7 +68,7 @@ def compare(shifts, p, I, mu, hard, post, decided, label):
         rng = np.random.default_rng(5)
         up = rng.integers(0, 2, size=mu.shape).astype(bool)
         m2 = np.where(up, np.nextafter(mu, np.float32(np.inf)), np.nextafter(mu, np.float32(-np.inf)))
-        _, _, p2, _, _ = run_oracle(shifts, p, I, m2.astype(np.float32))
+        _, _, p2, _, _ = run_oracle(shifts, p, I, m2.astype(np.float32), tanner)
         resp = np.abs(p2[:, sel] - po[:, sel]).max(axis=2, keepdims=True)
         allowed = np.maximum(REL * np.maximum(1.0, np.abs(po[:, sel])), SENS * resp)
         assert (dev <= allowed).all(), f"{label}: deviation {dev.max():.3e}"
@@ -141,3 +141,47 @@ def test_ldpccc_channel_matches_oracle(pkg):
         tol = s2 * (8e-7 * sigma * np.abs(gz) + 2.4e-7 * (1 + np.abs(1 + sigma * gz))) + 1.2e-7 * np.abs(mu64)
         assert np.all(np.abs(out[s] - mu64) <= tol + 1e-7)
     cc.close()
+
+
+# --------------------------------------------------------------------------
+# time-invariant code with delays D^{a_jl} (frames of p instants, ms = 1)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("J,L,p,I,gamma,T,windows,ebn0,zb", [
+    (3, 6, 16, 5, 40, 40, [40], 1.5, 0),         # ragged packages (40 streams)
+    (4, 8, 8, 3, 33, 30, [11, 19], 2.0, 0),      # two windows (continuity)
+    (4, 8, 9, 3, 32, 25, [25], 2.0, 5),          # zero blocks
+    (2, 6, 20, 6, 64, 40, [1, 39], 1.5, 0),      # a one-frame window first
+])
+def test_tanner_ldpccc_matches_oracle(pkg, J, L, p, I, gamma, T, windows, ebn0, zb):
+    shifts = synth.qc_shifts(J, L, p, seed=J * 10 + L + zb, zero_blocks=zb)
+    c = L * p
+    mu = synth.gaussian_llrs(gamma, T * c, seed=T + 1, ebn0_db=ebn0, rate=1 - J / L).reshape(gamma, T, c)
+    hard, post, decided = run_gpu(pkg, shifts, p, I, mu, windows, tanner=True)
+    compare(shifts, p, I, mu, hard, post, decided, f"tanner {J}x{L} p={p} I={I}", tanner=True)
+
+
+def test_tanner_ldpccc_dims_and_zero_delays(pkg):
+    """Dimensions of the time-invariant code; all delays 0 gives ms = 0 (frames decode independently),
+    decided one slot after I - 1 further frames, as the oracle's block decoding."""
+    shifts = synth.qc_shifts(3, 6, 16, seed=2)
+    cc = pkg.LDPCCC(shifts, 16, 4, 32, tanner=True)
+    assert (cc.c, cc.b, cc.ms, cc.Lambda) == (96, 48, 1, 1)
+    cc.close()
+    z = np.zeros((3, 6), dtype=np.int64)
+    mu = synth.gaussian_llrs(32, 12 * 30, seed=7, ebn0_db=2.0, rate=0.5).reshape(32, 12, 30)
+    hard, post, decided = run_gpu(pkg, z, 5, 4, mu, [12], tanner=True)
+    assert decided.sum() == 12 - 4 + 1
+    compare(z, 5, 4, mu, hard, post, decided, "tanner zero delays", tanner=True)
+
+
+def test_tanner_ldpccc_full_size_sampled(pkg):
+    """3x6 base, p = 128 delays (memory up to 127 instants; frames of 128 instants, c = 768), I = 30
+    processors, 1024 streams: two sampled streams against the oracle over 100 frames."""
+    J, L, p, I, g, T = 3, 6, 128, 30, 1024, 100
+    shifts = synth.qc_shifts(J, L, p, seed=3)
+    c = L * p
+    mu = synth.gaussian_llrs(g, T * c, seed=12, ebn0_db=2.0, rate=0.5).reshape(g, T, c)
+    hard, post, decided = run_gpu(pkg, shifts, p, I, mu, [40, 60], tanner=True)
+    assert decided.sum() == T - I * 2 + 1
+    idx = [0, 901]
+    compare(shifts, p, I, mu[idx], hard[idx], post[idx], decided, "tanner cfg3 sampled", tanner=True)
