@@ -198,3 +198,48 @@ def test_encoder_argument_errors(pkg):
     with pytest.raises(pkg.LdpcError) as e:
         pkg.ldpc_encode(code.handle, host, cw)
     assert e.value.status == 1 and "device" in str(e.value)
+
+
+@pytest.mark.parametrize("case", ["noms_f32", "noms_f16", "sp_f16"])
+def test_ber_sim_random_codewords_other_decoders(pkg, case):
+    """Random codewords with the learned min-sum (per-iteration parameter rows) and with FP16 storage (two
+    frames per lane word): FP32 exactly the batch path's counts; FP16 statistically (the batch decoder's first
+    check pass reads the FP32 channel LLRs, the continuous one their FP16 rounding)."""
+    shifts = synth.qc_shifts(3, 6, 64, seed=1)
+    code = pkg.QCCode(shifts, 64)
+    T, frames, gamma, ebn0, seed, first = 9, 900, 128, 1.75, 31, 7
+    msg = pkg.MSG_F16 if case.endswith("f16") else pkg.MSG_F32
+    kw = dict(max_iter=T, early_stop=1, msg=msg)
+    prm = None
+    if case.startswith("noms"):
+        rng = np.random.default_rng(4)
+        p = np.stack([rng.uniform(0.7, 1.0, size=(T, 18)), rng.uniform(0.0, 0.3, size=(T, 18))], axis=-1)
+        prm = torch.from_numpy(p.astype(np.float32)).cuda()
+        kw["algo"] = pkg.ALGO_NOMS
+    o = pkg.default_opts(codewords=pkg.CODEWORDS_RANDOM, **kw)
+    if prm is not None:
+        o.noms_params = prm.data_ptr()
+    res = pkg.ldpc_ber_sim(code.handle, ebn0, seed, first, frames, 10 ** 9, gamma, o)
+    k, pos = code.info_set()
+    _, cw = code.random_codewords(seed, first, frames, want_info=False)
+    llr = code.channel_codewords(ebn0, seed, first, cw)
+    hard = torch.empty((frames, code.N), dtype=torch.uint8, device="cuda")
+    iters = torch.empty(frames, dtype=torch.int32, device="cuda")
+    ok = torch.empty(frames, dtype=torch.int32, device="cuda")
+    ob = pkg.default_opts(**kw)
+    if prm is not None:
+        ob.noms_params = prm.data_ptr()
+    pkg.ldpc_decode(code.handle, llr, ob, None, hard, iters, ok)
+    pos_t = torch.from_numpy(pos.astype(np.int64)).cuda()
+    errs = (hard[:, pos_t] != cw[:, pos_t]).sum(dim=1).cpu().numpy().astype(np.int64)
+    okn = ok.cpu().numpy()
+    want = {"frames": frames, "frame_errors": int((errs > 0).sum()), "bit_errors": int(errs.sum()),
+            "iters_sum": int(iters.cpu().numpy().sum()), "undetected": int(((errs > 0) & (okn == 1)).sum())}
+    assert 0 < want["frame_errors"] < frames
+    if msg == pkg.MSG_F32:
+        for key, v in want.items():
+            assert res[key] == v, (key, res[key], v)
+    else:
+        assert res["frames"] == frames
+        assert abs(res["frame_errors"] - want["frame_errors"]) <= max(3, 0.05 * want["frame_errors"])
+        assert abs(res["iters_sum"] - want["iters_sum"]) <= 0.03 * want["iters_sum"]
