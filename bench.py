@@ -63,6 +63,7 @@ def args_parse():
     ap.add_argument("--no-ldpccc", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-sparse", action="store_true")
+    ap.add_argument("--no-noms", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU seconds of the oracle baseline")
     ap.add_argument("--seed", type=int, default=20120403)
     return ap.parse_args()
@@ -308,6 +309,8 @@ def run_ours(a):
         line["ldpccc_tanner"] = ldpccc_bench(a, pkg, stream, tanner=True)
     if not a.no_batch:
         line["hetero_batch"] = batch_bench(a, pkg, stream)
+    if not a.no_noms:
+        line["noms_training"] = noms_training_bench(a, pkg, code, stream)
     if not a.no_sparse:
         line["general_code"] = sparse_bench(a, pkg, code, stream)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -387,6 +390,41 @@ def ldpccc_bench(a, pkg, stream, tanner=False) -> dict:
             "value": g_ * decided * cc.b / (ms / 1e3) / 1e6, "unit": "Mbit/s", "ms_per_slot": ms / (windows * T),
             "achieved_gbs": g_ * slot_bytes * windows * T / (ms / 1e3) / 1e9,
             "bit_errors_last_window": errs}
+
+
+def noms_training_bench(a, pkg, code, stream) -> dict:
+    """One training step of the learned min-sum on the headline code: ldpc_noms_forward + ldpc_noms_backward on
+    1024 frames (3.5 dB), 10 unrolled iterations, FP16 saved messages, a checkpoint every 2 iterations."""
+    import torch
+
+    B, T, ck = 1024, 10, 2
+    llr = torch.empty((B, code.N), dtype=torch.float32, device="cuda")
+    pkg.ldpc_channel(code.handle, 3.5, a.seed, 1 << 45, llr, stream)
+    prm = torch.empty((T, J * L, 2), dtype=torch.float32, device="cuda")
+    prm[..., 0] = 0.8
+    prm[..., 1] = 0.1
+    grad = torch.zeros_like(prm)
+    for _ in range(2):
+        pkg.ldpc_noms_forward(code.handle, llr, prm, pkg.MSG_F16, ck, 30.0, False, stream)
+        pkg.ldpc_noms_backward(code.handle, prm, grad, stream)
+    torch.cuda.synchronize()
+    k = 5
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(3 * k)]
+    for i in range(k):
+        evs[3 * i].record(stream)
+        pkg.ldpc_noms_forward(code.handle, llr, prm, pkg.MSG_F16, ck, 30.0, False, stream)
+        evs[3 * i + 1].record(stream)
+        pkg.ldpc_noms_backward(code.handle, prm, grad, stream)
+        evs[3 * i + 2].record(stream)
+    torch.cuda.synchronize()
+    fwd = sum(evs[3 * i].elapsed_time(evs[3 * i + 1]) for i in range(k)) / k
+    bwd = sum(evs[3 * i + 1].elapsed_time(evs[3 * i + 2]) for i in range(k)) / k
+    # canonical forward bytes per frame-iteration: FP16 messages read + written in both passes, channel LLRs
+    fwd_bytes = B * T * (4 * E_EDGES * 2 + N_BITS * 4)
+    peak = load_peaks().get("hbm_gbs", 6800.0)
+    return {"workload": "learned min-sum training step, n=18360, 1024 frames, 10 iterations, FP16, checkpoint every 2",
+            "frames_per_s": B / ((fwd + bwd) / 1e3), "fwd_ms": fwd, "bwd_ms": bwd, "bwd_over_fwd": bwd / fwd,
+            "fwd_achieved_gbs": fwd_bytes / (fwd / 1e3) / 1e9, "fwd_frac": fwd_bytes / (fwd / 1e3) / 1e9 / peak}
 
 
 def batch_bench(a, pkg, stream) -> dict:

@@ -202,9 +202,14 @@ nm_vn_bwd(const QcDesc d, const float *__restrict__ A, const float *__restrict__
 // backward check step: parameter gradients of iteration l and the adjoint of
 // beta^(l-1).  m_e = |beta_{e*}| with e* the arg-min over the other edges
 // (lowest index among ties): e* = idx2 for e = idx1, else idx1; so only the
-// two smallest inputs of a row receive gradient.  Persistent blocks; parameter
-// sums in shared memory, flushed once per block.
+// two smallest inputs of a row receive gradient.  Persistent warps take items of
+// kBwdRows consecutive rows of one block row j, so every row of an item adds to
+// the same circulants' gradients: each lane keeps its partial sums per edge slot
+// in registers and the warp reduces them once per item (not once per row) into
+// block sums in shared memory, flushed once per block.
 // ---------------------------------------------------------------------------
+constexpr int kBwdRows = 16;
+
 template <int DCMAX, typename S, bool FROM_MU>
 __global__ void __launch_bounds__(kWarps * 32)
 nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict__ GA, const float *__restrict__ prm_l,
@@ -213,77 +218,108 @@ nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict_
     for (int i = threadIdx.x; i < d.J * d.L * 2; i += blockDim.x) sg[i] = 0.0f;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long total = (long long)P * d.M;
+    const int chunks = (d.p + kBwdRows - 1) / kBwdRows;
+    const long long total = (long long)P * d.J * chunks;
     for (long long item = (long long)blockIdx.x * kWarps + warp; item < total; item += (long long)gridDim.x * kWarps) {
-        const int pk = (int)(item / d.M), m = (int)(item - (long long)pk * d.M);
-        const int j = m / d.p, r = m - j * d.p;
-        float ab[DCMAX], sgn[DCMAX];
-        int eid[DCMAX];
-        uint32_t neg = 0u;
-        float mn1 = INFINITY, mn2 = INFINITY;
-        int i1 = -1, i2 = -1;
-#pragma unroll
-        for (int l = 0; l < DCMAX; ++l) {
-            ab[l] = INFINITY;
-            sgn[l] = 0.0f;
-            eid[l] = -1;
-            if (l >= d.L || d.shift[j * d.L + l] < 0) continue;
-            int k = r + d.shift[j * d.L + l];
-            if (k >= d.p) k -= d.p;
-            eid[l] = d.eoff[j * d.L + l] + k;
-            const float x = nm_beta<S, FROM_MU>(bin, d, pk, eid[l], l * d.p + k, lane);
-            ab[l] = fabsf(x);
-            sgn[l] = x > 0.0f ? 1.0f : (x < 0.0f ? -1.0f : 0.0f);
-            neg |= (x < 0.0f ? 1u : 0u) << l;
-            // strict < keeps the lowest index among ties
-            if (ab[l] < mn1) {
-                mn2 = mn1;
-                i2 = i1;
-                mn1 = ab[l];
-                i1 = l;
-            } else if (ab[l] < mn2) {
-                mn2 = ab[l];
-                i2 = l;
-            }
-        }
-        const uint32_t par = __popc(neg) & 1u;
+        const int pk = (int)(item / ((long long)d.J * chunks));
+        const int rem = (int)(item - (long long)pk * d.J * chunks);
+        const int j = rem / chunks, r0 = (rem - j * chunks) * kBwdRows;
+        const int r1 = min(r0 + kBwdRows, d.p);
         const float *prm = prm_l + (size_t)j * d.L * 2;
-        float g1 = 0.0f, g2 = 0.0f;  // adjoints landing on edges i1 and i2
+        float aw[DCMAX], ao[DCMAX];  // this lane's partial gradients of (w, o) per edge slot l
 #pragma unroll
-        for (int l = 0; l < DCMAX; ++l) {
-            float gw = 0.0f, go = 0.0f;
-            if (eid[l] >= 0) {
+        for (int l = 0; l < DCMAX; ++l) aw[l] = ao[l] = 0.0f;
+        // edge index of slot l in row r (-1: absent block)
+        auto edge = [&](int l, int r) -> int {
+            if (l >= d.L) return -1;
+            const int sh = d.shift[j * d.L + l];
+            if (sh < 0) return -1;
+            int k = r + sh;
+            if (k >= d.p) k -= d.p;
+            return d.eoff[j * d.L + l] + k;
+        };
+        for (int r = r0; r < r1; ++r) {
+            // every load of the row first (beta^(l-1) and the adjoints of alpha^(l) do not depend on
+            // each other): one memory round trip per row
+            float xin[DCMAX], ga[DCMAX];
+#pragma unroll
+            for (int l = 0; l < DCMAX; ++l) {
+                xin[l] = 0.0f;
+                ga[l] = 0.0f;
+                const int e = edge(l, r);
+                if (e < 0) continue;
+                const int k = e - d.eoff[j * d.L + l];
+                xin[l] = nm_beta<S, FROM_MU>(bin, d, pk, e, l * d.p + k, lane);
+                ga[l] = GA[((size_t)pk * d.E + e) * 32 + lane];
+            }
+            float ab[DCMAX];
+            uint32_t neg = 0u;
+            float mn1 = INFINITY, mn2 = INFINITY;
+            int i1 = -1, i2 = -1;
+#pragma unroll
+            for (int l = 0; l < DCMAX; ++l) {
+                ab[l] = INFINITY;
+                if (edge(l, r) < 0) continue;
+                const float x = xin[l];
+                ab[l] = fabsf(x);
+                neg |= (x < 0.0f ? 1u : 0u) << l;
+                // strict < keeps the lowest index among ties
+                if (ab[l] < mn1) {
+                    mn2 = mn1;
+                    i2 = i1;
+                    mn1 = ab[l];
+                    i1 = l;
+                } else if (ab[l] < mn2) {
+                    mn2 = ab[l];
+                    i2 = l;
+                }
+            }
+            const uint32_t par = __popc(neg) & 1u;
+            float g1 = 0.0f, g2 = 0.0f;  // adjoints landing on edges i1 and i2
+#pragma unroll
+            for (int l = 0; l < DCMAX; ++l) {
+                const int e = edge(l, r);
+                if (e < 0) continue;
                 const float w = __ldg(prm + 2 * l), o = __ldg(prm + 2 * l + 1);
                 const bool first = l == i1;
                 const float mv = first ? mn2 : mn1;
                 const float s = (par ^ ((neg >> l) & 1u)) ? -1.0f : 1.0f;
                 const bool act = (first ? i2 : i1) >= 0 && fmaf(w, mv, -o) > 0.0f;
                 if (act) {
-                    const float ga = GA[((size_t)pk * d.E + eid[l]) * 32 + lane];
-                    gw = ga * s * mv;
-                    go = -ga * s;
-                    if (first) g2 += ga * s * w;
-                    else g1 += ga * s * w;
+                    const float gs = ga[l] * s;
+                    aw[l] = fmaf(gs, mv, aw[l]);
+                    ao[l] -= gs;
+                    if (first) g2 += gs * w;
+                    else g1 += gs * w;
                 }
             }
-            // warp sums of this circulant's two gradients
+            if (want_gb) {
+#pragma unroll
+                for (int l = 0; l < DCMAX; ++l) {
+                    const int e = edge(l, r);
+                    if (e < 0) continue;
+                    // sign(beta) of the two smallest inputs (0 for beta = 0)
+                    const float sg_l = ab[l] == 0.0f ? 0.0f : (((neg >> l) & 1u) ? -1.0f : 1.0f);
+                    float g = 0.0f;
+                    if (l == i1) g = g1 * sg_l;
+                    else if (l == i2) g = g2 * sg_l;
+                    GB[((size_t)pk * d.E + e) * 32 + lane] = g;
+                }
+            }
+        }
+        // warp sums of this item's gradients per circulant (j, l)
+#pragma unroll
+        for (int l = 0; l < DCMAX; ++l) {
+            if (edge(l, r0) < 0) continue;  // warp-uniform
+            float gw = aw[l], go = ao[l];
+#pragma unroll
             for (int of = 16; of > 0; of >>= 1) {
                 gw += __shfl_xor_sync(0xffffffffu, gw, of);
                 go += __shfl_xor_sync(0xffffffffu, go, of);
             }
-            if (lane == 0 && eid[l] >= 0 && (gw != 0.0f || go != 0.0f)) {
+            if (lane == 0 && (gw != 0.0f || go != 0.0f)) {
                 atomicAdd(&sg[(j * d.L + l) * 2], gw);
                 atomicAdd(&sg[(j * d.L + l) * 2 + 1], go);
-            }
-        }
-        if (want_gb) {
-#pragma unroll
-            for (int l = 0; l < DCMAX; ++l) {
-                if (eid[l] < 0) continue;
-                float g = 0.0f;
-                if (l == i1) g = g1 * sgn[l];
-                else if (l == i2) g = g2 * sgn[l];
-                GB[((size_t)pk * d.E + eid[l]) * 32 + lane] = g;
             }
         }
     }
