@@ -243,3 +243,30 @@ def test_ber_sim_random_codewords_other_decoders(pkg, case):
         assert res["frames"] == frames
         assert abs(res["frame_errors"] - want["frame_errors"]) <= max(3, 0.05 * want["frame_errors"])
         assert abs(res["iters_sum"] - want["iters_sum"]) <= 0.03 * want["iters_sum"]
+
+
+def test_ber_sim_random_codewords_ragged_length(pkg):
+    """N = 162 (3 x 6, p = 27): codeword rows end inside a 32-bit word and inside a group of four
+    channel values; the continuous simulation still counts exactly what the batch path counts."""
+    shifts = synth.qc_shifts(3, 6, 27, seed=6)
+    code = pkg.QCCode(shifts, 27)
+    assert code.N % 32 and code.N % 4
+    res = code.ber_sim(1.25, seed=8, first_frame=11, max_frames=500, target_frame_errors=10 ** 9, gamma=96,
+                       max_iter=10, early_stop=1, codewords=pkg.CODEWORDS_RANDOM)
+    want = _batch_counts_cw(pkg, code, 1.25, 8, 11, 500, max_iter=10, early_stop=True)
+    for key, v in want.items():
+        assert res[key] == v, (key, res[key], v)
+    assert want["frame_errors"] > 0
+
+
+def test_encoder_dimension_zero(pkg):
+    """H = I (a general code with one check per variable): k = 0, the only codeword is zero."""
+    N = 40
+    code = pkg.SparseCode(np.arange(N + 1), np.arange(N), N)
+    k, pos = code.info_set()
+    assert k == 0 and pos.size == 0
+    cw = torch.full((5, N), 7, dtype=torch.uint8, device="cuda")
+    pkg.ldpc_encode(code.handle, None, cw)
+    assert not cw.any()
+    info, cw2 = code.random_codewords(seed=1, first_frame=0, gamma=3)
+    assert info is None and not cw2.any()
