@@ -17,6 +17,13 @@ holds the definitional pieces that are plain matrix constructions:
 * ``ldpccc_unwrap``    -- H of the LDPC convolutional code derived from a QC
   base by the three steps of Sec. II-D (partition into Lambda x Lambda
   sub-blocks, split into lower / strictly-upper parts, unwrap and repeat).
+* ``ldpccc_tanner``    -- H of the time-invariant LDPCCC with delays D^{a_jl}
+  (the other unwrapping Sec. II-D cites): check j at instant t meets bit l at
+  instant t - a_jl.
+* ``Encoder``          -- the systematic encoder of the transmitted codewords
+  (Sec. V): information set = complement of the greedy right-to-left column
+  basis of H, codeword = the unique null-space word with those bits.
+* ``info_bits``        -- the information bits a frame id draws from Philox.
 """
 from __future__ import annotations
 
