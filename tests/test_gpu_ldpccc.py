@@ -185,3 +185,15 @@ def test_tanner_ldpccc_full_size_sampled(pkg):
     assert decided.sum() == T - I * 2 + 1
     idx = [0, 901]
     compare(shifts, p, I, mu[idx], hard[idx], post[idx], decided, "tanner cfg3 sampled", tanner=True)
+
+
+def test_tanner_ldpccc_single_processor_single_stream(pkg):
+    """I = 1 (each frame gets one iteration, decided one frame later) and a single stream (one lane of one
+    package), fed one frame per window."""
+    J, L, p, I, T = 3, 6, 12, 1, 9
+    shifts = synth.qc_shifts(J, L, p, seed=21)
+    c = L * p
+    mu = synth.gaussian_llrs(1, T * c, seed=5, ebn0_db=2.5, rate=0.5).reshape(1, T, c)
+    hard, post, decided = run_gpu(pkg, shifts, p, I, mu, [1] * T, tanner=True)
+    assert decided.sum() == T - I * 2 + 1
+    compare(shifts, p, I, mu, hard, post, decided, "tanner I=1 one stream", tanner=True)
