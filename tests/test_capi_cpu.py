@@ -142,3 +142,26 @@ def test_codeword_options_validated(lib):
             assert e.value.status == 1 and "codewords" in str(e.value)
     finally:
         pkg.ldpc_code_destroy(h)
+
+
+def test_encoder_calls_reject_bad_arguments_without_a_device(lib):
+    """The encoder entry points refuse null handles, empty batches and a non-finite Eb/N0 before any device
+    memory is touched."""
+    import paper_1204_0334_gb300 as pkg
+
+    L = pkg.lib()
+    k = ctypes.c_int64()
+    assert L.ldpc_code_info_set(None, ctypes.byref(k), None) == 1
+    dummy = ctypes.c_void_p(16)
+    assert L.ldpc_encode(None, dummy, 4, dummy, None) == 1
+    assert L.ldpc_random_codewords(None, 1, 0, 4, None, dummy, None) == 1
+    h = pkg.ldpc_code_create(np.array([[0, 1, 2, 3], [1, 3, 0, 2]]), 8)
+    try:
+        assert L.ldpc_encode(h, dummy, 0, dummy, None) == 1          # gamma < 1
+        assert L.ldpc_encode(h, dummy, 4, None, None) == 1           # no output
+        assert L.ldpc_random_codewords(h, 1, 0, 0, None, dummy, None) == 1
+        assert L.ldpc_channel_codewords(h, float("nan"), 1, 0, 4, dummy, dummy, None) == 1
+        assert L.ldpc_channel_codewords(h, 2.0, 1, 0, 4, None, dummy, None) == 1
+        assert L.ldpccc_create_tanner(None, 3, 6, 8, 2, 4, ctypes.byref(ctypes.c_void_p())) == 1
+    finally:
+        pkg.ldpc_code_destroy(h)
