@@ -64,6 +64,7 @@ def args_parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-sparse", action="store_true")
     ap.add_argument("--no-noms", action="store_true")
+    ap.add_argument("--no-paper", action="store_true", help="skip the paper's codes A-D and LDPCCCs A'-D'")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU seconds of the oracle baseline")
     ap.add_argument("--seed", type=int, default=20120403)
     return ap.parse_args()
@@ -311,6 +312,8 @@ def run_ours(a):
         line["hetero_batch"] = batch_bench(a, pkg, stream)
     if not a.no_noms:
         line["noms_training"] = noms_training_bench(a, pkg, code, stream)
+    if not a.no_paper:
+        line["paper_workloads"] = paper_workloads_bench(a, pkg, stream)
     if not a.no_sparse:
         line["general_code"] = sparse_bench(a, pkg, code, stream)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -425,6 +428,62 @@ def noms_training_bench(a, pkg, code, stream) -> dict:
     return {"workload": "learned min-sum training step, n=18360, 1024 frames, 10 iterations, FP16, checkpoint every 2",
             "frames_per_s": B / ((fwd + bwd) / 1e3), "fwd_ms": fwd, "bwd_ms": bwd, "bwd_over_fwd": bwd / fwd,
             "fwd_achieved_gbs": fwd_bytes / (fwd / 1e3) / 1e9, "fwd_frac": fwd_bytes / (fwd / 1e3) / 1e9 / peak}
+
+
+# the paper's own workloads (Sec. V, tables "newdectime" and "dectime_ldpccc"): GTX460 time per
+# codeword / frame in ms, for context beside this GPU's
+PAPER_BLOCK_MS = {422: 2.12, 632: 2.9, 768: 3.4, 1024: 4.5}
+PAPER_LDPCCC_MS = {422: 0.23, 632: 0.31, 768: 0.38, 1024: 0.48}
+
+
+def paper_workloads_bench(a, pkg, stream) -> dict:
+    """Codes A-D (4x24, p = 422 .. 1024, seeded shifts) at 3.2 dB with 30 iterations (no early stop) in 4096 slots,
+    and their LDPCCCs A'-D' (Lambda = 4) at 3.1 dB with I = 20 processors for 1024 streams: time per codeword /
+    per frame on this GPU beside the paper's GTX460 figures (context, not a target)."""
+    import torch
+
+    import synth
+
+    out = {}
+    for p_, ms_paper in PAPER_BLOCK_MS.items():
+        code = pkg.QCCode(synth.qc_shifts(4, 24, p_, seed=7), p_)
+        o = pkg.default_opts(max_iter=30, early_stop=0)
+        frames = 16384
+        pkg.ldpc_ber_sim(code.handle, 3.2, a.seed, 0, 4096, 1 << 60, 4096, o, stream)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        r = pkg.ldpc_ber_sim(code.handle, 3.2, a.seed, 1 << 20, frames, 1 << 60, 4096, o, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        us = ms * 1e3 / r["frames"]
+        out[f"block_p{p_}"] = {"us_per_codeword": us, "mbit_s": r["frames"] * code.K / (ms / 1e3) / 1e6,
+                               "fer": r["frame_errors"] / r["frames"], "paper_gtx460_us": ms_paper * 1e3,
+                               "ratio": ms_paper * 1e3 / us}
+        code.close()
+    for p_, ms_paper in PAPER_LDPCCC_MS.items():
+        g, T = 1024, 32
+        cc = pkg.LDPCCC(synth.qc_shifts(4, 24, p_, seed=7), p_, 20, g)
+        llr = cc.channel(3.1, a.seed, 0, T)
+        hard = torch.empty((g, T, cc.c), dtype=torch.uint8, device="cuda")
+        pkg.ldpccc_decode_window(cc.handle, llr, 30.0, hard, None, stream)  # fills the pipeline
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        decided = 0
+        for w in range(2):
+            pkg.ldpccc_channel(cc.handle, 3.1, a.seed, T * (w + 1), llr, stream)
+            _, n = pkg.ldpccc_decode_window(cc.handle, llr, 30.0, hard, None, stream)
+            decided += n
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        us = ms * 1e3 / (decided * g)
+        out[f"ldpccc_p{p_}"] = {"us_per_frame": us, "mbit_s": decided * g * cc.b / (ms / 1e3) / 1e6,
+                                "paper_gtx460_us": ms_paper * 1e3, "ratio": ms_paper * 1e3 / us}
+        cc.close()
+    return out
 
 
 def batch_bench(a, pkg, stream) -> dict:
