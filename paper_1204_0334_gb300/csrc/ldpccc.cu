@@ -615,6 +615,7 @@ ldpc_status ldpccc_decode_window(ldpccc cc, const float *llr, int32_t T, float c
         else if (dcm <= 6) cc_cn_launch<6>(cc, g, t, clip, n_cn, s);
         else if (dcm <= 8) cc_cn_launch<8>(cc, g, t, clip, n_cn, s);
         else if (dcm <= 16) cc_cn_launch<16>(cc, g, t, clip, n_cn, s);
+        else if (dcm <= 24) cc_cn_launch<24>(cc, g, t, clip, n_cn, s);
         else cc_cn_launch<32>(cc, g, t, clip, n_cn, s);
         const long long Fd = t - (long long)cc->ring + 1;  // frame decided at this slot
         const int q = Fd >= 0 ? (int)(Fd - (first_dec > 0 ? first_dec : 0)) : -1;

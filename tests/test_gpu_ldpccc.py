@@ -82,6 +82,7 @@ def compare(shifts, p, I, mu, hard, post, decided, label, tanner=False):
     (4, 8, 8, 3, 33, 50, [17, 25, 8], 2.0),    # Lambda = 4, three windows (continuity)
     (3, 7, 11, 4, 32, 30, [30], 2.0),          # Lambda = 1: frames decode independently
     (2, 6, 20, 6, 64, 70, [1, 69], 1.5),       # Lambda = 2, a one-frame window first
+    (4, 24, 7, 3, 32, 30, [30], 3.5),          # Lambda = 4, rows of 24 edges (the paper's A'-D' shape)
 ])
 def test_ldpccc_matches_oracle(pkg, J, L, p, I, gamma, T, windows, ebn0):
     shifts = synth.qc_shifts(J, L, p, seed=J * 100 + L)
@@ -151,6 +152,7 @@ def test_ldpccc_channel_matches_oracle(pkg):
     (4, 8, 8, 3, 33, 30, [11, 19], 2.0, 0),      # two windows (continuity)
     (4, 8, 9, 3, 32, 25, [25], 2.0, 5),          # zero blocks
     (2, 6, 20, 6, 64, 40, [1, 39], 1.5, 0),      # a one-frame window first
+    (4, 24, 7, 3, 32, 20, [20], 3.5, 0),         # rows of 24 edges
 ])
 def test_tanner_ldpccc_matches_oracle(pkg, J, L, p, I, gamma, T, windows, ebn0, zb):
     shifts = synth.qc_shifts(J, L, p, seed=J * 10 + L + zb, zero_blocks=zb)
