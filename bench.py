@@ -465,15 +465,19 @@ def paper_workloads_bench(a, pkg, stream) -> dict:
     for p_, ms_paper in PAPER_LDPCCC_MS.items():
         g, T = 1024, 32
         cc = pkg.LDPCCC(synth.qc_shifts(4, 24, p_, seed=7), p_, 20, g)
-        llr = cc.channel(3.1, a.seed, 0, T)
+        llr = torch.empty((g, T, cc.c), dtype=torch.float32, device="cuda")
         hard = torch.empty((g, T, cc.c), dtype=torch.uint8, device="cuda")
-        pkg.ldpccc_decode_window(cc.handle, llr, 30.0, hard, None, stream)  # fills the pipeline
+        # fill the pipeline (I * Lambda = 80 frames) so that every timed slot decides a frame
+        fill = (20 * cc.Lambda + T - 1) // T + 1
+        for w in range(fill):
+            pkg.ldpccc_channel(cc.handle, 3.1, a.seed, T * w, llr, stream)
+            pkg.ldpccc_decode_window(cc.handle, llr, 30.0, hard, None, stream)
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         decided = 0
-        for w in range(2):
-            pkg.ldpccc_channel(cc.handle, 3.1, a.seed, T * (w + 1), llr, stream)
+        for w in range(fill, fill + 2):
+            pkg.ldpccc_channel(cc.handle, 3.1, a.seed, T * w, llr, stream)
             _, n = pkg.ldpccc_decode_window(cc.handle, llr, 30.0, hard, None, stream)
             decided += n
         ev1.record(stream)
