@@ -165,3 +165,22 @@ def test_encoder_calls_reject_bad_arguments_without_a_device(lib):
         assert L.ldpccc_create_tanner(None, 3, 6, 8, 2, 4, ctypes.byref(ctypes.c_void_p())) == 1
     finally:
         pkg.ldpc_code_destroy(h)
+
+
+def test_bench_reference_arm_line(lib):
+    """bench.py --impl reference times the FP64 oracle on the host cores and prints one JSON line with the
+    contract's keys (a short run: one step of a small sample)."""
+    import json
+    import subprocess
+    import sys
+
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0", "--cpu-seconds", "1"], capture_output=True, text=True, timeout=600,
+                         cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
