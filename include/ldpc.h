@@ -239,8 +239,9 @@ typedef struct {
  * frames generated and decoded on the device, error counts reduced on the
  * device.  The decoders run continuously: gamma frame slots (rounded up to
  * whole packages of 32 V frames), and a slot takes the next frame in the
- * step after its frame stops (C-11 syndrome check after >= 1 iterations when
- * opts->early_stop, or the iteration cap), so each frame gets exactly the
+ * step after its frame stops (when opts->early_stop, its decisions satisfy
+ * every check, tested after each complete iteration i >= 1; or the iteration
+ * cap), so each frame gets exactly the
  * iterations and decisions that ldpc_decode gives it (learned NOMS: each
  * frame's iteration i uses parameter row i).
  * Once frame_errors >= target_frame_errors (the paper uses 100) no new frame

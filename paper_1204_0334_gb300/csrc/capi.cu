@@ -40,7 +40,7 @@ int pointer_kind(const void *p) {
     return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? 0 : 1;
 }
 
-static ldpc_status check_opts(const ldpc_code c, const ldpc_decode_opts *o) {
+ldpc_status check_opts(const ldpc_code c, const ldpc_decode_opts *o) {
     if (!o) {
         set_error("opts is NULL");
         return LDPC_EINVAL;

@@ -115,6 +115,8 @@ ldpc_status cuda_fail(cudaError_t e, const char *what);
 
 // 0: device pointer (or managed); 1: host pointer; -1: null
 int pointer_kind(const void *p);
+// validation of decode options shared by every decode entry point (LDPC_OK or the error)
+ldpc_status check_opts(const ldpc_code c, const ldpc_decode_opts *o);
 // noise level of Eb/N0 (dB) at the code's design rate: sigma^2 = 1 / (2 R 10^(EbN0/10))
 double channel_sigma(const ldpc_code c, double ebn0_db);
 

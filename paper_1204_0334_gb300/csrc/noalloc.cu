@@ -91,18 +91,13 @@ ldpc_status ldpc_decode_noalloc(ldpc_code c, const float *llr, int32_t gamma, co
         set_error("ldpc_decode_noalloc takes device buffers only (host buffers would need staging memory)");
         return LDPC_EINVAL;
     }
+    ldpc_status st = check_opts(c, opts);
+    if (st != LDPC_OK) return st;
     if (opts->algo == LDPC_ALGO_NOMS) {
         set_error("ldpc_decode_noalloc supports sum-product and min-sum");
         return LDPC_EUNSUPPORTED;
     }
-    ldpc_decode_opts o = *opts;
-    if (o.max_iter < 1 || o.max_iter > 100000 || (o.algo != LDPC_ALGO_SP && o.algo != LDPC_ALGO_MS) ||
-        (o.algo == LDPC_ALGO_SP && o.msg != LDPC_MSG_F32 && o.msg != LDPC_MSG_F16) ||
-        (o.algo == LDPC_ALGO_MS && o.msg != LDPC_MSG_I8) || !(o.clip > 0.0f) || o.clip > 60000.0f ||
-        o.frac_bits < 0 || o.frac_bits > 6) {
-        set_error("invalid decode options (see ldpc_decode)");
-        return LDPC_EINVAL;
-    }
+    const ldpc_decode_opts o = *opts;
     const size_t cap = ((size_t)gamma + 127) / 128 * 128;
     size_t off[8];
     const size_t need = noalloc_need(c->d, cap, off);
@@ -113,13 +108,18 @@ ldpc_status ldpc_decode_noalloc(ldpc_code c, const float *llr, int32_t gamma, co
         return LDPC_EINVAL;
     }
     void *base_v = nullptr;
-    ldpc_status st = noalloc_base(&base_v);
+    st = noalloc_base(&base_v);
     if (st != LDPC_OK) return st;
     noalloc_need(c->d, cap, off);
     unsigned char *base = (unsigned char *)base_v;
-    // a private view of the code object whose workspace points into the scratch
+    // A private view of the code object whose workspace points into the scratch.  It
+    // carries everything the decode steps read from a code: the QC description, and for
+    // a general code the flag and the device index tables (which stay owned by c).  The
+    // view is never passed to ldpc_code_destroy, the only place a workspace is freed.
     ldpc_code_s view;
     view.d = c->d;
+    view.sparse = c->sparse;
+    view.sp = c->sp;
     view.device = c->device;
     view.rate = c->rate;
     view.noms = nullptr;
@@ -138,10 +138,7 @@ ldpc_status ldpc_decode_noalloc(ldpc_code c, const float *llr, int32_t gamma, co
     if (st != LDPC_OK) return st;
     st = qc_decode_device(&view, gamma, o, post != nullptr, s);
     if (st != LDPC_OK) return st;
-    st = qc_unpack_outputs(&view, gamma, o, post, hard, iters, ok, s);
-    // the view's destructor must not free the borrowed scratch
-    view.ws = DecodeWs();
-    return st;
+    return qc_unpack_outputs(&view, gamma, o, post, hard, iters, ok, s);
 }
 
 }  // extern "C"

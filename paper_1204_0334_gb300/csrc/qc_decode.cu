@@ -535,7 +535,7 @@ ldpc_status qc_decode_device(ldpc_code c, int gamma, const ldpc_decode_opts &o, 
             else if (dcm <= 24) cn_first_dispatch<24>(c, P, o, s);
             else cn_first_dispatch<32>(c, P, o, s);
         } else {
-            // C-11 stopping: the syndrome of the decisions after it-1 iterations, then the check pass
+            // early stop: the syndrome of the decisions after it-1 complete iterations (never before the first), then the check pass
             if (syn) {
                 st = qc_syndrome(c, P, V, (1 + par) * V, s);
                 if (st != LDPC_OK) return st;

@@ -8,9 +8,9 @@
 // simulation is
 //
 //   syndrome: of every slot's decisions so far (eq. (hrddcs))
-//   retire:   a frame whose decisions after a >= 1 iterations satisfy every
-//             check (C-11 stopping), or that has run max_iter iterations,
-//             leaves its slot; the next frame id takes the slot
+//   retire:   a frame whose decisions after a >= 1 complete iterations satisfy
+//             every check, or that has run max_iter iterations, leaves its
+//             slot; the next frame id takes the slot
 //   compact:  the packages with a running or retiring frame
 //   channel:  the new frames' channel LLRs (Philox + Box-Muller with the
 //             counter of ldpc_channel) into the slots' channel store

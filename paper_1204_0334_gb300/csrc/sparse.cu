@@ -4,7 +4,7 @@
 // eq. simpleH) and of a variable (the column table) from index tables -- the
 // role of the paper's LUT_c / LUT_v (Sec. IV-A) -- instead of circulant
 // address arithmetic.  The first iteration starts from messages beta = mu
-// written by an initialization pass; the syndrome for early stopping (C-11)
+// written by an initialization pass; the syndrome for early stopping (tested after each complete iteration i >= 1)
 // and the final ok flags gather the hard decisions through the row table.
 #include "qc_device.cuh"
 
@@ -96,7 +96,7 @@ ldpc_status sparse_decode_device(ldpc_code c, int gamma, const ldpc_decode_opts 
     for (int it = 1; it <= o.max_iter; ++it) {
         const bool syn = o.early_stop && it >= 2;
         const int par = it & 1;
-        if (syn) {  // C-11: the syndrome of the decisions after it - 1 iterations
+        if (syn) {  // early stop: the syndrome of the decisions after it - 1 complete iterations
             st = sparse_syndrome(c, P, V, (1 + par) * V, s);
             if (st != LDPC_OK) return st;
         }

@@ -413,6 +413,71 @@ def test_noms_with_unit_weight_is_min_sum():
     assert np.array_equal(post, mpost * 0.25)
 
 
+def test_noms_single_check_hand_values():
+    """One check of degree 5 (each edge its own circulant), one iteration, (w, o) != (1, 0).
+
+    alpha_e = sign * max(w * m - o, 0) with m the smallest |beta| over the other edges and sign
+    the product of their signs; post_v = mu_v + alpha_e.  Worked by hand:
+      e0: others (-0.5, 2, -3, 0.75): m = 0.5, sign +, 0.8*0.5 - 0.1 = 0.3     -> post 1.8
+      e1: others (1.5, 2, -3, 0.75):  m = 0.75, sign -, 0.5*0.75 - 0.3 = 0.075 -> post -0.575
+      e2: others (1.5, -0.5, -3, 0.75): m = 0.5, +, 1.0*0.5 - 0.6 < 0 -> alpha 0 -> post 2.0
+      e3: others (1.5, -0.5, 2, 0.75): m = 0.5, -, 0.9*0.5 - 0 = 0.45         -> post -3.45
+      e4: others (1.5, -0.5, 2, -3):   m = 0.5, +, 0.7*0.5 - 0.2 = 0.15        -> post 0.9
+    (w * max(m - o, 0) would give 0.32 on e0; sign * (w m - o) without the max -0.1 on e2.)
+    """
+    rp = np.array([0, 5], dtype=np.int32)
+    col = np.arange(5, dtype=np.int32)
+    cb = np.arange(5, dtype=np.int32)
+    mu = np.array([[1.5, -0.5, 2.0, -3.0, 0.75]], dtype=np.float32)
+    params = np.array([[[0.8, 0.1], [0.5, 0.3], [1.0, 0.6], [0.9, 0.0], [0.7, 0.2]]])
+    loss, post, _ = oracle.noms(rp, col, cb, 5, mu, 1, params)
+    want = np.array([1.8, -0.575, 2.0, -3.45, 0.9])
+    assert np.allclose(post[0], want, rtol=0, atol=1e-12), post
+    # loss: mean of softplus(-post) over the five bits of the single iteration
+    assert abs(loss - np.mean(np.log1p(np.exp(-want)))) <= 1e-12
+    # a tie in the minimum (|1.0| twice) and a zero input: e2 sees m = 1.0 from either tied edge
+    mu2 = np.array([[1.0, -1.0, 2.0, 0.0, -2.5]], dtype=np.float32)
+    ones = np.zeros((1, 5, 2))
+    ones[..., 0] = 0.5
+    ones[..., 1] = 0.125
+    _, post2, _ = oracle.noms(rp, col, cb, 5, mu2, 1, ones)
+    # every edge but e3 has the zero input among its others: m = 0, 0.5*0 - 0.125 < 0 -> alpha 0;
+    # e3: others (1, -1, 2, -2.5): m = 1, sign + (two negatives), 0.5 - 0.125 = 0.375
+    assert np.allclose(post2[0], [1.0, -1.0, 2.0, 0.375, -2.5], rtol=0, atol=1e-12), post2
+
+
+def test_noms_two_checks_two_iterations_hand_values():
+    """Two checks sharing variable 2 (base [[0,0,0,-1,-1],[-1,-1,0,0,0]], p = 1), two iterations with
+    different parameter rows: pins the extrinsic variable rule, which row each iteration uses, and the
+    circulant index j*L + l.  Worked by hand (all values exact in binary):
+      iteration 1, (w, o) = (0.75, 0.125) everywhere:
+        c0 on (2, -1.25, 0.5): alpha = (-0.25, +0.25, -0.8125)
+        c1 on (0.5, 1.75, -3):  alpha = (-1.1875, -0.25, +0.25)
+        beta(c0, v2) = 0.5 - 1.1875 = -0.6875, beta(c1, v2) = 0.5 - 0.8125 = -0.3125
+        post = (1.75, -1.0, -1.5, 1.5, -2.75)
+      iteration 2, (w, o) = (0.625, 0.0625) on circulant 0, (0.5, 0.25) elsewhere:
+        c0 on (2, -1.25, -0.6875): alpha = (+0.3671875, -0.09375, -0.375)
+        c1 on (-0.3125, 1.75, -3): alpha = (-0.625, 0, 0)   (0.5 * 0.3125 - 0.25 < 0)
+        post = (2.3671875, -1.34375, -0.5, 1.75, -3.0)
+    """
+    H = oracle.qc_parity_check([[0, 0, 0, -1, -1], [-1, -1, 0, 0, 0]], 1)
+    rp, col = oracle.csr_rows(H)
+    cb = oracle.circulant_index(rp, col, 1, 5)
+    assert cb.tolist() == [0, 1, 2, 7, 8, 9]
+    mu = np.array([[2.0, -1.25, 0.5, 1.75, -3.0]], dtype=np.float32)
+    params = np.zeros((2, 10, 2))
+    params[0, :, :] = (0.75, 0.125)
+    params[1, :, :] = (0.5, 0.25)
+    params[1, 0, :] = (0.625, 0.0625)
+    post1 = np.array([1.75, -1.0, -1.5, 1.5, -2.75])
+    post2 = np.array([2.3671875, -1.34375, -0.5, 1.75, -3.0])
+    _, p1, _ = oracle.noms(rp, col, cb, 5, mu, 1, params[:1])
+    assert np.array_equal(p1[0], post1), p1
+    loss, p2, _ = oracle.noms(rp, col, cb, 5, mu, 2, params)
+    assert np.array_equal(p2[0], post2), p2
+    assert abs(loss - np.mean(np.log1p(np.exp(-np.concatenate([post1, post2]))))) <= 1e-12
+
+
 def test_noms_gradient_matches_finite_differences():
     """Hand-written reverse mode against central differences of the FP64 loss (away from ties and kinks)."""
     H, rp, col, cb = _qc(3, 6, 8, 5)
