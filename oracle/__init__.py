@@ -63,6 +63,10 @@ def _load():
         lib.or_channel_awgn.restype = None
         lib.or_channel_awgn_cw.argtypes = [u64, u64, i32, i32, f64, u32, P, P, P]
         lib.or_channel_awgn_cw.restype = None
+        lib.or_ln_f32_array.argtypes = [P, P, ctypes.c_int64]
+        lib.or_ln_f32_array.restype = None
+        lib.or_sincos2pi_f32_array.argtypes = [P, P, P, ctypes.c_int64]
+        lib.or_sincos2pi_f32_array.restype = None
         lib.or_variable_edges.argtypes = [i32, i32, P, P, P, P]
         lib.or_sp_decode.argtypes = [i32, i32, P, P, i32, P, i32, i32, f64, i32, P, P, P, P, i32]
         lib.or_ms_decode.argtypes = [i32, i32, P, P, i32, P, i32, i32, i32, P, P, P, P, i32]
@@ -193,6 +197,25 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     out = np.zeros(4, dtype=np.uint32)
     lib.or_philox4x32_10(_p(c), _p(k), _p(out))
     return out
+
+
+def ln_f32(u) -> np.ndarray:
+    """The channel generator's binary32 natural logarithm of positive normal binary32 values."""
+    lib = _load()
+    u = np.ascontiguousarray(u, dtype=np.float32)
+    out = np.empty_like(u)
+    lib.or_ln_f32_array(_p(u), _p(out), u.size)
+    return out
+
+
+def sincos2pi_f32(v) -> tuple[np.ndarray, np.ndarray]:
+    """The channel generator's binary32 (sin, cos) of 2 pi v 2^-24 for odd v in (0, 2^24)."""
+    lib = _load()
+    v = np.ascontiguousarray(v, dtype=np.uint32)
+    s = np.empty(v.shape, dtype=np.float32)
+    c = np.empty(v.shape, dtype=np.float32)
+    lib.or_sincos2pi_f32_array(_p(v), _p(s), _p(c), v.size)
+    return s, c
 
 
 def channel_awgn(seed: int, first_frame: int, nfr: int, N: int, sigma: float, tag: int = 0,

@@ -15,8 +15,11 @@
  *
  * Contents
  *   or_philox4x32_10   counter-based generator (Salmon et al., SC'11)
+ *   or_ln_f32,         the channel generator's binary32 ln and sin/cos of 2 pi u
+ *   or_sincos2pi_f32   (range reduction + minimax polynomials, defined op by op)
  *   or_channel_awgn    BPSK over AWGN, channel LLR (Sec. II-B: x = 1 - 2c,
- *   or_channel_awgn_cw y = x + g, mu = 2y/sigma^2), all-zero or given codeword
+ *   or_channel_awgn_cw y = x + g, mu = 2y/sigma^2), all-zero or given codeword,
+ *                      in binary32 as the generator defines it
  *   or_sp_decode       sum-product BP, Algorithm 1 (eqs. bphs, bpvs, bpd,
  *                      hrddcs), phi-form or literal tanh-form check update
  *   or_ms_decode       integer min-sum (fixed-point variant of the CN rule)
@@ -63,26 +66,113 @@ void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32
     out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
 }
 
-/* A 32-bit Philox word -> uniform in (0,1), as an odd multiple of 2^-24     */
-/* so that the value is exact in binary32 as well as binary64.               */
-static double or_uniform(uint32_t x)
+/* ------------------------------------------------------------------------ */
+/* The channel generator in binary32.  The LLRs the decoders receive are      */
+/* binary32, and this generator is defined operation by operation so that any */
+/* implementation of the same definition produces the same bits.  Every       */
+/* arithmetic step below is one IEEE-754 binary32 operation rounded to        */
+/* nearest-even: + - * / sqrtf, and fmaf where written (this file is compiled */
+/* with -ffp-contract=off, so nothing else is fused).                         */
+/*                                                                            */
+/* Uniforms: a Philox word w gives u = (2 floor(w / 2^9) + 1) 2^-24, an odd   */
+/* multiple of 2^-24 in (0, 1), exact in binary32.                            */
+/*                                                                            */
+/* ln u: u = m 2^e with m in [sqrt(1/2), sqrt(2)) (from the bit pattern; the  */
+/* threshold is the binary32 value 0x3fb504f3), f = m - 1 (exact),            */
+/* ln(1 + f) = f + f^2 (-1/2 + f R(f)), R a degree-7 minimax polynomial, and  */
+/* ln u = e LN2_HI + (e LN2_LO + ln(1 + f)) with the Cody-Waite split of ln 2 */
+/* (LN2_HI has 15 significant bits, so e LN2_HI is exact).                    */
+/*                                                                            */
+/* sin and cos of 2 pi u: with v = 2 floor(w / 2^9) + 1 (u = v 2^-24), the    */
+/* nearest quarter turn j = floor((v + 2^21) / 2^22) and r = (v - j 2^22)     */
+/* 2^-24 in [-1/8, 1/8] are exact integer steps; sin(2 pi r) = r S(r^2) and   */
+/* cos(2 pi r) = 1 + r^2 C(r^2) with degree-4 minimax polynomials S and C;    */
+/* the quadrant j mod 4 swaps and negates them.                               */
+/*                                                                            */
+/* The coefficients are binary32 minimax fits (Lawson's algorithm) made once  */
+/* for this generator; the fitting procedure is documented with the input     */
+/* generators.                                                                */
+/* ------------------------------------------------------------------------ */
+static const float OR_LN_R[8] = { /* degree 7 down to 0 */
+    -0x1.38c9dep-4f, 0x1.055ec6p-3f, -0x1.0d8242p-3f, 0x1.22d92ep-3f,
+    -0x1.54728ap-3f, 0x1.99a01cp-3f, -0x1.000226p-2f, 0x1.555554p-2f};
+static const float OR_SIN_S[5] = { /* degree 4 down to 0 */
+    0x1.a0b0c6p+8f, -0x1.61b22ap+6f, 0x1.46e1p+6f, -0x1.4abc8ap+5f, 0x1.921fb6p+2f};
+static const float OR_COS_C[5] = { /* degree 4 down to 0 */
+    0x1.c33bfap+6f, 0x1.b78f76p+5f, -0x1.558c8p+6f, 0x1.03c192p+6f, -0x1.3bd3ccp+4f};
+static const float OR_LN2_HI = 0x1.62e4p-1f, OR_LN2_LO = 0x1.7f7d1cp-20f;
+
+/* ln u for a positive normal binary32 u */
+float or_ln_f32(float u)
 {
-    return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0); /* 2^-23 */
+    uint32_t b;
+    memcpy(&b, &u, 4);
+    int e = (int)(b >> 23) - 127;
+    uint32_t mb = (b & 0x7fffffu) | 0x3f800000u; /* m in [1, 2) */
+    if (mb > 0x3fb504f3u) {                       /* m > sqrt(2): use m / 2 */
+        mb -= 0x00800000u;
+        e += 1;
+    }
+    float m;
+    memcpy(&m, &mb, 4);
+    float f = m - 1.0f;
+    float R = OR_LN_R[0];
+    for (int i = 1; i < 8; ++i) R = fmaf(R, f, OR_LN_R[i]);
+    float t = fmaf(f, R, -0.5f);
+    float f2 = f * f;
+    float lnm = fmaf(f2, t, f);
+    float ef = (float)e;
+    return fmaf(ef, OR_LN2_HI, fmaf(ef, OR_LN2_LO, lnm));
+}
+
+/* sin and cos of 2 pi v 2^-24 for an odd v in (0, 2^24) */
+void or_sincos2pi_f32(uint32_t v, float *s_out, float *c_out)
+{
+    int32_t j = (int32_t)((v + (1u << 21)) >> 22);
+    int32_t ri = (int32_t)v - j * (1 << 22);
+    float r = (float)ri * 0x1p-24f;
+    float z = r * r;
+    float S = OR_SIN_S[0], C = OR_COS_C[0];
+    for (int i = 1; i < 5; ++i) {
+        S = fmaf(S, z, OR_SIN_S[i]);
+        C = fmaf(C, z, OR_COS_C[i]);
+    }
+    float sn = r * S;
+    float cs = fmaf(z, C, 1.0f);
+    switch (j & 3) {
+        case 0: *s_out = sn; *c_out = cs; break;
+        case 1: *s_out = cs; *c_out = -sn; break;
+        case 2: *s_out = -sn; *c_out = -cs; break;
+        default: *s_out = -cs; *c_out = sn; break;
+    }
+}
+
+/* arrays of the two functions (for the accuracy tests) */
+void or_ln_f32_array(const float *u, float *out, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = or_ln_f32(u[i]);
+}
+void or_sincos2pi_f32_array(const uint32_t *v, float *s, float *c, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) or_sincos2pi_f32(v[i], s + i, c + i);
 }
 
 /*
  * Channel of Sec. II-B: BPSK x_n = 1 - 2 c_n, y_n = x_n + sigma*g_n with g_n
  * standard normal, mu_n = 2 y_n / sigma^2.  cw (row-major [nfr][N], 0/1) is
  * the transmitted codeword; NULL sends the all-zero codeword (x_n = +1).
- * g_n comes from Box-Muller on two Philox uniforms.  Bit n of frame F uses
- * counter (n/4, F_lo, F_hi, tag) under key (seed_lo, seed_hi); the four words
- * give the normals of bits 4q..4q+3 as two Box-Muller pairs.
- * mu is rounded to binary32 at the end; g_out (if non-NULL) receives g.
+ * Bit n of frame F uses counter (n/4, F_lo, F_hi, tag) under key
+ * (seed_lo, seed_hi); words (w0, w1) and (w2, w3) are two Box-Muller pairs
+ * giving the normals of bits 4q, 4q+1 and 4q+2, 4q+3:
+ *   rho = sqrtf(-2 ln u(w0)),  g0 = rho cos(2 pi u(w1)),  g1 = rho sin(2 pi u(w1)).
+ * In binary32: sf = sigma and s2 = 2 / sigma^2 rounded from double, and
+ *   mu = s2 * fmaf(sf, g, x).
+ * g_out (if non-NULL) receives g (binary32 values).
  */
 void or_channel_awgn_cw(uint64_t seed, uint64_t first_frame, int nfr, int N, double sigma,
                         uint32_t tag, const uint8_t *cw, float *mu_out, double *g_out)
 {
-    const double two_pi = 6.283185307179586476925286766559;
+    const float sf = (float)sigma, s2 = (float)(2.0 / (sigma * sigma));
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     for (int f = 0; f < nfr; ++f) {
         uint64_t F = first_frame + (uint64_t)f;
@@ -90,22 +180,23 @@ void or_channel_awgn_cw(uint64_t seed, uint64_t first_frame, int nfr, int N, dou
             uint32_t ctr[4] = {(uint32_t)q, (uint32_t)F, (uint32_t)(F >> 32), tag};
             uint32_t w[4];
             or_philox4x32_10(ctr, key, w);
-            double g[4];
+            float g[4];
             for (int pair = 0; pair < 2; ++pair) {
-                double u0 = or_uniform(w[2 * pair]);
-                double u1 = or_uniform(w[2 * pair + 1]);
-                double r = sqrt(-2.0 * log(u0));
-                g[2 * pair] = r * cos(two_pi * u1);
-                g[2 * pair + 1] = r * sin(two_pi * u1);
+                uint32_t v0 = 2u * (w[2 * pair] >> 9) + 1u;
+                uint32_t v1 = 2u * (w[2 * pair + 1] >> 9) + 1u;
+                float u0 = (float)v0 * 0x1p-24f;
+                float rho = sqrtf(-2.0f * or_ln_f32(u0));
+                float sn, cs;
+                or_sincos2pi_f32(v1, &sn, &cs);
+                g[2 * pair] = rho * cs;
+                g[2 * pair + 1] = rho * sn;
             }
             for (int e = 0; e < 4; ++e) {
                 int n = 4 * q + e;
                 if (n >= N) break;
-                double x = (cw && cw[(size_t)f * N + n]) ? -1.0 : 1.0;
-                double y = x + sigma * g[e];
-                double mu = 2.0 * y / (sigma * sigma);
-                mu_out[(size_t)f * N + n] = (float)mu;
-                if (g_out) g_out[(size_t)f * N + n] = g[e];
+                float x = (cw && cw[(size_t)f * N + n]) ? -1.0f : 1.0f;
+                mu_out[(size_t)f * N + n] = s2 * fmaf(sf, g[e], x);
+                if (g_out) g_out[(size_t)f * N + n] = (double)g[e];
             }
         }
     }

@@ -1,8 +1,8 @@
 """GPU parity of the systematic encoder and of the simulation with random codewords (through the C-ABI).
 
 Encoding is bit work: information sets, codewords and information bits are compared bit-exactly with
-the oracle (its own greedy column basis and Philox).  The channel of a codeword is FP32 arithmetic on
-the same noise: within the FP32 rounding bound of the all-zero channel test.  The simulation with
+the oracle (its own greedy column basis and Philox).  The channel of a codeword is the generator's
+binary32 arithmetic on the same noise: bit-exact against the oracle.  The simulation with
 random codewords is compared with the batch path on the same frames (random_codewords ->
 channel_codewords -> decode, errors over the information positions): exact counts for FP32
 sum-product and integer min-sum.
@@ -92,7 +92,8 @@ def test_random_codewords_full_size(pkg):
 
 
 def test_channel_codewords_matches_oracle(pkg):
-    """mu = 2 (x + sigma g) / sigma^2 with x = 1 - 2c on the all-zero channel's noise g."""
+    """mu = 2 (x + sigma g) / sigma^2 with x = 1 - 2c on the all-zero channel's noise g: the oracle's
+    implementation of the generator, bit for bit."""
     shifts = synth.qc_shifts(3, 6, 64, seed=1)
     code = pkg.QCCode(shifts, 64)
     _, cw = code.random_codewords(seed=3, first_frame=17, gamma=50)
@@ -100,12 +101,8 @@ def test_channel_codewords_matches_oracle(pkg):
         out = code.channel_codewords(ebn0, 77, first, cw).cpu().numpy().astype(np.float64)
         sigma = oracle.sigma_from_ebn0(ebn0, 0.5)
         c = cw.cpu().numpy()
-        mu, g = oracle.channel_awgn(77, first, 50, code.N, sigma, return_g=True, cw=c)
-        x = 1.0 - 2.0 * c
-        mu64 = 2 * (x + sigma * g) / sigma**2
-        s2 = 2 / sigma**2
-        tol = s2 * (8e-7 * sigma * np.abs(g) + 2.4e-7 * (1 + np.abs(x + sigma * g))) + 1.2e-7 * np.abs(mu64)
-        assert np.all(np.abs(out - mu64) <= tol + 1e-7)
+        mu = oracle.channel_awgn(77, first, 50, code.N, sigma, cw=c)
+        assert np.array_equal(out, mu.astype(np.float64))  # the generator's binary32 bits
         # the all-zero word reproduces ldpc_channel exactly
         z = code.channel_codewords(ebn0, 77, first, torch.zeros_like(cw)).cpu().numpy()
         assert np.array_equal(z, code.channel(ebn0, 77, first, 50).cpu().numpy())
@@ -149,7 +146,7 @@ def test_ber_sim_random_codewords_equals_batch(pkg, case):
 
 def test_ber_sim_random_codewords_matches_oracle(pkg):
     """Oracle channel of the oracle's codewords + FP64 decoding, errors over the information positions:
-    the same counts as the device simulation (frames whose outcome rounding could change give slack)."""
+    the same counts as the device simulation (the channel is bit-exact, so every count agrees)."""
     shifts = synth.qc_shifts(3, 6, 64, seed=1)
     H = oracle.qc_parity_check(shifts, 64)
     rp, col = oracle.csr_rows(H)
@@ -162,14 +159,10 @@ def test_ber_sim_random_codewords_matches_oracle(pkg):
     mu = oracle.channel_awgn(5, 10, 300, code.N, sigma, cw=cw)
     po, ho, io, oo = oracle.sp_decode(rp, col, code.N, mu, 20, early_stop=True, nthreads=8)
     errs = (ho[:, enc.info] != cw[:, enc.info]).sum(axis=1)
-    marginal = (np.abs(po) < 1e-2).any(axis=1)
     want = {"frame_errors": int((errs > 0).sum()), "bit_errors": int(errs.sum()), "iters_sum": int(io.sum()),
             "undetected": int(((errs > 0) & (oo == 1)).sum())}
-    slack = int(marginal.sum())
-    assert abs(res["frame_errors"] - want["frame_errors"]) <= slack
-    if slack == 0:
-        for key, v in want.items():
-            assert res[key] == v, (key, res[key], v)
+    for key, v in want.items():
+        assert res[key] == v, (key, res[key], v)
     assert want["frame_errors"] > 0
 
 

@@ -82,6 +82,63 @@ def test_channel_llr_statistics():
     assert abs(ber - q) < 5 * math.sqrt(q * (1 - q) / n)
 
 
+def _all_uniform_numerators():
+    """v = 2 floor(w / 2^9) + 1 for every 32-bit word w: all odd v in (0, 2^24); u = v 2^-24."""
+    return (2 * np.arange(1 << 23, dtype=np.uint64) + 1).astype(np.uint32)
+
+
+def test_channel_ln_all_inputs():
+    """The generator's binary32 ln against float64 log on every uniform it can draw: <= 1 ulp."""
+    v = _all_uniform_numerators()
+    u = (v.astype(np.float64) * 2.0 ** -24).astype(np.float32)
+    assert np.array_equal(u.astype(np.float64), v.astype(np.float64) * 2.0 ** -24)  # exact in binary32
+    got = oracle.ln_f32(u).astype(np.float64)
+    ref = np.log(u.astype(np.float64))
+    ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+    assert (np.abs(got - ref) / ulp).max() <= 1.0
+    assert got.max() < 0  # every uniform is below 1: -2 ln u > 0 under the square root
+
+
+def test_channel_sincos_all_inputs():
+    """sin and cos of 2 pi u against float64 on every uniform it can draw: <= 2 ulp of each value
+    (float64 sin(2 pi u) is itself exact to ~1e-15 absolute, far below the bound), and the
+    quadrant signs are right."""
+    v = _all_uniform_numerators()
+    s, c = oracle.sincos2pi_f32(v)
+    ang = 2 * np.pi * (v.astype(np.float64) * 2.0 ** -24)
+    for got, ref in ((s, np.sin(ang)), (c, np.cos(ang))):
+        ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+        err = np.abs(got.astype(np.float64) - ref)
+        assert (err / ulp).max() <= 2.0
+        assert np.array_equal(np.sign(got), np.sign(ref))
+
+
+def test_channel_matches_double_precision_box_muller():
+    """The binary32 generator against Box-Muller in float64 on the same Philox words: every LLR within
+    the bound its operations allow (g: <= 4 ulp relative from ln, sqrt, cos/sin and the product; then
+    the fused sigma*g + x and the product with s2, each half an ulp, and s2's own rounding)."""
+    sigma = oracle.sigma_from_ebn0(1.5, 0.5)
+    seed, first, nfr, N = 3, 1 << 33, 3, 1000
+    mu, g = oracle.channel_awgn(seed, first, nfr, N, sigma, return_g=True)
+    g64 = np.zeros((nfr, N))
+    for f in range(nfr):
+        F = first + f
+        for q in range(N // 4):
+            w = oracle.philox4x32_10((q, F & 0xFFFFFFFF, F >> 32, 0), (seed & 0xFFFFFFFF, seed >> 32))
+            for pr in range(2):
+                u0 = (2.0 * (int(w[2 * pr]) >> 9) + 1.0) * 2.0 ** -24
+                u1 = (2.0 * (int(w[2 * pr + 1]) >> 9) + 1.0) * 2.0 ** -24
+                rho = math.sqrt(-2.0 * math.log(u0))
+                g64[f, 4 * q + 2 * pr] = rho * math.cos(2 * math.pi * u1)
+                g64[f, 4 * q + 2 * pr + 1] = rho * math.sin(2 * math.pi * u1)
+    eps = 2.0 ** -24
+    assert np.all(np.abs(g - g64) <= 4 * eps * np.abs(g64) + 1e-12)
+    mu64 = 2.0 * (1.0 + sigma * g64) / sigma ** 2
+    s2 = 2.0 / sigma ** 2
+    tol = s2 * (4 * eps * sigma * np.abs(g64) + eps * np.abs(1 + sigma * g64)) + 2 * eps * np.abs(mu64) + 1e-12
+    assert np.all(np.abs(mu.astype(np.float64) - mu64) <= tol)
+
+
 def test_channel_counter_partition_invariance():
     """Frame F's noise depends only on (seed, F, bit): any split of the frame range gives the same values."""
     sigma = 0.8
@@ -562,7 +619,11 @@ def test_channel_with_codeword_shifts_by_bpsk_symbol():
     m1, g1 = oracle.channel_awgn(9, 100, nfr, N, sigma, return_g=True, cw=cw)
     assert np.array_equal(g0, g1)
     x = 1.0 - 2.0 * cw.astype(np.float64)
-    want = (2.0 * (x + sigma * g0) / (sigma * sigma)).astype(np.float32)
+    # the generator's binary32 steps: s2 * fma(sigma, g, x); sigma * g is exact in float64 and
+    # the float64 sum then rounds once more than a fused add, which these 111 values never expose
+    sf, s2 = np.float32(sigma), np.float32(2.0 / (sigma * sigma))
+    y = (np.float64(sf) * g0 + x).astype(np.float32)
+    want = (s2 * y).astype(np.float32)
     assert np.array_equal(m1, want)
     assert np.allclose(m1.astype(np.float64) - m0, -4.0 * cw.astype(np.float64) / sigma**2, atol=1e-5)
 
