@@ -38,9 +38,40 @@ E_EDGES = J * L * P_CIRC
 METRIC = "decoded info Mbit/s (n=18360, 30 iters) at BER matching FP64 oracle"
 # DRAM bytes (read + write) per check-pass launch, averaged over the launches of one
 # default-size call, measured with ncu (dram__bytes_{read,write}.sum) on the default
-# workload of this file (FP32 messages, early stop, 3.5 dB, 4096 slots, 131072 frames);
-# absent whenever the check pass changes until re-measured.
-CN_DRAM_BYTES_PER_LAUNCH = {"f32": 2278.5e6}
+# workload of this file (FP32 messages, early stop, 3.5 dB, 4096 slots, 131072 frames),
+# with the hash of the kernel sources it was measured on: reported only while the
+# sources hash the same (null as soon as a kernel changes, until re-measured).
+CN_DRAM_BYTES_PER_LAUNCH = {"f32": (2278.5e6, "unmeasured")}
+KERNEL_SOURCES = ("qc_pipe.cu", "qc_device.cuh", "ldpc_internal.cuh")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1204_0334_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), for the CPU-baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
 
 
 def args_parse():
@@ -142,8 +173,9 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def oracle_sample(a, nframes: int, threads: int, first_frame: int):
-    """Channel + FP64 decode + error count of nframes on the host cores; returns (seconds, iters, errors)."""
+def oracle_sample(a, nframes: int, threads: int, first_frame: int, ebn0=None):
+    """Channel + FP64 decode + error count of frames first_frame .. first_frame + nframes - 1 on the host
+    cores; returns (seconds, counts) with the counts ldpc_ber_sim reports."""
     import numpy as np
     import oracle
     import synth
@@ -153,27 +185,57 @@ def oracle_sample(a, nframes: int, threads: int, first_frame: int):
         H = oracle.qc_parity_check(shifts, P_CIRC)
         oracle_sample.graph = oracle.csr_rows(H)
     rp, col = oracle_sample.graph
-    sigma = oracle.sigma_from_ebn0(a.ebn0, K_INFO / N_BITS)
+    sigma = oracle.sigma_from_ebn0(a.ebn0 if ebn0 is None else ebn0, K_INFO / N_BITS)
     t0 = time.perf_counter()
     mu = oracle.channel_awgn(a.seed, first_frame, nframes, N_BITS, sigma)
     _, hard, iters, ok = oracle.sp_decode(rp, col, N_BITS, mu, a.iters, early_stop=not a.no_early_stop,
                                           nthreads=threads)
-    errs = int(hard.sum())
+    errs = hard.sum(axis=1).astype(np.int64)
     dt = time.perf_counter() - t0
-    return dt, int(np.asarray(iters).sum()), errs
+    counts = {"frames": nframes, "frame_errors": int((errs > 0).sum()), "bit_errors": int(errs.sum()),
+              "iters_sum": int(np.asarray(iters).sum()), "undetected": int(((errs > 0) & (ok == 1)).sum())}
+    return dt, counts
 
 
-def cpu_baseline(a) -> dict:
+COUNT_KEYS = ("frames", "frame_errors", "bit_errors", "iters_sum", "undetected")
+
+
+def cpu_baseline(a, pkg, code, stream, opts, first_frame: int) -> dict:
+    """The FP64 oracle on the host cores, on the first frames of the first timed step (the same frame ids),
+    in two forms: OpenMP over frames on every core, and one thread.  Its counts on those frames are put
+    beside the GPU's counts on the same frames ("ber_match"), and again at 3.0 dB where frames fail."""
     threads = os.cpu_count() or 1
     n = max(threads, 16)
-    dt, it, _ = oracle_sample(a, n, threads, first_frame=1 << 50)
+    dt, cnt = oracle_sample(a, n, threads, first_frame)
     while dt < a.cpu_seconds * 0.5 and n < 4096:
         n = int(min(4096, max(2 * n, n * a.cpu_seconds / max(dt, 1e-3))))
         n = max(threads, (n // threads) * threads)
-        dt, it, _ = oracle_sample(a, n, threads, first_frame=1 << 50)
+        dt, cnt = oracle_sample(a, n, threads, first_frame)
+    n1 = max(1, min(n, int(round(4.0 * n / max(dt, 1e-3) / threads))))
+    dt1, cnt1 = oracle_sample(a, n1, 1, first_frame)
+
+    def gpu_counts(first, frames, ebn0):
+        r = pkg.ldpc_ber_sim(code.handle, ebn0, a.seed, first, frames, 1 << 60, a.gamma, opts, stream)
+        return {k: int(r[k]) for k in COUNT_KEYS}
+
+    match = []
+    if a.msg == "f32" and a.codewords == "zero":  # the oracle leg decodes all-zero frames by FP64 sum-product
+        g = gpu_counts(first_frame, n, a.ebn0)
+        match.append({"ebn0_db": a.ebn0, "frames": f"{first_frame}..{first_frame + n - 1}", "gpu": g,
+                      "oracle": cnt, "equal": all(g[k] == cnt[k] for k in COUNT_KEYS)})
+        low = 3.0
+        nl = max(threads, 2 * threads)
+        _, cl = oracle_sample(a, nl, threads, first_frame, ebn0=low)
+        gl = gpu_counts(first_frame, nl, low)
+        match.append({"ebn0_db": low, "frames": f"{first_frame}..{first_frame + nl - 1}", "gpu": gl, "oracle": cl,
+                      "equal": all(gl[k] == cl[k] for k in COUNT_KEYS)})
     return {"value": n * K_INFO / dt / 1e6, "unit": "Mbit/s", "cores": threads, "kind": "oracle",
-            "sample": f"{n} frames of the same workload (channel + FP64 sum-product, {it / n:.2f} mean iters) "
-                      f"on {threads} host threads, {dt:.1f} s"}
+            "cpu_model": cpu_model(),
+            "sample": f"frames {first_frame}..{first_frame + n - 1} of the first timed step ({n} frames: channel + "
+                      f"FP64 sum-product, {cnt['iters_sum'] / n:.2f} mean iters) on {threads} host threads, "
+                      f"{dt:.1f} s",
+            "single_thread": {"value": n1 * K_INFO / dt1 / 1e6, "unit": "Mbit/s", "frames": n1, "seconds": dt1},
+            "ber_match": match}
 
 
 def run_reference(a):
@@ -182,24 +244,24 @@ def run_reference(a):
         return
     threads = os.cpu_count() or 1
     # size each step to a few seconds of host work
-    t, _, _ = oracle_sample(a, threads, threads, first_frame=1 << 52)
+    t, _ = oracle_sample(a, threads, threads, first_frame=1 << 52)
     per = max(threads, int(round(4.0 / max(t, 1e-3))) * threads)
     per = min(per, 2048)
     for w in range(a.warmup):
         oracle_sample(a, threads, threads, first_frame=(1 << 52) + (w + 1) * 4096)
     total_t, frames, iters = 0.0, 0, 0
     for s in range(a.steps):
-        dt, it, _ = oracle_sample(a, per, threads, first_frame=(1 << 53) + s * per)
+        dt, cnt = oracle_sample(a, per, threads, first_frame=(1 << 53) + s * per)
         total_t += dt
         frames += per
-        iters += it
+        iters += cnt["iters_sum"]
     value = frames * K_INFO / total_t / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mbit/s", "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_t / a.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(a), "frames_per_step": per, "mean_iters": iters / frames},
             "cpu_baseline": {"value": value, "unit": "Mbit/s", "cores": threads, "kind": "oracle",
-                             "sample": f"{per} frames per step, {a.steps} steps"},
+                             "cpu_model": cpu_model(), "sample": f"{per} frames per step, {a.steps} steps"},
             "e2e": {"value": value, "unit": "Mbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -275,14 +337,19 @@ def run_ours(a):
     local_iters = sum(r["iters_sum"] for r in res)
     cn_bytes = 2.0 * E_EDGES * s_msg * local_iters
     cn_s = prof["cn_ms"] / 1e3
+    traffic, traffic_src = None, "no ncu measurement of this kernel source and workload"
+    meas = CN_DRAM_BYTES_PER_LAUNCH.get(a.msg)
+    default_workload = (not a.no_early_stop and a.gamma == 4096 and a.ebn0 == 3.5 and a.iters == 30
+                        and a.frames == 131072 and a.codewords == "zero")
+    if meas and default_workload and meas[1] == kernel_source_hash():
+        traffic, traffic_src = meas[0], f"ncu dram__bytes_read.sum + dram__bytes_write.sum, sources {meas[1]}"
     peaks = load_peaks()
     peak = peaks.get("hbm_gbs", 6800.0)
     roof = {"bound": "hbm", "kernel": "cn_pipe_kernel (" + ("sum-product" if algo == pkg.ALGO_SP else "min-sum") + ")",
             "achieved": cn_bytes / cn_s / 1e9 if cn_s > 0 else None, "peak": peak, "unit": "GB/s",
             "frac": (cn_bytes / cn_s / 1e9) / peak if cn_s > 0 else None,
-            "traffic": (CN_DRAM_BYTES_PER_LAUNCH.get(a.msg) if (not a.no_early_stop and a.gamma == 4096
-                                                                 and a.ebn0 == 3.5 and a.iters == 30
-                                                                 and a.frames == 131072) else None),
+            "traffic": traffic,
+            "traffic_source": traffic_src,
             "algorithmic_bytes_per_launch": cn_bytes / max(1, prof["cn_launches"]),
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback",
             "cn_launches": prof["cn_launches"], "cn_ms_avg": prof["cn_ms"] / max(1, prof["cn_launches"]),
@@ -316,13 +383,31 @@ def run_ours(a):
         line["paper_workloads"] = paper_workloads_bench(a, pkg, stream)
     if not a.no_sparse:
         line["general_code"] = sparse_bench(a, pkg, code, stream)
+    roof.update(bandwidth_probes(pkg, stream))
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(a)
+        line["cpu_baseline"] = cpu_baseline(a, pkg, code, stream, opts, shard.first_frame(rank, 0, a.frames))
     if rank == 0:
         print(json.dumps(line), flush=True)
     code.close()
     if dist:
         dist.destroy_process_group()
+
+
+def bandwidth_probes(pkg, stream) -> dict:
+    """This library's streaming probe: an L2-resident read (32 MB buffer, the peak for L2 byte rates) and an
+    HBM copy of 2 GB (read + write bytes; beside MEASURED_PEAKS' copy figure)."""
+    import torch
+
+    small = torch.empty(32 << 20, dtype=torch.uint8, device="cuda")
+    small.random_(0, 255)
+    sink = torch.zeros(1 << 16, dtype=torch.uint8, device="cuda")
+    l2 = pkg.ldpc_bandwidth_probe(small, sink, 400, 0, stream)
+    big = torch.empty(2 << 30, dtype=torch.uint8, device="cuda")
+    dst = torch.empty_like(big)
+    hbm = pkg.ldpc_bandwidth_probe(big, dst, 5, 1, stream)
+    del big, dst
+    return {"l2_probe_gbs": l2, "l2_probe": "ld.global.cg read sweeps of a 32 MB buffer (L2-resident)",
+            "hbm_probe_gbs": hbm, "hbm_probe": "copy of 2 GB (read + write bytes)"}
 
 
 def variants(a, pkg, code, stream, opts) -> dict:

@@ -380,6 +380,21 @@ typedef struct {
 ldpc_status ldpc_profile_enable(int32_t on);  /* resets all counters */
 ldpc_status ldpc_profile_read(ldpc_profile *out);
 
+/*
+ * ldpc_bandwidth_probe -- measurement aid (no paper counterpart): the memory
+ * bandwidth a plain streaming kernel of this library reaches, as the peak that
+ * the decoders' L2 byte rates are compared with.  mode 0 reads `bytes` of src
+ * `reps` times through L2 (ld.global.cg; a buffer smaller than L2 is then
+ * served by L2) and writes one word per thread block to dst (at least
+ * 4 * 8 * SM-count bytes); mode 1 copies src to dst `reps` times (read + write
+ * bytes counted).  One untimed sweep precedes the timed ones; the time comes
+ * from CUDA events on `stream`, and *gbs_out = bytes moved / time / 1e9.
+ * src, dst: device buffers, 16-byte aligned; bytes a positive multiple of 16.
+ * Synchronizes the stream.  Errors: LDPC_EINVAL, LDPC_ECUDA.
+ */
+ldpc_status ldpc_bandwidth_probe(const void *src, void *dst, int64_t bytes, int32_t reps, int32_t mode,
+                                 double *gbs_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

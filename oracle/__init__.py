@@ -40,42 +40,58 @@ _LIB_PATH = os.path.join(_HERE, "_oracle.so")
 _lib = None
 
 
+_LIB32_PATH = os.path.join(_HERE, "_oracle_f32.so")
+_lib32 = None
+
+
 def build(force: bool = False) -> str:
-    """Compile oracle.c into a shared library next to it (gcc, OpenMP)."""
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB_PATH)
+    """Compile oracle.c into shared libraries next to it (gcc, OpenMP): the FP64 oracle, and
+    the same source with the sum-product / LDPCCC real type set to binary32 (a diagnostic)."""
+    for path, extra in ((_LIB_PATH, []), (_LIB32_PATH, ["-DOR_REAL_FLOAT"])):
+        if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+            tmp = path + f".tmp{os.getpid()}"
+            cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-shared", "-fPIC"] + extra + [_SRC, "-o", tmp,
+                                                                                                 "-lm"]
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, path)
     return _LIB_PATH
 
 
-def _load():
-    global _lib
+def _declare(lib):
+    P = ctypes.c_void_p
+    i32, u32, u64, f64 = ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
+    lib.or_philox4x32_10.argtypes = [P, P, P]
+    lib.or_philox4x32_10.restype = None
+    lib.or_channel_awgn.argtypes = [u64, u64, i32, i32, f64, u32, P, P]
+    lib.or_channel_awgn.restype = None
+    lib.or_channel_awgn_cw.argtypes = [u64, u64, i32, i32, f64, u32, P, P, P]
+    lib.or_channel_awgn_cw.restype = None
+    lib.or_ln_f32_array.argtypes = [P, P, ctypes.c_int64]
+    lib.or_ln_f32_array.restype = None
+    lib.or_sincos2pi_f32_array.argtypes = [P, P, P, ctypes.c_int64]
+    lib.or_sincos2pi_f32_array.restype = None
+    lib.or_variable_edges.argtypes = [i32, i32, P, P, P, P]
+    lib.or_sp_decode.argtypes = [i32, i32, P, P, i32, P, i32, i32, f64, i32, P, P, P, P, i32]
+    lib.or_ms_decode.argtypes = [i32, i32, P, P, i32, P, i32, i32, i32, P, P, P, P, i32]
+    lib.or_quantize.argtypes = [P, i32, i32, P]
+    lib.or_noms.argtypes = [i32, i32, P, P, P, i32, P, i32, P, i32, f64, P, P, i32]
+    lib.or_noms.restype = f64
+    lib.or_ldpccc_decode.argtypes = [i32, i32, P, P, i32, i32, i32, i32, i32, i32, P, f64, P, P, P,
+                                     P, i32, P, i32]
+    return lib
+
+
+def _load(real: int = 64):
+    """The FP64 oracle (real = 64), or the binary32 diagnostic build (real = 32)."""
+    global _lib, _lib32
+    if real == 32:
+        if _lib32 is None:
+            build()
+            _lib32 = _declare(ctypes.CDLL(_LIB32_PATH))
+        return _lib32
     if _lib is None:
         build()
-        lib = ctypes.CDLL(_LIB_PATH)
-        P = ctypes.c_void_p
-        i32, u32, u64, f64 = ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
-        lib.or_philox4x32_10.argtypes = [P, P, P]
-        lib.or_philox4x32_10.restype = None
-        lib.or_channel_awgn.argtypes = [u64, u64, i32, i32, f64, u32, P, P]
-        lib.or_channel_awgn.restype = None
-        lib.or_channel_awgn_cw.argtypes = [u64, u64, i32, i32, f64, u32, P, P, P]
-        lib.or_channel_awgn_cw.restype = None
-        lib.or_ln_f32_array.argtypes = [P, P, ctypes.c_int64]
-        lib.or_ln_f32_array.restype = None
-        lib.or_sincos2pi_f32_array.argtypes = [P, P, P, ctypes.c_int64]
-        lib.or_sincos2pi_f32_array.restype = None
-        lib.or_variable_edges.argtypes = [i32, i32, P, P, P, P]
-        lib.or_sp_decode.argtypes = [i32, i32, P, P, i32, P, i32, i32, f64, i32, P, P, P, P, i32]
-        lib.or_ms_decode.argtypes = [i32, i32, P, P, i32, P, i32, i32, i32, P, P, P, P, i32]
-        lib.or_quantize.argtypes = [P, i32, i32, P]
-        lib.or_noms.argtypes = [i32, i32, P, P, P, i32, P, i32, P, i32, f64, P, P, i32]
-        lib.or_noms.restype = f64
-        lib.or_ldpccc_decode.argtypes = [i32, i32, P, P, i32, i32, i32, i32, i32, i32, P, f64, P, P, P,
-                                         P, i32, P, i32]
-        _lib = lib
+        _lib = _declare(ctypes.CDLL(_LIB_PATH))
     return _lib
 
 
@@ -339,12 +355,13 @@ def info_bits(seed: int, first_frame: int, nfr: int, k: int) -> np.ndarray:
 # Decoders
 # --------------------------------------------------------------------------
 def sp_decode(row_ptr, col, N: int, mu, max_iter: int, early_stop: bool = False, clip: float = 30.0,
-              form: str = "phi", nthreads: int = 1):
-    """Sum-product BP, Algorithm 1, double precision.
+              form: str = "phi", nthreads: int = 1, real: int = 64):
+    """Sum-product BP, Algorithm 1, double precision (real = 32: the same steps in binary32,
+    a diagnostic of FP32 rounding, not a reference).
 
     Returns (post[nfr][N] float64, hard[nfr][N] uint8, iters[nfr], ok[nfr]).
     """
-    lib = _load()
+    lib = _load(real)
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
     col = np.ascontiguousarray(col, dtype=np.int32)
     mu = np.ascontiguousarray(mu, dtype=np.float32)
@@ -395,13 +412,13 @@ def ms_decode(row_ptr, col, N: int, mu, max_iter: int, early_stop: bool = False,
 
 
 def ldpccc_decode(Hconv, geo: dict, T: int, I: int, mu, clip: float = 30.0, nthreads: int = 1,
-                  log_cap: int = 0):
-    """Pipelined BP of Algorithm 2 over T slots.
+                  log_cap: int = 0, real: int = 64):
+    """Pipelined BP of Algorithm 2 over T slots (real = 32: the binary32 diagnostic build).
 
     mu is [nstreams][T*c] (or [T*c]).  Returns (post, hard, decided[nstreams][T], log) where
     post/hard are [nstreams][T*c]; frames F <= T - I*(ms+1) are decided.
     """
-    lib = _load()
+    lib = _load(real)
     row_ptr = np.ascontiguousarray(Hconv.indptr, dtype=np.int32)
     col = np.ascontiguousarray(Hconv.indices, dtype=np.int32)
     c, cb, ms = geo["c"], geo["cb"], geo["ms"]

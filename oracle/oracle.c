@@ -264,13 +264,35 @@ static double or_clip(double x, double c)
     return x;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Real type of the sum-product and LDPCCC decoders.  The oracle is double    */
+/* precision; the same source compiled with -DOR_REAL_FLOAT is a binary32     */
+/* build of the same steps in the same order (a diagnostic that shows how far */
+/* any FP32 implementation of Algorithm 1 moves from the FP64 result; it is   */
+/* not a reference).                                                          */
+/* ------------------------------------------------------------------------ */
+#ifdef OR_REAL_FLOAT
+typedef float or_real;
+#define OR_R(fn) fn##f
+#else
+typedef double or_real;
+#define OR_R(fn) fn
+#endif
+
+static or_real or_clip_r(or_real x, or_real c)
+{
+    if (x > c) return c;
+    if (x < -c) return -c;
+    return x;
+}
+
 /* phi(x) = -ln tanh(x/2) = ln((e^x + 1)/(e^x - 1)) for x >= 0; phi(0) = +inf. */
 /* phi is its own inverse on [0, inf], and tanh(x/2) = exp(-phi(|x|)), so the   */
 /* product of tanh in eq. (bphs) becomes a sum of phi values.                   */
-static double or_phi(double x)
+static or_real or_phi(or_real x)
 {
-    if (x <= 0.0) return INFINITY;
-    return log1p(2.0 / expm1(x));
+    if (x <= (or_real)0) return INFINITY;
+    return OR_R(log1p)((or_real)2 / OR_R(expm1)(x));
 }
 
 /*
@@ -280,27 +302,27 @@ static double or_phi(double x)
  * The extrinsic set excludes the edge itself; an empty product is 1.
  * Every output is clipped to +-clip.
  */
-static void or_check_update(const double *beta, double *alpha, int d, double clip, int form)
+static void or_check_update(const or_real *beta, or_real *alpha, int d, or_real clip, int form)
 {
     for (int a = 0; a < d; ++a) {
         if (form == 1) {
-            double prod = 1.0;
+            or_real prod = 1;
             for (int b = 0; b < d; ++b)
-                if (b != a) prod *= tanh(beta[b] / 2.0);
-            double v;
-            if (prod >= 1.0) v = INFINITY;
-            else if (prod <= -1.0) v = -INFINITY;
-            else v = 2.0 * atanh(prod);
-            alpha[a] = or_clip(v, clip);
+                if (b != a) prod *= OR_R(tanh)(beta[b] / 2);
+            or_real v;
+            if (prod >= 1) v = INFINITY;
+            else if (prod <= -1) v = -INFINITY;
+            else v = 2 * OR_R(atanh)(prod);
+            alpha[a] = or_clip_r(v, clip);
         } else {
-            double s = 0.0;
+            or_real s = 0;
             int neg = 0;
             for (int b = 0; b < d; ++b) {
                 if (b == a) continue;
-                s += or_phi(fabs(beta[b]));
-                if (beta[b] < 0.0) neg ^= 1;
+                s += or_phi(OR_R(fabs)(beta[b]));
+                if (beta[b] < 0) neg ^= 1;
             }
-            double mag = or_phi(s); /* phi(0) = inf for an empty set */
+            or_real mag = or_phi(s); /* phi(0) = inf for an empty set */
             if (mag > clip) mag = clip;
             alpha[a] = neg ? -mag : mag;
         }
@@ -308,16 +330,17 @@ static void or_check_update(const double *beta, double *alpha, int d, double cli
 }
 
 /* One frame of Algorithm 1 with the syndrome stopping rule.                 */
-static void or_sp_frame(const or_graph *g, const float *mu_f, int max_iter, int early_stop, double clip,
+static void or_sp_frame(const or_graph *g, const float *mu_f, int max_iter, int early_stop, double clip_d,
                         int form, double *post, uint8_t *hard, int *iters, int *ok)
 {
     int E = g->E, M = g->M, N = g->N;
-    double *beta = (double *)malloc(sizeof(double) * (size_t)(E ? E : 1));
-    double *alpha = (double *)malloc(sizeof(double) * (size_t)(E ? E : 1));
-    double *mu = (double *)malloc(sizeof(double) * (size_t)(N ? N : 1));
-    double *in = (double *)malloc(sizeof(double) * (size_t)(N + 1));
-    double *outv = (double *)malloc(sizeof(double) * (size_t)(N + 1));
-    for (int n = 0; n < N; ++n) mu[n] = or_clip((double)mu_f[n], clip);
+    const or_real clip = (or_real)clip_d;
+    or_real *beta = (or_real *)malloc(sizeof(or_real) * (size_t)(E ? E : 1));
+    or_real *alpha = (or_real *)malloc(sizeof(or_real) * (size_t)(E ? E : 1));
+    or_real *mu = (or_real *)malloc(sizeof(or_real) * (size_t)(N ? N : 1));
+    or_real *in = (or_real *)malloc(sizeof(or_real) * (size_t)(N + 1));
+    or_real *outv = (or_real *)malloc(sizeof(or_real) * (size_t)(N + 1));
+    for (int n = 0; n < N; ++n) mu[n] = or_clip_r((or_real)mu_f[n], clip);
 
     /* [Initialization] beta_mn = mu_n on every edge. */
     for (int e = 0; e < E; ++e) beta[e] = mu[g->col[e]];
@@ -334,15 +357,15 @@ static void or_sp_frame(const or_graph *g, const float *mu_f, int max_iter, int 
         /* [Vertical step] eqs. (bpvs) and (bpd). */
         for (int n = 0; n < N; ++n) {
             int v0 = g->vptr[n], dv = g->vptr[n + 1] - v0;
-            double total = mu[n];
+            or_real total = mu[n];
             for (int k = 0; k < dv; ++k) total += alpha[g->vedge[v0 + k]];
             for (int k = 0; k < dv; ++k) {
-                double s = mu[n];
+                or_real s = mu[n];
                 for (int k2 = 0; k2 < dv; ++k2)
                     if (k2 != k) s += alpha[g->vedge[v0 + k2]];
-                beta[g->vedge[v0 + k]] = or_clip(s, clip);
+                beta[g->vedge[v0 + k]] = or_clip_r(s, clip);
             }
-            post[n] = or_clip(total, clip);
+            post[n] = (double)or_clip_r(total, clip);
             /* eq. (hrddcs): 0 if beta_n >= 0, else 1 */
             hard[n] = post[n] < 0.0 ? 1 : 0;
         }
@@ -494,14 +517,15 @@ int or_ms_decode(int M, int N, const int *row_ptr, const int *col, int nfr, cons
 /* Returns the number of decided frames, or -1.                               */
 /* ------------------------------------------------------------------------ */
 static int or_ldpccc_stream(const or_graph *g, int T, int c, int cb, int ms, int I, const float *mu_f,
-                            double clip, double *post, uint8_t *hard, uint8_t *decided, int *log,
+                            double clip_d, double *post, uint8_t *hard, uint8_t *decided, int *log,
                             int log_cap, int *log_n)
 {
     int E = g->E;
-    double *beta = (double *)calloc((size_t)(E ? E : 1), sizeof(double));
-    double *alpha = (double *)calloc((size_t)(E ? E : 1), sizeof(double));
-    double *in = (double *)malloc(sizeof(double) * (size_t)(g->N + 1));
-    double *outv = (double *)malloc(sizeof(double) * (size_t)(g->N + 1));
+    const or_real clip = (or_real)clip_d;
+    or_real *beta = (or_real *)calloc((size_t)(E ? E : 1), sizeof(or_real));
+    or_real *alpha = (or_real *)calloc((size_t)(E ? E : 1), sizeof(or_real));
+    or_real *in = (or_real *)malloc(sizeof(or_real) * (size_t)(g->N + 1));
+    or_real *outv = (or_real *)malloc(sizeof(or_real) * (size_t)(g->N + 1));
     int ndec = 0, nl = 0;
 #define OR_LOG(t_, k_, x_, i_)                                                                     \
     do {                                                                                           \
@@ -514,7 +538,7 @@ static int or_ldpccc_stream(const or_graph *g, int T, int c, int cb, int ms, int
     for (int t = 0; t < T; ++t) {
         /* [Initialization] frame t and its channel messages enter processor 1. */
         for (int v = t * c; v < (t + 1) * c; ++v) {
-            double m = or_clip((double)mu_f[v], clip);
+            or_real m = or_clip_r((or_real)mu_f[v], clip);
             for (int k = g->vptr[v]; k < g->vptr[v + 1]; ++k) beta[g->vedge[k]] = m;
         }
         OR_LOG(t, 0, t, 1);
@@ -537,12 +561,12 @@ static int or_ldpccc_stream(const or_graph *g, int T, int c, int cb, int ms, int
             OR_LOG(t, 2, F, i);
             for (int n = F * c; n < (F + 1) * c; ++n) {
                 int v0 = g->vptr[n], dv = g->vptr[n + 1] - v0;
-                double m0 = or_clip((double)mu_f[n], clip);
+                or_real m0 = or_clip_r((or_real)mu_f[n], clip);
                 for (int k = 0; k < dv; ++k) {
-                    double s = m0;
+                    or_real s = m0;
                     for (int k2 = 0; k2 < dv; ++k2)
                         if (k2 != k) s += alpha[g->vedge[v0 + k2]];
-                    beta[g->vedge[v0 + k]] = or_clip(s, clip);
+                    beta[g->vedge[v0 + k]] = or_clip_r(s, clip);
                 }
             }
         }
@@ -553,11 +577,11 @@ static int or_ldpccc_stream(const or_graph *g, int T, int c, int cb, int ms, int
                 OR_LOG(t, 3, F, I);
                 for (int n = F * c; n < (F + 1) * c; ++n) {
                     int v0 = g->vptr[n], dv = g->vptr[n + 1] - v0;
-                    double total = or_clip((double)mu_f[n], clip);
+                    or_real total = or_clip_r((or_real)mu_f[n], clip);
                     for (int k = 0; k < dv; ++k) total += alpha[g->vedge[v0 + k]];
-                    total = or_clip(total, clip);
-                    post[n] = total;
-                    hard[n] = total < 0.0 ? 1 : 0;
+                    total = or_clip_r(total, clip);
+                    post[n] = (double)total;
+                    hard[n] = total < 0 ? 1 : 0;
                 }
                 decided[F] = 1;
                 ++ndec;

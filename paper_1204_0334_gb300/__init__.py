@@ -87,6 +87,7 @@ _SIGNATURES = [
     ("ldpc_phi_eval", ctypes.c_int, [P, P, ctypes.c_int64, ctypes.c_int32, P]),
     ("ldpc_profile_enable", ctypes.c_int, [ctypes.c_int32]),
     ("ldpc_profile_read", ctypes.c_int, [P]),
+    ("ldpc_bandwidth_probe", ctypes.c_int, [P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P, P]),
 ]
 
 
@@ -396,6 +397,15 @@ def ldpc_profile_read() -> dict:
     r = Profile()
     _check(lib().ldpc_profile_read(ctypes.byref(r)), "ldpc_profile_read")
     return {k: getattr(r, k) for k, _ in Profile._fields_}
+
+
+def ldpc_bandwidth_probe(src, dst, reps: int, mode: int, stream=None) -> float:
+    """GB/s of the library's streaming probe: mode 0 reads src through L2, mode 1 copies src to dst."""
+    out = ctypes.c_double(0.0)
+    nbytes = src.numel() * src.element_size()
+    _check(lib().ldpc_bandwidth_probe(_ptr(src), _ptr(dst), nbytes, int(reps), int(mode), ctypes.byref(out),
+                                      _stream(stream)), "ldpc_bandwidth_probe")
+    return out.value
 
 
 # ----------------------------------------------------------------- convenience

@@ -41,6 +41,46 @@ void prof_end(int slot, cudaStream_t s) {
     cudaEventRecord(g_pool[(size_t)slot].b, s);
 }
 
+// Bandwidth probe kernels: a grid-stride sweep over the buffer with four independent
+// 16-byte loads in flight per thread.  mode 0 reads through L2 only (ld.global.cg, so
+// an L2-resident buffer is served by L2, not L1) and folds the data into one word per
+// thread block; mode 1 copies src to dst.
+__global__ void __launch_bounds__(256) bw_read_kernel(const uint4 *__restrict__ src, size_t n16,
+                                                     uint32_t *__restrict__ sink) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t acc = 0;
+    for (; i + 3 * stride < n16; i += 4 * stride) {
+        uint4 a, b, c, d;
+        asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w) : "l"(src + i));
+        asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w) : "l"(src + i + stride));
+        asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(c.x), "=r"(c.y), "=r"(c.z), "=r"(c.w) : "l"(src + i + 2 * stride));
+        asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(d.x), "=r"(d.y), "=r"(d.z), "=r"(d.w) : "l"(src + i + 3 * stride));
+        acc ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w ^ c.x ^ c.y ^ c.z ^ c.w ^ d.x ^ d.y ^ d.z ^ d.w;
+    }
+    for (; i < n16; i += stride) {
+        uint4 a;
+        asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w) : "l"(src + i));
+        acc ^= a.x ^ a.y ^ a.z ^ a.w;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc ^= __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicXor(sink + blockIdx.x, acc);
+}
+
+__global__ void __launch_bounds__(256) bw_copy_kernel(const uint4 *__restrict__ src, uint4 *__restrict__ dst,
+                                                     size_t n16) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n16; i += 4 * stride) {
+        const uint4 a = src[i], b = src[i + stride], c = src[i + 2 * stride], d = src[i + 3 * stride];
+        dst[i] = a;
+        dst[i + stride] = b;
+        dst[i + 2 * stride] = c;
+        dst[i + 3 * stride] = d;
+    }
+    for (; i < n16; i += stride) dst[i] = src[i];
+}
+
 }  // namespace ldpc
 
 using namespace ldpc;
@@ -74,6 +114,50 @@ ldpc_status ldpc_profile_read(ldpc_profile *out) {
             out->vn_ms += ms;
         }
     }
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_bandwidth_probe(const void *src, void *dst, int64_t bytes, int32_t reps, int32_t mode,
+                                 double *gbs_out, void *stream) {
+    if (!src || !dst || !gbs_out || bytes < 16 || (bytes & 15) || reps < 1 || reps > 100000 ||
+        (mode != 0 && mode != 1) || ((uintptr_t)src & 15) || ((uintptr_t)dst & 15)) {
+        set_error("need 16-byte aligned device src/dst, bytes a positive multiple of 16, 1 <= reps <= 100000, "
+                  "mode 0 or 1, gbs_out");
+        return LDPC_EINVAL;
+    }
+    if (pointer_kind(src) != 0 || pointer_kind(dst) != 0) {
+        set_error("ldpc_bandwidth_probe takes device buffers");
+        return LDPC_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 1;
+    LDPC_CUDA_TRY(cudaGetDevice(&dev));
+    LDPC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned blocks = (unsigned)sms * 8u;
+    if (mode == 0 && (size_t)bytes < (size_t)blocks * 4u + 16u) {
+        set_error("mode 0 needs dst to hold one word per block (%u blocks)", blocks);
+        return LDPC_EINVAL;
+    }
+    const size_t n16 = (size_t)bytes / 16;
+    cudaEvent_t a, b;
+    LDPC_CUDA_TRY(cudaEventCreate(&a));
+    LDPC_CUDA_TRY(cudaEventCreate(&b));
+    // one untimed sweep (brings an L2-sized buffer into L2), then the timed ones
+    for (int r = 0; r <= reps; ++r) {
+        if (r == 1) cudaEventRecord(a, s);
+        count_launch();
+        if (mode == 0) bw_read_kernel<<<blocks, 256, 0, s>>>((const uint4 *)src, n16, (uint32_t *)dst);
+        else bw_copy_kernel<<<blocks, 256, 0, s>>>((const uint4 *)src, (uint4 *)dst, n16);
+    }
+    cudaEventRecord(b, s);
+    cudaError_t e = cudaEventSynchronize(b);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) return cuda_fail(e, "bandwidth probe");
+    const double moved = (double)bytes * reps * (mode == 1 ? 2.0 : 1.0);
+    *gbs_out = ms > 0 ? moved / (ms * 1e-3) / 1e9 : 0.0;
     return LDPC_OK;
 }
 
