@@ -372,6 +372,9 @@ def run_ours(a):
         line["variants"] = variants(a, pkg, code, stream, opts)
     if not a.no_e2e:
         line["e2e"] = e2e(a, pkg, code, stream, opts)
+    if not a.no_variants:
+        # the library's slot-count autotuner on the same code and options (the headline keeps its slots)
+        line["autotune"] = pkg.ldpc_tune_slots(code.handle, a.ebn0, a.seed, opts, stream)
     if not a.no_ldpccc:
         line["ldpccc"] = ldpccc_bench(a, pkg, stream)
         line["ldpccc_tanner"] = ldpccc_bench(a, pkg, stream, tanner=True)
@@ -401,7 +404,7 @@ def bandwidth_probes(pkg, stream) -> dict:
     small = torch.empty(32 << 20, dtype=torch.uint8, device="cuda")
     small.random_(0, 255)
     sink = torch.zeros(1 << 16, dtype=torch.uint8, device="cuda")
-    l2 = pkg.ldpc_bandwidth_probe(small, sink, 400, 0, stream)
+    l2 = pkg.ldpc_bandwidth_probe(small, sink, 2000, 0, stream)
     big = torch.empty(2 << 30, dtype=torch.uint8, device="cuda")
     dst = torch.empty_like(big)
     hbm = pkg.ldpc_bandwidth_probe(big, dst, 5, 1, stream)

@@ -253,11 +253,27 @@ typedef struct {
  * resumed from (seed, first_frame + out->frames) and partial results added.
  * Blocks the calling thread until the run ends (it reads the totals every
  * two steps).
+ *   gamma: frame slots; 0 = the slot count ldpc_tune_slots picked for this code and
+ *   opts->algo / opts->msg (tuned on the spot, at this Eb/N0 and seed, if it has not been).
  *   out: host pointer, filled on return.
  */
 ldpc_status ldpc_ber_sim(ldpc_code code, double ebn0_db, uint64_t seed, uint64_t first_frame, int64_t max_frames,
                          int64_t target_frame_errors, int32_t gamma, const ldpc_decode_opts *opts,
                          ldpc_ber_result *out, void *stream);
+/*
+ * ldpc_tune_slots -- the autotuner of the continuous simulation's slot count Gamma
+ * (no paper counterpart; the paper fixes Gamma = 32 for its GPU, Sec. IV-A).  Times
+ * ldpc_ber_sim's decoding at 16384, 8192, 4096, 2048 and 1024 slots (a settling run
+ * of one frame per slot, then a timed run of four frames per slot, frames drawn from
+ * the reserved id range [2^63, 2^63 + 2^43), which the caller's runs should avoid) and
+ * keeps the fastest in the code object for opts->algo / opts->msg.
+ *   gamma_out: host int32, the slot count picked; mbit_s: host double[5] (decoded
+ *   information Mbit/s of each candidate, in the order above) or NULL.
+ * Synchronizes the stream; grows the code's workspace to 16384 slots.
+ * Errors: as ldpc_ber_sim.
+ */
+ldpc_status ldpc_tune_slots(ldpc_code code, double ebn0_db, uint64_t seed, const ldpc_decode_opts *opts,
+                            int32_t *gamma_out, double *mbit_s, void *stream);
 
 /*
  * LDPC convolutional codes derived from a QC base (Sec. II-D): partition H_QC
@@ -356,7 +372,9 @@ ldpc_status ldpc_noms_backward(ldpc_code code, const float *params, float *grad,
  * alpha = prod(sign) * phi(sum_{n' != n} phi(|beta_n'|)) (phi is its own inverse).
  * Exposed so that its accuracy can be checked against the definition.
  *   x, y: device float [n]; variant 0 = the decoder's SFU-based evaluation,
- *   variant 1 = CUDA's expm1f/log1pf form.  Errors: LDPC_EINVAL.
+ *   variant 1 = CUDA's expm1f/log1pf form, variant 2 = the decoder's evaluation
+ *   on packed pairs (consecutive elements; bit-identical to variant 0 by
+ *   construction).  Errors: LDPC_EINVAL.
  */
 ldpc_status ldpc_phi_eval(const float *x, float *y, int64_t n, int32_t variant, void *stream);
 
@@ -384,11 +402,12 @@ ldpc_status ldpc_profile_read(ldpc_profile *out);
  * ldpc_bandwidth_probe -- measurement aid (no paper counterpart): the memory
  * bandwidth a plain streaming kernel of this library reaches, as the peak that
  * the decoders' L2 byte rates are compared with.  mode 0 reads `bytes` of src
- * `reps` times through L2 (ld.global.cg; a buffer smaller than L2 is then
- * served by L2) and writes one word per thread block to dst (at least
- * 4 * 8 * SM-count bytes); mode 1 copies src to dst `reps` times (read + write
- * bytes counted).  One untimed sweep precedes the timed ones; the time comes
- * from CUDA events on `stream`, and *gbs_out = bytes moved / time / 1e9.
+ * `reps` times through L2 (ld.global.cg, all sweeps in one launch; a buffer
+ * smaller than L2 is then served by L2) and writes one word per thread block to
+ * dst (at least 4 * 8 * SM-count bytes); mode 1 copies src to dst `reps` times
+ * (one launch each, read + write bytes counted).  One untimed sweep precedes
+ * the timed ones; the time comes from CUDA events on `stream`, and
+ * *gbs_out = bytes moved / time / 1e9.
  * src, dst: device buffers, 16-byte aligned; bytes a positive multiple of 16.
  * Synchronizes the stream.  Errors: LDPC_EINVAL, LDPC_ECUDA.
  */

@@ -88,6 +88,7 @@ _SIGNATURES = [
     ("ldpc_profile_enable", ctypes.c_int, [ctypes.c_int32]),
     ("ldpc_profile_read", ctypes.c_int, [P]),
     ("ldpc_bandwidth_probe", ctypes.c_int, [P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P, P]),
+    ("ldpc_tune_slots", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, P, P, P, P]),
 ]
 
 
@@ -397,6 +398,18 @@ def ldpc_profile_read() -> dict:
     r = Profile()
     _check(lib().ldpc_profile_read(ctypes.byref(r)), "ldpc_profile_read")
     return {k: getattr(r, k) for k, _ in Profile._fields_}
+
+
+TUNE_SLOTS = (16384, 8192, 4096, 2048, 1024)
+
+
+def ldpc_tune_slots(code: int, ebn0_db: float, seed: int, opts: DecodeOpts, stream=None) -> dict:
+    """The slot count the library's autotuner picks for this code and opts, with each candidate's Mbit/s."""
+    g = ctypes.c_int32(0)
+    rates = (ctypes.c_double * len(TUNE_SLOTS))()
+    _check(lib().ldpc_tune_slots(ctypes.c_void_p(code), float(ebn0_db), int(seed), ctypes.byref(opts),
+                                 ctypes.byref(g), rates, _stream(stream)), "ldpc_tune_slots")
+    return {"gamma": int(g.value), "candidates": dict(zip(TUNE_SLOTS, list(rates)))}
 
 
 def ldpc_bandwidth_probe(src, dst, reps: int, mode: int, stream=None) -> float:

@@ -387,11 +387,69 @@ ldpc_status ldpc_channel(ldpc_code c, double ebn0_db, uint64_t seed, uint64_t fi
     return LDPC_OK;
 }
 
+// candidate slot counts of the autotuner, largest first (the workspace is allocated once)
+static const int kTuneSlots[] = {16384, 8192, 4096, 2048, 1024};
+constexpr int kTuneCands = 5;
+
+ldpc_status ldpc_tune_slots(ldpc_code c, double ebn0_db, uint64_t seed, const ldpc_decode_opts *opts,
+                            int32_t *gamma_out, double *mbit_s, void *stream) {
+    if (!c || !gamma_out || !std::isfinite(ebn0_db)) {
+        set_error("need code, gamma_out and a finite Eb/N0");
+        return LDPC_EINVAL;
+    }
+    if (c->sparse) {
+        set_error("the continuous simulation takes QC codes");
+        return LDPC_EUNSUPPORTED;
+    }
+    ldpc_status st = check_opts(c, opts);
+    if (st != LDPC_OK) return st;
+    if (!(c->rate > 0.0)) {
+        set_error("design rate K/N = %g is not positive", c->rate);
+        return LDPC_EINVAL;
+    }
+    const ldpc_decode_opts &o = *opts;
+    cudaStream_t s = (cudaStream_t)stream;
+    const double sigma = channel_sigma(c, ebn0_db);
+    const double K = (double)c->d.N - c->d.M;
+    unsigned long long h[8];
+    int best = 0;
+    double best_rate = -1.0;
+    for (int i = 0; i < kTuneCands; ++i) {
+        const int slots = kTuneSlots[i];
+        // frames of a reserved id range (top bit set): a short run to settle the workspace and
+        // caches, then the timed run of four frames per slot
+        const uint64_t base = (1ull << 63) + (uint64_t)i * (1ull << 40);
+        st = qc_ber_sim_refill(c, sigma, seed, base, slots, 1ll << 60, slots, o, h, s);
+        if (st != LDPC_OK) return st;
+        const auto t0 = std::chrono::steady_clock::now();
+        st = qc_ber_sim_refill(c, sigma, seed, base + (1ull << 39), 4ll * slots, 1ll << 60, slots, o, h, s);
+        if (st != LDPC_OK) return st;
+        const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        const double rate = sec > 0 ? (double)h[0] * K / sec / 1e6 : 0.0;
+        if (mbit_s) mbit_s[i] = rate;
+        if (rate > best_rate) best_rate = rate, best = slots;
+    }
+    c->tuned_slots[o.algo][o.msg] = best;
+    *gamma_out = best;
+    return LDPC_OK;
+}
+
 ldpc_status ldpc_ber_sim(ldpc_code c, double ebn0_db, uint64_t seed, uint64_t first_frame, int64_t max_frames,
                          int64_t target_frame_errors, int32_t gamma, const ldpc_decode_opts *opts,
                          ldpc_ber_result *out, void *stream) {
-    if (!c || !out || gamma < 1 || max_frames < 1 || !std::isfinite(ebn0_db)) {
-        set_error("need code, out, gamma >= 1, max_frames >= 1 and a finite Eb/N0");
+    if (!c || !out || gamma < 0 || max_frames < 1 || !std::isfinite(ebn0_db)) {
+        set_error("need code, out, gamma >= 0, max_frames >= 1 and a finite Eb/N0");
+        return LDPC_EINVAL;
+    }
+    if (gamma == 0 && opts && !c->sparse && opts->algo >= 0 && opts->algo < 3 && opts->msg >= 0 && opts->msg < 3) {
+        gamma = c->tuned_slots[opts->algo][opts->msg];
+        if (gamma == 0) {
+            ldpc_status ts = ldpc_tune_slots(c, ebn0_db, seed, opts, &gamma, nullptr, stream);
+            if (ts != LDPC_OK) return ts;
+        }
+    }
+    if (gamma < 1) {
+        set_error("gamma must be >= 1, or 0 for the tuned slot count");
         return LDPC_EINVAL;
     }
     if (!(c->rate > 0.0)) {
@@ -423,8 +481,8 @@ ldpc_status ldpc_ber_sim(ldpc_code c, double ebn0_db, uint64_t seed, uint64_t fi
 }
 
 ldpc_status ldpc_phi_eval(const float *x, float *y, int64_t n, int32_t variant, void *stream) {
-    if (!x || !y || n < 0 || n > (int64_t)1 << 30 || (variant != 0 && variant != 1)) {
-        set_error("need device x, y, 0 <= n <= 2^30 and variant 0 or 1");
+    if (!x || !y || n < 0 || n > (int64_t)1 << 30 || variant < 0 || variant > 2) {
+        set_error("need device x, y, 0 <= n <= 2^30 and variant 0, 1 or 2");
         return LDPC_EINVAL;
     }
     if (pointer_kind(x) != 0 || pointer_kind(y) != 0) {

@@ -98,6 +98,7 @@ struct ldpc_code_s {
     std::vector<int> h_rp, h_col;    // sparse code: H in compressed-row form (host copy)
     int device = 0;
     double rate = 0.0;   // design rate K/N
+    int tuned_slots[3][3] = {};      // slot count picked by ldpc_tune_slots, per [algo][msg] (0 = not tuned)
     ldpc::DecodeWs ws;
 };
 

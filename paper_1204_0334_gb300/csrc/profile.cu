@@ -41,27 +41,30 @@ void prof_end(int slot, cudaStream_t s) {
     cudaEventRecord(g_pool[(size_t)slot].b, s);
 }
 
-// Bandwidth probe kernels: a grid-stride sweep over the buffer with four independent
+// Bandwidth probe kernels: grid-stride sweeps over the buffer with four independent
 // 16-byte loads in flight per thread.  mode 0 reads through L2 only (ld.global.cg, so
-// an L2-resident buffer is served by L2, not L1) and folds the data into one word per
-// thread block; mode 1 copies src to dst.
-__global__ void __launch_bounds__(256) bw_read_kernel(const uint4 *__restrict__ src, size_t n16,
+// an L2-resident buffer is served by L2, not L1), `sweeps` times within one launch (a
+// sweep of an L2-sized buffer is too short to time against the launch), and folds the
+// data into one word per thread block; mode 1 copies src to dst.
+__global__ void __launch_bounds__(256) bw_read_kernel(const uint4 *__restrict__ src, size_t n16, int sweeps,
                                                      uint32_t *__restrict__ sink) {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
-    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t acc = 0;
-    for (; i + 3 * stride < n16; i += 4 * stride) {
-        uint4 a, b, c, d;
-        asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w) : "l"(src + i));
-        asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w) : "l"(src + i + stride));
-        asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(c.x), "=r"(c.y), "=r"(c.z), "=r"(c.w) : "l"(src + i + 2 * stride));
-        asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(d.x), "=r"(d.y), "=r"(d.z), "=r"(d.w) : "l"(src + i + 3 * stride));
-        acc ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w ^ c.x ^ c.y ^ c.z ^ c.w ^ d.x ^ d.y ^ d.z ^ d.w;
-    }
-    for (; i < n16; i += stride) {
-        uint4 a;
-        asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w) : "l"(src + i));
-        acc ^= a.x ^ a.y ^ a.z ^ a.w;
+    for (int r = 0; r < sweeps; ++r) {
+        size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+        for (; i + 3 * stride < n16; i += 4 * stride) {
+            uint4 a, b, c, d;
+            asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w) : "l"(src + i));
+            asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w) : "l"(src + i + stride));
+            asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(c.x), "=r"(c.y), "=r"(c.z), "=r"(c.w) : "l"(src + i + 2 * stride));
+            asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(d.x), "=r"(d.y), "=r"(d.z), "=r"(d.w) : "l"(src + i + 3 * stride));
+            acc ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w ^ c.x ^ c.y ^ c.z ^ c.w ^ d.x ^ d.y ^ d.z ^ d.w;
+        }
+        for (; i < n16; i += stride) {
+            uint4 a;
+            asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w) : "l"(src + i));
+            acc ^= a.x ^ a.y ^ a.z ^ a.w;
+        }
     }
     for (int o = 16; o > 0; o >>= 1) acc ^= __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) atomicXor(sink + blockIdx.x, acc);
@@ -142,12 +145,20 @@ ldpc_status ldpc_bandwidth_probe(const void *src, void *dst, int64_t bytes, int3
     cudaEvent_t a, b;
     LDPC_CUDA_TRY(cudaEventCreate(&a));
     LDPC_CUDA_TRY(cudaEventCreate(&b));
-    // one untimed sweep (brings an L2-sized buffer into L2), then the timed ones
-    for (int r = 0; r <= reps; ++r) {
-        if (r == 1) cudaEventRecord(a, s);
+    // one untimed sweep (brings an L2-sized buffer into L2), then the timed ones: reads in one
+    // launch, copies one launch per sweep
+    count_launch();
+    if (mode == 0) bw_read_kernel<<<blocks, 256, 0, s>>>((const uint4 *)src, n16, 1, (uint32_t *)dst);
+    else bw_copy_kernel<<<blocks, 256, 0, s>>>((const uint4 *)src, (uint4 *)dst, n16);
+    cudaEventRecord(a, s);
+    if (mode == 0) {
         count_launch();
-        if (mode == 0) bw_read_kernel<<<blocks, 256, 0, s>>>((const uint4 *)src, n16, (uint32_t *)dst);
-        else bw_copy_kernel<<<blocks, 256, 0, s>>>((const uint4 *)src, (uint4 *)dst, n16);
+        bw_read_kernel<<<blocks, 256, 0, s>>>((const uint4 *)src, n16, reps, (uint32_t *)dst);
+    } else {
+        for (int r = 0; r < reps; ++r) {
+            count_launch();
+            bw_copy_kernel<<<blocks, 256, 0, s>>>((const uint4 *)src, (uint4 *)dst, n16);
+        }
     }
     cudaEventRecord(b, s);
     cudaError_t e = cudaEventSynchronize(b);

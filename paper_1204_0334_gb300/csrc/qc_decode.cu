@@ -392,7 +392,19 @@ ldpc_status unpack_frames_w32(const float *src, float *dst, int gamma, int N, cu
 }
 
 // the check-node transform on its own, for verification (ldpc_phi_eval)
+// variant 0: the decoders' scalar evaluation; 1: CUDA's expm1f/log1pf form; 2: the packed-pair
+// evaluation the node passes use (pairs of consecutive elements)
 __global__ void phi_eval_kernel(const float *__restrict__ x, float *__restrict__ y, int n, int variant) {
+    if (variant == 2) {
+        for (int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x); i < n; i += 2 * gridDim.x * blockDim.x) {
+            const float x0 = x[i], x1 = i + 1 < n ? x[i + 1] : 1.0f;
+            float y0, y1;
+            phi2(x0, x1, y0, y1);
+            y[i] = y0;
+            if (i + 1 < n) y[i + 1] = y1;
+        }
+        return;
+    }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         y[i] = variant == 0 ? phi_f(x[i]) : phi_ref(x[i]);
 }

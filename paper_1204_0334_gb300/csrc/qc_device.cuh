@@ -84,6 +84,88 @@ __device__ __forceinline__ float phi_fin(float x) {
     const float hi = phi_hi<false>(x), lo = phi_lo(x);
     return x < 1.0f ? lo : hi;
 }
+// ---------------------------------------------------------------------------
+// Packed pairs: the sm_100-family FP32x2 instructions (add/mul/fma .rn.f32x2) do two
+// IEEE binary32 operations, each rounded to nearest-even, per issue slot.  phi2 /
+// phi_fin2 run phi_f / phi_fin on two arguments with exactly the scalar versions'
+// operations (so the results are bit-identical), halving the issue cost of the
+// polynomial and error-term arithmetic; ex2/lg2 and the min/select stay scalar.
+// ---------------------------------------------------------------------------
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 f2(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2split(f32x2 r, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ f32x2 f2mul(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2add(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2fma(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2c(float c) { return f2(c, c); }
+
+// phi_hi of two arguments (already clamped when CLAMP is wanted), as pairs
+__device__ __forceinline__ f32x2 phi_hi2(f32x2 x) {
+    const float L2E = 1.44269502f, L2E_LO = 1.92596299e-8f, LN2 = 0.693147182f;
+    const f32x2 a = f2mul(x, f2c(-L2E));         // -x * L2E
+    const f32x2 na = f2mul(x, f2c(L2E));         // -a, exactly
+    f32x2 alo = f2fma(x, f2c(-L2E), na);         // fmaf(-x, L2E, -a)
+    alo = f2fma(x, f2c(-L2E_LO), alo);           // fmaf(-x, L2E_LO, alo)
+    float a0, a1;
+    f2split(a, a0, a1);
+    const f32x2 t0 = f2(ex2_approx(a0), ex2_approx(a1));
+    const f32x2 t = f2fma(t0, f2mul(alo, f2c(LN2)), t0);
+    const f32x2 v = f2mul(t, t);
+    const f32x2 w = f2mul(f2c(2.0f), t);
+    f32x2 P = f2fma(f2c(0.147845685f), v, f2c(0.138392285f));
+    P = f2fma(P, v, f2c(0.200207084f));
+    P = f2fma(P, v, f2c(0.333330393f));
+    const f32x2 sv = f2mul(v, P);
+    return f2fma(w, sv, w);
+}
+__device__ __forceinline__ f32x2 phi_lo2(f32x2 x) {
+    const float LN2 = 0.693147182f;
+    const f32x2 y = f2mul(f2c(0.5f), x);
+    const f32x2 u = f2mul(y, y);
+    f32x2 G = f2fma(f2c(-0.00555368373f), u, f2c(0.0216362253f));
+    G = f2fma(G, u, f2c(-0.0777590200f));
+    G = f2fma(G, u, f2c(0.333332866f));
+    G = f2mul(u, G);
+    float y0, y1;
+    f2split(y, y0, y1);
+    return f2fma(f2(lg2_approx(y0), lg2_approx(y1)), f2c(-LN2), G);
+}
+// phi_f of (x0, x1)
+__device__ __forceinline__ void phi2(float x0, float x1, float &y0, float &y1) {
+    float h0, h1, l0, l1;
+    f2split(phi_hi2(f2(fminf(x0, 100.0f), fminf(x1, 100.0f))), h0, h1);
+    f2split(phi_lo2(f2(x0, x1)), l0, l1);
+    y0 = x0 < 1.0f ? l0 : h0;
+    y1 = x1 < 1.0f ? l1 : h1;
+}
+// phi_fin of (x0, x1) (finite arguments, no clamp)
+__device__ __forceinline__ void phi_fin2(float x0, float x1, float &y0, float &y1) {
+    const f32x2 x = f2(x0, x1);
+    float h0, h1, l0, l1;
+    f2split(phi_hi2(x), h0, h1);
+    f2split(phi_lo2(x), l0, l1);
+    y0 = x0 < 1.0f ? l0 : h0;
+    y1 = x1 < 1.0f ? l1 : h1;
+}
+
 // Transformed message storage (the variable pass stores what the check pass sums):
 // FP32 keeps sign(beta) * phi(|beta|); FP16 keeps it scaled by 2^12, so that the
 // normal range of halves covers phi of |beta| in [2.3e-7, 18.7] -- a larger phi

@@ -44,8 +44,9 @@ struct CnStage {
 // ring holds only message packages and three blocks of eight warps fit on an SM.
 // ---------------------------------------------------------------------------
 // SPARSE: a general code (index tables; edges of a row are consecutive)
+// (register budgets: three blocks per SM for one-frame lane words, two otherwise)
 template <int DCMAX, int V, bool XF, int MODE, bool REG, bool SPARSE = false>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, (V == 1 ? 3 : 2))
 cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__restrict__ flags,
                const uint32_t *__restrict__ fresh, const int *__restrict__ act, float clip,
                const float *__restrict__ nparams, const int *__restrict__ ages, int T, SparseTab tab) {
@@ -163,26 +164,29 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
             if (fr[v]) frmask |= 0xffu << (8 * v);
         }
         if constexpr (MODE == kModeSP) {
-            // xs: signed terms sign(beta) * phi(|beta|) (XF: as stored by the variable pass);
-            // the output sign is the XOR of the other edges' sign bits
-            float xs[DCMAX][V];
-            uint32_t sgn[V];
+            // xa: |sign(beta) * phi(|beta|)| (XF: as stored by the variable pass); nm: the edges'
+            // sign bits (bit l); the output sign of edge l is the XOR of the other edges' signs
+            static_assert(DCMAX <= 32, "sign masks of one word");
+            float xa[DCMAX][V];
+            uint32_t nm[V];
 #pragma unroll
-            for (int v = 0; v < V; ++v) sgn[v] = 0u;
+            for (int v = 0; v < V; ++v) nm[v] = 0u;
 #pragma unroll
             for (int l = 0; l < DCMAX; ++l) {
 #pragma unroll
-                for (int v = 0; v < V; ++v) xs[l][v] = 0.0f;
+                for (int v = 0; v < V; ++v) xa[l][v] = 0.0f;
                 if (REG || (l < LB && __shfl_sync(0xffffffffu, myoff, l) >= 0)) {
                     float x[V];
                     Lane<V>::unpack(S[l * 32 + lane], x);
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
-                        xs[l][v] = XF ? x[v] * XfScale<V>::load : copysignf(phi_f(fabsf(x[v])), x[v]);
-                        sgn[v] ^= __float_as_uint(x[v]);
+                        xa[l][v] = XF ? fabsf(x[v]) * XfScale<V>::load : phi_f(fabsf(x[v]));
+                        nm[v] |= (__float_as_uint(x[v]) >> 31) << l;
                     }
                 }
             }
+            // pre[l]: the extrinsic sum over the other edges of the row, as prefix + suffix
+            // (forward-backward, no subtraction from the total)
             float pre[DCMAX][V];
             {
                 float acc[V];
@@ -193,29 +197,49 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
                         pre[l][v] = acc[v];
-                        acc[v] += fabsf(xs[l][v]);
+                        acc[v] += xa[l][v];
                     }
-            }
-            float suf[V];
 #pragma unroll
-            for (int v = 0; v < V; ++v) suf[v] = 0.0f;
+                for (int v = 0; v < V; ++v) acc[v] = 0.0f;
 #pragma unroll
-            for (int l = DCMAX - 1; l >= 0; --l) {
-                const int o = __shfl_sync(0xffffffffu, myoff, l);
-                if (REG || o >= 0) {
-                    float out[V];
+                for (int l = DCMAX - 1; l >= 0; --l)
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
-                        const float mag = fminf(phi_f(pre[l][v] + suf[v]), clip);
-                        // |alpha| with the XOR of the other edges' signs; 0 for a frame that has just
-                        // entered its slot
-                        out[v] = __uint_as_float(
-                            (__float_as_uint(mag) | ((sgn[v] ^ __float_as_uint(xs[l][v])) & 0x80000000u)) & keep[v]);
+                        pre[l][v] += acc[v];
+                        acc[v] += xa[l][v];
                     }
-                    if (lane_on) gmsg[(size_t)o * 32] = Lane<V>::pack(out);
+            }
+            uint32_t par[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) par[v] = __popc(nm[v]) & 1u;
+            // phi of the sums on packed pairs: the two frames of a lane word (V = 2), or two
+            // consecutive edges (V = 1); |alpha| with the XOR of the other edges' signs, 0 for a
+            // frame that has just entered its slot
+            static_assert(V <= 2 || MODE != kModeSP, "sum-product lane words hold one or two frames");
+            static_assert(DCMAX % 2 == 0, "edge pairs");
+#pragma unroll
+            for (int l = 0; l < DCMAX; l += (V == 1 ? 2 : 1)) {
+                float mag[2][V];
+                if constexpr (V == 1) {
+                    phi2(pre[l][0], pre[l + 1][0], mag[0][0], mag[1][0]);
+                } else {
+                    phi2(pre[l][0], pre[l][1], mag[0][0], mag[0][1]);
                 }
 #pragma unroll
-                for (int v = 0; v < V; ++v) suf[v] += fabsf(xs[l][v]);
+                for (int h = 0; h < (V == 1 ? 2 : 1); ++h) {
+                    const int le = l + h;
+                    const int o = __shfl_sync(0xffffffffu, myoff, le);
+                    if (REG || o >= 0) {
+                        float out[V];
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            const float m = fminf(mag[h][v], clip);
+                            const uint32_t sb = ((par[v] ^ (nm[v] >> le)) & 1u) << 31;
+                            out[v] = __uint_as_float((__float_as_uint(m) | sb) & keep[v]);
+                        }
+                        if (lane_on) gmsg[(size_t)o * 32] = Lane<V>::pack(out);
+                    }
+                }
             }
         } else if constexpr (MODE == kModeNOMS) {
             // normalized/offset min-sum: alpha = sign * max(w * m - o, 0), (w, o) of this
@@ -569,25 +593,48 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
                         for (int v = 0; v < V; ++v) tot[v] += aj[jj][v];
                     }
                 }
+                // extrinsic sums beta = mu + the other edges' alpha
+                float bs[JMAX][V];
 #pragma unroll
-                for (int jj = 0; jj < JMAX; ++jj) {
-                    if (!REG && eo[jj] < 0) continue;  // warp-uniform
-                    float b[V];
+                for (int jj = 0; jj < JMAX; ++jj)
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
                         float s = m[v];
 #pragma unroll
                         for (int j2 = 0; j2 < JMAX; ++j2)
                             if (j2 != jj) s += aj[j2][v];
-                        if (XF) {
-                            // the check pass sums phi(|beta|): evaluate it here, from the unrounded
-                            // beta (|clip(s)| = min(|s|, clip)), and keep beta's sign
-                            b[v] = with_sign_of(phi_fin(fminf(fabsf(s), clip)) * XfScale<V>::store, s);
-                        } else {
-                            b[v] = clipf(s, clip);
-                        }
+                        bs[jj][v] = s;
                     }
-                    if (lane_on) gmsg[(size_t)eo[jj] * 32] = Lane<V>::pack(b);
+                if constexpr (XF) {
+                    // the check pass sums phi(|beta|): evaluate it here, from the unrounded beta
+                    // (|clip(s)| = min(|s|, clip)), keep beta's sign; packed pairs as in the check pass
+                    float ph[JMAX][V];
+                    if constexpr (V == 2) {
+#pragma unroll
+                        for (int jj = 0; jj < JMAX; ++jj)
+                            phi_fin2(fminf(fabsf(bs[jj][0]), clip), fminf(fabsf(bs[jj][1]), clip), ph[jj][0],
+                                     ph[jj][1]);
+                    } else {
+#pragma unroll
+                        for (int jj = 0; jj + 1 < JMAX; jj += 2)
+                            phi_fin2(fminf(fabsf(bs[jj][0]), clip), fminf(fabsf(bs[jj + 1][0]), clip), ph[jj][0],
+                                     ph[jj + 1][0]);
+                        if (JMAX % 2) ph[JMAX - 1][0] = phi_fin(fminf(fabsf(bs[JMAX - 1][0]), clip));
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < JMAX; ++jj)
+#pragma unroll
+                        for (int v = 0; v < V; ++v) bs[jj][v] = with_sign_of(ph[jj][v] * XfScale<V>::store, bs[jj][v]);
+                } else {
+#pragma unroll
+                    for (int jj = 0; jj < JMAX; ++jj)
+#pragma unroll
+                        for (int v = 0; v < V; ++v) bs[jj][v] = clipf(bs[jj][v], clip);
+                }
+#pragma unroll
+                for (int jj = 0; jj < JMAX; ++jj) {
+                    if (!REG && eo[jj] < 0) continue;  // warp-uniform
+                    if (lane_on) gmsg[(size_t)eo[jj] * 32] = Lane<V>::pack(bs[jj]);
                 }
                 float pst[V];
 #pragma unroll

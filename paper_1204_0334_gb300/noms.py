@@ -77,20 +77,31 @@ def draw_frames(code: QCCode, batch: int, seed: int, first_frame: int, ebn0_lo: 
 
 
 def train_noms(code: QCCode, T: int = 10, steps: int = 200, batch: int = 1024, ebn0=(2.5, 4.5), lr: float = 0.02,
-               seed: int = 1, msg: int = MSG_F16, ckpt_every: int = 2, clip: float = 30.0, params=None, log=None):
-    """Adam on the NOMS parameters; returns (params, list of losses)."""
+               seed: int = 1, msg: int = MSG_F16, ckpt_every: int = 2, clip: float = 30.0, params=None, log=None,
+               unroll: int = 0, dist=None):
+    """Adam on the NOMS parameters; returns (params, list of losses).
+
+    unroll > T trains the decoder as it runs for `unroll` iterations: iterations beyond T use the
+    last trained row (the parameters are tied, their gradients summed by autograd).
+    dist: a torch.distributed process group of several ranks -- data-parallel training, each rank on
+    its own frames (frame ids offset by rank), gradients averaged over all frames every step."""
+    from .shard import average_gradient
+
     torch = _torch()
     ncirc = _ncirc(code)
     p = (params if params is not None else init_params(T, ncirc)).clone().requires_grad_(True)
     opt = torch.optim.Adam([p], lr=lr)
     losses = []
-    frame = 0
+    rank = dist.get_rank() if dist is not None and dist.is_initialized() else 0
+    frame = rank << 40
     for it in range(steps):
         llr = draw_frames(code, batch, seed, frame, *ebn0)
         frame += batch
         opt.zero_grad()
-        loss = NomsLoss.apply(p, llr, code.handle, msg, ckpt_every, clip)
+        P = extend_params(p, unroll) if unroll > T else p
+        loss = NomsLoss.apply(P, llr, code.handle, msg, ckpt_every, clip)
         loss.backward()
+        p.grad = average_gradient(p.grad, batch, dist)
         opt.step()
         with torch.no_grad():
             p[..., 1].clamp_(min=0.0)

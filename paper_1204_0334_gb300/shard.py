@@ -1,7 +1,14 @@
-"""Multi-GPU Monte-Carlo sharding (host side): frames are independent and the channel is
-counter-based (Philox counter = frame id), so rank r simulates its own disjoint range of
-frame ids and the only exchange is a sum of the integer counters (and a max of the timed
-duration).  No collective touches the data path.
+"""Multi-GPU sharding (host side).
+
+Monte-Carlo simulation: frames are independent and the channel is counter-based (Philox
+counter = frame id), so rank r simulates its own disjoint range of frame ids and the only
+exchange is a sum of the integer counters (and a max of the timed duration).  No
+collective touches the data path.
+
+Data-parallel training of the learned min-sum: each rank draws its own frames and runs the
+forward and backward kernels on them; the loss is a mean over frames, so the gradient over
+all ranks' frames is the frame-weighted mean of the ranks' gradients -- one all-reduce of
+the [T][J*L][2] gradient (with the frame count appended) per step.
 """
 from __future__ import annotations
 
@@ -39,3 +46,17 @@ def max_over_ranks(x: float, dist=None, device=None) -> float:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
     return float(x)
+
+
+def average_gradient(grad, frames: int, dist=None):
+    """Gradient over the frames of every rank, from this rank's gradient of a per-frame mean loss on
+    `frames` frames: sum_r frames_r * grad_r / sum_r frames_r (one all-reduce of grad and the count).
+    Returns a new tensor on grad's device; without a process group of more than one rank, grad itself."""
+    import torch
+
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return grad
+    flat = torch.cat([(grad.detach().to(torch.float64) * frames).reshape(-1),
+                      torch.tensor([float(frames)], dtype=torch.float64, device=grad.device)])
+    dist.all_reduce(flat, op=dist.ReduceOp.SUM)
+    return (flat[:-1] / flat[-1]).reshape(grad.shape).to(grad.dtype)

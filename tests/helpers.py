@@ -12,6 +12,15 @@ import numpy as np
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
+# parity figures of the GPU tests, printed in the pytest summary (conftest.py)
+PARITY_RECORDS: list = []
+
+
+def record_parity(label: str, **figures):
+    """Keep one comparison's figures: frames, elements, frames/elements that needed the
+    conditioning arm of the FP32 tolerance, largest relative deviation."""
+    PARITY_RECORDS.append(dict(label=label, **figures))
+
 
 def read_sections(name: str) -> dict:
     out, cur = {}, None

@@ -1,7 +1,9 @@
 """The N > 1 path on CPU: two gloo ranks shard the Monte-Carlo frames by frame id (disjoint
 ranges, counter-based channel) and merge only their integer counters (sum) and durations
 (max), with the FP64 oracle standing in for the GPU decoder.  The merged counts must equal
-one process decoding the union of the ranges."""
+one process decoding the union of the ranges.  For data-parallel training of the learned
+min-sum, the ranks' gradients on their own frames, averaged by the all-reduce, must equal
+one process's gradient on the union of the frames."""
 import os
 import socket
 
@@ -90,3 +92,59 @@ def test_rank_ranges_are_disjoint_and_bounded():
     assert a + (1 << 17) <= b
     with pytest.raises(ValueError):
         shard.first_frame(0, 1 << 30, 1 << 17)
+
+
+def _noms_setup():
+    shifts = synth.qc_shifts(3, 6, 8, seed=5)
+    H = oracle.qc_parity_check(shifts, 8)
+    rp, col = oracle.csr_rows(H)
+    cb = oracle.circulant_index(rp, col, 8, 6)
+    rng = np.random.default_rng(3)
+    T = 3
+    params = np.stack([rng.uniform(0.6, 1.0, (T, 18)), rng.uniform(0.0, 0.4, (T, 18))], axis=-1)
+    return rp, col, cb, 48, T, params
+
+
+def _noms_frames(first, n):
+    return oracle.channel_awgn(21, first, n, 48, oracle.sigma_from_ebn0(1.0, 0.5))
+
+
+NOMS_FRAMES = (5, 3)  # uneven shards: the average must weight by frame counts
+
+
+def _noms_worker(rank, world, port, q):
+    from paper_1204_0334_gb300 import shard
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        rp, col, cb, N, T, params = _noms_setup()
+        n = NOMS_FRAMES[rank]
+        mu = _noms_frames(rank * 100, n)
+        _, _, g = oracle.noms(rp, col, cb, N, mu, T, params, want_grad=True)
+        avg = shard.average_gradient(torch.from_numpy(g), n, dist)
+        q.put((rank, avg.numpy()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_average_noms_gradient_over_all_frames():
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_noms_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = sorted([q.get(timeout=120) for _ in range(world)], key=lambda x: x[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    rp, col, cb, N, T, params = _noms_setup()
+    union = np.concatenate([_noms_frames(r * 100, NOMS_FRAMES[r]) for r in range(world)])
+    _, _, want = oracle.noms(rp, col, cb, N, union, T, params, want_grad=True)
+    assert np.abs(want).max() > 0
+    for _, g in got:
+        assert np.allclose(g, want, rtol=1e-12, atol=1e-15 * np.abs(want).max())
+    assert np.array_equal(got[0][1], got[1][1])  # every rank steps with the same gradient
