@@ -660,10 +660,12 @@ def sparse_bench(a, pkg, qc, stream) -> dict:
 
 
 def e2e(a, pkg, code, stream, opts) -> dict:
-    """Same metric through ldpc_decode with pinned HOST buffers: LLRs copied in, hard decisions copied out."""
+    """Same metric through ldpc_decode with pinned HOST buffers: 8 x slots frames per call (the LLRs of
+    the call read from host memory, the hard decisions, iteration counts and ok flags written back to
+    host memory, inside the timed region; with early stop the frames stream through the slots)."""
     import torch
 
-    gamma = a.gamma
+    gamma = 8 * a.gamma
     llr_dev = torch.empty((gamma, code.N), dtype=torch.float32, device="cuda")
     pkg.ldpc_channel(code.handle, a.ebn0, a.seed, 3 << 44, llr_dev, stream)
     llr = llr_dev.cpu().pin_memory()
@@ -684,7 +686,8 @@ def e2e(a, pkg, code, stream, opts) -> dict:
     ms = ev0.elapsed_time(ev1)
     return {"value": gamma * k * K_INFO / (ms / 1e3) / 1e6, "unit": "Mbit/s",
             "h2d_bytes_per_step": gamma * code.N * 4, "d2h_bytes_per_step": gamma * code.N + 2 * gamma * 4,
-            "ms_per_step": ms / k, "call": "ldpc_decode(host llr [gamma][N] f32 -> host hard [gamma][N] u8)"}
+            "ms_per_step": ms / k, "frames_per_step": gamma, "mean_iters": float(iters.float().mean()),
+            "call": "ldpc_decode(pinned host llr [gamma][N] f32 -> pinned host hard [gamma][N] u8, iters, ok)"}
 
 
 def main():

@@ -122,8 +122,18 @@ ldpc_status ldpc_code_dims(ldpc_code code, int64_t *N, int64_t *M, int64_t *E, i
  *   iters: [gamma] int32 iterations run per frame, or NULL.
  *   ok:    [gamma] int32, 1 iff the hard decisions satisfy every check, or NULL.
  * gamma >= 1 (any value; internally padded to the package width).
+ * Streaming: for a QC code with opts->early_stop, sum-product with F32 messages
+ * or integer min-sum, post == NULL, gamma at least twice the slot count (the
+ * one ldpc_tune_slots picked for this code and algo/msg, else 4096) and every
+ * buffer in device or pinned host memory, the frames stream through that many
+ * slots as in ldpc_ber_sim: a frame enters a slot as soon as the previous one
+ * stops, reading its LLR row directly (pinned host rows through their device
+ * mapping, no staging copy), and writes its decisions, iteration count and ok
+ * flag when it stops.  Each frame gets exactly the iterations and decisions of
+ * the batch path.  This form returns when the batch is decoded (it synchronizes
+ * the stream).
  * Errors: LDPC_EINVAL (null code/llr, gamma < 1, bad opts), LDPC_EUNSUPPORTED
- * (algo/msg pair not built), LDPC_ENOMEM, LDPC_ECUDA.
+ * (algo/msg pair not built), LDPC_ENOMEM, LDPC_ECUDA, LDPC_ETIMEOUT.
  */
 ldpc_status ldpc_decode(ldpc_code code, const float *llr, int32_t gamma, const ldpc_decode_opts *opts,
                         float *post, uint8_t *hard, int32_t *iters, int32_t *ok, void *stream);
@@ -232,6 +242,9 @@ typedef struct {
     int64_t iters_sum;     /* sum over frames of the iterations run */
     int64_t undetected;    /* frames with ok = 1 but >= 1 wrong bit */
     double seconds;        /* wall time of the call */
+    int64_t bit_errors_sq; /* sum over frames of (the frame's wrong bits)^2: with bit_errors,
+                              the frame-level variance behind a confidence interval of the
+                              BER (the bits of one frame do not fail independently) */
 } ldpc_ber_result;
 
 /*

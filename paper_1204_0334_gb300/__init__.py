@@ -40,7 +40,8 @@ class DecodeOpts(ctypes.Structure):
 
 class BerResult(ctypes.Structure):
     _fields_ = [("frames", ctypes.c_int64), ("frame_errors", ctypes.c_int64), ("bit_errors", ctypes.c_int64),
-                ("iters_sum", ctypes.c_int64), ("undetected", ctypes.c_int64), ("seconds", ctypes.c_double)]
+                ("iters_sum", ctypes.c_int64), ("undetected", ctypes.c_int64), ("seconds", ctypes.c_double),
+                ("bit_errors_sq", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -322,6 +322,34 @@ ldpc_status ldpc_code_dims(ldpc_code c, int64_t *N, int64_t *M, int64_t *E, int6
     return LDPC_OK;
 }
 
+// the address a kernel uses for p: p itself for device or managed memory, the device mapping of
+// pinned (page-locked) host memory, NULL for pageable host memory (or NULL)
+static void *mapped_ptr(const void *p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return const_cast<void *>(p);
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) return a.devicePointer;
+    return nullptr;
+}
+
+// Slot count of the streaming decode, or 0 when ldpc_decode keeps its batch path: the stream
+// gives every frame exactly the batch path's iterations and decisions (QC codes, sum-product
+// with FP32 messages or integer min-sum, early stop -- without it a stream has nothing to
+// refill), does not produce posteriors, and pays off once the batch is at least twice the slots.
+static int stream_slots(const ldpc_code c, int gamma, const ldpc_decode_opts &o, const float *post) {
+    if (c->sparse || !o.early_stop || post) return 0;
+    if (!((o.algo == LDPC_ALGO_SP && o.msg == LDPC_MSG_F32) || o.algo == LDPC_ALGO_MS)) return 0;
+    const int W = 32 * lanes_per_word(o.msg);
+    int slots = c->tuned_slots[o.algo][o.msg];
+    if (slots <= 0) slots = 4096;
+    slots = (slots + W - 1) / W * W;
+    return gamma >= 2 * slots ? slots : 0;
+}
+
 ldpc_status ldpc_decode(ldpc_code c, const float *llr, int32_t gamma, const ldpc_decode_opts *opts, float *post,
                         uint8_t *hard, int32_t *iters, int32_t *ok, void *stream) {
     if (!c || !llr || gamma < 1) {
@@ -332,6 +360,18 @@ ldpc_status ldpc_decode(ldpc_code c, const float *llr, int32_t gamma, const ldpc
     if (st != LDPC_OK) return st;
     const ldpc_decode_opts &o = *opts;
     cudaStream_t s = (cudaStream_t)stream;
+    if (const int slots = stream_slots(c, gamma, o, post)) {
+        StreamIO io;
+        io.llr = (const float *)mapped_ptr(llr);
+        io.hard = (uint8_t *)mapped_ptr(hard);
+        io.iters = (int32_t *)mapped_ptr(iters);
+        io.ok = (int32_t *)mapped_ptr(ok);
+        // every buffer device-accessible (device memory or pinned host memory): stream
+        if (io.llr && (!hard || io.hard) && (!iters || io.iters) && (!ok || io.ok)) {
+            unsigned long long h[8];
+            return qc_ber_sim_refill(c, 0.0, 0, 0, gamma, 0, slots, o, h, s, &io);
+        }
+    }
     const bool host_in = pointer_kind(llr) == 1;
     const bool host_out = (post && pointer_kind(post) == 1) || (hard && pointer_kind(hard) == 1) ||
                           (iters && pointer_kind(iters) == 1) || (ok && pointer_kind(ok) == 1);
@@ -476,6 +516,7 @@ ldpc_status ldpc_ber_sim(ldpc_code c, double ebn0_db, uint64_t seed, uint64_t fi
     out->bit_errors = (int64_t)h[2];
     out->iters_sum = (int64_t)h[3];
     out->undetected = (int64_t)h[4];
+    out->bit_errors_sq = (int64_t)h[5];
     out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return LDPC_OK;
 }

@@ -158,9 +158,16 @@ ldpc_status qc_init_flags(ldpc_code c, int gamma, int V, cudaStream_t s);
 ldpc_status qc_finish_frames(ldpc_code c, int gamma, const ldpc_decode_opts &o, cudaStream_t s);
 // continuous simulation (sim.cu)
 void sim_free(ldpc_sim_state *st);
+// streaming decode (ldpc_decode): the caller's [gamma][N] channel LLRs (device-accessible) and
+// the outputs each frame writes as it retires (NULL = not wanted)
+struct StreamIO {
+    const float *llr;
+    uint8_t *hard;
+    int32_t *iters, *ok;
+};
 ldpc_status qc_ber_sim_refill(ldpc_code c, double sigma, uint64_t seed, uint64_t first_frame, int64_t max_frames,
                               int64_t target, int gamma, const ldpc_decode_opts &o, unsigned long long *h,
-                              cudaStream_t s);
+                              cudaStream_t s, const StreamIO *io = nullptr);
 
 // systematic encoder (encode.cu)
 void enc_free(ldpc_encoder_s *e);

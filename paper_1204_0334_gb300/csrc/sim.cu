@@ -43,6 +43,7 @@ struct ldpc_sim_state {
     size_t slots = 0;
     uint32_t *sflags = nullptr;           // [P][2V]: retire[V], refill[V]
     uint64_t *fid = nullptr;              // [slots] frame id of the slot's frame
+    uint64_t *rfid = nullptr;             // [slots] frame id of the frame that retired from the slot this step
     int *errs = nullptr;                  // [slots] wrong bits of the frame retired last step
     int *age = nullptr;                   // [slots] iterations completed by the slot's frame
     int *pend = nullptr;                  // [slots] 2 * iterations + ok of the frame retired last step, or -1
@@ -64,6 +65,7 @@ void sim_free(ldpc_sim_state *st) {
     if (!st) return;
     cudaFree(st->sflags);
     cudaFree(st->fid);
+    cudaFree(st->rfid);
     cudaFree(st->errs);
     cudaFree(st->age);
     cudaFree(st->pend);
@@ -90,6 +92,7 @@ ldpc_status sim_ensure(ldpc_code c, size_t slots) {
     st = new ldpc_sim_state();
     const size_t words = slots / 32 * 2;  // 2 words per 32 slots, any V
     if (cudaMalloc(&st->sflags, words * 4) != cudaSuccess || cudaMalloc(&st->fid, slots * 8) != cudaSuccess ||
+        cudaMalloc(&st->rfid, slots * 8) != cudaSuccess ||
         cudaMalloc(&st->errs, slots * 4) != cudaSuccess || cudaMalloc(&st->age, slots * 4) != cudaSuccess ||
         cudaMalloc(&st->pend, slots * 4) != cudaSuccess || cudaMalloc(&st->next, 8) != cudaSuccess ||
         cudaMalloc(&st->rlist, slots * 4) != cudaSuccess || cudaMalloc(&st->rcount, 2 * 4) != cudaSuccess ||
@@ -135,7 +138,7 @@ __global__ void sim_init_kernel(uint32_t *flags, int *errs, int *age, int *pend,
 struct SimArgs {
     const uint32_t *hw;
     uint32_t *flags, *sflags;
-    uint64_t *fid;
+    uint64_t *fid, *rfid;
     int *errs, *age, *pend;
     unsigned long long *next, *counters;
     int *rlist, *rcount, *act;
@@ -155,13 +158,14 @@ __device__ void retire_word(const SimArgs &sa, int pk, int v, int lane) {
 
     // frames retired by the previous step: their wrong bits were counted by its variable pass
     const int pr = sa.pend[slot];
-    unsigned long long fr = 0, fe = 0, be = 0, is = 0, ud = 0;
+    unsigned long long fr = 0, fe = 0, be = 0, is = 0, ud = 0, b2 = 0;
     if (pr >= 0) {
         const int e = sa.errs[slot];
         sa.errs[slot] = 0;
         sa.pend[slot] = -1;
         fr = 1;
         be = (unsigned long long)e;
+        b2 = be * be;
         fe = e > 0;
         is = (unsigned long long)(pr >> 1);
         ud = (e > 0 && (pr & 1)) ? 1 : 0;
@@ -174,6 +178,7 @@ __device__ void retire_word(const SimArgs &sa, int pk, int v, int lane) {
             be += __shfl_xor_sync(0xffffffffu, be, o);
             is += __shfl_xor_sync(0xffffffffu, is, o);
             ud += __shfl_xor_sync(0xffffffffu, ud, o);
+            b2 += __shfl_xor_sync(0xffffffffu, b2, o);
         }
         if (lane == 0) {
             atomicAdd(sa.counters + 0, fr);
@@ -181,6 +186,7 @@ __device__ void retire_word(const SimArgs &sa, int pk, int v, int lane) {
             if (be) atomicAdd(sa.counters + 2, be);
             atomicAdd(sa.counters + 3, is);
             if (ud) atomicAdd(sa.counters + 4, ud);
+            if (b2) atomicAdd(sa.counters + 5, b2);
         }
     }
 
@@ -189,7 +195,10 @@ __device__ void retire_word(const SimArgs &sa, int pk, int v, int lane) {
     int a = sa.age[slot];
     const bool sat = !((U >> lane) & 1u);
     const bool ret = running && ((sa.early_stop && a >= 1 && sat) || a >= sa.max_iter);
-    if (ret) sa.pend[slot] = 2 * a + (sat ? 1 : 0);
+    if (ret) {
+        sa.pend[slot] = 2 * a + (sat ? 1 : 0);
+        sa.rfid[slot] = sa.fid[slot];
+    }
 
     // refill: no new frame once the frame-error target is met (read from earlier totals)
     const bool stop = *(volatile unsigned long long *)(sa.counters + 1) >= sa.target;
@@ -346,11 +355,82 @@ __global__ void sim_channel_kernel(void *__restrict__ mu, const int *__restrict_
     }
 }
 
-// Runs the continuous simulation; h receives counters[0..4] (frames, frame
-// errors, bit errors, iterations, undetected).
+// Streaming decode of a caller's batch (ldpc_decode): the frames that entered a slot
+// this step copy their channel LLRs from row fid of the caller's [gamma][N] buffer
+// (device memory, or pinned host memory read through its device mapping) into the
+// slots' frame-major store: clipped for sum-product, quantized for min-sum exactly as
+// the batch path's packing does.
+template <bool I8>
+__global__ void stream_load_kernel(const float *__restrict__ llr, void *__restrict__ mu,
+                                   const int *__restrict__ rlist, const int *__restrict__ rcount,
+                                   const uint64_t *__restrict__ fid, int N, int parity, float clip, float qscale) {
+    const int cnt = rcount[parity];
+    if (cnt == 0) return;
+    const int Q = (N + 3) / 4;
+    const size_t N4 = (size_t)Q * 4;
+    const long long total = (long long)cnt * Q;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / Q);
+        const int q = (int)(i - (long long)r * Q);
+        const int slot = rlist[r];
+        const float *row = llr + (size_t)fid[slot] * N;
+        float x[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) x[e] = 4 * q + e < N ? row[4 * q + e] : 0.0f;
+        if (I8) {
+            uint32_t w = 0u;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float v = fminf(fmaxf(rintf(x[e] * qscale), -127.0f), 127.0f);
+                w |= (uint32_t)(uint8_t)(int8_t)v << (8 * e);
+            }
+            reinterpret_cast<uint32_t *>(mu)[((size_t)slot * N4 + 4 * q) / 4] = w;
+        } else {
+            reinterpret_cast<float4 *>(mu)[((size_t)slot * N4 + 4 * q) / 4] =
+                make_float4(clipf(x[0], clip), clipf(x[1], clip), clipf(x[2], clip), clipf(x[3], clip));
+        }
+    }
+}
+
+// Streaming decode: the outputs of the frames that retired this step, written before the
+// step's passes overwrite their slots -- hard decisions (row fid of the caller's
+// [gamma][N] bytes, from the slots' packed decision words), iteration count and ok flag.
+// Block (package, word v); threads over the variables.
+__global__ void __launch_bounds__(256)
+stream_out_kernel(const uint32_t *__restrict__ hw, const uint32_t *__restrict__ sflags, const uint64_t *__restrict__ rfid,
+                  const int *__restrict__ pend, uint8_t *__restrict__ hard, int32_t *__restrict__ iters,
+                  int32_t *__restrict__ ok, int N, int V) {
+    const int pk = blockIdx.x, v = blockIdx.y;
+    const uint32_t R = sflags[(size_t)pk * 2 * V + v];  // retire word
+    if (R == 0u) return;
+    if (threadIdx.x < 32 && ((R >> threadIdx.x) & 1u)) {
+        const size_t slot = (size_t)pk * 32 * V + threadIdx.x * V + v;
+        const uint64_t f = rfid[slot];
+        const int pr = pend[slot];
+        if (iters) iters[f] = pr >> 1;
+        if (ok) ok[f] = pr & 1;
+    }
+    if (!hard) return;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        const uint32_t w = hw[((size_t)pk * N + n) * V + v];
+        for (uint32_t b = R; b; b &= b - 1) {
+            const int ln = __ffs(b) - 1;
+            const uint64_t f = rfid[(size_t)pk * 32 * V + ln * V + v];
+            hard[f * (uint64_t)N + n] = (uint8_t)((w >> ln) & 1u);
+        }
+    }
+}
+
+// Runs the continuous simulation; h receives counters[0..5] (frames, frame
+// errors, bit errors, iterations, undetected, sum over frames of the squared
+// bit-error count).
+// With io (streaming decode of a caller's batch): frames 0 .. max_frames - 1 are the rows of
+// io->llr, each frame's outputs go to io->hard / iters / ok as it retires, and no errors are
+// counted (sigma, seed, first_frame and target are unused).
 ldpc_status qc_ber_sim_refill(ldpc_code c, double sigma, uint64_t seed, uint64_t first_frame, int64_t max_frames,
                               int64_t target, int gamma, const ldpc_decode_opts &o, unsigned long long *h,
-                              cudaStream_t s) {
+                              cudaStream_t s, const StreamIO *io) {
     const int V = lanes_per_word(o.msg), W = 32 * V;
     const int P = (gamma + W - 1) / W;
     const size_t slots = (size_t)P * W;
@@ -366,7 +446,11 @@ ldpc_status qc_ber_sim_refill(ldpc_code c, double sigma, uint64_t seed, uint64_t
         count_launch();
     }
     // random codewords: the encoder and each slot's codeword row
-    const bool cw = o.codewords == LDPC_CODEWORDS_RANDOM;
+    const bool cw = !io && o.codewords == LDPC_CODEWORDS_RANDOM;
+    if (io) {
+        first_frame = 0;
+        target = (int64_t)1 << 62;
+    }
     const int NW = enc_words(c);
     if (cw) {
         st = enc_ensure_device(c, slots / 32);
@@ -387,7 +471,7 @@ ldpc_status qc_ber_sim_refill(ldpc_code c, double sigma, uint64_t seed, uint64_t
     }
     RefillArgs rf;
     rf.sflags = S->sflags;
-    rf.errs = cw ? nullptr : S->errs;  // with codewords the errors are counted against them
+    rf.errs = (cw || io) ? nullptr : S->errs;  // with codewords the errors are counted against them
     rf.mu = S->mu;
     const float fsig = (float)sigma, s2 = (float)(2.0 / (sigma * sigma));
     const bool i8 = o.algo == LDPC_ALGO_MS;
@@ -404,6 +488,7 @@ ldpc_status qc_ber_sim_refill(ldpc_code c, double sigma, uint64_t seed, uint64_t
     sa.flags = c->ws.flags;
     sa.sflags = S->sflags;
     sa.fid = S->fid;
+    sa.rfid = S->rfid;
     sa.errs = S->errs;
     sa.age = S->age;
     sa.pend = S->pend;
@@ -427,6 +512,29 @@ ldpc_status qc_ber_sim_refill(ldpc_code c, double sigma, uint64_t seed, uint64_t
         else if (V == 2) sim_check_kernel<2><<<cgrd, 256, 0, s>>>(c->d, sa);
         else sim_check_kernel<4><<<cgrd, 256, 0, s>>>(c->d, sa);
         ldpc_status e = LDPC_OK;
+        if (io) {
+            // the retiring frames' outputs, then the new frames' channel LLRs from the caller's rows
+            stream_out_kernel<<<dim3(P, V), 256, 0, s>>>(c->ws.hw, S->sflags, S->rfid, S->pend, io->hard, io->iters,
+                                                         io->ok, c->d.N, V);
+            if (i8)
+                stream_load_kernel<true><<<cblocks, 256, 0, s>>>(io->llr, S->mu, S->rlist, S->rcount, S->fid, c->d.N,
+                                                                 parity, 1e30f, ldexpf(1.0f, o.frac_bits));
+            else
+                stream_load_kernel<false><<<cblocks, 256, 0, s>>>(io->llr, S->mu, S->rlist, S->rcount, S->fid, c->d.N,
+                                                                  parity, o.clip, 1.0f);
+            count_launch(2);
+            parity ^= 1;
+            const int slot_cn = prof_begin(0, s);
+            e = qc_cn_pipe(c, o, 1, s, S->sflags, o.algo == LDPC_ALGO_NOMS ? S->age : nullptr);
+            if (e != LDPC_OK) return e;
+            prof_end(slot_cn, s);
+            const int slot_vn = prof_begin(1, s);
+            e = qc_vn_refill(c, o, rf, s);
+            if (e != LDPC_OK) return e;
+            prof_end(slot_vn, s);
+            count_launch(3);
+            return LDPC_OK;
+        }
         if (cw) {
             // wrong information bits of the frames retiring now, then the new frames' codewords
             e = enc_sim_errors(c, P, V, S->sflags, S->cwf, S->errs, s);

@@ -140,6 +140,23 @@ def clopper_pearson(k: int, n: int, conf: float = 0.95):
     return lo, hi
 
 
+def ber_interval(r: dict, N: int, conf: float = 0.95):
+    """Confidence interval of the BER from ldpc_ber_sim's counts.  Frames are independent, the bits
+    of one frame are not (a failed frame carries many wrong bits), so the interval is the normal
+    one of the mean of the per-frame error counts e_f (variance from sum e_f and sum e_f^2), divided
+    by N.  With no frame error the BER is 0 and bounded by the FER's Clopper-Pearson upper limit
+    (BER <= FER, since a frame has at most N wrong bits)."""
+    from scipy.stats import norm
+
+    n = int(r["frames"])
+    if r["frame_errors"] == 0 or n < 2:
+        return 0.0, clopper_pearson(int(r["frame_errors"]), n, conf)[1]
+    m = r["bit_errors"] / n
+    var = max(0.0, (r["bit_errors_sq"] - n * m * m) / (n - 1))
+    h = float(norm.ppf(0.5 + conf / 2)) * math.sqrt(var / n)
+    return max(0.0, (m - h) / N), (m + h) / N
+
+
 def _timed_ber(code, opts, ebn0, frames, gamma, target_fe, seed=4242):
     torch = _torch()
     torch.cuda.synchronize()
@@ -147,8 +164,9 @@ def _timed_ber(code, opts, ebn0, frames, gamma, target_fe, seed=4242):
     r["mbit_s"] = r["frames"] * code.K / r["seconds"] / 1e6
     nb = r["frames"] * code.N
     r["ber"] = r["bit_errors"] / nb
-    r["ber_ci95"] = clopper_pearson(r["bit_errors"], nb)
+    r["ber_ci95"] = ber_interval(r, code.N)
     r["fer"] = r["frame_errors"] / r["frames"]
+    r["fer_ci95"] = clopper_pearson(r["frame_errors"], r["frames"])
     return r
 
 

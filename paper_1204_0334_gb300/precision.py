@@ -1,6 +1,7 @@
 """BER/FER of the message precisions on one code: sum-product with FP32 and FP16 messages
 and integer min-sum, each through ldpc_ber_sim (device channel, continuous simulation) on
-the same frames, with exact 95% confidence intervals.
+the same frames, with 95% confidence intervals (exact for the FER; for the BER from the
+frame-level variance of the error counts, since the bits of a frame do not fail independently).
 
     python -m paper_1204_0334_gb300.precision --ebn0 3.0 3.25 --target-errors 200
 """
@@ -12,7 +13,7 @@ import os
 import sys
 
 from . import ALGO_MS, ALGO_SP, MSG_F16, MSG_F32, MSG_I8, QCCode, default_opts, ldpc_ber_sim
-from .noms import clopper_pearson
+from .noms import ber_interval, clopper_pearson
 
 CASES = [("sp_f32", dict(algo=ALGO_SP, msg=MSG_F32)), ("sp_f16", dict(algo=ALGO_SP, msg=MSG_F16)),
          ("minsum_i8", dict(algo=ALGO_MS, msg=MSG_I8))]
@@ -27,7 +28,7 @@ def run(code: QCCode, ebn0_points, max_frames: int, target_errors: int, iters: i
             r = ldpc_ber_sim(code.handle, e, seed, 0, max_frames, target_errors, gamma, o)
             nb = r["frames"] * code.N
             r["ber"] = r["bit_errors"] / nb
-            r["ber_ci95"] = clopper_pearson(r["bit_errors"], nb)
+            r["ber_ci95"] = ber_interval(r, code.N)
             r["fer"] = r["frame_errors"] / r["frames"]
             r["fer_ci95"] = clopper_pearson(r["frame_errors"], r["frames"])
             r["mean_iters"] = r["iters_sum"] / r["frames"]

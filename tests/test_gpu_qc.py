@@ -332,6 +332,36 @@ def test_ber_sim_refill_equals_batch_decode(pkg, algo, msg, exact):
         assert abs(res["iters_sum"] - want["iters_sum"]) <= 0.02 * want["iters_sum"]
 
 
+@pytest.mark.parametrize("algo", ["sp", "ms"])
+def test_streaming_decode_equals_batch_path(pkg, algo):
+    """ldpc_decode of more frames than twice its slot count streams the frames through the slots (early
+    stop, no posteriors): every frame's decisions, iteration count and ok flag equal the batch path's
+    (forced by asking for posteriors), with device buffers and with pinned host buffers read and
+    written through their device mapping."""
+    A = {"sp": pkg.ALGO_SP, "ms": pkg.ALGO_MS}[algo]
+    M = {"sp": pkg.MSG_F32, "ms": pkg.MSG_I8}[algo]
+    shifts = synth.qc_shifts(3, 6, 64, seed=1)
+    code = pkg.QCCode(shifts, 64)
+    o = pkg.default_opts(max_iter=25, early_stop=1, algo=A, msg=M)
+    g = 2 * max(pkg.TUNE_SLOTS) + 37  # above twice any slot count the library may use
+    llr = code.channel(1.75, 9, 5, g)
+    ref = code.decode(llr, max_iter=25, early_stop=True, algo=A, msg=M, want_post=True)
+    got = code.decode(llr, max_iter=25, early_stop=True, algo=A, msg=M, want_post=False)
+    for a, b, name in zip(ref[1:], got[1:], ("hard", "iters", "ok")):
+        assert torch.equal(a, b), name
+    it = ref[2].cpu().numpy()
+    assert it.min() >= 1 and it.max() == 25 and len(set(it.tolist())) > 5  # frames stop at many iterations
+    # pinned host buffers
+    hl = llr.cpu().pin_memory()
+    hh = torch.empty((g, code.N), dtype=torch.uint8).pin_memory()
+    hi = torch.empty(g, dtype=torch.int32).pin_memory()
+    hk = torch.empty(g, dtype=torch.int32).pin_memory()
+    pkg.ldpc_decode(code.handle, hl, o, None, hh, hi, hk)
+    torch.cuda.synchronize()
+    assert torch.equal(hh, ref[1].cpu()) and torch.equal(hi, ref[2].cpu()) and torch.equal(hk, ref[3].cpu())
+    code.close()
+
+
 def _batch_counts(pkg, code, ebn0, seed, first, frames, **kw):
     llr = code.channel(ebn0, seed, first, frames)
     _, hard, iters, ok = code.decode(llr, want_post=False, **kw)
