@@ -179,23 +179,41 @@ def extend_params(params, iters: int):
     return torch.cat([params, params[-1:].expand(iters - T, -1, -1)], dim=0).contiguous()
 
 
-def evaluate(code, params, ebn0_points, frames=1 << 20, gamma=8192, target_fe=100, sp_iters=30, long_iters=30):
-    """BER, 95% CI and Mbit/s at each Eb/N0 of: sum-product (sp_iters, FP32), the trained NOMS over its
-    T trained iterations and over long_iters (last trained row reused), and untrained min-sum (w=1, o=0)."""
+def _overlap(a, b) -> bool:
+    return a[0] <= b[1] and b[0] <= a[1]
+
+
+def evaluate(code, params, ebn0_points, frames=1 << 20, gamma=8192, target_fe=100, sp_iters=30, long_iters=50,
+             frame_caps=None):
+    """At each Eb/N0: sum-product (sp_iters iterations, FP32 messages) and the trained NOMS run for
+    long_iters iterations (FP16 messages; iterations past the trained rows reuse the last row), both
+    with early stop on the same frames, each until target_fe frame errors or its frame cap
+    (frame_caps[e] if given, else `frames`); plus untrained min-sum (w = 1, o = 0) as the method
+    without the learned parameters.  Every arm reports BER and FER with 95% intervals (exact for the
+    FER, frame-clustered for the BER) and decoded Mbit/s; `match` records whether NOMS's intervals
+    overlap sum-product's, and `faster` whether NOMS decodes more Mbit/s."""
     T = params.shape[0]
     ncirc = params.shape[1]
-    plain = init_params(T, ncirc)
-    cases = [("noms_trained", params, T), ("noms_trained", extend_params(params, long_iters), long_iters),
-             ("minsum_untrained", plain, T)]
     out = {}
     for e in ebn0_points:
+        cap = (frame_caps or {}).get(e, frames)
         row = {}
         o = default_opts(max_iter=sp_iters, early_stop=1, msg=MSG_F32)
-        row[f"sp{sp_iters}_f32"] = _timed_ber(code, o, e, frames, gamma, target_fe)
-        for name, prm, it in cases:
-            o = default_opts(max_iter=it, early_stop=1, algo=ALGO_NOMS, msg=MSG_F16)
-            o.noms_params = prm.contiguous().data_ptr()
-            row[f"{name}_{it}it_f16"] = _timed_ber(code, o, e, frames, gamma, target_fe)
+        sp = _timed_ber(code, o, e, cap, gamma, target_fe)
+        row[f"sp{sp_iters}_f32"] = sp
+        o = default_opts(max_iter=long_iters, early_stop=1, algo=ALGO_NOMS, msg=MSG_F16)
+        prm = extend_params(params, long_iters)
+        o.noms_params = prm.data_ptr()
+        nm = _timed_ber(code, o, e, cap, gamma, target_fe)
+        row[f"noms_trained_{long_iters}it_f16"] = nm
+        o = default_opts(max_iter=long_iters, early_stop=1, algo=ALGO_NOMS, msg=MSG_F16)
+        plain = init_params(long_iters, ncirc)
+        o.noms_params = plain.data_ptr()
+        row[f"minsum_untrained_{long_iters}it_f16"] = _timed_ber(code, o, e, min(cap, 1 << 18), gamma, target_fe)
+        row["match"] = {"fer_intervals_overlap": _overlap(sp["fer_ci95"], nm["fer_ci95"]),
+                        "ber_intervals_overlap": _overlap(sp["ber_ci95"], nm["ber_ci95"]),
+                        "both_reached_target": sp["frame_errors"] >= target_fe and nm["frame_errors"] >= target_fe,
+                        "faster": nm["mbit_s"] > sp["mbit_s"]}
         out[str(e)] = row
     return out
 
@@ -214,12 +232,17 @@ def main(argv=None):
     ap.add_argument("--L", type=int, default=24)
     ap.add_argument("--p", type=int, default=765)
     ap.add_argument("--shift-seed", type=int, default=2)
-    ap.add_argument("--T", type=int, default=10)
-    ap.add_argument("--steps", type=int, default=256)
-    ap.add_argument("--batch", type=int, default=4096)
-    ap.add_argument("--lr", type=float, default=0.02)
-    ap.add_argument("--ebn0", type=float, nargs="*", default=[3.0, 3.25, 3.5])
-    ap.add_argument("--eval-frames", type=int, default=1 << 20)
+    ap.add_argument("--T", type=int, default=10, help="trained parameter rows (iterations)")
+    ap.add_argument("--unroll", type=int, default=20, help="iterations unrolled in training (rows past T tied)")
+    ap.add_argument("--steps", type=int, default=768)
+    ap.add_argument("--batch", type=int, default=2048)
+    ap.add_argument("--lr", type=float, default=0.01)
+    ap.add_argument("--train-ebn0", type=float, nargs=2, default=[2.9, 3.6])
+    ap.add_argument("--ebn0", type=float, nargs="*", default=[3.0, 3.25, 3.375, 3.5])
+    ap.add_argument("--eval-frames", type=int, default=1 << 24, help="frame cap per arm")
+    ap.add_argument("--frames-3p5", type=int, default=1 << 27, help="frame cap per arm at 3.5 dB")
+    ap.add_argument("--long-iters", type=int, default=50, help="iterations of the trained decoder")
+    ap.add_argument("--target-errors", type=int, default=100)
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     import sys
@@ -232,17 +255,20 @@ def main(argv=None):
 
     code = QCCode(synth.qc_shifts(a.J, a.L, a.p, seed=a.shift_seed), a.p)
     t0 = time.time()
-    params, losses = train_noms(code, T=a.T, steps=a.steps, batch=a.batch, lr=a.lr, log=print)
+    params, losses = train_noms(code, T=a.T, steps=a.steps, batch=a.batch, lr=a.lr, ebn0=tuple(a.train_ebn0),
+                                unroll=a.unroll, log=print)
     torch.cuda.synchronize()
     train_s = time.time() - t0
-    res = {"code": f"QC {a.J}x{a.L} p={a.p} n={code.N}", "T": a.T,
-           "training": {"frames": a.steps * a.batch, "seconds": train_s, "loss_first": losses[0],
-                        "loss_last": float(np.mean(losses[-10:]))},
-           "eval": evaluate(code, params, a.ebn0, frames=a.eval_frames),
+    res = {"code": f"QC {a.J}x{a.L} p={a.p} n={code.N}", "T": a.T, "unroll": a.unroll,
+           "training": {"frames": a.steps * a.batch, "ebn0": a.train_ebn0, "seconds": train_s,
+                        "loss_first": losses[0], "loss_last": float(np.mean(losses[-10:]))},
+           "eval": evaluate(code, params, a.ebn0, frames=a.eval_frames, target_fe=a.target_errors,
+                            long_iters=a.long_iters, frame_caps={3.5: a.frames_3p5}),
            "params_w_mean_per_iter": params[..., 0].mean(dim=1).tolist(),
            "params_o_mean_per_iter": params[..., 1].mean(dim=1).tolist()}
     print(json.dumps(res, indent=1))
     if a.out:
+        torch.save(params.cpu(), os.path.splitext(a.out)[0] + "_params.pt")
         with open(a.out, "w") as fh:
             json.dump(res, fh, indent=1)
 
