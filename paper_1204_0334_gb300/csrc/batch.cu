@@ -30,6 +30,7 @@ namespace ldpc {
 
 struct BCode {
     int J, L, p, N, M, E, P, gamma, tab;
+    FastDiv dp;                           // n / p by multiply-high
     long long msg, mu, hw, flags, iters;  // offsets (words / ints) into the shared regions
 };
 
@@ -55,26 +56,25 @@ __device__ __forceinline__ void b_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-template <int V, bool SYN, bool FIRST, bool MS>
+template <int V, bool FIRST, bool MS>
 struct BCnStage {
     static constexpr int MUW = MS ? 32 : 32 * V;     // words of one channel-LLR package
     static constexpr int SEGW = FIRST ? MUW : 32;    // words per edge in the stage
     static constexpr int SEG = kBDC * SEGW;
-    static constexpr int HW = SEG;
-    static constexpr int FL = HW + (SYN ? kBDC * V : 0);
+    static constexpr int FL = SEG;
     static constexpr int WORDS = (FL + V + 3) & ~3;
 };
 
 // ---------------------------------------------------------------------------
 // check pass over all codes (FIRST: beta = mu)
 // ---------------------------------------------------------------------------
-template <int V, bool SYN, bool XF, bool MS, bool FIRST>
+template <int V, bool XF, bool MS, bool FIRST>
 __global__ void __launch_bounds__(kWarps * 32, 2)  // two blocks of eight warps per SM
 bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const int *__restrict__ eotab,
-           uint32_t *__restrict__ msg, const uint32_t *__restrict__ mu, const uint32_t *__restrict__ hw,
-           uint32_t *__restrict__ flags, const int *__restrict__ tcount, const BTile *__restrict__ tiles, int TR,
-           float clip, int par) {
-    using St = BCnStage<V, SYN, FIRST, MS>;
+           uint32_t *__restrict__ msg, const uint32_t *__restrict__ mu, const uint32_t *__restrict__ flags,
+           const int *__restrict__ tcount, const BTile *__restrict__ tiles, int TR, float clip) {
+    using St = BCnStage<V, FIRST, MS>;
+    const int sTR = __ffs(TR) - 1;  // TR is a power of two
     extern __shared__ __align__(16) uint32_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *ring = smem + warp * kBStages * St::WORDS;
@@ -87,12 +87,12 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
     auto issue = [&](int it, int slot) -> int {
         int mine = -1;
         if (it < total) {
-            const BTile tl = tiles[it / TR];
-            const int ri = it - (it / TR) * TR;
+            const BTile tl = tiles[it >> sTR];
+            const int ri = it & (TR - 1);
             if (ri < tl.count) {
                 const BCode C = codes[tl.code];
                 const int m = tl.start + ri;
-                const int j = m / C.p, r = m - j * C.p;
+                const int j = (int)fdiv((uint32_t)m, C.dp), r = m - j * C.p;
                 uint32_t *dst = ring + slot * St::WORDS;
                 const uint32_t *gsrc = FIRST ? mu + C.mu + (size_t)tl.pk * C.N * St::MUW
                                              : msg + C.msg + (size_t)tl.pk * C.E * 32;
@@ -124,17 +124,6 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                         mine = __ldg(eotab + C.tab + j * C.L + lane) + k;
                     }
                 }
-                if (SYN) {
-                    for (int w = lane; w < kBDC * V; w += 32) {
-                        const int l = w / V, v = w - l * V;
-                        const int sh = l < C.L ? __ldg(shtab + C.tab + j * C.L + l) : -1;
-                        if (sh >= 0) {
-                            int k = r + sh;
-                            if (k >= C.p) k -= C.p;
-                            b_cp4(dst + St::HW + w, hw + C.hw + ((size_t)tl.pk * C.N + (size_t)l * C.p + k) * V + v);
-                        }
-                    }
-                }
                 if (lane < V) b_cp4(dst + St::FL + lane, flags + C.flags + (size_t)tl.pk * 5 * V + lane);
             }
         }
@@ -153,20 +142,15 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
         const int myoff = offr[0];
 #pragma unroll
         for (int s = 0; s < kBStages - 1; ++s) offr[s] = offr[s + 1];
-        const BTile tl = tiles[item / TR];
-        const int ri = item - (item / TR) * TR;
+        const BTile tl = tiles[item >> sTR];
+        const int ri = item & (TR - 1);
         if (ri < tl.count) {
             const BCode C = codes[tl.code];
             const uint32_t *S = ring + slot * St::WORDS;
             uint32_t *gmsg = msg + C.msg + (size_t)tl.pk * C.E * 32 + lane;
-            uint32_t actv[V], syn[V];
             bool lane_on = false;
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                actv[v] = ~S[St::FL + v];
-                lane_on |= (actv[v] >> lane) & 1u;
-                syn[v] = 0u;
-            }
+            for (int v = 0; v < V; ++v) lane_on |= ((~S[St::FL + v]) >> lane) & 1u;
             if constexpr (!MS) {
                 float ph[kBDC][V];
                 uint32_t neg[V];
@@ -191,7 +175,6 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                             // the sign bit: a transformed FP16 message of a strongly negative beta
                             // may round to -0
                             neg[v] |= (__float_as_uint(x[v]) >> 31) << l;
-                            if (SYN) syn[v] ^= S[St::HW + l * V + v];
                         }
                     }
                 }
@@ -212,20 +195,34 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                 float suf[V];
 #pragma unroll
                 for (int v = 0; v < V; ++v) par_all[v] = __popc(neg[v]) & 1u, suf[v] = 0.0f;
+                // phi on packed pairs: two edges (V = 1) or the two frames of a lane word (V = 2)
+                static_assert(V <= 2 && kBDC % 2 == 0, "pairs of edges or frames");
 #pragma unroll
-                for (int l = kBDC - 1; l >= 0; --l) {
-                    const int o = __shfl_sync(0xffffffffu, myoff, l);
-                    if (o >= 0) {
-                        float out[V];
+                for (int l = kBDC - 1; l >= 0; l -= (V == 1 ? 2 : 1)) {
+                    float arg[2][V], mag[2][V];
+#pragma unroll
+                    for (int h = 0; h < (V == 1 ? 2 : 1); ++h)
 #pragma unroll
                         for (int v = 0; v < V; ++v) {
-                            const float mag = fminf(phi_f(pre[l][v] + suf[v]), clip);
-                            out[v] = (par_all[v] ^ ((neg[v] >> l) & 1u)) ? -mag : mag;
+                            arg[h][v] = pre[l - h][v] + suf[v];
+                            suf[v] += ph[l - h][v];
                         }
-                        if (lane_on) gmsg[(size_t)o * 32] = Lane<V>::pack(out);
-                    }
+                    if constexpr (V == 1) phi2(arg[0][0], arg[1][0], mag[0][0], mag[1][0]);
+                    else phi2(arg[0][0], arg[0][1], mag[0][0], mag[0][1]);
 #pragma unroll
-                    for (int v = 0; v < V; ++v) suf[v] += ph[l][v];
+                    for (int h = 0; h < (V == 1 ? 2 : 1); ++h) {
+                        const int le = l - h;
+                        const int o = __shfl_sync(0xffffffffu, myoff, le);
+                        if (o >= 0) {
+                            float out[V];
+#pragma unroll
+                            for (int v = 0; v < V; ++v) {
+                                const float m = fminf(mag[h][v], clip);
+                                out[v] = (par_all[v] ^ ((neg[v] >> le) & 1u)) ? -m : m;
+                            }
+                            if (lane_on) gmsg[(size_t)o * 32] = Lane<V>::pack(out);
+                        }
+                    }
                 }
             } else {
                 uint32_t ab[kBDC], sg[kBDC];
@@ -242,10 +239,6 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                         sgn ^= sg[l];
                         min2 = __vminu4(min2, __vmaxu4(min1, av));
                         min1 = __vminu4(min1, av);
-                        if (SYN) {
-#pragma unroll
-                            for (int v = 0; v < V; ++v) syn[v] ^= S[St::HW + l * V + v];
-                        }
                     }
                 }
 #pragma unroll
@@ -258,18 +251,69 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                     if (lane_on) gmsg[(size_t)o * 32] = __vadd4(mag ^ (sneg * 0xffu), sneg);
                 }
             }
-            if (SYN && lane == 0) {
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    const uint32_t bad = syn[v] & actv[v];
-                    if (bad) atomicOr(flags + C.flags + (size_t)tl.pk * 5 * V + (1 + par) * V + v, bad);
-                }
-            }
         }
         __syncwarp();
         slot = (slot + 1) % kBStages;
     }
     b_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
+// syndrome of the decisions after the previous iteration (eq. (hrddcs)) for every
+// row of the listed check-pass tiles, ORed into the package's unsat words (par):
+// one thread per row, reading the packed decision words of the row's variables
+// (L2-resident); a warp whose rows all belong to one tile ORs its lanes' words
+// before a single atomic.  Frames already stopped are masked out.
+// ---------------------------------------------------------------------------
+template <int V>
+__global__ void __launch_bounds__(256)
+bsyn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const uint32_t *__restrict__ hw,
+            uint32_t *__restrict__ flags, const int *__restrict__ tcount, const BTile *__restrict__ tiles, int TR,
+            int par) {
+    const int sTR = __ffs(TR) - 1;  // TR is a power of two
+    const int total = *tcount * TR;
+    const int lane = threadIdx.x & 31;
+    for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
+        const int it = base + threadIdx.x;
+        int tile = -1;
+        uint32_t syn[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) syn[v] = 0u;
+        BTile tl{0, 0, 0, 0};
+        long long fl = 0;
+        if (it < total) {
+            tile = it >> sTR;
+            tl = tiles[tile];
+            const int ri = it & (TR - 1);
+            const BCode C = codes[tl.code];
+            fl = C.flags + (long long)tl.pk * 5 * V;
+            if (ri < tl.count) {
+                const int m = tl.start + ri;
+                const int j = (int)fdiv((uint32_t)m, C.dp), r = m - j * C.p;
+                const uint32_t *h = hw + C.hw + (size_t)tl.pk * C.N * V;
+                for (int l = 0; l < C.L; ++l) {
+                    const int sh = __ldg(shtab + C.tab + j * C.L + l);
+                    if (sh < 0) continue;
+                    int k = r + sh;
+                    if (k >= C.p) k -= C.p;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) syn[v] ^= __ldg(h + ((size_t)l * C.p + k) * V + v);
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v) syn[v] &= ~flags[fl + v];  // running frames only
+            }
+        }
+        const bool one_tile = __all_sync(0xffffffffu, tile == __shfl_sync(0xffffffffu, tile, 0));
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            if (one_tile) {
+                const uint32_t any = __reduce_or_sync(0xffffffffu, syn[v]);
+                if (lane == 0 && any && tile >= 0) atomicOr(flags + fl + (1 + par) * V + v, any);
+            } else if (syn[v]) {
+                atomicOr(flags + fl + (1 + par) * V + v, syn[v]);
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -293,6 +337,7 @@ bvn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
            const BTile *__restrict__ tiles, int TG, float clip, int it, int par) {
     using St = BVnStage<V, MS>;
     constexpr int W = 32 * V;
+    const int sTG = __ffs(TG) - 1;  // TG is a power of two
     constexpr int MU_SEGS = St::MUW / 32;
     constexpr int NSEG = kBNV * (MU_SEGS + kBJ);
     extern __shared__ __align__(16) uint32_t smem[];
@@ -307,12 +352,12 @@ bvn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
     auto issue = [&](int itm, int slot) -> int {
         int mine = -1;
         if (itm < total) {
-            const BTile tl = tiles[itm / TG];
-            const int gi = itm - (itm / TG) * TG;
+            const BTile tl = tiles[itm >> sTG];
+            const int gi = itm & (TG - 1);
             if (gi < tl.count) {
                 const BCode C = codes[tl.code];
                 const int n0 = (tl.start + gi) * kBNV;
-                const int l0 = n0 / C.p, k0 = n0 - l0 * C.p;
+                const int l0 = (int)fdiv((uint32_t)n0, C.dp), k0 = n0 - l0 * C.p;
                 uint32_t *dst = ring + slot * St::WORDS;
                 const uint32_t *gmsg = msg + C.msg + (size_t)tl.pk * C.E * 32;
                 const uint32_t *gmu = mu + C.mu + (size_t)tl.pk * C.N * St::MUW;
@@ -373,8 +418,8 @@ bvn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
         const int myoff = offr[0];
 #pragma unroll
         for (int s = 0; s < kBStages - 1; ++s) offr[s] = offr[s + 1];
-        const BTile tl = tiles[item / TG];
-        const int gi = item - (item / TG) * TG;
+        const BTile tl = tiles[item >> sTG];
+        const int gi = item & (TG - 1);
         if (gi < tl.count) {
             const BCode C = codes[tl.code];
             const uint32_t *S = ring + slot * St::WORDS;
@@ -428,23 +473,42 @@ bvn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                             for (int v = 0; v < V; ++v) tot[v] += aj[jj][v];
                         }
                     }
+                    float bj[kBJ][V];
 #pragma unroll
-                    for (int jj = 0; jj < kBJ; ++jj) {
-                        if (eo[jj] < 0) continue;
-                        float b[V];
+                    for (int jj = 0; jj < kBJ; ++jj)
 #pragma unroll
                         for (int v = 0; v < V; ++v) {
                             float s = m[v];
 #pragma unroll
                             for (int j2 = 0; j2 < kBJ; ++j2)
                                 if (j2 != jj) s += aj[j2][v];
-                            b[v] = clipf(s, clip);
-                            if (XF) {
-                                const float f = phi_f(fabsf(b[v])) * XfScale<V>::store;
-                                b[v] = b[v] < 0.0f ? -f : f;
-                            }
+                            bj[jj][v] = clipf(s, clip);
                         }
-                        if (lane_on) gmsg[(size_t)eo[jj] * 32] = Lane<V>::pack(b);
+                    if constexpr (XF) {
+                        // phi of |beta| on packed pairs (two edges, or the two frames of a lane word)
+                        float f[kBJ][V];
+                        if constexpr (V == 2) {
+#pragma unroll
+                            for (int jj = 0; jj < kBJ; ++jj)
+                                phi_fin2(fabsf(bj[jj][0]), fabsf(bj[jj][1]), f[jj][0], f[jj][1]);
+                        } else {
+                            static_assert(kBJ % 2 == 0, "edge pairs");
+#pragma unroll
+                            for (int jj = 0; jj < kBJ; jj += 2)
+                                phi_fin2(fabsf(bj[jj][0]), fabsf(bj[jj + 1][0]), f[jj][0], f[jj + 1][0]);
+                        }
+#pragma unroll
+                        for (int jj = 0; jj < kBJ; ++jj)
+#pragma unroll
+                            for (int v = 0; v < V; ++v) {
+                                const float t = f[jj][v] * XfScale<V>::store;
+                                bj[jj][v] = bj[jj][v] < 0.0f ? -t : t;
+                            }
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < kBJ; ++jj) {
+                        if (eo[jj] < 0) continue;
+                        if (lane_on) gmsg[(size_t)eo[jj] * 32] = Lane<V>::pack(bj[jj]);
                     }
 #pragma unroll
                     for (int v = 0; v < V; ++v) outb[v] = __ballot_sync(0xffffffffu, clipf(tot[v], clip) < 0.0f);
@@ -602,18 +666,29 @@ static int b_blocks(K kernel, size_t smem) {
 
 template <int V, bool XF, bool MS>
 static void b_cn(ldpc_batch b, bool first, bool syn, int par, cudaStream_t s) {
-#define B_CN(SYNV, FIRSTV)                                                                                          \
-    do {                                                                                                            \
-        auto k = bcn_kernel<V, SYNV, XF, MS, FIRSTV>;                                                               \
-        const size_t sm = (size_t)kWarps * kBStages * BCnStage<V, SYNV, FIRSTV, MS>::WORDS * 4;                     \
-        static int blocks = 0;                                                                                      \
-        if (!blocks) blocks = b_blocks(k, sm);                                                                      \
+    if (syn) {
+        // the syndrome of the decisions after it - 1 iterations, before the check pass
+        static int sblocks = 0;
+        if (!sblocks) {
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            sblocks = (sms > 0 ? sms : 1) * 8;
+        }
+        bsyn_kernel<V><<<sblocks, 256, 0, s>>>(b->codes, b->shtab, b->hw, b->flags, b->counts, b->cn_tiles, b->TR,
+                                               par);
+    }
+#define B_CN(FIRSTV)                                                                                               \
+    do {                                                                                                           \
+        auto k = bcn_kernel<V, XF, MS, FIRSTV>;                                                                    \
+        const size_t sm = (size_t)kWarps * kBStages * BCnStage<V, FIRSTV, MS>::WORDS * 4;                          \
+        static int blocks = 0;                                                                                     \
+        if (!blocks) blocks = b_blocks(k, sm);                                                                     \
         k<<<blocks, kWarps * 32, sm, s>>>(b->codes, b->shtab, b->eotab, (uint32_t *)b->msg, (const uint32_t *)b->mu, \
-                                          b->hw, b->flags, b->counts, b->cn_tiles, b->TR, b->o.clip, par);          \
+                                          b->flags, b->counts, b->cn_tiles, b->TR, b->o.clip);                     \
     } while (0)
-    if (first) B_CN(false, true);
-    else if (syn) B_CN(true, false);
-    else B_CN(false, false);
+    if (first) B_CN(true);
+    else B_CN(false);
 #undef B_CN
 }
 
@@ -654,7 +729,7 @@ static void b_iteration(ldpc_batch b, int it, cudaStream_t s) {
         b_vn<1, true, false>(b, syn, it, par, s);
     }
     if (b->o.early_stop && it < b->o.max_iter) b_tiles(b, false, s);
-    count_launch(b->o.early_stop && it < b->o.max_iter ? 3 : 2);
+    count_launch((b->o.early_stop && it < b->o.max_iter ? 3 : 2) + (syn ? 1 : 0));
 }
 
 static void b_loop(ldpc_batch b, int iters, cudaStream_t s) {
@@ -721,6 +796,7 @@ ldpc_status ldpc_batch_create(const ldpc_code *codes, int32_t ncodes, const int3
         BCode &bc = b->hcodes[i];
         bc.J = c->d.J; bc.L = c->d.L; bc.p = c->d.p; bc.N = c->d.N; bc.M = c->d.M; bc.E = c->d.E;
         bc.P = P; bc.gamma = gammas[i];
+        bc.dp = fast_div((uint32_t)c->d.p);
         bc.tab = (int)hsh.size();
         for (int q = 0; q < c->d.J * c->d.L; ++q) hsh.push_back(c->d.shift[q]), heo.push_back(c->d.eoff[q]);
         bc.msg = (long long)msg_w;
@@ -821,7 +897,8 @@ static ldpc_status b_prepare(ldpc_batch b, const float *const *llr, cudaStream_t
     return LDPC_OK;
 }
 
-// autotuner: rows per check-pass tile and variable groups per variable-pass tile
+// autotuner: rows per check-pass tile and variable groups per variable-pass tile (powers of two:
+// the passes split work items by shifts)
 static ldpc_status b_tune(ldpc_batch b, const float *const *llr, cudaStream_t s) {
     const int cand[3][2] = {{16, 8}, {64, 32}, {256, 128}};
     const int iters = b->o.max_iter < 3 ? b->o.max_iter : 3;

@@ -66,21 +66,29 @@ nm_cn_fwd(const QcDesc d, const void *__restrict__ bin, float *__restrict__ A, c
     const int m = blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int pk = blockIdx.y;
     if (m >= d.M || pk >= P) return;
-    const int j = m / d.p, r = m - j * d.p;
+    const int j = (int)fdiv((uint32_t)m, d.divP), r = m - j * d.p;
     float ab[DCMAX];
     int eid[DCMAX];
     uint32_t neg = 0u;
     float mn1 = INFINITY, mn2 = INFINITY;
+    // every load of the row first (independent of each other: all in flight together), then the
+    // minima
 #pragma unroll
     for (int l = 0; l < DCMAX; ++l) {
-        ab[l] = INFINITY;
         eid[l] = -1;
-        if (l >= d.L || d.shift[j * d.L + l] < 0) continue;
-        int k = r + d.shift[j * d.L + l];
-        if (k >= d.p) k -= d.p;
-        eid[l] = d.eoff[j * d.L + l] + k;
-        const float x = nm_beta<S, FROM_MU>(bin, d, pk, eid[l], l * d.p + k, lane);
-        ab[l] = fabsf(x);
+        ab[l] = 0.0f;
+        const int sh = l < d.L ? d.shift[j * d.L + l] : -1;
+        if (sh >= 0) {
+            int k = r + sh;
+            if (k >= d.p) k -= d.p;
+            eid[l] = d.eoff[j * d.L + l] + k;
+            ab[l] = nm_beta<S, FROM_MU>(bin, d, pk, eid[l], l * d.p + k, lane);
+        }
+    }
+#pragma unroll
+    for (int l = 0; l < DCMAX; ++l) {
+        const float x = ab[l];
+        ab[l] = eid[l] >= 0 ? fabsf(x) : INFINITY;
         neg |= (x < 0.0f ? 1u : 0u) << l;
         mn2 = fminf(mn2, fmaxf(mn1, ab[l]));
         mn1 = fminf(mn1, ab[l]);

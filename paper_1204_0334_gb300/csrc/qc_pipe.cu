@@ -164,29 +164,26 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
             if (fr[v]) frmask |= 0xffu << (8 * v);
         }
         if constexpr (MODE == kModeSP) {
-            // xa: |sign(beta) * phi(|beta|)| (XF: as stored by the variable pass); nm: the edges'
-            // sign bits (bit l); the output sign of edge l is the XOR of the other edges' signs
-            static_assert(DCMAX <= 32, "sign masks of one word");
-            float xa[DCMAX][V];
-            uint32_t nm[V];
+            // xs: signed terms sign(beta) * phi(|beta|) (XF: as stored by the variable pass);
+            // the output sign is the XOR of the other edges' sign bits
+            float xs[DCMAX][V];
+            uint32_t sgn[V];
 #pragma unroll
-            for (int v = 0; v < V; ++v) nm[v] = 0u;
+            for (int v = 0; v < V; ++v) sgn[v] = 0u;
 #pragma unroll
             for (int l = 0; l < DCMAX; ++l) {
 #pragma unroll
-                for (int v = 0; v < V; ++v) xa[l][v] = 0.0f;
+                for (int v = 0; v < V; ++v) xs[l][v] = 0.0f;
                 if (REG || (l < LB && __shfl_sync(0xffffffffu, myoff, l) >= 0)) {
                     float x[V];
                     Lane<V>::unpack(S[l * 32 + lane], x);
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
-                        xa[l][v] = XF ? fabsf(x[v]) * XfScale<V>::load : phi_f(fabsf(x[v]));
-                        nm[v] |= (__float_as_uint(x[v]) >> 31) << l;
+                        xs[l][v] = XF ? x[v] * XfScale<V>::load : copysignf(phi_f(fabsf(x[v])), x[v]);
+                        sgn[v] ^= __float_as_uint(x[v]);
                     }
                 }
             }
-            // pre[l]: the extrinsic sum over the other edges of the row, as prefix + suffix
-            // (forward-backward, no subtraction from the total)
             float pre[DCMAX][V];
             {
                 float acc[V];
@@ -197,45 +194,40 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
                         pre[l][v] = acc[v];
-                        acc[v] += xa[l][v];
-                    }
-#pragma unroll
-                for (int v = 0; v < V; ++v) acc[v] = 0.0f;
-#pragma unroll
-                for (int l = DCMAX - 1; l >= 0; --l)
-#pragma unroll
-                    for (int v = 0; v < V; ++v) {
-                        pre[l][v] += acc[v];
-                        acc[v] += xa[l][v];
+                        acc[v] += fabsf(xs[l][v]);
                     }
             }
-            uint32_t par[V];
+            float suf[V];
 #pragma unroll
-            for (int v = 0; v < V; ++v) par[v] = __popc(nm[v]) & 1u;
-            // phi of the sums on packed pairs: the two frames of a lane word (V = 2), or two
-            // consecutive edges (V = 1); |alpha| with the XOR of the other edges' signs, 0 for a
-            // frame that has just entered its slot
-            static_assert(V <= 2 || MODE != kModeSP, "sum-product lane words hold one or two frames");
-            static_assert(DCMAX % 2 == 0, "edge pairs");
+            for (int v = 0; v < V; ++v) suf[v] = 0.0f;
+            // two edges (V = 1) or the two frames of a lane word (V = 2) per packed phi evaluation,
+            // in the same descending order as the suffix sums
 #pragma unroll
-            for (int l = 0; l < DCMAX; l += (V == 1 ? 2 : 1)) {
-                float mag[2][V];
-                if constexpr (V == 1) {
-                    phi2(pre[l][0], pre[l + 1][0], mag[0][0], mag[1][0]);
-                } else {
-                    phi2(pre[l][0], pre[l][1], mag[0][0], mag[0][1]);
-                }
+            for (int l = DCMAX - 1; l >= 0; l -= (V == 1 ? 2 : 1)) {
+                float arg[2][V], mag[2][V];
+#pragma unroll
+                for (int h = 0; h < (V == 1 ? 2 : 1); ++h)
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        arg[h][v] = pre[l - h][v] + suf[v];
+                        suf[v] += fabsf(xs[l - h][v]);
+                    }
+                if constexpr (V == 1) phi2(arg[0][0], arg[1][0], mag[0][0], mag[1][0]);
+                else phi2(arg[0][0], arg[0][1], mag[0][0], mag[0][1]);
 #pragma unroll
                 for (int h = 0; h < (V == 1 ? 2 : 1); ++h) {
-                    const int le = l + h;
+                    const int le = l - h;
                     const int o = __shfl_sync(0xffffffffu, myoff, le);
                     if (REG || o >= 0) {
                         float out[V];
 #pragma unroll
                         for (int v = 0; v < V; ++v) {
                             const float m = fminf(mag[h][v], clip);
-                            const uint32_t sb = ((par[v] ^ (nm[v] >> le)) & 1u) << 31;
-                            out[v] = __uint_as_float((__float_as_uint(m) | sb) & keep[v]);
+                            // |alpha| with the XOR of the other edges' signs; 0 for a frame that has
+                            // just entered its slot
+                            out[v] = __uint_as_float(
+                                (__float_as_uint(m) | ((sgn[v] ^ __float_as_uint(xs[le][v])) & 0x80000000u)) &
+                                keep[v]);
                         }
                         if (lane_on) gmsg[(size_t)o * 32] = Lane<V>::pack(out);
                     }

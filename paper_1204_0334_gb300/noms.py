@@ -243,6 +243,10 @@ def main(argv=None):
     ap.add_argument("--frames-3p5", type=int, default=1 << 27, help="frame cap per arm at 3.5 dB")
     ap.add_argument("--long-iters", type=int, default=50, help="iterations of the trained decoder")
     ap.add_argument("--target-errors", type=int, default=100)
+    ap.add_argument("--params", default=None, help="evaluate these trained parameters (torch.save of [T][J*L][2]) "
+                                                   "instead of training")
+    ap.add_argument("--frames-at", type=float, nargs=2, action="append", default=[], metavar=("EBN0", "FRAMES"),
+                    help="frame cap per arm at one Eb/N0 (repeatable)")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     import sys
@@ -254,20 +258,26 @@ def main(argv=None):
     import synth
 
     code = QCCode(synth.qc_shifts(a.J, a.L, a.p, seed=a.shift_seed), a.p)
-    t0 = time.time()
-    params, losses = train_noms(code, T=a.T, steps=a.steps, batch=a.batch, lr=a.lr, ebn0=tuple(a.train_ebn0),
-                                unroll=a.unroll, log=print)
-    torch.cuda.synchronize()
-    train_s = time.time() - t0
-    res = {"code": f"QC {a.J}x{a.L} p={a.p} n={code.N}", "T": a.T, "unroll": a.unroll,
-           "training": {"frames": a.steps * a.batch, "ebn0": a.train_ebn0, "seconds": train_s,
-                        "loss_first": losses[0], "loss_last": float(np.mean(losses[-10:]))},
+    caps = {3.5: a.frames_3p5}
+    caps.update({float(e): int(f) for e, f in a.frames_at})
+    res = {"code": f"QC {a.J}x{a.L} p={a.p} n={code.N}", "T": a.T, "unroll": a.unroll}
+    if a.params:
+        params = torch.load(a.params).cuda()
+        res["params_from"] = a.params
+    else:
+        t0 = time.time()
+        params, losses = train_noms(code, T=a.T, steps=a.steps, batch=a.batch, lr=a.lr, ebn0=tuple(a.train_ebn0),
+                                    unroll=a.unroll, log=print)
+        torch.cuda.synchronize()
+        res["training"] = {"frames": a.steps * a.batch, "ebn0": a.train_ebn0, "seconds": time.time() - t0,
+                           "loss_first": losses[0], "loss_last": float(np.mean(losses[-10:]))}
+    res.update({
            "eval": evaluate(code, params, a.ebn0, frames=a.eval_frames, target_fe=a.target_errors,
-                            long_iters=a.long_iters, frame_caps={3.5: a.frames_3p5}),
+                            long_iters=a.long_iters, frame_caps=caps),
            "params_w_mean_per_iter": params[..., 0].mean(dim=1).tolist(),
-           "params_o_mean_per_iter": params[..., 1].mean(dim=1).tolist()}
+           "params_o_mean_per_iter": params[..., 1].mean(dim=1).tolist()})
     print(json.dumps(res, indent=1))
-    if a.out:
+    if a.out and not a.params:
         torch.save(params.cpu(), os.path.splitext(a.out)[0] + "_params.pt")
         with open(a.out, "w") as fh:
             json.dump(res, fh, indent=1)
