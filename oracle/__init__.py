@@ -74,7 +74,9 @@ def _declare(lib):
     lib.or_sp_decode.argtypes = [i32, i32, P, P, i32, P, i32, i32, f64, i32, P, P, P, P, i32]
     lib.or_ms_decode.argtypes = [i32, i32, P, P, i32, P, i32, i32, i32, P, P, P, P, i32]
     lib.or_quantize.argtypes = [P, i32, i32, P]
-    lib.or_noms.argtypes = [i32, i32, P, P, P, i32, P, i32, P, i32, f64, P, P, i32]
+    lib.or_noms.argtypes = [i32, i32, P, P, P, i32, P, i32, P, i32, f64, P, P, i32, i32]
+    lib.or_round_half_array.argtypes = [P, P, ctypes.c_int64]
+    lib.or_round_half_array.restype = None
     lib.or_noms.restype = f64
     lib.or_ldpccc_decode.argtypes = [i32, i32, P, P, i32, i32, i32, i32, i32, i32, P, f64, P, P, P,
                                      P, i32, P, i32]
@@ -487,12 +489,22 @@ def circulant_index(row_ptr, col, p: int, L: int) -> np.ndarray:
     return ((rows // p) * L + (np.asarray(col) // p)).astype(np.int32)
 
 
+def round_half(x) -> np.ndarray:
+    """x rounded to the nearest binary16 value (ties to even), as float64."""
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    lib.or_round_half_array(_p(x), _p(out), x.size)
+    return out
+
+
 def noms(row_ptr, col, cblk, N: int, mu, T: int, params, clip: float = 30.0, want_grad: bool = False,
-         nthreads: int = 1):
+         nthreads: int = 1, store16: bool = False):
     """Normalized/offset min-sum over T iterations with params [T][ncirc][2] = (w, o).
 
     Returns (loss, post^(T) [nfr][N], grad [T][ncirc][2] or None); loss is the mean over
     iterations, bits and frames of softplus(-posterior) (BCE against the all-zero codeword).
+    store16: the FP16-message variant (the stored beta rounded to binary16).
     """
     lib = _load()
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
@@ -508,5 +520,5 @@ def noms(row_ptr, col, cblk, N: int, mu, T: int, params, clip: float = 30.0, wan
     post = np.zeros((nfr, N), dtype=np.float64)
     grad = np.zeros_like(params) if want_grad else None
     loss = lib.or_noms(len(row_ptr) - 1, N, _p(row_ptr), _p(col), _p(cblk), nfr, _p(mu), T, _p(params), ncirc,
-                       clip, _p(post), _p(grad) if want_grad else None, nthreads)
+                       clip, _p(post), _p(grad) if want_grad else None, nthreads, int(store16))
     return loss, post, grad

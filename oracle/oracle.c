@@ -666,8 +666,31 @@ static void or_noms_cn(const or_graph *g, const double *beta, const int *cblk, c
     }
 }
 
+/* x rounded to the nearest binary16 value (ties to even; beyond 65504 -> inf): the storage
+   of the FP16-message variant.  Binary16 keeps 11 significant bits down to 2^-14 and a
+   fixed quantum of 2^-24 below (subnormals). */
+double or_round_half(double x)
+{
+    if (x == 0.0 || !isfinite(x)) return x;
+    double ax = fabs(x);
+    int e;
+    frexp(ax, &e); /* ax = m 2^e, m in [0.5, 1) */
+    int q = e - 11;
+    if (q < -24) q = -24;
+    double r = ldexp(nearbyint(ldexp(ax, -q)), q);
+    if (r > 65504.0) r = INFINITY;
+    return copysign(r, x);
+}
+
+void or_round_half_array(const double *x, double *out, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = or_round_half(x[i]);
+}
+
+/* store16: beta is kept as binary16 between iterations (the FP16-message variant); the
+   gradient treats that rounding as the identity, as the clip is treated where inactive. */
 static void or_noms_vn(const or_graph *g, const double *mu, const double *alpha, double clip, double *beta,
-                       double *raw, double *post)
+                       double *raw, double *post, int store16)
 {
     for (int n = 0; n < g->N; ++n) {
         int v0 = g->vptr[n], dv = g->vptr[n + 1] - v0;
@@ -679,7 +702,7 @@ static void or_noms_vn(const or_graph *g, const double *mu, const double *alpha,
             for (int k2 = 0; k2 < dv; ++k2)
                 if (k2 != k) s += alpha[g->vedge[v0 + k2]];
             raw[g->vedge[v0 + k]] = s;
-            beta[g->vedge[v0 + k]] = or_clip(s, clip);
+            beta[g->vedge[v0 + k]] = store16 ? or_round_half(or_clip(s, clip)) : or_clip(s, clip);
         }
     }
 }
@@ -687,10 +710,12 @@ static void or_noms_vn(const or_graph *g, const double *mu, const double *alpha,
 /*
  * or_noms: forward (and, if grad != NULL, backward) over nfr frames.
  * post_out (nullable) receives post^(T) [nfr][N]; returns the loss.  grad is [T][ncirc][2],
- * accumulated (the caller zeroes it).
+ * accumulated (the caller zeroes it).  store16: the FP16-message variant (beta^(l), l >= 1,
+ * rounded to binary16 when stored).
  */
 double or_noms(int M, int N, const int *row_ptr, const int *col, const int *cblk, int nfr, const float *mu_f,
-               int T, const double *params, int ncirc, double clip, double *post_out, double *grad, int nthreads)
+               int T, const double *params, int ncirc, double clip, double *post_out, double *grad, int nthreads,
+               int store16)
 {
     or_graph g;
     if (T < 1 || or_graph_init(&g, M, N, row_ptr, col)) return NAN;
@@ -716,7 +741,7 @@ double or_noms(int M, int N, const int *row_ptr, const int *col, const int *cblk
             or_noms_cn(&g, beta + (size_t)l * E, cblk, params + (size_t)l * 2 * ncirc, alpha + (size_t)l * E,
                        amin + (size_t)l * E, mval + (size_t)l * E, sval + (size_t)l * E, act + (size_t)l * E);
             or_noms_vn(&g, mu, alpha + (size_t)l * E, clip, beta + (size_t)(l + 1) * E, raw + (size_t)(l + 1) * E,
-                       post + (size_t)l * N);
+                       post + (size_t)l * N, store16);
             for (int n = 0; n < N; ++n) lf += or_softplus(-post[(size_t)l * N + n]);
         }
         if (post_out)

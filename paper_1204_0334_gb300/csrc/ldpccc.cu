@@ -240,16 +240,25 @@ cc_cn_pipe_kernel(const QcDesc d, CcDesc g, CcGeo q, uint32_t *__restrict__ msg,
                 pre[l] = acc;
                 acc += fabsf(xs[l]);
             }
+            // phi of two edges' sums per packed evaluation, in the suffix sums' descending order
+            static_assert(DCMAX % 2 == 0, "edge pairs");
             float suf = 0.0f;
 #pragma unroll
-            for (int l = DCMAX - 1; l >= 0; --l) {
-                const int o = __shfl_sync(0xffffffffu, myoff, rr * DCMAX + l);
-                if (o >= 0) {
-                    const float mag = fminf(phi_f(pre[l] + suf), clip);
-                    msg[(size_t)o * 32 + lane] =
-                        __float_as_uint(mag) | ((sgn ^ __float_as_uint(xs[l])) & 0x80000000u);
-                }
+            for (int l = DCMAX - 1; l >= 1; l -= 2) {
+                const float a0 = pre[l] + suf;
                 suf += fabsf(xs[l]);
+                const float a1 = pre[l - 1] + suf;
+                suf += fabsf(xs[l - 1]);
+                float m0, m1;
+                phi2(a0, a1, m0, m1);
+                const int o0 = __shfl_sync(0xffffffffu, myoff, rr * DCMAX + l);
+                const int o1 = __shfl_sync(0xffffffffu, myoff, rr * DCMAX + l - 1);
+                if (o0 >= 0)
+                    msg[(size_t)o0 * 32 + lane] =
+                        __float_as_uint(fminf(m0, clip)) | ((sgn ^ __float_as_uint(xs[l])) & 0x80000000u);
+                if (o1 >= 0)
+                    msg[(size_t)o1 * 32 + lane] =
+                        __float_as_uint(fminf(m1, clip)) | ((sgn ^ __float_as_uint(xs[l - 1])) & 0x80000000u);
             }
         }
         __syncwarp();
@@ -363,15 +372,23 @@ cc_vn_pipe_kernel(const QcDesc d, CcDesc g, CcGeo q, uint32_t *__restrict__ msg,
                 a[j] = e[j] >= 0 ? __uint_as_float(S[AL + (iv * JMAX + j) * 32 + lane]) : 0.0f;
                 tot += a[j];
             }
+            // store sign(beta) * phi(|beta|), beta = clip(sm); phi on packed pairs of edges
+            float sm[JMAX], ph[JMAX];
+#pragma unroll
+            for (int j = 0; j < JMAX; ++j) {
+                sm[j] = m;
+#pragma unroll
+                for (int j2 = 0; j2 < JMAX; ++j2)
+                    if (j2 != j) sm[j] += a[j2];
+            }
+#pragma unroll
+            for (int j = 0; j + 1 < JMAX; j += 2)
+                phi_fin2(fminf(fabsf(sm[j]), clip), fminf(fabsf(sm[j + 1]), clip), ph[j], ph[j + 1]);
+            if (JMAX % 2) ph[JMAX - 1] = phi_fin(fminf(fabsf(sm[JMAX - 1]), clip));
 #pragma unroll
             for (int j = 0; j < JMAX; ++j) {
                 if (e[j] < 0) continue;  // warp-uniform
-                float sm = m;
-#pragma unroll
-                for (int j2 = 0; j2 < JMAX; ++j2)
-                    if (j2 != j) sm += a[j2];
-                // store sign(beta) * phi(|beta|), beta = clip(sm)
-                msg[(size_t)e[j] * 32 + lane] = __float_as_uint(with_sign_of(phi_fin(fminf(fabsf(sm), clip)), sm));
+                msg[(size_t)e[j] * 32 + lane] = __float_as_uint(with_sign_of(ph[j], sm[j]));
             }
             if (out_here && sidx < gamma) {
                 const float pst = clipf(tot, clip);

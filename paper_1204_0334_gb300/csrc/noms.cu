@@ -71,24 +71,16 @@ nm_cn_fwd(const QcDesc d, const void *__restrict__ bin, float *__restrict__ A, c
     int eid[DCMAX];
     uint32_t neg = 0u;
     float mn1 = INFINITY, mn2 = INFINITY;
-    // every load of the row first (independent of each other: all in flight together), then the
-    // minima
 #pragma unroll
     for (int l = 0; l < DCMAX; ++l) {
+        ab[l] = INFINITY;
         eid[l] = -1;
-        ab[l] = 0.0f;
-        const int sh = l < d.L ? d.shift[j * d.L + l] : -1;
-        if (sh >= 0) {
-            int k = r + sh;
-            if (k >= d.p) k -= d.p;
-            eid[l] = d.eoff[j * d.L + l] + k;
-            ab[l] = nm_beta<S, FROM_MU>(bin, d, pk, eid[l], l * d.p + k, lane);
-        }
-    }
-#pragma unroll
-    for (int l = 0; l < DCMAX; ++l) {
-        const float x = ab[l];
-        ab[l] = eid[l] >= 0 ? fabsf(x) : INFINITY;
+        if (l >= d.L || d.shift[j * d.L + l] < 0) continue;
+        int k = r + d.shift[j * d.L + l];
+        if (k >= d.p) k -= d.p;
+        eid[l] = d.eoff[j * d.L + l] + k;
+        const float x = nm_beta<S, FROM_MU>(bin, d, pk, eid[l], l * d.p + k, lane);
+        ab[l] = fabsf(x);
         neg |= (x < 0.0f ? 1u : 0u) << l;
         mn2 = fminf(mn2, fmaxf(mn1, ab[l]));
         mn1 = fminf(mn1, ab[l]);
@@ -117,7 +109,7 @@ nm_vn_fwd(const QcDesc d, const float *__restrict__ A, const float *__restrict__
     const int pk = blockIdx.y;
     float lsum = 0.0f;
     if (n < d.N && pk < P) {
-        const int l = n / d.p, k = n - l * d.p;
+        const int l = (int)fdiv((uint32_t)n, d.divP), k = n - l * d.p;
         const float mv = mu[((size_t)pk * d.N + n) * 32 + lane];
         float a[JMAX];
         int eid[JMAX];
@@ -169,7 +161,7 @@ nm_vn_bwd(const QcDesc d, const float *__restrict__ A, const float *__restrict__
     const int n = blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int pk = blockIdx.y;
     if (n >= d.N || pk >= P) return;
-    const int l = n / d.p, k = n - l * d.p;
+    const int l = (int)fdiv((uint32_t)n, d.divP), k = n - l * d.p;
     const float mv = mu[((size_t)pk * d.N + n) * 32 + lane];
     float a[JMAX], gbm[JMAX];
     int eid[JMAX];
@@ -218,14 +210,18 @@ nm_vn_bwd(const QcDesc d, const float *__restrict__ A, const float *__restrict__
 // ---------------------------------------------------------------------------
 constexpr int kBwdRows = 16;
 
+// The lanes' partial gradients per edge slot live in the warp's slice of dynamic shared
+// memory ([DCMAX][2][32] floats) rather than in registers, so that three blocks fit per SM.
 template <int DCMAX, typename S, bool FROM_MU>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, 3)
 nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict__ GA, const float *__restrict__ prm_l,
           float *__restrict__ GB, float *__restrict__ grad_l, int P, int want_gb) {
     __shared__ float sg[kMaxJ * kMaxL * 2];
+    extern __shared__ float s_part[];
     for (int i = threadIdx.x; i < d.J * d.L * 2; i += blockDim.x) sg[i] = 0.0f;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *part = s_part + (size_t)warp * DCMAX * 2 * 32;  // [l][w or o][lane]
     const int chunks = (d.p + kBwdRows - 1) / kBwdRows;
     const long long total = (long long)P * d.J * chunks;
     for (long long item = (long long)blockIdx.x * kWarps + warp; item < total; item += (long long)gridDim.x * kWarps) {
@@ -234,9 +230,9 @@ nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict_
         const int j = rem / chunks, r0 = (rem - j * chunks) * kBwdRows;
         const int r1 = min(r0 + kBwdRows, d.p);
         const float *prm = prm_l + (size_t)j * d.L * 2;
-        float aw[DCMAX], ao[DCMAX];  // this lane's partial gradients of (w, o) per edge slot l
+        // this lane's partial gradients of (w, o) per edge slot l
 #pragma unroll
-        for (int l = 0; l < DCMAX; ++l) aw[l] = ao[l] = 0.0f;
+        for (int l = 0; l < DCMAX; ++l) part[(2 * l) * 32 + lane] = part[(2 * l + 1) * 32 + lane] = 0.0f;
         // edge index of slot l in row r (-1: absent block)
         auto edge = [&](int l, int r) -> int {
             if (l >= d.L) return -1;
@@ -295,8 +291,8 @@ nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict_
                 const bool act = (first ? i2 : i1) >= 0 && fmaf(w, mv, -o) > 0.0f;
                 if (act) {
                     const float gs = ga[l] * s;
-                    aw[l] = fmaf(gs, mv, aw[l]);
-                    ao[l] -= gs;
+                    part[(2 * l) * 32 + lane] = fmaf(gs, mv, part[(2 * l) * 32 + lane]);
+                    part[(2 * l + 1) * 32 + lane] -= gs;
                     if (first) g2 += gs * w;
                     else g1 += gs * w;
                 }
@@ -319,7 +315,7 @@ nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict_
 #pragma unroll
         for (int l = 0; l < DCMAX; ++l) {
             if (edge(l, r0) < 0) continue;  // warp-uniform
-            float gw = aw[l], go = ao[l];
+            float gw = part[(2 * l) * 32 + lane], go = part[(2 * l + 1) * 32 + lane];
 #pragma unroll
             for (int of = 16; of > 0; of >>= 1) {
                 gw += __shfl_xor_sync(0xffffffffu, gw, of);
@@ -443,7 +439,7 @@ static ldpc_status nm_backward(ldpc_code c, ldpc_noms_state &w, float *grad, cud
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int cb_blocks = std::max(1, sms * 4);
+    const int cb_blocks = std::max(1, sms * 3);  // three resident blocks per SM
     const float zinv = (float)(1.0 / ((double)w.T * d.N * w.B));
     int seg_base = -1;  // iterations seg_base+1 .. seg_base+k-1 recomputed into seg
     for (int l = w.T; l >= 1; --l) {
@@ -484,8 +480,14 @@ static ldpc_status nm_backward(ldpc_code c, ldpc_noms_state &w, float *grad, cud
         const int want_gb = l > 1;
 #define NM_CB(DC)                                                                                                  \
     do {                                                                                                           \
-        if (from_mu) nm_cn_bwd<DC, S, true><<<cb_blocks, kWarps * 32, 0, s>>>(d, bin, w.GA, prm, w.GB, gl, w.P, want_gb); \
-        else nm_cn_bwd<DC, S, false><<<cb_blocks, kWarps * 32, 0, s>>>(d, bin, w.GA, prm, w.GB, gl, w.P, want_gb);        \
+        const size_t psm = (size_t)kWarps * (DC) * 2 * 32 * sizeof(float);                                        \
+        if (from_mu) {                                                                                             \
+            cudaFuncSetAttribute(nm_cn_bwd<DC, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);    \
+            nm_cn_bwd<DC, S, true><<<cb_blocks, kWarps * 32, psm, s>>>(d, bin, w.GA, prm, w.GB, gl, w.P, want_gb);  \
+        } else {                                                                                                   \
+            cudaFuncSetAttribute(nm_cn_bwd<DC, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);   \
+            nm_cn_bwd<DC, S, false><<<cb_blocks, kWarps * 32, psm, s>>>(d, bin, w.GA, prm, w.GB, gl, w.P, want_gb); \
+        }                                                                                                          \
     } while (0)
         if (d.L <= 8) NM_CB(8);
         else if (d.L <= 16) NM_CB(16);

@@ -70,7 +70,10 @@ def test_noms_loss_and_gradient_match_oracle(pkg, msg, ckpt):
     assert np.max(np.abs(post.cpu().numpy() - po) / np.maximum(1, np.abs(po))) < 1e-4
     g = grad.cpu().numpy().astype(np.float64)
     scale = np.abs(go).max()
-    assert np.max(np.abs(g - go)) <= 1e-3 * scale, (np.max(np.abs(g - go)), scale)
+    # element by element: within 1e-3 of each gradient entry (entries below 1e-3 of the largest
+    # measured against that floor); measured 8e-5
+    rel = np.abs(g - go) / np.maximum(np.abs(go), 1e-3 * scale)
+    assert rel.max() <= 1e-3, (rel.max(), scale)
 
 
 def test_noms_checkpointing_does_not_change_gradients(pkg):
@@ -92,7 +95,9 @@ def test_noms_checkpointing_does_not_change_gradients(pkg):
 
 
 def test_noms_fp16_storage_gradient(pkg):
-    """FP16 storage of the saved messages: loss and gradient close to the FP64 oracle."""
+    """FP16 storage of the saved messages against the oracle of the same variant (the stored beta rounded
+    to binary16): loss and gradient element by element.  Against the unrounded FP64 oracle the min-sum
+    gradient jumps wherever rounding changes the arg-min edge, so that comparison is not element-wise."""
     shifts, rp, col, cb = setup(3, 6, 32, 2)
     code = pkg.QCCode(shifts, 32)
     T, B = 5, 64
@@ -102,10 +107,13 @@ def test_noms_fp16_storage_gradient(pkg):
     loss, _ = pkg.ldpc_noms_forward(code.handle, torch.from_numpy(mu).cuda(), prm_d, pkg.MSG_F16, 2, 30.0)
     grad = torch.zeros_like(prm_d)
     pkg.ldpc_noms_backward(code.handle, prm_d, grad)
-    lo, _, go = oracle.noms(rp, col, cb, code.N, mu, T, prm.astype(np.float64), want_grad=True, nthreads=8)
-    assert abs(float(loss) - lo) <= 2e-3 * abs(lo)
-    g = grad.cpu().numpy()
-    assert np.linalg.norm(g - go) <= 5e-2 * np.linalg.norm(go)
+    lo, _, go = oracle.noms(rp, col, cb, code.N, mu, T, prm.astype(np.float64), want_grad=True, nthreads=8,
+                            store16=True)
+    assert abs(float(loss) - lo) <= 1e-5 * abs(lo)
+    g = grad.cpu().numpy().astype(np.float64)
+    rel = np.abs(g - go) / np.maximum(np.abs(go), 1e-3 * np.abs(go).max())
+    print(f"FP16 gradient: largest element-wise relative deviation {rel.max():.2e}")
+    assert rel.max() <= 1e-3, rel.max()
 
 
 def test_backward_requires_forward(pkg):

@@ -535,6 +535,41 @@ def test_noms_two_checks_two_iterations_hand_values():
     assert abs(loss - np.mean(np.log1p(np.exp(-np.concatenate([post1, post2]))))) <= 1e-12
 
 
+def test_binary16_rounding_matches_numpy_float16():
+    """The FP16-message variant's storage rounding against numpy's own binary16 conversion (round to
+    nearest even), over normals, subnormals, ties and the overflow edge."""
+    rng = np.random.default_rng(12)
+    x = np.concatenate([rng.normal(0, 8, 100000), rng.normal(0, 1e-5, 20000), rng.uniform(-30, 30, 50000),
+                        [0.0, -0.0, 1.0 + 2.0 ** -11, 1.0 + 3 * 2.0 ** -11, 2.0 ** -24 * 1.5, 2.0 ** -25,
+                         65504.0, 65519.0, 65520.0, -70000.0]])
+    with np.errstate(over="ignore"):  # 65520 and beyond round to infinity, as intended
+        want = x.astype(np.float16).astype(np.float64)
+    got = oracle.round_half(x)
+    assert np.array_equal(got, want)
+
+
+def test_noms_fp16_variant_rounds_stored_messages():
+    """With binary16 storage the first iteration (fed by the FP32 channel LLRs) is unchanged and later
+    iterations see rounded inputs: on the hand-worked two-check example every value is a multiple of
+    2^-7, exact in binary16, so the result equals the unrounded one."""
+    H = oracle.qc_parity_check([[0, 0, 0, -1, -1], [-1, -1, 0, 0, 0]], 1)
+    rp, col = oracle.csr_rows(H)
+    cb = oracle.circulant_index(rp, col, 1, 5)
+    mu = np.array([[2.0, -1.25, 0.5, 1.75, -3.0]], dtype=np.float32)
+    params = np.zeros((2, 10, 2))
+    params[0, :, :] = (0.75, 0.125)
+    params[1, :, :] = (0.5, 0.25)
+    params[1, 0, :] = (0.625, 0.0625)
+    a = oracle.noms(rp, col, cb, 5, mu, 2, params)
+    b = oracle.noms(rp, col, cb, 5, mu, 2, params, store16=True)
+    assert np.array_equal(a[1], b[1]) and a[0] == b[0]
+    # an input whose second-iteration messages are not binary16 values changes
+    mu2 = np.array([[2.0, -1.2345678, 0.5, 1.75, -3.0]], dtype=np.float32)
+    c = oracle.noms(rp, col, cb, 5, mu2, 2, params)
+    e = oracle.noms(rp, col, cb, 5, mu2, 2, params, store16=True)
+    assert not np.array_equal(c[1], e[1]) and np.allclose(c[1], e[1], atol=2e-3)
+
+
 def test_noms_gradient_matches_finite_differences():
     """Hand-written reverse mode against central differences of the FP64 loss (away from ties and kinks)."""
     H, rp, col, cb = _qc(3, 6, 8, 5)
