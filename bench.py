@@ -620,6 +620,7 @@ def batch_bench(a, pkg, stream) -> dict:
         for p0 in range(0, g, 64):
             visited += float(it_np[p0:p0 + 64].max()) * 64 * (8 * c.E + 4 * c.N + c.N / 8)
     info = pkg.ldpc_batch_info(b)
+    moved = sum(pkg.ldpc_batch_moved(b, len(codes)))
     pkg.ldpc_batch_destroy(b)
     peak = load_peaks().get("hbm_gbs", 6800.0)
     return {"workload": "64 QC codes 3x6..4x24, p 32..765, %d frames total (1..4096 per code), FP16, 30 iters "
@@ -628,7 +629,8 @@ def batch_bench(a, pkg, stream) -> dict:
             "path_achieved_gbs": path_bytes / (ms / 1e3) / 1e9, "path_frac": path_bytes / (ms / 1e3) / 1e9 / peak,
             "visited_over_canonical": visited / path_bytes,
             "visited_frac": visited / (ms / 1e3) / 1e9 / peak,
-            "tile_rows": info["tile_rows"], "tile_groups": info["tile_groups"]}
+            "tile_rows": info["tile_rows"], "tile_groups": info["tile_groups"],
+            "frames_compacted": moved}
 
 
 def sparse_bench(a, pkg, qc, stream) -> dict:

@@ -65,6 +65,7 @@ _SIGNATURES = [
     ("ldpc_batch_decode", ctypes.c_int, [P, P, P, P, P, P]),
     ("ldpc_batch_info", ctypes.c_int, [P, P, P, P]),
     ("ldpc_batch_destroy", ctypes.c_int, [P]),
+    ("ldpc_batch_moved", ctypes.c_int, [P, P]),
     ("ldpc_channel", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, P, P]),
     ("ldpc_ber_sim", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
                                     ctypes.c_int64, ctypes.c_int32, P, P, P]),
@@ -380,6 +381,13 @@ def ldpc_batch_info(batch: int) -> dict:
     ms = (ctypes.c_double * 3)()
     _check(lib().ldpc_batch_info(batch, ctypes.byref(tr), ctypes.byref(tg), ms), "ldpc_batch_info")
     return {"tile_rows": tr.value, "tile_groups": tg.value, "tune_ms": list(ms)}
+
+
+def ldpc_batch_moved(batch: int, ncodes: int) -> list:
+    """Frames of each code the last decode moved to the code's second package area."""
+    out = (ctypes.c_int32 * ncodes)()
+    _check(lib().ldpc_batch_moved(batch, out), "ldpc_batch_moved")
+    return list(out)
 
 
 def ldpc_batch_destroy(batch: int):

@@ -32,6 +32,7 @@ struct BCode {
     int J, L, p, N, M, E, P, gamma, tab;
     FastDiv dp;                           // n / p by multiply-high
     long long msg, mu, hw, flags, iters;  // offsets (words / ints) into the shared regions
+    long long map;                        // offset of the code's compaction map (ints)
 };
 
 struct BTile {
@@ -560,6 +561,199 @@ bvn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
 }
 
 // ---------------------------------------------------------------------------
+// Frame-level compaction.  Early stop frees lanes, but a package of W frames is
+// visited until its slowest frame stops.  After iteration K every code whose
+// running frames are few enough moves them, densely and in frame order, into its
+// second package area (entered in the code table as code nc + c): messages,
+// channel LLRs, decision bits; the first area's frames are then all marked done,
+// and the tile lists pick up the second area.  map[k] is the frame (slot of the
+// first area) now in slot k of the second; its outputs are scattered back at the
+// end.  Codes whose running frames exceed limit of their frames are left as they are.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int b_block_sum(int x, int *sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    __syncthreads();
+    if (lane == 0) sh[warp] = x;
+    __syncthreads();
+    int t = 0;
+    for (int w = 0; w < nw; ++w) t += sh[w];
+    return t;
+}
+
+// one block per code: count, decide, number the running frames in frame order, retire the first area
+__global__ void __launch_bounds__(1024)
+bcompact_plan_kernel(const BCode *__restrict__ codes, uint32_t *__restrict__ flags, int *__restrict__ map,
+                     int *__restrict__ moved, int V, float limit) {
+    __shared__ int sh[32];
+    __shared__ int s_base;
+    const int c = blockIdx.x;
+    const BCode C = codes[c];
+    const int W = 32 * V, frames = C.P * W;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *F = flags + C.flags;
+    auto running = [&](int f) -> bool {
+        const int pk = f / W, ln = (f % W) / V, v = f % V;
+        const uint32_t *b = F + (size_t)pk * 5 * V;
+        return !((b[v] >> ln) & 1u) && ((b[3 * V + v] >> ln) & 1u);
+    };
+    int cnt = 0, val = 0;
+    for (int f = threadIdx.x; f < frames; f += blockDim.x) {
+        const int pk = f / W, ln = (f % W) / V, v = f % V;
+        val += (F[(size_t)pk * 5 * V + 3 * V + v] >> ln) & 1u;
+        cnt += running(f) ? 1 : 0;
+    }
+    const int R = b_block_sum(cnt, sh);
+    const int valid = b_block_sum(val, sh);
+    if (R == 0 || (float)R > limit * (float)valid) {
+        if (threadIdx.x == 0) moved[c] = 0;
+        return;
+    }
+    if (threadIdx.x == 0) s_base = 0;
+    __syncthreads();
+    for (int f0 = 0; f0 < frames; f0 += blockDim.x) {
+        const int f = f0 + threadIdx.x;
+        const bool r = f < frames && running(f);
+        const uint32_t bal = __ballot_sync(0xffffffffu, r);
+        __syncthreads();
+        if (lane == 0) sh[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, all = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            if (w < warp) before += sh[w];
+            all += sh[w];
+        }
+        if (r) map[C.map + s_base + before + __popc(bal & ((1u << lane) - 1u))] = f;
+        __syncthreads();
+        if (threadIdx.x == 0) s_base += all;
+        __syncthreads();
+    }
+    // every frame of the first area is now done (stopped, or moved on)
+    for (int i = threadIdx.x; i < C.P * V; i += blockDim.x) F[(size_t)(i / V) * 5 * V + i % V] = 0xffffffffu;
+    if (threadIdx.x == 0) moved[c] = R;
+}
+
+// the second area of code c: messages (one thread per destination lane word), channel LLRs
+// (per destination element) and decision words (one warp per destination word, a ballot of
+// the moved frames' bits), flags (done past the moved frames, unsat and fin cleared)
+template <int V, bool MS>
+__global__ void __launch_bounds__(256)
+bcompact_gather_kernel(const BCode *__restrict__ codes, uint32_t *__restrict__ msg, uint32_t *__restrict__ mu,
+                       uint32_t *__restrict__ hw, uint32_t *__restrict__ flags, const int *__restrict__ map,
+                       const int *__restrict__ moved, int nc) {
+    constexpr int W = 32 * V;
+    constexpr int EB = 32 / V;  // bits of one message element
+    const int c = blockIdx.y;
+    const int R = moved[c];
+    if (R == 0) return;
+    const BCode A = codes[c], B = codes[nc + c];
+    const int P2 = (R + W - 1) / W;
+    const int *mp = map + A.map;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // messages: word (pk2, e, lane2)
+    const long long nmsg = (long long)P2 * A.E * 32;
+    for (long long i = tid; i < nmsg; i += stride) {
+        const int lane2 = (int)(i & 31);
+        const long long pe = i >> 5;
+        const int e = (int)(pe % A.E), pk2 = (int)(pe / A.E);
+        uint32_t w = 0u;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int k = pk2 * W + lane2 * V + v;
+            if (k >= R) break;
+            const int f = mp[k];
+            const int pk = f / W, ln = (f % W) / V, vs = f % V;
+            const uint32_t src = msg[A.msg + ((size_t)pk * A.E + e) * 32 + ln];
+            const uint32_t sub = V == 1 ? src : (src >> (vs * EB)) & ((1u << EB) - 1u);
+            w |= sub << (v * EB);
+        }
+        msg[B.msg + ((size_t)pk2 * A.E + e) * 32 + lane2] = w;
+    }
+    // channel LLRs: element (pk2, n, j) of [P][N][W] (floats; int8 for min-sum)
+    const long long nmu = (long long)P2 * A.N * W;
+    for (long long i = tid; i < nmu; i += stride) {
+        const int j = (int)(i % W);
+        const long long pn = i / W;
+        const int n = (int)(pn % A.N), pk2 = (int)(pn / A.N);
+        const int k = pk2 * W + j;
+        if (k >= R) continue;
+        const int f = mp[k];
+        const size_t si = ((size_t)(f / W) * A.N + n) * W + (f % W), di = ((size_t)pk2 * A.N + n) * W + j;
+        if (MS) reinterpret_cast<int8_t *>(mu + B.mu)[di] = reinterpret_cast<const int8_t *>(mu + A.mu)[si];
+        else reinterpret_cast<float *>(mu + B.mu)[di] = reinterpret_cast<const float *>(mu + A.mu)[si];
+    }
+    // decision words: one warp per destination word (pk2, n, v)
+    const long long nhw = (long long)P2 * A.N * V;
+    const int lane = threadIdx.x & 31;
+    for (long long wi = tid >> 5; wi < nhw; wi += stride >> 5) {
+        const int v = (int)(wi % V);
+        const long long pn = wi / V;
+        const int n = (int)(pn % A.N), pk2 = (int)(pn / A.N);
+        const int k = pk2 * W + lane * V + v;
+        uint32_t bit = 0u;
+        if (k < R) {
+            const int f = mp[k];
+            bit = (hw[A.hw + ((size_t)(f / W) * A.N + n) * V + f % V] >> ((f % W) / V)) & 1u;
+        }
+        const uint32_t word = __ballot_sync(0xffffffffu, bit != 0u);
+        if (lane == 0) hw[B.hw + ((size_t)pk2 * A.N + n) * V + v] = word;
+    }
+    // flags of the second area
+    for (long long i = tid; i < (long long)A.P * V; i += stride) {
+        const int pk2 = (int)(i / V), v = (int)(i % V);
+        uint32_t valid = 0u;
+        for (int ln = 0; ln < 32; ++ln)
+            if (pk2 * W + ln * V + v < R) valid |= 1u << ln;
+        uint32_t *b = flags + B.flags + (size_t)pk2 * 5 * V;
+        b[v] = ~valid;
+        b[V + v] = 0u;
+        b[2 * V + v] = 0u;
+        b[3 * V + v] = valid;
+        b[4 * V + v] = 0u;
+    }
+}
+
+// every package of the second areas holds no frame (done), before a decode
+__global__ void bsecond_init_kernel(const BCode *__restrict__ codes, uint32_t *__restrict__ flags, int *__restrict__ moved,
+                                    int nc, int V) {
+    const int c = blockIdx.x;
+    const BCode B = codes[nc + c];
+    for (int i = threadIdx.x; i < B.P * 5 * V; i += blockDim.x) flags[B.flags + i] = (i % (5 * V)) < V ? 0xffffffffu : 0u;
+    if (threadIdx.x == 0) moved[c] = 0;
+}
+
+// after the finish of the second areas: the moved frames' decisions, iteration counts and ok flags
+// go to their rows of the caller's outputs (pointer arrays per code, entries may be NULL)
+__global__ void __launch_bounds__(256)
+bscatter_kernel(const BCode *__restrict__ codes, const uint32_t *__restrict__ hw, const int32_t *__restrict__ iters,
+                const int *__restrict__ map, const int *__restrict__ moved, int nc, int V,
+                uint8_t *const *__restrict__ hard, int32_t *const *__restrict__ itout, int32_t *const *__restrict__ okout) {
+    const int c = blockIdx.y;
+    const int R = moved[c];
+    if (R == 0) return;
+    const BCode A = codes[c], B = codes[nc + c];
+    const int W = 32 * V;
+    const int *mp = map + A.map;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t cap = (size_t)B.P * W;  // ok flags follow the iteration counts
+    for (long long i = tid; i < R; i += stride) {
+        const int f = mp[i];
+        if (itout && itout[c]) itout[c][f] = iters[B.iters + i];
+        if (okout && okout[c]) okout[c][f] = iters[B.iters + cap + i];
+    }
+    if (!hard || !hard[c]) return;
+    uint8_t *h = hard[c];
+    const long long total = (long long)R * A.N;
+    for (long long i = tid; i < total; i += stride) {
+        const int k = (int)(i / A.N), n = (int)(i % A.N);
+        const uint32_t w = hw[B.hw + ((size_t)(k / W) * A.N + n) * V + k % V];
+        h[(size_t)mp[k] * A.N + n] = (uint8_t)((w >> ((k % W) / V)) & 1u);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // tile lists of the packages with a running frame, over all codes
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024)
@@ -650,6 +844,16 @@ struct ldpc_batch_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     double tune_ms[3] = {0, 0, 0};
+    // frame-level compaction: entries ncodes .. 2 ncodes - 1 of the code table are the codes'
+    // second package areas; after iteration K a code's running frames move there when they are
+    // at most `limit` of its frames
+    int *map = nullptr;     // per code: second-area slot -> frame
+    int *moved = nullptr;   // [ncodes] frames moved by the last decode
+    uint8_t **d_hard = nullptr;   // device copies of the caller's output pointer arrays
+    int32_t **d_iters = nullptr, **d_ok = nullptr;
+    int K = 8;
+    float limit = 0.75f;
+    int sms = 1;
 };
 
 namespace ldpc {
@@ -728,6 +932,21 @@ static void b_iteration(ldpc_batch b, int it, cudaStream_t s) {
         b_cn<1, true, false>(b, first, syn, par, s);
         b_vn<1, true, false>(b, syn, it, par, s);
     }
+    if (b->o.early_stop && it == b->K && it < b->o.max_iter) {
+        // frame-level compaction (the tile rebuild below lists the second areas' packages)
+        bcompact_plan_kernel<<<b->ncodes, 1024, 0, s>>>(b->codes, b->flags, b->map, b->moved, b->V, b->limit);
+        const dim3 grd((unsigned)(b->sms * 2), (unsigned)b->ncodes);
+        if (b->o.algo == LDPC_ALGO_MS)
+            bcompact_gather_kernel<4, true><<<grd, 256, 0, s>>>(b->codes, (uint32_t *)b->msg, (uint32_t *)b->mu, b->hw,
+                                                               b->flags, b->map, b->moved, b->ncodes);
+        else if (b->o.msg == LDPC_MSG_F16)
+            bcompact_gather_kernel<2, false><<<grd, 256, 0, s>>>(b->codes, (uint32_t *)b->msg, (uint32_t *)b->mu, b->hw,
+                                                                b->flags, b->map, b->moved, b->ncodes);
+        else
+            bcompact_gather_kernel<1, false><<<grd, 256, 0, s>>>(b->codes, (uint32_t *)b->msg, (uint32_t *)b->mu, b->hw,
+                                                                b->flags, b->map, b->moved, b->ncodes);
+        count_launch(2);
+    }
     if (b->o.early_stop && it < b->o.max_iter) b_tiles(b, false, s);
     count_launch((b->o.early_stop && it < b->o.max_iter ? 3 : 2) + (syn ? 1 : 0));
 }
@@ -779,7 +998,8 @@ ldpc_status ldpc_batch_create(const ldpc_code *codes, int32_t ncodes, const int3
     size_t msg_w = 0, mu_w = 0, hw_w = 0, fl_w = 0, it_n = 0, post_n = 0;
     std::vector<int> hsh, heo, pc, pp;
     size_t max_ct = 0, max_vt = 0;
-    b->hcodes.resize(ncodes);
+    b->hcodes.resize(2 * (size_t)ncodes);
+    size_t map_n = 0;
     for (int i = 0; i < ncodes; ++i) {
         const ldpc_code c = codes[i];
         if (!c || gammas[i] < 1) {
@@ -813,6 +1033,29 @@ ldpc_status ldpc_batch_create(const ldpc_code *codes, int32_t ncodes, const int3
         for (int pk = 0; pk < P; ++pk) pc.push_back(i), pp.push_back(pk);
         max_ct += (size_t)P * c->d.M;                    // tiles of one row each at most
         max_vt += (size_t)P * ((c->d.N + kBNV - 1) / kBNV);
+        bc.map = (long long)map_n;
+        map_n += (size_t)P * W;
+    }
+    // the second package areas (frame-level compaction): entries ncodes + i, same geometry
+    for (int i = 0; i < ncodes; ++i) {
+        const ldpc_code c = codes[i];
+        BCode bc = b->hcodes[i];
+        const int P = bc.P;
+        bc.gamma = 0;
+        bc.msg = (long long)msg_w;
+        bc.mu = (long long)mu_w;
+        bc.hw = (long long)hw_w;
+        bc.flags = (long long)fl_w;
+        bc.iters = (long long)it_n;
+        msg_w += (size_t)P * c->d.E * 32;
+        mu_w += (size_t)P * c->d.N * (o.algo == LDPC_ALGO_MS ? 32 : W);
+        hw_w += (size_t)P * c->d.N * V;
+        fl_w += (size_t)P * 5 * V;
+        it_n += (size_t)P * W * 2;
+        b->hcodes[ncodes + i] = bc;
+        for (int pk = 0; pk < P; ++pk) pc.push_back(ncodes + i), pp.push_back(pk);
+        max_ct += (size_t)P * c->d.M;
+        max_vt += (size_t)P * ((c->d.N + kBNV - 1) / kBNV);
     }
     b->npairs = (int)pc.size();
     auto fail = [&](const char *what) {
@@ -826,7 +1069,17 @@ ldpc_status ldpc_batch_create(const ldpc_code *codes, int32_t ncodes, const int3
     if (cudaMalloc(&b->hw, hw_w * 4)) return fail("hard words");
     if (cudaMalloc(&b->flags, fl_w * 4)) return fail("flags");
     if (cudaMalloc(&b->iters, it_n * 4)) return fail("iterations");
-    if (cudaMalloc(&b->codes, sizeof(BCode) * ncodes)) return fail("code table");
+    if (cudaMalloc(&b->codes, sizeof(BCode) * 2 * ncodes)) return fail("code table");
+    if (cudaMalloc(&b->map, (map_n ? map_n : 1) * sizeof(int)) || cudaMalloc(&b->moved, ncodes * sizeof(int)) ||
+        cudaMalloc(&b->d_hard, ncodes * sizeof(void *)) || cudaMalloc(&b->d_iters, ncodes * sizeof(void *)) ||
+        cudaMalloc(&b->d_ok, ncodes * sizeof(void *)))
+        return fail("compaction tables");
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+        if (b->sms < 1) b->sms = 1;
+    }
     if (cudaMalloc(&b->shtab, hsh.size() * 4) || cudaMalloc(&b->eotab, heo.size() * 4)) return fail("shift tables");
     if (cudaMalloc(&b->pair_code, pc.size() * 4) || cudaMalloc(&b->pair_pk, pp.size() * 4)) return fail("pairs");
     if (cudaMalloc(&b->counts, 2 * sizeof(int))) return fail("counts");
@@ -837,22 +1090,22 @@ ldpc_status ldpc_batch_create(const ldpc_code *codes, int32_t ncodes, const int3
     b->hw_words = hw_w;
     b->flags_words = fl_w;
     b->iters_total = it_n;
-    if (cudaMemcpy(b->codes, b->hcodes.data(), sizeof(BCode) * ncodes, cudaMemcpyHostToDevice) ||
+    if (cudaMemcpy(b->codes, b->hcodes.data(), sizeof(BCode) * 2 * ncodes, cudaMemcpyHostToDevice) ||
         cudaMemcpy(b->shtab, hsh.data(), hsh.size() * 4, cudaMemcpyHostToDevice) ||
         cudaMemcpy(b->eotab, heo.data(), heo.size() * 4, cudaMemcpyHostToDevice) ||
         cudaMemcpy(b->pair_code, pc.data(), pc.size() * 4, cudaMemcpyHostToDevice) ||
         cudaMemcpy(b->pair_pk, pp.data(), pp.size() * 4, cudaMemcpyHostToDevice))
         return fail("table upload");
     // per-code views: the single-code pack / finish / unpack kernels run on them
-    b->views.reset(new (std::nothrow) ldpc_code_s[ncodes]);
+    b->views.reset(new (std::nothrow) ldpc_code_s[2 * (size_t)ncodes]);
     if (!b->views) return fail("host allocation");
-    b->nviews = ncodes;
-    for (int i = 0; i < ncodes; ++i) {
+    b->nviews = 2 * ncodes;
+    for (int i = 0; i < 2 * ncodes; ++i) {
         ldpc_code_s &v = b->views[i];
         const BCode &bc = b->hcodes[i];
-        v.d = codes[i]->d;
-        v.device = codes[i]->device;
-        v.rate = codes[i]->rate;
+        v.d = codes[i % ncodes]->d;
+        v.device = codes[i % ncodes]->device;
+        v.rate = codes[i % ncodes]->rate;
         v.noms = nullptr;
         v.ws.gamma_cap = (size_t)bc.P * W;
         v.ws.msg = (uint32_t *)b->msg + bc.msg;
@@ -873,6 +1126,7 @@ ldpc_status ldpc_batch_destroy(ldpc_batch b) {
     cudaFree(b->msg); cudaFree(b->mu); cudaFree(b->hw); cudaFree(b->flags); cudaFree(b->iters);
     cudaFree(b->codes); cudaFree(b->shtab); cudaFree(b->eotab); cudaFree(b->pair_code); cudaFree(b->pair_pk);
     cudaFree(b->counts); cudaFree(b->cn_tiles); cudaFree(b->vn_tiles);
+    cudaFree(b->map); cudaFree(b->moved); cudaFree(b->d_hard); cudaFree(b->d_iters); cudaFree(b->d_ok);
     for (int i = 0; i < b->nviews; ++i) b->views[i].ws = DecodeWs();  // borrowed
     delete b;
     return LDPC_OK;
@@ -891,6 +1145,8 @@ static ldpc_status b_prepare(ldpc_batch b, const float *const *llr, cudaStream_t
         if (st != LDPC_OK) return st;
     }
     LDPC_CUDA_TRY(cudaMemsetAsync(b->hw, 0, b->hw_words * 4, s));
+    bsecond_init_kernel<<<b->ncodes, 256, 0, s>>>(b->codes, b->flags, b->moved, b->ncodes, b->V);
+    count_launch();
     b_tiles(b, true, s);
     count_launch();
     LDPC_CUDA_TRY(cudaGetLastError());
@@ -981,6 +1237,33 @@ ldpc_status ldpc_batch_decode(ldpc_batch b, const float *const *llr, uint8_t *co
                                ok ? ok[i] : nullptr, s);
         if (st != LDPC_OK) return st;
     }
+    if (b->o.early_stop && b->K < b->o.max_iter) {
+        // frames moved to the second areas: finish there (a code that moved none has every slot
+        // done and nothing to scatter), then write their rows of the outputs
+        const int W = 32 * b->V;
+        for (int i = 0; i < b->ncodes; ++i) {
+            st = qc_finish(&b->views[b->ncodes + i], b->hcodes[i].P * W, b->o, s);
+            if (st != LDPC_OK) return st;
+        }
+        const size_t pb = (size_t)b->ncodes * sizeof(void *);
+        std::vector<void *> zeros(b->ncodes, nullptr);
+        LDPC_CUDA_TRY(cudaMemcpyAsync(b->d_hard, hard ? (const void *)hard : zeros.data(), pb, cudaMemcpyHostToDevice, s));
+        LDPC_CUDA_TRY(cudaMemcpyAsync(b->d_iters, iters ? (const void *)iters : zeros.data(), pb, cudaMemcpyHostToDevice, s));
+        LDPC_CUDA_TRY(cudaMemcpyAsync(b->d_ok, ok ? (const void *)ok : zeros.data(), pb, cudaMemcpyHostToDevice, s));
+        bscatter_kernel<<<dim3((unsigned)(b->sms * 2), (unsigned)b->ncodes), 256, 0, s>>>(
+            b->codes, b->hw, b->iters, b->map, b->moved, b->ncodes, b->V, b->d_hard, b->d_iters, b->d_ok);
+        count_launch();
+        LDPC_CUDA_TRY(cudaStreamSynchronize(s));  // the host arrays copied above are the caller's
+    }
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_batch_moved(ldpc_batch b, int32_t *moved) {
+    if (!b || !moved) {
+        set_error("need a batch and moved");
+        return LDPC_EINVAL;
+    }
+    LDPC_CUDA_TRY(cudaMemcpy(moved, b->moved, (size_t)b->ncodes * sizeof(int), cudaMemcpyDeviceToHost));
     return LDPC_OK;
 }
 

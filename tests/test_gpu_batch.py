@@ -28,6 +28,7 @@ def batch_vs_single(pkg, specs, opts_kw, seeds, ebn0=2.0):
     gammas = [g for _, _, _, g, _ in specs]
     o = pkg.default_opts(**opts_kw)
     b = pkg.ldpc_batch_create(codes, gammas, o)
+    moved = []
     for seed in seeds:
         llrs = [torch.from_numpy(synth.gaussian_llrs(g, c.N, seed=seed + i, ebn0_db=ebn0, rate=1 - J / L)).cuda()
                 for i, (c, (J, L, p, g, s)) in enumerate(zip(codes, specs))]
@@ -35,11 +36,13 @@ def batch_vs_single(pkg, specs, opts_kw, seeds, ebn0=2.0):
         its = [torch.empty(g, dtype=torch.int32, device="cuda") for g in gammas]
         oks = [torch.empty(g, dtype=torch.int32, device="cuda") for g in gammas]
         pkg.ldpc_batch_decode(b, llrs, hards, its, oks)
+        moved.append(sum(pkg.ldpc_batch_moved(b, len(codes))))
         for c, llr, h, it, ok in zip(codes, llrs, hards, its, oks):
             _, h1, it1, ok1 = c.decode(llr, want_post=False, **{k: v for k, v in opts_kw.items()
                                                                  if k in ("max_iter", "early_stop", "algo", "msg")})
             assert torch.equal(h, h1) and torch.equal(it, it1) and torch.equal(ok, ok1)
     info = pkg.ldpc_batch_info(b)
+    info["moved"] = moved
     pkg.ldpc_batch_destroy(b)
     return codes, info
 
@@ -53,6 +56,19 @@ def test_batch_equals_per_code_decode(pkg, opts_kw):
     # three calls: the tuned eager run, the capture run, a graph replay
     _, info = batch_vs_single(pkg, specs, opts_kw, seeds=[10, 20, 30])
     assert info["tile_rows"] in (16, 64, 256) and all(t > 0 for t in info["tune_ms"])
+    if not (opts_kw.get("early_stop") and opts_kw["max_iter"] > 8):
+        assert not any(info["moved"])  # compaction only with early stop, after iteration 8
+
+
+@pytest.mark.parametrize("opts_kw", [dict(max_iter=25, early_stop=1, msg=0),
+                                     dict(max_iter=25, early_stop=1, msg=1),
+                                     dict(max_iter=25, early_stop=1, algo=1, msg=2)])
+def test_batch_compaction_equals_per_code_decode(pkg, opts_kw):
+    """Frame-level compaction after iteration 8 (FP32, FP16 and int8 storage): the frames still running
+    move to each code's second package area and their results still equal the per-code decoder's."""
+    specs = [(3, 6, 40, 200, 11), (4, 8, 37, 150, 12), (3, 12, 50, 96, 13), (4, 24, 64, 70, 14), (3, 9, 16, 3, 15)]
+    _, info = batch_vs_single(pkg, specs, opts_kw, seeds=[50, 60, 70], ebn0=2.75)
+    assert all(m > 0 for m in info["moved"]), info["moved"]
 
 
 def test_batch_matches_oracle(pkg):
@@ -91,7 +107,10 @@ def test_mixed_64_code_batch(pkg):
         hards = [torch.empty((l.shape[0], c.N), dtype=torch.uint8, device="cuda") for c, l in zip(codes, llrs)]
         its = [torch.empty(l.shape[0], dtype=torch.int32, device="cuda") for l in llrs]
         pkg.ldpc_batch_decode(b, llrs, hards, its, None)
-    for i in range(0, 64, 7):
+    moved = pkg.ldpc_batch_moved(b, 64)
+    assert sum(moved) > 0
+    checked = set(range(0, 64, 7)) | {i for i in range(64) if moved[i]}  # every compacted code too
+    for i in sorted(checked):
         _, h1, it1, _ = codes[i].decode(llrs[i], max_iter=30, early_stop=True, msg=1, want_post=False)
         assert torch.equal(hards[i], h1) and torch.equal(its[i], it1)
     pkg.ldpc_batch_destroy(b)
