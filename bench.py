@@ -612,25 +612,19 @@ def batch_bench(a, pkg, stream) -> dict:
     mean_it = sum(it_sums) / sum(counts)
     # canonical bytes: per frame-iteration 4*E*2 (FP16 messages) + N*4 (channel LLRs) + N/8 (hard bits)
     path_bytes = sum(s_ * (8 * c.E + 4 * c.N + c.N / 8) for c, s_ in zip(codes, it_sums))
-    # bytes the passes stream: a package of 64 FP16 frames is visited, all its lanes, for as many
-    # iterations as its slowest frame runs (early stop per package), padding lanes included
-    visited = 0.0
-    for c, g, t in zip(codes, counts, its):
-        it_np = t.cpu().numpy()
-        for p0 in range(0, g, 64):
-            visited += float(it_np[p0:p0 + 64].max()) * 64 * (8 * c.E + 4 * c.N + c.N / 8)
+
     info = pkg.ldpc_batch_info(b)
     moved = sum(pkg.ldpc_batch_moved(b, len(codes)))
+    comp = pkg.ldpc_batch_compaction(b)
     pkg.ldpc_batch_destroy(b)
     peak = load_peaks().get("hbm_gbs", 6800.0)
     return {"workload": "64 QC codes 3x6..4x24, p 32..765, %d frames total (1..4096 per code), FP16, 30 iters "
                         "early stop, 3.0 dB" % sum(counts),
             "value": info_bits / (ms / 1e3) / 1e6, "unit": "Mbit/s", "ms_per_batch": ms, "mean_iters": mean_it,
             "path_achieved_gbs": path_bytes / (ms / 1e3) / 1e9, "path_frac": path_bytes / (ms / 1e3) / 1e9 / peak,
-            "visited_over_canonical": visited / path_bytes,
-            "visited_frac": visited / (ms / 1e3) / 1e9 / peak,
             "tile_rows": info["tile_rows"], "tile_groups": info["tile_groups"],
-            "frames_compacted": moved}
+            "frames_compacted": moved, "compaction_after_iter": comp["after_iter"],
+            "compaction_tune_ms": comp["tune_ms"]}
 
 
 def sparse_bench(a, pkg, qc, stream) -> dict:

@@ -169,15 +169,16 @@ ldpc_status ldpc_decode_noalloc(ldpc_code code, const float *llr, int32_t gamma,
  * with a shared iteration loop: per iteration one check-pass and one
  * variable-pass launch over the tiles (code, package, row/variable range) of
  * every package that still has a running frame, listed again after each
- * variable pass.  With early stop, after iteration 8 the frames of a code that
+ * variable pass.  With early stop, after iteration K the frames of a code that
  * are still running, when they are at most three quarters of its frames, move
  * densely into a second package area of that code (frame-level compaction), so
  * later iterations visit only their packages; their outputs are written back
  * to their own rows.  The workspace holds both areas.  The loop is captured
  * into a CUDA graph on the second call and replayed afterwards; the first call
  * also tunes the tile sizes by timing three candidates on its frames
- * (ldpc_batch_info reports the choice).  With early stop the call returns once
- * the outputs are written (it synchronizes the stream).
+ * (ldpc_batch_info reports the choice) and, unless set, K among none, 8, 12
+ * and 16 by timing whole decodes (ldpc_batch_compaction).  With compaction in
+ * use the call returns once the outputs are written (it synchronizes the stream).
  *   llr: host array of ncodes device pointers, [gammas[i]][N_i] float each.
  *   hard / iters / ok: host arrays of ncodes device pointers (entries or the
  *   arrays may be NULL): [gammas[i]][N_i] uint8, [gammas[i]] int32, int32.
@@ -192,6 +193,12 @@ ldpc_status ldpc_batch_info(ldpc_batch batch, int32_t *tile_rows, int32_t *tile_
 /* frames of each code the last ldpc_batch_decode moved to its second area (host int32[ncodes]; 0 for
    codes left in place); synchronizes the stream of that decode */
 ldpc_status ldpc_batch_moved(ldpc_batch batch, int32_t *moved);
+/* the compaction point: after_iter >= 1 compacts after that iteration, 0 never, -1 lets the next
+   decode's autotuner choose (the default); resets the captured graph.  Errors: LDPC_EINVAL. */
+ldpc_status ldpc_batch_set_compaction(ldpc_batch batch, int32_t after_iter);
+/* the compaction point in use and the autotuner's whole-decode times (ms) for none, 8, 12, 16
+   (host double[4] or NULL; 0 where a candidate was not timed) */
+ldpc_status ldpc_batch_compaction(ldpc_batch batch, int32_t *after_iter, double *tune_ms4);
 ldpc_status ldpc_batch_destroy(ldpc_batch batch);
 
 /*

@@ -66,6 +66,8 @@ _SIGNATURES = [
     ("ldpc_batch_info", ctypes.c_int, [P, P, P, P]),
     ("ldpc_batch_destroy", ctypes.c_int, [P]),
     ("ldpc_batch_moved", ctypes.c_int, [P, P]),
+    ("ldpc_batch_set_compaction", ctypes.c_int, [P, ctypes.c_int32]),
+    ("ldpc_batch_compaction", ctypes.c_int, [P, P, P]),
     ("ldpc_channel", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, P, P]),
     ("ldpc_ber_sim", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
                                     ctypes.c_int64, ctypes.c_int32, P, P, P]),
@@ -388,6 +390,18 @@ def ldpc_batch_moved(batch: int, ncodes: int) -> list:
     out = (ctypes.c_int32 * ncodes)()
     _check(lib().ldpc_batch_moved(batch, out), "ldpc_batch_moved")
     return list(out)
+
+
+def ldpc_batch_set_compaction(batch: int, after_iter: int):
+    """Compaction after iteration after_iter (0: never, -1: autotuned by the next decode)."""
+    _check(lib().ldpc_batch_set_compaction(batch, int(after_iter)), "ldpc_batch_set_compaction")
+
+
+def ldpc_batch_compaction(batch: int) -> dict:
+    k = ctypes.c_int32(0)
+    ms = (ctypes.c_double * 4)()
+    _check(lib().ldpc_batch_compaction(batch, ctypes.byref(k), ms), "ldpc_batch_compaction")
+    return {"after_iter": k.value, "tune_ms": dict(zip((0, 8, 12, 16), list(ms)))}
 
 
 def ldpc_batch_destroy(batch: int):

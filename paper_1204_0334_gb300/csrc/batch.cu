@@ -851,8 +851,9 @@ struct ldpc_batch_s {
     int *moved = nullptr;   // [ncodes] frames moved by the last decode
     uint8_t **d_hard = nullptr;   // device copies of the caller's output pointer arrays
     int32_t **d_iters = nullptr, **d_ok = nullptr;
-    int K = 8;
+    int K = -1;             // compaction after iteration K (0: never, -1: chosen by the autotuner)
     float limit = 0.75f;
+    double tune_k_ms[4] = {0, 0, 0, 0};  // full-decode times of the compaction candidates
     int sms = 1;
 };
 
@@ -932,7 +933,7 @@ static void b_iteration(ldpc_batch b, int it, cudaStream_t s) {
         b_cn<1, true, false>(b, first, syn, par, s);
         b_vn<1, true, false>(b, syn, it, par, s);
     }
-    if (b->o.early_stop && it == b->K && it < b->o.max_iter) {
+    if (b->o.early_stop && b->K > 0 && it == b->K && it < b->o.max_iter) {
         // frame-level compaction (the tile rebuild below lists the second areas' packages)
         bcompact_plan_kernel<<<b->ncodes, 1024, 0, s>>>(b->codes, b->flags, b->map, b->moved, b->V, b->limit);
         const dim3 grd((unsigned)(b->sms * 2), (unsigned)b->ncodes);
@@ -1180,10 +1181,31 @@ static ldpc_status b_tune(ldpc_batch b, const float *const *llr, cudaStream_t s)
         b->tune_ms[q] = ms;
         if (ms < best) best = ms, bi = q;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     b->TR = cand[bi][0];
     b->TG = cand[bi][1];
+    // the compaction point: whole decodes without it and with it after iterations 8, 12, 16
+    if (b->K < 0) {
+        const int kc[4] = {0, 8, 12, 16};
+        double kbest = 1e30;
+        int kb = 0;
+        for (int q = 0; q < 4; ++q) {
+            if (kc[q] > 0 && (!b->o.early_stop || kc[q] >= b->o.max_iter)) continue;
+            b->K = kc[q];
+            ldpc_status st = b_prepare(b, llr, s);
+            if (st != LDPC_OK) return st;
+            LDPC_CUDA_TRY(cudaEventRecord(e0, s));
+            b_loop(b, b->o.max_iter, s);
+            LDPC_CUDA_TRY(cudaEventRecord(e1, s));
+            LDPC_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            LDPC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            b->tune_k_ms[q] = ms;
+            if (ms < kbest) kbest = ms, kb = kc[q];
+        }
+        b->K = kb;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     b->tuned = true;
     return LDPC_OK;
 }
@@ -1237,7 +1259,7 @@ ldpc_status ldpc_batch_decode(ldpc_batch b, const float *const *llr, uint8_t *co
                                ok ? ok[i] : nullptr, s);
         if (st != LDPC_OK) return st;
     }
-    if (b->o.early_stop && b->K < b->o.max_iter) {
+    if (b->o.early_stop && b->K > 0 && b->K < b->o.max_iter) {
         // frames moved to the second areas: finish there (a code that moved none has every slot
         // done and nothing to scatter), then write their rows of the outputs
         const int W = 32 * b->V;
@@ -1255,6 +1277,20 @@ ldpc_status ldpc_batch_decode(ldpc_batch b, const float *const *llr, uint8_t *co
         count_launch();
         LDPC_CUDA_TRY(cudaStreamSynchronize(s));  // the host arrays copied above are the caller's
     }
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_batch_set_compaction(ldpc_batch b, int32_t after_iter) {
+    if (!b || after_iter < -1) {
+        set_error("need a batch and after_iter >= -1");
+        return LDPC_EINVAL;
+    }
+    b->K = after_iter;
+    if (after_iter < 0) b->tuned = false;  // tuned again by the next decode
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
     return LDPC_OK;
 }
 
@@ -1276,6 +1312,17 @@ ldpc_status ldpc_batch_info(ldpc_batch b, int32_t *tile_rows, int32_t *tile_grou
     if (tile_groups) *tile_groups = b->TG;
     if (tune_ms3)
         for (int q = 0; q < 3; ++q) tune_ms3[q] = b->tune_ms[q];
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_batch_compaction(ldpc_batch b, int32_t *after_iter, double *tune_ms4) {
+    if (!b || !after_iter) {
+        set_error("need a batch and after_iter");
+        return LDPC_EINVAL;
+    }
+    *after_iter = b->K;
+    if (tune_ms4)
+        for (int q = 0; q < 4; ++q) tune_ms4[q] = b->tune_k_ms[q];
     return LDPC_OK;
 }
 

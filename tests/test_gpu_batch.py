@@ -21,13 +21,15 @@ def pkg():
     return p
 
 
-def batch_vs_single(pkg, specs, opts_kw, seeds, ebn0=2.0):
+def batch_vs_single(pkg, specs, opts_kw, seeds, ebn0=2.0, compaction=None):
     """specs: list of (J, L, p, gamma, shift seed).  Runs the batch once per seed and compares every
     code's hard decisions, iteration counts and ok flags with a per-code ldpc_decode."""
     codes = [pkg.QCCode(synth.qc_shifts(J, L, p, seed=s), p) for J, L, p, g, s in specs]
     gammas = [g for _, _, _, g, _ in specs]
     o = pkg.default_opts(**opts_kw)
     b = pkg.ldpc_batch_create(codes, gammas, o)
+    if compaction is not None:
+        pkg.ldpc_batch_set_compaction(b, compaction)
     moved = []
     for seed in seeds:
         llrs = [torch.from_numpy(synth.gaussian_llrs(g, c.N, seed=seed + i, ebn0_db=ebn0, rate=1 - J / L)).cuda()
@@ -56,8 +58,8 @@ def test_batch_equals_per_code_decode(pkg, opts_kw):
     # three calls: the tuned eager run, the capture run, a graph replay
     _, info = batch_vs_single(pkg, specs, opts_kw, seeds=[10, 20, 30])
     assert info["tile_rows"] in (16, 64, 256) and all(t > 0 for t in info["tune_ms"])
-    if not (opts_kw.get("early_stop") and opts_kw["max_iter"] > 8):
-        assert not any(info["moved"])  # compaction only with early stop, after iteration 8
+    if not opts_kw.get("early_stop"):
+        assert not any(info["moved"])  # compaction only with early stop
 
 
 @pytest.mark.parametrize("opts_kw", [dict(max_iter=25, early_stop=1, msg=0),
@@ -67,7 +69,7 @@ def test_batch_compaction_equals_per_code_decode(pkg, opts_kw):
     """Frame-level compaction after iteration 8 (FP32, FP16 and int8 storage): the frames still running
     move to each code's second package area and their results still equal the per-code decoder's."""
     specs = [(3, 6, 40, 200, 11), (4, 8, 37, 150, 12), (3, 12, 50, 96, 13), (4, 24, 64, 70, 14), (3, 9, 16, 3, 15)]
-    _, info = batch_vs_single(pkg, specs, opts_kw, seeds=[50, 60, 70], ebn0=2.75)
+    _, info = batch_vs_single(pkg, specs, opts_kw, seeds=[50, 60, 70], ebn0=2.75, compaction=8)
     assert all(m > 0 for m in info["moved"]), info["moved"]
 
 
@@ -101,6 +103,7 @@ def test_mixed_64_code_batch(pkg):
     codes = [pkg.QCCode(sh, p) for (J, L, p, sh) in mixed]
     o = pkg.default_opts(max_iter=30, early_stop=1, msg=1)
     b = pkg.ldpc_batch_create(codes, [int(g) for g in counts], o)
+    pkg.ldpc_batch_set_compaction(b, 12)
     llrs = [torch.from_numpy(synth.gaussian_llrs(int(g), c.N, seed=100 + i, ebn0_db=3.0, rate=1 - J / L)).cuda()
             for i, (c, (J, L, p, g, s)) in enumerate(zip(codes, specs))]
     for rep in range(2):
