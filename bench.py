@@ -665,12 +665,12 @@ def sparse_bench(a, pkg, qc, stream) -> dict:
 
 
 def e2e(a, pkg, code, stream, opts) -> dict:
-    """Same metric through ldpc_decode with pinned HOST buffers: 8 x slots frames per call (the LLRs of
+    """Same metric through ldpc_decode with pinned HOST buffers: 16 x slots frames per call (the LLRs of
     the call read from host memory, the hard decisions, iteration counts and ok flags written back to
     host memory, inside the timed region; with early stop the frames stream through the slots)."""
     import torch
 
-    gamma = 8 * a.gamma
+    gamma = 16 * a.gamma
     llr_dev = torch.empty((gamma, code.N), dtype=torch.float32, device="cuda")
     pkg.ldpc_channel(code.handle, a.ebn0, a.seed, 3 << 44, llr_dev, stream)
     llr = llr_dev.cpu().pin_memory()

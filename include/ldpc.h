@@ -178,7 +178,8 @@ ldpc_status ldpc_decode_noalloc(ldpc_code code, const float *llr, int32_t gamma,
  * also tunes the tile sizes by timing three candidates on its frames
  * (ldpc_batch_info reports the choice) and, unless set, K among none, 8, 12
  * and 16 by timing whole decodes (ldpc_batch_compaction).  With compaction in
- * use the call returns once the outputs are written (it synchronizes the stream).
+ * use a call first waits until the previous call on the batch has copied its
+ * output pointer arrays.
  *   llr: host array of ncodes device pointers, [gammas[i]][N_i] float each.
  *   hard / iters / ok: host arrays of ncodes device pointers (entries or the
  *   arrays may be NULL): [gammas[i]][N_i] uint8, [gammas[i]] int32, int32.
@@ -437,7 +438,8 @@ ldpc_status ldpc_profile_read(ldpc_profile *out);
  * (one launch each, read + write bytes counted).  One untimed sweep precedes
  * the timed ones; the time comes from CUDA events on `stream`, and
  * *gbs_out = bytes moved / time / 1e9.
- * src, dst: device buffers, 16-byte aligned; bytes a positive multiple of 16.
+ * src, dst: device buffers, 16-byte aligned; bytes a positive multiple of 16;
+ * bytes * reps below 2^38.
  * Synchronizes the stream.  Errors: LDPC_EINVAL, LDPC_ECUDA.
  */
 ldpc_status ldpc_bandwidth_probe(const void *src, void *dst, int64_t bytes, int32_t reps, int32_t mode,

@@ -85,8 +85,13 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
 
     // starts the copies of item it; returns this lane's edge offset (lane l < kBDC: edge l of
     // the row in 32-word packages, -1 if absent)
+    // the message base (words) of each staged item, -1 for an empty item: the compute phase
+    // needs nothing else from the tile and code tables
+    long long gbase[kBStages];
+    long long base_out = -1;  // the base of the item issue() staged last
     auto issue = [&](int it, int slot) -> int {
         int mine = -1;
+        long long base = -1;
         if (it < total) {
             const BTile tl = tiles[it >> sTR];
             const int ri = it & (TR - 1);
@@ -94,6 +99,7 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                 const BCode C = codes[tl.code];
                 const int m = tl.start + ri;
                 const int j = (int)fdiv((uint32_t)m, C.dp), r = m - j * C.p;
+                base = C.msg + (long long)tl.pk * C.E * 32;
                 uint32_t *dst = ring + slot * St::WORDS;
                 const uint32_t *gsrc = FIRST ? mu + C.mu + (size_t)tl.pk * C.N * St::MUW
                                              : msg + C.msg + (size_t)tl.pk * C.E * 32;
@@ -129,26 +135,29 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
             }
         }
         b_commit();
+        base_out = base;
         return mine;
     };
 
     int offr[kBStages];
 #pragma unroll
-    for (int s = 0; s < kBStages - 1; ++s) offr[s] = issue(item + s * GW, s);
+    for (int s = 0; s < kBStages - 1; ++s) {
+        offr[s] = issue(item + s * GW, s);
+        gbase[s] = base_out;
+    }
     int slot = 0;
     for (; item < total; item += GW) {
         offr[kBStages - 1] = issue(item + (kBStages - 1) * GW, (slot + kBStages - 1) % kBStages);
+        gbase[kBStages - 1] = base_out;
         b_wait<kBStages - 1>();
         __syncwarp();
         const int myoff = offr[0];
+        const long long base = gbase[0];
 #pragma unroll
-        for (int s = 0; s < kBStages - 1; ++s) offr[s] = offr[s + 1];
-        const BTile tl = tiles[item >> sTR];
-        const int ri = item & (TR - 1);
-        if (ri < tl.count) {
-            const BCode C = codes[tl.code];
+        for (int s = 0; s < kBStages - 1; ++s) offr[s] = offr[s + 1], gbase[s] = gbase[s + 1];
+        if (base >= 0) {
             const uint32_t *S = ring + slot * St::WORDS;
-            uint32_t *gmsg = msg + C.msg + (size_t)tl.pk * C.E * 32 + lane;
+            uint32_t *gmsg = msg + base + lane;
             bool lane_on = false;
 #pragma unroll
             for (int v = 0; v < V; ++v) lane_on |= ((~S[St::FL + v]) >> lane) & 1u;
@@ -723,12 +732,43 @@ __global__ void bsecond_init_kernel(const BCode *__restrict__ codes, uint32_t *_
     if (threadIdx.x == 0) moved[c] = 0;
 }
 
-// after the finish of the second areas: the moved frames' decisions, iteration counts and ok flags
-// go to their rows of the caller's outputs (pointer arrays per code, entries may be NULL)
+// the syndrome of the moved frames' last decisions (eq. (hrddcs)) into the fin words of the second
+// areas: one thread per (package, row) of the packages holding moved frames
 __global__ void __launch_bounds__(256)
-bscatter_kernel(const BCode *__restrict__ codes, const uint32_t *__restrict__ hw, const int32_t *__restrict__ iters,
-                const int *__restrict__ map, const int *__restrict__ moved, int nc, int V,
-                uint8_t *const *__restrict__ hard, int32_t *const *__restrict__ itout, int32_t *const *__restrict__ okout) {
+bsec_syndrome_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const uint32_t *__restrict__ hw,
+                     uint32_t *__restrict__ flags, const int *__restrict__ moved, int nc, int V) {
+    const int c = blockIdx.y;
+    const int R = moved[c];
+    if (R == 0) return;
+    const BCode B = codes[nc + c];
+    const int W = 32 * V;
+    const long long total = (long long)((R + W - 1) / W) * B.M;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int pk2 = (int)(i / B.M), m = (int)(i % B.M);
+        const int j = (int)fdiv((uint32_t)m, B.dp), r = m - j * B.p;
+        const uint32_t *h = hw + B.hw + (size_t)pk2 * B.N * V;
+        uint32_t syn[4] = {0u, 0u, 0u, 0u};
+        for (int l = 0; l < B.L; ++l) {
+            const int sh = __ldg(shtab + B.tab + j * B.L + l);
+            if (sh < 0) continue;
+            int k = r + sh;
+            if (k >= B.p) k -= B.p;
+            for (int v = 0; v < V; ++v) syn[v] ^= __ldg(h + ((size_t)l * B.p + k) * V + v);
+        }
+        for (int v = 0; v < V; ++v)
+            if (syn[v]) atomicOr(flags + B.flags + (size_t)pk2 * 5 * V + 4 * V + v, syn[v]);
+    }
+}
+
+// the moved frames' decisions, iteration counts (as the frames stopped, else max_iter) and ok flags
+// (last decisions satisfy every check) go to their rows of the caller's outputs (pointer arrays per
+// code, entries may be NULL)
+__global__ void __launch_bounds__(256)
+bscatter_kernel(const BCode *__restrict__ codes, const uint32_t *__restrict__ hw, const uint32_t *__restrict__ flags,
+                const int32_t *__restrict__ iters, const int *__restrict__ map, const int *__restrict__ moved, int nc,
+                int V, int max_iter, uint8_t *const *__restrict__ hard, int32_t *const *__restrict__ itout,
+                int32_t *const *__restrict__ okout) {
     const int c = blockIdx.y;
     const int R = moved[c];
     if (R == 0) return;
@@ -737,11 +777,13 @@ bscatter_kernel(const BCode *__restrict__ codes, const uint32_t *__restrict__ hw
     const int *mp = map + A.map;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t cap = (size_t)B.P * W;  // ok flags follow the iteration counts
     for (long long i = tid; i < R; i += stride) {
         const int f = mp[i];
-        if (itout && itout[c]) itout[c][f] = iters[B.iters + i];
-        if (okout && okout[c]) okout[c][f] = iters[B.iters + cap + i];
+        const int pk2 = (int)i / W, ln = ((int)i % W) / V, v = (int)i % V;
+        const uint32_t *fl = flags + B.flags + (size_t)pk2 * 5 * V;
+        const bool stopped = (fl[v] >> ln) & 1u;
+        if (itout && itout[c]) itout[c][f] = stopped ? iters[B.iters + i] : max_iter;
+        if (okout && okout[c]) okout[c][f] = ((fl[4 * V + v] >> ln) & 1u) ? 0 : 1;
     }
     if (!hard || !hard[c]) return;
     uint8_t *h = hard[c];
@@ -851,6 +893,8 @@ struct ldpc_batch_s {
     int *moved = nullptr;   // [ncodes] frames moved by the last decode
     uint8_t **d_hard = nullptr;   // device copies of the caller's output pointer arrays
     int32_t **d_iters = nullptr, **d_ok = nullptr;
+    void **h_ptrs = nullptr;      // pinned staging of those arrays [3][ncodes]
+    cudaEvent_t ptr_ev = nullptr; // recorded after their copy; waited on before the next overwrite
     int K = -1;             // compaction after iteration K (0: never, -1: chosen by the autotuner)
     float limit = 0.75f;
     double tune_k_ms[4] = {0, 0, 0, 0};  // full-decode times of the compaction candidates
@@ -1075,6 +1119,9 @@ ldpc_status ldpc_batch_create(const ldpc_code *codes, int32_t ncodes, const int3
         cudaMalloc(&b->d_hard, ncodes * sizeof(void *)) || cudaMalloc(&b->d_iters, ncodes * sizeof(void *)) ||
         cudaMalloc(&b->d_ok, ncodes * sizeof(void *)))
         return fail("compaction tables");
+    if (cudaHostAlloc(&b->h_ptrs, 3 * (size_t)ncodes * sizeof(void *), cudaHostAllocDefault) ||
+        cudaEventCreateWithFlags(&b->ptr_ev, cudaEventDisableTiming))
+        return fail("output pointer staging");
     {
         int dev = 0;
         cudaGetDevice(&dev);
@@ -1128,6 +1175,8 @@ ldpc_status ldpc_batch_destroy(ldpc_batch b) {
     cudaFree(b->codes); cudaFree(b->shtab); cudaFree(b->eotab); cudaFree(b->pair_code); cudaFree(b->pair_pk);
     cudaFree(b->counts); cudaFree(b->cn_tiles); cudaFree(b->vn_tiles);
     cudaFree(b->map); cudaFree(b->moved); cudaFree(b->d_hard); cudaFree(b->d_iters); cudaFree(b->d_ok);
+    if (b->h_ptrs) cudaFreeHost(b->h_ptrs);
+    if (b->ptr_ev) cudaEventDestroy(b->ptr_ev);
     for (int i = 0; i < b->nviews; ++i) b->views[i].ws = DecodeWs();  // borrowed
     delete b;
     return LDPC_OK;
@@ -1260,22 +1309,26 @@ ldpc_status ldpc_batch_decode(ldpc_batch b, const float *const *llr, uint8_t *co
         if (st != LDPC_OK) return st;
     }
     if (b->o.early_stop && b->K > 0 && b->K < b->o.max_iter) {
-        // frames moved to the second areas: finish there (a code that moved none has every slot
-        // done and nothing to scatter), then write their rows of the outputs
-        const int W = 32 * b->V;
-        for (int i = 0; i < b->ncodes; ++i) {
-            st = qc_finish(&b->views[b->ncodes + i], b->hcodes[i].P * W, b->o, s);
-            if (st != LDPC_OK) return st;
+        // frames moved to the second areas: the syndrome of their last decisions, then their rows of
+        // the outputs (one launch each over all codes)
+        const int nc = b->ncodes;
+        LDPC_CUDA_TRY(cudaEventSynchronize(b->ptr_ev));  // the previous decode's copy has read h_ptrs
+        for (int i = 0; i < nc; ++i) {
+            b->h_ptrs[i] = hard ? (void *)hard[i] : nullptr;
+            b->h_ptrs[nc + i] = iters ? (void *)iters[i] : nullptr;
+            b->h_ptrs[2 * nc + i] = ok ? (void *)ok[i] : nullptr;
         }
-        const size_t pb = (size_t)b->ncodes * sizeof(void *);
-        std::vector<void *> zeros(b->ncodes, nullptr);
-        LDPC_CUDA_TRY(cudaMemcpyAsync(b->d_hard, hard ? (const void *)hard : zeros.data(), pb, cudaMemcpyHostToDevice, s));
-        LDPC_CUDA_TRY(cudaMemcpyAsync(b->d_iters, iters ? (const void *)iters : zeros.data(), pb, cudaMemcpyHostToDevice, s));
-        LDPC_CUDA_TRY(cudaMemcpyAsync(b->d_ok, ok ? (const void *)ok : zeros.data(), pb, cudaMemcpyHostToDevice, s));
-        bscatter_kernel<<<dim3((unsigned)(b->sms * 2), (unsigned)b->ncodes), 256, 0, s>>>(
-            b->codes, b->hw, b->iters, b->map, b->moved, b->ncodes, b->V, b->d_hard, b->d_iters, b->d_ok);
-        count_launch();
-        LDPC_CUDA_TRY(cudaStreamSynchronize(s));  // the host arrays copied above are the caller's
+        const size_t pb = (size_t)nc * sizeof(void *);
+        LDPC_CUDA_TRY(cudaMemcpyAsync(b->d_hard, b->h_ptrs, pb, cudaMemcpyHostToDevice, s));
+        LDPC_CUDA_TRY(cudaMemcpyAsync(b->d_iters, b->h_ptrs + nc, pb, cudaMemcpyHostToDevice, s));
+        LDPC_CUDA_TRY(cudaMemcpyAsync(b->d_ok, b->h_ptrs + 2 * nc, pb, cudaMemcpyHostToDevice, s));
+        LDPC_CUDA_TRY(cudaEventRecord(b->ptr_ev, s));
+        const dim3 grd((unsigned)(b->sms * 2), (unsigned)nc);
+        bsec_syndrome_kernel<<<grd, 256, 0, s>>>(b->codes, b->shtab, b->hw, b->flags, b->moved, nc, b->V);
+        bscatter_kernel<<<grd, 256, 0, s>>>(b->codes, b->hw, b->flags, b->iters, b->map, b->moved, nc, b->V,
+                                            b->o.max_iter, b->d_hard, b->d_iters, b->d_ok);
+        count_launch(2);
+        LDPC_CUDA_TRY(cudaGetLastError());
     }
     return LDPC_OK;
 }

@@ -132,6 +132,10 @@ ldpc_status ldpc_bandwidth_probe(const void *src, void *dst, int64_t bytes, int3
         set_error("ldpc_bandwidth_probe takes device buffers");
         return LDPC_EINVAL;
     }
+    if ((double)bytes * reps > 0x1p38) {  // keeps one probe to seconds
+        set_error("bytes * reps must stay below 2^38");
+        return LDPC_EINVAL;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     int dev = 0, sms = 1;
     LDPC_CUDA_TRY(cudaGetDevice(&dev));
