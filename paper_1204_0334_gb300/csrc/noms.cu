@@ -59,62 +59,40 @@ __device__ __forceinline__ float nm_beta(const void *src, const QcDesc &d, int p
 // forward check step: alpha^(l) from beta^(l-1); one warp = one row of one package
 // ---------------------------------------------------------------------------
 template <int DCMAX, typename S, bool FROM_MU>
-__global__ void __launch_bounds__(kWarps * 32, 2)  // two blocks of eight warps per SM
+__global__ void __launch_bounds__(kWarps * 32)
 nm_cn_fwd(const QcDesc d, const void *__restrict__ bin, float *__restrict__ A, const float *__restrict__ prm_l,
           float clip, int P) {
-    // persistent warps over items (package, row); the next item's inputs are loaded into registers
-    // before the current item is computed, so the gathers of one overlap the work of the other
     const int lane = threadIdx.x & 31;
-    const int total = P * d.M;  // the host keeps P * M below 2^31
-    const int GW = gridDim.x * kWarps;
-    int item = blockIdx.x * kWarps + (threadIdx.x >> 5);
-    auto load = [&](int it, float *x) {
-        const int pk = (int)fdiv((uint32_t)it, d.divM), m = it - pk * d.M;
-        const int j = (int)fdiv((uint32_t)m, d.divP), r = m - j * d.p;
+    const int m = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int pk = blockIdx.y;
+    if (m >= d.M || pk >= P) return;
+    const int j = (int)fdiv((uint32_t)m, d.divP), r = m - j * d.p;
+    float ab[DCMAX];
+    int eid[DCMAX];
+    uint32_t neg = 0u;
+    float mn1 = INFINITY, mn2 = INFINITY;
 #pragma unroll
-        for (int l = 0; l < DCMAX; ++l) {
-            x[l] = 0.0f;
-            const int sh = l < d.L ? d.shift[j * d.L + l] : -1;
-            if (sh < 0) continue;
-            int k = r + sh;
-            if (k >= d.p) k -= d.p;
-            x[l] = nm_beta<S, FROM_MU>(bin, d, pk, d.eoff[j * d.L + l] + k, l * d.p + k, lane);
-        }
-    };
-    float cur[DCMAX];
-    if (item < total) load(item, cur);
-    for (; item < total; item += GW) {
-        float nxt[DCMAX];
-        if (item + GW < total) load(item + GW, nxt);
-        const int pk = (int)fdiv((uint32_t)item, d.divM), m = item - pk * d.M;
-        const int j = (int)fdiv((uint32_t)m, d.divP), r = m - j * d.p;
-        float ab[DCMAX];
-        uint32_t neg = 0u;
-        float mn1 = INFINITY, mn2 = INFINITY;
+    for (int l = 0; l < DCMAX; ++l) {
+        ab[l] = INFINITY;
+        eid[l] = -1;
+        if (l >= d.L || d.shift[j * d.L + l] < 0) continue;
+        int k = r + d.shift[j * d.L + l];
+        if (k >= d.p) k -= d.p;
+        eid[l] = d.eoff[j * d.L + l] + k;
+        const float x = nm_beta<S, FROM_MU>(bin, d, pk, eid[l], l * d.p + k, lane);
+        ab[l] = fabsf(x);
+        neg |= (x < 0.0f ? 1u : 0u) << l;
+        mn2 = fminf(mn2, fmaxf(mn1, ab[l]));
+        mn1 = fminf(mn1, ab[l]);
+    }
+    const uint32_t par = __popc(neg) & 1u;
+    const float *prm = prm_l + (size_t)j * d.L * 2;
 #pragma unroll
-        for (int l = 0; l < DCMAX; ++l) {
-            ab[l] = INFINITY;
-            if (l >= d.L || d.shift[j * d.L + l] < 0) continue;
-            const float x = cur[l];
-            ab[l] = fabsf(x);
-            neg |= (x < 0.0f ? 1u : 0u) << l;
-            mn2 = fminf(mn2, fmaxf(mn1, ab[l]));
-            mn1 = fminf(mn1, ab[l]);
-        }
-        const uint32_t par = __popc(neg) & 1u;
-        const float *prm = prm_l + (size_t)j * d.L * 2;
-#pragma unroll
-        for (int l = 0; l < DCMAX; ++l) {
-            const int sh = l < d.L ? d.shift[j * d.L + l] : -1;
-            if (sh < 0) continue;
-            int k = r + sh;
-            if (k >= d.p) k -= d.p;
-            const float mv = ab[l] == mn1 ? mn2 : mn1;
-            const float mag = fminf(fmaxf(fmaf(__ldg(prm + 2 * l), mv, -__ldg(prm + 2 * l + 1)), 0.0f), clip);
-            A[((size_t)pk * d.E + d.eoff[j * d.L + l] + k) * 32 + lane] = (par ^ ((neg >> l) & 1u)) ? -mag : mag;
-        }
-#pragma unroll
-        for (int l = 0; l < DCMAX; ++l) cur[l] = nxt[l];
+    for (int l = 0; l < DCMAX; ++l) {
+        if (eid[l] < 0) continue;
+        const float mv = ab[l] == mn1 ? mn2 : mn1;
+        const float mag = fminf(fmaxf(fmaf(__ldg(prm + 2 * l), mv, -__ldg(prm + 2 * l + 1)), 0.0f), clip);
+        A[((size_t)pk * d.E + eid[l]) * 32 + lane] = (par ^ ((neg >> l) & 1u)) ? -mag : mag;
     }
 }
 
@@ -399,14 +377,7 @@ template <typename S>
 static ldpc_status nm_step_fwd(ldpc_code c, ldpc_noms_state &w, int l, const void *bin, bool from_mu, void *bout,
                                bool loss, float *post, cudaStream_t s) {
     const QcDesc &d = c->d;
-    static int cblocks = 0;
-    if (!cblocks) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cblocks = (sms > 0 ? sms : 1) * 2;  // the resident blocks of the check step
-    }
-    const dim3 cg(cblocks), vg((d.N + kWarps - 1) / kWarps, w.P);
+    dim3 cg((d.M + kWarps - 1) / kWarps, w.P), vg((d.N + kWarps - 1) / kWarps, w.P);
     const float *prm = w.params + (size_t)(l - 1) * d.J * d.L * 2;
     const float zinv = (float)(1.0 / ((double)w.T * d.N * w.B));
 #define NM_CN(DC)                                                                                       \
