@@ -63,7 +63,8 @@ typedef struct {
     float clip;                /* SP/NOMS: channel LLRs, messages and posteriors are clipped to
                                   [-clip, clip] (default 30) */
     int32_t frac_bits;         /* MS: q = clamp(rint(mu * 2^frac_bits), -127, 127) (default 2) */
-    const float *noms_params;  /* NOMS: device [max_iter][J*L][2] of (w, o); else NULL */
+    const float *noms_params;  /* NOMS: device [max_iter][J*L][2] of (w, o), 8-byte aligned
+                                  (LDPC_EINVAL otherwise); else NULL */
     int32_t codewords;         /* ldpc_ber_sim only: LDPC_CODEWORDS_ZERO (default) or
                                   LDPC_CODEWORDS_RANDOM; the other calls ignore it */
     int32_t reserved[3];       /* must be zero */
@@ -371,7 +372,9 @@ ldpc_status ldpccc_channel(ldpccc cc, double ebn0_db, uint64_t seed, int64_t fir
 /*
  * Learned normalized/offset min-sum (NOMS).  The paper cites reduced-complexity
  * BP (Sec. II-B) without defining it; this is the parameterized min-sum
- *   alpha_e = sign * max(w_{l,c(e)} * m_e - o_{l,c(e)}, 0),  m_e = min_{e' != e} |beta_e'|
+ *   alpha_e = sign * min(max(w_{l,c(e)} * m_e - o_{l,c(e)}, 0), clip),  m_e = min_{e' != e} |beta_e'|
+ * (every message is clipped at +-clip, as in the other decoders: the clip on alpha
+ * acts only where w * m_e - o > clip, e.g. for w > 1 and saturated inputs)
  * with one (w, o) per iteration l and circulant block c = j*L + l, used with
  * the variable rule of eq. (bpvs) (clipped at +-clip) for T iterations.
  * Inference: ldpc_decode / ldpc_ber_sim with opts.algo = LDPC_ALGO_NOMS and
@@ -380,7 +383,8 @@ ldpc_status ldpccc_channel(ldpccc cc, double ebn0_db, uint64_t seed, int64_t fir
  * ldpc_noms_forward -- training forward pass over B frames:
  *   loss = 1/(T N B) sum over iterations l, bits n, frames of softplus(-post^(l)_n)
  *   (BCE of every iteration's posterior against the all-zero codeword).
- *   llr: device [B][N] float; params: device [T][J*L][2] float (w, o); msg: LDPC_MSG_F32
+ *   llr: device [B][N] float; params: device [T][J*L][2] float (w, o), 8-byte aligned
+ *   (LDPC_EINVAL otherwise); msg: LDPC_MSG_F32
  *   or LDPC_MSG_F16 storage of the saved messages; ckpt_every = k: the messages of every
  *   k-th iteration are kept and the others recomputed in the backward pass;
  *   loss: device float[1]; post: device [B][N] float (post^(T)) or NULL.
@@ -388,8 +392,8 @@ ldpc_status ldpccc_channel(ldpccc cc, double ebn0_db, uint64_t seed, int64_t fir
  * ldpc_noms_backward -- d loss / d params accumulated into grad (device [T][J*L][2],
  *   the caller zeroes it).  Needs the forward of the same params on the same code
  *   object just before.  Reverse mode written out by hand: through the arg-min edge
- *   of each m_e (lowest index among ties), through max(., 0) where positive and
- *   through the clip where inactive.
+ *   of each m_e (lowest index among ties), through min(max(., 0), clip) where that is
+ *   positive and below clip, and through the clip of beta where inactive.
  * Errors: LDPC_EINVAL (sizes, host pointers, backward without forward), LDPC_ENOMEM.
  */
 ldpc_status ldpc_noms_forward(ldpc_code code, const float *llr, int32_t B, int32_t T, const float *params,

@@ -618,7 +618,9 @@ int or_ldpccc_decode(int M, int N, const int *row_ptr, const int *col, int T, in
 /* complexity BP (Sec. II-B); this is the usual parameterized min-sum with a   */
 /* weight w and an offset o per iteration and per circulant block:            */
 /*   beta^(0)_e = clip(mu_v)                                                   */
-/*   alpha^(l)_e = s_e * max(w_{l,c(e)} * m_e - o_{l,c(e)}, 0),               */
+/*   alpha^(l)_e = s_e * min(max(w_{l,c(e)} * m_e - o_{l,c(e)}, 0), clip)     */
+/*        (every message clipped at +-clip, like the other decoders; an empty */
+/*        set of other edges gives m_e = inf, i.e. alpha = s_e * clip),       */
 /*        m_e = min_{e' != e in the row} |beta^(l-1)_e'|,                      */
 /*        s_e = prod_{e' != e} sign(beta^(l-1)_e')   (sign(0) = +)             */
 /*   beta^(l)_e = clip(mu_v + sum_{e' != e in the column} alpha^(l)_e'),       */
@@ -628,7 +630,8 @@ int or_ldpccc_decode(int M, int N, const int *row_ptr, const int *col, int T, in
 /* the circulant index of edge e; params is [T][ncirc][2] = (w, o).           */
 /* The gradient is reverse mode written out by hand: through the arg-min edge */
 /* of each m_e (the lowest index among ties), through max(., 0) where it is   */
-/* positive, and through the clip where |beta| < clip; signs carry none.      */
+/* positive and below clip, and through the clip where |beta| < clip; signs  */
+/* carry none.                                                                */
 /* ------------------------------------------------------------------------ */
 static double or_softplus(double x)
 {
@@ -641,8 +644,8 @@ static double or_sigmoid(double x)
 }
 
 /* CN of one iteration; also returns, per edge, the arg-min edge, m_e, s_e and the active flag */
-static void or_noms_cn(const or_graph *g, const double *beta, const int *cblk, const double *par_l, double *alpha,
-                       int *amin, double *mval, double *sval, int *act)
+static void or_noms_cn(const or_graph *g, const double *beta, const int *cblk, const double *par_l, double clip,
+                       double *alpha, int *amin, double *mval, double *sval, int *act)
 {
     for (int m = 0; m < g->M; ++m) {
         int e0 = g->row_ptr[m], e1 = g->row_ptr[m + 1];
@@ -659,9 +662,9 @@ static void or_noms_cn(const or_graph *g, const double *beta, const int *cblk, c
             double w = par_l[2 * cblk[e]], o = par_l[2 * cblk[e] + 1];
             double z = (arg < 0) ? INFINITY : w * best - o;
             int on = z > 0.0;
-            alpha[e] = on ? s * z : 0.0;
-            if (arg < 0) alpha[e] = s * INFINITY;  /* empty set: the clip below bounds it */
-            amin[e] = arg; mval[e] = best; sval[e] = s; act[e] = on && arg >= 0;
+            alpha[e] = on ? s * (z < clip ? z : clip) : 0.0;
+            /* the gradient passes where alpha = s (w m - o): positive, below the clip */
+            amin[e] = arg; mval[e] = best; sval[e] = s; act[e] = on && arg >= 0 && z < clip;
         }
     }
 }
@@ -687,10 +690,8 @@ void or_round_half_array(const double *x, double *out, int64_t n)
     for (int64_t i = 0; i < n; ++i) out[i] = or_round_half(x[i]);
 }
 
-/* store16: beta is kept as binary16 between iterations (the FP16-message variant); the
-   gradient treats that rounding as the identity, as the clip is treated where inactive. */
 static void or_noms_vn(const or_graph *g, const double *mu, const double *alpha, double clip, double *beta,
-                       double *raw, double *post, int store16)
+                       double *raw, double *post)
 {
     for (int n = 0; n < g->N; ++n) {
         int v0 = g->vptr[n], dv = g->vptr[n + 1] - v0;
@@ -702,7 +703,58 @@ static void or_noms_vn(const or_graph *g, const double *mu, const double *alpha,
             for (int k2 = 0; k2 < dv; ++k2)
                 if (k2 != k) s += alpha[g->vedge[v0 + k2]];
             raw[g->vedge[v0 + k]] = s;
-            beta[g->vedge[v0 + k]] = store16 ? or_round_half(or_clip(s, clip)) : or_clip(s, clip);
+            beta[g->vedge[v0 + k]] = or_clip(s, clip);
+        }
+    }
+}
+
+/* The FP16-message variant's forward (store16).  Rounding a message to binary16 and picking
+   the arg-min of the rounded messages are decisions taken on a floating-point value, so this
+   forward takes them on the value the device computes: binary32 arithmetic, w * m - o as one
+   fused multiply-add, the sums of the variable rule in the column's edge order (increasing
+   check index).  Every input of these steps (binary16 messages, binary32 channel LLRs and
+   parameters) is exact in binary32; results are stored as doubles.  beta is kept as binary16
+   between iterations; the gradient treats that rounding as the identity, as it treats the
+   clip where inactive. */
+static void or_noms_cn_f32(const or_graph *g, const double *beta, const int *cblk, const double *par_l, double clip,
+                           double *alpha, int *amin, double *mval, double *sval, int *act)
+{
+    const float cf = (float)clip;
+    for (int m = 0; m < g->M; ++m) {
+        int e0 = g->row_ptr[m], e1 = g->row_ptr[m + 1];
+        for (int e = e0; e < e1; ++e) {
+            float best = INFINITY;
+            int arg = -1, neg = 0;
+            for (int e2 = e0; e2 < e1; ++e2) {
+                if (e2 == e) continue;
+                float a = fabsf((float)beta[e2]);
+                if (a < best) { best = a; arg = e2; }
+                if (beta[e2] < 0.0) neg ^= 1;
+            }
+            float sg = neg ? -1.0f : 1.0f;
+            float w = (float)par_l[2 * cblk[e]], o = (float)par_l[2 * cblk[e] + 1];
+            float z = (arg < 0) ? INFINITY : fmaf(w, best, -o);
+            int on = z > 0.0f;
+            alpha[e] = on ? (double)(sg * (z < cf ? z : cf)) : 0.0;
+            amin[e] = arg; mval[e] = best; sval[e] = sg; act[e] = on && arg >= 0 && z < cf;
+        }
+    }
+}
+
+static void or_noms_vn_f32(const or_graph *g, const double *mu, const double *alpha, double clip, double *beta,
+                           double *raw, double *post)
+{
+    for (int n = 0; n < g->N; ++n) {
+        int v0 = g->vptr[n], dv = g->vptr[n + 1] - v0;
+        float tot = (float)mu[n];
+        for (int k = 0; k < dv; ++k) tot += (float)alpha[g->vedge[v0 + k]];
+        post[n] = tot;
+        for (int k = 0; k < dv; ++k) {
+            float sm = (float)mu[n];
+            for (int k2 = 0; k2 < dv; ++k2)
+                if (k2 != k) sm += (float)alpha[g->vedge[v0 + k2]];
+            raw[g->vedge[v0 + k]] = sm;
+            beta[g->vedge[v0 + k]] = or_round_half(or_clip(sm, clip));
         }
     }
 }
@@ -711,7 +763,7 @@ static void or_noms_vn(const or_graph *g, const double *mu, const double *alpha,
  * or_noms: forward (and, if grad != NULL, backward) over nfr frames.
  * post_out (nullable) receives post^(T) [nfr][N]; returns the loss.  grad is [T][ncirc][2],
  * accumulated (the caller zeroes it).  store16: the FP16-message variant (beta^(l), l >= 1,
- * rounded to binary16 when stored).
+ * rounded to binary16 when stored; its forward in binary32, see or_noms_cn_f32).
  */
 double or_noms(int M, int N, const int *row_ptr, const int *col, const int *cblk, int nfr, const float *mu_f,
                int T, const double *params, int ncirc, double clip, double *post_out, double *grad, int nthreads,
@@ -738,10 +790,19 @@ double or_noms(int M, int N, const int *row_ptr, const int *col, const int *cblk
         for (int n = 0; n < N; ++n) mu[n] = or_clip((double)mu_f[(size_t)f * N + n], clip);
         for (int e = 0; e < E; ++e) beta[e] = mu[col[e]];
         for (int l = 0; l < T; ++l) {
-            or_noms_cn(&g, beta + (size_t)l * E, cblk, params + (size_t)l * 2 * ncirc, alpha + (size_t)l * E,
-                       amin + (size_t)l * E, mval + (size_t)l * E, sval + (size_t)l * E, act + (size_t)l * E);
-            or_noms_vn(&g, mu, alpha + (size_t)l * E, clip, beta + (size_t)(l + 1) * E, raw + (size_t)(l + 1) * E,
-                       post + (size_t)l * N, store16);
+            if (store16) {
+                or_noms_cn_f32(&g, beta + (size_t)l * E, cblk, params + (size_t)l * 2 * ncirc, clip,
+                               alpha + (size_t)l * E, amin + (size_t)l * E, mval + (size_t)l * E,
+                               sval + (size_t)l * E, act + (size_t)l * E);
+                or_noms_vn_f32(&g, mu, alpha + (size_t)l * E, clip, beta + (size_t)(l + 1) * E,
+                               raw + (size_t)(l + 1) * E, post + (size_t)l * N);
+            } else {
+                or_noms_cn(&g, beta + (size_t)l * E, cblk, params + (size_t)l * 2 * ncirc, clip,
+                           alpha + (size_t)l * E, amin + (size_t)l * E, mval + (size_t)l * E,
+                           sval + (size_t)l * E, act + (size_t)l * E);
+                or_noms_vn(&g, mu, alpha + (size_t)l * E, clip, beta + (size_t)(l + 1) * E,
+                           raw + (size_t)(l + 1) * E, post + (size_t)l * N);
+            }
             for (int n = 0; n < N; ++n) lf += or_softplus(-post[(size_t)l * N + n]);
         }
         if (post_out)

@@ -89,9 +89,13 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
     // needs nothing else from the tile and code tables
     long long gbase[kBStages];
     long long base_out = -1;  // the base of the item issue() staged last
+    // the row degree slot bound (edge slots >= it are absent) of each staged item
+    int gdeg[kBStages];
+    int deg_out = 0;
     auto issue = [&](int it, int slot) -> int {
         int mine = -1;
         long long base = -1;
+        int deg = 0;
         if (it < total) {
             const BTile tl = tiles[it >> sTR];
             const int ri = it & (TR - 1);
@@ -100,6 +104,7 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                 const int m = tl.start + ri;
                 const int j = (int)fdiv((uint32_t)m, C.dp), r = m - j * C.p;
                 base = C.msg + (long long)tl.pk * C.E * 32;
+                deg = C.L;
                 uint32_t *dst = ring + slot * St::WORDS;
                 const uint32_t *gsrc = FIRST ? mu + C.mu + (size_t)tl.pk * C.N * St::MUW
                                              : msg + C.msg + (size_t)tl.pk * C.E * 32;
@@ -136,6 +141,7 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
         }
         b_commit();
         base_out = base;
+        deg_out = deg;
         return mine;
     };
 
@@ -144,17 +150,20 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
     for (int s = 0; s < kBStages - 1; ++s) {
         offr[s] = issue(item + s * GW, s);
         gbase[s] = base_out;
+        gdeg[s] = deg_out;
     }
     int slot = 0;
     for (; item < total; item += GW) {
         offr[kBStages - 1] = issue(item + (kBStages - 1) * GW, (slot + kBStages - 1) % kBStages);
         gbase[kBStages - 1] = base_out;
+        gdeg[kBStages - 1] = deg_out;
         b_wait<kBStages - 1>();
         __syncwarp();
         const int myoff = offr[0];
         const long long base = gbase[0];
+        const int deg = gdeg[0];  // warp-uniform
 #pragma unroll
-        for (int s = 0; s < kBStages - 1; ++s) offr[s] = offr[s + 1], gbase[s] = gbase[s + 1];
+        for (int s = 0; s < kBStages - 1; ++s) offr[s] = offr[s + 1], gbase[s] = gbase[s + 1], gdeg[s] = gdeg[s + 1];
         if (base >= 0) {
             const uint32_t *S = ring + slot * St::WORDS;
             uint32_t *gmsg = msg + base + lane;
@@ -170,7 +179,7 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                 for (int l = 0; l < kBDC; ++l) {
 #pragma unroll
                     for (int v = 0; v < V; ++v) ph[l][v] = 0.0f;
-                    if (__shfl_sync(0xffffffffu, myoff, l) >= 0) {
+                    if (l < deg && __shfl_sync(0xffffffffu, myoff, l) >= 0) {
                         float x[V];
                         if (FIRST) {
                             const float *mf = reinterpret_cast<const float *>(S + l * St::SEGW) + lane * V;
@@ -209,6 +218,8 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                 static_assert(V <= 2 && kBDC % 2 == 0, "pairs of edges or frames");
 #pragma unroll
                 for (int l = kBDC - 1; l >= 0; l -= (V == 1 ? 2 : 1)) {
+                    // slots at or past the row degree hold no edge (phi term 0): nothing to add or emit
+                    if (l - (V == 1 ? 1 : 0) >= deg) continue;
                     float arg[2][V], mag[2][V];
 #pragma unroll
                     for (int h = 0; h < (V == 1 ? 2 : 1); ++h)
@@ -241,7 +252,7 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                 for (int l = 0; l < kBDC; ++l) {
                     ab[l] = 0u;
                     sg[l] = 0u;
-                    if (__shfl_sync(0xffffffffu, myoff, l) >= 0) {
+                    if (l < deg && __shfl_sync(0xffffffffu, myoff, l) >= 0) {
                         const uint32_t x = S[l * St::SEGW + lane];
                         const uint32_t av = __vabsss4(x);
                         sg[l] = x & 0x80808080u;
@@ -253,6 +264,7 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                 }
 #pragma unroll
                 for (int l = 0; l < kBDC; ++l) {
+                    if (l >= deg) break;  // warp-uniform
                     const int o = __shfl_sync(0xffffffffu, myoff, l);
                     if (o < 0) continue;  // warp-uniform
                     const uint32_t eq = __vcmpeq4(ab[l], min1);

@@ -85,8 +85,8 @@ ldpc_status check_opts(const ldpc_code c, const ldpc_decode_opts *o) {
             set_error("normalized/offset min-sum takes F32 or F16 messages");
             return LDPC_EUNSUPPORTED;
         }
-        if (!o->noms_params || pointer_kind(o->noms_params) != 0) {
-            set_error("NOMS needs device noms_params [max_iter][J*L][2]");
+        if (!o->noms_params || pointer_kind(o->noms_params) != 0 || ((uintptr_t)o->noms_params & 7u)) {
+            set_error("NOMS needs device noms_params [max_iter][J*L][2], 8-byte aligned");
             return LDPC_EINVAL;
         }
         if (!(o->clip > 0.0f) || !std::isfinite(o->clip) || o->clip > 60000.0f) {

@@ -1,7 +1,7 @@
 // Learned normalized/offset min-sum (NOMS): forward and backward kernels for
 // training the per-iteration, per-circulant weights and offsets, over T
 // unrolled flooding iterations of Algorithm 1 with the check rule
-//   alpha_e = s_e * max(w_{l,c(e)} * m_e - o_{l,c(e)}, 0),  m_e = min_{e' != e} |beta_e'|,
+//   alpha_e = s_e * min(max(w_{l,c(e)} * m_e - o_{l,c(e)}, 0), clip),  m_e = min_{e' != e} |beta_e'|,
 // the variable rule of eq. (bpvs) with clipping, and the loss
 //   loss = 1/(T N B) sum_l sum_n softplus(-post^(l)_n)
 // (BCE of every iteration's posterior against the all-zero codeword).
@@ -58,7 +58,12 @@ __device__ __forceinline__ float nm_beta(const void *src, const QcDesc &d, int p
 // ---------------------------------------------------------------------------
 // forward check step: alpha^(l) from beta^(l-1); one warp = one row of one package
 // ---------------------------------------------------------------------------
-template <int DCMAX, typename S, bool FROM_MU>
+// REG: every block of the row is present and L == DCMAX, so the gathers carry no branches
+// and all DCMAX loads of a row are in flight together.  Only the two smallest magnitudes,
+// the index of the first smallest and the sign bits outlive the gathers: the other edges'
+// minimum is mn2 for that index and mn1 for every other edge (on a tie mn2 == mn1), and the
+// edge indices are recomputed for the stores.
+template <int DCMAX, typename S, bool FROM_MU, bool REG>
 __global__ void __launch_bounds__(kWarps * 32)
 nm_cn_fwd(const QcDesc d, const void *__restrict__ bin, float *__restrict__ A, const float *__restrict__ prm_l,
           float clip, int P) {
@@ -67,39 +72,49 @@ nm_cn_fwd(const QcDesc d, const void *__restrict__ bin, float *__restrict__ A, c
     const int pk = blockIdx.y;
     if (m >= d.M || pk >= P) return;
     const int j = (int)fdiv((uint32_t)m, d.divP), r = m - j * d.p;
-    float ab[DCMAX];
-    int eid[DCMAX];
+    // (edge, position k in its circulant) of slot l in this row; edge -1: absent block
+    auto edge = [&](int l) -> int2 {
+        const int sh = (REG || l < d.L) ? d.shift[j * d.L + l] : -1;
+        if (!REG && sh < 0) return make_int2(-1, 0);
+        int k = r + sh;
+        if (k >= d.p) k -= d.p;
+        return make_int2(d.eoff[j * d.L + l] + k, k);
+    };
+    float x[DCMAX];
+#pragma unroll
+    for (int l = 0; l < DCMAX; ++l) {
+        const int2 ek = edge(l);
+        x[l] = ek.x < 0 ? INFINITY : nm_beta<S, FROM_MU>(bin, d, pk, ek.x, l * d.p + ek.y, lane);
+    }
     uint32_t neg = 0u;
     float mn1 = INFINITY, mn2 = INFINITY;
+    int i1 = -1;
 #pragma unroll
     for (int l = 0; l < DCMAX; ++l) {
-        ab[l] = INFINITY;
-        eid[l] = -1;
-        if (l >= d.L || d.shift[j * d.L + l] < 0) continue;
-        int k = r + d.shift[j * d.L + l];
-        if (k >= d.p) k -= d.p;
-        eid[l] = d.eoff[j * d.L + l] + k;
-        const float x = nm_beta<S, FROM_MU>(bin, d, pk, eid[l], l * d.p + k, lane);
-        ab[l] = fabsf(x);
-        neg |= (x < 0.0f ? 1u : 0u) << l;
-        mn2 = fminf(mn2, fmaxf(mn1, ab[l]));
-        mn1 = fminf(mn1, ab[l]);
+        const float a = fabsf(x[l]);  // absent edges: +inf, never below mn1
+        neg |= (x[l] < 0.0f ? 1u : 0u) << l;
+        const bool lo = a < mn1;
+        mn2 = lo ? mn1 : fminf(mn2, a);
+        i1 = lo ? l : i1;
+        mn1 = lo ? a : mn1;
     }
     const uint32_t par = __popc(neg) & 1u;
-    const float *prm = prm_l + (size_t)j * d.L * 2;
+    const float2 *prm = reinterpret_cast<const float2 *>(prm_l) + (size_t)j * d.L;
 #pragma unroll
     for (int l = 0; l < DCMAX; ++l) {
-        if (eid[l] < 0) continue;
-        const float mv = ab[l] == mn1 ? mn2 : mn1;
-        const float mag = fminf(fmaxf(fmaf(__ldg(prm + 2 * l), mv, -__ldg(prm + 2 * l + 1)), 0.0f), clip);
-        A[((size_t)pk * d.E + eid[l]) * 32 + lane] = (par ^ ((neg >> l) & 1u)) ? -mag : mag;
+        const int e = edge(l).x;
+        if (!REG && e < 0) continue;
+        const float2 wo = __ldg(prm + l);
+        const float mv = l == i1 ? mn2 : mn1;
+        const float mag = fminf(fmaxf(fmaf(wo.x, mv, -wo.y), 0.0f), clip);
+        A[((size_t)pk * d.E + e) * 32 + lane] = (par ^ ((neg >> l) & 1u)) ? -mag : mag;
     }
 }
 
 // ---------------------------------------------------------------------------
 // forward variable step: beta^(l) (clipped, stored as S), posterior, loss term
 // ---------------------------------------------------------------------------
-template <int JMAX, typename S>
+template <int JMAX, typename S, bool REG>
 __global__ void __launch_bounds__(kWarps * 32)
 nm_vn_fwd(const QcDesc d, const float *__restrict__ A, const float *__restrict__ mu, S *__restrict__ bout,
           double *__restrict__ acc, float *__restrict__ post, float zinv, float clip, int P, int B) {
@@ -118,15 +133,16 @@ nm_vn_fwd(const QcDesc d, const float *__restrict__ A, const float *__restrict__
         for (int j = 0; j < JMAX; ++j) {
             a[j] = 0.0f;
             eid[j] = -1;
-            if (j >= d.J || d.shift[j * d.L + l] < 0) continue;
+            if (!REG && (j >= d.J || d.shift[j * d.L + l] < 0)) continue;
             eid[j] = d.eoff[j * d.L + l] + k;
             a[j] = A[((size_t)pk * d.E + eid[j]) * 32 + lane];
-            tot += a[j];
         }
+#pragma unroll
+        for (int j = 0; j < JMAX; ++j) tot += a[j];
         if (bout) {
 #pragma unroll
             for (int j = 0; j < JMAX; ++j) {
-                if (eid[j] < 0) continue;
+                if (!REG && eid[j] < 0) continue;
                 float s = mv;
 #pragma unroll
                 for (int j2 = 0; j2 < JMAX; ++j2)
@@ -153,7 +169,7 @@ nm_vn_fwd(const QcDesc d, const float *__restrict__ A, const float *__restrict__
 // backward variable step: adjoint of alpha^(l) from the loss at iteration l and
 // the adjoint of beta^(l) (zero at l = T), through the clip
 // ---------------------------------------------------------------------------
-template <int JMAX>
+template <int JMAX, bool REG>
 __global__ void __launch_bounds__(kWarps * 32)
 nm_vn_bwd(const QcDesc d, const float *__restrict__ A, const float *__restrict__ mu, const float *__restrict__ GB,
           float *__restrict__ GA, float zinv, float clip, int P, int B) {
@@ -169,27 +185,29 @@ nm_vn_bwd(const QcDesc d, const float *__restrict__ A, const float *__restrict__
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
         a[j] = 0.0f;
+        gbm[j] = 0.0f;
         eid[j] = -1;
-        if (j >= d.J || d.shift[j * d.L + l] < 0) continue;
+        if (!REG && (j >= d.J || d.shift[j * d.L + l] < 0)) continue;
         eid[j] = d.eoff[j * d.L + l] + k;
         a[j] = A[((size_t)pk * d.E + eid[j]) * 32 + lane];
-        tot += a[j];
+        // adjoint of beta^(l)_e, loaded with alpha (independent of it) and masked below
+        if (GB) gbm[j] = GB[((size_t)pk * d.E + eid[j]) * 32 + lane];
     }
-    // adjoint of beta^(l)_e, masked where the clip was active
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j) tot += a[j];
+    // the adjoint passes the clip only where it was inactive
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
-        gbm[j] = 0.0f;
-        if (eid[j] < 0 || !GB) continue;
         float s = mv;
 #pragma unroll
         for (int j2 = 0; j2 < JMAX; ++j2)
             if (j2 != j) s += a[j2];
-        if (fabsf(s) < clip) gbm[j] = GB[((size_t)pk * d.E + eid[j]) * 32 + lane];
+        if (!(fabsf(s) < clip)) gbm[j] = 0.0f;
     }
     const float dpost = (pk * 32 + lane < B) ? -sigmoidf(-tot) * zinv : 0.0f;
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
-        if (eid[j] < 0) continue;
+        if (!REG && eid[j] < 0) continue;
         float g = dpost;
 #pragma unroll
         for (int j2 = 0; j2 < JMAX; ++j2)
@@ -215,7 +233,7 @@ constexpr int kBwdRows = 16;
 template <int DCMAX, typename S, bool FROM_MU>
 __global__ void __launch_bounds__(kWarps * 32, 3)
 nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict__ GA, const float *__restrict__ prm_l,
-          float *__restrict__ GB, float *__restrict__ grad_l, int P, int want_gb) {
+          float *__restrict__ GB, float *__restrict__ grad_l, float clip, int P, int want_gb) {
     __shared__ float sg[kMaxJ * kMaxL * 2];
     extern __shared__ float s_part[];
     for (int i = threadIdx.x; i < d.J * d.L * 2; i += blockDim.x) sg[i] = 0.0f;
@@ -288,7 +306,9 @@ nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict_
                 const bool first = l == i1;
                 const float mv = first ? mn2 : mn1;
                 const float s = (par ^ ((neg >> l) & 1u)) ? -1.0f : 1.0f;
-                const bool act = (first ? i2 : i1) >= 0 && fmaf(w, mv, -o) > 0.0f;
+                const float z = fmaf(w, mv, -o);
+                // alpha = s (w m - o) only where that is positive and below the clip
+                const bool act = (first ? i2 : i1) >= 0 && z > 0.0f && z < clip;
                 if (act) {
                     const float gs = ga[l] * s;
                     part[(2 * l) * 32 + lane] = fmaf(gs, mv, part[(2 * l) * 32 + lane]);
@@ -373,6 +393,13 @@ static ldpc_status nm_alloc(ldpc_code c, ldpc_noms_state &w, size_t frames, size
     return LDPC_OK;
 }
 
+// every block of the base matrix is present (the REG kernels)
+static bool nm_full(const QcDesc &d) {
+    for (int i = 0; i < d.J * d.L; ++i)
+        if (d.shift[i] < 0) return false;
+    return true;
+}
+
 template <typename S>
 static ldpc_status nm_step_fwd(ldpc_code c, ldpc_noms_state &w, int l, const void *bin, bool from_mu, void *bout,
                                bool loss, float *post, cudaStream_t s) {
@@ -380,10 +407,17 @@ static ldpc_status nm_step_fwd(ldpc_code c, ldpc_noms_state &w, int l, const voi
     dim3 cg((d.M + kWarps - 1) / kWarps, w.P), vg((d.N + kWarps - 1) / kWarps, w.P);
     const float *prm = w.params + (size_t)(l - 1) * d.J * d.L * 2;
     const float zinv = (float)(1.0 / ((double)w.T * d.N * w.B));
-#define NM_CN(DC)                                                                                       \
-    do {                                                                                                \
-        if (from_mu) nm_cn_fwd<DC, S, true><<<cg, kWarps * 32, 0, s>>>(d, bin, w.A, prm, w.clip, w.P);  \
-        else nm_cn_fwd<DC, S, false><<<cg, kWarps * 32, 0, s>>>(d, bin, w.A, prm, w.clip, w.P);         \
+    const bool full = nm_full(d);
+#define NM_CN(DC)                                                                                             \
+    do {                                                                                                      \
+        if (full && d.L == (DC)) {                                                                            \
+            if (from_mu) nm_cn_fwd<DC, S, true, true><<<cg, kWarps * 32, 0, s>>>(d, bin, w.A, prm, w.clip, w.P); \
+            else nm_cn_fwd<DC, S, false, true><<<cg, kWarps * 32, 0, s>>>(d, bin, w.A, prm, w.clip, w.P);        \
+        } else if (from_mu) {                                                                                 \
+            nm_cn_fwd<DC, S, true, false><<<cg, kWarps * 32, 0, s>>>(d, bin, w.A, prm, w.clip, w.P);           \
+        } else {                                                                                              \
+            nm_cn_fwd<DC, S, false, false><<<cg, kWarps * 32, 0, s>>>(d, bin, w.A, prm, w.clip, w.P);          \
+        }                                                                                                     \
     } while (0)
     if (d.L <= 8) NM_CN(8);
     else if (d.L <= 16) NM_CN(16);
@@ -392,12 +426,13 @@ static ldpc_status nm_step_fwd(ldpc_code c, ldpc_noms_state &w, int l, const voi
 #undef NM_CN
     count_launch();
     if (bout || loss || post) {
-        if (d.J <= 4)
-            nm_vn_fwd<4, S><<<vg, kWarps * 32, 0, s>>>(d, w.A, w.mu, (S *)bout, loss ? w.acc : nullptr, post, zinv,
-                                                       w.clip, w.P, w.B);
+        double *acc = loss ? w.acc : nullptr;
+        if (full && d.J == 4)
+            nm_vn_fwd<4, S, true><<<vg, kWarps * 32, 0, s>>>(d, w.A, w.mu, (S *)bout, acc, post, zinv, w.clip, w.P, w.B);
+        else if (d.J <= 4)
+            nm_vn_fwd<4, S, false><<<vg, kWarps * 32, 0, s>>>(d, w.A, w.mu, (S *)bout, acc, post, zinv, w.clip, w.P, w.B);
         else
-            nm_vn_fwd<8, S><<<vg, kWarps * 32, 0, s>>>(d, w.A, w.mu, (S *)bout, loss ? w.acc : nullptr, post, zinv,
-                                                       w.clip, w.P, w.B);
+            nm_vn_fwd<8, S, false><<<vg, kWarps * 32, 0, s>>>(d, w.A, w.mu, (S *)bout, acc, post, zinv, w.clip, w.P, w.B);
         count_launch();
     }
     LDPC_CUDA_TRY(cudaGetLastError());
@@ -441,6 +476,7 @@ static ldpc_status nm_backward(ldpc_code c, ldpc_noms_state &w, float *grad, cud
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int cb_blocks = std::max(1, sms * 3);  // three resident blocks per SM
     const float zinv = (float)(1.0 / ((double)w.T * d.N * w.B));
+    const bool full = nm_full(d);
     int seg_base = -1;  // iterations seg_base+1 .. seg_base+k-1 recomputed into seg
     for (int l = w.T; l >= 1; --l) {
         // beta^(l-1): mu, a checkpoint, or a recomputed member of its segment
@@ -471,29 +507,34 @@ static ldpc_status nm_backward(ldpc_code c, ldpc_noms_state &w, float *grad, cud
         // alpha^(l), then the adjoints
         ldpc_status st = nm_step_fwd<S>(c, w, l, bin, from_mu, nullptr, false, nullptr, s);
         if (st != LDPC_OK) return st;
-        if (d.J <= 4)
-            nm_vn_bwd<4><<<vg, kWarps * 32, 0, s>>>(d, w.A, w.mu, l == w.T ? nullptr : w.GB, w.GA, zinv, w.clip, w.P, w.B);
+        const float *gbin = l == w.T ? nullptr : w.GB;
+        if (full && d.J == 4)
+            nm_vn_bwd<4, true><<<vg, kWarps * 32, 0, s>>>(d, w.A, w.mu, gbin, w.GA, zinv, w.clip, w.P, w.B);
+        else if (d.J <= 4)
+            nm_vn_bwd<4, false><<<vg, kWarps * 32, 0, s>>>(d, w.A, w.mu, gbin, w.GA, zinv, w.clip, w.P, w.B);
         else
-            nm_vn_bwd<8><<<vg, kWarps * 32, 0, s>>>(d, w.A, w.mu, l == w.T ? nullptr : w.GB, w.GA, zinv, w.clip, w.P, w.B);
+            nm_vn_bwd<8, false><<<vg, kWarps * 32, 0, s>>>(d, w.A, w.mu, gbin, w.GA, zinv, w.clip, w.P, w.B);
         const float *prm = w.params + (size_t)(l - 1) * d.J * d.L * 2;
         float *gl = grad + (size_t)(l - 1) * d.J * d.L * 2;
         const int want_gb = l > 1;
-#define NM_CB(DC)                                                                                                  \
-    do {                                                                                                           \
-        const size_t psm = (size_t)kWarps * (DC) * 2 * 32 * sizeof(float);                                        \
-        if (from_mu) {                                                                                             \
-            cudaFuncSetAttribute(nm_cn_bwd<DC, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);    \
-            nm_cn_bwd<DC, S, true><<<cb_blocks, kWarps * 32, psm, s>>>(d, bin, w.GA, prm, w.GB, gl, w.P, want_gb);  \
-        } else {                                                                                                   \
-            cudaFuncSetAttribute(nm_cn_bwd<DC, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);   \
-            nm_cn_bwd<DC, S, false><<<cb_blocks, kWarps * 32, psm, s>>>(d, bin, w.GA, prm, w.GB, gl, w.P, want_gb); \
-        }                                                                                                          \
+#define NM_CB1(DC, FM)                                                                                      \
+    do {                                                                                                    \
+        const size_t psm = (size_t)kWarps * (DC) * 2 * 32 * sizeof(float);                                 \
+        auto kfn = nm_cn_bwd<DC, S, FM>;                                                                    \
+        cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);                   \
+        kfn<<<cb_blocks, kWarps * 32, psm, s>>>(d, bin, w.GA, prm, w.GB, gl, w.clip, w.P, want_gb);         \
+    } while (0)
+#define NM_CB(DC)                     \
+    do {                              \
+        if (from_mu) NM_CB1(DC, true); \
+        else NM_CB1(DC, false);       \
     } while (0)
         if (d.L <= 8) NM_CB(8);
         else if (d.L <= 16) NM_CB(16);
         else if (d.L <= 24) NM_CB(24);
         else NM_CB(32);
 #undef NM_CB
+#undef NM_CB1
         count_launch(2);
         LDPC_CUDA_TRY(cudaGetLastError());
     }
@@ -513,8 +554,9 @@ extern "C" {
 ldpc_status ldpc_noms_forward(ldpc_code c, const float *llr, int32_t B, int32_t T, const float *params, int32_t msg,
                               int32_t ckpt_every, float clip, float *loss, float *post, void *stream) {
     if (!c || !llr || B < 1 || T < 1 || !params || !loss || ckpt_every < 1 || !(clip > 0.0f) || clip > 60000.0f ||
-        (msg != LDPC_MSG_F32 && msg != LDPC_MSG_F16)) {
-        set_error("need code, llr, B >= 1, T >= 1, params, loss, ckpt_every >= 1, 0 < clip <= 60000, F32/F16");
+        (msg != LDPC_MSG_F32 && msg != LDPC_MSG_F16) || ((uintptr_t)params & 7u)) {
+        set_error("need code, llr, B >= 1, T >= 1, params (8-byte aligned), loss, ckpt_every >= 1, 0 < clip <= 60000, "
+                  "F32/F16");
         return LDPC_EINVAL;
     }
     if (pointer_kind(llr) != 0 || pointer_kind(params) != 0 || pointer_kind(loss) != 0 ||

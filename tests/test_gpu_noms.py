@@ -54,13 +54,19 @@ def test_noms_inference_matches_oracle(pkg):
     assert np.array_equal(hard.cpu().numpy()[sure], (po < 0)[sure])
 
 
+# rows of 6 edges (padded to 8: the general kernels) and full rows of 8 and 24 edges (the kernels
+# for codes whose base matrix has no zero block and whose row degree fills the template)
+SHAPES = [(3, 6, 32), (4, 8, 16), (4, 24, 11)]
+
+
+@pytest.mark.parametrize("J,L,p", SHAPES)
 @pytest.mark.parametrize("msg,ckpt", [(0, 1), (0, 3)])
-def test_noms_loss_and_gradient_match_oracle(pkg, msg, ckpt):
-    shifts, rp, col, cb = setup(3, 6, 32, 2)
-    code = pkg.QCCode(shifts, 32)
+def test_noms_loss_and_gradient_match_oracle(pkg, msg, ckpt, J, L, p):
+    shifts, rp, col, cb = setup(J, L, p, 2)
+    code = pkg.QCCode(shifts, p)
     T, B = 5, 70
-    prm = rand_params(T, 18, 3)
-    mu = synth.gaussian_llrs(B, code.N, seed=5, ebn0_db=1.5, rate=0.5)
+    prm = rand_params(T, J * L, 3)
+    mu = synth.gaussian_llrs(B, code.N, seed=5, ebn0_db=1.5 + 0.5 * (L > 8), rate=1 - J / L)
     prm_d = torch.from_numpy(prm).cuda()
     loss, post = pkg.ldpc_noms_forward(code.handle, torch.from_numpy(mu).cuda(), prm_d, msg, ckpt, 30.0, True)
     grad = torch.zeros_like(prm_d)
@@ -94,15 +100,17 @@ def test_noms_checkpointing_does_not_change_gradients(pkg):
         assert np.allclose(gk, out[0][1], rtol=1e-5, atol=1e-6 * np.abs(out[0][1]).max())
 
 
-def test_noms_fp16_storage_gradient(pkg):
+@pytest.mark.parametrize("J,L,p", SHAPES)
+def test_noms_fp16_storage_gradient(pkg, J, L, p):
     """FP16 storage of the saved messages against the oracle of the same variant (the stored beta rounded
-    to binary16): loss and gradient element by element.  Against the unrounded FP64 oracle the min-sum
+    to binary16, its forward in binary32 so that both sides round the same values and pick the same
+    arg-min edges): loss and gradient element by element.  Against the unrounded FP64 oracle the min-sum
     gradient jumps wherever rounding changes the arg-min edge, so that comparison is not element-wise."""
-    shifts, rp, col, cb = setup(3, 6, 32, 2)
-    code = pkg.QCCode(shifts, 32)
+    shifts, rp, col, cb = setup(J, L, p, 2)
+    code = pkg.QCCode(shifts, p)
     T, B = 5, 64
-    prm = rand_params(T, 18, 4)
-    mu = synth.gaussian_llrs(B, code.N, seed=6, ebn0_db=1.5, rate=0.5)
+    prm = rand_params(T, J * L, 4)
+    mu = synth.gaussian_llrs(B, code.N, seed=6, ebn0_db=1.5 + 0.5 * (L > 8), rate=1 - J / L)
     prm_d = torch.from_numpy(prm).cuda()
     loss, _ = pkg.ldpc_noms_forward(code.handle, torch.from_numpy(mu).cuda(), prm_d, pkg.MSG_F16, 2, 30.0)
     grad = torch.zeros_like(prm_d)
@@ -114,6 +122,53 @@ def test_noms_fp16_storage_gradient(pkg):
     rel = np.abs(g - go) / np.maximum(np.abs(go), 1e-3 * np.abs(go).max())
     print(f"FP16 gradient: largest element-wise relative deviation {rel.max():.2e}")
     assert rel.max() <= 1e-3, rel.max()
+
+
+@pytest.mark.parametrize("msg", [0, 1])
+def test_noms_gradient_with_clipped_check_messages(pkg, msg):
+    """Weights above 1 and a low clip: w * m - o often exceeds the clip, so alpha is clipped and its
+    gradient is zero there.  Loss, posteriors and the gradient against the oracle (FP16 storage
+    against its binary16 variant), element by element."""
+    J, L, p = 4, 8, 16
+    shifts, rp, col, cb = setup(J, L, p, 5)
+    code = pkg.QCCode(shifts, p)
+    T, B, clip = 4, 64, 6.0
+    rng = np.random.default_rng(11)
+    prm = np.stack([rng.uniform(1.0, 1.6, (T, J * L)), rng.uniform(0.0, 0.3, (T, J * L))], axis=-1).astype(
+        np.float32)
+    mu = synth.gaussian_llrs(B, code.N, seed=12, ebn0_db=3.0, rate=0.5)
+    prm_d = torch.from_numpy(prm).cuda()
+    loss, post = pkg.ldpc_noms_forward(code.handle, torch.from_numpy(mu).cuda(), prm_d, msg, 2, clip, True)
+    grad = torch.zeros_like(prm_d)
+    pkg.ldpc_noms_backward(code.handle, prm_d, grad)
+    lo, po, go = oracle.noms(rp, col, cb, code.N, mu, T, prm.astype(np.float64), clip=clip, want_grad=True,
+                             nthreads=8, store16=bool(msg))
+    assert abs(float(loss) - lo) <= 1e-5 * abs(lo)
+    assert np.max(np.abs(post.cpu().numpy() - po) / np.maximum(1, np.abs(po))) < 1e-4
+    # the messages saturate (a posterior of at least 2 * clip needs several inputs at the clip, and with
+    # w > 1 and inputs at the clip w * m - o exceeds it)
+    assert np.mean(np.abs(po) >= 2 * clip) > 0.1
+    g = grad.cpu().numpy().astype(np.float64)
+    rel = np.abs(g - go) / np.maximum(np.abs(go), 1e-3 * np.abs(go).max())
+    assert rel.max() <= 1e-3, rel.max()
+
+
+def test_parameters_must_be_8_byte_aligned(pkg):
+    """The kernels read (w, o) as pairs: a parameter pointer 4 bytes past an 8-byte boundary is refused
+    before any launch, for training and for inference."""
+    code = pkg.QCCode(synth.qc_shifts(3, 6, 8, seed=1), 8)
+    store = torch.ones(3 * 18 * 2 + 1, device="cuda")
+    prm = store[1:].view(3, 18, 2)
+    assert prm.data_ptr() % 8 == 4
+    llr = torch.from_numpy(synth.gaussian_llrs(32, code.N, seed=1, ebn0_db=2.0, rate=0.5)).cuda()
+    with pytest.raises(pkg.LdpcError):
+        pkg.ldpc_noms_forward(code.handle, llr, prm, 0, 1, 30.0)
+    o = pkg.default_opts(max_iter=3, algo=pkg.ALGO_NOMS, msg=pkg.MSG_F32)
+    o.noms_params = prm.data_ptr()
+    post = torch.empty((32, code.N), device="cuda")
+    hard = torch.empty((32, code.N), dtype=torch.uint8, device="cuda")
+    with pytest.raises(pkg.LdpcError):
+        pkg.ldpc_decode(code.handle, llr, o, post, hard)
 
 
 def test_backward_requires_forward(pkg):

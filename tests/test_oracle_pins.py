@@ -570,6 +570,42 @@ def test_noms_fp16_variant_rounds_stored_messages():
     assert not np.array_equal(c[1], e[1]) and np.allclose(c[1], e[1], atol=2e-3)
 
 
+def test_noms_check_messages_are_clipped():
+    """With w > 1 a saturated input can push w * m - o past the clip: alpha is clipped at +-clip like
+    every other message, and the gradient of a clipped alpha is zero.  One check of degree 3, each edge
+    its own circulant, (w, o) = (1.5, 1), clip 30, one iteration; by hand:
+      e0: others (30, -25): m = 25, sign -, 1.5*25 - 1 = 36.5 -> clipped to 30 -> post 20 - 30 = -10
+      e1: others (20, -25): m = 20, sign -, 1.5*20 - 1 = 29                    -> post 30 - 29 = 1
+      e2: others (20, 30):  m = 20, sign +, 29                                 -> post -25 + 29 = 4
+    (without the clip e0 would end at -16.5).  loss = mean softplus(-post); d loss / d (w, o) of edge
+    e1 = (1/3) sigmoid(-post) * (-d post / d (w, o)), with d post1 / d w1 = -20, d post1 / d o1 = +1;
+    edge e0's circulant gets none; a central difference of the loss agrees."""
+    rp = np.array([0, 3], dtype=np.int32)
+    col = np.arange(3, dtype=np.int32)
+    cb = np.arange(3, dtype=np.int32)
+    mu = np.array([[20.0, 30.0, -25.0]], dtype=np.float32)
+    params = np.tile(np.array([1.5, 1.0]), (1, 3, 1))
+    loss, post, grad = oracle.noms(rp, col, cb, 3, mu, 1, params, want_grad=True, clip=30.0)
+    want = np.array([-10.0, 1.0, 4.0])
+    assert np.allclose(post[0], want, rtol=0, atol=1e-12), post
+    assert abs(loss - np.mean(np.log1p(np.exp(-want)))) <= 1e-12
+    sig = lambda x: 1.0 / (1.0 + np.exp(-x))
+    assert np.allclose(grad[0, 0], 0.0, atol=1e-15), grad
+    assert abs(grad[0, 1, 0] - sig(-1.0) * 20.0 / 3.0) <= 1e-12, grad
+    assert abs(grad[0, 1, 1] - (-sig(-1.0) / 3.0)) <= 1e-12, grad
+    # e2's alpha feeds post2 = 4: d post2 / d w2 = +20, d post2 / d o2 = -1
+    assert abs(grad[0, 2, 0] - (-sig(-4.0) * 20.0 / 3.0)) <= 1e-12, grad
+    h = 1e-6
+    for c in range(3):
+        for k in range(2):
+            pp, pm = params.copy(), params.copy()
+            pp[0, c, k] += h
+            pm[0, c, k] -= h
+            fd = (oracle.noms(rp, col, cb, 3, mu, 1, pp, clip=30.0)[0]
+                  - oracle.noms(rp, col, cb, 3, mu, 1, pm, clip=30.0)[0]) / (2 * h)
+            assert abs(fd - grad[0, c, k]) <= 1e-7, (c, k, fd, grad[0, c, k])
+
+
 def test_noms_gradient_matches_finite_differences():
     """Hand-written reverse mode against central differences of the FP64 loss (away from ties and kinks)."""
     H, rp, col, cb = _qc(3, 6, 8, 5)
