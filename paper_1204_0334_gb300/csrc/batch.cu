@@ -39,6 +39,13 @@ struct BTile {
     int code, pk, start, count;
 };
 
+static_assert(sizeof(BTile) == 16, "one 16-byte load per tile");
+// tile i of a list the pass only reads (the list is 16-byte aligned)
+__device__ __forceinline__ BTile b_tile(const BTile *tiles, int i) {
+    const int4 t = __ldg(reinterpret_cast<const int4 *>(tiles) + i);
+    return BTile{t.x, t.y, t.z, t.w};
+}
+
 constexpr int kBStages = 3;
 constexpr int kBDC = 24;  // largest row degree of a batch
 constexpr int kBJ = 4;    // largest column degree of a batch
@@ -92,12 +99,16 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
     // the row degree slot bound (edge slots >= it are absent) of each staged item
     int gdeg[kBStages];
     int deg_out = 0;
+    // the tile of the next item this warp stages, loaded one item ahead (items are staged in
+    // order it, it + GW, ...), so that staging waits on the code tables only
+    BTile tl_next = item < total ? b_tile(tiles, item >> sTR) : BTile{0, 0, 0, 0};
     auto issue = [&](int it, int slot) -> int {
         int mine = -1;
         long long base = -1;
         int deg = 0;
+        const BTile tl = tl_next;
+        if (it + GW < total) tl_next = b_tile(tiles, (it + GW) >> sTR);
         if (it < total) {
-            const BTile tl = tiles[it >> sTR];
             const int ri = it & (TR - 1);
             if (ri < tl.count) {
                 const BCode C = codes[tl.code];
@@ -218,8 +229,6 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                 static_assert(V <= 2 && kBDC % 2 == 0, "pairs of edges or frames");
 #pragma unroll
                 for (int l = kBDC - 1; l >= 0; l -= (V == 1 ? 2 : 1)) {
-                    // slots at or past the row degree hold no edge (phi term 0): nothing to add or emit
-                    if (l - (V == 1 ? 1 : 0) >= deg) continue;
                     float arg[2][V], mag[2][V];
 #pragma unroll
                     for (int h = 0; h < (V == 1 ? 2 : 1); ++h)
@@ -348,7 +357,11 @@ struct BVnStage {
     static constexpr int AL = kBNV * MUW;
     static constexpr int HW = AL + kBNV * kBJ * 32;
     static constexpr int FL = HW + kBNV * V;
-    static constexpr int WORDS = (FL + 2 * V + 3) & ~3;
+    // what the compute phase needs of the item's tile and code, written by lane 0 when the item
+    // is staged: variable group g (-1: empty item), N, then the message, decision-word, flag and
+    // iteration-count bases of the item's package (8-byte aligned)
+    static constexpr int META = (FL + 2 * V + 1) & ~1;
+    static constexpr int WORDS = (META + 2 + 8 + 3) & ~3;
 };
 
 template <int V, bool STOP, bool XF, bool MS>
@@ -371,16 +384,29 @@ bvn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
 
     // starts the copies of item itm; returns this lane's edge offset (lane t < kBNV * kBJ:
     // edge (variable t / kBJ, block row t % kBJ) of the item, -1 if absent)
+    // the tile of the next item this warp stages, loaded one item ahead
+    BTile tl_next = item < total ? b_tile(tiles, item >> sTG) : BTile{0, 0, 0, 0};
     auto issue = [&](int itm, int slot) -> int {
         int mine = -1;
+        uint32_t *dst = ring + slot * St::WORDS;
+        int g_meta = -1;
+        const BTile tl = tl_next;
+        if (itm + GW < total) tl_next = b_tile(tiles, (itm + GW) >> sTG);
         if (itm < total) {
-            const BTile tl = tiles[itm >> sTG];
             const int gi = itm & (TG - 1);
             if (gi < tl.count) {
                 const BCode C = codes[tl.code];
+                g_meta = tl.start + gi;
+                if (lane == 0) {
+                    dst[St::META + 1] = (uint32_t)C.N;
+                    long long *mb = reinterpret_cast<long long *>(dst + St::META + 2);
+                    mb[0] = C.msg + (long long)tl.pk * C.E * 32;
+                    mb[1] = C.hw + (long long)tl.pk * C.N * V;
+                    mb[2] = C.flags + (long long)tl.pk * 5 * V;
+                    mb[3] = C.iters + (long long)tl.pk * W;
+                }
                 const int n0 = (tl.start + gi) * kBNV;
                 const int l0 = (int)fdiv((uint32_t)n0, C.dp), k0 = n0 - l0 * C.p;
-                uint32_t *dst = ring + slot * St::WORDS;
                 const uint32_t *gmsg = msg + C.msg + (size_t)tl.pk * C.E * 32;
                 const uint32_t *gmu = mu + C.mu + (size_t)tl.pk * C.N * St::MUW;
                 const int grp = lane >> 3, sub = lane & 7;
@@ -425,6 +451,7 @@ bvn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                 }
             }
         }
+        if (lane == 0) dst[St::META] = (uint32_t)g_meta;
         b_commit();
         return mine;
     };
@@ -440,14 +467,13 @@ bvn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
         const int myoff = offr[0];
 #pragma unroll
         for (int s = 0; s < kBStages - 1; ++s) offr[s] = offr[s + 1];
-        const BTile tl = tiles[item >> sTG];
-        const int gi = item & (TG - 1);
-        if (gi < tl.count) {
-            const BCode C = codes[tl.code];
-            const uint32_t *S = ring + slot * St::WORDS;
-            const int pk = tl.pk;
-            const int g = tl.start + gi;
-            uint32_t *gmsg = msg + C.msg + (size_t)pk * C.E * 32 + lane;
+        const uint32_t *S = ring + slot * St::WORDS;
+        const int g = (int)S[St::META];  // warp-uniform
+        if (g >= 0) {
+            const int CN = (int)S[St::META + 1];
+            const long long *mb = reinterpret_cast<const long long *>(S + St::META + 2);
+            const long long msg_b = mb[0], hw_b = mb[1], fl_b = mb[2], it_b = mb[3];
+            uint32_t *gmsg = msg + msg_b + lane;
             uint32_t frozen[V];
             bool lane_on = false;
 #pragma unroll
@@ -456,12 +482,12 @@ bvn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                 if (STOP) {
                     const uint32_t newly = ~dn & ~S[St::FL + V + v];
                     if (g == 0 && lane == 0) {
-                        uint32_t *F = flags + C.flags + (size_t)pk * 5 * V;
+                        uint32_t *F = flags + fl_b;
                         if (newly) {
                             F[v] = dn | newly;
                             for (uint32_t b = newly; b; b &= b - 1) {
                                 const int ln = __ffs(b) - 1;
-                                iters[C.iters + (size_t)pk * W + ln * V + v] = it - 1;
+                                iters[it_b + ln * V + v] = it - 1;
                             }
                         }
                         F[(1 + (par ^ 1)) * V + v] = 0u;
@@ -475,7 +501,7 @@ bvn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
 #pragma unroll
             for (int i = 0; i < kBNV; ++i) {
                 const int n = n0 + i;
-                if (n >= C.N) break;
+                if (n >= CN) break;
                 int eo[kBJ];  // the item's edge offsets, -1 absent (warp-uniform)
 #pragma unroll
                 for (int jj = 0; jj < kBJ; ++jj) eo[jj] = __shfl_sync(0xffffffffu, myoff, i * kBJ + jj);
@@ -570,7 +596,7 @@ bvn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
                         const uint32_t old = S[St::HW + i * V + v];
-                        hw[C.hw + ((size_t)pk * C.N + n) * V + v] = (outb[v] & ~frozen[v]) | (old & frozen[v]);
+                        hw[hw_b + (size_t)n * V + v] = (outb[v] & ~frozen[v]) | (old & frozen[v]);
                     }
                 }
             }

@@ -223,17 +223,24 @@ nm_vn_bwd(const QcDesc d, const float *__restrict__ A, const float *__restrict__
 // two smallest inputs of a row receive gradient.  Persistent warps take items of
 // kBwdRows consecutive rows of one block row j, so every row of an item adds to
 // the same circulants' gradients: each lane keeps its partial sums per edge slot
-// in registers and the warp reduces them once per item (not once per row) into
-// block sums in shared memory, flushed once per block.
+// in the warp's slice of dynamic shared memory ([DCMAX][2][32] floats, so that
+// three blocks fit per SM) and the warp reduces them once per item (not once per
+// row) into block sums in shared memory, flushed once per block.  Lane l holds
+// slot l's shift and edge offset; a row's edge indices are computed once per row
+// (one per lane) and broadcast by shuffles.  REG: every block of the row is
+// present and L == DCMAX (no branches on absent slots).
 // ---------------------------------------------------------------------------
 constexpr int kBwdRows = 16;
+#ifndef LDPC_NM_BWD_BLOCKS
+#define LDPC_NM_BWD_BLOCKS 3
+#endif
+constexpr int kBwdBlocks = LDPC_NM_BWD_BLOCKS;  // resident blocks per SM of the backward check step
 
-// The lanes' partial gradients per edge slot live in the warp's slice of dynamic shared
-// memory ([DCMAX][2][32] floats) rather than in registers, so that three blocks fit per SM.
-template <int DCMAX, typename S, bool FROM_MU>
-__global__ void __launch_bounds__(kWarps * 32, 3)
+template <int DCMAX, typename S, bool FROM_MU, bool REG>
+__global__ void __launch_bounds__(kWarps * 32, kBwdBlocks)
 nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict__ GA, const float *__restrict__ prm_l,
           float *__restrict__ GB, float *__restrict__ grad_l, float clip, int P, int want_gb) {
+    static_assert(DCMAX <= 32, "one lane per edge slot");
     __shared__ float sg[kMaxJ * kMaxL * 2];
     extern __shared__ float s_part[];
     for (int i = threadIdx.x; i < d.J * d.L * 2; i += blockDim.x) sg[i] = 0.0f;
@@ -247,94 +254,88 @@ nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict_
         const int rem = (int)(item - (long long)pk * d.J * chunks);
         const int j = rem / chunks, r0 = (rem - j * chunks) * kBwdRows;
         const int r1 = min(r0 + kBwdRows, d.p);
-        const float *prm = prm_l + (size_t)j * d.L * 2;
+        const float2 *prm = reinterpret_cast<const float2 *>(prm_l) + (size_t)j * d.L;
+        // slot `lane` of this block row: shift (-1 absent) and first edge of its block
+        const int my_sh = (lane < DCMAX && (REG || lane < d.L)) ? d.shift[j * d.L + lane] : -1;
+        const int my_eo = my_sh >= 0 ? d.eoff[j * d.L + lane] : 0;
         // this lane's partial gradients of (w, o) per edge slot l
 #pragma unroll
         for (int l = 0; l < DCMAX; ++l) part[(2 * l) * 32 + lane] = part[(2 * l + 1) * 32 + lane] = 0.0f;
-        // edge index of slot l in row r (-1: absent block)
-        auto edge = [&](int l, int r) -> int {
-            if (l >= d.L) return -1;
-            const int sh = d.shift[j * d.L + l];
-            if (sh < 0) return -1;
-            int k = r + sh;
-            if (k >= d.p) k -= d.p;
-            return d.eoff[j * d.L + l] + k;
-        };
+        const size_t base = (size_t)pk * d.E;
         for (int r = r0; r < r1; ++r) {
+            // edge of slot `lane` in row r (-1: absent) and its variable (for FROM_MU)
+            int my_e = -1, my_n = 0;
+            if (REG || my_sh >= 0) {
+                int k = r + my_sh;
+                if (k >= d.p) k -= d.p;
+                my_e = my_eo + k;
+                my_n = lane * d.p + k;
+            }
             // every load of the row first (beta^(l-1) and the adjoints of alpha^(l) do not depend on
             // each other): one memory round trip per row
             float xin[DCMAX], ga[DCMAX];
 #pragma unroll
             for (int l = 0; l < DCMAX; ++l) {
-                xin[l] = 0.0f;
+                const int e = __shfl_sync(0xffffffffu, my_e, l);
+                xin[l] = INFINITY;
                 ga[l] = 0.0f;
-                const int e = edge(l, r);
-                if (e < 0) continue;
-                const int k = e - d.eoff[j * d.L + l];
-                xin[l] = nm_beta<S, FROM_MU>(bin, d, pk, e, l * d.p + k, lane);
-                ga[l] = GA[((size_t)pk * d.E + e) * 32 + lane];
+                if (!REG && e < 0) continue;  // warp-uniform
+                const int n = FROM_MU ? __shfl_sync(0xffffffffu, my_n, l) : 0;
+                xin[l] = nm_beta<S, FROM_MU>(bin, d, pk, e, n, lane);
+                ga[l] = GA[(base + e) * 32 + lane];
             }
-            float ab[DCMAX];
+            // the two smallest magnitudes and their slots (strict <: the lowest index among ties);
+            // absent slots hold +inf and never qualify
             uint32_t neg = 0u;
             float mn1 = INFINITY, mn2 = INFINITY;
             int i1 = -1, i2 = -1;
 #pragma unroll
             for (int l = 0; l < DCMAX; ++l) {
-                ab[l] = INFINITY;
-                if (edge(l, r) < 0) continue;
-                const float x = xin[l];
-                ab[l] = fabsf(x);
-                neg |= (x < 0.0f ? 1u : 0u) << l;
-                // strict < keeps the lowest index among ties
-                if (ab[l] < mn1) {
-                    mn2 = mn1;
-                    i2 = i1;
-                    mn1 = ab[l];
-                    i1 = l;
-                } else if (ab[l] < mn2) {
-                    mn2 = ab[l];
-                    i2 = l;
-                }
+                const float a = fabsf(xin[l]);
+                neg |= (xin[l] < 0.0f ? 1u : 0u) << l;
+                const bool lo1 = a < mn1, lo2 = a < mn2;
+                mn2 = lo1 ? mn1 : (lo2 ? a : mn2);
+                i2 = lo1 ? i1 : (lo2 ? l : i2);
+                mn1 = lo1 ? a : mn1;
+                i1 = lo1 ? l : i1;
             }
             const uint32_t par = __popc(neg) & 1u;
-            float g1 = 0.0f, g2 = 0.0f;  // adjoints landing on edges i1 and i2
+            float g1 = 0.0f, g2 = 0.0f;  // adjoints landing on slots i1 and i2
 #pragma unroll
             for (int l = 0; l < DCMAX; ++l) {
-                const int e = edge(l, r);
-                if (e < 0) continue;
-                const float w = __ldg(prm + 2 * l), o = __ldg(prm + 2 * l + 1);
+                if (!REG && ga[l] == 0.0f) continue;  // absent slot, or nothing to propagate
+                const float2 wo = __ldg(prm + l);
                 const bool first = l == i1;
                 const float mv = first ? mn2 : mn1;
-                const float s = (par ^ ((neg >> l) & 1u)) ? -1.0f : 1.0f;
-                const float z = fmaf(w, mv, -o);
+                const float sgn = (par ^ ((neg >> l) & 1u)) ? -1.0f : 1.0f;
+                const float z = fmaf(wo.x, mv, -wo.y);
                 // alpha = s (w m - o) only where that is positive and below the clip
                 const bool act = (first ? i2 : i1) >= 0 && z > 0.0f && z < clip;
                 if (act) {
-                    const float gs = ga[l] * s;
+                    const float gs = ga[l] * sgn;
                     part[(2 * l) * 32 + lane] = fmaf(gs, mv, part[(2 * l) * 32 + lane]);
                     part[(2 * l + 1) * 32 + lane] -= gs;
-                    if (first) g2 += gs * w;
-                    else g1 += gs * w;
+                    if (first) g2 += gs * wo.x;
+                    else g1 += gs * wo.x;
                 }
             }
             if (want_gb) {
+                // sign(beta) of the two smallest inputs (0 for beta = 0)
+                const float s1 = (i1 < 0 || mn1 == 0.0f) ? 0.0f : (((neg >> i1) & 1u) ? -1.0f : 1.0f);
+                const float s2 = (i2 < 0 || mn2 == 0.0f) ? 0.0f : (((neg >> i2) & 1u) ? -1.0f : 1.0f);
 #pragma unroll
                 for (int l = 0; l < DCMAX; ++l) {
-                    const int e = edge(l, r);
-                    if (e < 0) continue;
-                    // sign(beta) of the two smallest inputs (0 for beta = 0)
-                    const float sg_l = ab[l] == 0.0f ? 0.0f : (((neg >> l) & 1u) ? -1.0f : 1.0f);
-                    float g = 0.0f;
-                    if (l == i1) g = g1 * sg_l;
-                    else if (l == i2) g = g2 * sg_l;
-                    GB[((size_t)pk * d.E + e) * 32 + lane] = g;
+                    const int e = __shfl_sync(0xffffffffu, my_e, l);
+                    if (!REG && e < 0) continue;  // warp-uniform
+                    const float g = l == i1 ? g1 * s1 : (l == i2 ? g2 * s2 : 0.0f);
+                    GB[(base + e) * 32 + lane] = g;
                 }
             }
         }
         // warp sums of this item's gradients per circulant (j, l)
 #pragma unroll
         for (int l = 0; l < DCMAX; ++l) {
-            if (edge(l, r0) < 0) continue;  // warp-uniform
+            if (!REG && __shfl_sync(0xffffffffu, my_sh, l) < 0) continue;  // warp-uniform
             float gw = part[(2 * l) * 32 + lane], go = part[(2 * l + 1) * 32 + lane];
 #pragma unroll
             for (int of = 16; of > 0; of >>= 1) {
@@ -474,7 +475,7 @@ static ldpc_status nm_backward(ldpc_code c, ldpc_noms_state &w, float *grad, cud
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int cb_blocks = std::max(1, sms * 3);  // three resident blocks per SM
+    const int cb_blocks = std::max(1, sms * kBwdBlocks);  // the resident blocks
     const float zinv = (float)(1.0 / ((double)w.T * d.N * w.B));
     const bool full = nm_full(d);
     int seg_base = -1;  // iterations seg_base+1 .. seg_base+k-1 recomputed into seg
@@ -517,17 +518,23 @@ static ldpc_status nm_backward(ldpc_code c, ldpc_noms_state &w, float *grad, cud
         const float *prm = w.params + (size_t)(l - 1) * d.J * d.L * 2;
         float *gl = grad + (size_t)(l - 1) * d.J * d.L * 2;
         const int want_gb = l > 1;
-#define NM_CB1(DC, FM)                                                                                      \
+#define NM_CB1(DC, FM, RG)                                                                                  \
     do {                                                                                                    \
         const size_t psm = (size_t)kWarps * (DC) * 2 * 32 * sizeof(float);                                 \
-        auto kfn = nm_cn_bwd<DC, S, FM>;                                                                    \
+        auto kfn = nm_cn_bwd<DC, S, FM, RG>;                                                                \
         cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);                   \
         kfn<<<cb_blocks, kWarps * 32, psm, s>>>(d, bin, w.GA, prm, w.GB, gl, w.clip, w.P, want_gb);         \
     } while (0)
-#define NM_CB(DC)                     \
-    do {                              \
-        if (from_mu) NM_CB1(DC, true); \
-        else NM_CB1(DC, false);       \
+#define NM_CB(DC)                                  \
+    do {                                           \
+        if (full && d.L == (DC)) {                 \
+            if (from_mu) NM_CB1(DC, true, true);   \
+            else NM_CB1(DC, false, true);          \
+        } else if (from_mu) {                      \
+            NM_CB1(DC, true, false);               \
+        } else {                                   \
+            NM_CB1(DC, false, false);              \
+        }                                          \
     } while (0)
         if (d.L <= 8) NM_CB(8);
         else if (d.L <= 16) NM_CB(16);
