@@ -386,7 +386,9 @@ ldpc_status ldpccc_channel(ldpccc cc, double ebn0_db, uint64_t seed, int64_t fir
  *   llr: device [B][N] float; params: device [T][J*L][2] float (w, o), 8-byte aligned
  *   (LDPC_EINVAL otherwise); msg: LDPC_MSG_F32
  *   or LDPC_MSG_F16 storage of the saved messages; ckpt_every = k: the messages of every
- *   k-th iteration are kept and the others recomputed in the backward pass;
+ *   k-th iteration are kept and the others recomputed in the backward pass (the
+ *   posteriors of every iteration, 4 N bytes per frame, and one bit per edge and frame
+ *   are kept as well, so check messages are never recomputed);
  *   loss: device float[1]; post: device [B][N] float (post^(T)) or NULL.
  *   The code object keeps the state for the following ldpc_noms_backward.
  * ldpc_noms_backward -- d loss / d params accumulated into grad (device [T][J*L][2],

@@ -504,8 +504,9 @@ def noms(row_ptr, col, cblk, N: int, mu, T: int, params, clip: float = 30.0, wan
 
     Returns (loss, post^(T) [nfr][N], grad [T][ncirc][2] or None); loss is the mean over
     iterations, bits and frames of softplus(-posterior) (BCE against the all-zero codeword).
-    store16: the FP16-message variant (the stored beta rounded to binary16); its forward runs in
-    binary32 like the device's, so that each rounding and each arg-min is decided on the same value.
+    store16: the FP16-message variant (the stored alpha and beta rounded to binary16); its forward
+    runs in binary32 like the device's, so that each rounding and each arg-min is decided on the same
+    value.
     """
     lib = _load()
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)

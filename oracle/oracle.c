@@ -691,7 +691,7 @@ void or_round_half_array(const double *x, double *out, int64_t n)
 }
 
 static void or_noms_vn(const or_graph *g, const double *mu, const double *alpha, double clip, double *beta,
-                       double *raw, double *post)
+                       double *post)
 {
     for (int n = 0; n < g->N; ++n) {
         int v0 = g->vptr[n], dv = g->vptr[n + 1] - v0;
@@ -702,7 +702,6 @@ static void or_noms_vn(const or_graph *g, const double *mu, const double *alpha,
             double s = mu[n];
             for (int k2 = 0; k2 < dv; ++k2)
                 if (k2 != k) s += alpha[g->vedge[v0 + k2]];
-            raw[g->vedge[v0 + k]] = s;
             beta[g->vedge[v0 + k]] = or_clip(s, clip);
         }
     }
@@ -713,8 +712,9 @@ static void or_noms_vn(const or_graph *g, const double *mu, const double *alpha,
    forward takes them on the value the device computes: binary32 arithmetic, w * m - o as one
    fused multiply-add, the sums of the variable rule in the column's edge order (increasing
    check index).  Every input of these steps (binary16 messages, binary32 channel LLRs and
-   parameters) is exact in binary32; results are stored as doubles.  beta is kept as binary16
-   between iterations; the gradient treats that rounding as the identity, as it treats the
+   parameters) is exact in binary32; results are stored as doubles.  Both message kinds are
+   kept as binary16 (alpha after the check step, beta after the variable step), as the FP16
+   decoder stores them; the gradient treats that rounding as the identity, as it treats the
    clip where inactive. */
 static void or_noms_cn_f32(const or_graph *g, const double *beta, const int *cblk, const double *par_l, double clip,
                            double *alpha, int *amin, double *mval, double *sval, int *act)
@@ -735,14 +735,15 @@ static void or_noms_cn_f32(const or_graph *g, const double *beta, const int *cbl
             float w = (float)par_l[2 * cblk[e]], o = (float)par_l[2 * cblk[e] + 1];
             float z = (arg < 0) ? INFINITY : fmaf(w, best, -o);
             int on = z > 0.0f;
-            alpha[e] = on ? (double)(sg * (z < cf ? z : cf)) : 0.0;
+            /* stored as binary16, like beta */
+            alpha[e] = on ? or_round_half((double)(sg * (z < cf ? z : cf))) : 0.0;
             amin[e] = arg; mval[e] = best; sval[e] = sg; act[e] = on && arg >= 0 && z < cf;
         }
     }
 }
 
 static void or_noms_vn_f32(const or_graph *g, const double *mu, const double *alpha, double clip, double *beta,
-                           double *raw, double *post)
+                           double *post)
 {
     for (int n = 0; n < g->N; ++n) {
         int v0 = g->vptr[n], dv = g->vptr[n + 1] - v0;
@@ -753,7 +754,6 @@ static void or_noms_vn_f32(const or_graph *g, const double *mu, const double *al
             float sm = (float)mu[n];
             for (int k2 = 0; k2 < dv; ++k2)
                 if (k2 != k) sm += (float)alpha[g->vedge[v0 + k2]];
-            raw[g->vedge[v0 + k]] = sm;
             beta[g->vedge[v0 + k]] = or_round_half(or_clip(sm, clip));
         }
     }
@@ -762,8 +762,8 @@ static void or_noms_vn_f32(const or_graph *g, const double *mu, const double *al
 /*
  * or_noms: forward (and, if grad != NULL, backward) over nfr frames.
  * post_out (nullable) receives post^(T) [nfr][N]; returns the loss.  grad is [T][ncirc][2],
- * accumulated (the caller zeroes it).  store16: the FP16-message variant (beta^(l), l >= 1,
- * rounded to binary16 when stored; its forward in binary32, see or_noms_cn_f32).
+ * accumulated (the caller zeroes it).  store16: the FP16-message variant (alpha^(l) and beta^(l),
+ * l >= 1, rounded to binary16 when stored; its forward in binary32, see or_noms_cn_f32).
  */
 double or_noms(int M, int N, const int *row_ptr, const int *col, const int *cblk, int nfr, const float *mu_f,
                int T, const double *params, int ncirc, double clip, double *post_out, double *grad, int nthreads,
@@ -779,7 +779,6 @@ double or_noms(int M, int N, const int *row_ptr, const int *col, const int *cblk
     for (int f = 0; f < nfr; ++f) {
         double *mu = malloc(sizeof(double) * N);
         double *beta = malloc(sizeof(double) * (size_t)E * (T + 1)); /* beta^(0..T) */
-        double *raw = malloc(sizeof(double) * (size_t)E * (T + 1));
         double *alpha = malloc(sizeof(double) * (size_t)E * T);
         double *post = malloc(sizeof(double) * (size_t)N * T);
         double *mval = malloc(sizeof(double) * (size_t)E * T), *sval = malloc(sizeof(double) * (size_t)E * T);
@@ -795,13 +794,13 @@ double or_noms(int M, int N, const int *row_ptr, const int *col, const int *cblk
                                alpha + (size_t)l * E, amin + (size_t)l * E, mval + (size_t)l * E,
                                sval + (size_t)l * E, act + (size_t)l * E);
                 or_noms_vn_f32(&g, mu, alpha + (size_t)l * E, clip, beta + (size_t)(l + 1) * E,
-                               raw + (size_t)(l + 1) * E, post + (size_t)l * N);
+                               post + (size_t)l * N);
             } else {
                 or_noms_cn(&g, beta + (size_t)l * E, cblk, params + (size_t)l * 2 * ncirc, clip,
                            alpha + (size_t)l * E, amin + (size_t)l * E, mval + (size_t)l * E,
                            sval + (size_t)l * E, act + (size_t)l * E);
                 or_noms_vn(&g, mu, alpha + (size_t)l * E, clip, beta + (size_t)(l + 1) * E,
-                           raw + (size_t)(l + 1) * E, post + (size_t)l * N);
+                           post + (size_t)l * N);
             }
             for (int n = 0; n < N; ++n) lf += or_softplus(-post[(size_t)l * N + n]);
         }
@@ -812,7 +811,9 @@ double or_noms(int M, int N, const int *row_ptr, const int *col, const int *cblk
             /* gb = adjoint of beta^(l) (zero for l = T) */
             for (int l = T - 1; l >= 0; --l) {
                 const double *bl = beta + (size_t)l * E;                 /* input of CN l */
-                const double *rawn = raw + (size_t)(l + 1) * E;          /* VN l output, unclipped */
+                /* VN l output as stored: the clip was inactive where |beta| < clip (with binary16
+                   storage, where the stored value is below the clip) */
+                const double *bn = beta + (size_t)(l + 1) * E;
                 const double *pl = post + (size_t)l * N;
                 /* adjoint of alpha^(l) */
                 for (int n = 0; n < N; ++n) {
@@ -823,7 +824,7 @@ double or_noms(int M, int N, const int *row_ptr, const int *col, const int *cblk
                         for (int k2 = 0; k2 < dv; ++k2) {
                             if (k2 == k) continue;
                             int e2 = g.vedge[v0 + k2];
-                            if (fabs(rawn[e2]) < clip) s += gb[e2];
+                            if (fabs(bn[e2]) < clip) s += gb[e2];
                         }
                         ga[g.vedge[v0 + k]] = s;
                     }
@@ -847,7 +848,7 @@ double or_noms(int M, int N, const int *row_ptr, const int *col, const int *cblk
                 for (int e = 0; e < E; ++e) gb[e] = gb_prev[e];
             }
         }
-        free(mu); free(beta); free(raw); free(alpha); free(post); free(mval); free(sval); free(amin); free(act);
+        free(mu); free(beta); free(alpha); free(post); free(mval); free(sval); free(amin); free(act);
         free(gb); free(ga); free(gb_prev);
     }
     or_graph_free(&g);

@@ -9,8 +9,11 @@
 // Layout: packages of 32 frames, one frame per lane, msg-like buffers
 // [P][E][32] (edge order of the block decoder: edge k of block (j, l) is
 // variable l*p + k).  Betas are kept at checkpoints every k iterations in the
-// storage type S (float or half); alphas and adjoints in float.  The backward
-// pass recomputes each segment of k iterations from its checkpoint.
+// storage type S (float or half), and so are the alphas; adjoints in float.  The backward
+// pass recomputes each segment of k iterations from its checkpoint.  The forward
+// also keeps every iteration's posteriors ([T][P][N][32] floats): with them and
+// beta^(l) the backward variable step needs nothing of alpha^(l), so the check
+// messages are never recomputed.
 #include "qc_device.cuh"
 
 #include <algorithm>
@@ -25,7 +28,8 @@ struct ldpc_noms_state {
     void *ckpt = nullptr;      // [nck][P][E][32] (S): beta^(k), beta^(2k), ...
     void *seg = nullptr;       // [k][P][E][32] (S): recomputed betas of one segment
     float *A = nullptr, *GA = nullptr, *GB = nullptr;  // [P][E][32]
-    float *postbuf = nullptr;  // [P][N][32]
+    float *posts = nullptr;    // [T][P][N][32] (stride N * cap_frames): post^(1..T) of the forward
+    size_t cap_T = 0;
     double *acc = nullptr;     // loss accumulator
     bool have_forward = false;
     const float *params = nullptr;
@@ -65,7 +69,7 @@ __device__ __forceinline__ float nm_beta(const void *src, const QcDesc &d, int p
 // edge indices are recomputed for the stores.
 template <int DCMAX, typename S, bool FROM_MU, bool REG>
 __global__ void __launch_bounds__(kWarps * 32)
-nm_cn_fwd(const QcDesc d, const void *__restrict__ bin, float *__restrict__ A, const float *__restrict__ prm_l,
+nm_cn_fwd(const QcDesc d, const void *__restrict__ bin, S *__restrict__ A, const float *__restrict__ prm_l,
           float clip, int P) {
     const int lane = threadIdx.x & 31;
     const int m = blockIdx.x * kWarps + (threadIdx.x >> 5);
@@ -107,7 +111,7 @@ nm_cn_fwd(const QcDesc d, const void *__restrict__ bin, float *__restrict__ A, c
         const float2 wo = __ldg(prm + l);
         const float mv = l == i1 ? mn2 : mn1;
         const float mag = fminf(fmaxf(fmaf(wo.x, mv, -wo.y), 0.0f), clip);
-        A[((size_t)pk * d.E + e) * 32 + lane] = (par ^ ((neg >> l) & 1u)) ? -mag : mag;
+        Store<S>::st(A + ((size_t)pk * d.E + e) * 32 + lane, (par ^ ((neg >> l) & 1u)) ? -mag : mag);
     }
 }
 
@@ -116,7 +120,7 @@ nm_cn_fwd(const QcDesc d, const void *__restrict__ bin, float *__restrict__ A, c
 // ---------------------------------------------------------------------------
 template <int JMAX, typename S, bool REG>
 __global__ void __launch_bounds__(kWarps * 32)
-nm_vn_fwd(const QcDesc d, const float *__restrict__ A, const float *__restrict__ mu, S *__restrict__ bout,
+nm_vn_fwd(const QcDesc d, const S *__restrict__ A, const float *__restrict__ mu, S *__restrict__ bout,
           double *__restrict__ acc, float *__restrict__ post, float zinv, float clip, int P, int B) {
     __shared__ float red[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -135,7 +139,7 @@ nm_vn_fwd(const QcDesc d, const float *__restrict__ A, const float *__restrict__
             eid[j] = -1;
             if (!REG && (j >= d.J || d.shift[j * d.L + l] < 0)) continue;
             eid[j] = d.eoff[j * d.L + l] + k;
-            a[j] = A[((size_t)pk * d.E + eid[j]) * 32 + lane];
+            a[j] = Store<S>::ld(A + ((size_t)pk * d.E + eid[j]) * 32 + lane);
         }
 #pragma unroll
         for (int j = 0; j < JMAX; ++j) tot += a[j];
@@ -167,42 +171,34 @@ nm_vn_fwd(const QcDesc d, const float *__restrict__ A, const float *__restrict__
 
 // ---------------------------------------------------------------------------
 // backward variable step: adjoint of alpha^(l) from the loss at iteration l and
-// the adjoint of beta^(l) (zero at l = T), through the clip
+// the adjoint of beta^(l) (zero at l = T), through the clip.  What this step needs
+// of iteration l is the posterior post^(l), saved by the forward, and where beta^(l)
+// stayed inside the clip, read off the stored beta^(l) itself (|beta| < clip exactly
+// where the clip was inactive), so alpha^(l) is not recomputed.
 // ---------------------------------------------------------------------------
-template <int JMAX, bool REG>
+template <int JMAX, typename S, bool REG>
 __global__ void __launch_bounds__(kWarps * 32)
-nm_vn_bwd(const QcDesc d, const float *__restrict__ A, const float *__restrict__ mu, const float *__restrict__ GB,
-          float *__restrict__ GA, float zinv, float clip, int P, int B) {
+nm_vn_bwd(const QcDesc d, const float *__restrict__ post, const S *__restrict__ bl, const float *__restrict__ GB,
+          float *__restrict__ GA, float clip, float zinv, int P, int B) {
     const int lane = threadIdx.x & 31;
     const int n = blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int pk = blockIdx.y;
     if (n >= d.N || pk >= P) return;
     const int l = (int)fdiv((uint32_t)n, d.divP), k = n - l * d.p;
-    const float mv = mu[((size_t)pk * d.N + n) * 32 + lane];
-    float a[JMAX], gbm[JMAX];
+    const float tot = post[((size_t)pk * d.N + n) * 32 + lane];
+    float gbm[JMAX];
     int eid[JMAX];
-    float tot = mv;
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
-        a[j] = 0.0f;
         gbm[j] = 0.0f;
         eid[j] = -1;
         if (!REG && (j >= d.J || d.shift[j * d.L + l] < 0)) continue;
         eid[j] = d.eoff[j * d.L + l] + k;
-        a[j] = A[((size_t)pk * d.E + eid[j]) * 32 + lane];
-        // adjoint of beta^(l)_e, loaded with alpha (independent of it) and masked below
-        if (GB) gbm[j] = GB[((size_t)pk * d.E + eid[j]) * 32 + lane];
-    }
-#pragma unroll
-    for (int j = 0; j < JMAX; ++j) tot += a[j];
-    // the adjoint passes the clip only where it was inactive
-#pragma unroll
-    for (int j = 0; j < JMAX; ++j) {
-        float s = mv;
-#pragma unroll
-        for (int j2 = 0; j2 < JMAX; ++j2)
-            if (j2 != j) s += a[j2];
-        if (!(fabsf(s) < clip)) gbm[j] = 0.0f;
+        // the adjoint of beta^(l)_e passes the clip only where it was inactive
+        if (GB) {
+            const size_t x = ((size_t)pk * d.E + eid[j]) * 32 + lane;
+            if (fabsf(Store<S>::ld(bl + x)) < clip) gbm[j] = GB[x];
+        }
     }
     const float dpost = (pk * 32 + lane < B) ? -sigmoidf(-tot) * zinv : 0.0f;
 #pragma unroll
@@ -358,7 +354,7 @@ __global__ void nm_loss_out(const double *acc, float *out) { *out = (float)*acc;
 // ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
-static ldpc_status nm_alloc(ldpc_code c, ldpc_noms_state &w, size_t frames, size_t nck, size_t nseg) {
+static ldpc_status nm_alloc(ldpc_code c, ldpc_noms_state &w, size_t frames, size_t nck, size_t nseg, size_t T) {
     const size_t E = c->d.E, N = c->d.N;
     const size_t fr = (frames + 31) / 32 * 32;
     auto fail = [&]() {
@@ -369,15 +365,22 @@ static ldpc_status nm_alloc(ldpc_code c, ldpc_noms_state &w, size_t frames, size
     if (fr > w.cap_frames) {
         cudaDeviceSynchronize();
         cudaFree(w.mu); cudaFree(w.ping[0]); cudaFree(w.ping[1]); cudaFree(w.A); cudaFree(w.GA); cudaFree(w.GB);
-        cudaFree(w.postbuf); cudaFree(w.ckpt); cudaFree(w.seg);
+        cudaFree(w.posts); cudaFree(w.ckpt); cudaFree(w.seg);
+        w.posts = nullptr;
         w.ckpt = w.seg = nullptr;
-        w.cap_nck = w.cap_seg = 0;
+        w.cap_nck = w.cap_seg = w.cap_T = 0;
         if (cudaMalloc(&w.mu, N * fr * 4) || cudaMalloc(&w.ping[0], E * fr * 4) || cudaMalloc(&w.ping[1], E * fr * 4) ||
-            cudaMalloc(&w.A, E * fr * 4) || cudaMalloc(&w.GA, E * fr * 4) || cudaMalloc(&w.GB, E * fr * 4) ||
-            cudaMalloc(&w.postbuf, N * fr * 4))
+            cudaMalloc(&w.A, E * fr * 4) || cudaMalloc(&w.GA, E * fr * 4) || cudaMalloc(&w.GB, E * fr * 4))
             return fail();
         if (!w.acc && cudaMalloc(&w.acc, sizeof(double))) return fail();
         w.cap_frames = fr;
+    }
+    if (T > w.cap_T) {
+        cudaDeviceSynchronize();
+        cudaFree(w.posts);
+        w.posts = nullptr;
+        if (cudaMalloc(&w.posts, T * N * w.cap_frames * 4)) return fail();
+        w.cap_T = T;
     }
     if (nck > w.cap_nck) {
         cudaDeviceSynchronize();
@@ -412,12 +415,12 @@ static ldpc_status nm_step_fwd(ldpc_code c, ldpc_noms_state &w, int l, const voi
 #define NM_CN(DC)                                                                                             \
     do {                                                                                                      \
         if (full && d.L == (DC)) {                                                                            \
-            if (from_mu) nm_cn_fwd<DC, S, true, true><<<cg, kWarps * 32, 0, s>>>(d, bin, w.A, prm, w.clip, w.P); \
-            else nm_cn_fwd<DC, S, false, true><<<cg, kWarps * 32, 0, s>>>(d, bin, w.A, prm, w.clip, w.P);        \
+            if (from_mu) nm_cn_fwd<DC, S, true, true><<<cg, kWarps * 32, 0, s>>>(d, bin, (S *)w.A, prm, w.clip, w.P); \
+            else nm_cn_fwd<DC, S, false, true><<<cg, kWarps * 32, 0, s>>>(d, bin, (S *)w.A, prm, w.clip, w.P);        \
         } else if (from_mu) {                                                                                 \
-            nm_cn_fwd<DC, S, true, false><<<cg, kWarps * 32, 0, s>>>(d, bin, w.A, prm, w.clip, w.P);           \
+            nm_cn_fwd<DC, S, true, false><<<cg, kWarps * 32, 0, s>>>(d, bin, (S *)w.A, prm, w.clip, w.P);           \
         } else {                                                                                              \
-            nm_cn_fwd<DC, S, false, false><<<cg, kWarps * 32, 0, s>>>(d, bin, w.A, prm, w.clip, w.P);          \
+            nm_cn_fwd<DC, S, false, false><<<cg, kWarps * 32, 0, s>>>(d, bin, (S *)w.A, prm, w.clip, w.P);          \
         }                                                                                                     \
     } while (0)
     if (d.L <= 8) NM_CN(8);
@@ -429,11 +432,14 @@ static ldpc_status nm_step_fwd(ldpc_code c, ldpc_noms_state &w, int l, const voi
     if (bout || loss || post) {
         double *acc = loss ? w.acc : nullptr;
         if (full && d.J == 4)
-            nm_vn_fwd<4, S, true><<<vg, kWarps * 32, 0, s>>>(d, w.A, w.mu, (S *)bout, acc, post, zinv, w.clip, w.P, w.B);
+            nm_vn_fwd<4, S, true><<<vg, kWarps * 32, 0, s>>>(d, (const S *)w.A, w.mu, (S *)bout, acc, post, zinv, w.clip,
+                                                             w.P, w.B);
         else if (d.J <= 4)
-            nm_vn_fwd<4, S, false><<<vg, kWarps * 32, 0, s>>>(d, w.A, w.mu, (S *)bout, acc, post, zinv, w.clip, w.P, w.B);
+            nm_vn_fwd<4, S, false><<<vg, kWarps * 32, 0, s>>>(d, (const S *)w.A, w.mu, (S *)bout, acc, post, zinv, w.clip,
+                                                              w.P, w.B);
         else
-            nm_vn_fwd<8, S, false><<<vg, kWarps * 32, 0, s>>>(d, w.A, w.mu, (S *)bout, acc, post, zinv, w.clip, w.P, w.B);
+            nm_vn_fwd<8, S, false><<<vg, kWarps * 32, 0, s>>>(d, (const S *)w.A, w.mu, (S *)bout, acc, post, zinv, w.clip,
+                                                              w.P, w.B);
         count_launch();
     }
     LDPC_CUDA_TRY(cudaGetLastError());
@@ -449,8 +455,12 @@ static void *sg(ldpc_code c, ldpc_noms_state &w, int idx) {
     return (char *)w.seg + (size_t)idx * c->d.E * w.cap_frames * sizeof(S);
 }
 
+static float *nm_post(ldpc_code c, ldpc_noms_state &w, int l) {  // post^(l), l >= 1
+    return w.posts + (size_t)(l - 1) * c->d.N * w.cap_frames;
+}
+
 template <typename S>
-static ldpc_status nm_forward(ldpc_code c, ldpc_noms_state &w, float *post_out, cudaStream_t s) {
+static ldpc_status nm_forward(ldpc_code c, ldpc_noms_state &w, cudaStream_t s) {
     LDPC_CUDA_TRY(cudaMemsetAsync(w.acc, 0, sizeof(double), s));
     const void *prev = w.mu;
     bool from_mu = true;
@@ -459,12 +469,11 @@ static ldpc_status nm_forward(ldpc_code c, ldpc_noms_state &w, float *post_out, 
         if (l == w.T) out = nullptr;  // beta^(T) is never used
         else if (l % w.k == 0) out = ck<S>(c, w, l / w.k);
         else out = w.ping[l & 1];
-        ldpc_status st = nm_step_fwd<S>(c, w, l, prev, from_mu, out, true, l == w.T ? w.postbuf : nullptr, s);
+        ldpc_status st = nm_step_fwd<S>(c, w, l, prev, from_mu, out, true, nm_post(c, w, l), s);
         if (st != LDPC_OK) return st;
         prev = out;
         from_mu = false;
     }
-    (void)post_out;
     return LDPC_OK;
 }
 
@@ -479,6 +488,10 @@ static ldpc_status nm_backward(ldpc_code c, ldpc_noms_state &w, float *grad, cud
     const float zinv = (float)(1.0 / ((double)w.T * d.N * w.B));
     const bool full = nm_full(d);
     int seg_base = -1;  // iterations seg_base+1 .. seg_base+k-1 recomputed into seg
+    // beta^(l): the input of the previous (l + 1) step, a checkpoint or a member of the segment
+    // that step used -- which is also beta^(l-1)'s segment unless l is a checkpoint, so it is
+    // still there
+    const void *bnext = nullptr;
     for (int l = w.T; l >= 1; --l) {
         // beta^(l-1): mu, a checkpoint, or a recomputed member of its segment
         const int b = l - 1;
@@ -505,16 +518,17 @@ static ldpc_status nm_backward(ldpc_code c, ldpc_noms_state &w, float *grad, cud
             }
             bin = sg<S>(c, w, b - c0 - 1);
         }
-        // alpha^(l), then the adjoints
-        ldpc_status st = nm_step_fwd<S>(c, w, l, bin, from_mu, nullptr, false, nullptr, s);
-        if (st != LDPC_OK) return st;
+        // the adjoints of alpha^(l) (from the saved posteriors and beta^(l)), then of the parameters
+        // and beta^(l-1)
         const float *gbin = l == w.T ? nullptr : w.GB;
+        const S *bl = l == w.T ? nullptr : (const S *)bnext;
+        const float *pl = nm_post(c, w, l);
         if (full && d.J == 4)
-            nm_vn_bwd<4, true><<<vg, kWarps * 32, 0, s>>>(d, w.A, w.mu, gbin, w.GA, zinv, w.clip, w.P, w.B);
+            nm_vn_bwd<4, S, true><<<vg, kWarps * 32, 0, s>>>(d, pl, bl, gbin, w.GA, w.clip, zinv, w.P, w.B);
         else if (d.J <= 4)
-            nm_vn_bwd<4, false><<<vg, kWarps * 32, 0, s>>>(d, w.A, w.mu, gbin, w.GA, zinv, w.clip, w.P, w.B);
+            nm_vn_bwd<4, S, false><<<vg, kWarps * 32, 0, s>>>(d, pl, bl, gbin, w.GA, w.clip, zinv, w.P, w.B);
         else
-            nm_vn_bwd<8, false><<<vg, kWarps * 32, 0, s>>>(d, w.A, w.mu, gbin, w.GA, zinv, w.clip, w.P, w.B);
+            nm_vn_bwd<8, S, false><<<vg, kWarps * 32, 0, s>>>(d, pl, bl, gbin, w.GA, w.clip, zinv, w.P, w.B);
         const float *prm = w.params + (size_t)(l - 1) * d.J * d.L * 2;
         float *gl = grad + (size_t)(l - 1) * d.J * d.L * 2;
         const int want_gb = l > 1;
@@ -544,6 +558,7 @@ static ldpc_status nm_backward(ldpc_code c, ldpc_noms_state &w, float *grad, cud
 #undef NM_CB1
         count_launch(2);
         LDPC_CUDA_TRY(cudaGetLastError());
+        bnext = bin;
     }
     return LDPC_OK;
 }
@@ -584,7 +599,8 @@ ldpc_status ldpc_noms_forward(ldpc_code c, const float *llr, int32_t B, int32_t 
     }
     ldpc_noms_state &w = *c->noms;
     const int nck = (T - 1) / ckpt_every;
-    ldpc_status st = nm_alloc(c, w, (size_t)B, (size_t)std::max(nck, 1), (size_t)std::max(ckpt_every - 1, 1));
+    ldpc_status st =
+        nm_alloc(c, w, (size_t)B, (size_t)std::max(nck, 1), (size_t)std::max(ckpt_every - 1, 1), (size_t)T);
     if (st != LDPC_OK) return st;
     w.B = B;
     w.T = T;
@@ -596,12 +612,12 @@ ldpc_status ldpc_noms_forward(ldpc_code c, const float *llr, int32_t B, int32_t 
     cudaStream_t s = (cudaStream_t)stream;
     st = pack_frames_w32(llr, w.mu, B, c->d.N, clip, s);
     if (st != LDPC_OK) return st;
-    st = msg == LDPC_MSG_F16 ? nm_forward<__half>(c, w, post, s) : nm_forward<float>(c, w, post, s);
+    st = msg == LDPC_MSG_F16 ? nm_forward<__half>(c, w, s) : nm_forward<float>(c, w, s);
     if (st != LDPC_OK) return st;
     nm_loss_out<<<1, 1, 0, s>>>(w.acc, loss);
     count_launch();
     if (post) {
-        st = unpack_frames_w32(w.postbuf, post, B, c->d.N, s);
+        st = unpack_frames_w32(nm_post(c, w, T), post, B, c->d.N, s);
         if (st != LDPC_OK) return st;
     }
     w.have_forward = true;
@@ -633,7 +649,7 @@ namespace ldpc {
 void noms_free(ldpc_noms_state *w) {
     if (!w) return;
     cudaFree(w->mu); cudaFree(w->ping[0]); cudaFree(w->ping[1]); cudaFree(w->ckpt); cudaFree(w->seg);
-    cudaFree(w->A); cudaFree(w->GA); cudaFree(w->GB); cudaFree(w->postbuf); cudaFree(w->acc);
+    cudaFree(w->A); cudaFree(w->GA); cudaFree(w->GB); cudaFree(w->posts); cudaFree(w->acc);
     delete w;
 }
 }  // namespace ldpc

@@ -102,9 +102,9 @@ def test_noms_checkpointing_does_not_change_gradients(pkg):
 
 @pytest.mark.parametrize("J,L,p", SHAPES)
 def test_noms_fp16_storage_gradient(pkg, J, L, p):
-    """FP16 storage of the saved messages against the oracle of the same variant (the stored beta rounded
-    to binary16, its forward in binary32 so that both sides round the same values and pick the same
-    arg-min edges): loss and gradient element by element.  Against the unrounded FP64 oracle the min-sum
+    """FP16 storage of the messages against the oracle of the same variant (the stored alpha and beta
+    rounded to binary16, its forward in binary32 so that both sides round the same values and pick the
+    same arg-min edges): loss and gradient element by element.  Against the unrounded FP64 oracle the min-sum
     gradient jumps wherever rounding changes the arg-min edge, so that comparison is not element-wise."""
     shifts, rp, col, cb = setup(J, L, p, 2)
     code = pkg.QCCode(shifts, p)

@@ -549,9 +549,9 @@ def test_binary16_rounding_matches_numpy_float16():
 
 
 def test_noms_fp16_variant_rounds_stored_messages():
-    """With binary16 storage the first iteration (fed by the FP32 channel LLRs) is unchanged and later
-    iterations see rounded inputs: on the hand-worked two-check example every value is a multiple of
-    2^-7, exact in binary16, so the result equals the unrounded one."""
+    """With binary16 storage the check messages and the later iterations' variable messages are rounded
+    (the first check step reads the FP32 channel LLRs): on the hand-worked two-check example every value
+    is a multiple of 2^-7, exact in binary16, so the result equals the unrounded one."""
     H = oracle.qc_parity_check([[0, 0, 0, -1, -1], [-1, -1, 0, 0, 0]], 1)
     rp, col = oracle.csr_rows(H)
     cb = oracle.circulant_index(rp, col, 1, 5)
