@@ -665,12 +665,13 @@ def sparse_bench(a, pkg, qc, stream) -> dict:
 
 
 def e2e(a, pkg, code, stream, opts) -> dict:
-    """Same metric through ldpc_decode with pinned HOST buffers: 16 x slots frames per call (the LLRs of
-    the call read from host memory, the hard decisions, iteration counts and ok flags written back to
-    host memory, inside the timed region; with early stop the frames stream through the slots)."""
+    """Same metric through ldpc_decode with pinned HOST buffers: one call per step on the step's frames
+    (--frames, at least 2 x slots so that they stream; the LLRs of the call read from host memory, the
+    hard decisions, iteration counts and ok flags written back to host memory, inside the timed region;
+    with early stop the frames stream through the slots)."""
     import torch
 
-    gamma = 16 * a.gamma
+    gamma = max(a.frames, 2 * a.gamma)
     llr_dev = torch.empty((gamma, code.N), dtype=torch.float32, device="cuda")
     pkg.ldpc_channel(code.handle, a.ebn0, a.seed, 3 << 44, llr_dev, stream)
     llr = llr_dev.cpu().pin_memory()

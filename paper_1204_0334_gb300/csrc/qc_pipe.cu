@@ -112,16 +112,7 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
                 for (int v = 0; v < V; ++v)
                     cp_async4(dst + St::WORDS + lane * V + v, ages + (size_t)pk * W + lane * V + v);
             }
-#pragma unroll
-            for (int q = 0; q < DCMAX / 4; ++q) {
-                const int l = 4 * q + g;
-                const int sh = (REG || l < d.L) ? s_sh[j * d.L + l] : -1;
-                if (REG || sh >= 0) {
-                    int k = r + sh;
-                    if (k >= d.p) k -= d.p;
-                    cp_async16(dst + l * 32 + sub * 4, gmsg + (size_t)(s_eo[j * d.L + l] + k) * 32 + sub * 4);
-                }
-            }
+            // lane l computes edge l's offset once; the copies take it by shuffle
             if (lane < DCMAX && (REG || lane < d.L)) {
                 const int sh = s_sh[j * d.L + lane];
                 if (REG || sh >= 0) {
@@ -129,6 +120,12 @@ cn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, const uint32_t *__res
                     if (k >= d.p) k -= d.p;
                     mine = s_eo[j * d.L + lane] + k;
                 }
+            }
+#pragma unroll
+            for (int q = 0; q < DCMAX / 4; ++q) {
+                const int l = 4 * q + g;
+                const int o = __shfl_sync(0xffffffffu, mine, l);
+                if (REG || o >= 0) cp_async16(dst + l * 32 + sub * 4, gmsg + (size_t)o * 32 + sub * 4);
             }
             if (lane < V) cp_async4(dst + St::FL + lane, flags + (size_t)pk * 5 * V + lane);
             else if (fresh && lane < 2 * V) cp_async4(dst + St::FL + lane, fresh + (size_t)pk * 2 * V + lane);

@@ -124,6 +124,27 @@ def test_noms_fp16_storage_gradient(pkg, J, L, p):
     assert rel.max() <= 1e-3, rel.max()
 
 
+def test_noms_fp16_gradient_ten_iterations(pkg):
+    """The training configuration's depth (10 unrolled iterations, a checkpoint every 2) on a code with
+    full rows of 24 edges, FP16 messages against the oracle's binary16 variant, element by element."""
+    J, L, p = 4, 24, 31
+    shifts, rp, col, cb = setup(J, L, p, 7)
+    code = pkg.QCCode(shifts, p)
+    T, B = 10, 64
+    prm = rand_params(T, J * L, 9)
+    mu = synth.gaussian_llrs(B, code.N, seed=10, ebn0_db=3.0, rate=1 - J / L)
+    prm_d = torch.from_numpy(prm).cuda()
+    loss, _ = pkg.ldpc_noms_forward(code.handle, torch.from_numpy(mu).cuda(), prm_d, pkg.MSG_F16, 2, 30.0)
+    grad = torch.zeros_like(prm_d)
+    pkg.ldpc_noms_backward(code.handle, prm_d, grad)
+    lo, _, go = oracle.noms(rp, col, cb, code.N, mu, T, prm.astype(np.float64), want_grad=True, nthreads=8,
+                            store16=True)
+    assert abs(float(loss) - lo) <= 1e-5 * abs(lo)
+    g = grad.cpu().numpy().astype(np.float64)
+    rel = np.abs(g - go) / np.maximum(np.abs(go), 1e-3 * np.abs(go).max())
+    assert rel.max() <= 1e-3, rel.max()
+
+
 @pytest.mark.parametrize("msg", [0, 1])
 def test_noms_gradient_with_clipped_check_messages(pkg, msg):
     """Weights above 1 and a low clip: w * m - o often exceeds the clip, so alpha is clipped and its
