@@ -30,7 +30,7 @@ struct ldpc_noms_state {
     float *A = nullptr, *GA = nullptr, *GB = nullptr;  // [P][E][32]
     float *posts = nullptr;    // [T][P][N][32] (stride N * cap_frames): post^(1..T) of the forward
     size_t cap_T = 0;
-    double *acc = nullptr;     // loss accumulator
+    double *acc = nullptr;     // loss: one partial sum per variable-step block, [P][ceil(N / 8)]
     bool have_forward = false;
     const float *params = nullptr;
 };
@@ -47,9 +47,11 @@ template <> struct Store<__half> {
     static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
 };
 
-__device__ __forceinline__ float softplusf(float x) { return x > 0.0f ? x + log1pf(__expf(-x)) : log1pf(__expf(x)); }
+// one exponential each: softplus(x) = max(x, 0) + log1p(e^-|x|); sigmoid from e = e^-|x|
+__device__ __forceinline__ float softplusf(float x) { return fmaxf(x, 0.0f) + log1pf(__expf(-fabsf(x))); }
 __device__ __forceinline__ float sigmoidf(float x) {
-    return x >= 0.0f ? 1.0f / (1.0f + __expf(-x)) : __expf(x) / (1.0f + __expf(x));
+    const float e = __expf(-fabsf(x));
+    return x >= 0.0f ? 1.0f / (1.0f + e) : e / (1.0f + e);
 }
 
 // beta^(l-1) of edge (block offset eo + k) and variable n, from mu (l = 1) or a store
@@ -62,13 +64,16 @@ __device__ __forceinline__ float nm_beta(const void *src, const QcDesc &d, int p
 // ---------------------------------------------------------------------------
 // forward check step: alpha^(l) from beta^(l-1); one warp = one row of one package
 // ---------------------------------------------------------------------------
+#ifndef NM_FWD_MINB
+#define NM_FWD_MINB 4  // resident blocks per SM of the forward check step (a 64-register budget)
+#endif
 // REG: every block of the row is present and L == DCMAX, so the gathers carry no branches
 // and all DCMAX loads of a row are in flight together.  Only the two smallest magnitudes,
 // the index of the first smallest and the sign bits outlive the gathers: the other edges'
-// minimum is mn2 for that index and mn1 for every other edge (on a tie mn2 == mn1), and the
-// edge indices are recomputed for the stores.
+// minimum is mn2 for that index and mn1 for every other edge (on a tie mn2 == mn1).  Lane l
+// holds slot l's edge index and the gathers take it by shuffle.
 template <int DCMAX, typename S, bool FROM_MU, bool REG>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, NM_FWD_MINB)
 nm_cn_fwd(const QcDesc d, const void *__restrict__ bin, S *__restrict__ A, const float *__restrict__ prm_l,
           float clip, int P) {
     const int lane = threadIdx.x & 31;
@@ -76,19 +81,21 @@ nm_cn_fwd(const QcDesc d, const void *__restrict__ bin, S *__restrict__ A, const
     const int pk = blockIdx.y;
     if (m >= d.M || pk >= P) return;
     const int j = (int)fdiv((uint32_t)m, d.divP), r = m - j * d.p;
-    // (edge, position k in its circulant) of slot l in this row; edge -1: absent block
-    auto edge = [&](int l) -> int2 {
-        const int sh = (REG || l < d.L) ? d.shift[j * d.L + l] : -1;
-        if (!REG && sh < 0) return make_int2(-1, 0);
-        int k = r + sh;
+    // lane l: the edge of slot l in this row (-1: absent block) and its variable, computed once and
+    // broadcast by shuffles
+    int my_e = -1, my_n = 0;
+    if (REG ? lane < DCMAX : (lane < d.L && d.shift[j * d.L + lane] >= 0)) {
+        int k = r + d.shift[j * d.L + lane];
         if (k >= d.p) k -= d.p;
-        return make_int2(d.eoff[j * d.L + l] + k, k);
-    };
+        my_e = d.eoff[j * d.L + lane] + k;
+        my_n = lane * d.p + k;
+    }
     float x[DCMAX];
 #pragma unroll
     for (int l = 0; l < DCMAX; ++l) {
-        const int2 ek = edge(l);
-        x[l] = ek.x < 0 ? INFINITY : nm_beta<S, FROM_MU>(bin, d, pk, ek.x, l * d.p + ek.y, lane);
+        const int e = __shfl_sync(0xffffffffu, my_e, l);
+        const int n = FROM_MU ? __shfl_sync(0xffffffffu, my_n, l) : 0;
+        x[l] = (!REG && e < 0) ? INFINITY : nm_beta<S, FROM_MU>(bin, d, pk, e, n, lane);
     }
     uint32_t neg = 0u;
     float mn1 = INFINITY, mn2 = INFINITY;
@@ -106,8 +113,13 @@ nm_cn_fwd(const QcDesc d, const void *__restrict__ bin, S *__restrict__ A, const
     const float2 *prm = reinterpret_cast<const float2 *>(prm_l) + (size_t)j * d.L;
 #pragma unroll
     for (int l = 0; l < DCMAX; ++l) {
-        const int e = edge(l).x;
-        if (!REG && e < 0) continue;
+        // the edge again from the tables (cheap to recompute, unlike a shuffle result that would
+        // stay live from the gathers)
+        const int sh = (REG || l < d.L) ? d.shift[j * d.L + l] : -1;
+        if (!REG && sh < 0) continue;  // warp-uniform
+        int k = r + sh;
+        if (k >= d.p) k -= d.p;
+        const int e = d.eoff[j * d.L + l] + k;
         const float2 wo = __ldg(prm + l);
         const float mv = l == i1 ? mn2 : mn1;
         const float mag = fminf(fmaxf(fmaf(wo.x, mv, -wo.y), 0.0f), clip);
@@ -158,13 +170,15 @@ nm_vn_fwd(const QcDesc d, const S *__restrict__ A, const float *__restrict__ mu,
         if (pk * 32 + lane < B) lsum = softplusf(-tot) * zinv;
     }
     if (acc) {
+        // this block's sum is added to its own partial (the launches of the iterations follow one
+        // another on the stream, so no atomic is needed and the total does not depend on timing)
         for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
         if (lane == 0) red[warp] = lsum;
         __syncthreads();
         if (threadIdx.x == 0) {
             double s = 0.0;
             for (int w = 0; w < kWarps; ++w) s += red[w];
-            if (s != 0.0) atomicAdd(acc, s);
+            acc[(size_t)blockIdx.y * gridDim.x + blockIdx.x] += s;
         }
     }
 }
@@ -349,7 +363,24 @@ nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict_
         if (sg[i] != 0.0f) atomicAdd(grad_l + i, sg[i]);
 }
 
-__global__ void nm_loss_out(const double *acc, float *out) { *out = (float)*acc; }
+// the loss: the partial sums added in a fixed order (one block of 1024 threads)
+__global__ void __launch_bounds__(1024) nm_loss_out(const double *__restrict__ part, long long np, float *out) {
+    __shared__ double sh[1024];
+    double t = 0.0;
+    for (long long i = threadIdx.x; i < np; i += blockDim.x) t += part[i];
+    sh[threadIdx.x] = t;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = (float)sh[0];
+}
+
+// partial loss sums of the variable step: one per block of its grid ((N + 7) / 8, P)
+static size_t nm_loss_parts(ldpc_code c, const ldpc_noms_state &w) {
+    return (size_t)((c->d.N + kWarps - 1) / kWarps) * (w.cap_frames / 32);
+}
 
 // ---------------------------------------------------------------------------
 // host orchestration
@@ -365,32 +396,41 @@ static ldpc_status nm_alloc(ldpc_code c, ldpc_noms_state &w, size_t frames, size
     if (fr > w.cap_frames) {
         cudaDeviceSynchronize();
         cudaFree(w.mu); cudaFree(w.ping[0]); cudaFree(w.ping[1]); cudaFree(w.A); cudaFree(w.GA); cudaFree(w.GB);
-        cudaFree(w.posts); cudaFree(w.ckpt); cudaFree(w.seg);
-        w.posts = nullptr;
-        w.ckpt = w.seg = nullptr;
-        w.cap_nck = w.cap_seg = w.cap_T = 0;
+        cudaFree(w.posts); cudaFree(w.ckpt); cudaFree(w.seg); cudaFree(w.acc);
+        // nothing is held until every buffer of the new size exists (a failed call leaves no
+        // capacity behind that the next call would trust)
+        w.mu = w.A = w.GA = w.GB = w.posts = nullptr;
+        w.ping[0] = w.ping[1] = w.ckpt = w.seg = nullptr;
+        w.acc = nullptr;
+        w.cap_frames = w.cap_nck = w.cap_seg = w.cap_T = 0;
+        const size_t np = (size_t)((N + kWarps - 1) / kWarps) * (fr / 32);
         if (cudaMalloc(&w.mu, N * fr * 4) || cudaMalloc(&w.ping[0], E * fr * 4) || cudaMalloc(&w.ping[1], E * fr * 4) ||
-            cudaMalloc(&w.A, E * fr * 4) || cudaMalloc(&w.GA, E * fr * 4) || cudaMalloc(&w.GB, E * fr * 4))
+            cudaMalloc(&w.A, E * fr * 4) || cudaMalloc(&w.GA, E * fr * 4) || cudaMalloc(&w.GB, E * fr * 4) ||
+            cudaMalloc(&w.acc, np * sizeof(double)))
             return fail();
-        if (!w.acc && cudaMalloc(&w.acc, sizeof(double))) return fail();
         w.cap_frames = fr;
     }
     if (T > w.cap_T) {
         cudaDeviceSynchronize();
         cudaFree(w.posts);
         w.posts = nullptr;
+        w.cap_T = 0;
         if (cudaMalloc(&w.posts, T * N * w.cap_frames * 4)) return fail();
         w.cap_T = T;
     }
     if (nck > w.cap_nck) {
         cudaDeviceSynchronize();
         cudaFree(w.ckpt);
+        w.ckpt = nullptr;
+        w.cap_nck = 0;
         if (cudaMalloc(&w.ckpt, nck * E * w.cap_frames * 4)) return fail();
         w.cap_nck = nck;
     }
     if (nseg > w.cap_seg) {
         cudaDeviceSynchronize();
         cudaFree(w.seg);
+        w.seg = nullptr;
+        w.cap_seg = 0;
         if (cudaMalloc(&w.seg, nseg * E * w.cap_frames * 4)) return fail();
         w.cap_seg = nseg;
     }
@@ -461,7 +501,7 @@ static float *nm_post(ldpc_code c, ldpc_noms_state &w, int l) {  // post^(l), l 
 
 template <typename S>
 static ldpc_status nm_forward(ldpc_code c, ldpc_noms_state &w, cudaStream_t s) {
-    LDPC_CUDA_TRY(cudaMemsetAsync(w.acc, 0, sizeof(double), s));
+    LDPC_CUDA_TRY(cudaMemsetAsync(w.acc, 0, nm_loss_parts(c, w) * sizeof(double), s));
     const void *prev = w.mu;
     bool from_mu = true;
     for (int l = 1; l <= w.T; ++l) {
@@ -598,6 +638,7 @@ ldpc_status ldpc_noms_forward(ldpc_code c, const float *llr, int32_t B, int32_t 
         }
     }
     ldpc_noms_state &w = *c->noms;
+    w.have_forward = false;  // set again only once this forward has been queued in full
     const int nck = (T - 1) / ckpt_every;
     ldpc_status st =
         nm_alloc(c, w, (size_t)B, (size_t)std::max(nck, 1), (size_t)std::max(ckpt_every - 1, 1), (size_t)T);
@@ -614,7 +655,7 @@ ldpc_status ldpc_noms_forward(ldpc_code c, const float *llr, int32_t B, int32_t 
     if (st != LDPC_OK) return st;
     st = msg == LDPC_MSG_F16 ? nm_forward<__half>(c, w, s) : nm_forward<float>(c, w, s);
     if (st != LDPC_OK) return st;
-    nm_loss_out<<<1, 1, 0, s>>>(w.acc, loss);
+    nm_loss_out<<<1, 1024, 0, s>>>(w.acc, (long long)nm_loss_parts(c, w), loss);
     count_launch();
     if (post) {
         st = unpack_frames_w32(nm_post(c, w, T), post, B, c->d.N, s);
