@@ -423,27 +423,22 @@ vn_pipe_kernel(const QcDesc d, uint32_t *__restrict__ msg, uint32_t *__restrict_
                     if (e >= 0) cp_async16(dst + St::AL + (t0 + grp) * 32 + sub * 4, gmsg + (size_t)e * 32 + sub * 4);
                 }
             } else {
-                // edge packages: kNV * JMAX of them
+                // edge packages: kNV * JMAX of them; lane t computes edge t's offset once and the
+                // copies take it by shuffle
+                if (lane < kNV * JMAX) {
+                    const int i = lane / JMAX, jj = lane - i * JMAX;
+                    int l = l0, k = k0 + i;
+                    if (k >= d.p) k -= d.p, ++l;
+                    if ((EVEN || n0 + i < d.N) && (REG || (jj < d.J && s_sh[jj * d.L + l] >= 0)))
+                        mine = s_eo[jj * d.L + l] + k;
+                }
 #pragma unroll
                 for (int t0 = 0; t0 < kNV * JMAX; t0 += 4) {
                     const int t = t0 + grp;
-                    const int i = t / JMAX, jj = t - i * JMAX;
-                    const int n = n0 + i;
-                    int l = l0, k = k0 + i;
-                    if (k >= d.p) k -= d.p, ++l;
-                    if (((kNV * JMAX) % 4 == 0 || t < kNV * JMAX) && (EVEN || n < d.N) && (REG || jj < d.J)) {
-                        if (REG || s_sh[jj * d.L + l] >= 0)
-                            cp_async16(dst + St::AL + (i * JMAX + jj) * 32 + sub * 4,
-                                       gmsg + (size_t)(s_eo[jj * d.L + l] + k) * 32 + sub * 4);
-                    }
+                    const int e = __shfl_sync(0xffffffffu, mine, t & 31);
+                    if (((kNV * JMAX) % 4 == 0 || t < kNV * JMAX) && ((REG && EVEN) || e >= 0))
+                        cp_async16(dst + St::AL + t * 32 + sub * 4, gmsg + (size_t)e * 32 + sub * 4);
                 }
-            }
-            if (!SPARSE && lane < kNV * JMAX) {
-                const int i = lane / JMAX, jj = lane - i * JMAX;
-                int l = l0, k = k0 + i;
-                if (k >= d.p) k -= d.p, ++l;
-                if ((EVEN || n0 + i < d.N) && (REG || (jj < d.J && s_sh[jj * d.L + l] >= 0)))
-                    mine = s_eo[jj * d.L + l] + k;
             }
             if (lane < kNV * V) {
                 const int i = lane / V, v = lane - i * V;
