@@ -120,31 +120,31 @@ bcn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                 const uint32_t *gsrc = FIRST ? mu + C.mu + (size_t)tl.pk * C.N * St::MUW
                                              : msg + C.msg + (size_t)tl.pk * C.E * 32;
                 const int g = lane >> 3, sub = lane & 7;
-#pragma unroll
-                for (int q = 0; q < kBDC / 4; ++q) {
-                    const int l = 4 * q + g;
-                    const int sh = l < C.L ? __ldg(shtab + C.tab + j * C.L + l) : -1;
-                    int o = -1;
-                    if (sh >= 0) {
-                        int k = r + sh;
-                        if (k >= C.p) k -= C.p;
-                        o = __ldg(eotab + C.tab + j * C.L + l) + k;
-                        if (FIRST) {
-                            const int n = l * C.p + k;
-#pragma unroll
-                            for (int h = 0; h < St::MUW / 32; ++h)
-                                b_cp16(dst + l * St::SEGW + h * 32 + sub * 4, gsrc + (size_t)n * St::MUW + h * 32 + sub * 4);
-                        } else {
-                            b_cp16(dst + l * 32 + sub * 4, gsrc + (size_t)o * 32 + sub * 4);
-                        }
-                    }
-                }
+                // lane l looks up edge l of the row once (its offset, and its variable for FIRST);
+                // the copies take them by shuffle
+                int my_n = 0;
                 if (lane < kBDC && lane < C.L) {
                     const int sh = __ldg(shtab + C.tab + j * C.L + lane);
                     if (sh >= 0) {
                         int k = r + sh;
                         if (k >= C.p) k -= C.p;
                         mine = __ldg(eotab + C.tab + j * C.L + lane) + k;
+                        my_n = lane * C.p + k;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kBDC / 4; ++q) {
+                    const int l = 4 * q + g;
+                    const int o = __shfl_sync(0xffffffffu, mine, l);
+                    if (FIRST) {
+                        const int n = __shfl_sync(0xffffffffu, my_n, l);
+                        if (o >= 0) {
+#pragma unroll
+                            for (int h = 0; h < St::MUW / 32; ++h)
+                                b_cp16(dst + l * St::SEGW + h * 32 + sub * 4, gsrc + (size_t)n * St::MUW + h * 32 + sub * 4);
+                        }
+                    } else if (o >= 0) {
+                        b_cp16(dst + l * 32 + sub * 4, gsrc + (size_t)o * 32 + sub * 4);
                     }
                 }
                 if (lane < V) b_cp4(dst + St::FL + lane, flags + C.flags + (size_t)tl.pk * 5 * V + lane);
@@ -410,35 +410,29 @@ bvn_kernel(const BCode *__restrict__ codes, const int *__restrict__ shtab, const
                 const uint32_t *gmsg = msg + C.msg + (size_t)tl.pk * C.E * 32;
                 const uint32_t *gmu = mu + C.mu + (size_t)tl.pk * C.N * St::MUW;
                 const int grp = lane >> 3, sub = lane & 7;
-#pragma unroll
-                for (int s0 = 0; s0 < NSEG; s0 += 4) {
-                    const int s = s0 + grp;
-                    if (s < kBNV * MU_SEGS) {
-                        const int i = s / MU_SEGS, h = s - i * MU_SEGS;
-                        const int n = n0 + i;
-                        if (n < C.N)
-                            b_cp16(dst + St::MU + i * St::MUW + h * 32 + sub * 4,
-                                   gmu + (size_t)n * St::MUW + h * 32 + sub * 4);
-                    } else if (s < NSEG) {
-                        const int t = s - kBNV * MU_SEGS;
-                        const int i = t / kBJ, jj = t - i * kBJ;
-                        const int n = n0 + i;
-                        int l = l0, k = k0 + i;
-                        if (k >= C.p) k -= C.p, ++l;
-                        if (n < C.N && jj < C.J) {
-                            const int sh = __ldg(shtab + C.tab + jj * C.L + l);
-                            if (sh >= 0)
-                                b_cp16(dst + St::AL + (i * kBJ + jj) * 32 + sub * 4,
-                                       gmsg + (size_t)(__ldg(eotab + C.tab + jj * C.L + l) + k) * 32 + sub * 4);
-                        }
-                    }
-                }
+                // lane t < kBNV * kBJ looks up edge t's offset once; the copies take it by shuffle
                 if (lane < kBNV * kBJ) {
                     const int i = lane / kBJ, jj = lane - i * kBJ;
                     int l = l0, k = k0 + i;
                     if (k >= C.p) k -= C.p, ++l;
                     if (n0 + i < C.N && jj < C.J && __ldg(shtab + C.tab + jj * C.L + l) >= 0)
                         mine = __ldg(eotab + C.tab + jj * C.L + l) + k;
+                }
+#pragma unroll
+                for (int s0 = 0; s0 < NSEG; s0 += 4) {
+                    const int s = s0 + grp;
+                    // the segment index is warp-uniform per group of 8 lanes; the shuffle runs on all lanes
+                    const int t = s - kBNV * MU_SEGS;
+                    const int o = __shfl_sync(0xffffffffu, mine, t >= 0 && t < kBNV * kBJ ? t : 0);
+                    if (s < kBNV * MU_SEGS) {
+                        const int i = s / MU_SEGS, h = s - i * MU_SEGS;
+                        const int n = n0 + i;
+                        if (n < C.N)
+                            b_cp16(dst + St::MU + i * St::MUW + h * 32 + sub * 4,
+                                   gmu + (size_t)n * St::MUW + h * 32 + sub * 4);
+                    } else if (s < NSEG && o >= 0) {
+                        b_cp16(dst + St::AL + t * 32 + sub * 4, gmsg + (size_t)o * 32 + sub * 4);
+                    }
                 }
                 if (lane < kBNV * V) {
                     const int i = lane / V, v = lane - i * V;

@@ -185,16 +185,16 @@ cc_cn_pipe_kernel(const QcDesc d, CcDesc g, CcGeo q, uint32_t *__restrict__ msg,
             uint32_t *dst = ring + slot * WORDS;
             const uint32_t *base = o.i == 0 ? reinterpret_cast<const uint32_t *>(mu) : msg;
             const int grp = lane >> 3, sub = lane & 7;
+            // lane e < NE looks up edge e once (the line it reads and the one it writes); the
+            // copies take the read lines by shuffle
+            int my_src = -1;
+            if (lane < NE) edge(o, lane, my_src, mine);
 #pragma unroll
             for (int e0 = 0; e0 < NE; e0 += 4) {
                 const int e = e0 + grp;
-                int src = -1, dl;
-                if (NE % 4 == 0 || e < NE) edge(o, e, src, dl);
-                if (src >= 0) cp_async16(dst + e * 32 + sub * 4, base + (size_t)src * 32 + sub * 4);
-            }
-            if (lane < NE) {
-                int src;
-                edge(o, lane, src, mine);
+                const int src = __shfl_sync(0xffffffffu, my_src, e & 31);
+                if ((NE % 4 == 0 || e < NE) && src >= 0)
+                    cp_async16(dst + e * 32 + sub * 4, base + (size_t)src * 32 + sub * 4);
             }
         }
         cp_async_commit();
@@ -328,13 +328,14 @@ cc_vn_pipe_kernel(const QcDesc d, CcDesc g, CcGeo q, uint32_t *__restrict__ msg,
                 cp_async16(dst + MU + grp * 32 + sub * 4,
                            reinterpret_cast<const uint32_t *>(mu) +
                                ((size_t)(o.fs * g.P + o.pk) * g.c + o.v0 + grp) * 32 + sub * 4);
+            // lane tt looks up edge (variable tt / JMAX, row tt % JMAX) once; the copies take it by shuffle
+            if (lane < kCcNV * JMAX) mine = eline(o, lane / JMAX, lane % JMAX);
 #pragma unroll
             for (int qq = 0; qq < JMAX; ++qq) {
-                const int tt = 4 * qq + grp;  // (variable tt / JMAX, row tt % JMAX)
-                const int e = eline(o, tt / JMAX, tt % JMAX);
+                const int tt = 4 * qq + grp;
+                const int e = __shfl_sync(0xffffffffu, mine, tt & 31);
                 if (e >= 0) cp_async16(dst + AL + tt * 32 + sub * 4, msg + (size_t)e * 32 + sub * 4);
             }
-            if (lane < kCcNV * JMAX) mine = eline(o, lane / JMAX, lane % JMAX);
         }
         cp_async_commit();
         return mine;
