@@ -41,7 +41,7 @@ METRIC = "decoded info Mbit/s (n=18360, 30 iters) at BER matching FP64 oracle"
 # workload of this file (FP32 messages, early stop, 3.5 dB, 4096 slots, 131072 frames),
 # with the hash of the kernel sources it was measured on: reported only while the
 # sources hash the same (null as soon as a kernel changes, until re-measured).
-CN_DRAM_BYTES_PER_LAUNCH = {"f32": (2277.8e6, "e8628aa1c32a9478")}
+CN_DRAM_BYTES_PER_LAUNCH = {"f32": (2277.8e6, "f63b990e626641ef")}
 KERNEL_SOURCES = ("qc_pipe.cu", "qc_device.cuh", "ldpc_internal.cuh")
 
 
