@@ -37,14 +37,30 @@ struct ldpc_noms_state {
 
 namespace ldpc {
 
-template <typename S> struct Store;
-template <> struct Store<float> {
-    static __device__ __forceinline__ float ld(const float *p) { return *p; }
-    static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+// A lane's 32-bit word of one edge package: one FP32 frame (S = float, packages of
+// 32 frames), or two binary16 frames (S = __half, packages of 64 frames, lane l
+// holding frames 2l and 2l + 1 -- the FP16 decoder's layout).  Per-frame FP32
+// arrays (channel LLRs, posteriors, adjoints) follow the same order:
+// [..][32 lanes][V frames].
+template <typename S> struct Word;
+template <> struct Word<float> {
+    static constexpr int V = 1;
+    static constexpr uint32_t INF = 0x7f800000u;  // +inf
+    static __device__ __forceinline__ void ld(uint32_t w, float *x) { x[0] = __uint_as_float(w); }
+    static __device__ __forceinline__ uint32_t pack(const float *x) { return __float_as_uint(x[0]); }
 };
-template <> struct Store<__half> {
-    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(*p); }
-    static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+template <> struct Word<__half> {
+    static constexpr int V = 2;
+    static constexpr uint32_t INF = 0x7c007c00u;  // +inf twice
+    static __device__ __forceinline__ void ld(uint32_t w, float *x) {
+        const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w));
+        x[0] = f.x;
+        x[1] = f.y;
+    }
+    static __device__ __forceinline__ uint32_t pack(const float *x) {
+        const __half2 h = __floats2half2_rn(x[0], x[1]);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    }
 };
 
 // one exponential each: softplus(x) = max(x, 0) + log1p(e^-|x|); sigmoid from e = e^-|x|
@@ -52,13 +68,6 @@ __device__ __forceinline__ float softplusf(float x) { return fmaxf(x, 0.0f) + lo
 __device__ __forceinline__ float sigmoidf(float x) {
     const float e = __expf(-fabsf(x));
     return x >= 0.0f ? 1.0f / (1.0f + e) : e / (1.0f + e);
-}
-
-// beta^(l-1) of edge (block offset eo + k) and variable n, from mu (l = 1) or a store
-template <typename S, bool FROM_MU>
-__device__ __forceinline__ float nm_beta(const void *src, const QcDesc &d, int pk, int eidx, int n, int lane) {
-    if (FROM_MU) return reinterpret_cast<const float *>(src)[((size_t)pk * d.N + n) * 32 + lane];
-    return Store<S>::ld(reinterpret_cast<const S *>(src) + ((size_t)pk * d.E + eidx) * 32 + lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -71,11 +80,13 @@ __device__ __forceinline__ float nm_beta(const void *src, const QcDesc &d, int p
 // and all DCMAX loads of a row are in flight together.  Only the two smallest magnitudes,
 // the index of the first smallest and the sign bits outlive the gathers: the other edges'
 // minimum is mn2 for that index and mn1 for every other edge (on a tie mn2 == mn1).  Lane l
-// holds slot l's edge index and the gathers take it by shuffle.
+// holds slot l's edge index and the gathers take it by shuffle.  From the channel LLRs
+// (FROM_MU, FP32) the frames of a lane word are done one after the other.
 template <int DCMAX, typename S, bool FROM_MU, bool REG>
-__global__ void __launch_bounds__(kWarps * 32, NM_FWD_MINB)
-nm_cn_fwd(const QcDesc d, const void *__restrict__ bin, S *__restrict__ A, const float *__restrict__ prm_l,
+__global__ void __launch_bounds__(kWarps * 32, FROM_MU ? 3 : NM_FWD_MINB)
+nm_cn_fwd(const QcDesc d, const void *__restrict__ bin, uint32_t *__restrict__ A, const float *__restrict__ prm_l,
           float clip, int P) {
+    constexpr int V = Word<S>::V;
     const int lane = threadIdx.x & 31;
     const int m = blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int pk = blockIdx.y;
@@ -90,40 +101,97 @@ nm_cn_fwd(const QcDesc d, const void *__restrict__ bin, S *__restrict__ A, const
         my_e = d.eoff[j * d.L + lane] + k;
         my_n = lane * d.p + k;
     }
-    float x[DCMAX];
-#pragma unroll
-    for (int l = 0; l < DCMAX; ++l) {
-        const int e = __shfl_sync(0xffffffffu, my_e, l);
-        const int n = FROM_MU ? __shfl_sync(0xffffffffu, my_n, l) : 0;
-        x[l] = (!REG && e < 0) ? INFINITY : nm_beta<S, FROM_MU>(bin, d, pk, e, n, lane);
-    }
-    uint32_t neg = 0u;
-    float mn1 = INFINITY, mn2 = INFINITY;
-    int i1 = -1;
-#pragma unroll
-    for (int l = 0; l < DCMAX; ++l) {
-        const float a = fabsf(x[l]);  // absent edges: +inf, never below mn1
-        neg |= (x[l] < 0.0f ? 1u : 0u) << l;
-        const bool lo = a < mn1;
-        mn2 = lo ? mn1 : fminf(mn2, a);
-        i1 = lo ? l : i1;
-        mn1 = lo ? a : mn1;
-    }
-    const uint32_t par = __popc(neg) & 1u;
     const float2 *prm = reinterpret_cast<const float2 *>(prm_l) + (size_t)j * d.L;
-#pragma unroll
-    for (int l = 0; l < DCMAX; ++l) {
-        // the edge again from the tables (cheap to recompute, unlike a shuffle result that would
-        // stay live from the gathers)
+    // the edge of slot l again from the tables (cheap to recompute, unlike a shuffle result that
+    // would stay live from the gathers); -1: absent
+    auto edge = [&](int l) -> int {
         const int sh = (REG || l < d.L) ? d.shift[j * d.L + l] : -1;
-        if (!REG && sh < 0) continue;  // warp-uniform
+        if (!REG && sh < 0) return -1;
         int k = r + sh;
         if (k >= d.p) k -= d.p;
-        const int e = d.eoff[j * d.L + l] + k;
-        const float2 wo = __ldg(prm + l);
-        const float mv = l == i1 ? mn2 : mn1;
-        const float mag = fminf(fmaxf(fmaf(wo.x, mv, -wo.y), 0.0f), clip);
-        Store<S>::st(A + ((size_t)pk * d.E + e) * 32 + lane, (par ^ ((neg >> l) & 1u)) ? -mag : mag);
+        return d.eoff[j * d.L + l] + k;
+    };
+    if constexpr (FROM_MU) {
+        const float *mu = reinterpret_cast<const float *>(bin);
+#pragma unroll 1
+        for (int v = 0; v < V; ++v) {
+            float x[DCMAX];
+#pragma unroll
+            for (int l = 0; l < DCMAX; ++l) {
+                const int e = __shfl_sync(0xffffffffu, my_e, l);
+                const int n = __shfl_sync(0xffffffffu, my_n, l);
+                x[l] = (!REG && e < 0) ? INFINITY : mu[(((size_t)pk * d.N + n) * 32 + lane) * V + v];
+            }
+            uint32_t neg = 0u;
+            float mn1 = INFINITY, mn2 = INFINITY;
+            int i1 = -1;
+#pragma unroll
+            for (int l = 0; l < DCMAX; ++l) {
+                const float a = fabsf(x[l]);  // absent edges: +inf, never below mn1
+                neg |= (x[l] < 0.0f ? 1u : 0u) << l;
+                const bool lo = a < mn1;
+                mn2 = lo ? mn1 : fminf(mn2, a);
+                i1 = lo ? l : i1;
+                mn1 = lo ? a : mn1;
+            }
+            const uint32_t par = __popc(neg) & 1u;
+#pragma unroll
+            for (int l = 0; l < DCMAX; ++l) {
+                const int e = edge(l);
+                if (!REG && e < 0) continue;  // warp-uniform
+                const float2 wo = __ldg(prm + l);
+                const float mv = l == i1 ? mn2 : mn1;
+                const float mag = fminf(fmaxf(fmaf(wo.x, mv, -wo.y), 0.0f), clip);
+                const float out = (par ^ ((neg >> l) & 1u)) ? -mag : mag;
+                const size_t w = ((size_t)pk * d.E + e) * 32 + lane;
+                if constexpr (V == 1) A[w] = __float_as_uint(out);
+                else reinterpret_cast<__half *>(A)[w * 2 + v] = __float2half_rn(out);
+            }
+        }
+    } else {
+        const uint32_t *bw = reinterpret_cast<const uint32_t *>(bin);
+        uint32_t xw[DCMAX];
+#pragma unroll
+        for (int l = 0; l < DCMAX; ++l) {
+            const int e = __shfl_sync(0xffffffffu, my_e, l);
+            xw[l] = (!REG && e < 0) ? Word<S>::INF : bw[((size_t)pk * d.E + e) * 32 + lane];
+        }
+        uint32_t neg[V];
+        float mn1[V], mn2[V];
+        int i1[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) neg[v] = 0u, mn1[v] = mn2[v] = INFINITY, i1[v] = -1;
+#pragma unroll
+        for (int l = 0; l < DCMAX; ++l) {
+            float x[V];
+            Word<S>::ld(xw[l], x);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const float a = fabsf(x[v]);
+                neg[v] |= (x[v] < 0.0f ? 1u : 0u) << l;
+                const bool lo = a < mn1[v];
+                mn2[v] = lo ? mn1[v] : fminf(mn2[v], a);
+                i1[v] = lo ? l : i1[v];
+                mn1[v] = lo ? a : mn1[v];
+            }
+        }
+        uint32_t par[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) par[v] = __popc(neg[v]) & 1u;
+#pragma unroll
+        for (int l = 0; l < DCMAX; ++l) {
+            const int e = edge(l);
+            if (!REG && e < 0) continue;  // warp-uniform
+            const float2 wo = __ldg(prm + l);
+            float out[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const float mv = l == i1[v] ? mn2[v] : mn1[v];
+                const float mag = fminf(fmaxf(fmaf(wo.x, mv, -wo.y), 0.0f), clip);
+                out[v] = (par[v] ^ ((neg[v] >> l) & 1u)) ? -mag : mag;
+            }
+            A[((size_t)pk * d.E + e) * 32 + lane] = Word<S>::pack(out);
+        }
     }
 }
 
@@ -132,8 +200,9 @@ nm_cn_fwd(const QcDesc d, const void *__restrict__ bin, S *__restrict__ A, const
 // ---------------------------------------------------------------------------
 template <int JMAX, typename S, bool REG>
 __global__ void __launch_bounds__(kWarps * 32)
-nm_vn_fwd(const QcDesc d, const S *__restrict__ A, const float *__restrict__ mu, S *__restrict__ bout,
+nm_vn_fwd(const QcDesc d, const uint32_t *__restrict__ A, const float *__restrict__ mu, uint32_t *__restrict__ bout,
           double *__restrict__ acc, float *__restrict__ post, float zinv, float clip, int P, int B) {
+    constexpr int V = Word<S>::V;
     __shared__ float red[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n = blockIdx.x * kWarps + warp;
@@ -141,33 +210,55 @@ nm_vn_fwd(const QcDesc d, const S *__restrict__ A, const float *__restrict__ mu,
     float lsum = 0.0f;
     if (n < d.N && pk < P) {
         const int l = (int)fdiv((uint32_t)n, d.divP), k = n - l * d.p;
-        const float mv = mu[((size_t)pk * d.N + n) * 32 + lane];
-        float a[JMAX];
+        const size_t fb = (((size_t)pk * d.N + n) * 32 + lane) * V;  // this lane's frames, per-frame arrays
+        float mv[V];
+        if constexpr (V == 1) mv[0] = mu[fb];
+        else {
+            const float2 m2 = *reinterpret_cast<const float2 *>(mu + fb);
+            mv[0] = m2.x;
+            mv[1] = m2.y;
+        }
+        float a[JMAX][V];
         int eid[JMAX];
-        float tot = mv;
 #pragma unroll
         for (int j = 0; j < JMAX; ++j) {
-            a[j] = 0.0f;
+#pragma unroll
+            for (int v = 0; v < V; ++v) a[j][v] = 0.0f;
             eid[j] = -1;
             if (!REG && (j >= d.J || d.shift[j * d.L + l] < 0)) continue;
             eid[j] = d.eoff[j * d.L + l] + k;
-            a[j] = Store<S>::ld(A + ((size_t)pk * d.E + eid[j]) * 32 + lane);
+            Word<S>::ld(A[((size_t)pk * d.E + eid[j]) * 32 + lane], a[j]);
         }
+        float tot[V];
 #pragma unroll
-        for (int j = 0; j < JMAX; ++j) tot += a[j];
+        for (int v = 0; v < V; ++v) {
+            tot[v] = mv[v];
+#pragma unroll
+            for (int j = 0; j < JMAX; ++j) tot[v] += a[j][v];
+        }
         if (bout) {
 #pragma unroll
             for (int j = 0; j < JMAX; ++j) {
                 if (!REG && eid[j] < 0) continue;
-                float s = mv;
+                float out[V];
 #pragma unroll
-                for (int j2 = 0; j2 < JMAX; ++j2)
-                    if (j2 != j) s += a[j2];
-                Store<S>::st(bout + ((size_t)pk * d.E + eid[j]) * 32 + lane, clipf(s, clip));
+                for (int v = 0; v < V; ++v) {
+                    float s = mv[v];
+#pragma unroll
+                    for (int j2 = 0; j2 < JMAX; ++j2)
+                        if (j2 != j) s += a[j2][v];
+                    out[v] = clipf(s, clip);
+                }
+                bout[((size_t)pk * d.E + eid[j]) * 32 + lane] = Word<S>::pack(out);
             }
         }
-        if (post) post[((size_t)pk * d.N + n) * 32 + lane] = tot;
-        if (pk * 32 + lane < B) lsum = softplusf(-tot) * zinv;
+        if (post) {
+            if constexpr (V == 1) post[fb] = tot[0];
+            else *reinterpret_cast<float2 *>(post + fb) = make_float2(tot[0], tot[1]);
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            if ((pk * 32 + lane) * V + v < B) lsum += softplusf(-tot[v]) * zinv;
     }
     if (acc) {
         // this block's sum is added to its own partial (the launches of the iterations follow one
@@ -192,37 +283,64 @@ nm_vn_fwd(const QcDesc d, const S *__restrict__ A, const float *__restrict__ mu,
 // ---------------------------------------------------------------------------
 template <int JMAX, typename S, bool REG>
 __global__ void __launch_bounds__(kWarps * 32)
-nm_vn_bwd(const QcDesc d, const float *__restrict__ post, const S *__restrict__ bl, const float *__restrict__ GB,
-          float *__restrict__ GA, float clip, float zinv, int P, int B) {
+nm_vn_bwd(const QcDesc d, const float *__restrict__ post, const uint32_t *__restrict__ bl,
+          const float *__restrict__ GB, float *__restrict__ GA, float clip, float zinv, int P, int B) {
+    constexpr int V = Word<S>::V;
     const int lane = threadIdx.x & 31;
     const int n = blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int pk = blockIdx.y;
     if (n >= d.N || pk >= P) return;
     const int l = (int)fdiv((uint32_t)n, d.divP), k = n - l * d.p;
-    const float tot = post[((size_t)pk * d.N + n) * 32 + lane];
-    float gbm[JMAX];
+    const size_t fb = (((size_t)pk * d.N + n) * 32 + lane) * V;
+    float tot[V];
+    if constexpr (V == 1) tot[0] = post[fb];
+    else {
+        const float2 t2 = *reinterpret_cast<const float2 *>(post + fb);
+        tot[0] = t2.x;
+        tot[1] = t2.y;
+    }
+    float gbm[JMAX][V];
     int eid[JMAX];
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
-        gbm[j] = 0.0f;
+#pragma unroll
+        for (int v = 0; v < V; ++v) gbm[j][v] = 0.0f;
         eid[j] = -1;
         if (!REG && (j >= d.J || d.shift[j * d.L + l] < 0)) continue;
         eid[j] = d.eoff[j * d.L + l] + k;
         // the adjoint of beta^(l)_e passes the clip only where it was inactive
         if (GB) {
-            const size_t x = ((size_t)pk * d.E + eid[j]) * 32 + lane;
-            if (fabsf(Store<S>::ld(bl + x)) < clip) gbm[j] = GB[x];
+            const size_t w = ((size_t)pk * d.E + eid[j]) * 32 + lane;
+            float b[V], g[V];
+            Word<S>::ld(bl[w], b);
+            if constexpr (V == 1) g[0] = GB[w];
+            else {
+                const float2 g2 = *reinterpret_cast<const float2 *>(GB + w * 2);
+                g[0] = g2.x;
+                g[1] = g2.y;
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                if (fabsf(b[v]) < clip) gbm[j][v] = g[v];
         }
     }
-    const float dpost = (pk * 32 + lane < B) ? -sigmoidf(-tot) * zinv : 0.0f;
+    float dpost[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) dpost[v] = ((pk * 32 + lane) * V + v < B) ? -sigmoidf(-tot[v]) * zinv : 0.0f;
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
         if (!REG && eid[j] < 0) continue;
-        float g = dpost;
+        float g[V];
 #pragma unroll
-        for (int j2 = 0; j2 < JMAX; ++j2)
-            if (j2 != j) g += gbm[j2];
-        GA[((size_t)pk * d.E + eid[j]) * 32 + lane] = g;
+        for (int v = 0; v < V; ++v) {
+            g[v] = dpost[v];
+#pragma unroll
+            for (int j2 = 0; j2 < JMAX; ++j2)
+                if (j2 != j) g[v] += gbm[j2][v];
+        }
+        const size_t w = ((size_t)pk * d.E + eid[j]) * 32 + lane;
+        if constexpr (V == 1) GA[w] = g[0];
+        else *reinterpret_cast<float2 *>(GA + w * 2) = make_float2(g[0], g[1]);
     }
 }
 
@@ -238,7 +356,8 @@ nm_vn_bwd(const QcDesc d, const float *__restrict__ post, const S *__restrict__ 
 // row) into block sums in shared memory, flushed once per block.  Lane l holds
 // slot l's shift and edge offset; a row's edge indices are computed once per row
 // (one per lane) and broadcast by shuffles.  REG: every block of the row is
-// present and L == DCMAX (no branches on absent slots).
+// present and L == DCMAX (no branches on absent slots).  The frames of a lane
+// word (two with binary16 messages) are done one after the other.
 // ---------------------------------------------------------------------------
 constexpr int kBwdRows = 16;
 #ifndef LDPC_NM_BWD_BLOCKS
@@ -251,6 +370,7 @@ __global__ void __launch_bounds__(kWarps * 32, kBwdBlocks)
 nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict__ GA, const float *__restrict__ prm_l,
           float *__restrict__ GB, float *__restrict__ grad_l, float clip, int P, int want_gb) {
     static_assert(DCMAX <= 32, "one lane per edge slot");
+    constexpr int V = Word<S>::V;
     __shared__ float sg[kMaxJ * kMaxL * 2];
     extern __shared__ float s_part[];
     for (int i = threadIdx.x; i < d.J * d.L * 2; i += blockDim.x) sg[i] = 0.0f;
@@ -281,6 +401,8 @@ nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict_
                 my_e = my_eo + k;
                 my_n = lane * d.p + k;
             }
+#pragma unroll 1
+            for (int v = 0; v < V; ++v) {  // the frames of the lane word
             // every load of the row first (beta^(l-1) and the adjoints of alpha^(l) do not depend on
             // each other): one memory round trip per row
             float xin[DCMAX], ga[DCMAX];
@@ -291,8 +413,13 @@ nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict_
                 ga[l] = 0.0f;
                 if (!REG && e < 0) continue;  // warp-uniform
                 const int n = FROM_MU ? __shfl_sync(0xffffffffu, my_n, l) : 0;
-                xin[l] = nm_beta<S, FROM_MU>(bin, d, pk, e, n, lane);
-                ga[l] = GA[(base + e) * 32 + lane];
+                if (FROM_MU)
+                    xin[l] = reinterpret_cast<const float *>(bin)[(((size_t)pk * d.N + n) * 32 + lane) * V + v];
+                else if (V == 1)
+                    xin[l] = reinterpret_cast<const float *>(bin)[(base + e) * 32 + lane];
+                else
+                    xin[l] = __half2float(reinterpret_cast<const __half *>(bin)[((base + e) * 32 + lane) * 2 + v]);
+                ga[l] = GA[((base + e) * 32 + lane) * V + v];
             }
             // the two smallest magnitudes and their slots (strict <: the lowest index among ties);
             // absent slots hold +inf and never qualify
@@ -338,8 +465,9 @@ nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict_
                     const int e = __shfl_sync(0xffffffffu, my_e, l);
                     if (!REG && e < 0) continue;  // warp-uniform
                     const float g = l == i1 ? g1 * s1 : (l == i2 ? g2 * s2 : 0.0f);
-                    GB[(base + e) * 32 + lane] = g;
+                    GB[((base + e) * 32 + lane) * V + v] = g;
                 }
+            }
             }
         }
         // warp sums of this item's gradients per circulant (j, l)
@@ -387,7 +515,7 @@ static size_t nm_loss_parts(ldpc_code c, const ldpc_noms_state &w) {
 // ---------------------------------------------------------------------------
 static ldpc_status nm_alloc(ldpc_code c, ldpc_noms_state &w, size_t frames, size_t nck, size_t nseg, size_t T) {
     const size_t E = c->d.E, N = c->d.N;
-    const size_t fr = (frames + 31) / 32 * 32;
+    const size_t fr = (frames + 63) / 64 * 64;  // whole packages of 32 or 64 frames
     auto fail = [&]() {
         cudaGetLastError();
         set_error("NOMS workspace allocation failed");
@@ -455,12 +583,12 @@ static ldpc_status nm_step_fwd(ldpc_code c, ldpc_noms_state &w, int l, const voi
 #define NM_CN(DC)                                                                                             \
     do {                                                                                                      \
         if (full && d.L == (DC)) {                                                                            \
-            if (from_mu) nm_cn_fwd<DC, S, true, true><<<cg, kWarps * 32, 0, s>>>(d, bin, (S *)w.A, prm, w.clip, w.P); \
-            else nm_cn_fwd<DC, S, false, true><<<cg, kWarps * 32, 0, s>>>(d, bin, (S *)w.A, prm, w.clip, w.P);        \
+            if (from_mu) nm_cn_fwd<DC, S, true, true><<<cg, kWarps * 32, 0, s>>>(d, bin, (uint32_t *)w.A, prm, w.clip, w.P); \
+            else nm_cn_fwd<DC, S, false, true><<<cg, kWarps * 32, 0, s>>>(d, bin, (uint32_t *)w.A, prm, w.clip, w.P);        \
         } else if (from_mu) {                                                                                 \
-            nm_cn_fwd<DC, S, true, false><<<cg, kWarps * 32, 0, s>>>(d, bin, (S *)w.A, prm, w.clip, w.P);           \
+            nm_cn_fwd<DC, S, true, false><<<cg, kWarps * 32, 0, s>>>(d, bin, (uint32_t *)w.A, prm, w.clip, w.P);           \
         } else {                                                                                              \
-            nm_cn_fwd<DC, S, false, false><<<cg, kWarps * 32, 0, s>>>(d, bin, (S *)w.A, prm, w.clip, w.P);          \
+            nm_cn_fwd<DC, S, false, false><<<cg, kWarps * 32, 0, s>>>(d, bin, (uint32_t *)w.A, prm, w.clip, w.P);          \
         }                                                                                                     \
     } while (0)
     if (d.L <= 8) NM_CN(8);
@@ -472,13 +600,13 @@ static ldpc_status nm_step_fwd(ldpc_code c, ldpc_noms_state &w, int l, const voi
     if (bout || loss || post) {
         double *acc = loss ? w.acc : nullptr;
         if (full && d.J == 4)
-            nm_vn_fwd<4, S, true><<<vg, kWarps * 32, 0, s>>>(d, (const S *)w.A, w.mu, (S *)bout, acc, post, zinv, w.clip,
+            nm_vn_fwd<4, S, true><<<vg, kWarps * 32, 0, s>>>(d, (const uint32_t *)w.A, w.mu, (uint32_t *)bout, acc, post, zinv, w.clip,
                                                              w.P, w.B);
         else if (d.J <= 4)
-            nm_vn_fwd<4, S, false><<<vg, kWarps * 32, 0, s>>>(d, (const S *)w.A, w.mu, (S *)bout, acc, post, zinv, w.clip,
+            nm_vn_fwd<4, S, false><<<vg, kWarps * 32, 0, s>>>(d, (const uint32_t *)w.A, w.mu, (uint32_t *)bout, acc, post, zinv, w.clip,
                                                               w.P, w.B);
         else
-            nm_vn_fwd<8, S, false><<<vg, kWarps * 32, 0, s>>>(d, (const S *)w.A, w.mu, (S *)bout, acc, post, zinv, w.clip,
+            nm_vn_fwd<8, S, false><<<vg, kWarps * 32, 0, s>>>(d, (const uint32_t *)w.A, w.mu, (uint32_t *)bout, acc, post, zinv, w.clip,
                                                               w.P, w.B);
         count_launch();
     }
@@ -561,7 +689,7 @@ static ldpc_status nm_backward(ldpc_code c, ldpc_noms_state &w, float *grad, cud
         // the adjoints of alpha^(l) (from the saved posteriors and beta^(l)), then of the parameters
         // and beta^(l-1)
         const float *gbin = l == w.T ? nullptr : w.GB;
-        const S *bl = l == w.T ? nullptr : (const S *)bnext;
+        const uint32_t *bl = l == w.T ? nullptr : (const uint32_t *)bnext;
         const float *pl = nm_post(c, w, l);
         if (full && d.J == 4)
             nm_vn_bwd<4, S, true><<<vg, kWarps * 32, 0, s>>>(d, pl, bl, gbin, w.GA, w.clip, zinv, w.P, w.B);
@@ -604,8 +732,8 @@ static ldpc_status nm_backward(ldpc_code c, ldpc_noms_state &w, float *grad, cud
 }
 
 // pack [B][N] -> [P][N][32] with clipping (qc_decode.cu)
-ldpc_status pack_frames_w32(const float *llr, float *dst, int gamma, int N, float clip, cudaStream_t s);
-ldpc_status unpack_frames_w32(const float *src, float *dst, int gamma, int N, cudaStream_t s);
+ldpc_status pack_frames_w(const float *llr, float *dst, int gamma, int N, float clip, int W, cudaStream_t s);
+ldpc_status unpack_frames_w(const float *src, float *dst, int gamma, int N, int W, cudaStream_t s);
 
 }  // namespace ldpc
 
@@ -646,19 +774,20 @@ ldpc_status ldpc_noms_forward(ldpc_code c, const float *llr, int32_t B, int32_t 
     w.B = B;
     w.T = T;
     w.k = ckpt_every;
-    w.P = (B + 31) / 32;
+    const int W = msg == LDPC_MSG_F16 ? 64 : 32;  // frames per package: one or two per lane word
+    w.P = (B + W - 1) / W;
     w.msg = msg;
     w.clip = clip;
     w.params = params;
     cudaStream_t s = (cudaStream_t)stream;
-    st = pack_frames_w32(llr, w.mu, B, c->d.N, clip, s);
+    st = pack_frames_w(llr, w.mu, B, c->d.N, clip, W, s);
     if (st != LDPC_OK) return st;
     st = msg == LDPC_MSG_F16 ? nm_forward<__half>(c, w, s) : nm_forward<float>(c, w, s);
     if (st != LDPC_OK) return st;
     nm_loss_out<<<1, 1024, 0, s>>>(w.acc, (long long)nm_loss_parts(c, w), loss);
     count_launch();
     if (post) {
-        st = unpack_frames_w32(nm_post(c, w, T), post, B, c->d.N, s);
+        st = unpack_frames_w(nm_post(c, w, T), post, B, c->d.N, W, s);
         if (st != LDPC_OK) return st;
     }
     w.have_forward = true;

@@ -373,20 +373,21 @@ __global__ void channel_frames_kernel(float *__restrict__ out, int N, int gamma,
     }
 }
 
-// [gamma][N] <-> [P][N][32] for the learned min-sum state (packages of 32 frames)
-ldpc_status pack_frames_w32(const float *llr, float *dst, int gamma, int N, float clip, cudaStream_t s) {
-    const int P = (gamma + 31) / 32;
-    dim3 blk(32, 8), grd((N + 31) / 32, P);
+// [gamma][N] <-> [P][N][W] for the learned min-sum state (packages of W = 32 or 64 frames;
+// frames beyond gamma up to the last package's end are set to +clip)
+ldpc_status pack_frames_w(const float *llr, float *dst, int gamma, int N, float clip, int W, cudaStream_t s) {
+    const int P = (gamma + W - 1) / W;
+    dim3 blk(32, 8), grd((N + 31) / 32, (P * W + 31) / 32);
     count_launch();
-    pack_llr_kernel<float><<<grd, blk, 0, s>>>(llr, dst, gamma, N, 32, P * 32, clip, 1.0f, clip);
+    pack_llr_kernel<float><<<grd, blk, 0, s>>>(llr, dst, gamma, N, W, P * W, clip, 1.0f, clip);
     LDPC_CUDA_TRY(cudaGetLastError());
     return LDPC_OK;
 }
 
-ldpc_status unpack_frames_w32(const float *src, float *dst, int gamma, int N, cudaStream_t s) {
+ldpc_status unpack_frames_w(const float *src, float *dst, int gamma, int N, int W, cudaStream_t s) {
     dim3 blk(32, 8), grd((N + 31) / 32, (gamma + 31) / 32);
     count_launch();
-    unpack_post_kernel<<<grd, blk, 0, s>>>(src, dst, gamma, N, 32);
+    unpack_post_kernel<<<grd, blk, 0, s>>>(src, dst, gamma, N, W);
     LDPC_CUDA_TRY(cudaGetLastError());
     return LDPC_OK;
 }

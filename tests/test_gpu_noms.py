@@ -108,7 +108,7 @@ def test_noms_fp16_storage_gradient(pkg, J, L, p):
     gradient jumps wherever rounding changes the arg-min edge, so that comparison is not element-wise."""
     shifts, rp, col, cb = setup(J, L, p, 2)
     code = pkg.QCCode(shifts, p)
-    T, B = 5, 64
+    T, B = 5, 70  # two packages of 64 frames, the second with 6
     prm = rand_params(T, J * L, 4)
     mu = synth.gaussian_llrs(B, code.N, seed=6, ebn0_db=1.5 + 0.5 * (L > 8), rate=1 - J / L)
     prm_d = torch.from_numpy(prm).cuda()
