@@ -491,6 +491,182 @@ nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict_
         if (sg[i] != 0.0f) atomicAdd(grad_l + i, sg[i]);
 }
 
+// The backward check step for iterations l >= 2 (inputs beta^(l-1) from a message
+// store): the same arithmetic as nm_cn_bwd, with the row's inputs staged in shared
+// memory.  Each warp keeps the next row's beta words and adjoints of alpha in flight
+// in a two-stage ring, copied with cp.async (16 bytes per lane, completion tracked by
+// cp.async groups), while it works on the current row out of shared memory; both
+// frames of a binary16 lane word are done together, and the partial gradients per
+// edge slot stay in registers.  Blocks of four warps, three per SM.
+constexpr int kRingWarps = 4;
+
+template <int DCMAX, typename S, bool REG>
+__global__ void __launch_bounds__(kRingWarps * 32, 3)
+nm_cn_bwd_ring(const QcDesc d, const uint32_t *__restrict__ bw, const float *__restrict__ GA,
+               const float *__restrict__ prm_l, float *__restrict__ GB, float *__restrict__ grad_l, float clip, int P,
+               int want_gb) {
+    static_assert(DCMAX <= 32 && DCMAX % 4 == 0, "one lane per edge slot, slots in groups of four");
+    constexpr int V = Word<S>::V;
+    constexpr int SB = DCMAX * 32;      // words: the beta packages of a row
+    constexpr int SG = DCMAX * 32 * V;  // floats: the adjoint packages of a row
+    constexpr int STAGE = SB + SG;
+    __shared__ float sg[kMaxJ * kMaxL * 2];
+    extern __shared__ __align__(16) uint32_t ring_all[];
+    for (int i = threadIdx.x; i < d.J * d.L * 2; i += blockDim.x) sg[i] = 0.0f;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *ring = ring_all + (size_t)warp * 2 * STAGE;
+    const int chunks = (d.p + kBwdRows - 1) / kBwdRows;
+    const long long total = (long long)P * d.J * chunks;
+    for (long long item = (long long)blockIdx.x * kRingWarps + warp; item < total;
+         item += (long long)gridDim.x * kRingWarps) {
+        const int pk = (int)(item / ((long long)d.J * chunks));
+        const int rem = (int)(item - (long long)pk * d.J * chunks);
+        const int j = rem / chunks, r0 = (rem - j * chunks) * kBwdRows;
+        const int r1 = min(r0 + kBwdRows, d.p);
+        const float2 *prm = reinterpret_cast<const float2 *>(prm_l) + (size_t)j * d.L;
+        // slot `lane` of this block row: shift (-1 absent) and first edge of its block
+        const int my_sh = (lane < DCMAX && (REG || lane < d.L)) ? d.shift[j * d.L + lane] : -1;
+        const int my_eo = my_sh >= 0 ? d.eoff[j * d.L + lane] : 0;
+        const uint32_t pres = __ballot_sync(0xffffffffu, my_sh >= 0);  // present slots (bit l)
+        const size_t base = (size_t)pk * d.E;
+        // edge of slot `lane` in row r (-1: absent)
+        auto row_edge = [&](int r) -> int {
+            if (!REG && my_sh < 0) return -1;
+            int k = r + my_sh;
+            if (k >= d.p) k -= d.p;
+            return my_eo + k;
+        };
+        // starts the copies of row r into stage st; returns this lane's edge of that row
+        auto issue = [&](int r, int st) -> int {
+            const int me = row_edge(r);
+            uint32_t *dst = ring + st * STAGE;
+#pragma unroll
+            for (int q = 0; q < DCMAX / 4; ++q) {  // beta: 8 chunks of 16 bytes per edge
+                const int l = 4 * q + (lane >> 3), sub = lane & 7;
+                const int e = __shfl_sync(0xffffffffu, me, l);
+                if (REG || e >= 0) cp_async16(dst + l * 32 + sub * 4, bw + (base + e) * 32 + sub * 4);
+            }
+#pragma unroll
+            for (int q = 0; q < DCMAX * V / 4; ++q) {  // adjoints: 8 V chunks per edge
+                const int c = 32 * q + lane;
+                const int l = c / (8 * V), sub = c - l * (8 * V);
+                const int e = __shfl_sync(0xffffffffu, me, l);
+                if (REG || e >= 0) cp_async16(dst + SB + l * 32 * V + sub * 4, GA + (base + e) * 32 * V + sub * 4);
+            }
+            cp_async_commit();
+            return me;
+        };
+        float pw[DCMAX], po[DCMAX];  // this lane's partial gradients of (w, o) per edge slot
+#pragma unroll
+        for (int l = 0; l < DCMAX; ++l) pw[l] = po[l] = 0.0f;
+        int me_cur = issue(r0, 0);
+        for (int r = r0, st = 0; r < r1; ++r, st ^= 1) {
+            int me_next = -1;
+            if (r + 1 < r1) me_next = issue(r + 1, st ^ 1);
+            else cp_async_commit();  // an empty group: the wait below always leaves one pending
+            cp_async_wait<1>();
+            __syncwarp();
+            const uint32_t *Sb = ring + st * STAGE;
+            const float *Sg = reinterpret_cast<const float *>(Sb + SB);
+            // the two smallest magnitudes of each frame and their slots (strict <: the lowest index
+            // among ties); absent slots never qualify
+            uint32_t neg[V];
+            float mn1[V], mn2[V];
+            int i1[V], i2[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) neg[v] = 0u, mn1[v] = mn2[v] = INFINITY, i1[v] = i2[v] = -1;
+#pragma unroll
+            for (int l = 0; l < DCMAX; ++l) {
+                if (!REG && !((pres >> l) & 1u)) continue;  // warp-uniform
+                float x[V];
+                Word<S>::ld(Sb[l * 32 + lane], x);
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const float a = fabsf(x[v]);
+                    neg[v] |= (x[v] < 0.0f ? 1u : 0u) << l;
+                    const bool lo1 = a < mn1[v], lo2 = a < mn2[v];
+                    mn2[v] = lo1 ? mn1[v] : (lo2 ? a : mn2[v]);
+                    i2[v] = lo1 ? i1[v] : (lo2 ? l : i2[v]);
+                    mn1[v] = lo1 ? a : mn1[v];
+                    i1[v] = lo1 ? l : i1[v];
+                }
+            }
+            uint32_t par[V];
+            float g1[V], g2[V];  // adjoints landing on slots i1 and i2
+#pragma unroll
+            for (int v = 0; v < V; ++v) par[v] = __popc(neg[v]) & 1u, g1[v] = g2[v] = 0.0f;
+#pragma unroll
+            for (int l = 0; l < DCMAX; ++l) {
+                if (!REG && !((pres >> l) & 1u)) continue;  // warp-uniform
+                const float2 wo = __ldg(prm + l);
+                float ga[V];
+                if constexpr (V == 1) ga[0] = Sg[l * 32 + lane];
+                else {
+                    const float2 g = *reinterpret_cast<const float2 *>(Sg + l * 64 + lane * 2);
+                    ga[0] = g.x;
+                    ga[1] = g.y;
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const bool first = l == i1[v];
+                    const float mv = first ? mn2[v] : mn1[v];
+                    const float sgn = (par[v] ^ ((neg[v] >> l) & 1u)) ? -1.0f : 1.0f;
+                    const float z = fmaf(wo.x, mv, -wo.y);
+                    // alpha = s (w m - o) only where that is positive and below the clip
+                    if ((first ? i2[v] : i1[v]) >= 0 && z > 0.0f && z < clip) {
+                        const float gs = ga[v] * sgn;
+                        pw[l] = fmaf(gs, mv, pw[l]);
+                        po[l] -= gs;
+                        if (first) g2[v] += gs * wo.x;
+                        else g1[v] += gs * wo.x;
+                    }
+                }
+            }
+            if (want_gb) {
+                // sign(beta) of the two smallest inputs (0 for beta = 0)
+                float s1[V], s2[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    s1[v] = (i1[v] < 0 || mn1[v] == 0.0f) ? 0.0f : (((neg[v] >> i1[v]) & 1u) ? -1.0f : 1.0f);
+                    s2[v] = (i2[v] < 0 || mn2[v] == 0.0f) ? 0.0f : (((neg[v] >> i2[v]) & 1u) ? -1.0f : 1.0f);
+                }
+#pragma unroll
+                for (int l = 0; l < DCMAX; ++l) {
+                    const int e = __shfl_sync(0xffffffffu, me_cur, l);
+                    if (!REG && e < 0) continue;  // warp-uniform
+                    float g[V];
+#pragma unroll
+                    for (int v = 0; v < V; ++v) g[v] = l == i1[v] ? g1[v] * s1[v] : (l == i2[v] ? g2[v] * s2[v] : 0.0f);
+                    if constexpr (V == 1) GB[(base + e) * 32 + lane] = g[0];
+                    else *reinterpret_cast<float2 *>(GB + ((base + e) * 32 + lane) * 2) = make_float2(g[0], g[1]);
+                }
+            }
+            __syncwarp();  // the stage is refilled by the next issue
+            me_cur = me_next;
+        }
+        cp_async_wait<0>();
+        // warp sums of this item's gradients per circulant (j, l)
+#pragma unroll
+        for (int l = 0; l < DCMAX; ++l) {
+            if (!REG && !((pres >> l) & 1u)) continue;  // warp-uniform
+            float gw = pw[l], go = po[l];
+#pragma unroll
+            for (int of = 16; of > 0; of >>= 1) {
+                gw += __shfl_xor_sync(0xffffffffu, gw, of);
+                go += __shfl_xor_sync(0xffffffffu, go, of);
+            }
+            if (lane == 0 && (gw != 0.0f || go != 0.0f)) {
+                atomicAdd(&sg[(j * d.L + l) * 2], gw);
+                atomicAdd(&sg[(j * d.L + l) * 2 + 1], go);
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < d.J * d.L * 2; i += blockDim.x)
+        if (sg[i] != 0.0f) atomicAdd(grad_l + i, sg[i]);
+}
+
 // the loss: the partial sums added in a fixed order (one block of 1024 threads)
 __global__ void __launch_bounds__(1024) nm_loss_out(const double *__restrict__ part, long long np, float *out) {
     __shared__ double sh[1024];
@@ -700,22 +876,32 @@ static ldpc_status nm_backward(ldpc_code c, ldpc_noms_state &w, float *grad, cud
         const float *prm = w.params + (size_t)(l - 1) * d.J * d.L * 2;
         float *gl = grad + (size_t)(l - 1) * d.J * d.L * 2;
         const int want_gb = l > 1;
-#define NM_CB1(DC, FM, RG)                                                                                  \
+#define NM_CB1(DC, RG)                                                                                      \
     do {                                                                                                    \
         const size_t psm = (size_t)kWarps * (DC) * 2 * 32 * sizeof(float);                                 \
-        auto kfn = nm_cn_bwd<DC, S, FM, RG>;                                                                \
+        auto kfn = nm_cn_bwd<DC, S, true, RG>;                                                              \
         cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);                   \
         kfn<<<cb_blocks, kWarps * 32, psm, s>>>(d, bin, w.GA, prm, w.GB, gl, w.clip, w.P, want_gb);         \
     } while (0)
+#define NM_CR1(DC, RG)                                                                                      \
+    do {                                                                                                    \
+        const size_t rsm = (size_t)kRingWarps * 2 * ((DC) * 32 * (1 + Word<S>::V)) * 4;                    \
+        auto kfn = nm_cn_bwd_ring<DC, S, RG>;                                                               \
+        cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);                   \
+        kfn<<<std::max(1, sms) * 3, kRingWarps * 32, rsm, s>>>(d, (const uint32_t *)bin, w.GA, prm, w.GB, gl, \
+                                                               w.clip, w.P, want_gb);                       \
+    } while (0)
+// iteration 1 reads the channel LLRs (nm_cn_bwd); later ones a message store (nm_cn_bwd_ring)
 #define NM_CB(DC)                                  \
     do {                                           \
-        if (full && d.L == (DC)) {                 \
-            if (from_mu) NM_CB1(DC, true, true);   \
-            else NM_CB1(DC, false, true);          \
-        } else if (from_mu) {                      \
-            NM_CB1(DC, true, false);               \
+        const bool rg = full && d.L == (DC);       \
+        if (from_mu) {                             \
+            if (rg) NM_CB1(DC, true);              \
+            else NM_CB1(DC, false);                \
+        } else if (rg) {                           \
+            NM_CR1(DC, true);                      \
         } else {                                   \
-            NM_CB1(DC, false, false);              \
+            NM_CR1(DC, false);                     \
         }                                          \
     } while (0)
         if (d.L <= 8) NM_CB(8);
@@ -724,6 +910,7 @@ static ldpc_status nm_backward(ldpc_code c, ldpc_noms_state &w, float *grad, cud
         else NM_CB(32);
 #undef NM_CB
 #undef NM_CB1
+#undef NM_CR1
         count_launch(2);
         LDPC_CUDA_TRY(cudaGetLastError());
         bnext = bin;
