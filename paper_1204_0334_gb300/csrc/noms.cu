@@ -27,7 +27,12 @@ struct ldpc_noms_state {
     void *ping[2] = {nullptr, nullptr};  // non-checkpoint betas (S)
     void *ckpt = nullptr;      // [nck][P][E][32] (S): beta^(k), beta^(2k), ...
     void *seg = nullptr;       // [k][P][E][32] (S): recomputed betas of one segment
-    float *A = nullptr, *GA = nullptr, *GB = nullptr;  // [P][E][32]
+    float *A = nullptr, *GA = nullptr;  // [P][E][32 V] (A holds lane words)
+    // adjoint of beta^(l-1), nonzero only on the two smallest inputs of each row and frame: per
+    // row and lane a word of their slots ([P][M][32]: int8 i1, i2 per frame) and their values
+    // ([P][M][2][32 V] floats)
+    uint32_t *GBs = nullptr;
+    float *GBv = nullptr;
     float *posts = nullptr;    // [T][P][N][32] (stride N * cap_frames): post^(1..T) of the forward
     size_t cap_T = 0;
     double *acc = nullptr;     // loss: one partial sum per variable-step block, [P][ceil(N / 8)]
@@ -284,7 +289,8 @@ nm_vn_fwd(const QcDesc d, const uint32_t *__restrict__ A, const float *__restric
 template <int JMAX, typename S, bool REG>
 __global__ void __launch_bounds__(kWarps * 32)
 nm_vn_bwd(const QcDesc d, const float *__restrict__ post, const uint32_t *__restrict__ bl,
-          const float *__restrict__ GB, float *__restrict__ GA, float clip, float zinv, int P, int B) {
+          const uint32_t *__restrict__ gbs, const float *__restrict__ gbv, float *__restrict__ GA, float clip,
+          float zinv, int P, int B) {
     constexpr int V = Word<S>::V;
     const int lane = threadIdx.x & 31;
     const int n = blockIdx.x * kWarps + (threadIdx.x >> 5);
@@ -308,20 +314,23 @@ nm_vn_bwd(const QcDesc d, const float *__restrict__ post, const uint32_t *__rest
         eid[j] = -1;
         if (!REG && (j >= d.J || d.shift[j * d.L + l] < 0)) continue;
         eid[j] = d.eoff[j * d.L + l] + k;
-        // the adjoint of beta^(l)_e passes the clip only where it was inactive
-        if (GB) {
-            const size_t w = ((size_t)pk * d.E + eid[j]) * 32 + lane;
-            float b[V], g[V];
-            Word<S>::ld(bl[w], b);
-            if constexpr (V == 1) g[0] = GB[w];
-            else {
-                const float2 g2 = *reinterpret_cast<const float2 *>(GB + w * 2);
-                g[0] = g2.x;
-                g[1] = g2.y;
-            }
+        // the adjoint of beta^(l)_e: nonzero where this edge (slot l of its row) is one of the row's
+        // two smallest inputs; it passes the clip only where the clip was inactive
+        if (gbs) {
+            int r = k - d.shift[j * d.L + l];
+            if (r < 0) r += d.p;
+            const size_t rw = (size_t)pk * d.M + j * d.p + r;  // the row's record
+            const uint32_t sw = gbs[rw * 32 + lane];
+            float b[V];
+            Word<S>::ld(bl[((size_t)pk * d.E + eid[j]) * 32 + lane], b);
 #pragma unroll
-            for (int v = 0; v < V; ++v)
-                if (fabsf(b[v]) < clip) gbm[j][v] = g[v];
+            for (int v = 0; v < V; ++v) {
+                const int s1 = (int)(int8_t)(sw >> (16 * v)), s2 = (int)(int8_t)(sw >> (16 * v + 8));
+                float g = 0.0f;
+                if (l == s1) g = gbv[(rw * 2) * 32 * V + lane * V + v];
+                else if (l == s2) g = gbv[(rw * 2 + 1) * 32 * V + lane * V + v];
+                if (fabsf(b[v]) < clip) gbm[j][v] = g;
+            }
         }
     }
     float dpost[V];
@@ -345,8 +354,9 @@ nm_vn_bwd(const QcDesc d, const float *__restrict__ post, const uint32_t *__rest
 }
 
 // ---------------------------------------------------------------------------
-// backward check step: parameter gradients of iteration l and the adjoint of
-// beta^(l-1).  m_e = |beta_{e*}| with e* the arg-min over the other edges
+// backward check step of iteration 1 (input: the channel LLRs): the parameter
+// gradients (beta^(0) = mu needs no adjoint).  m_e = |beta_{e*}| with e* the
+// arg-min over the other edges
 // (lowest index among ties): e* = idx2 for e = idx1, else idx1; so only the
 // two smallest inputs of a row receive gradient.  Persistent warps take items of
 // kBwdRows consecutive rows of one block row j, so every row of an item adds to
@@ -368,7 +378,7 @@ constexpr int kBwdBlocks = LDPC_NM_BWD_BLOCKS;  // resident blocks per SM of the
 template <int DCMAX, typename S, bool FROM_MU, bool REG>
 __global__ void __launch_bounds__(kWarps * 32, kBwdBlocks)
 nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict__ GA, const float *__restrict__ prm_l,
-          float *__restrict__ GB, float *__restrict__ grad_l, float clip, int P, int want_gb) {
+          float *__restrict__ grad_l, float clip, int P) {
     static_assert(DCMAX <= 32, "one lane per edge slot");
     constexpr int V = Word<S>::V;
     __shared__ float sg[kMaxJ * kMaxL * 2];
@@ -437,7 +447,6 @@ nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict_
                 i1 = lo1 ? l : i1;
             }
             const uint32_t par = __popc(neg) & 1u;
-            float g1 = 0.0f, g2 = 0.0f;  // adjoints landing on slots i1 and i2
 #pragma unroll
             for (int l = 0; l < DCMAX; ++l) {
                 if (!REG && ga[l] == 0.0f) continue;  // absent slot, or nothing to propagate
@@ -452,20 +461,6 @@ nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict_
                     const float gs = ga[l] * sgn;
                     part[(2 * l) * 32 + lane] = fmaf(gs, mv, part[(2 * l) * 32 + lane]);
                     part[(2 * l + 1) * 32 + lane] -= gs;
-                    if (first) g2 += gs * wo.x;
-                    else g1 += gs * wo.x;
-                }
-            }
-            if (want_gb) {
-                // sign(beta) of the two smallest inputs (0 for beta = 0)
-                const float s1 = (i1 < 0 || mn1 == 0.0f) ? 0.0f : (((neg >> i1) & 1u) ? -1.0f : 1.0f);
-                const float s2 = (i2 < 0 || mn2 == 0.0f) ? 0.0f : (((neg >> i2) & 1u) ? -1.0f : 1.0f);
-#pragma unroll
-                for (int l = 0; l < DCMAX; ++l) {
-                    const int e = __shfl_sync(0xffffffffu, my_e, l);
-                    if (!REG && e < 0) continue;  // warp-uniform
-                    const float g = l == i1 ? g1 * s1 : (l == i2 ? g2 * s2 : 0.0f);
-                    GB[((base + e) * 32 + lane) * V + v] = g;
                 }
             }
             }
@@ -503,8 +498,8 @@ constexpr int kRingWarps = 4;
 template <int DCMAX, typename S, bool REG>
 __global__ void __launch_bounds__(kRingWarps * 32, 3)
 nm_cn_bwd_ring(const QcDesc d, const uint32_t *__restrict__ bw, const float *__restrict__ GA,
-               const float *__restrict__ prm_l, float *__restrict__ GB, float *__restrict__ grad_l, float clip, int P,
-               int want_gb) {
+               const float *__restrict__ prm_l, uint32_t *__restrict__ gbs, float *__restrict__ gbv,
+               float *__restrict__ grad_l, float clip, int P, int want_gb) {
     static_assert(DCMAX <= 32 && DCMAX % 4 == 0, "one lane per edge slot, slots in groups of four");
     constexpr int V = Word<S>::V;
     constexpr int SB = DCMAX * 32;      // words: the beta packages of a row
@@ -537,8 +532,8 @@ nm_cn_bwd_ring(const QcDesc d, const uint32_t *__restrict__ bw, const float *__r
             if (k >= d.p) k -= d.p;
             return my_eo + k;
         };
-        // starts the copies of row r into stage st; returns this lane's edge of that row
-        auto issue = [&](int r, int st) -> int {
+        // starts the copies of row r into stage st
+        auto issue = [&](int r, int st) {
             const int me = row_edge(r);
             uint32_t *dst = ring + st * STAGE;
 #pragma unroll
@@ -555,15 +550,13 @@ nm_cn_bwd_ring(const QcDesc d, const uint32_t *__restrict__ bw, const float *__r
                 if (REG || e >= 0) cp_async16(dst + SB + l * 32 * V + sub * 4, GA + (base + e) * 32 * V + sub * 4);
             }
             cp_async_commit();
-            return me;
         };
         float pw[DCMAX], po[DCMAX];  // this lane's partial gradients of (w, o) per edge slot
 #pragma unroll
         for (int l = 0; l < DCMAX; ++l) pw[l] = po[l] = 0.0f;
-        int me_cur = issue(r0, 0);
+        issue(r0, 0);
         for (int r = r0, st = 0; r < r1; ++r, st ^= 1) {
-            int me_next = -1;
-            if (r + 1 < r1) me_next = issue(r + 1, st ^ 1);
+            if (r + 1 < r1) issue(r + 1, st ^ 1);
             else cp_async_commit();  // an empty group: the wait below always leaves one pending
             cp_async_wait<1>();
             __syncwarp();
@@ -631,19 +624,23 @@ nm_cn_bwd_ring(const QcDesc d, const uint32_t *__restrict__ bw, const float *__r
                     s1[v] = (i1[v] < 0 || mn1[v] == 0.0f) ? 0.0f : (((neg[v] >> i1[v]) & 1u) ? -1.0f : 1.0f);
                     s2[v] = (i2[v] < 0 || mn2[v] == 0.0f) ? 0.0f : (((neg[v] >> i2[v]) & 1u) ? -1.0f : 1.0f);
                 }
+                // the adjoint of beta^(l-1) is nonzero on slots i1 and i2 only: one record per row and lane
+                const size_t rw = (size_t)pk * d.M + j * d.p + r;
+                uint32_t sw = 0u;
 #pragma unroll
-                for (int l = 0; l < DCMAX; ++l) {
-                    const int e = __shfl_sync(0xffffffffu, me_cur, l);
-                    if (!REG && e < 0) continue;  // warp-uniform
-                    float g[V];
-#pragma unroll
-                    for (int v = 0; v < V; ++v) g[v] = l == i1[v] ? g1[v] * s1[v] : (l == i2[v] ? g2[v] * s2[v] : 0.0f);
-                    if constexpr (V == 1) GB[(base + e) * 32 + lane] = g[0];
-                    else *reinterpret_cast<float2 *>(GB + ((base + e) * 32 + lane) * 2) = make_float2(g[0], g[1]);
+                for (int v = 0; v < V; ++v)
+                    sw |= ((uint32_t)(uint8_t)i1[v] << (16 * v)) | ((uint32_t)(uint8_t)i2[v] << (16 * v + 8));
+                gbs[rw * 32 + lane] = sw;
+                if constexpr (V == 1) {
+                    gbv[(rw * 2) * 32 + lane] = g1[0] * s1[0];
+                    gbv[(rw * 2 + 1) * 32 + lane] = g2[0] * s2[0];
+                } else {
+                    *reinterpret_cast<float2 *>(gbv + (rw * 2) * 64 + lane * 2) = make_float2(g1[0] * s1[0], g1[1] * s1[1]);
+                    *reinterpret_cast<float2 *>(gbv + (rw * 2 + 1) * 64 + lane * 2) =
+                        make_float2(g2[0] * s2[0], g2[1] * s2[1]);
                 }
             }
             __syncwarp();  // the stage is refilled by the next issue
-            me_cur = me_next;
         }
         cp_async_wait<0>();
         // warp sums of this item's gradients per circulant (j, l)
@@ -690,7 +687,7 @@ static size_t nm_loss_parts(ldpc_code c, const ldpc_noms_state &w) {
 // host orchestration
 // ---------------------------------------------------------------------------
 static ldpc_status nm_alloc(ldpc_code c, ldpc_noms_state &w, size_t frames, size_t nck, size_t nseg, size_t T) {
-    const size_t E = c->d.E, N = c->d.N;
+    const size_t E = c->d.E, N = c->d.N, M = c->d.M;
     const size_t fr = (frames + 63) / 64 * 64;  // whole packages of 32 or 64 frames
     auto fail = [&]() {
         cudaGetLastError();
@@ -699,17 +696,19 @@ static ldpc_status nm_alloc(ldpc_code c, ldpc_noms_state &w, size_t frames, size
     };
     if (fr > w.cap_frames) {
         cudaDeviceSynchronize();
-        cudaFree(w.mu); cudaFree(w.ping[0]); cudaFree(w.ping[1]); cudaFree(w.A); cudaFree(w.GA); cudaFree(w.GB);
+        cudaFree(w.mu); cudaFree(w.ping[0]); cudaFree(w.ping[1]); cudaFree(w.A); cudaFree(w.GA); cudaFree(w.GBs); cudaFree(w.GBv);
         cudaFree(w.posts); cudaFree(w.ckpt); cudaFree(w.seg); cudaFree(w.acc);
         // nothing is held until every buffer of the new size exists (a failed call leaves no
         // capacity behind that the next call would trust)
-        w.mu = w.A = w.GA = w.GB = w.posts = nullptr;
+        w.mu = w.A = w.GA = w.GBv = w.posts = nullptr;
+        w.GBs = nullptr;
         w.ping[0] = w.ping[1] = w.ckpt = w.seg = nullptr;
         w.acc = nullptr;
         w.cap_frames = w.cap_nck = w.cap_seg = w.cap_T = 0;
         const size_t np = (size_t)((N + kWarps - 1) / kWarps) * (fr / 32);
         if (cudaMalloc(&w.mu, N * fr * 4) || cudaMalloc(&w.ping[0], E * fr * 4) || cudaMalloc(&w.ping[1], E * fr * 4) ||
-            cudaMalloc(&w.A, E * fr * 4) || cudaMalloc(&w.GA, E * fr * 4) || cudaMalloc(&w.GB, E * fr * 4) ||
+            cudaMalloc(&w.A, E * fr * 4) || cudaMalloc(&w.GA, E * fr * 4) || cudaMalloc(&w.GBs, M * fr * 4) ||
+            cudaMalloc(&w.GBv, 2 * M * fr * 4) ||
             cudaMalloc(&w.acc, np * sizeof(double)))
             return fail();
         w.cap_frames = fr;
@@ -864,15 +863,15 @@ static ldpc_status nm_backward(ldpc_code c, ldpc_noms_state &w, float *grad, cud
         }
         // the adjoints of alpha^(l) (from the saved posteriors and beta^(l)), then of the parameters
         // and beta^(l-1)
-        const float *gbin = l == w.T ? nullptr : w.GB;
+        const uint32_t *gbs = l == w.T ? nullptr : w.GBs;  // the adjoint of beta^(T) is zero
         const uint32_t *bl = l == w.T ? nullptr : (const uint32_t *)bnext;
         const float *pl = nm_post(c, w, l);
         if (full && d.J == 4)
-            nm_vn_bwd<4, S, true><<<vg, kWarps * 32, 0, s>>>(d, pl, bl, gbin, w.GA, w.clip, zinv, w.P, w.B);
+            nm_vn_bwd<4, S, true><<<vg, kWarps * 32, 0, s>>>(d, pl, bl, gbs, w.GBv, w.GA, w.clip, zinv, w.P, w.B);
         else if (d.J <= 4)
-            nm_vn_bwd<4, S, false><<<vg, kWarps * 32, 0, s>>>(d, pl, bl, gbin, w.GA, w.clip, zinv, w.P, w.B);
+            nm_vn_bwd<4, S, false><<<vg, kWarps * 32, 0, s>>>(d, pl, bl, gbs, w.GBv, w.GA, w.clip, zinv, w.P, w.B);
         else
-            nm_vn_bwd<8, S, false><<<vg, kWarps * 32, 0, s>>>(d, pl, bl, gbin, w.GA, w.clip, zinv, w.P, w.B);
+            nm_vn_bwd<8, S, false><<<vg, kWarps * 32, 0, s>>>(d, pl, bl, gbs, w.GBv, w.GA, w.clip, zinv, w.P, w.B);
         const float *prm = w.params + (size_t)(l - 1) * d.J * d.L * 2;
         float *gl = grad + (size_t)(l - 1) * d.J * d.L * 2;
         const int want_gb = l > 1;
@@ -881,15 +880,15 @@ static ldpc_status nm_backward(ldpc_code c, ldpc_noms_state &w, float *grad, cud
         const size_t psm = (size_t)kWarps * (DC) * 2 * 32 * sizeof(float);                                 \
         auto kfn = nm_cn_bwd<DC, S, true, RG>;                                                              \
         cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);                   \
-        kfn<<<cb_blocks, kWarps * 32, psm, s>>>(d, bin, w.GA, prm, w.GB, gl, w.clip, w.P, want_gb);         \
+        kfn<<<cb_blocks, kWarps * 32, psm, s>>>(d, bin, w.GA, prm, gl, w.clip, w.P);                         \
     } while (0)
 #define NM_CR1(DC, RG)                                                                                      \
     do {                                                                                                    \
         const size_t rsm = (size_t)kRingWarps * 2 * ((DC) * 32 * (1 + Word<S>::V)) * 4;                    \
         auto kfn = nm_cn_bwd_ring<DC, S, RG>;                                                               \
         cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);                   \
-        kfn<<<std::max(1, sms) * 3, kRingWarps * 32, rsm, s>>>(d, (const uint32_t *)bin, w.GA, prm, w.GB, gl, \
-                                                               w.clip, w.P, want_gb);                       \
+        kfn<<<std::max(1, sms) * 3, kRingWarps * 32, rsm, s>>>(d, (const uint32_t *)bin, w.GA, prm, w.GBs,   \
+                                                               w.GBv, gl, w.clip, w.P, want_gb);            \
     } while (0)
 // iteration 1 reads the channel LLRs (nm_cn_bwd); later ones a message store (nm_cn_bwd_ring)
 #define NM_CB(DC)                                  \
@@ -1006,7 +1005,7 @@ namespace ldpc {
 void noms_free(ldpc_noms_state *w) {
     if (!w) return;
     cudaFree(w->mu); cudaFree(w->ping[0]); cudaFree(w->ping[1]); cudaFree(w->ckpt); cudaFree(w->seg);
-    cudaFree(w->A); cudaFree(w->GA); cudaFree(w->GB); cudaFree(w->posts); cudaFree(w->acc);
+    cudaFree(w->A); cudaFree(w->GA); cudaFree(w->GBs); cudaFree(w->GBv); cudaFree(w->posts); cudaFree(w->acc);
     delete w;
 }
 }  // namespace ldpc
