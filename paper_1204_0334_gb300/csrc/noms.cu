@@ -320,15 +320,22 @@ nm_vn_bwd(const QcDesc d, const float *__restrict__ post, const uint32_t *__rest
             int r = k - d.shift[j * d.L + l];
             if (r < 0) r += d.p;
             const size_t rw = (size_t)pk * d.M + j * d.p + r;  // the row's record
+            // the slots and both values are loaded together (no load waits on another)
             const uint32_t sw = gbs[rw * 32 + lane];
-            float b[V];
+            float g1v[V], g2v[V], b[V];
+            if constexpr (V == 1) {
+                g1v[0] = gbv[(rw * 2) * 32 + lane];
+                g2v[0] = gbv[(rw * 2 + 1) * 32 + lane];
+            } else {
+                const float2 a1 = *reinterpret_cast<const float2 *>(gbv + (rw * 2) * 64 + lane * 2);
+                const float2 a2 = *reinterpret_cast<const float2 *>(gbv + (rw * 2 + 1) * 64 + lane * 2);
+                g1v[0] = a1.x, g1v[1] = a1.y, g2v[0] = a2.x, g2v[1] = a2.y;
+            }
             Word<S>::ld(bl[((size_t)pk * d.E + eid[j]) * 32 + lane], b);
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const int s1 = (int)(int8_t)(sw >> (16 * v)), s2 = (int)(int8_t)(sw >> (16 * v + 8));
-                float g = 0.0f;
-                if (l == s1) g = gbv[(rw * 2) * 32 * V + lane * V + v];
-                else if (l == s2) g = gbv[(rw * 2 + 1) * 32 * V + lane * V + v];
+                const float g = l == s1 ? g1v[v] : (l == s2 ? g2v[v] : 0.0f);
                 if (fabsf(b[v]) < clip) gbm[j][v] = g;
             }
         }
