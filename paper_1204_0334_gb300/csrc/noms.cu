@@ -92,8 +92,9 @@ __global__ void __launch_bounds__(kWarps * 32, FROM_MU ? 3 : NM_FWD_MINB)
 nm_cn_fwd(const QcDesc d, const void *__restrict__ bin, uint32_t *__restrict__ A, const float *__restrict__ prm_l,
           float clip, int P) {
     constexpr int V = Word<S>::V;
-    const int lane = threadIdx.x & 31;
-    const int m = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    __shared__ int s_e[kWarps][32];  // each warp's row: the edge of every slot (-1 absent)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int m = blockIdx.x * kWarps + warp;
     const int pk = blockIdx.y;
     if (m >= d.M || pk >= P) return;
     const int j = (int)fdiv((uint32_t)m, d.divP), r = m - j * d.p;
@@ -106,6 +107,8 @@ nm_cn_fwd(const QcDesc d, const void *__restrict__ bin, uint32_t *__restrict__ A
         my_e = d.eoff[j * d.L + lane] + k;
         my_n = lane * d.p + k;
     }
+    s_e[warp][lane] = my_e;
+    __syncwarp();
     const float2 *prm = reinterpret_cast<const float2 *>(prm_l) + (size_t)j * d.L;
     // the edge of slot l again from the tables (cheap to recompute, unlike a shuffle result that
     // would stay live from the gathers); -1: absent
@@ -185,7 +188,7 @@ nm_cn_fwd(const QcDesc d, const void *__restrict__ bin, uint32_t *__restrict__ A
         for (int v = 0; v < V; ++v) par[v] = __popc(neg[v]) & 1u;
 #pragma unroll
         for (int l = 0; l < DCMAX; ++l) {
-            const int e = edge(l);
+            const int e = s_e[warp][l];  // broadcast read of the row's edge table
             if (!REG && e < 0) continue;  // warp-uniform
             const float2 wo = __ldg(prm + l);
             float out[V];
