@@ -615,6 +615,9 @@ def batch_bench(a, pkg, stream) -> dict:
 
     info = pkg.ldpc_batch_info(b)
     moved = sum(pkg.ldpc_batch_moved(b, len(codes)))
+    # one decode's phase boundaries (30 iterations x tiles, syndrome, check, variable pass) as graph
+    # launches against grid barriers of one cooperative kernel, both without work
+    sync = pkg.ldpc_sync_probe(120, 100)
     comp = pkg.ldpc_batch_compaction(b)
     pkg.ldpc_batch_destroy(b)
     peak = load_peaks().get("hbm_gbs", 6800.0)
@@ -624,7 +627,9 @@ def batch_bench(a, pkg, stream) -> dict:
             "path_achieved_gbs": path_bytes / (ms / 1e3) / 1e9, "path_frac": path_bytes / (ms / 1e3) / 1e9 / peak,
             "tile_rows": info["tile_rows"], "tile_groups": info["tile_groups"],
             "frames_compacted": moved, "compaction_after_iter": comp["after_iter"],
-            "compaction_tune_ms": comp["tune_ms"]}
+            "compaction_tune_ms": comp["tune_ms"],
+            "phase_boundary_us": {"graph": sync["graph_us"], "cooperative": sync["cooperative_us"],
+                                  "boundaries_per_decode": 120}}
 
 
 def sparse_bench(a, pkg, qc, stream) -> dict:

@@ -451,6 +451,22 @@ ldpc_status ldpc_profile_read(ldpc_profile *out);
 ldpc_status ldpc_bandwidth_probe(const void *src, void *dst, int64_t bytes, int32_t reps, int32_t mode,
                                  double *gbs_out, void *stream);
 
+/*
+ * ldpc_sync_probe -- measurement aid (no paper counterpart): what one phase
+ * boundary of an iteration loop of persistent passes costs, done two ways with
+ * no work in the phases.  (a) `boundaries` back-to-back launches of an empty
+ * kernel (grids of 1, 4, 2 and 3 blocks per SM in turn, as the heterogeneous
+ * batch's tile, syndrome, check and variable passes), captured once in a CUDA
+ * graph and replayed `reps` times; (b) one cooperative kernel (two resident
+ * blocks of 256 threads per SM) with `boundaries` grid-wide barriers, launched
+ * `reps` times.  *graph_us and *coop_us: microseconds per boundary (CUDA events
+ * on a private stream, after three untimed runs of each).
+ * 1 <= boundaries <= 4096, 1 <= reps <= 10000.  Synchronizes the device's work on
+ * its own stream only.  Errors: LDPC_EINVAL, LDPC_EUNSUPPORTED (no cooperative
+ * launch), LDPC_ECUDA.
+ */
+ldpc_status ldpc_sync_probe(int32_t boundaries, int32_t reps, double *graph_us, double *coop_us);
+
 #ifdef __cplusplus
 }
 #endif

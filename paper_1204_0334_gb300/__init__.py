@@ -92,6 +92,7 @@ _SIGNATURES = [
     ("ldpc_profile_enable", ctypes.c_int, [ctypes.c_int32]),
     ("ldpc_profile_read", ctypes.c_int, [P]),
     ("ldpc_bandwidth_probe", ctypes.c_int, [P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P, P]),
+    ("ldpc_sync_probe", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, P, P]),
     ("ldpc_tune_slots", ctypes.c_int, [P, ctypes.c_double, ctypes.c_uint64, P, P, P, P]),
 ]
 
@@ -442,6 +443,14 @@ def ldpc_bandwidth_probe(src, dst, reps: int, mode: int, stream=None) -> float:
     _check(lib().ldpc_bandwidth_probe(_ptr(src), _ptr(dst), nbytes, int(reps), int(mode), ctypes.byref(out),
                                       _stream(stream)), "ldpc_bandwidth_probe")
     return out.value
+
+
+def ldpc_sync_probe(boundaries: int = 120, reps: int = 100) -> dict:
+    """Microseconds per phase boundary: a CUDA graph of empty launches against grid barriers in one
+    cooperative kernel (no work in either)."""
+    g, c = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib().ldpc_sync_probe(int(boundaries), int(reps), ctypes.byref(g), ctypes.byref(c)), "ldpc_sync_probe")
+    return {"graph_us": g.value, "cooperative_us": c.value}
 
 
 # ----------------------------------------------------------------- convenience

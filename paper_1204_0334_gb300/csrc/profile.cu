@@ -1,6 +1,8 @@
 // Launch counting and per-launch event timing behind ldpc_profile_enable / ldpc_profile_read.
 #include "ldpc_internal.cuh"
 
+#include <cooperative_groups.h>
+
 #include <atomic>
 #include <vector>
 
@@ -177,3 +179,90 @@ ldpc_status ldpc_bandwidth_probe(const void *src, void *dst, int64_t bytes, int3
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// phase-boundary probe: back-to-back launches replayed from a CUDA graph against
+// grid-wide barriers inside one cooperative kernel, both with no work
+// ---------------------------------------------------------------------------
+namespace ldpc {
+__global__ void __launch_bounds__(256) sync_empty_kernel(int *sink, int tag) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) sink[0] = tag;
+}
+
+__global__ void __launch_bounds__(256) sync_coop_kernel(int *sink, int barriers) {
+    cooperative_groups::grid_group g = cooperative_groups::this_grid();
+    for (int i = 0; i < barriers; ++i) {
+        if (threadIdx.x == 0 && blockIdx.x == 0) sink[0] = i;
+        g.sync();
+    }
+}
+}  // namespace ldpc
+
+extern "C" ldpc_status ldpc_sync_probe(int32_t boundaries, int32_t reps, double *graph_us, double *coop_us) {
+    if (boundaries < 1 || boundaries > 4096 || reps < 1 || reps > 10000 || !graph_us || !coop_us) {
+        set_error("need 1 <= boundaries <= 4096, 1 <= reps <= 10000, graph_us, coop_us");
+        return LDPC_EINVAL;
+    }
+    int dev = 0, sms = 1, coop = 0, per_sm = 0;
+    LDPC_CUDA_TRY(cudaGetDevice(&dev));
+    LDPC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    LDPC_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    LDPC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sync_coop_kernel, 256, 0));
+    if (!coop || per_sm < 1) {
+        set_error("cooperative launch unavailable on this device");
+        return LDPC_EUNSUPPORTED;
+    }
+    // two resident blocks per SM at most (the batch's check pass), all of them resident
+    const int cblocks = sms * (per_sm < 2 ? per_sm : 2);
+    int *sink = nullptr;
+    cudaStream_t s = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaMalloc(&sink, sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    // one phase per boundary, with the batch's grid sizes in turn: tile rebuild, syndrome,
+    // check pass, variable pass
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        static const int mult[4] = {1, 4, 2, 3};
+        for (int i = 0; i < boundaries; ++i) sync_empty_kernel<<<sms * mult[i & 3], 256, 0, s>>>(sink, i);
+        e = cudaStreamEndCapture(s, &graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    float ms_graph = 0.0f, ms_coop = 0.0f;
+    if (e == cudaSuccess) {
+        for (int w = 0; w < 3 && e == cudaSuccess; ++w) e = cudaGraphLaunch(exec, s);
+        if (e == cudaSuccess) e = cudaEventRecord(a, s);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(exec, s);
+        if (e == cudaSuccess) e = cudaEventRecord(b, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_graph, a, b);
+        count_launch((long long)(reps + 3) * boundaries);
+    }
+    if (e == cudaSuccess) {
+        int nb = boundaries;
+        void *args[] = {&sink, &nb};
+        for (int w = 0; w < 3 && e == cudaSuccess; ++w)
+            e = cudaLaunchCooperativeKernel((const void *)sync_coop_kernel, cblocks, 256, args, 0, s);
+        if (e == cudaSuccess) e = cudaEventRecord(a, s);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r)
+            e = cudaLaunchCooperativeKernel((const void *)sync_coop_kernel, cblocks, 256, args, 0, s);
+        if (e == cudaSuccess) e = cudaEventRecord(b, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_coop, a, b);
+        count_launch(reps + 3);
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (s) cudaStreamDestroy(s);
+    if (sink) cudaFree(sink);
+    if (e != cudaSuccess) return cuda_fail(e, "phase-boundary probe");
+    *graph_us = 1e3 * ms_graph / reps / boundaries;
+    *coop_us = 1e3 * ms_coop / reps / boundaries;
+    return LDPC_OK;
+}

@@ -117,3 +117,12 @@ def test_mixed_64_code_batch(pkg):
         _, h1, it1, _ = codes[i].decode(llrs[i], max_iter=30, early_stop=True, msg=1, want_post=False)
         assert torch.equal(hards[i], h1) and torch.equal(its[i], it1)
     pkg.ldpc_batch_destroy(b)
+
+
+def test_phase_boundary_probe(pkg):
+    """The synchronization probe behind the graph-versus-cooperative-loop reading: both forms run and
+    report a positive cost per boundary, and bad arguments are refused."""
+    r = pkg.ldpc_sync_probe(40, 5)
+    assert 0.0 < r["graph_us"] < 1e3 and 0.0 < r["cooperative_us"] < 1e3, r
+    with pytest.raises(pkg.LdpcError):
+        pkg.ldpc_sync_probe(0, 5)
