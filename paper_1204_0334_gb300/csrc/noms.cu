@@ -167,20 +167,51 @@ nm_cn_fwd(const QcDesc d, const void *__restrict__ bin, uint32_t *__restrict__ A
         uint32_t neg[V];
         float mn1[V], mn2[V];
         int i1[V];
+        if constexpr (V == 2) {
+            // both binary16 frames of a word at once: min and compare are exact on binary16, so the
+            // search takes the same decisions as on the FP32 conversions (a < mn1, ties keep the
+            // lower slot, -0 is not negative)
+            const __half2 inf2 = __half2half2(__ushort_as_half((unsigned short)0x7c00u));
+            const __half2 zero2 = __float2half2_rn(0.0f);
+            __half2 m1 = inf2, m2 = inf2;
+            uint32_t ip = 0xffffffffu, n0 = 0u, n1 = 0u;  // i1 of each frame in 16 bits; sign bits
 #pragma unroll
-        for (int v = 0; v < V; ++v) neg[v] = 0u, mn1[v] = mn2[v] = INFINITY, i1[v] = -1;
+            for (int l = 0; l < DCMAX; ++l) {
+                const uint32_t x = xw[l], ab = x & 0x7fff7fffu;
+                const __half2 a = *reinterpret_cast<const __half2 *>(&ab);
+                const uint32_t lo = __hlt2_mask(a, m1);  // 0xffff in each half where a < mn1
+                const __half2 t = __hmin2(m2, a);
+                const uint32_t m1b = *reinterpret_cast<const uint32_t *>(&m1);
+                const uint32_t tb = *reinterpret_cast<const uint32_t *>(&t);
+                const uint32_t m2b = (m1b & lo) | (tb & ~lo);
+                m2 = *reinterpret_cast<const __half2 *>(&m2b);
+                ip = ((uint32_t)l * 0x00010001u & lo) | (ip & ~lo);
+                m1 = __hmin2(m1, a);
+                const uint32_t ng = x & __hne2_mask(a, zero2) & 0x80008000u;
+                n0 |= ((ng >> 15) & 1u) << l;
+                n1 |= (ng >> 31) << l;
+            }
+            const float2 f1 = __half22float2(m1), f2 = __half22float2(m2);
+            mn1[0] = f1.x, mn1[1] = f1.y, mn2[0] = f2.x, mn2[1] = f2.y;
+            i1[0] = (int)(int16_t)(ip & 0xffffu);
+            i1[1] = (int)(int16_t)(ip >> 16);
+            neg[0] = n0, neg[1] = n1;
+        } else {
 #pragma unroll
-        for (int l = 0; l < DCMAX; ++l) {
-            float x[V];
-            Word<S>::ld(xw[l], x);
+            for (int v = 0; v < V; ++v) neg[v] = 0u, mn1[v] = mn2[v] = INFINITY, i1[v] = -1;
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const float a = fabsf(x[v]);
-                neg[v] |= (x[v] < 0.0f ? 1u : 0u) << l;
-                const bool lo = a < mn1[v];
-                mn2[v] = lo ? mn1[v] : fminf(mn2[v], a);
-                i1[v] = lo ? l : i1[v];
-                mn1[v] = lo ? a : mn1[v];
+            for (int l = 0; l < DCMAX; ++l) {
+                float x[V];
+                Word<S>::ld(xw[l], x);
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const float a = fabsf(x[v]);
+                    neg[v] |= (x[v] < 0.0f ? 1u : 0u) << l;
+                    const bool lo = a < mn1[v];
+                    mn2[v] = lo ? mn1[v] : fminf(mn2[v], a);
+                    i1[v] = lo ? l : i1[v];
+                    mn1[v] = lo ? a : mn1[v];
+                }
             }
         }
         uint32_t par[V];
