@@ -416,9 +416,9 @@ constexpr int kBwdRows = 16;
 #endif
 constexpr int kBwdBlocks = LDPC_NM_BWD_BLOCKS;  // resident blocks per SM of the backward check step
 
-template <int DCMAX, typename S, bool FROM_MU, bool REG>
+template <int DCMAX, typename S, bool REG>
 __global__ void __launch_bounds__(kWarps * 32, kBwdBlocks)
-nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict__ GA, const float *__restrict__ prm_l,
+nm_cn_bwd(const QcDesc d, const float *__restrict__ mu, const float *__restrict__ GA, const float *__restrict__ prm_l,
           float *__restrict__ grad_l, float clip, int P) {
     static_assert(DCMAX <= 32, "one lane per edge slot");
     constexpr int V = Word<S>::V;
@@ -444,7 +444,7 @@ nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict_
         for (int l = 0; l < DCMAX; ++l) part[(2 * l) * 32 + lane] = part[(2 * l + 1) * 32 + lane] = 0.0f;
         const size_t base = (size_t)pk * d.E;
         for (int r = r0; r < r1; ++r) {
-            // edge of slot `lane` in row r (-1: absent) and its variable (for FROM_MU)
+            // edge of slot `lane` in row r (-1: absent) and its variable
             int my_e = -1, my_n = 0;
             if (REG || my_sh >= 0) {
                 int k = r + my_sh;
@@ -463,13 +463,8 @@ nm_cn_bwd(const QcDesc d, const void *__restrict__ bin, const float *__restrict_
                 xin[l] = INFINITY;
                 ga[l] = 0.0f;
                 if (!REG && e < 0) continue;  // warp-uniform
-                const int n = FROM_MU ? __shfl_sync(0xffffffffu, my_n, l) : 0;
-                if (FROM_MU)
-                    xin[l] = reinterpret_cast<const float *>(bin)[(((size_t)pk * d.N + n) * 32 + lane) * V + v];
-                else if (V == 1)
-                    xin[l] = reinterpret_cast<const float *>(bin)[(base + e) * 32 + lane];
-                else
-                    xin[l] = __half2float(reinterpret_cast<const __half *>(bin)[((base + e) * 32 + lane) * 2 + v]);
+                const int n = __shfl_sync(0xffffffffu, my_n, l);
+                xin[l] = mu[(((size_t)pk * d.N + n) * 32 + lane) * V + v];
                 ga[l] = GA[((base + e) * 32 + lane) * V + v];
             }
             // the two smallest magnitudes and their slots (strict <: the lowest index among ties);
@@ -919,9 +914,9 @@ static ldpc_status nm_backward(ldpc_code c, ldpc_noms_state &w, float *grad, cud
 #define NM_CB1(DC, RG)                                                                                      \
     do {                                                                                                    \
         const size_t psm = (size_t)kWarps * (DC) * 2 * 32 * sizeof(float);                                 \
-        auto kfn = nm_cn_bwd<DC, S, true, RG>;                                                              \
+        auto kfn = nm_cn_bwd<DC, S, RG>;                                                                    \
         cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);                   \
-        kfn<<<cb_blocks, kWarps * 32, psm, s>>>(d, bin, w.GA, prm, gl, w.clip, w.P);                         \
+        kfn<<<cb_blocks, kWarps * 32, psm, s>>>(d, (const float *)bin, w.GA, prm, gl, w.clip, w.P);          \
     } while (0)
 #define NM_CR1(DC, RG)                                                                                      \
     do {                                                                                                    \

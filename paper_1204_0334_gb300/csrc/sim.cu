@@ -360,7 +360,9 @@ __global__ void sim_channel_kernel(void *__restrict__ mu, const int *__restrict_
 // (device memory, or pinned host memory read through its device mapping) into the
 // slots' frame-major store: clipped for sum-product, quantized for min-sum exactly as
 // the batch path's packing does.
-template <bool I8>
+// VEC: rows start on 16-byte boundaries (N a multiple of 4, llr 16-byte aligned), so each thread
+// reads its 4 values with one 16-byte load (a warp reads 512 contiguous bytes of the row)
+template <bool I8, bool VEC>
 __global__ void stream_load_kernel(const float *__restrict__ llr, void *__restrict__ mu,
                                    const int *__restrict__ rlist, const int *__restrict__ rcount,
                                    const uint64_t *__restrict__ fid, int N, int parity, float clip, float qscale) {
@@ -376,8 +378,13 @@ __global__ void stream_load_kernel(const float *__restrict__ llr, void *__restri
         const int slot = rlist[r];
         const float *row = llr + (size_t)fid[slot] * N;
         float x[4];
+        if (VEC) {
+            const float4 v4 = reinterpret_cast<const float4 *>(row)[q];
+            x[0] = v4.x, x[1] = v4.y, x[2] = v4.z, x[3] = v4.w;
+        } else {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) x[e] = 4 * q + e < N ? row[4 * q + e] : 0.0f;
+            for (int e = 0; e < 4; ++e) x[e] = 4 * q + e < N ? row[4 * q + e] : 0.0f;
+        }
         if (I8) {
             uint32_t w = 0u;
 #pragma unroll
@@ -396,7 +403,9 @@ __global__ void stream_load_kernel(const float *__restrict__ llr, void *__restri
 // Streaming decode: the outputs of the frames that retired this step, written before the
 // step's passes overwrite their slots -- hard decisions (row fid of the caller's
 // [gamma][N] bytes, from the slots' packed decision words), iteration count and ok flag.
-// Block (package, word v); threads over the variables.
+// Block (package, word v); threads over the variables.  VEC: rows of hard start on 4-byte
+// boundaries (N a multiple of 4, hard 4-byte aligned), so each thread writes 4 decisions at once.
+template <bool VEC>
 __global__ void __launch_bounds__(256)
 stream_out_kernel(const uint32_t *__restrict__ hw, const uint32_t *__restrict__ sflags, const uint64_t *__restrict__ rfid,
                   const int *__restrict__ pend, uint8_t *__restrict__ hard, int32_t *__restrict__ iters,
@@ -412,12 +421,28 @@ stream_out_kernel(const uint32_t *__restrict__ hw, const uint32_t *__restrict__ 
         if (ok) ok[f] = pr & 1;
     }
     if (!hard) return;
-    for (int n = threadIdx.x; n < N; n += blockDim.x) {
-        const uint32_t w = hw[((size_t)pk * N + n) * V + v];
-        for (uint32_t b = R; b; b &= b - 1) {
-            const int ln = __ffs(b) - 1;
-            const uint64_t f = rfid[(size_t)pk * 32 * V + ln * V + v];
-            hard[f * (uint64_t)N + n] = (uint8_t)((w >> ln) & 1u);
+    if constexpr (VEC) {
+        for (int n4 = threadIdx.x; 4 * n4 < N; n4 += blockDim.x) {
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) w[e] = hw[((size_t)pk * N + 4 * n4 + e) * V + v];
+            for (uint32_t b = R; b; b &= b - 1) {
+                const int ln = __ffs(b) - 1;
+                const uint64_t f = rfid[(size_t)pk * 32 * V + ln * V + v];
+                uint32_t out = 0u;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) out |= ((w[e] >> ln) & 1u) << (8 * e);
+                reinterpret_cast<uint32_t *>(hard + f * (uint64_t)N)[n4] = out;
+            }
+        }
+    } else {
+        for (int n = threadIdx.x; n < N; n += blockDim.x) {
+            const uint32_t w = hw[((size_t)pk * N + n) * V + v];
+            for (uint32_t b = R; b; b &= b - 1) {
+                const int ln = __ffs(b) - 1;
+                const uint64_t f = rfid[(size_t)pk * 32 * V + ln * V + v];
+                hard[f * (uint64_t)N + n] = (uint8_t)((w >> ln) & 1u);
+            }
         }
     }
 }
@@ -514,14 +539,24 @@ ldpc_status qc_ber_sim_refill(ldpc_code c, double sigma, uint64_t seed, uint64_t
         ldpc_status e = LDPC_OK;
         if (io) {
             // the retiring frames' outputs, then the new frames' channel LLRs from the caller's rows
-            stream_out_kernel<<<dim3(P, V), 256, 0, s>>>(c->ws.hw, S->sflags, S->rfid, S->pend, io->hard, io->iters,
-                                                         io->ok, c->d.N, V);
-            if (i8)
-                stream_load_kernel<true><<<cblocks, 256, 0, s>>>(io->llr, S->mu, S->rlist, S->rcount, S->fid, c->d.N,
-                                                                 parity, 1e30f, ldexpf(1.0f, o.frac_bits));
+            const bool vin = (c->d.N % 4) == 0 && ((uintptr_t)io->llr & 15u) == 0;
+            const bool vout = (c->d.N % 4) == 0 && ((uintptr_t)io->hard & 3u) == 0;
+            if (vout)
+                stream_out_kernel<true><<<dim3(P, V), 256, 0, s>>>(c->ws.hw, S->sflags, S->rfid, S->pend, io->hard,
+                                                                   io->iters, io->ok, c->d.N, V);
             else
-                stream_load_kernel<false><<<cblocks, 256, 0, s>>>(io->llr, S->mu, S->rlist, S->rcount, S->fid, c->d.N,
-                                                                  parity, o.clip, 1.0f);
+                stream_out_kernel<false><<<dim3(P, V), 256, 0, s>>>(c->ws.hw, S->sflags, S->rfid, S->pend, io->hard,
+                                                                    io->iters, io->ok, c->d.N, V);
+            auto load = [&](auto kfn, float clip, float qs) {
+                kfn<<<cblocks, 256, 0, s>>>(io->llr, S->mu, S->rlist, S->rcount, S->fid, c->d.N, parity, clip, qs);
+            };
+            if (i8) {
+                if (vin) load(stream_load_kernel<true, true>, 1e30f, ldexpf(1.0f, o.frac_bits));
+                else load(stream_load_kernel<true, false>, 1e30f, ldexpf(1.0f, o.frac_bits));
+            } else {
+                if (vin) load(stream_load_kernel<false, true>, o.clip, 1.0f);
+                else load(stream_load_kernel<false, false>, o.clip, 1.0f);
+            }
             count_launch(2);
             parity ^= 1;
             const int slot_cn = prof_begin(0, s);

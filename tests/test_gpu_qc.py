@@ -332,16 +332,18 @@ def test_ber_sim_refill_equals_batch_decode(pkg, algo, msg, exact):
         assert abs(res["iters_sum"] - want["iters_sum"]) <= 0.02 * want["iters_sum"]
 
 
+@pytest.mark.parametrize("p", [64, 33])
 @pytest.mark.parametrize("algo", ["sp", "ms"])
-def test_streaming_decode_equals_batch_path(pkg, algo):
+def test_streaming_decode_equals_batch_path(pkg, algo, p):
     """ldpc_decode of more frames than twice its slot count streams the frames through the slots (early
     stop, no posteriors): every frame's decisions, iteration count and ok flag equal the batch path's
     (forced by asking for posteriors), with device buffers and with pinned host buffers read and
-    written through their device mapping."""
+    written through their device mapping.  n = 384 takes the 16-byte row loads and 4-byte decision
+    stores, n = 198 (not a multiple of 4) the element-wise ones."""
     A = {"sp": pkg.ALGO_SP, "ms": pkg.ALGO_MS}[algo]
     M = {"sp": pkg.MSG_F32, "ms": pkg.MSG_I8}[algo]
-    shifts = synth.qc_shifts(3, 6, 64, seed=1)
-    code = pkg.QCCode(shifts, 64)
+    shifts = synth.qc_shifts(3, 6, p, seed=1)
+    code = pkg.QCCode(shifts, p)
     o = pkg.default_opts(max_iter=25, early_stop=1, algo=A, msg=M)
     g = 2 * max(pkg.TUNE_SLOTS) + 37  # above twice any slot count the library may use
     llr = code.channel(1.75, 9, 5, g)
