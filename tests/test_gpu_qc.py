@@ -221,6 +221,29 @@ def test_fp16_storage_deviation(pkg):
     assert np.max(np.abs(post1 - p1) / np.maximum(1, np.abs(p1))) < 4e-3
 
 
+def test_fp16_storage_error_growth(pkg):
+    """FP16 message storage against the FP64 oracle, iteration by iteration: each stored message
+    (sign(beta) * phi(|beta|) * 2^12, or alpha) carries a relative rounding error of at most 2^-11,
+    and the posterior error grows from there.  Element-wise bound per iteration on the frames of
+    cfg1's shape at 2.5 dB (a waterfall-region mix of converging and unconverged frames), with the
+    measured figures kept in the parity summary."""
+    shifts = synth.qc_shifts(3, 6, 64, seed=1)
+    H, rp, col = _graph(shifts, 64)
+    code = pkg.QCCode(shifts, 64)
+    mu = synth.gaussian_llrs(128, code.N, seed=21, ebn0_db=2.5, rate=0.5)
+    x = torch.from_numpy(mu).cuda()
+    # about twice the measured deviations (1.6e-3, 3.0e-3, 3.6e-3, 4.8e-3, 6.1e-3: ~1.2e-3 more per
+    # iteration, a few storage roundings of 2^-11 each)
+    bound = {1: 4e-3, 2: 6e-3, 3: 8e-3, 4: 1e-2, 5: 1.25e-2}
+    for it, b in bound.items():
+        post = code.decode(x, max_iter=it, msg=pkg.MSG_F16)[0].cpu().numpy().astype(np.float64)
+        po = oracle.sp_decode(rp, col, code.N, mu, it, nthreads=8)[0]
+        rel = np.abs(post - po) / np.maximum(1.0, np.abs(po))
+        record_parity(f"FP16 storage, iteration {it}: GPU vs FP64", frames=128, arm_frames=0, arm_elems=0,
+                      elems=rel.size, max_rel=float(rel.max()))
+        assert rel.max() < b, (it, rel.max())
+
+
 def test_host_buffers(pkg):
     """Host (pageable and pinned) inputs and outputs are staged through the device workspace."""
     shifts = synth.qc_shifts(3, 6, 64, seed=1)
