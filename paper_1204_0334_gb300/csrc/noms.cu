@@ -79,7 +79,7 @@ __device__ __forceinline__ float sigmoidf(float x) {
 // forward check step: alpha^(l) from beta^(l-1); one warp = one row of one package
 // ---------------------------------------------------------------------------
 #ifndef NM_FWD_MINB
-#define NM_FWD_MINB 4  // resident blocks per SM of the forward check step (a 64-register budget)
+#define NM_FWD_MINB 5  // resident blocks per SM of the forward check step, rows of up to 24 edges (51 registers)
 #endif
 // REG: every block of the row is present and L == DCMAX, so the gathers carry no branches
 // and all DCMAX loads of a row are in flight together.  Only the two smallest magnitudes,
@@ -88,7 +88,7 @@ __device__ __forceinline__ float sigmoidf(float x) {
 // holds slot l's edge index and the gathers take it by shuffle.  From the channel LLRs
 // (FROM_MU, FP32) the frames of a lane word are done one after the other.
 template <int DCMAX, typename S, bool FROM_MU, bool REG>
-__global__ void __launch_bounds__(kWarps * 32, FROM_MU ? 3 : NM_FWD_MINB)
+__global__ void __launch_bounds__(kWarps * 32, FROM_MU ? 3 : (DCMAX > 24 ? 4 : NM_FWD_MINB))
 nm_cn_fwd(const QcDesc d, const void *__restrict__ bin, uint32_t *__restrict__ A, const float *__restrict__ prm_l,
           float clip, int P) {
     constexpr int V = Word<S>::V;
