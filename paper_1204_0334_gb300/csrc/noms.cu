@@ -68,11 +68,13 @@ template <> struct Word<__half> {
     }
 };
 
-// one exponential each: softplus(x) = max(x, 0) + log1p(e^-|x|); sigmoid from e = e^-|x|
+// one exponential each: softplus(x) = max(x, 0) + log1p(e^-|x|) (the loss, reported); sigmoid from
+// e = e^-|x| and a correctly rounded reciprocal of 1 + e (an adjoint: within an ulp or two)
 __device__ __forceinline__ float softplusf(float x) { return fmaxf(x, 0.0f) + log1pf(__expf(-fabsf(x))); }
 __device__ __forceinline__ float sigmoidf(float x) {
     const float e = __expf(-fabsf(x));
-    return x >= 0.0f ? 1.0f / (1.0f + e) : e / (1.0f + e);
+    const float r = __frcp_rn(1.0f + e);
+    return x >= 0.0f ? r : e * r;
 }
 
 // ---------------------------------------------------------------------------
