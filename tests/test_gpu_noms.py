@@ -124,6 +124,36 @@ def test_noms_fp16_storage_gradient(pkg, J, L, p):
     assert rel.max() <= 1e-3, rel.max()
 
 
+@pytest.mark.parametrize("msg", [0, 1])
+def test_noms_gradient_with_zero_blocks(pkg, msg):
+    """A base matrix with zero blocks (rows of 8 slots with some absent, columns of 2 to 4 edges):
+    loss and gradient against the oracle (FP16 against its binary16 variant), element by element."""
+    J, L, p = 4, 8, 16
+    shifts = synth.qc_shifts(J, L, p, seed=6, zero_blocks=5)
+    H = oracle.qc_parity_check(shifts, p)
+    rp, col = oracle.csr_rows(H)
+    cb = oracle.circulant_index(rp, col, p, L)
+    assert (np.asarray(shifts) < 0).sum() == 5
+    code = pkg.QCCode(shifts, p)
+    T, B = 4, 70
+    prm = rand_params(T, J * L, 13)
+    mu = synth.gaussian_llrs(B, code.N, seed=14, ebn0_db=1.5, rate=0.5)
+    prm_d = torch.from_numpy(prm).cuda()
+    loss, post = pkg.ldpc_noms_forward(code.handle, torch.from_numpy(mu).cuda(), prm_d, msg, 2, 30.0, True)
+    grad = torch.zeros_like(prm_d)
+    pkg.ldpc_noms_backward(code.handle, prm_d, grad)
+    lo, po, go = oracle.noms(rp, col, cb, code.N, mu, T, prm.astype(np.float64), want_grad=True, nthreads=8,
+                             store16=bool(msg))
+    assert abs(float(loss) - lo) <= 1e-5 * abs(lo)
+    assert np.max(np.abs(post.cpu().numpy() - po) / np.maximum(1, np.abs(po))) < 1e-4
+    g = grad.cpu().numpy().astype(np.float64)
+    rel = np.abs(g - go) / np.maximum(np.abs(go), 1e-3 * np.abs(go).max())
+    # circulants of zero blocks have no edges: no gradient on either side
+    zb = (np.asarray(shifts).reshape(-1) < 0)
+    assert np.all(g[:, zb, :] == 0.0) and np.all(go[:, zb, :] == 0.0)
+    assert rel.max() <= 1e-3, rel.max()
+
+
 def test_noms_fp16_gradient_ten_iterations(pkg):
     """The training configuration's depth (10 unrolled iterations, a checkpoint every 2) on a code with
     full rows of 24 edges, FP16 messages against the oracle's binary16 variant, element by element."""
