@@ -6,14 +6,14 @@
 //   loss = 1/(T N B) sum_l sum_n softplus(-post^(l)_n)
 // (BCE of every iteration's posterior against the all-zero codeword).
 //
-// Layout: packages of 32 frames, one frame per lane, msg-like buffers
-// [P][E][32] (edge order of the block decoder: edge k of block (j, l) is
-// variable l*p + k).  Betas are kept at checkpoints every k iterations in the
-// storage type S (float or half), and so are the alphas; adjoints in float.  The backward
-// pass recomputes each segment of k iterations from its checkpoint.  The forward
-// also keeps every iteration's posteriors ([T][P][N][32] floats): with them and
-// beta^(l) the backward variable step needs nothing of alpha^(l), so the check
-// messages are never recomputed.
+// Layout: packages of 32 V frames, V = 1 for FP32 messages and 2 for binary16 (two
+// frames per 32-bit lane word, the FP16 decoder's layout); message buffers [P][E][32]
+// lane words (edge order of the block decoder: edge k of block (j, l) is variable
+// l*p + k), per-frame FP32 arrays [P][..][32][V].  Betas are kept at checkpoints every
+// k iterations in the storage type S (float or half), and so are the alphas; adjoints in
+// float.  The backward pass recomputes each segment of k iterations from its checkpoint.
+// The forward also keeps every iteration's posteriors: with them and beta^(l) the backward
+// variable step needs nothing of alpha^(l), so the check messages are never recomputed.
 #include "qc_device.cuh"
 
 #include <algorithm>
@@ -23,17 +23,17 @@ struct ldpc_noms_state {
     int B = 0, T = 0, k = 1, P = 0, msg = LDPC_MSG_F32;
     float clip = 30.0f;
     size_t cap_frames = 0, cap_nck = 0, cap_seg = 0;
-    float *mu = nullptr;       // [P][N][32]
+    float *mu = nullptr;       // [P][N][32 V]
     void *ping[2] = {nullptr, nullptr};  // non-checkpoint betas (S)
-    void *ckpt = nullptr;      // [nck][P][E][32] (S): beta^(k), beta^(2k), ...
-    void *seg = nullptr;       // [k][P][E][32] (S): recomputed betas of one segment
+    void *ckpt = nullptr;      // [nck][P][E][32] lane words: beta^(k), beta^(2k), ...
+    void *seg = nullptr;       // [k][P][E][32] lane words: recomputed betas of one segment
     float *A = nullptr, *GA = nullptr;  // [P][E][32 V] (A holds lane words)
     // adjoint of beta^(l-1), nonzero only on the two smallest inputs of each row and frame: per
     // row and lane a word of their slots ([P][M][32]: int8 i1, i2 per frame) and their values
     // ([P][M][2][32 V] floats)
     uint32_t *GBs = nullptr;
     float *GBv = nullptr;
-    float *posts = nullptr;    // [T][P][N][32] (stride N * cap_frames): post^(1..T) of the forward
+    float *posts = nullptr;    // [T][P][N][32 V] (stride N * cap_frames): post^(1..T) of the forward
     size_t cap_T = 0;
     double *acc = nullptr;     // loss: one partial sum per variable-step block, [P][ceil(N / 8)]
     bool have_forward = false;
